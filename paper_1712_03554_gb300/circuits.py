@@ -1,0 +1,281 @@
+"""Seeded synthetic circuit generators and a simulator-agnostic driver.
+
+This module holds no simulation arithmetic: it only builds gate lists (plain
+Python tuples) from a seed and walks them against any object exposing the
+stabilizer-frame calls (``apply_clifford``, ``apply_nonclifford``,
+``coalesce``, ``measure``).  Both the CUDA path and the CPU oracle are driven
+through it, so the two always see the same inputs.
+
+Op encoding (one tuple per op):
+  ("C", kind, q0, q1)              Clifford gate, kind in CLIFFORD_KINDS
+  ("N", kind, q0, q1, theta)       diagonal non-Clifford gate, kind in NONCLIFFORD_KINDS
+  ("K",)                           coalesce the frame
+  ("M", q, u)                      measure qubit q; outcome = 1 if u < p(1) else 0
+                                   (u is a seeded uniform draw, or None for
+                                   "probabilities only")
+
+Gate semantics follow the paper: H, P (= S) and CNOT are the Clifford gates of
+Table 2 (Sec. II-B); T/T-dagger are the technology-dependent non-Clifford gates
+of Sec. IV; controlled-R(alpha) is Eq. 3.  The Toffoli is expanded into
+Clifford+T as the paper does for its "Clifford+T" rows (Sec. VI, Toffoli
+decomposition), using the textbook 7-T network.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+# ---- gate kind codes (must match include/sf.h) --------------------------------
+H, S, SDG, X, Y, Z, CNOT, CZ, SWAP = range(9)
+CLIFFORD_KINDS = {"H": H, "S": S, "SDG": SDG, "X": X, "Y": Y, "Z": Z,
+                  "CNOT": CNOT, "CZ": CZ, "SWAP": SWAP}
+TWO_QUBIT_CLIFFORD = {CNOT, CZ, SWAP}
+T, TDG, PHASE, CPHASE = range(4)
+NONCLIFFORD_KINDS = {"T": T, "TDG": TDG, "PHASE": PHASE, "CPHASE": CPHASE}
+
+Op = Tuple
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    """Every workload draws from numpy's PCG64 seeded with an integer."""
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# ---- building blocks ------------------------------------------------------------
+def toffoli_clifford_t(a: int, b: int, c: int) -> List[Op]:
+    """Toffoli(controls a, b; target c) as 2 H + 6 CNOT + 7 T/T-dagger.
+
+    The textbook network (the decomposition the paper's "Clifford+T" table rows
+    use, Sec. VI).  Its 8x8 unitary is checked against the Toffoli in the dense
+    oracle tests.
+    """
+    return [
+        ("C", H, c, 0),
+        ("C", CNOT, b, c), ("N", TDG, c, 0, 0.0),
+        ("C", CNOT, a, c), ("N", T, c, 0, 0.0),
+        ("C", CNOT, b, c), ("N", TDG, c, 0, 0.0),
+        ("C", CNOT, a, c), ("N", T, b, 0, 0.0), ("N", T, c, 0, 0.0),
+        ("C", H, c, 0),
+        ("C", CNOT, a, b), ("N", T, a, 0, 0.0), ("N", TDG, b, 0, 0.0),
+        ("C", CNOT, a, b),
+    ]
+
+
+def with_coalesce_after_nonclifford(ops: Sequence[Op]) -> List[Op]:
+    out: List[Op] = []
+    for op in ops:
+        out.append(op)
+        if op[0] == "N":
+            out.append(("K",))
+    return out
+
+
+# ---- workload 1: random Clifford+T on 8 qubits ------------------------------------
+def random_clifford_t(n: int = 8, n_gates: int = 200, n_t: int = 4, seed: int = 0,
+                      t_kinds: Sequence[int] = (T,)) -> List[Op]:
+    """n qubits from |0..0>, n_gates gates of which exactly n_t are T at distinct
+    uniform positions; the rest uniform over {H, S, CNOT}, one-qubit targets
+    uniform over the qubits, CNOT ordered pairs uniform over the n(n-1) pairs.
+    A coalesce follows every T."""
+    g = rng_for(seed)
+    t_pos = set(int(p) for p in g.choice(n_gates, size=n_t, replace=False))
+    ops: List[Op] = []
+    for i in range(n_gates):
+        if i in t_pos:
+            kind = t_kinds[int(g.integers(len(t_kinds)))]
+            ops.append(("N", kind, int(g.integers(n)), 0, 0.0))
+            ops.append(("K",))
+            continue
+        kind = (H, S, CNOT)[int(g.integers(3))]
+        if kind == CNOT and n >= 2:
+            c = int(g.integers(n))
+            t = int(g.integers(n - 1))
+            t = t + 1 if t >= c else t
+            ops.append(("C", CNOT, c, t))
+        else:
+            ops.append(("C", kind if kind != CNOT else H, int(g.integers(n)), 0))
+    return ops
+
+
+def random_clifford(n: int, n_gates: int, seed: int,
+                    kinds: Sequence[int] = (H, S, CNOT)) -> List[Op]:
+    """Random stabilizer circuit over the given Clifford kinds (no non-Clifford)."""
+    g = rng_for(seed)
+    ops: List[Op] = []
+    for _ in range(n_gates):
+        kind = kinds[int(g.integers(len(kinds)))]
+        if kind in TWO_QUBIT_CLIFFORD:
+            if n < 2:
+                continue
+            c = int(g.integers(n))
+            t = int(g.integers(n - 1))
+            t = t + 1 if t >= c else t
+            ops.append(("C", kind, c, t))
+        else:
+            ops.append(("C", kind, int(g.integers(n)), 0))
+    return ops
+
+
+# ---- workload 2: QFT on a basis state ------------------------------------------------
+def qft_phase(k: int) -> float:
+    """R_k = diag(1, exp(2 pi i / 2^k)); k = distance + 1 (paper Sec. VI, QFT)."""
+    return 2.0 * math.pi / float(1 << k) if k < 1024 else 0.0
+
+
+def qft(n: int, x: int, coalesce: bool = True) -> List[Op]:
+    """X gates prepare |x> (bit q of x is qubit q), then the swap-free QFT:
+    for j = 0..n-1: H on j, then controlled-R_k (k = 2..n-j) with control
+    j+k-1 and target j.  n(n+1)/2 gates after the preparation."""
+    ops: List[Op] = [("C", X, q, 0) for q in range(n) if (x >> q) & 1]
+    for j in range(n):
+        ops.append(("C", H, j, 0))
+        for k in range(2, n - j + 1):
+            ops.append(("N", CPHASE, j + k - 1, j, qft_phase(k)))
+            if coalesce:
+                ops.append(("K",))
+    return ops
+
+
+def qft_random_input(n: int = 20, seed: int = 0) -> Tuple[int, List[Op]]:
+    g = rng_for(seed)
+    x = int(g.integers(0, 1 << n)) if n < 63 else int(g.integers(0, 1 << 62))
+    return x, qft(n, x)
+
+
+def qft_expected_amplitude(n: int, x: int, y: int) -> complex:
+    """Closed form of the swap-free QFT output (Sec. VI, QFT equation), read
+    with qubit j (0-based, the j-th to get its H) ending in
+    (|0> + exp(2 pi i 0.x_j x_{j+1} ... x_{n-1}) |1>)/sqrt(2), where x_j is bit j of x."""
+    amp = 1.0 + 0.0j
+    for j in range(n):
+        frac = 0.0
+        for m, q in enumerate(range(j, n)):
+            if (x >> q) & 1:
+                frac += 2.0 ** (-(m + 1))
+        if (y >> j) & 1:
+            amp *= complex(math.cos(2 * math.pi * frac), math.sin(2 * math.pi * frac))
+    return amp / math.sqrt(2.0 ** n)
+
+
+# ---- workload 3: Cuccaro ripple-carry adder -------------------------------------------
+def cuccaro_layout(nbits: int):
+    """Qubit 0 = ancilla (carry-in), then interleaved b_i, a_i for i = 0..nbits-1,
+    then the carry-out z.  Returns (anc, a[], b[], z)."""
+    anc = 0
+    b = [1 + 2 * i for i in range(nbits)]
+    a = [2 + 2 * i for i in range(nbits)]
+    z = 2 * nbits + 1
+    return anc, a, b, z
+
+
+def cuccaro_classical_ops(nbits: int):
+    """The reversible network as ('cnot', c, t) / ('tof', c1, c2, t) records:
+    MAJ blocks up the chain, a CNOT into the carry, UMA blocks down."""
+    anc, a, b, z = cuccaro_layout(nbits)
+    net = []
+
+    def maj(c, bb, aa):
+        net.extend([("cnot", aa, bb), ("cnot", aa, c), ("tof", c, bb, aa)])
+
+    def uma(c, bb, aa):
+        net.extend([("tof", c, bb, aa), ("cnot", aa, c), ("cnot", c, bb)])
+
+    maj(anc, b[0], a[0])
+    for i in range(1, nbits):
+        maj(a[i - 1], b[i], a[i])
+    net.append(("cnot", a[nbits - 1], z))
+    for i in range(nbits - 1, 0, -1):
+        uma(a[i - 1], b[i], a[i])
+    uma(anc, b[0], a[0])
+    return net
+
+
+def cuccaro(nbits: int, superpose: bool = True, a_val: int = 0, b_val: int = 0,
+            coalesce: bool = True) -> List[Op]:
+    """Cuccaro adder with every Toffoli as Clifford+7T.  With superpose=True the
+    inputs are H on every a and b qubit (the paper's benchmark, Sec. VI);
+    otherwise X gates load the basis inputs a_val, b_val."""
+    anc, a, b, z = cuccaro_layout(nbits)
+    ops: List[Op] = []
+    if superpose:
+        ops += [("C", H, q, 0) for q in a + b]
+    else:
+        ops += [("C", X, a[i], 0) for i in range(nbits) if (a_val >> i) & 1]
+        ops += [("C", X, b[i], 0) for i in range(nbits) if (b_val >> i) & 1]
+    for rec in cuccaro_classical_ops(nbits):
+        if rec[0] == "cnot":
+            ops.append(("C", CNOT, rec[1], rec[2]))
+        else:
+            ops += toffoli_clifford_t(rec[1], rec[2], rec[3])
+    return with_coalesce_after_nonclifford(ops) if coalesce else ops
+
+
+def cuccaro_reference(nbits: int, a_val: int, b_val: int) -> int:
+    """Run the reversible network on classical bits; return the output basis index."""
+    anc, a, b, z = cuccaro_layout(nbits)
+    nq = 2 * nbits + 2
+    bits = [0] * nq
+    for i in range(nbits):
+        bits[a[i]] = (a_val >> i) & 1
+        bits[b[i]] = (b_val >> i) & 1
+    for rec in cuccaro_classical_ops(nbits):
+        if rec[0] == "cnot":
+            bits[rec[2]] ^= bits[rec[1]]
+        else:
+            bits[rec[3]] ^= bits[rec[1]] & bits[rec[2]]
+    return sum(bit << q for q, bit in enumerate(bits))
+
+
+def cuccaro_sample_ops(nbits: int, seed: int) -> List[Op]:
+    """Measure every qubit in order with seeded uniform draws (sampling)."""
+    g = rng_for(seed)
+    return [("M", q, float(g.random())) for q in range(2 * nbits + 2)]
+
+
+# ---- driver ------------------------------------------------------------------------
+def run(sim, ops: Sequence[Op], drop_eps: float = 1e-12, batch_cliffords: bool = True):
+    """Walk ops against sim.  Consecutive Clifford gates are passed as one batch.
+    Returns the list of (q, p0, p1, outcome) for every measurement."""
+    pending: List[Tuple[int, int, int]] = []
+    results = []
+
+    def flush():
+        if pending:
+            sim.apply_clifford(list(pending))
+            pending.clear()
+
+    for op in ops:
+        tag = op[0]
+        if tag == "C":
+            pending.append((op[1], op[2], op[3]))
+            if not batch_cliffords:
+                flush()
+        elif tag == "N":
+            flush()
+            sim.apply_nonclifford(op[1], op[2], op[3], op[4])
+        elif tag == "K":
+            flush()
+            sim.coalesce(drop_eps)
+        elif tag == "M":
+            flush()
+            q, u = op[1], op[2]
+            p0, p1 = sim.measure(q, -1)
+            if u is None:
+                results.append((q, p0, p1, None))
+            else:
+                x = 1 if u < p1 else 0
+                sim.measure(q, x)
+                results.append((q, p0, p1, x))
+        else:
+            raise ValueError(f"unknown op {op!r}")
+    flush()
+    return results
+
+
+def count_ops(ops: Sequence[Op]):
+    c = {"C": 0, "N": 0, "K": 0, "M": 0}
+    for op in ops:
+        c[op[0]] += 1
+    return c
