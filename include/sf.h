@@ -1,0 +1,187 @@
+/*
+ * sf.h -- C ABI of libsf: a stabilizer-frame simulator that keeps one shared
+ * canonical stabilizer tableau and a frame of (phase vector, FP64 amplitude)
+ * pairs resident on one GPU (GB300, sm_103a).
+ *
+ * Model (Garcia & Markov, "Simulation of Quantum Circuits via Stabilizer
+ * Frames"):
+ *   - A stabilizer frame F = (M, {sigma_j}) (Def. 1, Sec. III) is an n x 2n
+ *     binary tableau M of n commuting Pauli rows plus k distinct phase vectors
+ *     sigma_j in {+1,-1}^n.  State j is M with the row signs set to sigma_j.
+ *     The represented state is Psi = sum_j a_j |psi_j> with FP64 complex a_j.
+ *   - M is kept in row-reduced echelon form after every operation
+ *     (Invariant 1, Sec. III): columns ordered x_0..x_{n-1}, z_0..z_{n-1};
+ *     rows with an X/Y literal first (X-block), then Z/I-only rows (Z-block).
+ *   - Pauli literals use two bits per qubit, 00=I 01=Z 10=X 11=Y (Sec. II-B).
+ *
+ * Conventions shared by every entry point:
+ *   - Qubit q is bit q of a basis index (qubit 0 = least significant bit).
+ *     W = ceil(n/64) 64-bit words hold one row half or one phase vector; bit r
+ *     of word r/64 is row r.  sigma bit r = 1 means the sign of row r is -1.
+ *   - Exported amplitudes follow one canonical phase convention: psi_j has
+ *     amplitude 2^{-r/2} (real, positive) at its anchor, the basis state in its
+ *     support whose bits at every X-block pivot qubit are 0 (r = X-block size).
+ *     With this convention the exported frame is unique for a given state.
+ *   - Ownership: a handle owns all of its device memory.  Host pointers passed
+ *     in are owned by the caller and are only read or written during the call.
+ *   - Errors: every entry point returns an sf_status; no C++ exception crosses
+ *     the ABI.  sf_last_error() gives a message.
+ *   - Asynchrony: calls are stream-ordered on the handle's CUDA stream and
+ *     return without waiting for the GPU unless marked "synchronises".
+ *     Errors found on the device (capacity exceeded, an internal check) are
+ *     deferred: the failing kernel leaves the frame as it was before that
+ *     call, every later kernel of the handle does nothing until the error is
+ *     reported, and the next synchronising call returns it and clears it.
+ *     The frame is then the one from before the failing call; asynchronous
+ *     calls made between the failure and the report were dropped.
+ *   - Threads: a handle is not thread-safe.  Distinct handles on distinct
+ *     streams are independent.
+ */
+#ifndef SF_ABI_H_
+#define SF_ABI_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sf_frame_s* sf_handle;
+
+typedef enum {
+    SF_OK = 0,
+    SF_EINVAL = 1,     /* bad argument (qubit out of range, q0 == q1, unknown kind, NULL) */
+    SF_ENOMEM = 2,     /* device or pinned host allocation failed */
+    SF_ECAPACITY = 3,  /* a branch or cofactor would exceed max_elems */
+    SF_ECUDA = 4,      /* a CUDA runtime call failed */
+    SF_ETIMEOUT = 5,   /* a bounded device wait ran out (hash probe limit) */
+    SF_ESTATE = 6,     /* operation invalid in the current state (e.g. collapse onto p = 0) */
+    SF_EINTERNAL = 7   /* a device-side consistency check of the tableau algebra failed */
+} sf_status;
+
+/* Clifford gate kinds.  H, S (the paper's P) and CNOT are Table 2 of the paper;
+ * the rest are products of those. */
+enum { SF_H = 0, SF_S = 1, SF_SDG = 2, SF_X = 3, SF_Y = 4, SF_Z = 5,
+       SF_CNOT = 6 /* control q0, target q1 */, SF_CZ = 7, SF_SWAP = 8 };
+
+typedef struct { uint32_t kind, q0, q1, pad; } sf_gate; /* q1 ignored for one-qubit kinds */
+
+/* Diagonal non-Clifford kinds (Sec. IV). */
+enum { SF_T = 0,      /* diag(1, e^{i pi/4}) on q0 */
+       SF_TDG = 1,    /* diag(1, e^{-i pi/4}) on q0 */
+       SF_PHASE = 2,  /* diag(1, e^{i theta}) on q0 */
+       SF_CPHASE = 3  /* controlled phase R(theta), Eq. 3: diag(1,1,1,e^{i theta}) on (q0, q1) */ };
+
+/* Create a frame for |0...0> (M = RREF{Z_0..Z_{n-1}}, one element sigma = 0,
+ * a = 1) on `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ * 1 <= n_qubits <= 1024.  max_elems bounds the number of frame elements that
+ * any step may hold, including the children of a branch before coalescing.
+ * Device memory: about max_elems * (16 W + 56) bytes plus O(n^2) for the
+ * tableau.  Synchronises. */
+sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf_handle* out);
+
+/* Free all device and host memory of the handle.  Synchronises. */
+sf_status sf_destroy(sf_handle h);
+
+/* Back to |0...0>, discarding any unreported device error.  Asynchronous. */
+sf_status sf_reset(sf_handle h);
+
+/* ROTATE(F, U) for each gate in order (Sec. III): the tableau is conjugated
+ * (Table 2), restored to RREF (Invariant 1), and every phase vector receives
+ * the resulting affine GF(2) update.  `gates` is a host array of n_gates
+ * records, copied before return.  Asynchronous. */
+sf_status sf_apply_clifford(sf_handle h, const sf_gate* gates, uint64_t n_gates);
+
+/* As sf_apply_clifford, with `dev_gates` already in device memory (it must
+ * stay valid until the stream reaches this call).  Suitable for stream
+ * capture into a CUDA graph.  Asynchronous. */
+sf_status sf_apply_clifford_device(sf_handle h, const sf_gate* dev_gates, uint64_t n_gates);
+
+/* Diagonal non-Clifford gate (Sec. IV): every element branches into at most
+ * two (one-qubit kinds) or four (SF_CPHASE) children along the
+ * anticommutation masks of the gate's Z-type Pauli terms.  Children are NOT
+ * merged: call sf_coalesce afterwards.  theta is used by SF_PHASE and
+ * SF_CPHASE only.  Asynchronous; exceeding max_elems is reported by the next
+ * synchronising call. */
+sf_status sf_apply_nonclifford(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta);
+
+/* Merge elements with equal phase vectors (summing amplitudes) and drop those
+ * with |a| < drop_eps (Def. 1: the phase vectors of a frame are distinct).
+ * If out_size is non-NULL the new frame size is written there and the call
+ * synchronises; otherwise it is asynchronous. */
+sf_status sf_coalesce(sf_handle h, double drop_eps, uint64_t* out_size);
+
+/* Measurement of qubit q in the computational basis (Sec. IV, "Measuring F").
+ * If q is random in M the frame is first cofactored on q (COFACTOR, Sec. III):
+ * M becomes RREF({rows commuting with Z_q} + {Z_q}), each element splits into
+ * its two cofactors, and the frame is coalesced with drop_eps = 1e-12.  Then
+ * p0/p1 (nullable) receive the outcome probabilities.  collapse_to = 0 or 1
+ * keeps only the consistent states and renormalises; -1 leaves the state
+ * as is (it is still cofactored).  Synchronises. */
+sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, double* p1);
+
+/* <x|Psi> for the basis state x given as W host words (bit q = qubit q),
+ * Observation 1 evaluated on the canonical tableau.  Synchronises. */
+sf_status sf_amplitude(sf_handle h, const uint64_t* x_bits, double* re, double* im);
+
+/* Current frame size (number of elements).  Synchronises. */
+sf_status sf_size(sf_handle h, uint64_t* k);
+
+/* Wait for all queued work and report any sticky device error.  Synchronises. */
+sf_status sf_sync(sf_handle h);
+
+/* Export the canonical tableau: x and z are n*W words each, row-major (row h
+ * occupies words [h*W, h*W+W)); n_xblock receives the X-block size r.
+ * Synchronises. */
+sf_status sf_get_tableau(sf_handle h, uint64_t* x, uint64_t* z, uint32_t* n_xblock);
+
+/* Export the frame in the canonical amplitude convention, sorted ascending by
+ * phase vector read as a W-word integer (word W-1 most significant).  sigma
+ * receives k*W words (element j at [j*W, j*W+W)), amp receives 2k doubles
+ * (re, im).  k receives the frame size; if it exceeds `capacity` nothing is
+ * written and SF_ECAPACITY is returned.  Call after sf_coalesce.
+ * Synchronises. */
+sf_status sf_get_frame(sf_handle h, uint64_t* sigma, double* amp, uint64_t capacity, uint64_t* k);
+
+/* Kernel classes of this library, for sf_time_kernel(). */
+enum { SF_K_CLIFFORD = 0,      /* tableau update of a Clifford batch (single CTA) */
+       SF_K_AFFINE = 1,        /* per-element affine phase-vector update */
+       SF_K_BRANCH_PREP = 2,   /* anticommutation masks of a diagonal gate (single CTA) */
+       SF_K_BRANCH = 3,        /* per-element branching */
+       SF_K_COAL_CLEAR = 4, SF_K_COAL_INSERT = 5, SF_K_COAL_ACCUM = 6,
+       SF_K_COUNT = 7, SF_K_SCAN = 8, SF_K_SCATTER = 9,  /* stream compaction */
+       SF_K_MEASURE_PREP = 10, /* cofactor planning (single CTA) */
+       SF_K_COFACTOR = 11,     /* per-element cofactor split */
+       SF_K_PROB = 12, SF_K_REDUCE = 13, SF_K_AMP_PREP = 14, SF_K_AMPLITUDE = 15,
+       SF_K_EXPORT = 16, SF_K_RESET = 17, SF_K_COUNT_CLASSES = 18 };
+
+/* Number of CUDA kernels this handle has launched since it was created. */
+uint64_t sf_kernel_launches(sf_handle h);
+
+/* From now on, bracket every launch of kernel class kernel_id (SF_K_*) with a
+ * pair of CUDA events on the handle's stream; -1 stops.  Resets the totals
+ * returned by sf_kernel_time.  Asynchronous. */
+sf_status sf_time_kernel(sf_handle h, int32_t kernel_id);
+
+/* Device time in milliseconds summed over the bracketed launches, and their
+ * number, since the last sf_time_kernel.  Synchronises. */
+sf_status sf_kernel_time(sf_handle h, double* total_ms, uint64_t* launches);
+
+/* The device-side representation, for tests: destabilizer row h is
+ * i^{de[h]} P(dx_h, dz_h) (rows laid out as in sf_get_tableau, de has n
+ * entries) and g (2 doubles) is the global phase.  Frame element (sigma, a)
+ * stands for g a D^sigma phi_0(M), phi_0 being the state stabilized by +M with
+ * <0|phi_0> = 2^{-r/2}.  Synchronises. */
+sf_status sf_get_internal(sf_handle h, uint64_t* dx, uint64_t* dz, uint32_t* de, double* g);
+
+/* Words per phase vector / row half used by this handle (ceil(n/64)). */
+uint32_t sf_words(sf_handle h);
+
+/* Message for the last error of the handle; NULL handle -> last global error. */
+const char* sf_last_error(sf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SF_ABI_H_ */

@@ -1,0 +1,540 @@
+// sf_api.cu -- the extern "C" boundary of libsf (declared in include/sf.h):
+// handle lifetime, device memory, argument checks, the launch sequence of each
+// operation and the synchronising reads.  All arithmetic of the method runs in
+// the kernels of sf_tableau.cu and sf_frame.cu.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "sf.h"
+#include "sf_device.cuh"
+
+struct sf_frame_s {
+    uint32_t n = 0;
+    int Wabi = 1;
+    SfDev d{};
+    cudaStream_t stream = nullptr;
+    int cur = 0;
+    uint64_t* gws = nullptr;
+    sf_gate_rec* dgates = nullptr;
+    size_t dgates_cap = 0;
+    sf_gate_rec* hstage = nullptr;
+    size_t hstage_cap = 0;
+    cudaEvent_t stage_ev = nullptr;
+    uint64_t* dy = nullptr;
+    uint64_t* hy = nullptr;
+    unsigned long long* hk = nullptr;
+    uint32_t* hstatus = nullptr;
+    double* hout = nullptr;
+    int32_t* hmeta = nullptr;
+    std::vector<void*> dallocs;
+    std::string err;
+    uint64_t launches = 0;
+    int time_id = -1;
+    std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
+    size_t ev_used = 0;
+    double time_ms = 0.0;
+    uint64_t time_count = 0;
+};
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_err;
+
+sf_status fail(sf_handle h, sf_status code, const std::string& msg) {
+    if (h) h->err = msg;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_err = msg;
+    return code;
+}
+
+sf_status cuda_fail(sf_handle h, cudaError_t e, const char* what) {
+    return fail(h, SF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SF_CK(h, call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+int pow2_at_least(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <typename T>
+cudaError_t dalloc(sf_handle h, T** p, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        h->dallocs.push_back(v);
+        *p = static_cast<T*>(v);
+    }
+    return e;
+}
+
+const char* status_text(uint32_t code) {
+    switch (code) {
+        case SF_EINVAL: return "invalid gate in a device gate list";
+        case SF_ECAPACITY: return "frame would exceed max_elems";
+        case SF_ETIMEOUT: return "hash probe limit reached during coalescing";
+        case SF_ESTATE: return "invalid state";
+        case SF_EINTERNAL: return "device-side consistency check of the tableau algebra failed";
+        default: return "device error";
+    }
+}
+
+// Launch one kernel of class `id`: count it and, when that class is being
+// timed, bracket it with a pair of events from the handle's pool.
+template <typename F>
+sf_status launch(sf_handle h, int id, const char* what, F&& fn) {
+    const bool timed = (h->time_id == id);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) {
+        while (h->ev_pool.size() < 2 * (h->ev_used + 1)) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(h, SF_ECUDA, "event creation failed");
+            h->ev_pool.push_back(e);
+        }
+        e0 = h->ev_pool[2 * h->ev_used];
+        e1 = h->ev_pool[2 * h->ev_used + 1];
+        h->ev_used++;
+        cudaEventRecord(e0, h->stream);
+    }
+    fn();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    if (timed) cudaEventRecord(e1, h->stream);
+    h->launches++;
+    return SF_OK;
+}
+
+#define SF_LAUNCH(h, id, call)                                  \
+    do {                                                        \
+        sf_status s_ = launch((h), (id), #call, [&] { call; }); \
+        if (s_ != SF_OK) return s_;                             \
+    } while (0)
+
+// wait for the stream and report a deferred device error, restoring the frame
+// buffer that was current when it happened and clearing the error
+sf_status sync_check(sf_handle h) {
+    SF_CK(h, cudaMemcpyAsync(h->hstatus, h->d.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaStreamSynchronize(h->stream));
+    const uint32_t st = *h->hstatus;
+    if (st) {
+        h->cur = (int)((st >> 8) & 1u);
+        SF_CK(h, cudaMemsetAsync(h->d.status, 0, sizeof(uint32_t), h->stream));
+        SF_CK(h, cudaStreamSynchronize(h->stream));
+        const uint32_t code = SF_ST_CODE(st);
+        char site[32];
+        snprintf(site, sizeof(site), " (check %u)", st >> 16);
+        return fail(h, (sf_status)code, std::string(status_text(code)) + site);
+    }
+    return SF_OK;
+}
+
+sf_status coalesce_seq(sf_handle h, double eps, int in_buf, int out_buf) {
+    const SfDev& d = h->d;
+    cudaStream_t s = h->stream;
+    SF_LAUNCH(h, SF_K_COAL_CLEAR, sf_launch_coal_clear(d, in_buf, s));
+    SF_LAUNCH(h, SF_K_COAL_INSERT, sf_launch_coal_insert(d, in_buf, s));
+    SF_LAUNCH(h, SF_K_COAL_ACCUM, sf_launch_coal_accum(d, in_buf, s));
+    SF_LAUNCH(h, SF_K_COUNT, sf_launch_count(d, in_buf, 0, eps * eps, 0, s));
+    SF_LAUNCH(h, SF_K_SCAN, sf_launch_scan(d, out_buf, s));
+    SF_LAUNCH(h, SF_K_SCATTER, sf_launch_scatter(d, in_buf, out_buf, 0, eps * eps, 0, s));
+    return SF_OK;
+}
+
+bool one_qubit(uint32_t kind) { return kind <= SF_Z; }
+
+sf_status check_gate(sf_handle h, const sf_gate& g) {
+    if (g.kind > SF_SWAP) return fail(h, SF_EINVAL, "unknown Clifford kind");
+    if (g.q0 >= h->n) return fail(h, SF_EINVAL, "qubit out of range");
+    if (!one_qubit(g.kind) && (g.q1 >= h->n || g.q1 == g.q0)) return fail(h, SF_EINVAL, "bad second qubit");
+    return SF_OK;
+}
+
+sf_status run_clifford(sf_handle h, const sf_gate_rec* dev, uint64_t ng) {
+    const uint64_t chunk = 1u << 20;
+    for (uint64_t off = 0; off < ng; off += chunk) {
+        const int m = (int)std::min<uint64_t>(chunk, ng - off);
+        SF_LAUNCH(h, SF_K_CLIFFORD, sf_launch_clifford(h->d, dev + off, m, h->cur, h->gws, h->stream));
+        // the affine map of each chunk is applied before the next chunk overwrites it
+        SF_LAUNCH(h, SF_K_AFFINE, sf_launch_affine(h->d, h->cur, h->stream));
+    }
+    return SF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf_handle* out) {
+    if (!out) return fail(nullptr, SF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > SF_MAX_N) return fail(nullptr, SF_EINVAL, "n_qubits must be in [1, 1024]");
+    if (max_elems < 1 || max_elems > (1ull << 31)) return fail(nullptr, SF_EINVAL, "max_elems must be in [1, 2^31]");
+    sf_handle h = new (std::nothrow) sf_frame_s();
+    if (!h) return fail(nullptr, SF_ENOMEM, "host allocation failed");
+    h->n = n_qubits;
+    h->Wabi = (int)((n_qubits + 63) / 64);
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    SfDev& d = h->d;
+    d.n = (int)n_qubits;
+    d.W = pow2_at_least(h->Wabi);
+    d.NT = std::max(32, (int)((n_qubits + 31) / 32) * 32);
+    d.cap = max_elems;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        sf_status st = cuda_fail(nullptr, e, "device query");
+        delete h;
+        return st;
+    }
+    d.nblk = std::max(1, sms) * 4;
+    const size_t n = n_qubits, W = d.W, cap = max_elems;
+    unsigned long long slots = 1024;
+    while (slots < 2 * cap) slots <<= 1;
+    d.slots_cap = slots;
+#define SF_ALLOC(p, cnt)                                       \
+    if ((e = dalloc(h, &(p), (cnt))) != cudaSuccess) {         \
+        sf_destroy(h);                                         \
+        return fail(nullptr, SF_ENOMEM, "device allocation failed"); \
+    }
+    SF_ALLOC(d.mx, W * n);
+    SF_ALLOC(d.mz, W * n);
+    SF_ALLOC(d.dx, W * n);
+    SF_ALLOC(d.dz, W * n);
+    SF_ALLOC(d.de, n);
+    SF_ALLOC(d.piv, n);
+    SF_ALLOC(d.meta, 4);
+    SF_ALLOC(d.g, 1);
+    for (int b = 0; b < 2; b++) {
+        SF_ALLOC(d.sig[b], W * cap);
+        SF_ALLOC(d.amp[b], cap);
+    }
+    SF_ALLOC(d.kcnt, 2);
+    SF_ALLOC(d.status, 1);
+    SF_ALLOC(d.plan, plan_words((int)n, (int)W));
+    SF_ALLOC(d.slots, slots);
+    SF_ALLOC(d.rep, cap);
+    SF_ALLOC(d.blk, 2 * (size_t)d.nblk + 2);
+    SF_ALLOC(d.red, 4 * (size_t)d.nblk);
+    SF_ALLOC(d.out, 8);
+    SF_ALLOC(h->dy, W);
+    h->dgates_cap = 256;
+    SF_ALLOC(h->dgates, h->dgates_cap);
+    const size_t wsb = sf_tableau_smem_bytes((int)n, (int)W, d.NT);
+    if (wsb > 200 * 1024) SF_ALLOC(h->gws, (wsb + 7) / 8);
+#undef SF_ALLOC
+    h->hstage_cap = 256;
+    if (cudaMallocHost(&h->hstage, h->hstage_cap * sizeof(sf_gate_rec)) != cudaSuccess ||
+        cudaMallocHost(&h->hy, W * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMallocHost(&h->hk, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&h->hstatus, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&h->hout, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&h->hmeta, 4 * sizeof(int32_t)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+        sf_destroy(h);
+        return fail(nullptr, SF_ENOMEM, "pinned host allocation failed");
+    }
+    cudaMemsetAsync(d.status, 0, sizeof(uint32_t), h->stream);
+    cudaMemsetAsync(d.plan, 0, plan_words((int)n, (int)W) * sizeof(uint64_t), h->stream);
+    cudaEventRecord(h->stage_ev, h->stream);
+    h->cur = 0;
+    sf_launch_reset(d, 0, h->stream);
+    h->launches++;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        sf_status st = cuda_fail(nullptr, e, "create");
+        sf_destroy(h);
+        return st;
+    }
+    *out = h;
+    return SF_OK;
+}
+
+sf_status sf_destroy(sf_handle h) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (h->stream || true) cudaStreamSynchronize(h->stream);
+    for (void* p : h->dallocs) cudaFree(p);
+    if (h->hstage) cudaFreeHost(h->hstage);
+    if (h->hy) cudaFreeHost(h->hy);
+    if (h->hk) cudaFreeHost(h->hk);
+    if (h->hstatus) cudaFreeHost(h->hstatus);
+    if (h->hout) cudaFreeHost(h->hout);
+    if (h->hmeta) cudaFreeHost(h->hmeta);
+    if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+    return SF_OK;
+}
+
+sf_status sf_reset(sf_handle h) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    h->cur = 0;
+    SF_LAUNCH(h, SF_K_RESET, sf_launch_reset(h->d, 0, h->stream));
+    return SF_OK;
+}
+
+sf_status sf_apply_clifford(sf_handle h, const sf_gate* gates, uint64_t n_gates) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (n_gates == 0) return SF_OK;
+    if (!gates) return fail(h, SF_EINVAL, "gates is NULL");
+    for (uint64_t i = 0; i < n_gates; i++) {
+        sf_status st = check_gate(h, gates[i]);
+        if (st) return st;
+    }
+    // the previous staging copy must have left the pinned buffer
+    SF_CK(h, cudaEventSynchronize(h->stage_ev));
+    if (n_gates > h->hstage_cap) {
+        cudaFreeHost(h->hstage);
+        h->hstage = nullptr;
+        size_t c = h->hstage_cap;
+        while (c < n_gates) c *= 2;
+        SF_CK(h, cudaMallocHost(&h->hstage, c * sizeof(sf_gate_rec)));
+        h->hstage_cap = c;
+    }
+    if (n_gates > h->dgates_cap) {
+        SF_CK(h, cudaStreamSynchronize(h->stream));
+        size_t c = h->dgates_cap;
+        while (c < n_gates) c *= 2;
+        sf_gate_rec* p = nullptr;
+        SF_CK(h, cudaMalloc(&p, c * sizeof(sf_gate_rec)));
+        auto it = std::find(h->dallocs.begin(), h->dallocs.end(), (void*)h->dgates);
+        if (it != h->dallocs.end()) {
+            cudaFree(*it);
+            *it = p;
+        }
+        h->dgates = p;
+        h->dgates_cap = c;
+    }
+    for (uint64_t i = 0; i < n_gates; i++) {
+        h->hstage[i].kind = gates[i].kind;
+        h->hstage[i].q0 = gates[i].q0;
+        h->hstage[i].q1 = one_qubit(gates[i].kind) ? 0u : gates[i].q1;
+        h->hstage[i].pad = 0;
+    }
+    SF_CK(h, cudaMemcpyAsync(h->dgates, h->hstage, n_gates * sizeof(sf_gate_rec), cudaMemcpyHostToDevice,
+                             h->stream));
+    SF_CK(h, cudaEventRecord(h->stage_ev, h->stream));
+    return run_clifford(h, h->dgates, n_gates);
+}
+
+sf_status sf_apply_clifford_device(sf_handle h, const sf_gate* dev_gates, uint64_t n_gates) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (n_gates == 0) return SF_OK;
+    if (!dev_gates) return fail(h, SF_EINVAL, "dev_gates is NULL");
+    return run_clifford(h, reinterpret_cast<const sf_gate_rec*>(dev_gates), n_gates);
+}
+
+sf_status sf_apply_nonclifford(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (kind > SF_CPHASE) return fail(h, SF_EINVAL, "unknown non-Clifford kind");
+    if (q0 >= h->n) return fail(h, SF_EINVAL, "qubit out of range");
+    if (kind == SF_CPHASE && (q1 >= h->n || q1 == q0)) return fail(h, SF_EINVAL, "bad second qubit");
+    const uint32_t q1v = kind == SF_CPHASE ? q1 : 0u;
+    SF_LAUNCH(h, SF_K_BRANCH_PREP, sf_launch_branch_prep(h->d, kind, q0, q1v, theta, h->cur, h->stream));
+    SF_LAUNCH(h, SF_K_BRANCH, sf_launch_branch(h->d, h->cur, h->cur ^ 1, h->stream));
+    h->cur ^= 1;
+    return SF_OK;
+}
+
+sf_status sf_coalesce(sf_handle h, double drop_eps, uint64_t* out_size) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");
+    sf_status cs = coalesce_seq(h, drop_eps, h->cur, h->cur ^ 1);
+    if (cs) return cs;
+    h->cur ^= 1;
+    if (out_size) {
+        SF_CK(h, cudaMemcpyAsync(h->hk, h->d.kcnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 h->stream));
+        sf_status st = sync_check(h);
+        if (st) return st;
+        *out_size = h->hk[h->cur];
+    }
+    return SF_OK;
+}
+
+sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, double* p1) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (q >= h->n || collapse_to < -1 || collapse_to > 1) return fail(h, SF_EINVAL, "bad measurement arguments");
+    SF_LAUNCH(h, SF_K_MEASURE_PREP, sf_launch_measure_prep(h->d, q, h->cur, h->gws, h->stream));
+    SF_CK(h, cudaMemcpyAsync(h->hmeta, h->d.meta, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    sf_status st = sync_check(h);
+    if (st) return st;
+    if (h->hmeta[2]) {
+        SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cofactor_split(h->d, h->cur, h->cur ^ 1, h->stream));
+        st = coalesce_seq(h, 1e-12, h->cur ^ 1, h->cur);
+        if (st) return st;
+    }
+    SF_LAUNCH(h, SF_K_PROB, sf_launch_prob(h->d, h->cur, h->stream));
+    SF_LAUNCH(h, SF_K_REDUCE, sf_launch_reduce_final(h->d, 0, h->stream));
+    SF_CK(h, cudaMemcpyAsync(h->hout, h->d.out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    st = sync_check(h);
+    if (st) return st;
+    const double pr[2] = {h->hout[0], h->hout[1]};
+    if (p0) *p0 = pr[0];
+    if (p1) *p1 = pr[1];
+    if (collapse_to >= 0) {
+        if (!(pr[collapse_to] > 0.0)) return fail(h, SF_ESTATE, "collapse onto an outcome of probability 0");
+        const int in = h->cur, outb = h->cur ^ 1;
+        SF_LAUNCH(h, SF_K_COUNT, sf_launch_count(h->d, in, 1, 0.0, collapse_to, h->stream));
+        SF_LAUNCH(h, SF_K_SCAN, sf_launch_scan(h->d, outb, h->stream));
+        SF_LAUNCH(h, SF_K_SCATTER, sf_launch_scatter(h->d, in, outb, 1, 0.0, collapse_to, h->stream));
+        h->cur ^= 1;
+    }
+    return SF_OK;
+}
+
+sf_status sf_amplitude(sf_handle h, const uint64_t* x_bits, double* re, double* im) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (!x_bits || !re || !im) return fail(h, SF_EINVAL, "NULL argument");
+    const int W = h->d.W;
+    for (int w = 0; w < W; w++) h->hy[w] = w < h->Wabi ? x_bits[w] : 0ull;
+    if (h->n % 64) h->hy[h->Wabi - 1] &= (1ull << (h->n % 64)) - 1ull;
+    SF_CK(h, cudaMemcpyAsync(h->dy, h->hy, W * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+    SF_LAUNCH(h, SF_K_AMP_PREP, sf_launch_amp_prep(h->d, h->dy, h->stream));
+    SF_LAUNCH(h, SF_K_AMPLITUDE, sf_launch_amplitude(h->d, h->cur, h->stream));
+    SF_LAUNCH(h, SF_K_REDUCE, sf_launch_reduce_final(h->d, 1, h->stream));
+    SF_CK(h, cudaMemcpyAsync(h->hout, h->d.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    sf_status st = sync_check(h);
+    if (st) return st;
+    *re = h->hout[2];
+    *im = h->hout[3];
+    return SF_OK;
+}
+
+sf_status sf_size(sf_handle h, uint64_t* k) {
+    if (!h || !k) return fail(h, SF_EINVAL, "NULL argument");
+    SF_CK(h, cudaMemcpyAsync(h->hk, h->d.kcnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    sf_status st = sync_check(h);
+    if (st) return st;
+    *k = h->hk[h->cur];
+    return SF_OK;
+}
+
+sf_status sf_sync(sf_handle h) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    return sync_check(h);
+}
+
+sf_status sf_get_tableau(sf_handle h, uint64_t* x, uint64_t* z, uint32_t* n_xblock) {
+    if (!h || !x || !z || !n_xblock) return fail(h, SF_EINVAL, "NULL argument");
+    sf_status st = sync_check(h);
+    if (st) return st;
+    const size_t n = h->n, W = h->d.W;
+    std::vector<uint64_t> bx(W * n), bz(W * n);
+    int32_t r = 0;
+    SF_CK(h, cudaMemcpy(bx.data(), h->d.mx, W * n * 8, cudaMemcpyDeviceToHost));
+    SF_CK(h, cudaMemcpy(bz.data(), h->d.mz, W * n * 8, cudaMemcpyDeviceToHost));
+    SF_CK(h, cudaMemcpy(&r, h->d.meta, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (size_t row = 0; row < n; row++)
+        for (int w = 0; w < h->Wabi; w++) {
+            x[row * h->Wabi + w] = bx[w * n + row];
+            z[row * h->Wabi + w] = bz[w * n + row];
+        }
+    *n_xblock = (uint32_t)r;
+    return SF_OK;
+}
+
+sf_status sf_get_frame(sf_handle h, uint64_t* sigma, double* amp, uint64_t capacity, uint64_t* k) {
+    if (!h || !k) return fail(h, SF_EINVAL, "NULL argument");
+    uint64_t kk = 0;
+    sf_status st = sf_size(h, &kk);
+    if (st) return st;
+    *k = kk;
+    if (kk > capacity) return fail(h, SF_ECAPACITY, "capacity smaller than the frame");
+    if (kk == 0) return SF_OK;
+    if (!sigma || !amp) return fail(h, SF_EINVAL, "NULL output");
+    const int stage = h->cur ^ 1;
+    SF_LAUNCH(h, SF_K_EXPORT, sf_launch_export(h->d, h->cur, stage, h->stream));
+    st = sync_check(h);
+    if (st) return st;
+    const size_t W = h->d.W;
+    std::vector<uint64_t> xs(kk * W);
+    std::vector<double> xa(2 * kk);
+    SF_CK(h, cudaMemcpy(xs.data(), h->d.sig[stage], kk * W * 8, cudaMemcpyDeviceToHost));
+    SF_CK(h, cudaMemcpy(xa.data(), h->d.amp[stage], kk * 16, cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> idx(kk);
+    std::iota(idx.begin(), idx.end(), 0ull);
+    std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) {
+        for (int w = (int)W - 1; w >= 0; w--) {
+            const uint64_t va = xs[a * W + w], vb = xs[b * W + w];
+            if (va != vb) return va < vb;
+        }
+        return false;
+    });
+    for (uint64_t j = 0; j < kk; j++) {
+        const uint64_t s = idx[j];
+        for (int w = 0; w < h->Wabi; w++) sigma[j * h->Wabi + w] = xs[s * W + w];
+        amp[2 * j] = xa[2 * s];
+        amp[2 * j + 1] = xa[2 * s + 1];
+    }
+    return SF_OK;
+}
+
+uint32_t sf_words(sf_handle h) { return h ? (uint32_t)h->Wabi : 0u; }
+
+uint64_t sf_kernel_launches(sf_handle h) { return h ? h->launches : 0ull; }
+
+sf_status sf_get_internal(sf_handle h, uint64_t* dx, uint64_t* dz, uint32_t* de, double* g) {
+    if (!h || !dx || !dz || !de || !g) return fail(h, SF_EINVAL, "NULL argument");
+    sf_status st = sync_check(h);
+    if (st) return st;
+    const size_t n = h->n, W = h->d.W;
+    std::vector<uint64_t> bx(W * n), bz(W * n);
+    SF_CK(h, cudaMemcpy(bx.data(), h->d.dx, W * n * 8, cudaMemcpyDeviceToHost));
+    SF_CK(h, cudaMemcpy(bz.data(), h->d.dz, W * n * 8, cudaMemcpyDeviceToHost));
+    SF_CK(h, cudaMemcpy(de, h->d.de, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    SF_CK(h, cudaMemcpy(g, h->d.g, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t row = 0; row < n; row++)
+        for (int w = 0; w < h->Wabi; w++) {
+            dx[row * h->Wabi + w] = bx[w * n + row];
+            dz[row * h->Wabi + w] = bz[w * n + row];
+        }
+    return SF_OK;
+}
+
+sf_status sf_time_kernel(sf_handle h, int32_t kernel_id) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (kernel_id < -1 || kernel_id >= SF_K_COUNT_CLASSES) return fail(h, SF_EINVAL, "unknown kernel class");
+    SF_CK(h, cudaStreamSynchronize(h->stream));
+    h->time_id = kernel_id;
+    h->ev_used = 0;
+    h->time_ms = 0.0;
+    h->time_count = 0;
+    return SF_OK;
+}
+
+sf_status sf_kernel_time(sf_handle h, double* total_ms, uint64_t* launches) {
+    if (!h || !total_ms || !launches) return fail(h, SF_EINVAL, "NULL argument");
+    SF_CK(h, cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < h->ev_used; i++) {
+        float ms = 0.f;
+        SF_CK(h, cudaEventElapsedTime(&ms, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]));
+        h->time_ms += ms;
+        h->time_count++;
+    }
+    h->ev_used = 0;
+    *total_ms = h->time_ms;
+    *launches = h->time_count;
+    return SF_OK;
+}
+
+const char* sf_last_error(sf_handle h) {
+    if (h) return h->err.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    return g_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,836 @@
+// sf_tableau.cu -- single-CTA kernels that work on the shared tableau:
+//   * k_clifford:      ROTATE(F, U) on M and D for a batch of Clifford gates
+//                      (Table 2 conjugation, Invariant 1 repair by Gauss-Jordan
+//                      from the first touched column, global-phase update by
+//                      the five-step rule of Sec. III evaluated once per gate),
+//                      emitting the composed affine map sigma' = A sigma ^ t that
+//                      k_affine applies to every phase vector.
+//   * k_branch_prep:   anticommutation masks and signs of the Z-type Pauli terms
+//                      of a diagonal non-Clifford gate (Sec. IV).
+//   * k_measure_prep:  deterministic/random test of a qubit and, if random, the
+//                      COFACTOR update of M (Sec. III, measurement of Sec. II-B
+//                      forced to both outcomes) with the tables that map old
+//                      frame elements to their two cofactor children.
+//   * k_amp_prep, k_reset.
+// One thread owns one tableau row (blockDim = NT >= n).  The tableau lives in
+// shared memory when it fits, else in a global workspace of the same layout.
+#include "sf_device.cuh"
+
+namespace {
+
+constexpr int kMaxWarps = 32;
+
+template <int W>
+struct Ws {
+    uint64_t *mx, *mz, *dx, *dz, *A, *d0x, *d0z;  // word-major [W][NT]
+    uint32_t *de, *d0e, *t0, *t1;                // [NT]
+    int32_t* piv;                                // [NT]
+};
+
+template <int W>
+__device__ Ws<W> carve(uint64_t* base, int NT) {
+    Ws<W> T;
+    size_t o = 0, s = (size_t)W * NT;
+    T.mx = base + o; o += s;
+    T.mz = base + o; o += s;
+    T.dx = base + o; o += s;
+    T.dz = base + o; o += s;
+    T.A = base + o; o += s;
+    T.d0x = base + o; o += s;
+    T.d0z = base + o; o += s;
+    uint32_t* u = reinterpret_cast<uint32_t*>(base + o);
+    T.de = u; u += NT;
+    T.d0e = u; u += NT;
+    T.t0 = u; u += NT;
+    T.t1 = u; u += NT;
+    T.piv = reinterpret_cast<int32_t*>(u);
+    return T;
+}
+
+template <int W>
+struct Scratch {
+    Pauli<W> red[kMaxWarps + 1];
+    int wmin[2][kMaxWarps];
+    uint64_t y[W], y2[W], words[4][W];
+    int iv[8];
+    double dv[8];
+};
+
+template <int W>
+__device__ __forceinline__ void load_m(const Ws<W>& T, int NT, int h, Pauli<W>& p) {
+#pragma unroll
+    for (int w = 0; w < W; w++) { p.x[w] = T.mx[w * NT + h]; p.z[w] = T.mz[w * NT + h]; }
+    p.e = 0;
+}
+template <int W>
+__device__ __forceinline__ void load_d(const Ws<W>& T, int NT, int h, Pauli<W>& p) {
+#pragma unroll
+    for (int w = 0; w < W; w++) { p.x[w] = T.dx[w * NT + h]; p.z[w] = T.dz[w * NT + h]; }
+    p.e = (int)T.de[h];
+}
+template <int W>
+__device__ __forceinline__ void store_d(const Ws<W>& T, int NT, int h, const Pauli<W>& p) {
+#pragma unroll
+    for (int w = 0; w < W; w++) { T.dx[w * NT + h] = p.x[w]; T.dz[w * NT + h] = p.z[w]; }
+    T.de[h] = (uint32_t)p.e;
+}
+
+template <int W>
+__device__ __forceinline__ void shfl_pauli(const Pauli<W>& v, Pauli<W>& o, int off) {
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        o.x[w] = __shfl_xor_sync(SF_FULL, v.x[w], off);
+        o.z[w] = __shfl_xor_sync(SF_FULL, v.z[w], off);
+    }
+    o.e = __shfl_xor_sync(SF_FULL, v.e, off);
+}
+
+// Product over all threads of the block of commuting Pauli operators; every
+// thread receives the result.  Commuting factors make the order irrelevant.
+template <int W>
+__device__ void cta_product(Pauli<W>& v, Scratch<W>& S) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        Pauli<W> o;
+        shfl_pauli<W>(v, o, off);
+        pauli_mul<W>(v, o);
+    }
+    __syncthreads();
+    if (lane == 0) S.red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        Pauli<W> u;
+        if (lane < nw) u = S.red[lane];
+        else pauli_id<W>(u);
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            Pauli<W> o;
+            shfl_pauli<W>(u, o, off);
+            pauli_mul<W>(u, o);
+        }
+        if (lane == 0) S.red[kMaxWarps] = u;
+    }
+    __syncthreads();
+    v = S.red[kMaxWarps];
+}
+
+// OR a per-thread bit (thread h -> bit h) into words[W] (must be zeroed).
+template <int W>
+__device__ void cta_bits(bool b, uint64_t* words) {
+    const int h = threadIdx.x;
+    unsigned bal = __ballot_sync(SF_FULL, b);
+    if ((h & 31) == 0 && bal) {
+        atomicOr(reinterpret_cast<unsigned long long*>(&words[h >> 6]),
+                 (unsigned long long)bal << (h & 32));
+    }
+}
+
+// <y| D^tau phi_0(M)> * 2^{r/2} as an i-power (0..3), or -1 when it is zero.
+// tau: per-row bits (nullptr = all zero).  y: W words in shared memory.
+template <int W>
+__device__ int cta_amp_phi(const Ws<W>& T, int n, int NT, int r, const uint32_t* tau, const uint64_t* y,
+                           Scratch<W>& S) {
+    const int h = threadIdx.x;
+    Pauli<W> q;
+    pauli_id<W>(q);
+    if (tau && h < n && tau[h]) load_d<W>(T, NT, h, q);
+    cta_product<W>(q, S);
+    uint64_t wv[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) wv[w] = y[w] ^ q.x[w];
+    Pauli<W> p;
+    pauli_id<W>(p);
+    if (h < r) {
+        int pv = T.piv[h];
+        if ((wv[pv >> 6] >> (pv & 63)) & 1) load_m<W>(T, NT, h, p);
+    }
+    cta_product<W>(p, S);
+    bool ok = true;
+#pragma unroll
+    for (int w = 0; w < W; w++) ok &= (p.x[w] == wv[w]);
+    if (!ok) return -1;
+    int tot = q.e + popc_and<W>(q.x, q.z) + 2 * popc_and<W>(q.z, wv) + p.e + popc_and<W>(p.x, p.z);
+    return tot & 3;
+}
+
+// Conjugate one row (x, z planes, word-major) by a Clifford gate; returns the
+// sign flip.  Per qubit: H swaps x,z (flip on Y); S: z ^= x (flip on Y);
+// S^dagger: z ^= x (flip on X); Paulis flip on anticommutation; CNOT(c,t):
+// x_t ^= x_c, z_c ^= z_t, flip = x_c z_t (x_t ^ z_c ^ 1); CZ(a,b): z_b ^= x_a,
+// z_a ^= x_b, flip = x_a x_b (z_a ^ z_b); SWAP exchanges the columns.
+__device__ __forceinline__ int conj_row(int kind, int q0, int q1, uint64_t* X, uint64_t* Z, int NT, int h) {
+    uint64_t* x0 = &X[(q0 >> 6) * NT + h];
+    uint64_t* z0 = &Z[(q0 >> 6) * NT + h];
+    const int b0 = q0 & 63;
+    const uint64_t m0 = 1ull << b0;
+    const int xa = (int)((*x0 >> b0) & 1), za = (int)((*z0 >> b0) & 1);
+    int f = 0;
+    switch (kind) {
+        case 0: f = xa & za; if (xa != za) { *x0 ^= m0; *z0 ^= m0; } break;
+        case 1: f = xa & za; if (xa) *z0 ^= m0; break;
+        case 2: f = xa & (za ^ 1); if (xa) *z0 ^= m0; break;
+        case 3: f = za; break;
+        case 4: f = xa ^ za; break;
+        case 5: f = xa; break;
+        default: {
+            uint64_t* x1 = &X[(q1 >> 6) * NT + h];
+            uint64_t* z1 = &Z[(q1 >> 6) * NT + h];
+            const int b1 = q1 & 63;
+            const uint64_t m1 = 1ull << b1;
+            const int xb = (int)((*x1 >> b1) & 1), zb = (int)((*z1 >> b1) & 1);
+            if (kind == 6) {
+                f = xa & zb & (xb ^ za ^ 1);
+                if (xa) *x1 ^= m1;
+                if (zb) *z0 ^= m0;
+            } else if (kind == 7) {
+                f = xa & xb & (za ^ zb);
+                if (xa) *z1 ^= m1;
+                if (xb) *z0 ^= m0;
+            } else {
+                if (xa != xb) { *x0 ^= m0; *x1 ^= m1; }
+                if (za != zb) { *z0 ^= m0; *z1 ^= m1; }
+            }
+        }
+    }
+    return f;
+}
+
+// Gauss-Jordan elimination to the canonical RREF over columns >= start, rows
+// whose pivot is < start keeping theirs.  Every row operation M_h <- M_h M_i is
+// mirrored as D_i <- D_i D_h (so D stays a destabilizer set and
+// D^sigma = D'^{A sigma} exactly), as A_h ^= A_i on the composed affine map
+// (if TRACK_A), and as t_h ^= t_i ^ c (c = sign bit of the row product) on the
+// sign vectors t0/t1.  Returns r.
+template <int W, bool TRACK_A>
+__device__ int cta_gj(const Ws<W>& T, int n, int NT, int start, Scratch<W>& S) {
+    const int h = threadIdx.x, lane = h & 31, wid = h >> 5, nw = NT >> 5;
+    int nxt = __syncthreads_count(h < n && T.piv[h] < start);
+    int par = 0;
+    for (int c = start; c < 2 * n && nxt < n; c++) {
+        const uint64_t* plane = c < n ? T.mx : T.mz;
+        const int cc = c < n ? c : c - n;
+        const int cwo = (cc >> 6) * NT, cb = cc & 63;
+        const bool cand = (h < n) && (h >= nxt) && ((plane[cwo + h] >> cb) & 1);
+        const unsigned bal = __ballot_sync(SF_FULL, cand);
+        if (lane == 0) S.wmin[par][wid] = bal ? (wid * 32 + __ffs(bal) - 1) : 0x7fffffff;
+        __syncthreads();
+        int p = 0x7fffffff;
+        for (int i = 0; i < nw; i++) p = min(p, S.wmin[par][i]);
+        par ^= 1;
+        if (p == 0x7fffffff) continue;
+        if (p != nxt) {
+            if (h < W) {
+                const int a = h * NT + p, b = h * NT + nxt;
+                uint64_t t;
+                t = T.mx[a]; T.mx[a] = T.mx[b]; T.mx[b] = t;
+                t = T.mz[a]; T.mz[a] = T.mz[b]; T.mz[b] = t;
+                t = T.dx[a]; T.dx[a] = T.dx[b]; T.dx[b] = t;
+                t = T.dz[a]; T.dz[a] = T.dz[b]; T.dz[b] = t;
+                if (TRACK_A) { t = T.A[a]; T.A[a] = T.A[b]; T.A[b] = t; }
+            } else if (h == W) {
+                uint32_t u;
+                u = T.de[p]; T.de[p] = T.de[nxt]; T.de[nxt] = u;
+                u = T.t0[p]; T.t0[p] = T.t0[nxt]; T.t0[nxt] = u;
+                u = T.t1[p]; T.t1[p] = T.t1[nxt]; T.t1[nxt] = u;
+            }
+            __syncthreads();
+        }
+        const int i = nxt;
+        const bool el = (h < n) && (h != i) && ((plane[cwo + h] >> cb) & 1);
+        if (el) {
+            uint64_t xh[W], zh[W], xi[W], zi[W];
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                xh[w] = T.mx[w * NT + h]; zh[w] = T.mz[w * NT + h];
+                xi[w] = T.mx[w * NT + i]; zi[w] = T.mz[w * NT + i];
+            }
+            const uint32_t cbit = (uint32_t)(pauli_lambda<W>(xh, zh, xi, zi) >> 1) & 1u;
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                T.mx[w * NT + h] = xh[w] ^ xi[w];
+                T.mz[w * NT + h] = zh[w] ^ zi[w];
+                if (TRACK_A) T.A[w * NT + h] ^= T.A[w * NT + i];
+            }
+            T.t0[h] ^= T.t0[i] ^ cbit;
+            T.t1[h] ^= T.t1[i] ^ cbit;
+        }
+        if (__syncthreads_or(el)) {
+            Pauli<W> v;
+            pauli_id<W>(v);
+            if (el) load_d<W>(T, NT, h, v);
+            cta_product<W>(v, S);
+            if (h == 0) {
+                Pauli<W> di;
+                load_d<W>(T, NT, i, di);
+                pauli_mul<W>(di, v);
+                store_d<W>(T, NT, i, di);
+            }
+        }
+        if (h == 0) T.piv[i] = c;
+        nxt++;
+        __syncthreads();
+    }
+    return __syncthreads_count(h < n && T.piv[h] < n);
+}
+
+template <int W>
+__device__ void load_tableau(const SfDev& d, const Ws<W>& T) {
+    const int h = threadIdx.x, n = d.n, NT = d.NT;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        T.mx[w * NT + h] = h < n ? d.mx[w * n + h] : 0;
+        T.mz[w * NT + h] = h < n ? d.mz[w * n + h] : 0;
+        T.dx[w * NT + h] = h < n ? d.dx[w * n + h] : 0;
+        T.dz[w * NT + h] = h < n ? d.dz[w * n + h] : 0;
+    }
+    T.de[h] = h < n ? d.de[h] : 0;
+    T.piv[h] = h < n ? d.piv[h] : 0x7fffffff;
+    T.t0[h] = 0;
+    T.t1[h] = 0;
+}
+
+template <int W>
+__device__ void store_tableau(const SfDev& d, const Ws<W>& T, int r) {
+    const int h = threadIdx.x, n = d.n, NT = d.NT;
+    if (h < n) {
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            d.mx[w * n + h] = T.mx[w * NT + h];
+            d.mz[w * n + h] = T.mz[w * NT + h];
+            d.dx[w * n + h] = T.dx[w * NT + h];
+            d.dz[w * n + h] = T.dz[w * NT + h];
+        }
+        d.de[h] = T.de[h];
+        d.piv[h] = T.piv[h];
+    }
+    if (h == 0) d.meta[0] = r;
+}
+
+__device__ __forceinline__ double2 ipow_c(int k) { return ipow_mul(make_double2(1.0, 0.0), k); }
+
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* gates, int ng, int buf,
+                                                   uint64_t* gws) {
+    extern __shared__ uint64_t smem[];
+    __shared__ Scratch<W> S;
+    if (*d.status) return;
+    const int n = d.n, NT = d.NT, h = threadIdx.x;
+    const Ws<W> T = carve<W>(gws ? gws : smem, NT);
+    load_tableau<W>(d, T);
+#pragma unroll
+    for (int w = 0; w < W; w++) T.A[w * NT + h] = (h < n && (h >> 6) == w) ? (1ull << (h & 63)) : 0ull;
+    int r = d.meta[0];
+    double2 g = *d.g;
+    __syncthreads();
+    const double rs2 = 0.70710678118654752440;
+    for (int gi = 0; gi < ng; gi++) {
+        const uint32_t ukind = gates[gi].kind, uq0 = gates[gi].q0, uq1 = gates[gi].q1;
+        const bool two = ukind >= 6;
+        if (ukind > 8 || uq0 >= (uint32_t)n || (two && (uq1 >= (uint32_t)n || uq1 == uq0))) {
+            if (h == 0) set_status(d.status, 1u, buf);  // SF_EINVAL: bad gate in a device list
+            return;
+        }
+        const int kind = (int)ukind, q0 = (int)uq0, q1 = two ? (int)uq1 : 0;
+        // numerator of the phase rule: a point y with <y|U phi_0(M)> != 0, in units of 2^{-r/2}
+        int yq = -1;
+        double2 num = make_double2(1.0, 0.0);
+        if (kind == 0) {
+            if (h < W) S.y[h] = (h == (q0 >> 6)) ? (1ull << (q0 & 63)) : 0ull;
+            __syncthreads();
+            const int cq = cta_amp_phi<W>(T, n, NT, r, nullptr, S.y, S);
+            if (cq != 2) {
+                double2 cv = cq < 0 ? make_double2(0.0, 0.0) : ipow_c(cq);
+                num = make_double2((1.0 + cv.x) * rs2, cv.y * rs2);
+            } else {
+                yq = q0;
+                num = make_double2(2.0 * rs2, 0.0);
+            }
+        } else if (kind == 3) {
+            yq = q0;
+        } else if (kind == 4) {
+            yq = q0;
+            num = make_double2(0.0, 1.0);
+        }
+        const int r_old = r;
+        // conjugate all rows; sign flips of M go to t0 (composed) and t1 (this gate)
+        if (h < n) {
+            const uint32_t f = (uint32_t)conj_row(kind, q0, q1, T.mx, T.mz, NT, h);
+            T.t0[h] ^= f;
+            T.t1[h] = f;
+            const int fd = conj_row(kind, q0, q1, T.dx, T.dz, NT, h);
+            T.de[h] = (T.de[h] + 2u * (uint32_t)fd) & 3u;
+        } else {
+            T.t1[h] = 0;
+        }
+        __syncthreads();
+        const int start = two ? min(q0, q1) : q0;
+        r = cta_gj<W, true>(T, n, NT, start, S);
+        // denominator: <y| D'^{t1} phi_0(M')>
+        if (h < W) S.y[h] = (yq >= 0 && h == (yq >> 6)) ? (1ull << (yq & 63)) : 0ull;
+        __syncthreads();
+        const int dq = cta_amp_phi<W>(T, n, NT, r, T.t1, S.y, S);
+        if (dq < 0) {
+            if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 1u);
+            return;
+        }
+        double2 om = ipow_mul(num, (4 - dq) & 3);
+        const int dr = r - r_old;
+        const double sc = dr == 0 ? 1.0 : (dr > 0 ? 1.41421356237309504880 : rs2);
+        om.x *= sc;
+        om.y *= sc;
+        g = cmul(g, om);
+        __syncthreads();
+    }
+    store_tableau<W>(d, T, r);
+    if (h == 0) *d.g = g;
+    // emit the affine map: columns of A (column j = image of e_j) and t as bit words
+    uint64_t* AT = T.d0x;  // free in this kernel; W*NT >= n*W words
+    for (int e = h; e < n * W; e += NT) AT[e] = 0;
+    if (h < W) S.words[0][h] = 0;
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        const bool b = (h < n) && ((T.A[(j >> 6) * NT + h] >> (j & 63)) & 1);
+        const unsigned bal = __ballot_sync(SF_FULL, b);
+        if ((h & 31) == 0 && bal)
+            atomicOr(reinterpret_cast<unsigned long long*>(&AT[(size_t)j * W + (h >> 6)]),
+                     (unsigned long long)bal << (h & 32));
+    }
+    __syncthreads();
+    uint64_t* pa = d.plan + plan_AT(n, W);
+    for (int e = h; e < n * W; e += NT) pa[e] = AT[e];
+    cta_bits<W>(h < n && T.t0[h], S.words[0]);
+    __syncthreads();
+    if (h < W) d.plan[plan_t(n, W) + h] = S.words[0][h];
+}
+
+// ---------------------------------------------------------------------------
+// Terms of a diagonal gate as sum_j c_j Z^{w_j}; for each term the coordinates
+// Z^w = eps D^u M^v (u_h = [Z^w anticommutes with M_h], v_h = [.. with D_h]),
+// so Z^w D^sigma phi_0 = eps (-1)^{v.sigma} D^{sigma^u} phi_0.  Terms with equal
+// u are grouped; the branch kernel writes one child per group.
+template <int W>
+__global__ void __launch_bounds__(1024) k_branch_prep(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1,
+                                                      double theta, int buf) {
+    __shared__ Scratch<W> S;
+    __shared__ uint64_t um[SF_BR_MAXT][W], vm[SF_BR_MAXT][W];
+    __shared__ int epsq[SF_BR_MAXT];
+    if (*d.status) return;
+    const int n = d.n, h = threadIdx.x;
+    double th = theta;
+    if (kind == 0) th = 0.78539816339744830962;
+    if (kind == 1) th = -0.78539816339744830962;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    int nt;
+    int wq[SF_BR_MAXT][2];
+    double2 cf[SF_BR_MAXT];
+    if (kind <= 2) {
+        nt = 2;
+        wq[0][0] = -1; wq[0][1] = -1; cf[0] = make_double2((1.0 + cs) * 0.5, sn * 0.5);
+        wq[1][0] = (int)q0; wq[1][1] = -1; cf[1] = make_double2((1.0 - cs) * 0.5, -sn * 0.5);
+    } else {
+        nt = 4;
+        const double2 dd = make_double2((cs - 1.0) * 0.25, sn * 0.25);
+        wq[0][0] = -1; wq[0][1] = -1; cf[0] = make_double2(1.0 + dd.x, dd.y);
+        wq[1][0] = (int)q0; wq[1][1] = -1; cf[1] = make_double2(-dd.x, -dd.y);
+        wq[2][0] = (int)q1; wq[2][1] = -1; cf[2] = make_double2(-dd.x, -dd.y);
+        wq[3][0] = (int)q0; wq[3][1] = (int)q1; cf[3] = dd;
+    }
+    for (int j = 0; j < nt; j++) {
+        uint64_t wz[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) wz[w] = 0;
+        for (int a = 0; a < 2; a++)
+            if (wq[j][a] >= 0) wz[wq[j][a] >> 6] ^= 1ull << (wq[j][a] & 63);
+        if (h < W) { um[j][h] = 0; vm[j][h] = 0; }
+        __syncthreads();
+        bool ub = false, vb = false;
+        Pauli<W> p;
+        pauli_id<W>(p);
+        if (h < n) {
+            uint64_t mx[W], dx[W];
+#pragma unroll
+            for (int w = 0; w < W; w++) { mx[w] = d.mx[w * n + h]; dx[w] = d.dx[w * n + h]; }
+            ub = popc_and<W>(mx, wz) & 1;
+            vb = popc_and<W>(dx, wz) & 1;
+            if (ub) {
+#pragma unroll
+                for (int w = 0; w < W; w++) { p.x[w] = dx[w]; p.z[w] = d.dz[w * n + h]; }
+                p.e = (int)d.de[h];
+            }
+            if (vb) {
+                Pauli<W> m;
+#pragma unroll
+                for (int w = 0; w < W; w++) { m.x[w] = mx[w]; m.z[w] = d.mz[w * n + h]; }
+                m.e = 0;
+                pauli_mul<W>(p, m);
+            }
+        }
+        cta_bits<W>(ub, um[j]);
+        cta_bits<W>(vb, vm[j]);
+        cta_product<W>(p, S);
+        if (h == 0) {
+            bool ok = true;
+#pragma unroll
+            for (int w = 0; w < W; w++) ok &= (p.x[w] == 0) && (p.z[w] == wz[w]);
+            if (!ok) set_status(d.status, SF_ST_INTERNAL, buf, 2u);
+            // D^u M^v is anti-Hermitian when u and v share a row, so eps is any i-power
+            epsq[j] = (4 - p.e) & 3;
+        }
+        __syncthreads();
+    }
+    if (h != 0) return;
+    if (*d.status) return;
+    // group terms by u
+    uint64_t* pb = d.plan + plan_br(n, W);
+    const size_t gw = br_group_words(W);
+    int gid[SF_BR_MAXT];
+    int ngp = 0;
+    for (int j = 0; j < nt; j++) {
+        int found = -1;
+        for (int j2 = 0; j2 < j; j2++) {
+            bool same = true;
+            for (int w = 0; w < W; w++) same &= um[j2][w] == um[j][w];
+            if (same) { found = gid[j2]; break; }
+        }
+        gid[j] = found >= 0 ? found : ngp++;
+    }
+    pb[0] = (uint64_t)ngp;
+    for (int g = 0; g < ngp; g++) {
+        uint64_t* G = pb + 1 + g * gw;
+        int cnt = 0;
+        for (int j = 0; j < nt; j++) {
+            if (gid[j] != g) continue;
+            if (cnt == 0)
+                for (int w = 0; w < W; w++) G[w] = um[j][w];
+            const double2 c = ipow_mul(cf[j], epsq[j]);
+            uint64_t* Tm = G + W + 1 + cnt * (2 + W);
+            Tm[0] = (uint64_t)__double_as_longlong(c.x);
+            Tm[1] = (uint64_t)__double_as_longlong(c.y);
+            for (int w = 0; w < W; w++) Tm[2 + w] = vm[j][w];
+            cnt++;
+        }
+        G[W] = (uint64_t)cnt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// COFACTOR(F, q) planning.  If q is random in M (some row has x_q = 1):
+//   pick the first such row i; multiply every other anticommuting row by M_i
+//   (dual: D_i <- D_i D_h); D_h <- D_h M_i for rows whose destabilizer
+//   anticommutes with Z_q; D_i <- M_i, M_i <- Z_q; Gauss-Jordan to RREF.
+//   For outcome y, P_y phi_0(M) = kappa_y D'^{tau_y} phi_0(M'); each old
+//   destabilizer is D_h = eps_h D'^{u'_h} M'^{v'_h}.  An element sigma then has
+//   children P_x D^sigma phi_0 = D^sigma P_{x ^ v.sigma} phi_0, expanded by
+//   applying the old D_h of sigma one at a time in the new basis.
+template <int W>
+__global__ void __launch_bounds__(1024) k_measure_prep(SfDev d, uint32_t q, int buf, uint64_t* gws) {
+    extern __shared__ uint64_t smem[];
+    __shared__ Scratch<W> S;
+    if (*d.status) return;
+    const int n = d.n, NT = d.NT, h = threadIdx.x, lane = h & 31, wid = h >> 5, nw = NT >> 5;
+    const Ws<W> T = carve<W>(gws ? gws : smem, NT);
+    load_tableau<W>(d, T);
+    const int r0 = d.meta[0];
+    const int qw = q >> 6;
+    const uint64_t qm = 1ull << (q & 63);
+    __syncthreads();
+    const bool uh = (h < n) && (T.mx[qw * NT + h] & qm);
+    const unsigned bal = __ballot_sync(SF_FULL, uh);
+    if (lane == 0) S.wmin[0][wid] = bal ? (wid * 32 + __ffs(bal) - 1) : 0x7fffffff;
+    __syncthreads();
+    int i = 0x7fffffff;
+    for (int a = 0; a < nw; a++) i = min(i, S.wmin[0][a]);
+    if (i == 0x7fffffff) {
+        // deterministic: Z_q is a canonical Z-block row
+        if (h == 0) d.meta[1] = -1;
+        __syncthreads();
+        bool isrow = (h < n) && (h >= r0) && (T.piv[h] == n + (int)q);
+        if (isrow) {
+#pragma unroll
+            for (int w = 0; w < W; w++)
+                isrow &= (T.mx[w * NT + h] == 0) && (T.mz[w * NT + h] == (w == qw ? qm : 0ull));
+            d.meta[1] = isrow ? h : -1;
+            if (!isrow) set_status(d.status, SF_ST_INTERNAL, buf, 3u);
+        }
+        if (h == 0) d.meta[2] = 0;
+        return;
+    }
+    // numerators: <0|phi_0> = 1 and <x_i|phi_0> = i^{popc(x_i & z_i)} (units 2^{-r/2})
+    if (h < W) {
+        S.y[h] = 0;
+        S.y2[h] = T.mx[h * NT + i];
+        S.words[0][h] = 0;
+        S.words[1][h] = 0;
+        S.words[2][h] = 0;
+    }
+    __syncthreads();
+    int num1 = 0;
+    {
+        uint64_t xi[W], zi[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) { xi[w] = T.mx[w * NT + i]; zi[w] = T.mz[w * NT + i]; }
+        num1 = popc_and<W>(xi, zi) & 3;
+    }
+    // v = destabilizers anticommuting with Z_q (before any change)
+    cta_bits<W>((h < n) && (T.dx[qw * NT + h] & qm), S.words[0]);
+    // keep a copy of the old destabilizers
+#pragma unroll
+    for (int w = 0; w < W; w++) { T.d0x[w * NT + h] = T.dx[w * NT + h]; T.d0z[w * NT + h] = T.dz[w * NT + h]; }
+    T.d0e[h] = T.de[h];
+    __syncthreads();
+    // rows anticommuting with Z_q (other than i) <- row * M_i
+    const bool el = uh && h != i;
+    if (el) {
+        uint64_t xh[W], zh[W], xi[W], zi[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            xh[w] = T.mx[w * NT + h]; zh[w] = T.mz[w * NT + h];
+            xi[w] = T.mx[w * NT + i]; zi[w] = T.mz[w * NT + i];
+        }
+        const uint32_t cbit = (uint32_t)(pauli_lambda<W>(xh, zh, xi, zi) >> 1) & 1u;
+#pragma unroll
+        for (int w = 0; w < W; w++) { T.mx[w * NT + h] = xh[w] ^ xi[w]; T.mz[w * NT + h] = zh[w] ^ zi[w]; }
+        T.t0[h] = cbit;
+        T.t1[h] = cbit;
+    }
+    if (__syncthreads_or(el)) {
+        Pauli<W> v;
+        pauli_id<W>(v);
+        if (el) load_d<W>(T, NT, h, v);
+        cta_product<W>(v, S);
+        if (h == 0) {
+            Pauli<W> di;
+            load_d<W>(T, NT, i, di);
+            pauli_mul<W>(di, v);
+            store_d<W>(T, NT, i, di);
+        }
+        __syncthreads();
+    }
+    Pauli<W> mi;
+    load_m<W>(T, NT, i, mi);
+    __syncthreads();
+    if (h < n && h != i && (T.dx[qw * NT + h] & qm)) {
+        Pauli<W> dh;
+        load_d<W>(T, NT, h, dh);
+        pauli_mul<W>(dh, mi);
+        store_d<W>(T, NT, h, dh);
+    }
+    __syncthreads();
+    if (h == i) {
+        store_d<W>(T, NT, i, mi);
+#pragma unroll
+        for (int w = 0; w < W; w++) { T.mx[w * NT + i] = 0; T.mz[w * NT + i] = (w == qw) ? qm : 0ull; }
+        T.t0[i] = 0;
+        T.t1[i] = 1;
+    }
+    T.piv[h] = 0x7fffffff;
+    __syncthreads();
+    const int r = cta_gj<W, false>(T, n, NT, 0, S);
+    const int den0 = cta_amp_phi<W>(T, n, NT, r, T.t0, S.y, S);
+    const int den1 = cta_amp_phi<W>(T, n, NT, r, T.t1, S.y2, S);
+    if (den0 < 0 || den1 < 0) {
+        if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 4u);
+        return;
+    }
+    const double sc = (r == r0) ? 1.0 : (r > r0 ? 1.41421356237309504880 : 0.70710678118654752440);
+    uint64_t* pl = d.plan;
+    cta_bits<W>(h < n && T.t0[h], S.words[1]);
+    cta_bits<W>(h < n && T.t1[h], S.words[2]);
+    __syncthreads();
+    if (h == 0) {
+        const double2 k0 = ipow_mul(make_double2(sc, 0.0), (4 - den0) & 3);
+        const double2 k1 = ipow_mul(make_double2(sc, 0.0), (num1 + 4 - den1) & 3);
+        const size_t ko = cf_kappa(n, W);
+        pl[ko + 0] = (uint64_t)__double_as_longlong(k0.x);
+        pl[ko + 1] = (uint64_t)__double_as_longlong(k0.y);
+        pl[ko + 2] = (uint64_t)__double_as_longlong(k1.x);
+        pl[ko + 3] = (uint64_t)__double_as_longlong(k1.y);
+    }
+    if (h < W) {
+        pl[cf_vq(n, W) + h] = S.words[0][h];
+        pl[cf_tau(n, W) + h] = S.words[1][h];
+        pl[cf_tau(n, W) + W + h] = S.words[2][h];
+    }
+    // tables: old D_hh = eps D'^{u'} M'^{v'}
+    Pauli<W> me, de;
+    if (h < n) {
+        load_m<W>(T, NT, h, me);
+        load_d<W>(T, NT, h, de);
+    }
+    if (h < W) { S.words[3][h] = 0; S.y[h] = 0; }
+    __syncthreads();
+    for (int hh = 0; hh < n; hh++) {
+        uint64_t ox[W], oz[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) { ox[w] = T.d0x[w * NT + hh]; oz[w] = T.d0z[w * NT + hh]; }
+        const int oe = (int)T.d0e[hh];
+        bool ub = false, vb = false;
+        Pauli<W> p;
+        pauli_id<W>(p);
+        if (h < n) {
+            ub = (popc_and<W>(ox, me.z) + popc_and<W>(oz, me.x)) & 1;
+            vb = (popc_and<W>(ox, de.z) + popc_and<W>(oz, de.x)) & 1;
+            if (ub) p = de;
+            if (vb) pauli_mul<W>(p, me);
+        }
+        if (h < W) { S.words[1][h] = 0; S.words[2][h] = 0; }
+        __syncthreads();
+        cta_bits<W>(ub, S.words[1]);
+        cta_bits<W>(vb, S.words[2]);
+        cta_product<W>(p, S);
+        if (h < W) {
+            pl[cf_u(n, W) + (size_t)hh * W + h] = S.words[1][h];
+            pl[cf_v(n, W) + (size_t)hh * W + h] = S.words[2][h];
+        }
+        if (h == 0) {
+            bool ok = true;
+#pragma unroll
+            for (int w = 0; w < W; w++) ok &= (p.x[w] == ox[w]) && (p.z[w] == oz[w]);
+            const int epsq = (oe - p.e + 4) & 3;
+            if (!ok) set_status(d.status, SF_ST_INTERNAL, buf, 5u);
+            if (epsq & 1) S.words[3][hh >> 6] |= 1ull << (hh & 63);
+            if (epsq & 2) S.y[hh >> 6] |= 1ull << (hh & 63);
+        }
+        __syncthreads();
+    }
+    if (h < W) {
+        pl[cf_eps(n, W) + h] = S.words[3][h];
+        pl[cf_eps(n, W) + W + h] = S.y[h];
+    }
+    // the Z_q row of the new tableau
+    if (h == 0) d.meta[1] = -1;
+    __syncthreads();
+    bool isrow = (h < n) && (h >= r) && (T.piv[h] == n + (int)q);
+    if (isrow) d.meta[1] = h;
+    if (h == 0) d.meta[2] = 1;
+    store_tableau<W>(d, T, r);
+}
+
+// ---------------------------------------------------------------------------
+// amplitude query: only elements whose Z-block signs match the parities of y
+// against the Z-block rows contribute (their support must contain y).
+template <int W>
+__global__ void k_amp_prep(SfDev d, const uint64_t* y) {
+    __shared__ uint64_t zm[W], ze[W];
+    const int n = d.n, h = threadIdx.x, r = d.meta[0];
+    if (h < W) { zm[h] = 0; ze[h] = 0; }
+    __syncthreads();
+    bool inz = false, par = false;
+    if (h < n && h >= r) {
+        uint64_t zr[W], yy[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) { zr[w] = d.mz[w * n + h]; yy[w] = y[w]; }
+        inz = true;
+        par = popc_and<W>(zr, yy) & 1;
+    }
+    cta_bits<W>(inz, zm);
+    cta_bits<W>(par, ze);
+    __syncthreads();
+    if (h < W) {
+        const size_t o = plan_am(n, W);
+        d.plan[o + h] = y[h];
+        d.plan[o + W + h] = zm[h];
+        d.plan[o + 2 * W + h] = ze[h];
+    }
+}
+
+template <int W>
+__global__ void k_reset(SfDev d, int buf) {
+    const int n = d.n, h = threadIdx.x;
+    if (h < n) {
+        for (int w = 0; w < W; w++) {
+            const uint64_t e = (w == (h >> 6)) ? (1ull << (h & 63)) : 0ull;
+            d.mx[w * n + h] = 0;
+            d.mz[w * n + h] = e;
+            d.dx[w * n + h] = e;
+            d.dz[w * n + h] = 0;
+        }
+        d.de[h] = 0;
+        d.piv[h] = n + h;
+    }
+    if (h < W) d.sig[buf][(size_t)h * d.cap] = 0;
+    if (h == 0) {
+        d.meta[0] = 0;
+        d.meta[1] = -1;
+        d.meta[2] = 0;
+        *d.g = make_double2(1.0, 0.0);
+        d.amp[buf][0] = make_double2(1.0, 0.0);
+        d.kcnt[buf] = 1;
+        d.kcnt[buf ^ 1] = 0;
+        *d.status = 0;
+    }
+}
+
+template <int W>
+size_t ws_bytes(int NT) {
+    return (size_t)7 * W * NT * 8 + (size_t)5 * NT * 4 + 16;
+}
+
+template <int W, typename K>
+uint64_t* pick_ws(const SfDev& d, K kern, size_t& smem, uint64_t* gws, int which) {
+    const size_t need = ws_bytes<W>(d.NT);
+    if (need <= 200 * 1024) {
+        smem = need;
+        static int attr_bytes = 48 * 1024;
+        if ((int)need > attr_bytes) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr_bytes = 200 * 1024;
+        }
+        return nullptr;
+    }
+    smem = 0;
+    return gws;
+}
+
+}  // namespace
+
+size_t sf_tableau_smem_bytes(int n, int W, int NT) {
+    switch (W) {
+        case 1: return ws_bytes<1>(NT);
+        case 2: return ws_bytes<2>(NT);
+        case 4: return ws_bytes<4>(NT);
+        case 8: return ws_bytes<8>(NT);
+        default: return ws_bytes<16>(NT);
+    }
+}
+
+#define SF_DISPATCH(W_, ...)                                  \
+    switch (W_) {                                             \
+        case 1: { constexpr int WW = 1; __VA_ARGS__; } break; \
+        case 2: { constexpr int WW = 2; __VA_ARGS__; } break; \
+        case 4: { constexpr int WW = 4; __VA_ARGS__; } break; \
+        case 8: { constexpr int WW = 8; __VA_ARGS__; } break; \
+        default: { constexpr int WW = 16; __VA_ARGS__; } break; \
+    }
+
+void sf_launch_reset(const SfDev& d, int buf, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_reset<WW><<<1, d.NT, 0, s>>>(d, buf));
+}
+
+void sf_launch_clifford(const SfDev& d, const void* dev_gates, int ngates, int buf, uint64_t* gws, cudaStream_t s) {
+    SF_DISPATCH(d.W, {
+        size_t sm;
+        uint64_t* ws = pick_ws<WW>(d, k_clifford<WW>, sm, gws, 0);
+        k_clifford<WW><<<1, d.NT, sm, s>>>(d, reinterpret_cast<const sf_gate_rec*>(dev_gates), ngates, buf, ws);
+    });
+}
+
+void sf_launch_branch_prep(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int buf,
+                           cudaStream_t s) {
+    SF_DISPATCH(d.W, k_branch_prep<WW><<<1, d.NT, 0, s>>>(d, kind, q0, q1, theta, buf));
+}
+
+void sf_launch_measure_prep(const SfDev& d, uint32_t q, int buf, uint64_t* gws, cudaStream_t s) {
+    SF_DISPATCH(d.W, {
+        size_t sm;
+        uint64_t* ws = pick_ws<WW>(d, k_measure_prep<WW>, sm, gws, 1);
+        k_measure_prep<WW><<<1, d.NT, sm, s>>>(d, q, buf, ws);
+    });
+}
+
+void sf_launch_amp_prep(const SfDev& d, const uint64_t* dev_y, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_amp_prep<WW><<<1, d.NT, 0, s>>>(d, dev_y));
+}
