@@ -1,0 +1,563 @@
+#!/usr/bin/env python3
+"""Benchmark of the stabilizer-frame hot path on the QFT workload.
+
+One step = one QFT on n = 20 qubits from a seeded random computational basis
+state (controlled-R_k applied as branches of the frame, a coalesce after each),
+then the measurement probabilities of qubit 0 (with its cofactoring) and one
+basis amplitude: every row of the hot path (Clifford update, branching,
+coalescing, measurement, amplitude) runs in every step.
+
+Metric: frame-element updates per second (one gate applied to one input
+element; measurement and the amplitude query count one update per element),
+whole job.  `value` replays the step from device-resident gate lists through a
+captured CUDA graph (measurement and amplitude outside the graph, they read
+results back); `e2e` runs the same step through the public C ABI with host
+gate arrays, host->device copies and result reads inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Multi-GPU: one process per GPU (torchrun), each rank simulates its own QFT
+instance (different seed); no data-path collective ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1712_03554_gb300 import circuits as c  # noqa: E402
+
+N_QUBITS = 20
+MAX_ELEMS = 1 << 21
+DROP_EPS = 1e-12
+METRIC = "frame-elem updates/s"
+UNIT = "updates/s"
+WORKLOAD = ("QFT n=20 on a seeded random basis state (controlled-R_k as frame branches, "
+            "coalesce after each) + measure qubit 0 + one amplitude")
+
+
+# ---------------------------------------------------------------------------
+def build_plan(n: int, seed: int):
+    """The step as a list of ops with consecutive Clifford gates grouped."""
+    x, ops = c.qft_random_input(n, seed)
+    plan, pending = [], []
+    for op in ops:
+        if op[0] == "C":
+            pending.append((op[1], op[2], op[3]))
+            continue
+        if pending:
+            plan.append(("C", list(pending)))
+            pending = []
+        plan.append(op)
+    if pending:
+        plan.append(("C", list(pending)))
+    y = int(c.rng_for(seed + 101).integers(0, 1 << n))
+    return x, plan, y
+
+
+def bytes_model(W: int, n: int = N_QUBITS):
+    """Algorithmic bytes of each kernel class as a function of its element counts.
+    Single-CTA tableau kernels move the tableau (4 n x W words in and out)."""
+    e = 8 * W + 16  # one element: phase vector + FP64 complex amplitude
+    tab = 2 * 4 * n * W * 8
+    return {
+        "clifford": lambda kin, kout: tab + n * W * 8,
+        "branch_prep": lambda kin, kout: tab // 2,
+        "measure_prep": lambda kin, kout: tab,
+        "amp_prep": lambda kin, kout: tab // 2,
+        "affine": lambda kin, kout: 2 * 8 * W * kin,
+        "branch": lambda kin, kout: e * kin + e * kout,
+        "coal_insert": lambda kin, kout: 8 * W * kin,
+        "coal_accum": lambda kin, kout: 20 * kin,
+        "count": lambda kin, kout: 20 * kin,
+        "scatter": lambda kin, kout: (4 + 16) * kin + e * kout + 8 * W * kout,
+        "cofactor": lambda kin, kout: e * kin + e * kout,
+        "prob": lambda kin, kout: 24 * kin,
+        "amplitude": lambda kin, kout: e * kin,
+        "coal_clear": lambda kin, kout: 4 * max(1024, 1 << max(0, (2 * kin - 1).bit_length())),
+        "scan": lambda kin, kout: 0,
+        "reduce": lambda kin, kout: 0,
+    }
+
+
+def instrumented_pass(sfm, n, plan, y):
+    """Run the step once eagerly with a sync after every op to record the
+    element counts each kernel class sees (the circuit is deterministic)."""
+    f = sfm.Frame(n, MAX_ELEMS)
+    W = 1 << max(0, math.ceil(math.log2(max(1, (n + 63) // 64))))
+    rec = {k: [] for k in bytes_model(W, n)}
+    updates = 0
+    coal_elems = 0
+    k = 1
+    peak = 1
+    for op in plan:
+        if op[0] == "C":
+            f.apply_clifford(op[1])
+            updates += len(op[1]) * k
+            rec["affine"].append((k, k))
+            rec["clifford"].append((k, k))
+        elif op[0] == "N":
+            f.apply_nonclifford(op[1], op[2], op[3], op[4])
+            kout = f.size()
+            updates += k
+            rec["branch"].append((k, kout))
+            rec["branch_prep"].append((k, k))
+            k = kout
+        elif op[0] == "K":
+            kin = k
+            k = f.coalesce(DROP_EPS, sync=True)
+            coal_elems += kin
+            for cls in ("coal_insert", "coal_accum", "count"):
+                rec[cls].append((kin, kin))
+            rec["scatter"].append((kin, k))
+        peak = max(peak, k)
+    # the captured (graph) part ends here; the tail is measured eagerly
+    graph_rec = {cls: list(v) for cls, v in rec.items()}
+    # measurement of qubit 0 (cofactor + coalesce + probabilities)
+    kin = k
+    f.measure(0, -1)
+    km = f.size()
+    updates += kin
+    rec["cofactor"].append((kin, 2 * kin))
+    for cls in ("coal_insert", "coal_accum", "count"):
+        rec[cls].append((2 * kin, 2 * kin))
+    rec["scatter"].append((2 * kin, km))
+    coal_elems += 2 * kin
+    rec["prob"].append((km, km))
+    f.amplitude(y)
+    updates += km
+    rec["amplitude"].append((km, km))
+    peak = max(peak, 2 * kin)
+    f.close()
+    return updates, coal_elems, rec, graph_rec, peak, W
+
+
+def measured_peak_gbs():
+    for path in (os.path.join(ROOT, "MEASURED_PEAKS.json"),):
+        try:
+            with open(path) as fh:
+                return float(json.load(fh)["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def kernel_sources_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1712_03554_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(cls: str):
+    """DRAM bytes per launch of `cls` from the committed ncu summary, or None if
+    absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+        if t.get("sources") != kernel_sources_hash():
+            return None
+        v = t.get("bytes_per_launch", {}).get(cls)
+        return float(v) if v is not None else None
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for ln in fh:
+                    p = [v.strip() for v in ln.split(",")]
+                    if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                        rows.append(p)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# ---------------------------------------------------------------------------
+def oracle_step(n, plan, y):
+    import oracle
+    f = oracle.FrameOracle(n)
+    for op in plan:
+        if op[0] == "C":
+            f.apply_clifford(op[1])
+        elif op[0] == "N":
+            f.apply_nonclifford(op[1], op[2], op[3], op[4])
+        elif op[0] == "K":
+            f.coalesce(DROP_EPS)
+    f.measure(0, -1)
+    return f.amplitude(y)
+
+
+def cpu_baseline(n, plan, y, updates, budget_s=12.0, max_reps=4):
+    times = []
+    t_all = time.perf_counter()
+    while len(times) < max_reps and (time.perf_counter() - t_all) < budget_s:
+        t0 = time.perf_counter()
+        oracle_step(n, plan, y)
+        times.append(time.perf_counter() - t0)
+    per = statistics.median(times)
+    return {"value": updates / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full steps of the same workload (single-threaded C oracle), "
+                      f"median {per:.3f} s/step"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    x, plan, y = build_plan(N_QUBITS, args.seed)
+    # updates of the workload, counted from the oracle's own frame sizes
+    import oracle
+    f = oracle.FrameOracle(N_QUBITS)
+    updates, k = 0, 1
+    for op in plan:
+        if op[0] == "C":
+            f.apply_clifford(op[1])
+            updates += len(op[1]) * k
+        elif op[0] == "N":
+            f.apply_nonclifford(op[1], op[2], op[3], op[4])
+            updates += k
+            k = f.size()
+        elif op[0] == "K":
+            k = f.coalesce(DROP_EPS)
+    updates += f.size()
+    f.measure(0, -1)
+    updates += f.size()
+    del f
+    for _ in range(args.warmup):
+        oracle_step(N_QUBITS, plan, y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(N_QUBITS, plan, y)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    val = updates / dt
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "seed": args.seed},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "each step is the full workload on the single-threaded C oracle"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1712_03554_gb300 import sf
+
+    seed = args.seed + rank
+    n = N_QUBITS
+    x, plan, y = build_plan(n, seed)
+    updates, coal_elems, rec, graph_rec, peak, W = instrumented_pass(sf, n, plan, y)
+    model = bytes_model(W, n)
+
+    stream = torch.cuda.Stream()
+    frame = sf.Frame(n, MAX_ELEMS, stream=stream)
+    # device-resident gate lists for the graph path
+    dev_lists = []
+    for op in plan:
+        if op[0] == "C":
+            arr = np.array([[g[0], g[1], g[2], 0] for g in op[1]], dtype=np.uint32)
+            t = torch.from_numpy(arr.view(np.int32)).cuda()
+            dev_lists.append(t)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def async_part(fr):
+        fr.reset()
+        di = 0
+        for op in plan:
+            if op[0] == "C":
+                fr.apply_clifford_device(dev_lists[di].data_ptr(), dev_lists[di].shape[0])
+                di += 1
+            elif op[0] == "N":
+                fr.apply_nonclifford(op[1], op[2], op[3], op[4])
+            elif op[0] == "K":
+                fr.coalesce(DROP_EPS)
+
+    def tail(fr):
+        p = fr.measure(0, -1)
+        a = fr.amplitude(y)
+        return p, a
+
+    # reference result of the eager path
+    with torch.cuda.stream(stream):
+        async_part(frame)
+    p_ref, a_ref = tail(frame)
+
+    # per-class device time of one eager step -> dominant kernel class
+    per_class = {}
+    for cls in sf.KERNEL_CLASSES:
+        if cls in ("export", "reset"):
+            continue
+        frame.time_kernel(cls)
+        async_part(frame)
+        tail(frame)
+        ms, cnt = frame.kernel_time()
+        per_class[cls] = ms
+    frame.time_kernel(-1)
+    # the roofline is reported for the class with the largest device time in the
+    # captured part of the step (where the timed event pairs live)
+    graph_classes = [cls for cls in per_class if graph_rec.get(cls)] or list(per_class)
+    dominant = max(graph_classes, key=per_class.get)
+
+    # capture the asynchronous part in a CUDA graph, with the dominant class timed
+    use_graph = not args.no_graph
+    graph = None
+    frame.time_kernel(dominant)
+    if use_graph:
+        try:
+            async_part(frame)  # warm (creates the event pairs outside capture)
+            tail(frame)
+            frame.time_kernel(dominant)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                async_part(frame)
+            frame.time_kernel(-1)  # keep the captured pairs; eager tail launches are not timed
+            with torch.cuda.stream(stream):
+                graph.replay()
+            p_g, a_g = tail(frame)
+            if abs(p_g[0] - p_ref[0]) > 1e-10 or abs(a_g - a_ref) > 1e-10:
+                raise RuntimeError("graph replay differs from the eager step")
+        except Exception as exc:  # fall back to eager launches from the host
+            print(f"# graph capture unavailable ({exc}); timing eager launches", file=sys.stderr)
+            graph = None
+    if graph is None:
+        frame.time_kernel(dominant)
+
+    def step():
+        if graph is not None:
+            with torch.cuda.stream(stream):
+                graph.replay()
+            return tail(frame)
+        frame.time_kernel(dominant)
+        with torch.cuda.stream(stream):
+            async_part(frame)
+        frame.time_kernel(-1)
+        return tail(frame)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+
+    launches0 = frame.kernel_launches()
+    step_ms = []
+    dom_ms = 0.0
+    dom_launches = 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # evict the frame from L2 between steps
+                ev0.record(stream)
+            step()
+            with torch.cuda.stream(stream):
+                ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            ms, cnt = frame.kernel_time()
+            dom_ms += ms
+            dom_launches += cnt
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+    clocks = clk.summary()
+    # graph replays do not pass through the host launch counter: add the captured kernels
+    launches_total = frame.kernel_launches() - launches0
+    if graph is not None:
+        launches_total += graph_launch_count(plan) * args.steps
+    ms_step = float(np.mean(step_ms))
+
+    # e2e: the public API with host gate arrays, eager launches
+    e2e_frame = sf.Frame(n, MAX_ELEMS, stream=stream)
+    h2d = 16 * sum(len(op[1]) for op in plan if op[0] == "C") + 8 * e2e_frame.W
+    d2h = 16 + 16
+
+    def e2e_step():
+        e2e_frame.reset()
+        for op in plan:
+            if op[0] == "C":
+                e2e_frame.apply_clifford(op[1])
+            elif op[0] == "N":
+                e2e_frame.apply_nonclifford(op[1], op[2], op[3], op[4])
+            elif op[0] == "K":
+                e2e_frame.coalesce(DROP_EPS)
+        p = e2e_frame.measure(0, -1)
+        a = e2e_frame.amplitude(y)
+        return p, a
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            e2e_step()
+        e2e_ms = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p_e, a_e = e2e_step()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    if abs(a_e - a_ref) > 1e-10:
+        raise RuntimeError("e2e result differs from the device path")
+    e2e_ms_step = float(np.mean(e2e_ms))
+
+    # whole-job aggregation
+    tot_updates = updates
+    max_ms = ms_step
+    max_e2e = e2e_ms_step
+    if dist is not None:
+        t = torch.tensor([float(updates), ms_step, e2e_ms_step], dtype=torch.float64, device="cuda")
+        tu = t.clone()
+        dist.all_reduce(tu[:1], op=dist.ReduceOp.SUM)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.MAX)
+        tot_updates, max_ms, max_e2e = float(tu[0]), float(t[1]), float(t[2])
+    value = tot_updates / (max_ms * 1e-3)
+    e2e_value = tot_updates / (max_e2e * 1e-3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    peak_gbs, peak_src = measured_peak_gbs()
+    dom_bytes_per_step = sum(model[dominant](a, b) for a, b in graph_rec[dominant])
+    dom_launch_per_step = max(1, len(graph_rec[dominant]))
+    avg_launch_ms = dom_ms / max(1, dom_launches)
+    bytes_per_launch = dom_bytes_per_step / dom_launch_per_step
+    achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9 if avg_launch_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                "frac": achieved / peak_gbs, "peak_source": peak_src, "traffic": ncu_traffic(dominant),
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_ms * 1e3,
+                "launches_timed": dom_launches}
+    step_share = {k: round(v / max(1e-9, sum(per_class.values())), 4) for k, v in
+                  sorted(per_class.items(), key=lambda kv: -kv[1])}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, plan, y, updates)
+
+    out = {
+        "impl": "gb300", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": n, "seed": args.seed, "max_elems": MAX_ELEMS,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed between steps (512 MiB write)", "cuda_graph": graph is not None,
+                   "updates_per_step": updates, "coalesce_elems_per_step": coal_elems,
+                   "coalesce_elems_per_s": coal_elems * world / (max_ms * 1e-3), "frame_peak": peak,
+                   "wall_s_timed_region": wall},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": max_e2e},
+        "roofline": roofline,
+        "kernel_time_share_eager_step": step_share,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": int(launches_total),
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def graph_launch_count(plan) -> int:
+    """Kernels in the captured part of a step: reset, 2 per Clifford batch
+    (tableau + affine), 2 per branch (prep + per-element), 6 per coalesce."""
+    cnt = 1
+    for op in plan:
+        cnt += {"C": 2, "N": 2, "K": 6}[op[0]]
+    return cnt
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -159,12 +159,15 @@ enum { SF_K_CLIFFORD = 0,      /* tableau update of a Clifford batch (single CTA
 uint64_t sf_kernel_launches(sf_handle h);
 
 /* From now on, bracket every launch of kernel class kernel_id (SF_K_*) with a
- * pair of CUDA events on the handle's stream; -1 stops.  Resets the totals
- * returned by sf_kernel_time.  Asynchronous. */
+ * pair of CUDA events on the handle's stream, forgetting the pairs recorded so
+ * far; kernel_id = -1 stops recording and keeps them.  Waits for the stream
+ * (so it must not be called while the stream is being captured). */
 sf_status sf_time_kernel(sf_handle h, int32_t kernel_id);
 
-/* Device time in milliseconds summed over the bracketed launches, and their
- * number, since the last sf_time_kernel.  Synchronises. */
+/* Device time in milliseconds summed over the event pairs recorded since the
+ * last sf_time_kernel, and their number.  Inside a captured CUDA graph each
+ * replay records the same pairs again, so read this after every replay.
+ * Synchronises. */
 sf_status sf_kernel_time(sf_handle h, double* total_ms, uint64_t* launches);
 
 /* The device-side representation, for tests: destabilizer row h is

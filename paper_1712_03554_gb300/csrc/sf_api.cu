@@ -37,8 +37,6 @@ struct sf_frame_s {
     int time_id = -1;
     std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
     size_t ev_used = 0;
-    double time_ms = 0.0;
-    uint64_t time_count = 0;
 };
 
 namespace {
@@ -106,12 +104,16 @@ sf_status launch(sf_handle h, int id, const char* what, F&& fn) {
         e0 = h->ev_pool[2 * h->ev_used];
         e1 = h->ev_pool[2 * h->ev_used + 1];
         h->ev_used++;
-        cudaEventRecord(e0, h->stream);
     }
+    // inside stream capture the pair must become event-record nodes of the graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (timed) cudaStreamIsCapturing(h->stream, &cap);
+    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (timed) cudaEventRecordWithFlags(e0, h->stream, rec_flags);
     fn();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, what);
-    if (timed) cudaEventRecord(e1, h->stream);
+    if (timed) cudaEventRecordWithFlags(e1, h->stream, rec_flags);
     h->launches++;
     return SF_OK;
 }
@@ -510,24 +512,21 @@ sf_status sf_time_kernel(sf_handle h, int32_t kernel_id) {
     if (kernel_id < -1 || kernel_id >= SF_K_COUNT_CLASSES) return fail(h, SF_EINVAL, "unknown kernel class");
     SF_CK(h, cudaStreamSynchronize(h->stream));
     h->time_id = kernel_id;
-    h->ev_used = 0;
-    h->time_ms = 0.0;
-    h->time_count = 0;
+    if (kernel_id >= 0) h->ev_used = 0;  // -1 stops recording and keeps the pairs
     return SF_OK;
 }
 
 sf_status sf_kernel_time(sf_handle h, double* total_ms, uint64_t* launches) {
     if (!h || !total_ms || !launches) return fail(h, SF_EINVAL, "NULL argument");
     SF_CK(h, cudaStreamSynchronize(h->stream));
+    double tot = 0.0;
     for (size_t i = 0; i < h->ev_used; i++) {
         float ms = 0.f;
         SF_CK(h, cudaEventElapsedTime(&ms, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]));
-        h->time_ms += ms;
-        h->time_count++;
+        tot += ms;
     }
-    h->ev_used = 0;
-    *total_ms = h->time_ms;
-    *launches = h->time_count;
+    *total_ms = tot;
+    *launches = h->ev_used;
     return SF_OK;
 }
 
