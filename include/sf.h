@@ -177,6 +177,37 @@ sf_status sf_kernel_time(sf_handle h, double* total_ms, uint64_t* launches);
  * <0|phi_0> = 2^{-r/2}.  Synchronises. */
 sf_status sf_get_internal(sf_handle h, uint64_t* dx, uint64_t* dz, uint32_t* de, double* g);
 
+/* Largest input accepted by sf_coalesce_noalloc. */
+#define SF_COALESCE_NOALLOC_MAX_ELEMS 65536u
+
+/* Coalescing of caller-owned device buffers that allocates nothing.  The paper
+ * has no counterpart: it is an addition for callers that cannot allocate
+ * device memory where they merge a frame -- code running while its stream is
+ * captured into a CUDA graph (cudaMalloc is not allowed there), frameworks
+ * whose device memory belongs to their own caching pool, and serving loops
+ * that plan all memory up front.
+ *
+ * sigma_in: k_in phase vectors of n_words (1..16) 64-bit words each,
+ * row-major (element j at [j*n_words, j*n_words+n_words)); amp_in: k_in FP64
+ * complex amplitudes (re, im).  Both are device pointers.  Elements with equal
+ * phase vectors are merged by summing their amplitudes, and merged elements
+ * with |a| < drop_eps are dropped.  The survivors are written to sigma_out /
+ * amp_out (device, same layouts, room for k_in elements) in the order of their
+ * first occurrence, and their number to *k_out (host).
+ *
+ * Limits and behaviour: k_in must not exceed SF_COALESCE_NOALLOC_MAX_ELEMS
+ * (SF_EINVAL otherwise).  The hash table and accumulators are one fixed
+ * __device__ array of about 1.8 MB that every GPU loading this library holds
+ * until the process exits; it is shared by all calls on a device and is
+ * cleared by each call before use, so calls whose work overlaps on the GPU
+ * (different streams or host threads) race and must be ordered by the caller.
+ * The first call on each device looks up the array's device address; make that
+ * first call before any stream capture.  Runs on cuda_stream (a cudaStream_t)
+ * and synchronises it. */
+sf_status sf_coalesce_noalloc(const uint64_t* sigma_in, const double* amp_in, uint64_t k_in, uint32_t n_words,
+                              double drop_eps, uint64_t* sigma_out, double* amp_out, uint64_t* k_out,
+                              void* cuda_stream);
+
 /* Words per phase vector / row half used by this handle (ceil(n/64)). */
 uint32_t sf_words(sf_handle h);
 

@@ -71,6 +71,8 @@ def load(build: bool = True) -> C.CDLL:
         "sf_time_kernel": ([H, C.c_int32], st),
         "sf_kernel_time": ([H, PD, P64], st),
         "sf_last_error": ([H], C.c_char_p),
+        "sf_coalesce_noalloc": ([C.c_void_p, C.c_void_p, u64, u32, dbl, C.c_void_p, C.c_void_p, P64, C.c_void_p],
+                                st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -78,6 +80,22 @@ def load(build: bool = True) -> C.CDLL:
         fn.restype = res
     _lib = lib
     return lib
+
+
+COALESCE_NOALLOC_MAX_ELEMS = 65536
+
+
+def coalesce_noalloc(sigma_in: int, amp_in: int, k_in: int, n_words: int, drop_eps: float, sigma_out: int,
+                     amp_out: int, stream: int = 0) -> int:
+    """sf_coalesce_noalloc on device pointers (ints); returns the output count.
+    For callers that cannot allocate device memory (see include/sf.h)."""
+    lib = load()
+    k = C.c_uint64()
+    code = lib.sf_coalesce_noalloc(C.c_void_p(sigma_in), C.c_void_p(amp_in), k_in, n_words, float(drop_eps),
+                                   C.c_void_p(sigma_out), C.c_void_p(amp_out), C.byref(k), C.c_void_p(stream))
+    if code != SF_OK:
+        raise SFError(code, "sf_coalesce_noalloc failed")
+    return int(k.value)
 
 
 def _current_stream_handle() -> int:
