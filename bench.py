@@ -53,14 +53,21 @@ def build_plan(n: int, seed: int):
     """The step as a list of ops with consecutive Clifford gates grouped."""
     x, ops = c.qft_random_input(n, seed)
     plan, pending = [], []
-    for op in ops:
+    i = 0
+    while i < len(ops):
+        op = ops[i]
+        i += 1
         if op[0] == "C":
             pending.append((op[1], op[2], op[3]))
             continue
         if pending:
             plan.append(("C", list(pending)))
             pending = []
-        plan.append(op)
+        if op[0] == "N" and i < len(ops) and ops[i][0] == "K":
+            plan.append(("NK",) + tuple(op[1:]))  # branch + merge in one call
+            i += 1
+        else:
+            plan.append(op)
     if pending:
         plan.append(("C", list(pending)))
     y = int(c.rng_for(seed + 101).integers(0, 1 << n))
@@ -68,26 +75,23 @@ def build_plan(n: int, seed: int):
 
 
 def bytes_model(W: int, n: int = N_QUBITS):
-    """Algorithmic bytes of each kernel class as a function of its element counts.
-    Single-CTA tableau kernels move the tableau (4 n x W words in and out)."""
+    """Algorithmic bytes of each kernel class as a function of the element counts
+    it sees (kin elements read, kout elements written).  The merge table of
+    insert/compact is scratch and not counted; single-CTA tableau kernels move
+    the tableau (4 n x W words in and out)."""
     e = 8 * W + 16  # one element: phase vector + FP64 complex amplitude
     tab = 2 * 4 * n * W * 8
     return {
         "clifford": lambda kin, kout: tab + n * W * 8,
-        "branch_prep": lambda kin, kout: tab // 2,
         "measure_prep": lambda kin, kout: tab,
         "amp_prep": lambda kin, kout: tab // 2,
         "affine": lambda kin, kout: 2 * 8 * W * kin,
         "branch": lambda kin, kout: e * kin + e * kout,
-        "coal_insert": lambda kin, kout: 8 * W * kin,
-        "coal_accum": lambda kin, kout: 20 * kin,
-        "count": lambda kin, kout: 20 * kin,
-        "scatter": lambda kin, kout: (4 + 16) * kin + e * kout + 8 * W * kout,
-        "cofactor": lambda kin, kout: e * kin + e * kout,
+        "insert": lambda kin, kout: e * kin,
+        "compact": lambda kin, kout: e * kout,
+        "filter": lambda kin, kout: e * kin + e * kout,
         "prob": lambda kin, kout: 24 * kin,
         "amplitude": lambda kin, kout: e * kin,
-        "coal_clear": lambda kin, kout: 4 * max(1024, 1 << max(0, (2 * kin - 1).bit_length())),
-        "scan": lambda kin, kout: 0,
         "reduce": lambda kin, kout: 0,
     }
 
@@ -108,20 +112,26 @@ def instrumented_pass(sfm, n, plan, y):
             updates += len(op[1]) * k
             rec["affine"].append((k, k))
             rec["clifford"].append((k, k))
+        elif op[0] == "NK":
+            f.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], DROP_EPS)
+            kout = f.size()
+            updates += k
+            coal_elems += k
+            rec["insert"].append((k, kout))
+            rec["compact"].append((k, kout))
+            k = kout
         elif op[0] == "N":
             f.apply_nonclifford(op[1], op[2], op[3], op[4])
             kout = f.size()
             updates += k
             rec["branch"].append((k, kout))
-            rec["branch_prep"].append((k, k))
             k = kout
         elif op[0] == "K":
             kin = k
             k = f.coalesce(DROP_EPS, sync=True)
             coal_elems += kin
-            for cls in ("coal_insert", "coal_accum", "count"):
-                rec[cls].append((kin, kin))
-            rec["scatter"].append((kin, k))
+            rec["insert"].append((kin, k))
+            rec["compact"].append((kin, k))
         peak = max(peak, k)
     # the captured (graph) part ends here; the tail is measured eagerly
     graph_rec = {cls: list(v) for cls, v in rec.items()}
@@ -130,10 +140,8 @@ def instrumented_pass(sfm, n, plan, y):
     f.measure(0, -1)
     km = f.size()
     updates += kin
-    rec["cofactor"].append((kin, 2 * kin))
-    for cls in ("coal_insert", "coal_accum", "count"):
-        rec[cls].append((2 * kin, 2 * kin))
-    rec["scatter"].append((2 * kin, km))
+    rec["insert"].append((kin, km))
+    rec["compact"].append((kin, km))
     coal_elems += 2 * kin
     rec["prob"].append((km, km))
     f.amplitude(y)
@@ -241,8 +249,10 @@ def oracle_step(n, plan, y):
     for op in plan:
         if op[0] == "C":
             f.apply_clifford(op[1])
-        elif op[0] == "N":
+        elif op[0] in ("N", "NK"):
             f.apply_nonclifford(op[1], op[2], op[3], op[4])
+            if op[0] == "NK":
+                f.coalesce(DROP_EPS)
         elif op[0] == "K":
             f.coalesce(DROP_EPS)
     f.measure(0, -1)
@@ -274,10 +284,12 @@ def run_reference(args, rank, world):
         if op[0] == "C":
             f.apply_clifford(op[1])
             updates += len(op[1]) * k
-        elif op[0] == "N":
+        elif op[0] in ("N", "NK"):
             f.apply_nonclifford(op[1], op[2], op[3], op[4])
             updates += k
             k = f.size()
+            if op[0] == "NK":
+                k = f.coalesce(DROP_EPS)
         elif op[0] == "K":
             k = f.coalesce(DROP_EPS)
     updates += f.size()
@@ -355,6 +367,8 @@ def main():
             if op[0] == "C":
                 fr.apply_clifford_device(dev_lists[di].data_ptr(), dev_lists[di].shape[0])
                 di += 1
+            elif op[0] == "NK":
+                fr.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], DROP_EPS)
             elif op[0] == "N":
                 fr.apply_nonclifford(op[1], op[2], op[3], op[4])
             elif op[0] == "K":
@@ -373,7 +387,7 @@ def main():
     # per-class device time of one eager step -> dominant kernel class
     per_class = {}
     for cls in sf.KERNEL_CLASSES:
-        if cls in ("export", "reset"):
+        if cls in ("export", "reset", "filter"):
             continue
         frame.time_kernel(cls)
         async_part(frame)
@@ -467,6 +481,8 @@ def main():
         for op in plan:
             if op[0] == "C":
                 e2e_frame.apply_clifford(op[1])
+            elif op[0] == "NK":
+                e2e_frame.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], DROP_EPS)
             elif op[0] == "N":
                 e2e_frame.apply_nonclifford(op[1], op[2], op[3], op[4])
             elif op[0] == "K":
@@ -552,10 +568,10 @@ def main():
 
 def graph_launch_count(plan) -> int:
     """Kernels in the captured part of a step: reset, 2 per Clifford batch
-    (tableau + affine), 2 per branch (prep + per-element), 6 per coalesce."""
+    (tableau + affine), 1 per unmerged branch, 2 per merge (insert + compact)."""
     cnt = 1
     for op in plan:
-        cnt += {"C": 2, "N": 2, "K": 6}[op[0]]
+        cnt += {"C": 2, "N": 1, "K": 2, "NK": 2}[op[0]]
     return cnt
 
 

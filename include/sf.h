@@ -76,7 +76,7 @@ enum { SF_T = 0,      /* diag(1, e^{i pi/4}) on q0 */
  * a = 1) on `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
  * 1 <= n_qubits <= 1024.  max_elems bounds the number of frame elements that
  * any step may hold, including the children of a branch before coalescing.
- * Device memory: about max_elems * (16 W + 56) bytes plus O(n^2) for the
+ * Device memory: about max_elems * (24 W + 72) bytes plus O(n^2) for the
  * tableau.  Synchronises. */
 sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf_handle* out);
 
@@ -104,6 +104,13 @@ sf_status sf_apply_clifford_device(sf_handle h, const sf_gate* dev_gates, uint64
  * SF_CPHASE only.  Asynchronous; exceeding max_elems is reported by the next
  * synchronising call. */
 sf_status sf_apply_nonclifford(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta);
+
+/* sf_apply_nonclifford followed by sf_coalesce(h, drop_eps, NULL), done in one
+ * pass: the children are hashed straight into the merge table instead of being
+ * written out first.  Children whose coefficient is exactly zero are skipped.
+ * Same frame as the two calls; asynchronous. */
+sf_status sf_apply_nonclifford_coalesce(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
+                                        double drop_eps);
 
 /* Merge elements with equal phase vectors (summing amplitudes) and drop those
  * with |a| < drop_eps (Def. 1: the phase vectors of a frame are distinct).
@@ -146,14 +153,13 @@ sf_status sf_get_frame(sf_handle h, uint64_t* sigma, double* amp, uint64_t capac
 /* Kernel classes of this library, for sf_time_kernel(). */
 enum { SF_K_CLIFFORD = 0,      /* tableau update of a Clifford batch (single CTA) */
        SF_K_AFFINE = 1,        /* per-element affine phase-vector update */
-       SF_K_BRANCH_PREP = 2,   /* anticommutation masks of a diagonal gate (single CTA) */
-       SF_K_BRANCH = 3,        /* per-element branching */
-       SF_K_COAL_CLEAR = 4, SF_K_COAL_INSERT = 5, SF_K_COAL_ACCUM = 6,
-       SF_K_COUNT = 7, SF_K_SCAN = 8, SF_K_SCATTER = 9,  /* stream compaction */
-       SF_K_MEASURE_PREP = 10, /* cofactor planning (single CTA) */
-       SF_K_COFACTOR = 11,     /* per-element cofactor split */
-       SF_K_PROB = 12, SF_K_REDUCE = 13, SF_K_AMP_PREP = 14, SF_K_AMPLITUDE = 15,
-       SF_K_EXPORT = 16, SF_K_RESET = 17, SF_K_COUNT_CLASSES = 18 };
+       SF_K_BRANCH = 2,        /* per-element branching, children written unmerged */
+       SF_K_INSERT = 3,        /* children hashed into the slot table (branch, cofactor or frame) */
+       SF_K_COMPACT = 4,       /* slot table -> frame, dropping |a| < eps */
+       SF_K_MEASURE_PREP = 5,  /* cofactor planning (single CTA) */
+       SF_K_PROB = 6, SF_K_REDUCE = 7, SF_K_AMP_PREP = 8, SF_K_AMPLITUDE = 9,
+       SF_K_FILTER = 10,       /* collapse */
+       SF_K_EXPORT = 11, SF_K_RESET = 12, SF_K_COUNT_CLASSES = 13 };
 
 /* Number of CUDA kernels this handle has launched since it was created. */
 uint64_t sf_kernel_launches(sf_handle h);

@@ -236,8 +236,10 @@ def cuccaro_sample_ops(nbits: int, seed: int) -> List[Op]:
 
 # ---- driver ------------------------------------------------------------------------
 def run(sim, ops: Sequence[Op], drop_eps: float = 1e-12, batch_cliffords: bool = True):
-    """Walk ops against sim.  Consecutive Clifford gates are passed as one batch.
-    Returns the list of (q, p0, p1, outcome) for every measurement."""
+    """Walk ops against sim.  Consecutive Clifford gates are passed as one batch;
+    a non-Clifford gate directly followed by a coalesce goes to
+    sim.apply_nonclifford_coalesce when sim has it.  Returns the list of
+    (q, p0, p1, outcome) for every measurement."""
     pending: List[Tuple[int, int, int]] = []
     results = []
 
@@ -246,7 +248,12 @@ def run(sim, ops: Sequence[Op], drop_eps: float = 1e-12, batch_cliffords: bool =
             sim.apply_clifford(list(pending))
             pending.clear()
 
-    for op in ops:
+    fused = getattr(sim, "apply_nonclifford_coalesce", None)
+    skip_next = False
+    for i, op in enumerate(ops):
+        if skip_next:
+            skip_next = False
+            continue
         tag = op[0]
         if tag == "C":
             pending.append((op[1], op[2], op[3]))
@@ -254,7 +261,11 @@ def run(sim, ops: Sequence[Op], drop_eps: float = 1e-12, batch_cliffords: bool =
                 flush()
         elif tag == "N":
             flush()
-            sim.apply_nonclifford(op[1], op[2], op[3], op[4])
+            if fused is not None and i + 1 < len(ops) and ops[i + 1][0] == "K":
+                fused(op[1], op[2], op[3], op[4], drop_eps)  # branch and merge in one call
+                skip_next = True
+            else:
+                sim.apply_nonclifford(op[1], op[2], op[3], op[4])
         elif tag == "K":
             flush()
             sim.coalesce(drop_eps)

@@ -124,6 +124,8 @@ sf_status launch(sf_handle h, int id, const char* what, F&& fn) {
         if (s_ != SF_OK) return s_;                             \
     } while (0)
 
+sf_status clean_table(sf_handle h);
+
 // wait for the stream and report a deferred device error, restoring the frame
 // buffer that was current when it happened and clearing the error
 sf_status sync_check(sf_handle h) {
@@ -133,6 +135,8 @@ sf_status sync_check(sf_handle h) {
     if (st) {
         h->cur = (int)((st >> 8) & 1u);
         SF_CK(h, cudaMemsetAsync(h->d.status, 0, sizeof(uint32_t), h->stream));
+        sf_status cs = clean_table(h);
+        if (cs) return cs;
         SF_CK(h, cudaStreamSynchronize(h->stream));
         const uint32_t code = SF_ST_CODE(st);
         char site[32];
@@ -142,15 +146,23 @@ sf_status sync_check(sf_handle h) {
     return SF_OK;
 }
 
-sf_status coalesce_seq(sf_handle h, double eps, int in_buf, int out_buf) {
+// children of in_buf (kind: a diagonal gate, the frame itself or its cofactor
+// split) merged into out_buf through the slot table
+sf_status merge_seq(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta, double eps, int in_buf,
+                    int out_buf) {
     const SfDev& d = h->d;
     cudaStream_t s = h->stream;
-    SF_LAUNCH(h, SF_K_COAL_CLEAR, sf_launch_coal_clear(d, in_buf, s));
-    SF_LAUNCH(h, SF_K_COAL_INSERT, sf_launch_coal_insert(d, in_buf, s));
-    SF_LAUNCH(h, SF_K_COAL_ACCUM, sf_launch_coal_accum(d, in_buf, s));
-    SF_LAUNCH(h, SF_K_COUNT, sf_launch_count(d, in_buf, 0, eps * eps, 0, s));
-    SF_LAUNCH(h, SF_K_SCAN, sf_launch_scan(d, out_buf, s));
-    SF_LAUNCH(h, SF_K_SCATTER, sf_launch_scatter(d, in_buf, out_buf, 0, eps * eps, 0, s));
+    SF_LAUNCH(h, SF_K_INSERT, sf_launch_insert(d, kind, q0, q1, theta, in_buf, out_buf, s));
+    SF_LAUNCH(h, SF_K_COMPACT, sf_launch_compact(d, eps, out_buf, s));
+    return SF_OK;
+}
+
+// empty the slot table (after an error left it partly filled)
+sf_status clean_table(sf_handle h) {
+    const SfDev& d = h->d;
+    if (d.W == 1) SF_CK(h, cudaMemsetAsync(d.tkey, 0xff, d.tcap * sizeof(uint64_t), h->stream));
+    else SF_CK(h, cudaMemsetAsync(d.tstate, 0, d.tcap * sizeof(uint32_t), h->stream));
+    SF_CK(h, cudaMemsetAsync(d.tacc, 0, d.tcap * sizeof(double2), h->stream));
     return SF_OK;
 }
 
@@ -190,7 +202,9 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     SfDev& d = h->d;
     d.n = (int)n_qubits;
-    d.W = pow2_at_least(h->Wabi);
+    // words per phase vector: a power of two with at least one bit to spare
+    // above qubit n-1 (the slot table marks empty keys with that bit)
+    d.W = pow2_at_least((int)(n_qubits / 64) + 1);
     d.NT = std::max(32, (int)((n_qubits + 31) / 32) * 32);
     d.cap = max_elems;
     int dev = 0, sms = 0;
@@ -205,7 +219,7 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     const size_t n = n_qubits, W = d.W, cap = max_elems;
     unsigned long long slots = 1024;
     while (slots < 2 * cap) slots <<= 1;
-    d.slots_cap = slots;
+    d.tcap = slots;
 #define SF_ALLOC(p, cnt)                                       \
     if ((e = dalloc(h, &(p), (cnt))) != cudaSuccess) {         \
         sf_destroy(h);                                         \
@@ -226,9 +240,10 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     SF_ALLOC(d.kcnt, 2);
     SF_ALLOC(d.status, 1);
     SF_ALLOC(d.plan, plan_words((int)n, (int)W));
-    SF_ALLOC(d.slots, slots);
-    SF_ALLOC(d.rep, cap);
-    SF_ALLOC(d.blk, 2 * (size_t)d.nblk + 2);
+    if (W > 1) SF_ALLOC(d.tstate, slots);
+    SF_ALLOC(d.tkey, W * slots);
+    SF_ALLOC(d.tacc, slots);
+    SF_ALLOC(d.tsize, 1);
     SF_ALLOC(d.red, 4 * (size_t)d.nblk);
     SF_ALLOC(d.out, 8);
     SF_ALLOC(h->dy, W);
@@ -249,6 +264,10 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
         return fail(nullptr, SF_ENOMEM, "pinned host allocation failed");
     }
     cudaMemsetAsync(d.status, 0, sizeof(uint32_t), h->stream);
+    if (clean_table(h) != SF_OK) {
+        sf_destroy(h);
+        return fail(nullptr, SF_ECUDA, "table initialisation failed");
+    }
     cudaMemsetAsync(d.plan, 0, plan_words((int)n, (int)W) * sizeof(uint64_t), h->stream);
     cudaEventRecord(h->stage_ev, h->stream);
     h->cur = 0;
@@ -345,8 +364,21 @@ sf_status sf_apply_nonclifford(sf_handle h, uint32_t kind, uint32_t q0, uint32_t
     if (q0 >= h->n) return fail(h, SF_EINVAL, "qubit out of range");
     if (kind == SF_CPHASE && (q1 >= h->n || q1 == q0)) return fail(h, SF_EINVAL, "bad second qubit");
     const uint32_t q1v = kind == SF_CPHASE ? q1 : 0u;
-    SF_LAUNCH(h, SF_K_BRANCH_PREP, sf_launch_branch_prep(h->d, kind, q0, q1v, theta, h->cur, h->stream));
-    SF_LAUNCH(h, SF_K_BRANCH, sf_launch_branch(h->d, h->cur, h->cur ^ 1, h->stream));
+    SF_LAUNCH(h, SF_K_BRANCH, sf_launch_branch(h->d, kind, q0, q1v, theta, h->cur, h->cur ^ 1, h->stream));
+    h->cur ^= 1;
+    return SF_OK;
+}
+
+sf_status sf_apply_nonclifford_coalesce(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
+                                        double drop_eps) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (kind > SF_CPHASE) return fail(h, SF_EINVAL, "unknown non-Clifford kind");
+    if (q0 >= h->n) return fail(h, SF_EINVAL, "qubit out of range");
+    if (kind == SF_CPHASE && (q1 >= h->n || q1 == q0)) return fail(h, SF_EINVAL, "bad second qubit");
+    if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");
+    const uint32_t q1v = kind == SF_CPHASE ? q1 : 0u;
+    sf_status st = merge_seq(h, kind, q0, q1v, theta, drop_eps, h->cur, h->cur ^ 1);
+    if (st) return st;
     h->cur ^= 1;
     return SF_OK;
 }
@@ -354,7 +386,7 @@ sf_status sf_apply_nonclifford(sf_handle h, uint32_t kind, uint32_t q0, uint32_t
 sf_status sf_coalesce(sf_handle h, double drop_eps, uint64_t* out_size) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
     if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");
-    sf_status cs = coalesce_seq(h, drop_eps, h->cur, h->cur ^ 1);
+    sf_status cs = merge_seq(h, SF_INSERT_FRAME, 0u, 0u, 0.0, drop_eps, h->cur, h->cur ^ 1);
     if (cs) return cs;
     h->cur ^= 1;
     if (out_size) {
@@ -375,9 +407,9 @@ sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, d
     sf_status st = sync_check(h);
     if (st) return st;
     if (h->hmeta[2]) {
-        SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cofactor_split(h->d, h->cur, h->cur ^ 1, h->stream));
-        st = coalesce_seq(h, 1e-12, h->cur ^ 1, h->cur);
+        st = merge_seq(h, SF_INSERT_COFACTOR, 0u, 0u, 0.0, 1e-12, h->cur, h->cur ^ 1);
         if (st) return st;
+        h->cur ^= 1;
     }
     SF_LAUNCH(h, SF_K_PROB, sf_launch_prob(h->d, h->cur, h->stream));
     SF_LAUNCH(h, SF_K_REDUCE, sf_launch_reduce_final(h->d, 0, h->stream));
@@ -390,9 +422,8 @@ sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, d
     if (collapse_to >= 0) {
         if (!(pr[collapse_to] > 0.0)) return fail(h, SF_ESTATE, "collapse onto an outcome of probability 0");
         const int in = h->cur, outb = h->cur ^ 1;
-        SF_LAUNCH(h, SF_K_COUNT, sf_launch_count(h->d, in, 1, 0.0, collapse_to, h->stream));
-        SF_LAUNCH(h, SF_K_SCAN, sf_launch_scan(h->d, outb, h->stream));
-        SF_LAUNCH(h, SF_K_SCATTER, sf_launch_scatter(h->d, in, outb, 1, 0.0, collapse_to, h->stream));
+        SF_CK(h, cudaMemsetAsync(h->d.kcnt + outb, 0, sizeof(unsigned long long), h->stream));
+        SF_LAUNCH(h, SF_K_FILTER, sf_launch_filter(h->d, collapse_to, in, outb, h->stream));
         h->cur ^= 1;
     }
     return SF_OK;

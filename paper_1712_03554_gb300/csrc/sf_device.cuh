@@ -52,29 +52,31 @@ struct SfDev {
     uint32_t* status;
     // plan (written by a single-CTA prep kernel, read by the per-element kernels)
     uint64_t* plan;
-    // scratch
-    uint32_t* slots;           // hash table, slots_cap entries
-    unsigned long long slots_cap;
-    uint32_t* rep;             // [cap]
-    unsigned long long* blk;   // [2 * nblk + 2] per-CTA counts / offsets
+    // slot table used by coalescing (children are hashed into it, amplitudes
+    // accumulate there, the compaction pass empties it again)
+    uint32_t* tstate;          // [tcap] 0 empty, 1 being written, 2 ready (W > 1 only)
+    uint64_t* tkey;            // [W][tcap] phase vector of the slot (W = 1: all ones = empty)
+    double2* tacc;             // [tcap] accumulated amplitude
+    unsigned long long tcap;   // power of two >= 2 cap
+    unsigned long long* tsize; // slots in use by the current merge
     double* red;               // [4 * nblk] reduction partials
     double* out;               // [8] small results (p0, p1, amplitude re, im)
 };
+
+// An empty slot key: phase vectors never set bit 63 of their last word
+// (the word count W leaves at least one spare bit above qubit n-1).
+#define SF_EMPTY_KEY 0xffffffffffffffffull
 
 // ---- plan layout (in 64-bit words) ---------------------------------------
 // affine map of a Clifford batch: sigma'_h = parity(A_h & sigma) ^ t_h
 // A is stored by columns: column j (the image of e_j) at [j*W, j*W+W).
 __host__ __device__ inline size_t plan_AT(int n, int W) { return 0; }
 __host__ __device__ inline size_t plan_t(int n, int W) { return (size_t)n * W; }
-// branch plan: header word, then SF_BR_MAXG groups of (u[W], nt, terms[4] of (re, im, v[W]))
+// at most four Z-type Pauli terms per diagonal gate, grouped by anticommutation mask
 #define SF_BR_MAXG 4
 #define SF_BR_MAXT 4
-__host__ __device__ inline size_t plan_br(int n, int W) { return (size_t)n * W + W; }
-__host__ __device__ inline size_t br_group_words(int W) { return (size_t)W + 1 + SF_BR_MAXT * (2 + W); }
 // cofactor plan
-__host__ __device__ inline size_t plan_cf(int n, int W) {
-    return plan_br(n, W) + 1 + SF_BR_MAXG * br_group_words(W);
-}
+__host__ __device__ inline size_t plan_cf(int n, int W) { return (size_t)n * W + W; }
 // cofactor: u'[n][W], v'[n][W], eps i-powers as two bit planes [2][W], kappa[4] doubles, tau0[W], tau1[W], v[W]
 __host__ __device__ inline size_t cf_u(int n, int W) { return plan_cf(n, W); }
 __host__ __device__ inline size_t cf_v(int n, int W) { return cf_u(n, W) + (size_t)n * W; }
@@ -152,21 +154,22 @@ __device__ __forceinline__ void set_status(uint32_t* st, uint32_t code, int buf,
 void sf_launch_reset(const SfDev& d, int buf, cudaStream_t s);
 void sf_launch_clifford(const SfDev& d, const void* dev_gates, int ngates, int buf, uint64_t* gws,
                         cudaStream_t s);
-void sf_launch_branch_prep(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int buf,
-                           cudaStream_t s);
 void sf_launch_measure_prep(const SfDev& d, uint32_t q, int buf, uint64_t* gws, cudaStream_t s);
 void sf_launch_amp_prep(const SfDev& d, const uint64_t* dev_y, cudaStream_t s);
 size_t sf_tableau_smem_bytes(int n, int W, int NT);
 
 void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s);
-void sf_launch_branch(const SfDev& d, int in_buf, int out_buf, cudaStream_t s);
-void sf_launch_coal_clear(const SfDev& d, int buf, cudaStream_t s);
-void sf_launch_coal_insert(const SfDev& d, int buf, cudaStream_t s);
-void sf_launch_coal_accum(const SfDev& d, int buf, cudaStream_t s);
-void sf_launch_count(const SfDev& d, int buf, int mode, double eps2, int x, cudaStream_t s);
-void sf_launch_scan(const SfDev& d, int out_buf, cudaStream_t s);
-void sf_launch_scatter(const SfDev& d, int in_buf, int out_buf, int mode, double eps2, int x, cudaStream_t s);
-void sf_launch_cofactor_split(const SfDev& d, int in_buf, int out_buf, cudaStream_t s);
+// children of a diagonal gate written out unmerged (in -> out)
+void sf_launch_branch(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
+                      int out_buf, cudaStream_t s);
+// children hashed into the slot table: diagonal gate (kind < 4), plain
+// coalescing of a frame (kind = SF_INSERT_FRAME) or cofactor split (kind = SF_INSERT_COFACTOR)
+#define SF_INSERT_FRAME 16u
+#define SF_INSERT_COFACTOR 17u
+void sf_launch_insert(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
+                      int out_buf, cudaStream_t s);
+void sf_launch_compact(const SfDev& d, double eps, int out_buf, cudaStream_t s);
+void sf_launch_filter(const SfDev& d, int x, int in_buf, int out_buf, cudaStream_t s);
 void sf_launch_prob(const SfDev& d, int buf, cudaStream_t s);
 void sf_launch_reduce_final(const SfDev& d, int what, cudaStream_t s);
 void sf_launch_amplitude(const SfDev& d, int buf, cudaStream_t s);

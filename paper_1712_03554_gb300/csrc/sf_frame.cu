@@ -3,11 +3,12 @@
 //   k_affine      per-element Clifford update sigma' = A sigma ^ t (Sec. III,
 //                 ROTATE: the memoised row operations of Invariant 1 applied
 //                 to every phase vector), 4-bit table lookups in shared memory
-//   k_branch      diagonal non-Clifford branching (Sec. IV)
-//   k_coal_*      COALESCE in the set sense of Def. 1: hash equal phase
-//                 vectors, segmented amplitude sum, drop |a| < eps, stable
-//                 stream compaction
-//   k_cof_split   cofactor children of every element (COFACTOR, Sec. III)
+//   k_branch      diagonal non-Clifford branching (Sec. IV), children unmerged
+//   k_insert      children (of a branch, a cofactor split, or the frame itself)
+//                 hashed into a slot table with FP64 amplitude accumulation
+//   k_compact     COALESCE in the set sense of Def. 1: emit every slot with
+//                 |a| >= eps and leave the table empty
+//   k_filter      collapse after a measurement
 //   k_prob        measurement probabilities (Sec. IV, measuring F)
 //   k_amplitude   <y|Psi> (Observation 1)
 //   k_export      canonical-convention amplitudes for export
@@ -18,7 +19,6 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr uint32_t kEmpty = 0xffffffffu;
 
 __device__ __forceinline__ unsigned long long table_size(unsigned long long k, unsigned long long cap) {
     unsigned long long t = 1024;
@@ -75,14 +75,6 @@ __device__ void block_sum(double* v, double (*sh)[32]) {
             v[c] = warp_sum(t);
         }
     }
-}
-
-// element range of this CTA for chunked (order-preserving) passes
-__device__ __forceinline__ void chunk_range(unsigned long long k, int nblk, unsigned long long& lo,
-                                            unsigned long long& hi) {
-    const unsigned long long ch = (k + nblk - 1) / nblk;
-    lo = min(k, ch * blockIdx.x);
-    hi = min(k, lo + ch);
 }
 
 // ---- per-element amplitude of D^sigma phi_0(M) ------------------------------
@@ -245,30 +237,160 @@ __global__ void __launch_bounds__(kThreads) k_affine_cols(SfDev d, int buf) {
 }
 
 // ---------------------------------------------------------------------------
+// Plan of a diagonal gate sum_j c_j Z^{w_j} (Sec. IV), computed by one warp of
+// every CTA from the tableau: Z^w = eps D^u M^v with u_h = [Z^w anticommutes
+// with M_h], v_h = [Z^w anticommutes with D_h], so that
+// Z^w D^sigma phi_0 = eps (-1)^{v.sigma} D^{sigma ^ u} phi_0.  eps may be +-i.
+// Terms with equal u form one group (one child per element).
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_branch(SfDev d, int in_buf, int out_buf) {
-    __shared__ uint64_t sh_u[SF_BR_MAXG][W];
-    __shared__ uint64_t sh_v[SF_BR_MAXG][SF_BR_MAXT][W];
-    __shared__ double2 sh_c[SF_BR_MAXG][SF_BR_MAXT];
-    __shared__ int sh_nt[SF_BR_MAXG];
-    if (*d.status) return;
-    const int n = d.n;
-    const uint64_t* pb = d.plan + plan_br(n, W);
-    const int ng = (int)pb[0];
-    const size_t gw = br_group_words(W);
-    if (threadIdx.x < ng) {
-        const uint64_t* G = pb + 1 + threadIdx.x * gw;
-        for (int w = 0; w < W; w++) sh_u[threadIdx.x][w] = G[w];
-        const int nt = (int)G[W];
-        sh_nt[threadIdx.x] = nt;
-        for (int t = 0; t < nt; t++) {
-            const uint64_t* Tm = G + W + 1 + t * (2 + W);
-            sh_c[threadIdx.x][t] = make_double2(__longlong_as_double((long long)Tm[0]),
-                                                __longlong_as_double((long long)Tm[1]));
-            for (int w = 0; w < W; w++) sh_v[threadIdx.x][t][w] = Tm[2 + w];
+struct BrPlan {
+    int ng, bad;
+    int nt[SF_BR_MAXG];
+    uint64_t u[SF_BR_MAXG][W];
+    uint64_t v[SF_BR_MAXG][SF_BR_MAXT][W];
+    double2 c[SF_BR_MAXG][SF_BR_MAXT];
+};
+
+template <int W>
+__device__ __forceinline__ void warp_pauli_product(Pauli<W>& p) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        Pauli<W> o;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            o.x[w] = __shfl_xor_sync(SF_FULL, p.x[w], off);
+            o.z[w] = __shfl_xor_sync(SF_FULL, p.z[w], off);
         }
+        o.e = __shfl_xor_sync(SF_FULL, p.e, off);
+        pauli_mul<W>(p, o);
     }
+}
+
+__device__ __forceinline__ uint64_t warp_or(uint64_t v) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v |= __shfl_xor_sync(SF_FULL, v, off);
+    return v;
+}
+
+// called by the 32 lanes of one warp; lane 0 writes P
+template <int W>
+__device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
+                                 BrPlan<W>& P) {
+    const int lane = threadIdx.x & 31, n = d.n;
+    double th = theta;
+    if (kind == 0) th = 0.78539816339744830962;
+    if (kind == 1) th = -0.78539816339744830962;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    int nt;
+    int wq[SF_BR_MAXT][2];
+    double2 cf[SF_BR_MAXT];
+    if (kind <= 2) {  // P(theta) = (1 + e^{i theta})/2 I + (1 - e^{i theta})/2 Z_q0
+        nt = 2;
+        wq[0][0] = -1; wq[0][1] = -1; cf[0] = make_double2((1.0 + cs) * 0.5, sn * 0.5);
+        wq[1][0] = (int)q0; wq[1][1] = -1; cf[1] = make_double2((1.0 - cs) * 0.5, -sn * 0.5);
+    } else {  // CR(theta) = I + (e^{i theta} - 1)(I - Z_c - Z_t + Z_c Z_t)/4
+        nt = 4;
+        const double2 dd = make_double2((cs - 1.0) * 0.25, sn * 0.25);
+        wq[0][0] = -1; wq[0][1] = -1; cf[0] = make_double2(1.0 + dd.x, dd.y);
+        wq[1][0] = (int)q0; wq[1][1] = -1; cf[1] = make_double2(-dd.x, -dd.y);
+        wq[2][0] = (int)q1; wq[2][1] = -1; cf[2] = make_double2(-dd.x, -dd.y);
+        wq[3][0] = (int)q0; wq[3][1] = (int)q1; cf[3] = dd;
+    }
+    uint64_t um[SF_BR_MAXT][W], vm[SF_BR_MAXT][W];
+    int epsq[SF_BR_MAXT];
+    int bad = 0;
+    for (int j = 0; j < nt; j++) {
+        uint64_t wz[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) { wz[w] = 0; um[j][w] = 0; vm[j][w] = 0; }
+        for (int a = 0; a < 2; a++)
+            if (wq[j][a] >= 0) wz[wq[j][a] >> 6] ^= 1ull << (wq[j][a] & 63);
+        Pauli<W> p;
+        pauli_id<W>(p);
+        for (int h = lane; h < n; h += 32) {
+            uint64_t mx[W], dx[W];
+#pragma unroll
+            for (int w = 0; w < W; w++) { mx[w] = __ldg(&d.mx[w * n + h]); dx[w] = __ldg(&d.dx[w * n + h]); }
+            const bool ub = popc_and<W>(mx, wz) & 1;
+            const bool vb = popc_and<W>(dx, wz) & 1;
+            if (ub) {
+                um[j][h >> 6] |= 1ull << (h & 63);
+                Pauli<W> dh;
+#pragma unroll
+                for (int w = 0; w < W; w++) { dh.x[w] = dx[w]; dh.z[w] = __ldg(&d.dz[w * n + h]); }
+                dh.e = (int)__ldg(&d.de[h]);
+                pauli_mul<W>(p, dh);
+            }
+            if (vb) {
+                vm[j][h >> 6] |= 1ull << (h & 63);
+                Pauli<W> m;
+#pragma unroll
+                for (int w = 0; w < W; w++) { m.x[w] = mx[w]; m.z[w] = __ldg(&d.mz[w * n + h]); }
+                m.e = 0;
+                pauli_mul<W>(p, m);
+            }
+        }
+        warp_pauli_product<W>(p);
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            um[j][w] = warp_or(um[j][w]);
+            vm[j][w] = warp_or(vm[j][w]);
+            if (p.x[w] != 0 || p.z[w] != wz[w]) bad = 1;
+        }
+        epsq[j] = (4 - p.e) & 3;
+    }
+    if (lane != 0) return;
+    int gid[SF_BR_MAXT];
+    int ng = 0;
+    for (int j = 0; j < nt; j++) {
+        int found = -1;
+        for (int j2 = 0; j2 < j; j2++) {
+            bool same = true;
+            for (int w = 0; w < W; w++) same &= um[j2][w] == um[j][w];
+            if (same) { found = gid[j2]; break; }
+        }
+        gid[j] = found >= 0 ? found : ng++;
+    }
+    P.ng = ng;
+    P.bad = bad;
+    for (int g = 0; g < ng; g++) P.nt[g] = 0;
+    for (int j = 0; j < nt; j++) {
+        const int g = gid[j], t = P.nt[g]++;
+        for (int w = 0; w < W; w++) {
+            P.u[g][w] = um[j][w];
+            P.v[g][t][w] = vm[j][w];
+        }
+        P.c[g][t] = ipow_mul(cf[j], epsq[j]);
+    }
+}
+
+// coefficient of group g for phase vector s
+template <int W>
+__device__ __forceinline__ double2 group_coef(const BrPlan<W>& P, int g, const uint64_t* s) {
+    double2 cf = make_double2(0.0, 0.0);
+    for (int t = 0; t < P.nt[g]; t++) {
+        const double sg = (popc_and<W>(P.v[g][t], s) & 1) ? -1.0 : 1.0;
+        cf.x += sg * P.c[g][t].x;
+        cf.y += sg * P.c[g][t].y;
+    }
+    return cf;
+}
+
+// children of a diagonal gate written out unmerged: child g of element j at
+// g * k + j
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_branch(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
+                                                     int in_buf, int out_buf) {
+    __shared__ BrPlan<W> P;
+    if (*d.status) return;
+    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, theta, P);
     __syncthreads();
+    if (P.bad) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 23u);
+        return;
+    }
+    const int ng = P.ng;
     const unsigned long long k = d.kcnt[in_buf];
     if ((unsigned long long)ng * k > d.cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_CAPACITY, in_buf);
@@ -286,16 +408,11 @@ __global__ void __launch_bounds__(kThreads) k_branch(SfDev d, int in_buf, int ou
         load_sig<W>(Si, cap, j, s);
         const double2 a = Ai[j];
         for (int g = 0; g < ng; g++) {
-            double2 cf = make_double2(0.0, 0.0);
-            for (int t = 0; t < sh_nt[g]; t++) {
-                const double sg = (popc_and<W>(sh_v[g][t], s) & 1) ? -1.0 : 1.0;
-                cf.x += sg * sh_c[g][t].x;
-                cf.y += sg * sh_c[g][t].y;
-            }
+            const double2 cf = group_coef<W>(P, g, s);
             const unsigned long long o = (unsigned long long)g * k + j;
             uint64_t c[W];
 #pragma unroll
-            for (int w = 0; w < W; w++) c[w] = s[w] ^ sh_u[g][w];
+            for (int w = 0; w < W; w++) c[w] = s[w] ^ P.u[g][w];
             store_sig<W>(So, cap, o, c);
             Ao[o] = cmul(cf, a);
         }
@@ -303,221 +420,271 @@ __global__ void __launch_bounds__(kThreads) k_branch(SfDev d, int in_buf, int ou
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_coal_clear(SfDev d, int buf) {
-    if (*d.status) return;
-    const unsigned long long T = table_size(d.kcnt[buf], d.slots_cap);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < T;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        d.slots[i] = kEmpty;
-}
-
+// Slot table.  W = 1: the key word itself is claimed by compare-and-swap
+// (all ones = empty, never a phase vector).  W > 1: a state word is claimed
+// (empty -> being written), the key is written, then published (ready);
+// readers of a slot being written wait for it with a bounded spin.
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_coal_insert(SfDev d, int buf) {
-    if (*d.status) return;
-    const unsigned long long k = d.kcnt[buf];
-    const unsigned long long T = table_size(k, d.slots_cap);
-    const uint64_t* S = d.sig[buf];
-    const uint64_t cap = d.cap;
-    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        uint64_t s[W];
-        load_sig<W>(S, cap, j, s);
-        unsigned long long hh = hash_sig<W>(s) & (T - 1);
-        uint32_t rep = kEmpty;
-        for (unsigned long long probe = 0; probe < T; probe++) {
-            uint32_t cur = d.slots[hh];
-            if (cur == kEmpty) {
-                cur = atomicCAS(&d.slots[hh], kEmpty, (uint32_t)j);
-                if (cur == kEmpty) { rep = (uint32_t)j; break; }
+__device__ __forceinline__ bool table_insert(const SfDev& d, unsigned long long T, const uint64_t* key, double2 c) {
+    const unsigned long long tcap = d.tcap;
+    unsigned long long slot = hash_sig<W>(key) & (T - 1);
+    for (unsigned long long probe = 0; probe < T; probe++) {
+        if constexpr (W == 1) {
+            unsigned long long* K = reinterpret_cast<unsigned long long*>(d.tkey);
+            unsigned long long cur = *(volatile unsigned long long*)&K[slot];
+            if (cur == SF_EMPTY_KEY) cur = atomicCAS(&K[slot], SF_EMPTY_KEY, (unsigned long long)key[0]);
+            if (cur == SF_EMPTY_KEY || cur == key[0]) {
+                atomicAdd(&d.tacc[slot].x, c.x);
+                atomicAdd(&d.tacc[slot].y, c.y);
+                return true;
             }
+        } else {
+            uint32_t st = *(volatile uint32_t*)&d.tstate[slot];
+            if (st == 0) {
+                st = atomicCAS(&d.tstate[slot], 0u, 1u);
+                if (st == 0) {
+#pragma unroll
+                    for (int w = 0; w < W; w++) d.tkey[(size_t)w * tcap + slot] = key[w];
+                    __threadfence();
+                    atomicExch(&d.tstate[slot], 2u);
+                    atomicAdd(&d.tacc[slot].x, c.x);
+                    atomicAdd(&d.tacc[slot].y, c.y);
+                    return true;
+                }
+            }
+            for (int spin = 0; st == 1u && spin < (1 << 22); spin++) st = *(volatile uint32_t*)&d.tstate[slot];
+            if (st != 2u) return false;
+            __threadfence();
             bool eq = true;
 #pragma unroll
-            for (int w = 0; w < W; w++) eq &= (S[(size_t)w * cap + cur] == s[w]);
-            if (eq) { rep = cur; break; }
-            hh = (hh + 1) & (T - 1);
+            for (int w = 0; w < W; w++) eq &= (*(volatile uint64_t*)&d.tkey[(size_t)w * tcap + slot] == key[w]);
+            if (eq) {
+                atomicAdd(&d.tacc[slot].x, c.x);
+                atomicAdd(&d.tacc[slot].y, c.y);
+                return true;
+            }
         }
-        if (rep == kEmpty) set_status(d.status, SF_ST_TIMEOUT, buf);
-        d.rep[j] = rep;
+        slot = (slot + 1) & (T - 1);
     }
+    return false;
 }
 
-__global__ void k_coal_accum(SfDev d, int buf) {
-    if (*d.status) return;
-    const unsigned long long k = d.kcnt[buf];
-    double2* A = d.amp[buf];
-    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t r = d.rep[j];
-        if (r != (uint32_t)j) {
-            const double2 a = A[j];
-            atomicAdd(&A[r].x, a.x);
-            atomicAdd(&A[r].y, a.y);
-        }
-    }
-}
-
-// keep predicate.  mode 0: representative with |a| >= eps; mode 1: bit `bit`
-// of sigma equals x.
+// Cofactor children (COFACTOR, Sec. III) of one element from the plan written
+// by k_measure_prep: for outcome x, y = x ^ parity(v & sigma); the child starts
+// at (tau_y, kappa_y) and the old destabilizers of sigma are applied one at a
+// time in the new basis: D_h phi'(t) = eps_h (-1)^{v'_h . t} phi'(t ^ u'_h).
 template <int W>
-__device__ __forceinline__ bool keep_elem(const SfDev& d, int buf, unsigned long long j, int mode, double eps2,
-                                          int bit, int x) {
-    if (mode == 0) {
-        if (d.rep[j] != (uint32_t)j) return false;
-        const double2 a = d.amp[buf][j];
-        return a.x * a.x + a.y * a.y >= eps2;
-    }
-    const uint64_t w = d.sig[buf][(size_t)(bit >> 6) * d.cap + j];
-    return (int)((w >> (bit & 63)) & 1) == x;
-}
+struct CofPlan {
+    double2 kap[2];
+    uint64_t vq[W], tau[2][W], eps0[W], eps1[W];
+};
 
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_count(SfDev d, int buf, int mode, double eps2, int x) {
-    __shared__ double sh[1][32];
-    if (*d.status) return;
-    const int bit = mode == 1 ? d.meta[1] : 0;
-    if (bit < 0 || bit >= d.n) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, buf, 20u);
-        return;
-    }
-    unsigned long long lo, hi;
-    chunk_range(d.kcnt[buf], d.nblk, lo, hi);
-    double c = 0;
-    for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x)
-        c += keep_elem<W>(d, buf, j, mode, eps2, bit, x) ? 1.0 : 0.0;
-    block_sum<1>(&c, sh);
-    if (threadIdx.x == 0) d.blk[blockIdx.x] = (unsigned long long)c;
-}
-
-// exclusive scan of the per-CTA counts; total -> kcnt[out_buf]
-__global__ void __launch_bounds__(1024) k_scan(SfDev d, int out_buf) {
-    __shared__ unsigned long long sh[1024];
-    if (*d.status) return;
-    const int nb = d.nblk, t = threadIdx.x;
-    unsigned long long carry = 0;
-    for (int base = 0; base < nb; base += 1024) {
-        const unsigned long long v = (base + t < nb) ? d.blk[base + t] : 0ull;
-        sh[t] = v;
-        __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {
-            unsigned long long a = t >= o ? sh[t - o] : 0ull;
-            __syncthreads();
-            sh[t] += a;
-            __syncthreads();
-        }
-        if (base + t < nb) d.blk[nb + base + t] = carry + sh[t] - v;
-        carry += sh[1023];
-        __syncthreads();
-    }
-    if (t == 0) d.kcnt[out_buf] = carry;
-}
-
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_scatter(SfDev d, int in_buf, int out_buf, int mode, double eps2, int x) {
-    __shared__ int wc[kThreads / 32];
-    __shared__ int wo[kThreads / 32 + 1];
-    if (*d.status) return;
-    const int bit = mode == 1 ? d.meta[1] : 0;
-    if (bit < 0 || bit >= d.n) return;
-    double scale = 1.0;
-    if (mode == 1) scale = 1.0 / sqrt(d.out[x]);
-    unsigned long long lo, hi;
-    chunk_range(d.kcnt[in_buf], d.nblk, lo, hi);
-    unsigned long long base = d.blk[d.nblk + blockIdx.x];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint64_t* Si = d.sig[in_buf];
-    uint64_t* So = d.sig[out_buf];
-    const uint64_t cap = d.cap;
-    for (unsigned long long t0 = lo; t0 < hi; t0 += blockDim.x) {
-        const unsigned long long j = t0 + threadIdx.x;
-        const bool kp = j < hi && keep_elem<W>(d, in_buf, j, mode, eps2, bit, x);
-        const unsigned bal = __ballot_sync(SF_FULL, kp);
-        if (lane == 0) wc[wid] = __popc(bal);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int s = 0;
-            for (int i = 0; i < nw; i++) { wo[i] = s; s += wc[i]; }
-            wo[nw] = s;
-        }
-        __syncthreads();
-        if (kp) {
-            const unsigned long long o = base + wo[wid] + __popc(bal & ((1u << lane) - 1u));
-            uint64_t s[W];
-            load_sig<W>(Si, cap, j, s);
-            store_sig<W>(So, cap, o, s);
-            double2 a = d.amp[in_buf][j];
-            a.x *= scale;
-            a.y *= scale;
-            d.amp[out_buf][o] = a;
-        }
-        base += wo[nw];
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_cof_split(SfDev d, int in_buf, int out_buf) {
-    if (*d.status) return;
-    if (!d.meta[2]) return;
+__device__ __forceinline__ void load_cof_plan(const SfDev& d, CofPlan<W>& C) {
     const int n = d.n;
     const uint64_t* pl = d.plan;
+    const size_t ko = cf_kappa(n, W);
+    C.kap[0] = make_double2(__longlong_as_double((long long)pl[ko]), __longlong_as_double((long long)pl[ko + 1]));
+    C.kap[1] = make_double2(__longlong_as_double((long long)pl[ko + 2]), __longlong_as_double((long long)pl[ko + 3]));
+    for (int w = 0; w < W; w++) {
+        C.vq[w] = pl[cf_vq(n, W) + w];
+        C.tau[0][w] = pl[cf_tau(n, W) + w];
+        C.tau[1][w] = pl[cf_tau(n, W) + W + w];
+        C.eps0[w] = pl[cf_eps(n, W) + w];
+        C.eps1[w] = pl[cf_eps(n, W) + W + w];
+    }
+}
+
+template <int W>
+__device__ __forceinline__ double2 cof_child(const SfDev& d, const CofPlan<W>& C, const uint64_t* s, double2 a,
+                                             int x, uint64_t* t) {
+    const int n = d.n;
+    const uint64_t* U = d.plan + cf_u(n, W);
+    const uint64_t* V = d.plan + cf_v(n, W);
+    const int y = x ^ (popc_and<W>(C.vq, s) & 1);
+#pragma unroll
+    for (int w = 0; w < W; w++) t[w] = C.tau[y][w];
+    int ip = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        uint64_t bits = s[w];
+        while (bits) {
+            const int b = __ffsll((long long)bits) - 1;
+            bits &= bits - 1;
+            const int h = 64 * w + b;
+            uint64_t vv[W];
+#pragma unroll
+            for (int u = 0; u < W; u++) vv[u] = __ldg(&V[(size_t)h * W + u]);
+            ip += (int)((C.eps0[w] >> b) & 1) + 2 * (int)((C.eps1[w] >> b) & 1) + 2 * (popc_and<W>(vv, t) & 1);
+#pragma unroll
+            for (int u = 0; u < W; u++) t[u] ^= __ldg(&U[(size_t)h * W + u]);
+        }
+    }
+    return ipow_mul(cmul(C.kap[y], a), ip & 3);
+}
+
+// Hash the children of every element of in_buf into the slot table,
+// accumulating amplitudes.  kind < 4: a diagonal gate; SF_INSERT_FRAME: the
+// elements themselves; SF_INSERT_COFACTOR: the two cofactor children.  Sets
+// the table size for the compaction and zeroes the output count.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_insert(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
+                                                     int in_buf, int out_buf) {
+    __shared__ BrPlan<W> P;
+    __shared__ CofPlan<W> CP;
+    if (*d.status) return;
+    int ng = 1;
+    if (kind < 4) {
+        if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, theta, P);
+        __syncthreads();
+        if (P.bad) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 24u);
+            return;
+        }
+        ng = P.ng;
+    } else if (kind == SF_INSERT_COFACTOR) {
+        if (!d.meta[2]) return;  // deterministic qubit: nothing to split
+        if (threadIdx.x == 0) load_cof_plan<W>(d, CP);
+        __syncthreads();
+        ng = 2;
+    }
     const unsigned long long k = d.kcnt[in_buf];
-    if (2 * k > d.cap) {
+    const unsigned long long nchild = (unsigned long long)ng * k;
+    if (nchild > d.cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_CAPACITY, in_buf);
         return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.kcnt[out_buf] = 2 * k;
-    double2 kap[2];
-    const size_t ko = cf_kappa(n, W);
-    kap[0] = make_double2(__longlong_as_double((long long)pl[ko]), __longlong_as_double((long long)pl[ko + 1]));
-    kap[1] = make_double2(__longlong_as_double((long long)pl[ko + 2]), __longlong_as_double((long long)pl[ko + 3]));
-    uint64_t vq[W], tau[2][W], eps0[W], eps1[W];
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-        vq[w] = pl[cf_vq(n, W) + w];
-        tau[0][w] = pl[cf_tau(n, W) + w];
-        tau[1][w] = pl[cf_tau(n, W) + W + w];
-        eps0[w] = pl[cf_eps(n, W) + w];
-        eps1[w] = pl[cf_eps(n, W) + W + w];
+    const unsigned long long T = table_size(nchild, d.tcap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *d.tsize = T;
+        d.kcnt[out_buf] = 0;
     }
-    const uint64_t* U = pl + cf_u(n, W);
-    const uint64_t* V = pl + cf_v(n, W);
     const uint64_t* Si = d.sig[in_buf];
-    uint64_t* So = d.sig[out_buf];
     const double2* Ai = d.amp[in_buf];
-    double2* Ao = d.amp[out_buf];
     const uint64_t cap = d.cap;
+    bool ok = true;
     for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
          j += (unsigned long long)gridDim.x * blockDim.x) {
         uint64_t s[W];
         load_sig<W>(Si, cap, j, s);
         const double2 a = Ai[j];
-        const int py = popc_and<W>(vq, s) & 1;
-        for (int x = 0; x < 2; x++) {
-            const int y = x ^ py;
-            uint64_t t[W];
-#pragma unroll
-            for (int w = 0; w < W; w++) t[w] = tau[y][w];
-            int ip = 0;  // i-power accumulated over the old destabilizers of sigma
-#pragma unroll
-            for (int w = 0; w < W; w++) {
-                uint64_t bits = s[w];
-                while (bits) {
-                    const int b = __ffsll((long long)bits) - 1;
-                    bits &= bits - 1;
-                    const int h = 64 * w + b;
-                    uint64_t vv[W];
-#pragma unroll
-                    for (int u = 0; u < W; u++) vv[u] = __ldg(&V[(size_t)h * W + u]);
-                    ip += (int)((eps0[w] >> b) & 1) + 2 * (int)((eps1[w] >> b) & 1) + 2 * (popc_and<W>(vv, t) & 1);
-#pragma unroll
-                    for (int u = 0; u < W; u++) t[u] ^= __ldg(&U[(size_t)h * W + u]);
-                }
+        if (kind == SF_INSERT_FRAME) {
+            ok &= table_insert<W>(d, T, s, a);
+        } else if (kind == SF_INSERT_COFACTOR) {
+            for (int x = 0; x < 2; x++) {
+                uint64_t t[W];
+                const double2 c = cof_child<W>(d, CP, s, a, x, t);
+                ok &= table_insert<W>(d, T, t, c);
             }
-            const double2 c = ipow_mul(cmul(kap[y], a), ip & 3);
-            const unsigned long long o = (unsigned long long)x * k + j;
-            store_sig<W>(So, cap, o, t);
-            Ao[o] = c;
+        } else {
+            for (int g = 0; g < ng; g++) {
+                const double2 cf = group_coef<W>(P, g, s);
+                if (cf.x == 0.0 && cf.y == 0.0) continue;  // an exactly cancelled child (e.g. control in |0>)
+                uint64_t c[W];
+#pragma unroll
+                for (int w = 0; w < W; w++) c[w] = s[w] ^ P.u[g][w];
+                ok &= table_insert<W>(d, T, c, cmul(cf, a));
+            }
+        }
+    }
+    if (!ok) set_status(d.status, SF_ST_TIMEOUT, in_buf);
+}
+
+// Emit every occupied slot with |a| >= eps into out_buf (warp-aggregated
+// output positions; the order of the frame is not meaningful) and empty the
+// slot again, so the table is clean for the next merge.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, double eps2) {
+    if (*d.status) return;
+    const unsigned long long T = *d.tsize;
+    const unsigned long long tcap = d.tcap;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    uint64_t* So = d.sig[out_buf];
+    double2* Ao = d.amp[out_buf];
+    const uint64_t cap = d.cap;
+    for (unsigned long long base = gw * 32; base < T; base += nw * 32) {
+        const unsigned long long i = base + lane;
+        bool keep = false;
+        uint64_t key[W];
+        double2 a = make_double2(0.0, 0.0);
+        if (i < T) {
+            bool occ;
+            if constexpr (W == 1) {
+                key[0] = d.tkey[i];
+                occ = key[0] != SF_EMPTY_KEY;
+            } else {
+                occ = d.tstate[i] == 2u;
+            }
+            if (occ) {
+                a = d.tacc[i];
+                if constexpr (W > 1) {
+#pragma unroll
+                    for (int w = 0; w < W; w++) key[w] = d.tkey[(size_t)w * tcap + i];
+                    d.tstate[i] = 0u;
+                } else {
+                    d.tkey[i] = SF_EMPTY_KEY;
+                }
+                d.tacc[i] = make_double2(0.0, 0.0);
+                keep = a.x * a.x + a.y * a.y >= eps2;
+            }
+        }
+        const unsigned bal = __ballot_sync(SF_FULL, keep);
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            unsigned long long b = 0;
+            if (lane == leader) b = atomicAdd(&d.kcnt[out_buf], (unsigned long long)__popc(bal));
+            b = __shfl_sync(SF_FULL, b, leader);
+            if (keep) {
+                const unsigned long long o = b + __popc(bal & ((1u << lane) - 1u));
+                store_sig<W>(So, cap, o, key);
+                Ao[o] = a;
+            }
+        }
+    }
+}
+
+// keep the elements whose sign of row meta[1] is x, scaled by 1/sqrt(p_x)
+// (collapse after a measurement); kcnt[out_buf] must be zero on entry
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_filter(SfDev d, int x, int in_buf, int out_buf) {
+    if (*d.status) return;
+    const int R = d.meta[1];
+    if (R < 0 || R >= d.n) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 25u);
+        return;
+    }
+    const double scale = 1.0 / sqrt(d.out[x]);
+    const unsigned long long k = d.kcnt[in_buf];
+    const int lane = threadIdx.x & 31;
+    const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const uint64_t* Si = d.sig[in_buf];
+    uint64_t* So = d.sig[out_buf];
+    const uint64_t cap = d.cap;
+    for (unsigned long long base = gw * 32; base < k; base += nw * 32) {
+        const unsigned long long j = base + lane;
+        bool keep = false;
+        uint64_t s[W];
+        if (j < k) {
+            load_sig<W>(Si, cap, j, s);
+            keep = (int)((s[R >> 6] >> (R & 63)) & 1) == x;
+        }
+        const unsigned bal = __ballot_sync(SF_FULL, keep);
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            unsigned long long b = 0;
+            if (lane == leader) b = atomicAdd(&d.kcnt[out_buf], (unsigned long long)__popc(bal));
+            b = __shfl_sync(SF_FULL, b, leader);
+            if (keep) {
+                const unsigned long long o = b + __popc(bal & ((1u << lane) - 1u));
+                store_sig<W>(So, cap, o, s);
+                double2 a = d.amp[in_buf][j];
+                a.x *= scale;
+                a.y *= scale;
+                d.amp[out_buf][o] = a;
+            }
         }
     }
 }
@@ -658,30 +825,22 @@ void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s) {
     });
 }
 
-void sf_launch_branch(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_branch<WW><<<d.nblk, kThreads, 0, s>>>(d, in_buf, out_buf));
+void sf_launch_branch(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
+                      int out_buf, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_branch<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, theta, in_buf, out_buf));
 }
 
-void sf_launch_coal_clear(const SfDev& d, int buf, cudaStream_t s) { k_coal_clear<<<d.nblk, kThreads, 0, s>>>(d, buf); }
-
-void sf_launch_coal_insert(const SfDev& d, int buf, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_coal_insert<WW><<<d.nblk, kThreads, 0, s>>>(d, buf));
+void sf_launch_insert(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
+                      int out_buf, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_insert<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, theta, in_buf, out_buf));
 }
 
-void sf_launch_coal_accum(const SfDev& d, int buf, cudaStream_t s) { k_coal_accum<<<d.nblk, kThreads, 0, s>>>(d, buf); }
-
-void sf_launch_count(const SfDev& d, int buf, int mode, double eps2, int x, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_count<WW><<<d.nblk, kThreads, 0, s>>>(d, buf, mode, eps2, x));
+void sf_launch_compact(const SfDev& d, double eps, int out_buf, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_compact<WW><<<d.nblk, kThreads, 0, s>>>(d, out_buf, eps * eps));
 }
 
-void sf_launch_scan(const SfDev& d, int out_buf, cudaStream_t s) { k_scan<<<1, 1024, 0, s>>>(d, out_buf); }
-
-void sf_launch_scatter(const SfDev& d, int in_buf, int out_buf, int mode, double eps2, int x, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_scatter<WW><<<d.nblk, kThreads, 0, s>>>(d, in_buf, out_buf, mode, eps2, x));
-}
-
-void sf_launch_cofactor_split(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_cof_split<WW><<<d.nblk, kThreads, 0, s>>>(d, in_buf, out_buf));
+void sf_launch_filter(const SfDev& d, int x, int in_buf, int out_buf, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_filter<WW><<<d.nblk, kThreads, 0, s>>>(d, x, in_buf, out_buf));
 }
 
 void sf_launch_prob(const SfDev& d, int buf, cudaStream_t s) {

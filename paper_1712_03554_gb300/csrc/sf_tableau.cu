@@ -5,8 +5,6 @@
 //                      the five-step rule of Sec. III evaluated once per gate),
 //                      emitting the composed affine map sigma' = A sigma ^ t that
 //                      k_affine applies to every phase vector.
-//   * k_branch_prep:   anticommutation masks and signs of the Z-type Pauli terms
-//                      of a diagonal non-Clifford gate (Sec. IV).
 //   * k_measure_prep:  deterministic/random test of a qubit and, if random, the
 //                      COFACTOR update of M (Sec. III, measurement of Sec. II-B
 //                      forced to both outcomes) with the tables that map old
@@ -406,117 +404,6 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
 }
 
 // ---------------------------------------------------------------------------
-// Terms of a diagonal gate as sum_j c_j Z^{w_j}; for each term the coordinates
-// Z^w = eps D^u M^v (u_h = [Z^w anticommutes with M_h], v_h = [.. with D_h]),
-// so Z^w D^sigma phi_0 = eps (-1)^{v.sigma} D^{sigma^u} phi_0.  Terms with equal
-// u are grouped; the branch kernel writes one child per group.
-template <int W>
-__global__ void __launch_bounds__(1024) k_branch_prep(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1,
-                                                      double theta, int buf) {
-    __shared__ Scratch<W> S;
-    __shared__ uint64_t um[SF_BR_MAXT][W], vm[SF_BR_MAXT][W];
-    __shared__ int epsq[SF_BR_MAXT];
-    if (*d.status) return;
-    const int n = d.n, h = threadIdx.x;
-    double th = theta;
-    if (kind == 0) th = 0.78539816339744830962;
-    if (kind == 1) th = -0.78539816339744830962;
-    double sn, cs;
-    sincos(th, &sn, &cs);
-    int nt;
-    int wq[SF_BR_MAXT][2];
-    double2 cf[SF_BR_MAXT];
-    if (kind <= 2) {
-        nt = 2;
-        wq[0][0] = -1; wq[0][1] = -1; cf[0] = make_double2((1.0 + cs) * 0.5, sn * 0.5);
-        wq[1][0] = (int)q0; wq[1][1] = -1; cf[1] = make_double2((1.0 - cs) * 0.5, -sn * 0.5);
-    } else {
-        nt = 4;
-        const double2 dd = make_double2((cs - 1.0) * 0.25, sn * 0.25);
-        wq[0][0] = -1; wq[0][1] = -1; cf[0] = make_double2(1.0 + dd.x, dd.y);
-        wq[1][0] = (int)q0; wq[1][1] = -1; cf[1] = make_double2(-dd.x, -dd.y);
-        wq[2][0] = (int)q1; wq[2][1] = -1; cf[2] = make_double2(-dd.x, -dd.y);
-        wq[3][0] = (int)q0; wq[3][1] = (int)q1; cf[3] = dd;
-    }
-    for (int j = 0; j < nt; j++) {
-        uint64_t wz[W];
-#pragma unroll
-        for (int w = 0; w < W; w++) wz[w] = 0;
-        for (int a = 0; a < 2; a++)
-            if (wq[j][a] >= 0) wz[wq[j][a] >> 6] ^= 1ull << (wq[j][a] & 63);
-        if (h < W) { um[j][h] = 0; vm[j][h] = 0; }
-        __syncthreads();
-        bool ub = false, vb = false;
-        Pauli<W> p;
-        pauli_id<W>(p);
-        if (h < n) {
-            uint64_t mx[W], dx[W];
-#pragma unroll
-            for (int w = 0; w < W; w++) { mx[w] = d.mx[w * n + h]; dx[w] = d.dx[w * n + h]; }
-            ub = popc_and<W>(mx, wz) & 1;
-            vb = popc_and<W>(dx, wz) & 1;
-            if (ub) {
-#pragma unroll
-                for (int w = 0; w < W; w++) { p.x[w] = dx[w]; p.z[w] = d.dz[w * n + h]; }
-                p.e = (int)d.de[h];
-            }
-            if (vb) {
-                Pauli<W> m;
-#pragma unroll
-                for (int w = 0; w < W; w++) { m.x[w] = mx[w]; m.z[w] = d.mz[w * n + h]; }
-                m.e = 0;
-                pauli_mul<W>(p, m);
-            }
-        }
-        cta_bits<W>(ub, um[j]);
-        cta_bits<W>(vb, vm[j]);
-        cta_product<W>(p, S);
-        if (h == 0) {
-            bool ok = true;
-#pragma unroll
-            for (int w = 0; w < W; w++) ok &= (p.x[w] == 0) && (p.z[w] == wz[w]);
-            if (!ok) set_status(d.status, SF_ST_INTERNAL, buf, 2u);
-            // D^u M^v is anti-Hermitian when u and v share a row, so eps is any i-power
-            epsq[j] = (4 - p.e) & 3;
-        }
-        __syncthreads();
-    }
-    if (h != 0) return;
-    if (*d.status) return;
-    // group terms by u
-    uint64_t* pb = d.plan + plan_br(n, W);
-    const size_t gw = br_group_words(W);
-    int gid[SF_BR_MAXT];
-    int ngp = 0;
-    for (int j = 0; j < nt; j++) {
-        int found = -1;
-        for (int j2 = 0; j2 < j; j2++) {
-            bool same = true;
-            for (int w = 0; w < W; w++) same &= um[j2][w] == um[j][w];
-            if (same) { found = gid[j2]; break; }
-        }
-        gid[j] = found >= 0 ? found : ngp++;
-    }
-    pb[0] = (uint64_t)ngp;
-    for (int g = 0; g < ngp; g++) {
-        uint64_t* G = pb + 1 + g * gw;
-        int cnt = 0;
-        for (int j = 0; j < nt; j++) {
-            if (gid[j] != g) continue;
-            if (cnt == 0)
-                for (int w = 0; w < W; w++) G[w] = um[j][w];
-            const double2 c = ipow_mul(cf[j], epsq[j]);
-            uint64_t* Tm = G + W + 1 + cnt * (2 + W);
-            Tm[0] = (uint64_t)__double_as_longlong(c.x);
-            Tm[1] = (uint64_t)__double_as_longlong(c.y);
-            for (int w = 0; w < W; w++) Tm[2 + w] = vm[j][w];
-            cnt++;
-        }
-        G[W] = (uint64_t)cnt;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // COFACTOR(F, q) planning.  If q is random in M (some row has x_q = 1):
 //   pick the first such row i; multiply every other anticommuting row by M_i
 //   (dual: D_i <- D_i D_h); D_h <- D_h M_i for rows whose destabilizer
@@ -816,11 +703,6 @@ void sf_launch_clifford(const SfDev& d, const void* dev_gates, int ngates, int b
         uint64_t* ws = pick_ws<WW>(d, k_clifford<WW>, sm, gws, 0);
         k_clifford<WW><<<1, d.NT, sm, s>>>(d, reinterpret_cast<const sf_gate_rec*>(dev_gates), ngates, buf, ws);
     });
-}
-
-void sf_launch_branch_prep(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int buf,
-                           cudaStream_t s) {
-    SF_DISPATCH(d.W, k_branch_prep<WW><<<1, d.NT, 0, s>>>(d, kind, q0, q1, theta, buf));
 }
 
 void sf_launch_measure_prep(const SfDev& d, uint32_t q, int buf, uint64_t* gws, cudaStream_t s) {

@@ -17,9 +17,8 @@ from . import _build
 
 SF_OK, SF_EINVAL, SF_ENOMEM, SF_ECAPACITY, SF_ECUDA, SF_ETIMEOUT, SF_ESTATE, SF_EINTERNAL = range(8)
 # kernel classes (SF_K_* in include/sf.h)
-KERNEL_CLASSES = ["clifford", "affine", "branch_prep", "branch", "coal_clear", "coal_insert", "coal_accum",
-                  "count", "scan", "scatter", "measure_prep", "cofactor", "prob", "reduce", "amp_prep",
-                  "amplitude", "export", "reset"]
+KERNEL_CLASSES = ["clifford", "affine", "branch", "insert", "compact", "measure_prep", "prob", "reduce",
+                  "amp_prep", "amplitude", "filter", "export", "reset"]
 STATUS_NAMES = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOMEM", 3: "SF_ECAPACITY", 4: "SF_ECUDA",
                 5: "SF_ETIMEOUT", 6: "SF_ESTATE", 7: "SF_EINTERNAL"}
 
@@ -58,6 +57,7 @@ def load(build: bool = True) -> C.CDLL:
         "sf_apply_clifford": ([H, C.POINTER(sf_gate), u64], st),
         "sf_apply_clifford_device": ([H, C.c_void_p, u64], st),
         "sf_apply_nonclifford": ([H, u32, u32, u32, dbl], st),
+        "sf_apply_nonclifford_coalesce": ([H, u32, u32, u32, dbl, dbl], st),
         "sf_coalesce": ([H, dbl, P64], st),
         "sf_measure": ([H, u32, C.c_int32, PD, PD], st),
         "sf_amplitude": ([H, P64, PD, PD], st),
@@ -169,6 +169,10 @@ class Frame:
 
     def apply_nonclifford(self, kind: int, q0: int, q1: int = 0, theta: float = 0.0) -> None:
         self._check(self.lib.sf_apply_nonclifford(self.h, kind, q0, q1, float(theta)), self.h)
+
+    def apply_nonclifford_coalesce(self, kind: int, q0: int, q1: int = 0, theta: float = 0.0,
+                                   eps: float = 1e-12) -> None:
+        self._check(self.lib.sf_apply_nonclifford_coalesce(self.h, kind, q0, q1, float(theta), float(eps)), self.h)
 
     def coalesce(self, eps: float = 1e-12, sync: bool = False) -> Optional[int]:
         if sync:

@@ -272,3 +272,29 @@ def test_empty_gate_batch_is_a_no_op(sfm):
     g.apply_clifford([])
     g.coalesce()
     assert g.size() == 1
+
+
+class _Unfused:
+    """The same frame driven with separate branch and coalesce calls."""
+
+    def __init__(self, g):
+        self.g = g
+
+    def __getattr__(self, name):
+        if name == "apply_nonclifford_coalesce":
+            raise AttributeError(name)
+        return getattr(self.g, name)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fused_and_separate_merge_agree(sfm, seed):
+    n = 9 if seed % 2 else 70
+    ops = c.random_clifford_t(n, 150, 5, seed, t_kinds=(c.T, c.TDG)) + [("N", c.CPHASE, 0, 1, 0.37), ("K",)]
+    g1 = sfm.Frame(n, 1 << 10)
+    g2 = sfm.Frame(n, 1 << 10)
+    c.run(g1, ops)
+    c.run(_Unfused(g2), ops)
+    o = oracle.FrameOracle(n)
+    c.run(o, ops)
+    frames_equal(g1, o)
+    frames_equal(g2, o)
