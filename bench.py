@@ -87,6 +87,9 @@ def bytes_model(W: int, n: int = N_QUBITS):
         "amp_prep": lambda kin, kout: tab // 2,
         "affine": lambda kin, kout: 2 * 8 * W * kin,
         "branch": lambda kin, kout: e * kin + e * kout,
+        "branch_merge": lambda kin, kout: e * kin + e * kout,
+        "cofactor": lambda kin, kout: e * kin + e * kout,
+        "index": lambda kin, kout: 8 * W * kin,
         "insert": lambda kin, kout: e * kin,
         "compact": lambda kin, kout: e * kout,
         "filter": lambda kin, kout: e * kin + e * kout,
@@ -106,19 +109,23 @@ def instrumented_pass(sfm, n, plan, y):
     coal_elems = 0
     k = 1
     peak = 1
+    indexed = True  # the index of the current frame is valid (see sf_api.cu)
     for op in plan:
         if op[0] == "C":
             f.apply_clifford(op[1])
             updates += len(op[1]) * k
             rec["affine"].append((k, k))
             rec["clifford"].append((k, k))
+            indexed = False
         elif op[0] == "NK":
             f.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], DROP_EPS)
             kout = f.size()
             updates += k
             coal_elems += k
-            rec["insert"].append((k, kout))
-            rec["compact"].append((k, kout))
+            if not indexed:
+                rec["index"].append((k, k))
+            rec["branch_merge"].append((k, kout))
+            indexed = True
             k = kout
         elif op[0] == "N":
             f.apply_nonclifford(op[1], op[2], op[3], op[4])
@@ -126,12 +133,14 @@ def instrumented_pass(sfm, n, plan, y):
             updates += k
             rec["branch"].append((k, kout))
             k = kout
+            indexed = False
         elif op[0] == "K":
             kin = k
             k = f.coalesce(DROP_EPS, sync=True)
             coal_elems += kin
             rec["insert"].append((kin, k))
             rec["compact"].append((kin, k))
+            indexed = True
         peak = max(peak, k)
     # the captured (graph) part ends here; the tail is measured eagerly
     graph_rec = {cls: list(v) for cls, v in rec.items()}
@@ -140,8 +149,9 @@ def instrumented_pass(sfm, n, plan, y):
     f.measure(0, -1)
     km = f.size()
     updates += kin
-    rec["insert"].append((kin, km))
-    rec["compact"].append((kin, km))
+    if not indexed:
+        rec["index"].append((kin, kin))
+    rec["cofactor"].append((kin, km))
     coal_elems += 2 * kin
     rec["prob"].append((km, km))
     f.amplitude(y)
@@ -400,34 +410,44 @@ def main():
     graph_classes = [cls for cls in per_class if graph_rec.get(cls)] or list(per_class)
     dominant = max(graph_classes, key=per_class.get)
 
-    # capture the asynchronous part in a CUDA graph, with the dominant class timed
+    # capture the asynchronous part in CUDA graphs: `graph` for the timed steps,
+    # `tgraph` (the same launches with the dominant class bracketed by CUDA
+    # events) for the roofline measurement
     use_graph = not args.no_graph
-    graph = None
-    frame.time_kernel(dominant)
+    graph = tgraph = None
+    token = 0
     if use_graph:
         try:
+            frame.time_kernel(dominant)
             async_part(frame)  # warm (creates the event pairs outside capture)
             tail(frame)
             frame.time_kernel(dominant)
+            tgraph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(tgraph, stream=stream):
+                async_part(frame)
+            frame.time_kernel(-1)  # keep the captured pairs; eager tail launches are not timed
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=stream):
                 async_part(frame)
-            frame.time_kernel(-1)  # keep the captured pairs; eager tail launches are not timed
-            with torch.cuda.stream(stream):
-                graph.replay()
-            p_g, a_g = tail(frame)
-            if abs(p_g[0] - p_ref[0]) > 1e-10 or abs(a_g - a_ref) > 1e-10:
-                raise RuntimeError("graph replay differs from the eager step")
+            token = frame.host_state()  # replays restore the handle's host bookkeeping
+            for gph in (graph, tgraph, graph):
+                with torch.cuda.stream(stream):
+                    gph.replay()
+                frame.set_host_state(token)
+                p_g, a_g = tail(frame)
+                if abs(p_g[0] - p_ref[0]) > 1e-10 or abs(a_g - a_ref) > 1e-10:
+                    raise RuntimeError("graph replay differs from the eager step")
         except Exception as exc:  # fall back to eager launches from the host
             print(f"# graph capture unavailable ({exc}); timing eager launches", file=sys.stderr)
-            graph = None
+            graph = tgraph = None
     if graph is None:
         frame.time_kernel(dominant)
 
-    def step():
+    def step(gph=None):
         if graph is not None:
             with torch.cuda.stream(stream):
-                graph.replay()
+                (gph or graph).replay()
+            frame.set_host_state(token)
             return tail(frame)
         frame.time_kernel(dominant)
         with torch.cuda.stream(stream):
@@ -459,16 +479,27 @@ def main():
                 ev1.record(stream)
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            ms, cnt = frame.kernel_time()
-            dom_ms += ms
-            dom_launches += cnt
+            if graph is None:
+                ms, cnt = frame.kernel_time()
+                dom_ms += ms
+                dom_launches += cnt
         torch.cuda.synchronize()
         wall = time.perf_counter() - t_wall
+        launches_timed = frame.kernel_launches() - launches0
+        # roofline of the dominant class: the same steps replayed with its event pairs
+        if tgraph is not None:
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                step(tgraph)
+                ms, cnt = frame.kernel_time()
+                dom_ms += ms
+                dom_launches += cnt
     clocks = clk.summary()
     # graph replays do not pass through the host launch counter: add the captured kernels
-    launches_total = frame.kernel_launches() - launches0
+    launches_total = launches_timed  # launched from the host inside the timed steps
     if graph is not None:
-        launches_total += graph_launch_count(plan) * args.steps
+        launches_total += graph_launch_count(plan) * args.steps  # graph replays of the timed steps
     ms_step = float(np.mean(step_ms))
 
     # e2e: the public API with host gate arrays, eager launches
@@ -568,10 +599,16 @@ def main():
 
 def graph_launch_count(plan) -> int:
     """Kernels in the captured part of a step: reset, 2 per Clifford batch
-    (tableau + affine), 1 per unmerged branch, 2 per merge (insert + compact)."""
+    (tableau + affine), 1 per unmerged branch, 2 per generic coalesce (insert +
+    compact), 1 per merged branch plus an index build when the previous op
+    left the frame unindexed."""
     cnt = 1
+    indexed = True
     for op in plan:
-        cnt += {"C": 2, "N": 1, "K": 2, "NK": 2}[op[0]]
+        cnt += {"C": 2, "N": 1, "K": 2, "NK": 1}[op[0]]
+        if op[0] == "NK" and not indexed:
+            cnt += 1
+        indexed = op[0] in ("NK", "K")
     return cnt
 
 

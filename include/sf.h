@@ -76,7 +76,7 @@ enum { SF_T = 0,      /* diag(1, e^{i pi/4}) on q0 */
  * a = 1) on `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
  * 1 <= n_qubits <= 1024.  max_elems bounds the number of frame elements that
  * any step may hold, including the children of a branch before coalescing.
- * Device memory: about max_elems * (24 W + 72) bytes plus O(n^2) for the
+ * Device memory: about max_elems * (40 W + 88) bytes plus O(n^2) for the
  * tableau.  Synchronises. */
 sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf_handle* out);
 
@@ -106,9 +106,10 @@ sf_status sf_apply_clifford_device(sf_handle h, const sf_gate* dev_gates, uint64
 sf_status sf_apply_nonclifford(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta);
 
 /* sf_apply_nonclifford followed by sf_coalesce(h, drop_eps, NULL), done in one
- * pass: the children are hashed straight into the merge table instead of being
- * written out first.  Children whose coefficient is exactly zero are skipped.
- * Same frame as the two calls; asynchronous. */
+ * pass: the anticommutation masks of the gate's terms form a group U, so each
+ * element looks up its partners sigma ^ u (u in U) in an index of the frame and
+ * every output element is computed by exactly one thread, summing its parents'
+ * contributions in a fixed order.  Same frame as the two calls; asynchronous. */
 sf_status sf_apply_nonclifford_coalesce(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
                                         double drop_eps);
 
@@ -154,12 +155,15 @@ sf_status sf_get_frame(sf_handle h, uint64_t* sigma, double* amp, uint64_t capac
 enum { SF_K_CLIFFORD = 0,      /* tableau update of a Clifford batch (single CTA) */
        SF_K_AFFINE = 1,        /* per-element affine phase-vector update */
        SF_K_BRANCH = 2,        /* per-element branching, children written unmerged */
-       SF_K_INSERT = 3,        /* children hashed into the slot table (branch, cofactor or frame) */
-       SF_K_COMPACT = 4,       /* slot table -> frame, dropping |a| < eps */
-       SF_K_MEASURE_PREP = 5,  /* cofactor planning (single CTA) */
-       SF_K_PROB = 6, SF_K_REDUCE = 7, SF_K_AMP_PREP = 8, SF_K_AMPLITUDE = 9,
-       SF_K_FILTER = 10,       /* collapse */
-       SF_K_EXPORT = 11, SF_K_RESET = 12, SF_K_COUNT_CLASSES = 13 };
+       SF_K_BRANCH_MERGE = 3,  /* branching merged through the phase-vector index */
+       SF_K_INSERT = 4,        /* generic coalescing: elements hashed into the slot table */
+       SF_K_COMPACT = 5,       /* generic coalescing: slot table -> frame, dropping |a| < eps */
+       SF_K_INDEX = 6,         /* (re)build of a frame's phase-vector index */
+       SF_K_MEASURE_PREP = 7,  /* cofactor planning (single CTA) */
+       SF_K_COFACTOR = 8,      /* cofactor split merged through the index */
+       SF_K_PROB = 9, SF_K_REDUCE = 10, SF_K_AMP_PREP = 11, SF_K_AMPLITUDE = 12,
+       SF_K_FILTER = 13,       /* collapse */
+       SF_K_EXPORT = 14, SF_K_RESET = 15, SF_K_COUNT_CLASSES = 16 };
 
 /* Number of CUDA kernels this handle has launched since it was created. */
 uint64_t sf_kernel_launches(sf_handle h);
@@ -213,6 +217,14 @@ sf_status sf_get_internal(sf_handle h, uint64_t* dx, uint64_t* dz, uint32_t* de,
 sf_status sf_coalesce_noalloc(const uint64_t* sigma_in, const double* amp_in, uint64_t k_in, uint32_t n_words,
                               double drop_eps, uint64_t* sigma_out, double* amp_out, uint64_t* k_out,
                               void* cuda_stream);
+
+/* Host-side bookkeeping of the handle: which of its two frame buffers holds
+ * the current frame and which buffers carry a valid phase-vector index.  A
+ * CUDA graph captured from this handle's stream replays device work only, so
+ * read the token right after the capture ends and restore it with
+ * sf_set_host_state after every replay, before the next call on the handle. */
+uint32_t sf_host_state(sf_handle h);
+sf_status sf_set_host_state(sf_handle h, uint32_t token);
 
 /* Words per phase vector / row half used by this handle (ceil(n/64)). */
 uint32_t sf_words(sf_handle h);

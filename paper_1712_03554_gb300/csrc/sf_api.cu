@@ -4,6 +4,7 @@
 // the kernels of sf_tableau.cu and sf_frame.cu.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <numeric>
@@ -33,6 +34,7 @@ struct sf_frame_s {
     int32_t* hmeta = nullptr;
     std::vector<void*> dallocs;
     std::string err;
+    bool idx_ok[2] = {false, false};  // buffer b has a valid phase-vector index
     uint64_t launches = 0;
     int time_id = -1;
     std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
@@ -134,7 +136,10 @@ sf_status sync_check(sf_handle h) {
     const uint32_t st = *h->hstatus;
     if (st) {
         h->cur = (int)((st >> 8) & 1u);
+        h->idx_ok[0] = h->idx_ok[1] = false;
         SF_CK(h, cudaMemsetAsync(h->d.status, 0, sizeof(uint32_t), h->stream));
+        SF_CK(h, cudaMemsetAsync(h->d.done, 0, sizeof(unsigned int), h->stream));
+        SF_CK(h, cudaMemsetAsync(h->d.ocnt, 0, sizeof(unsigned long long), h->stream));
         sf_status cs = clean_table(h);
         if (cs) return cs;
         SF_CK(h, cudaStreamSynchronize(h->stream));
@@ -146,14 +151,22 @@ sf_status sync_check(sf_handle h) {
     return SF_OK;
 }
 
-// children of in_buf (kind: a diagonal gate, the frame itself or its cofactor
-// split) merged into out_buf through the slot table
-sf_status merge_seq(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta, double eps, int in_buf,
-                    int out_buf) {
+// generic coalescing of in_buf into out_buf through the slot table
+sf_status merge_seq(sf_handle h, double eps, int in_buf, int out_buf) {
     const SfDev& d = h->d;
     cudaStream_t s = h->stream;
-    SF_LAUNCH(h, SF_K_INSERT, sf_launch_insert(d, kind, q0, q1, theta, in_buf, out_buf, s));
+    SF_LAUNCH(h, SF_K_INSERT, sf_launch_insert(d, in_buf, out_buf, s));
     SF_LAUNCH(h, SF_K_COMPACT, sf_launch_compact(d, eps, out_buf, s));
+    h->idx_ok[out_buf] = true;
+    return SF_OK;
+}
+
+// the index of buffer b, built if the last writer of b did not leave one
+sf_status need_index(sf_handle h, int b) {
+    if (!h->idx_ok[b]) {
+        SF_LAUNCH(h, SF_K_INDEX, sf_launch_build_index(h->d, b, h->stream));
+        h->idx_ok[b] = true;
+    }
     return SF_OK;
 }
 
@@ -183,6 +196,7 @@ sf_status run_clifford(sf_handle h, const sf_gate_rec* dev, uint64_t ng) {
         // the affine map of each chunk is applied before the next chunk overwrites it
         SF_LAUNCH(h, SF_K_AFFINE, sf_launch_affine(h->d, h->cur, h->stream));
     }
+    h->idx_ok[h->cur] = false;  // phase vectors changed; the index is rebuilt when needed
     return SF_OK;
 }
 
@@ -215,7 +229,9 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
         delete h;
         return st;
     }
-    d.nblk = std::max(1, sms) * 4;
+    int per_sm = 4;  // CTAs of 256 threads per SM for the per-element kernels
+    if (const char* env = getenv("SF_CTAS_PER_SM")) per_sm = std::max(1, std::min(16, atoi(env)));
+    d.nblk = std::max(1, sms) * per_sm;
     const size_t n = n_qubits, W = d.W, cap = max_elems;
     unsigned long long slots = 1024;
     while (slots < 2 * cap) slots <<= 1;
@@ -244,6 +260,15 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     SF_ALLOC(d.tkey, W * slots);
     SF_ALLOC(d.tacc, slots);
     SF_ALLOC(d.tsize, 1);
+    unsigned long long icap = 64;
+    while (icap < 2 * cap) icap <<= 1;
+    d.icap = icap;
+    for (int b = 0; b < 2; b++) SF_ALLOC(d.islot[b], (W + 1) * icap);
+    SF_ALLOC(d.itag, 2);
+    SF_ALLOC(d.isize, 2);
+    SF_ALLOC(d.done, 1);
+    SF_ALLOC(d.ocnt, 1);
+    SF_ALLOC(d.ipend, 1);
     SF_ALLOC(d.red, 4 * (size_t)d.nblk);
     SF_ALLOC(d.out, 8);
     SF_ALLOC(h->dy, W);
@@ -264,6 +289,11 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
         return fail(nullptr, SF_ENOMEM, "pinned host allocation failed");
     }
     cudaMemsetAsync(d.status, 0, sizeof(uint32_t), h->stream);
+    for (int b = 0; b < 2; b++) cudaMemsetAsync(d.islot[b], 0, (W + 1) * icap * sizeof(uint64_t), h->stream);
+    cudaMemsetAsync(d.itag, 0, 2 * sizeof(uint32_t), h->stream);
+    cudaMemsetAsync(d.isize, 0, 2 * sizeof(unsigned long long), h->stream);
+    cudaMemsetAsync(d.done, 0, sizeof(unsigned int), h->stream);
+    cudaMemsetAsync(d.ocnt, 0, sizeof(unsigned long long), h->stream);
     if (clean_table(h) != SF_OK) {
         sf_destroy(h);
         return fail(nullptr, SF_ECUDA, "table initialisation failed");
@@ -273,6 +303,7 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     h->cur = 0;
     sf_launch_reset(d, 0, h->stream);
     h->launches++;
+    h->idx_ok[0] = true;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -304,6 +335,8 @@ sf_status sf_reset(sf_handle h) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
     h->cur = 0;
     SF_LAUNCH(h, SF_K_RESET, sf_launch_reset(h->d, 0, h->stream));
+    h->idx_ok[0] = true;
+    h->idx_ok[1] = false;
     return SF_OK;
 }
 
@@ -366,6 +399,7 @@ sf_status sf_apply_nonclifford(sf_handle h, uint32_t kind, uint32_t q0, uint32_t
     const uint32_t q1v = kind == SF_CPHASE ? q1 : 0u;
     SF_LAUNCH(h, SF_K_BRANCH, sf_launch_branch(h->d, kind, q0, q1v, theta, h->cur, h->cur ^ 1, h->stream));
     h->cur ^= 1;
+    h->idx_ok[h->cur] = false;  // children may repeat phase vectors until coalesced
     return SF_OK;
 }
 
@@ -377,16 +411,19 @@ sf_status sf_apply_nonclifford_coalesce(sf_handle h, uint32_t kind, uint32_t q0,
     if (kind == SF_CPHASE && (q1 >= h->n || q1 == q0)) return fail(h, SF_EINVAL, "bad second qubit");
     if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");
     const uint32_t q1v = kind == SF_CPHASE ? q1 : 0u;
-    sf_status st = merge_seq(h, kind, q0, q1v, theta, drop_eps, h->cur, h->cur ^ 1);
+    sf_status st = need_index(h, h->cur);
     if (st) return st;
+    SF_LAUNCH(h, SF_K_BRANCH_MERGE,
+              sf_launch_branch_merge(h->d, kind, q0, q1v, theta, drop_eps, h->cur, h->cur ^ 1, h->stream));
     h->cur ^= 1;
+    h->idx_ok[h->cur] = true;
     return SF_OK;
 }
 
 sf_status sf_coalesce(sf_handle h, double drop_eps, uint64_t* out_size) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
     if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");
-    sf_status cs = merge_seq(h, SF_INSERT_FRAME, 0u, 0u, 0.0, drop_eps, h->cur, h->cur ^ 1);
+    sf_status cs = merge_seq(h, drop_eps, h->cur, h->cur ^ 1);
     if (cs) return cs;
     h->cur ^= 1;
     if (out_size) {
@@ -407,9 +444,11 @@ sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, d
     sf_status st = sync_check(h);
     if (st) return st;
     if (h->hmeta[2]) {
-        st = merge_seq(h, SF_INSERT_COFACTOR, 0u, 0u, 0.0, 1e-12, h->cur, h->cur ^ 1);
+        st = need_index(h, h->cur);
         if (st) return st;
+        SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cof_merge(h->d, h->cur, h->cur ^ 1, h->stream));
         h->cur ^= 1;
+        h->idx_ok[h->cur] = true;
     }
     SF_LAUNCH(h, SF_K_PROB, sf_launch_prob(h->d, h->cur, h->stream));
     SF_LAUNCH(h, SF_K_REDUCE, sf_launch_reduce_final(h->d, 0, h->stream));
@@ -425,6 +464,7 @@ sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, d
         SF_CK(h, cudaMemsetAsync(h->d.kcnt + outb, 0, sizeof(unsigned long long), h->stream));
         SF_LAUNCH(h, SF_K_FILTER, sf_launch_filter(h->d, collapse_to, in, outb, h->stream));
         h->cur ^= 1;
+        h->idx_ok[h->cur] = true;
     }
     return SF_OK;
 }
@@ -491,6 +531,7 @@ sf_status sf_get_frame(sf_handle h, uint64_t* sigma, double* amp, uint64_t capac
     if (!sigma || !amp) return fail(h, SF_EINVAL, "NULL output");
     const int stage = h->cur ^ 1;
     SF_LAUNCH(h, SF_K_EXPORT, sf_launch_export(h->d, h->cur, stage, h->stream));
+    h->idx_ok[stage] = false;
     st = sync_check(h);
     if (st) return st;
     const size_t W = h->d.W;
@@ -517,6 +558,20 @@ sf_status sf_get_frame(sf_handle h, uint64_t* sigma, double* amp, uint64_t capac
 }
 
 uint32_t sf_words(sf_handle h) { return h ? (uint32_t)h->Wabi : 0u; }
+
+uint32_t sf_host_state(sf_handle h) {
+    if (!h) return 0u;
+    return (uint32_t)h->cur | ((uint32_t)h->idx_ok[0] << 1) | ((uint32_t)h->idx_ok[1] << 2);
+}
+
+sf_status sf_set_host_state(sf_handle h, uint32_t token) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (token > 7u) return fail(h, SF_EINVAL, "invalid host-state token");
+    h->cur = (int)(token & 1u);
+    h->idx_ok[0] = (token >> 1) & 1u;
+    h->idx_ok[1] = (token >> 2) & 1u;
+    return SF_OK;
+}
 
 uint64_t sf_kernel_launches(sf_handle h) { return h ? h->launches : 0ull; }
 

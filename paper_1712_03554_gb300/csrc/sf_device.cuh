@@ -61,6 +61,18 @@ struct SfDev {
     unsigned long long* tsize; // slots in use by the current merge
     double* red;               // [4 * nblk] reduction partials
     double* out;               // [8] small results (p0, p1, amplitude re, im)
+    // index of each frame buffer: phase vector -> position.  Slots carry the
+    // generation tag of the index that wrote them, so an index is replaced by
+    // bumping the tag, never by clearing the table.
+    // slot s of buffer b's index is the W + 1 words islot[b][s * (W + 1) ..]:
+    // word 0 = tag << 32 | position, words 1..W = phase vector
+    uint64_t* islot[2];
+    unsigned long long icap;   // power of two >= 2 cap
+    uint32_t* itag;            // [2] tag of the valid index of each buffer (0 = none)
+    unsigned long long* isize; // [2] slots used by that index (power of two)
+    unsigned int* done;        // CTAs finished (last-CTA publication of tags and counts)
+    unsigned long long* ipend; // index size chosen by CTA 0, published by the last CTA
+    unsigned long long* ocnt;  // output counter of the merge kernels
 };
 
 // An empty slot key: phase vectors never set bit 63 of their last word
@@ -84,8 +96,10 @@ __host__ __device__ inline size_t cf_eps(int n, int W) { return cf_v(n, W) + (si
 __host__ __device__ inline size_t cf_kappa(int n, int W) { return cf_eps(n, W) + 2 * W; }
 __host__ __device__ inline size_t cf_tau(int n, int W) { return cf_kappa(n, W) + 4; }
 __host__ __device__ inline size_t cf_vq(int n, int W) { return cf_tau(n, W) + 2 * W; }
+// rows of the old tableau anticommuting with Z_q: elements sigma and sigma ^ uq share their cofactors
+__host__ __device__ inline size_t cf_uq(int n, int W) { return cf_vq(n, W) + W; }
 // amplitude-query plan: y[W], zmask[W], zexp[W], flag
-__host__ __device__ inline size_t plan_am(int n, int W) { return cf_vq(n, W) + W; }
+__host__ __device__ inline size_t plan_am(int n, int W) { return cf_uq(n, W) + W; }
 __host__ __device__ inline size_t plan_words(int n, int W) { return plan_am(n, W) + 3 * W + 8; }
 
 // ---- Pauli arithmetic -------------------------------------------------------
@@ -150,10 +164,137 @@ __device__ __forceinline__ void set_status(uint32_t* st, uint32_t code, int buf,
     atomicCAS(st, 0u, code | ((uint32_t)buf << 8) | (site << 16));
 }
 
+// ---- frame index ---------------------------------------------------------------
+__device__ __forceinline__ uint32_t next_tag(uint32_t t) { return (t % 0x7ffffffeu) + 1u; }
+
+__host__ __device__ inline unsigned long long index_slots(unsigned long long k, unsigned long long icap) {
+    unsigned long long t = 64;
+    while (t < 2 * k && t < icap) t <<= 1;
+    return t < icap ? t : icap;
+}
+
+// splitmix64 finaliser chained over the words
+template <int W>
+__device__ __forceinline__ uint64_t hash_sig(const uint64_t* s) {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        uint64_t v = s[w] + h;
+        v ^= v >> 30;
+        v *= 0xBF58476D1CE4E5B9ull;
+        v ^= v >> 27;
+        v *= 0x94D049BB133111EBull;
+        v ^= v >> 31;
+        h = v + 0x9E3779B97F4A7C15ull * (uint64_t)(w + 1);
+    }
+    return h;
+}
+
+// Insert a key that is distinct from every other key of this generation
+// (phase vectors of a frame are distinct, Def. 1): one 64-bit compare-and-swap
+// claims the slot and publishes the position, the key goes beside it in the
+// same sector.  Returns false only if the table is full.
+template <int W>
+__device__ __forceinline__ bool index_insert(const SfDev& d, int b, unsigned long long T, uint32_t tag,
+                                             const uint64_t* key, uint32_t pos) {
+    unsigned long long* sl = reinterpret_cast<unsigned long long*>(d.islot[b]);
+    const unsigned long long mine = ((unsigned long long)tag << 32) | pos;
+    unsigned long long slot = hash_sig<W>(key) & (T - 1);
+    for (unsigned long long probe = 0; probe < T; probe++) {
+        unsigned long long* tv = sl + slot * (W + 1);
+        unsigned long long cur = *(volatile unsigned long long*)tv;
+        while ((uint32_t)(cur >> 32) != tag) {
+            const unsigned long long old = atomicCAS(tv, cur, mine);
+            if (old == cur) {
+#pragma unroll
+                for (int w = 0; w < W; w++) tv[1 + w] = key[w];
+                return true;
+            }
+            cur = old;
+        }
+        slot = (slot + 1) & (T - 1);
+    }
+    return false;
+}
+
+// Position of key in the index of buffer b (written by an earlier kernel), or -1.
+template <int W>
+__device__ __forceinline__ long long index_find(const SfDev& d, int b, unsigned long long T, uint32_t tag,
+                                                const uint64_t* key) {
+    const uint64_t* sl = d.islot[b];
+    unsigned long long slot = hash_sig<W>(key) & (T - 1);
+    for (unsigned long long probe = 0; probe < T; probe++) {
+        const uint64_t* p = sl + slot * (W + 1);
+        uint64_t tv, k0;
+        if constexpr (W == 1) {
+            const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p));
+            tv = v.x;
+            k0 = v.y;
+        } else {
+            tv = __ldg(p);
+            k0 = __ldg(p + 1);
+        }
+        if ((uint32_t)(tv >> 32) != tag) return -1;
+        bool eq = k0 == key[0];
+#pragma unroll
+        for (int w = 1; w < W; w++) eq &= (__ldg(p + 1 + w) == key[w]);
+        if (eq) return (long long)(uint32_t)tv;
+        slot = (slot + 1) & (T - 1);
+    }
+    return -1;
+}
+
+// Reserve cnt consecutive output positions for each thread of the block with
+// one atomic per block: returns the first position of this thread's range.
+// Every thread of the block must call it (it synchronises the block).
+__device__ __forceinline__ unsigned long long block_out_range(unsigned long long* ctr, unsigned cnt,
+                                                              unsigned int* wsum, unsigned long long* bbase) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    unsigned incl = cnt;  // inclusive warp scan of the counts
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = 0;
+        for (int i = 0; i < nwarp; i++) {
+            const unsigned int c = wsum[i];
+            wsum[i] = t;
+            t += c;
+        }
+        *bbase = t ? atomicAdd(ctr, (unsigned long long)t) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long o = *bbase + wsum[wid] + (incl - cnt);
+    __syncthreads();
+    return o;
+}
+
+// True in exactly one thread-block: the last one to finish (all of its
+// threads receive the answer).  Every block of the grid must call it once.
+__device__ __forceinline__ bool last_block(unsigned int* done) {
+    __shared__ bool am_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int t = atomicAdd(done, 1u);
+        am_last = (t == gridDim.x - 1);
+        if (am_last) *done = 0u;
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
 // ---- launch wrappers implemented in the .cu files (one kernel each) --------
 void sf_launch_reset(const SfDev& d, int buf, cudaStream_t s);
 void sf_launch_clifford(const SfDev& d, const void* dev_gates, int ngates, int buf, uint64_t* gws,
                         cudaStream_t s);
+// single-warp version for n <= 63 (W = 1)
+void sf_launch_clifford_warp(const SfDev& d, const void* dev_gates, int ngates, int buf, cudaStream_t s);
 void sf_launch_measure_prep(const SfDev& d, uint32_t q, int buf, uint64_t* gws, cudaStream_t s);
 void sf_launch_amp_prep(const SfDev& d, const uint64_t* dev_y, cudaStream_t s);
 size_t sf_tableau_smem_bytes(int n, int W, int NT);
@@ -162,13 +303,15 @@ void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s);
 // children of a diagonal gate written out unmerged (in -> out)
 void sf_launch_branch(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
                       int out_buf, cudaStream_t s);
-// children hashed into the slot table: diagonal gate (kind < 4), plain
-// coalescing of a frame (kind = SF_INSERT_FRAME) or cofactor split (kind = SF_INSERT_COFACTOR)
-#define SF_INSERT_FRAME 16u
-#define SF_INSERT_COFACTOR 17u
-void sf_launch_insert(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
-                      int out_buf, cudaStream_t s);
+// the elements of a frame (possibly with repeated phase vectors) hashed into the slot table
+void sf_launch_insert(const SfDev& d, int in_buf, int out_buf, cudaStream_t s);
 void sf_launch_compact(const SfDev& d, double eps, int out_buf, cudaStream_t s);
+// diagonal gate with merging through the index of in_buf (children owned by one parent each)
+void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, double eps,
+                            int in_buf, int out_buf, cudaStream_t s);
+// cofactor split with merging of the two parents of each child
+void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s);
+void sf_launch_build_index(const SfDev& d, int buf, cudaStream_t s);
 void sf_launch_filter(const SfDev& d, int x, int in_buf, int out_buf, cudaStream_t s);
 void sf_launch_prob(const SfDev& d, int buf, cudaStream_t s);
 void sf_launch_reduce_final(const SfDev& d, int what, cudaStream_t s);

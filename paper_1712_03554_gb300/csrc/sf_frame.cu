@@ -26,23 +26,6 @@ __device__ __forceinline__ unsigned long long table_size(unsigned long long k, u
     return t < cap ? t : cap;
 }
 
-// splitmix64 finaliser chained over the words
-template <int W>
-__device__ __forceinline__ uint64_t hash_sig(const uint64_t* s) {
-    uint64_t h = 0x9E3779B97F4A7C15ull;
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-        uint64_t v = s[w] + h;
-        v ^= v >> 30;
-        v *= 0xBF58476D1CE4E5B9ull;
-        v ^= v >> 27;
-        v *= 0x94D049BB133111EBull;
-        v ^= v >> 31;
-        h = v + 0x9E3779B97F4A7C15ull * (uint64_t)(w + 1);
-    }
-    return h;
-}
-
 template <int W>
 __device__ __forceinline__ void load_sig(const uint64_t* S, uint64_t cap, unsigned long long j, uint64_t* s) {
 #pragma unroll
@@ -297,48 +280,52 @@ __device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uin
         wq[2][0] = (int)q1; wq[2][1] = -1; cf[2] = make_double2(-dd.x, -dd.y);
         wq[3][0] = (int)q0; wq[3][1] = (int)q1; cf[3] = dd;
     }
-    uint64_t um[SF_BR_MAXT][W], vm[SF_BR_MAXT][W];
+    uint64_t um[SF_BR_MAXT][W], vm[SF_BR_MAXT][W], wz[SF_BR_MAXT][W];
     int epsq[SF_BR_MAXT];
     int bad = 0;
+    Pauli<W> p[SF_BR_MAXT];
     for (int j = 0; j < nt; j++) {
-        uint64_t wz[W];
 #pragma unroll
-        for (int w = 0; w < W; w++) { wz[w] = 0; um[j][w] = 0; vm[j][w] = 0; }
+        for (int w = 0; w < W; w++) { wz[j][w] = 0; um[j][w] = 0; vm[j][w] = 0; }
         for (int a = 0; a < 2; a++)
-            if (wq[j][a] >= 0) wz[wq[j][a] >> 6] ^= 1ull << (wq[j][a] & 63);
-        Pauli<W> p;
-        pauli_id<W>(p);
-        for (int h = lane; h < n; h += 32) {
-            uint64_t mx[W], dx[W];
+            if (wq[j][a] >= 0) wz[j][wq[j][a] >> 6] ^= 1ull << (wq[j][a] & 63);
+        pauli_id<W>(p[j]);
+    }
+    // each row is read once for all terms: u_h = [Z^w anticommutes with M_h],
+    // v_h = [Z^w anticommutes with D_h], contribution D_h^{u_h} M_h^{v_h}
+    for (int h = lane; h < n; h += 32) {
+        Pauli<W> dh, mh;
 #pragma unroll
-            for (int w = 0; w < W; w++) { mx[w] = __ldg(&d.mx[w * n + h]); dx[w] = __ldg(&d.dx[w * n + h]); }
-            const bool ub = popc_and<W>(mx, wz) & 1;
-            const bool vb = popc_and<W>(dx, wz) & 1;
+        for (int w = 0; w < W; w++) {
+            mh.x[w] = __ldg(&d.mx[w * n + h]);
+            mh.z[w] = __ldg(&d.mz[w * n + h]);
+            dh.x[w] = __ldg(&d.dx[w * n + h]);
+            dh.z[w] = __ldg(&d.dz[w * n + h]);
+        }
+        mh.e = 0;
+        dh.e = (int)__ldg(&d.de[h]);
+        for (int j = 0; j < nt; j++) {
+            const bool ub = popc_and<W>(mh.x, wz[j]) & 1;
+            const bool vb = popc_and<W>(dh.x, wz[j]) & 1;
             if (ub) {
                 um[j][h >> 6] |= 1ull << (h & 63);
-                Pauli<W> dh;
-#pragma unroll
-                for (int w = 0; w < W; w++) { dh.x[w] = dx[w]; dh.z[w] = __ldg(&d.dz[w * n + h]); }
-                dh.e = (int)__ldg(&d.de[h]);
-                pauli_mul<W>(p, dh);
+                pauli_mul<W>(p[j], dh);
             }
             if (vb) {
                 vm[j][h >> 6] |= 1ull << (h & 63);
-                Pauli<W> m;
-#pragma unroll
-                for (int w = 0; w < W; w++) { m.x[w] = mx[w]; m.z[w] = __ldg(&d.mz[w * n + h]); }
-                m.e = 0;
-                pauli_mul<W>(p, m);
+                pauli_mul<W>(p[j], mh);
             }
         }
-        warp_pauli_product<W>(p);
+    }
+    for (int j = 0; j < nt; j++) {
+        warp_pauli_product<W>(p[j]);
 #pragma unroll
         for (int w = 0; w < W; w++) {
             um[j][w] = warp_or(um[j][w]);
             vm[j][w] = warp_or(vm[j][w]);
-            if (p.x[w] != 0 || p.z[w] != wz[w]) bad = 1;
+            if (p[j].x[w] != 0 || p[j].z[w] != wz[j][w]) bad = 1;
         }
-        epsq[j] = (4 - p.e) & 3;
+        epsq[j] = (4 - p[j].e) & 3;
     }
     if (lane != 0) return;
     int gid[SF_BR_MAXT];
@@ -523,38 +510,15 @@ __device__ __forceinline__ double2 cof_child(const SfDev& d, const CofPlan<W>& C
     return ipow_mul(cmul(C.kap[y], a), ip & 3);
 }
 
-// Hash the children of every element of in_buf into the slot table,
-// accumulating amplitudes.  kind < 4: a diagonal gate; SF_INSERT_FRAME: the
-// elements themselves; SF_INSERT_COFACTOR: the two cofactor children.  Sets
-// the table size for the compaction and zeroes the output count.
+// Hash every element of in_buf into the slot table, accumulating the
+// amplitudes of equal phase vectors (generic COALESCE of a frame that may hold
+// repeated phase vectors).  Sets the table size for the compaction and zeroes
+// the output count.
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_insert(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
-                                                     int in_buf, int out_buf) {
-    __shared__ BrPlan<W> P;
-    __shared__ CofPlan<W> CP;
+__global__ void __launch_bounds__(kThreads) k_insert(SfDev d, int in_buf, int out_buf) {
     if (*d.status) return;
-    int ng = 1;
-    if (kind < 4) {
-        if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, theta, P);
-        __syncthreads();
-        if (P.bad) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 24u);
-            return;
-        }
-        ng = P.ng;
-    } else if (kind == SF_INSERT_COFACTOR) {
-        if (!d.meta[2]) return;  // deterministic qubit: nothing to split
-        if (threadIdx.x == 0) load_cof_plan<W>(d, CP);
-        __syncthreads();
-        ng = 2;
-    }
     const unsigned long long k = d.kcnt[in_buf];
-    const unsigned long long nchild = (unsigned long long)ng * k;
-    if (nchild > d.cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_CAPACITY, in_buf);
-        return;
-    }
-    const unsigned long long T = table_size(nchild, d.tcap);
+    const unsigned long long T = table_size(k, d.tcap);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *d.tsize = T;
         d.kcnt[out_buf] = 0;
@@ -567,25 +531,7 @@ __global__ void __launch_bounds__(kThreads) k_insert(SfDev d, uint32_t kind, uin
          j += (unsigned long long)gridDim.x * blockDim.x) {
         uint64_t s[W];
         load_sig<W>(Si, cap, j, s);
-        const double2 a = Ai[j];
-        if (kind == SF_INSERT_FRAME) {
-            ok &= table_insert<W>(d, T, s, a);
-        } else if (kind == SF_INSERT_COFACTOR) {
-            for (int x = 0; x < 2; x++) {
-                uint64_t t[W];
-                const double2 c = cof_child<W>(d, CP, s, a, x, t);
-                ok &= table_insert<W>(d, T, t, c);
-            }
-        } else {
-            for (int g = 0; g < ng; g++) {
-                const double2 cf = group_coef<W>(P, g, s);
-                if (cf.x == 0.0 && cf.y == 0.0) continue;  // an exactly cancelled child (e.g. control in |0>)
-                uint64_t c[W];
-#pragma unroll
-                for (int w = 0; w < W; w++) c[w] = s[w] ^ P.u[g][w];
-                ok &= table_insert<W>(d, T, c, cmul(cf, a));
-            }
-        }
+        ok &= table_insert<W>(d, T, s, Ai[j]);
     }
     if (!ok) set_status(d.status, SF_ST_TIMEOUT, in_buf);
 }
@@ -597,6 +543,10 @@ template <int W>
 __global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, double eps2) {
     if (*d.status) return;
     const unsigned long long T = *d.tsize;
+    // outputs are at most the occupied slots, which are at most T / 2
+    const unsigned long long TI = index_slots(T / 2, d.icap);
+    const uint32_t tag = next_tag(d.itag[out_buf]);
+    bool ok = true;
     const unsigned long long tcap = d.tcap;
     const int lane = threadIdx.x & 31;
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
@@ -640,8 +590,14 @@ __global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, doub
                 const unsigned long long o = b + __popc(bal & ((1u << lane) - 1u));
                 store_sig<W>(So, cap, o, key);
                 Ao[o] = a;
+                ok &= index_insert<W>(d, out_buf, TI, tag, key, (uint32_t)o);
             }
         }
+    }
+    if (!ok) set_status(d.status, SF_ST_TIMEOUT, out_buf);
+    if (last_block(d.done) && threadIdx.x == 0) {
+        d.itag[out_buf] = tag;
+        d.isize[out_buf] = TI;
     }
 }
 
@@ -657,6 +613,9 @@ __global__ void __launch_bounds__(kThreads) k_filter(SfDev d, int x, int in_buf,
     }
     const double scale = 1.0 / sqrt(d.out[x]);
     const unsigned long long k = d.kcnt[in_buf];
+    const unsigned long long TI = index_slots(k, d.icap);
+    const uint32_t tag = next_tag(d.itag[out_buf]);
+    bool ok = true;
     const int lane = threadIdx.x & 31;
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -684,8 +643,264 @@ __global__ void __launch_bounds__(kThreads) k_filter(SfDev d, int x, int in_buf,
                 a.x *= scale;
                 a.y *= scale;
                 d.amp[out_buf][o] = a;
+                ok &= index_insert<W>(d, out_buf, TI, tag, s, (uint32_t)o);
             }
         }
+    }
+    if (!ok) set_status(d.status, SF_ST_TIMEOUT, out_buf);
+    if (last_block(d.done) && threadIdx.x == 0) {
+        d.itag[out_buf] = tag;
+        d.isize[out_buf] = TI;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// (Re)build the index of buffer b.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_build_index(SfDev d, int b) {
+    if (*d.status) return;
+    const unsigned long long k = d.kcnt[b];
+    const unsigned long long TI = index_slots(k, d.icap);
+    const uint32_t tag = next_tag(d.itag[b]);
+    bool ok = true;
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        uint64_t s[W];
+        load_sig<W>(d.sig[b], d.cap, j, s);
+        ok &= index_insert<W>(d, b, TI, tag, s, (uint32_t)j);
+    }
+    if (!ok) set_status(d.status, SF_ST_TIMEOUT, b);
+    if (last_block(d.done) && threadIdx.x == 0) {
+        d.itag[b] = tag;
+        d.isize[b] = TI;
+    }
+}
+
+// Diagonal gate sum_g G_g (G_g the terms with anticommutation mask u_g) with
+// merging: the masks form a group U (u_0 = 0), and the children of element s
+// are s ^ u_g.  Output tau = s ^ u_g is produced only by its owner, the parent
+// s such that no tau ^ u_g' with g' < g is in the frame; its amplitude sums the
+// contributions of every parent tau ^ u_g'' found through the index of in_buf,
+// in a fixed order.  No amplitude atomics; the output frame is indexed.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1,
+                                                           double theta, double eps2, int in_buf, int out_buf) {
+    __shared__ BrPlan<W> P;
+    __shared__ int xidx[SF_BR_MAXG][SF_BR_MAXG];
+    __shared__ unsigned int wsum[kThreads / 32];
+    __shared__ unsigned long long bbase;
+    if (*d.status) return;
+    const unsigned long long k = d.kcnt[in_buf];
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const uint32_t tag_out = next_tag(d.itag[out_buf]);
+    // CTAs without elements skip the plan and only take part in the publication
+    const bool idle = (unsigned long long)blockIdx.x * blockDim.x >= k && blockIdx.x != 0;
+    if (idle) {
+        if (last_block(d.done) && threadIdx.x == 0) {
+            d.kcnt[out_buf] = *d.ocnt;
+            *d.ocnt = 0;
+            d.itag[out_buf] = tag_out;
+            d.isize[out_buf] = *d.ipend;
+        }
+        return;
+    }
+    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, theta, P);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int bad = P.bad;
+        for (int g = 0; g < P.ng; g++)
+            for (int g2 = 0; g2 < P.ng; g2++) {
+                int m = -1;
+                for (int g3 = 0; g3 < P.ng; g3++) {
+                    bool eq = true;
+                    for (int w = 0; w < W; w++) eq &= (P.u[g][w] ^ P.u[g2][w]) == P.u[g3][w];
+                    if (eq) { m = g3; break; }
+                }
+                if (m < 0) bad = 1;
+                xidx[g][g2] = m < 0 ? 0 : m;
+            }
+        for (int w = 0; w < W; w++) bad |= (P.u[0][w] != 0);
+        P.bad = bad;
+    }
+    __syncthreads();
+    if (P.bad) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 26u);
+        return;
+    }
+    const int ng = P.ng;
+    const unsigned long long nmax = (unsigned long long)ng * k;
+    if (nmax > d.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_CAPACITY, in_buf);
+        return;
+    }
+    const unsigned long long Tin = d.isize[in_buf];
+    const uint32_t tag_in = d.itag[in_buf];
+    const unsigned long long Tout = index_slots(nmax, d.icap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d.ipend = Tout;
+    const uint64_t* Si = d.sig[in_buf];
+    const double2* Ai = d.amp[in_buf];
+    uint64_t* So = d.sig[out_buf];
+    double2* Ao = d.amp[out_buf];
+    const uint64_t cap = d.cap;
+    bool ok = tag_in != 0;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < k; base += stride) {
+        const unsigned long long j = base + threadIdx.x;
+        const bool act = j < k;
+        uint64_t s[W];
+        double2 a = make_double2(0.0, 0.0);
+        long long idx[SF_BR_MAXG];
+        idx[0] = act ? (long long)j : -1;
+        if (act) {
+            load_sig<W>(Si, cap, j, s);
+            a = Ai[j];
+            for (int g = 1; g < ng; g++) {
+                uint64_t key[W];
+#pragma unroll
+                for (int w = 0; w < W; w++) key[w] = s[w] ^ P.u[g][w];
+                idx[g] = index_find<W>(d, in_buf, Tin, tag_in, key);
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < W; w++) s[w] = 0;
+            for (int g = 1; g < ng; g++) idx[g] = -1;
+        }
+        double2 amps[SF_BR_MAXG];
+        unsigned keepm = 0;
+        for (int g = 0; g < ng; g++) {
+            bool own = act;
+            for (int g2 = 0; g2 < g; g2++) own &= idx[xidx[g][g2]] < 0;
+            double2 amp = make_double2(0.0, 0.0);
+            if (own) {
+                for (int g2 = 0; g2 < ng; g2++) {
+                    const int m = xidx[g][g2];
+                    if (idx[m] < 0) continue;
+                    uint64_t px[W];  // parent tau ^ u_g2 = s ^ u_m
+#pragma unroll
+                    for (int w = 0; w < W; w++) px[w] = s[w] ^ P.u[m][w];
+                    const double2 ap = m == 0 ? a : Ai[idx[m]];
+                    const double2 c = cmul(group_coef<W>(P, g2, px), ap);
+                    amp.x += c.x;
+                    amp.y += c.y;
+                }
+            }
+            amps[g] = amp;
+            if (own && (amp.x * amp.x + amp.y * amp.y >= eps2)) keepm |= 1u << g;
+        }
+        // one reservation per iteration for all kept outputs of the block
+        unsigned long long o = block_out_range(d.ocnt, __popc(keepm), wsum, &bbase);
+        for (int g = 0; g < ng; g++) {
+            if (!((keepm >> g) & 1u)) continue;
+            uint64_t tau[W];
+#pragma unroll
+            for (int w = 0; w < W; w++) tau[w] = s[w] ^ P.u[g][w];
+            store_sig<W>(So, cap, o, tau);
+            Ao[o] = amps[g];
+            ok &= index_insert<W>(d, out_buf, Tout, tag_out, tau, (uint32_t)o);
+            o++;
+        }
+    }
+    if (!ok) set_status(d.status, SF_ST_TIMEOUT, in_buf);
+    if (last_block(d.done) && threadIdx.x == 0) {
+        d.kcnt[out_buf] = *d.ocnt;
+        *d.ocnt = 0;
+        d.itag[out_buf] = tag_out;
+        d.isize[out_buf] = *d.ipend;
+    }
+}
+
+// Cofactor split with merging (COFACTOR, Sec. III): elements s and s ^ uq
+// (uq: rows of the old tableau anticommuting with Z_q) have the same two
+// cofactor children; the one with the smaller phase vector emits both, summing
+// the two contributions.
+template <int W>
+__device__ __forceinline__ bool sig_less(const uint64_t* a, const uint64_t* b) {
+#pragma unroll
+    for (int w = W - 1; w >= 0; w--)
+        if (a[w] != b[w]) return a[w] < b[w];
+    return false;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_cof_merge(SfDev d, double eps2, int in_buf, int out_buf) {
+    __shared__ CofPlan<W> CP;
+    __shared__ uint64_t uq[W];
+    __shared__ unsigned int wsum[kThreads / 32];
+    __shared__ unsigned long long bbase;
+    if (*d.status) return;
+    if (!d.meta[2]) return;
+    if (threadIdx.x == 0) {
+        load_cof_plan<W>(d, CP);
+        for (int w = 0; w < W; w++) uq[w] = d.plan[cf_uq(d.n, W) + w];
+    }
+    __syncthreads();
+    const unsigned long long k = d.kcnt[in_buf];
+    if (2 * k > d.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_CAPACITY, in_buf);
+        return;
+    }
+    const unsigned long long Tin = d.isize[in_buf];
+    const uint32_t tag_in = d.itag[in_buf];
+    const unsigned long long Tout = index_slots(2 * k, d.icap);
+    const uint32_t tag_out = next_tag(d.itag[out_buf]);
+    const uint64_t* Si = d.sig[in_buf];
+    const double2* Ai = d.amp[in_buf];
+    uint64_t* So = d.sig[out_buf];
+    double2* Ao = d.amp[out_buf];
+    const uint64_t cap = d.cap;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    bool ok = tag_in != 0;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < k; base += stride) {
+        const unsigned long long j = base + threadIdx.x;
+        const bool act = j < k;
+        uint64_t s[W], p[W];
+        double2 a = make_double2(0.0, 0.0), ap = make_double2(0.0, 0.0);
+        long long l = -1;
+        bool own = false;
+        if (act) {
+            load_sig<W>(Si, cap, j, s);
+            a = Ai[j];
+#pragma unroll
+            for (int w = 0; w < W; w++) p[w] = s[w] ^ uq[w];
+            l = index_find<W>(d, in_buf, Tin, tag_in, p);
+            own = l < 0 || sig_less<W>(s, p);
+            if (l >= 0) ap = Ai[l];
+        }
+        uint64_t t[2][W];
+        double2 cc[2];
+        unsigned keepm = 0;
+        for (int x = 0; x < 2; x++) {
+            double2 c = make_double2(0.0, 0.0);
+            if (own) {
+                c = cof_child<W>(d, CP, s, a, x, t[x]);
+                if (l >= 0) {
+                    uint64_t t2[W];
+                    const double2 c2 = cof_child<W>(d, CP, p, ap, x, t2);
+                    bool same = true;
+#pragma unroll
+                    for (int w = 0; w < W; w++) same &= t2[w] == t[x][w];
+                    if (!same) set_status(d.status, SF_ST_INTERNAL, in_buf, 27u);
+                    c.x += c2.x;
+                    c.y += c2.y;
+                }
+            }
+            cc[x] = c;
+            if (own && (c.x * c.x + c.y * c.y >= eps2)) keepm |= 1u << x;
+        }
+        unsigned long long o = block_out_range(d.ocnt, __popc(keepm), wsum, &bbase);
+        for (int x = 0; x < 2; x++) {
+            if (!((keepm >> x) & 1u)) continue;
+            store_sig<W>(So, cap, o, t[x]);
+            Ao[o] = cc[x];
+            ok &= index_insert<W>(d, out_buf, Tout, tag_out, t[x], (uint32_t)o);
+            o++;
+        }
+    }
+    if (!ok) set_status(d.status, SF_ST_TIMEOUT, in_buf);
+    if (last_block(d.done) && threadIdx.x == 0) {
+        d.kcnt[out_buf] = *d.ocnt;
+        *d.ocnt = 0;
+        d.itag[out_buf] = tag_out;
+        d.isize[out_buf] = Tout;
     }
 }
 
@@ -830,9 +1045,22 @@ void sf_launch_branch(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, d
     SF_DISPATCH(d.W, k_branch<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, theta, in_buf, out_buf));
 }
 
-void sf_launch_insert(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
-                      int out_buf, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_insert<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, theta, in_buf, out_buf));
+void sf_launch_insert(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_insert<WW><<<d.nblk, kThreads, 0, s>>>(d, in_buf, out_buf));
+}
+
+void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, double eps,
+                            int in_buf, int out_buf, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_branch_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, theta, eps * eps, in_buf,
+                                                                    out_buf));
+}
+
+void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_cof_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf));
+}
+
+void sf_launch_build_index(const SfDev& d, int buf, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_build_index<WW><<<d.nblk, kThreads, 0, s>>>(d, buf));
 }
 
 void sf_launch_compact(const SfDev& d, double eps, int out_buf, cudaStream_t s) {

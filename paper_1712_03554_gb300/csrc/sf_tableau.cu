@@ -49,7 +49,7 @@ template <int W>
 struct Scratch {
     Pauli<W> red[kMaxWarps + 1];
     int wmin[2][kMaxWarps];
-    uint64_t y[W], y2[W], words[4][W];
+    uint64_t y[W], y2[W], words[5][W];
     int iv[8];
     double dv[8];
 };
@@ -452,8 +452,11 @@ __global__ void __launch_bounds__(1024) k_measure_prep(SfDev d, uint32_t q, int 
         S.words[0][h] = 0;
         S.words[1][h] = 0;
         S.words[2][h] = 0;
+        S.words[4][h] = 0;
     }
     __syncthreads();
+    // rows anticommuting with Z_q: elements sigma and sigma ^ uq share their cofactors
+    cta_bits<W>(uh, S.words[4]);
     int num1 = 0;
     {
         uint64_t xi[W], zi[W];
@@ -537,6 +540,7 @@ __global__ void __launch_bounds__(1024) k_measure_prep(SfDev d, uint32_t q, int 
         pl[ko + 3] = (uint64_t)__double_as_longlong(k1.y);
     }
     if (h < W) {
+        pl[cf_uq(n, W) + h] = S.words[4][h];
         pl[cf_vq(n, W) + h] = S.words[0][h];
         pl[cf_tau(n, W) + h] = S.words[1][h];
         pl[cf_tau(n, W) + W + h] = S.words[2][h];
@@ -648,6 +652,15 @@ __global__ void k_reset(SfDev d, int buf) {
         d.kcnt[buf] = 1;
         d.kcnt[buf ^ 1] = 0;
         *d.status = 0;
+        *d.done = 0u;
+        *d.ocnt = 0ull;
+        // index of the one-element frame
+        const uint32_t tag = next_tag(d.itag[buf]);
+        uint64_t zero[W];
+        for (int w = 0; w < W; w++) zero[w] = 0;
+        index_insert<W>(d, buf, 64, tag, zero, 0u);
+        d.itag[buf] = tag;
+        d.isize[buf] = 64;
     }
 }
 
@@ -698,6 +711,10 @@ void sf_launch_reset(const SfDev& d, int buf, cudaStream_t s) {
 }
 
 void sf_launch_clifford(const SfDev& d, const void* dev_gates, int ngates, int buf, uint64_t* gws, cudaStream_t s) {
+    if (d.W == 1) {  // n <= 63: one warp, rows in registers
+        sf_launch_clifford_warp(d, dev_gates, ngates, buf, s);
+        return;
+    }
     SF_DISPATCH(d.W, {
         size_t sm;
         uint64_t* ws = pick_ws<WW>(d, k_clifford<WW>, sm, gws, 0);

@@ -17,8 +17,8 @@ from . import _build
 
 SF_OK, SF_EINVAL, SF_ENOMEM, SF_ECAPACITY, SF_ECUDA, SF_ETIMEOUT, SF_ESTATE, SF_EINTERNAL = range(8)
 # kernel classes (SF_K_* in include/sf.h)
-KERNEL_CLASSES = ["clifford", "affine", "branch", "insert", "compact", "measure_prep", "prob", "reduce",
-                  "amp_prep", "amplitude", "filter", "export", "reset"]
+KERNEL_CLASSES = ["clifford", "affine", "branch", "branch_merge", "insert", "compact", "index", "measure_prep",
+                  "cofactor", "prob", "reduce", "amp_prep", "amplitude", "filter", "export", "reset"]
 STATUS_NAMES = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOMEM", 3: "SF_ECAPACITY", 4: "SF_ECUDA",
                 5: "SF_ETIMEOUT", 6: "SF_ESTATE", 7: "SF_EINTERNAL"}
 
@@ -67,6 +67,8 @@ def load(build: bool = True) -> C.CDLL:
         "sf_get_frame": ([H, P64, PD, u64, P64], st),
         "sf_words": ([H], u32),
         "sf_kernel_launches": ([H], u64),
+        "sf_host_state": ([H], u32),
+        "sf_set_host_state": ([H, u32], st),
         "sf_get_internal": ([H, P64, P64, C.POINTER(C.c_uint32), PD], st),
         "sf_time_kernel": ([H, C.c_int32], st),
         "sf_kernel_time": ([H, PD, P64], st),
@@ -213,6 +215,13 @@ class Frame:
                                              de.ctypes.data_as(C.POINTER(C.c_uint32)),
                                              g.ctypes.data_as(C.POINTER(C.c_double))), self.h)
         return dx, dz, de, complex(g[0], g[1])
+
+    def host_state(self) -> int:
+        """Token of the host-side bookkeeping (restore it after replaying a graph)."""
+        return int(self.lib.sf_host_state(self.h))
+
+    def set_host_state(self, token: int) -> None:
+        self._check(self.lib.sf_set_host_state(self.h, token), self.h)
 
     def kernel_launches(self) -> int:
         return int(self.lib.sf_kernel_launches(self.h))

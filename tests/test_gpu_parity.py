@@ -298,3 +298,51 @@ def test_fused_and_separate_merge_agree(sfm, seed):
     c.run(o, ops)
     frames_equal(g1, o)
     frames_equal(g2, o)
+
+
+def test_graph_replay_matches_eager(sfm):
+    """A step captured in a CUDA graph (device gate lists, fused merges) and
+    replayed several times, with the host bookkeeping restored after each
+    replay, gives the eager result every time (measurement tail included)."""
+    import torch
+    n = 14
+    x, ops = c.qft_random_input(n, 4)
+    cl = [op for op in ops if op[0] == "C"]
+    stream = torch.cuda.Stream()
+    g = sfm.Frame(n, 1 << (n + 2), stream=stream)
+    seq = []
+    pending = []
+    for op in ops:
+        if op[0] == "C":
+            pending.append(op)
+            continue
+        if pending:
+            arr = np.array([[p[1], p[2], p[3], 0] for p in pending], dtype=np.uint32)
+            seq.append(("C", torch.from_numpy(arr.view(np.int32)).cuda()))
+            pending = []
+        seq.append(op)
+
+    def async_part():
+        g.reset()
+        for op in seq:
+            if op[0] == "C":
+                g.apply_clifford_device(op[1].data_ptr(), op[1].shape[0])
+            elif op[0] == "N":
+                g.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], 1e-12)
+
+    with torch.cuda.stream(stream):
+        async_part()
+    p_ref = g.measure(0)
+    s_ref, a_ref = g.frame()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        async_part()
+    token = g.host_state()
+    for _ in range(3):
+        with torch.cuda.stream(stream):
+            graph.replay()
+        g.set_host_state(token)
+        p = g.measure(0)
+        s, a = g.frame()
+        assert abs(p[0] - p_ref[0]) <= TOL
+        assert np.array_equal(s, s_ref) and np.max(np.abs(a - a_ref)) <= TOL
