@@ -1,0 +1,125 @@
+"""Per-kernel throughput of the frame kernels at a chosen frame size.
+
+A frame of exactly 2^m distinct elements is built on n = 40 qubits (H on every
+qubit, then T on qubits 0..m-1, merged after each), and each kernel class is
+timed with the library's CUDA-event brackets (sf_time_kernel) on its own
+stream.  GB/s use the algorithmic bytes of each kernel (phase vectors and
+amplitudes read and written; index and hash tables are not counted).
+
+  python -m paper_1712_03554_gb300.kernel_bench throughput 16 20 24
+  python -m paper_1712_03554_gb300.kernel_bench latency
+  python -m paper_1712_03554_gb300.kernel_bench merge-case 20   (a short run for ncu captures)
+"""
+from __future__ import annotations
+
+import json
+import sys
+import time
+
+from . import circuits as c
+from . import sf
+
+N = 40
+E = 24  # bytes of one element at W = 1: phase vector + FP64 complex amplitude
+
+
+def frame_of(n: int, m: int, cap: int, stream=None):
+    f = sf.Frame(n, cap, stream=stream)
+    f.apply_clifford([(c.H, q, 0) for q in range(n)])
+    for q in range(m):
+        f.apply_nonclifford_coalesce(c.T, q, 0, 0.0, 1e-12)
+    f.sync()
+    return f
+
+
+def timed(f, cls, fn, reps):
+    f.time_kernel(cls)
+    for _ in range(reps):
+        fn()
+    ms, cnt = f.kernel_time()
+    f.time_kernel(-1)
+    return ms / max(cnt, 1)
+
+
+def throughput(ms_list):
+    import torch
+    stream = torch.cuda.Stream()
+    for m in ms_list:
+        k = 1 << m
+        f = frame_of(N, m, 1 << (m + 2), stream)
+        assert f.size() == k
+        res = {"k": k}
+        gates = [(c.S, m + 1, 0), (c.CNOT, m + 2, m + 3), (c.H, m + 4, 0), (c.CZ, m + 5, m + 6)]
+        ms = timed(f, "affine", lambda: f.apply_clifford(gates), 5)
+        res["affine_us"] = ms * 1e3
+        res["affine_GBs"] = 2 * 8 * k / (ms * 1e-3) / 1e9
+        res["clifford_us_4_gates"] = timed(f, "clifford", lambda: f.apply_clifford(gates), 5) * 1e3
+
+        def tt():  # k -> 2k -> k
+            f.apply_nonclifford_coalesce(c.T, m, 0, 0.0, 1e-12)
+            f.apply_nonclifford_coalesce(c.TDG, m, 0, 0.0, 1e-12)
+        ms = timed(f, "branch_merge", tt, 3)
+        res["branch_merge_us"] = ms * 1e3
+        res["branch_merge_GBs"] = E * 3 * k / 2 / (ms * 1e-3) / 1e9  # (k in + 2k out, 2k in + k out) / 2
+
+        def br():
+            f.apply_nonclifford(c.T, m, 0, 0.0)
+            f.coalesce(1e-12)
+            f.apply_nonclifford(c.TDG, m, 0, 0.0)
+            f.coalesce(1e-12)
+        ms = timed(f, "branch", br, 2)
+        res["branch_us"] = ms * 1e3
+        res["branch_GBs"] = (E * 1.5 * k + E * 3 * k) / (ms * 1e-3) / 1e9
+        res["insert_us"] = timed(f, "insert", br, 2) * 1e3
+        res["compact_us"] = timed(f, "compact", br, 2) * 1e3
+        ms = timed(f, "index", lambda: (f.apply_clifford(gates),
+                                        f.apply_nonclifford_coalesce(c.PHASE, m + 7, 0, 0.0, 1e-12)), 2)
+        res["index_us"] = ms * 1e3
+        res["index_GBs"] = 8 * k / (ms * 1e-3) / 1e9
+        assert f.size() == k
+        t0 = time.perf_counter()
+        f.measure(m + 10, -1)
+        res["measure_ms_wall"] = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        f.amplitude(12345)
+        res["amplitude_ms_wall"] = (time.perf_counter() - t0) * 1e3
+        print(json.dumps(res), flush=True)
+        f.close()
+
+
+def latency():
+    import torch
+    stream = torch.cuda.Stream()
+    res = {}
+    for m in (4, 8, 12, 16, 20):
+        f = frame_of(30, m, 1 << (m + 2), stream)
+        res[f"branch_merge_us_k2^{m}"] = timed(f, "branch_merge", lambda: (
+            f.apply_nonclifford_coalesce(c.CPHASE, m, m + 1, 0.3, 1e-12),
+            f.apply_nonclifford_coalesce(c.CPHASE, m, m + 1, -0.3, 1e-12)), 5) * 1e3
+        res[f"affine_us_k2^{m}"] = timed(f, "affine", lambda: f.apply_clifford([(c.S, m + 2, 0)]), 5) * 1e3
+        res[f"clifford_us_k2^{m}"] = timed(f, "clifford", lambda: f.apply_clifford([(c.S, m + 2, 0)]), 5) * 1e3
+        f.close()
+    print(json.dumps({k: round(v, 2) for k, v in res.items()}), flush=True)
+
+
+def merge_case(m):
+    """m merged T gates (launches 0..m-1 of k_branch_merge at k = 2^i), then T
+    and T-dagger on a fresh qubit (launch m: 2^m -> 2^(m+1), launch m+1 back)."""
+    f = frame_of(N, m, 1 << (m + 2))
+    f.apply_nonclifford_coalesce(c.T, m, 0, 0.0, 1e-12)
+    f.apply_nonclifford_coalesce(c.TDG, m, 0, 0.0, 1e-12)
+    f.sync()
+    print("k", f.size())
+
+
+if __name__ == "__main__":
+    mode = sys.argv[1] if len(sys.argv) > 1 else "throughput"
+    args = [int(a) for a in sys.argv[2:]]
+    if mode == "throughput":
+        throughput(args or [16, 20, 24])
+    elif mode == "latency":
+        latency()
+    elif mode == "merge-case":
+        merge_case(args[0] if args else 20)
+    else:
+        raise SystemExit(f"unknown mode {mode}")
