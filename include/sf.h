@@ -232,6 +232,72 @@ uint32_t sf_words(sf_handle h);
 /* Message for the last error of the handle; NULL handle -> last global error. */
 const char* sf_last_error(sf_handle h);
 
+/* ---- Batched campaigns: many small independent circuits in one launch ------
+ * The same frame algebra (Sec. III-IV) run on many circuits of n <= 63 qubits
+ * at once, one circuit per CTA of a persistent kernel, with the circuit's
+ * tableau in registers and its frame in a per-CTA workspace -- for workloads
+ * such as fault-injection campaigns, where each circuit is small but there are
+ * thousands of them.  Every diagonal gate is merged as in
+ * sf_apply_nonclifford_coalesce; measurements are cofactored (COFACTOR,
+ * Sec. III), their outcome is drawn from the program and the frame collapsed;
+ * classically conditioned Clifford gates read the outcomes so far.
+ *
+ * A program is an array of sf_op records; circuit c is records
+ * [offsets[c], offsets[c+1]).  Op kinds:
+ *   0..8        Clifford gate (SF_H..SF_SWAP) on q0 (control) and q1
+ *   16 + k      diagonal gate k (SF_T..SF_CPHASE) on q0, q1, angle param;
+ *               merged, children with |a| < drop_eps dropped
+ *   SF_OP_MEASURE  measure Z on q0 and collapse: outcome 1 iff param < p(1),
+ *               param being a uniform draw in [0, 1) made by the caller;
+ *               p(1) is the unnormalised probability sum of the frame, and the
+ *               survivors are divided by sqrt(p(outcome))
+ *   SF_OP_COND  Clifford gate `arg` on q0, q1 applied iff the parity of
+ *               (outcome bits & mask) is 1, mask = the 64 bits of param
+ *               (bit m = outcome of the circuit's m-th measurement)
+ * At most 64 measurements per circuit. */
+#define SF_CAMPAIGN_MAX_ELEMS 16384u
+enum { SF_OP_DIAG = 16, SF_OP_MEASURE = 32, SF_OP_COND = 33 };
+
+typedef struct {
+    uint32_t kind, q0, q1, arg;
+    double param; /* angle, draw, or mask bits (memcpy of a uint64_t) */
+} sf_op;
+
+typedef struct sf_campaign_s* sf_campaign;
+
+/* Engine for circuits on n_qubits (1..63) whose frames never exceed
+ * max_elems (1..SF_CAMPAIGN_MAX_ELEMS) elements, on cuda_stream.  Allocates a
+ * workspace of about (#CTAs x max_elems x 48) bytes, #CTAs = SMs x resident
+ * CTAs per SM.  Synchronises. */
+sf_status sf_campaign_create(uint32_t n_qubits, uint32_t max_elems, void* cuda_stream, sf_campaign* out);
+
+/* Waits for the engine's stream and frees the workspace. */
+sf_status sf_campaign_destroy(sf_campaign c);
+
+/* Runs n_circuits circuits.  All pointers are device pointers, owned by the
+ * caller and valid until the stream reaches the launch: dev_ops (sf_op
+ * records), dev_offsets (n_circuits + 1 entries).  Per circuit c it writes
+ * dev_outcomes[c] (bit m = outcome of measurement m), dev_n_meas[c],
+ * dev_k_final[c] (final frame size), dev_norm[c] (sum of |a|^2 of the final
+ * frame, times |g|^2 = 1) and dev_status[c] (an sf_status: SF_EINVAL for a bad
+ * op, SF_ECAPACITY if a step would exceed max_elems, SF_ESTATE for a collapse
+ * onto probability 0, SF_EINTERNAL for a failed tableau check; the circuit
+ * stops at its first failing op and the others run on).  If the three export
+ * pointers are non-NULL, the final frame of circuit c is written in the
+ * canonical convention of sf_get_frame: dev_export_sigma[c * max_elems + j]
+ * (one word), dev_export_amp[2 * (c * max_elems + j) + {0, 1}] for
+ * j < k_final, in the frame's order (not sorted), and dev_export_tableau[c * 129 + {0..63, 64..127, 128}] = the x
+ * words, z words of the canonical rows and the X-block size r.  All three or
+ * none.  Results do not depend on the number of CTAs or the order in which
+ * circuits are run.  Asynchronous (one memset and one kernel on the stream). */
+sf_status sf_campaign_run(sf_campaign c, const sf_op* dev_ops, const uint64_t* dev_offsets, uint32_t n_circuits,
+                          double drop_eps, uint64_t* dev_outcomes, uint32_t* dev_n_meas, uint32_t* dev_k_final,
+                          double* dev_norm, int32_t* dev_status, uint64_t* dev_export_sigma,
+                          double* dev_export_amp, uint64_t* dev_export_tableau);
+
+/* Number of CTAs of the engine's persistent launch. */
+uint32_t sf_campaign_ctas(sf_campaign c);
+
 #ifdef __cplusplus
 }
 #endif

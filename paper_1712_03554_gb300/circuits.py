@@ -13,6 +13,9 @@ Op encoding (one tuple per op):
   ("M", q, u)                      measure qubit q; outcome = 1 if u < p(1) else 0
                                    (u is a seeded uniform draw, or None for
                                    "probabilities only")
+  ("Q", kind, q0, q1, mask)        classically controlled Clifford gate: applied
+                                   iff the parity of (outcome bits & mask) is 1,
+                                   bit m = outcome of the m-th drawn measurement
 
 Gate semantics follow the paper: H, P (= S) and CNOT are the Clifford gates of
 Table 2 (Sec. II-B); T/T-dagger are the technology-dependent non-Clifford gates
@@ -242,6 +245,8 @@ def run(sim, ops: Sequence[Op], drop_eps: float = 1e-12, batch_cliffords: bool =
     (q, p0, p1, outcome) for every measurement."""
     pending: List[Tuple[int, int, int]] = []
     results = []
+    outcome_bits = 0
+    n_drawn = 0
 
     def flush():
         if pending:
@@ -279,14 +284,153 @@ def run(sim, ops: Sequence[Op], drop_eps: float = 1e-12, batch_cliffords: bool =
                 x = 1 if u < p1 else 0
                 sim.measure(q, x)
                 results.append((q, p0, p1, x))
+                outcome_bits |= x << n_drawn
+                n_drawn += 1
+        elif tag == "Q":
+            if bin(outcome_bits & op[4]).count("1") & 1:
+                pending.append((op[1], op[2], op[3]))
+                if not batch_cliffords:
+                    flush()
         else:
             raise ValueError(f"unknown op {op!r}")
     flush()
     return results
 
 
+# ---- workload 4: Steane [[7,1,3]] fault-injection campaign ---------------------------
+# Hamming [7,4] parity checks; each support carries one X-type and one Z-type
+# stabilizer of the Steane code.  {0, 1, 2} is a weight-3 Hamming codeword, so
+# X and Z on qubits 0, 1, 2 are logical X and Z representatives.
+STEANE_CHECKS = ((3, 4, 5, 6), (1, 2, 5, 6), (0, 2, 4, 6))
+STEANE_LOGICAL = (0, 1, 2)
+STEANE_N = 49
+STEANE_ROUNDS = 3
+INVERSE_CLIFFORD = {H: H, S: SDG, SDG: S, X: X, Y: Y, Z: Z, CNOT: CNOT, CZ: CZ, SWAP: SWAP}
+
+
+def steane_layout():
+    """Qubit roles of the 49-qubit campaign circuit: data 0..6, magic-state
+    ancilla 7; for round r and stabilizer s (0..2 Z-type, 3..5 X-type) a
+    syndrome ancilla 8 + 12 r + 2 s and its flag 9 + 12 r + 2 s; readout
+    ancillas 44 (logical X), 45 (logical Z), 46..48 (final Z checks)."""
+    synd = {(r, s): (8 + 12 * r + 2 * s, 9 + 12 * r + 2 * s) for r in range(STEANE_ROUNDS) for s in range(6)}
+    return {"data": list(range(7)), "magic": 7, "synd": synd, "read_x": 44, "read_z": 45,
+            "checks": [46, 47, 48]}
+
+
+def _stabilizer_round(r: int, L) -> List[Op]:
+    """One flagged syndrome-extraction round: each weight-4 stabilizer is read
+    through one ancilla, with a flag qubit coupled between the first and the
+    last data CNOT."""
+    ops: List[Op] = []
+    for s in range(6):
+        a, f = L["synd"][(r, s)]
+        sup = STEANE_CHECKS[s % 3]
+        if s < 3:  # Z-type: data -> ancilla parity; flag in |+>, X-basis readout
+            ops += [("C", H, f, 0), ("C", CNOT, sup[0], a), ("C", CNOT, f, a), ("C", CNOT, sup[1], a),
+                    ("C", CNOT, sup[2], a), ("C", CNOT, f, a), ("C", CNOT, sup[3], a), ("C", H, f, 0),
+                    ("M", f, None), ("M", a, None)]
+        else:      # X-type: ancilla in |+> drives the data; flag in |0>
+            ops += [("C", H, a, 0), ("C", CNOT, a, sup[0]), ("C", CNOT, a, f), ("C", CNOT, a, sup[1]),
+                    ("C", CNOT, a, sup[2]), ("C", CNOT, a, f), ("C", CNOT, a, sup[3]), ("C", H, a, 0),
+                    ("M", a, None), ("M", f, None)]
+    return ops
+
+
+def steane_base() -> List[Op]:
+    """Encode |0>_L, transversal H (|+>_L), syndrome round 0, logical T by an
+    injected magic state (ancilla 7 in T|+>, CNOTs from the logical-Z support,
+    measure; outcome 1 -> S_L, which for the Steane code is S-dagger on every
+    data qubit), rounds 1..2, then logical X and Z readouts and three final
+    Z checks.  Measurement draws are left as None."""
+    L = steane_layout()
+    ops: List[Op] = [("C", H, 0, 0), ("C", H, 1, 0), ("C", H, 3, 0)]
+    for src, tgts in ((0, (2, 4, 6)), (1, (2, 5, 6)), (3, (4, 5, 6))):
+        ops += [("C", CNOT, src, t) for t in tgts]
+    ops += [("C", H, q, 0) for q in L["data"]]
+    ops += _stabilizer_round(0, L)
+    m = L["magic"]
+    ops += [("C", H, m, 0), ("N", T, m, 0, 0.0), ("K",)]
+    ops += [("C", CNOT, q, m) for q in STEANE_LOGICAL]
+    ops += [("M", m, None), ("QT",)]  # ("QT",): conditional S_L on the magic outcome, resolved below
+    for r in range(1, STEANE_ROUNDS):
+        ops += _stabilizer_round(r, L)
+    rx, rz = L["read_x"], L["read_z"]
+    ops += [("C", H, rx, 0)] + [("C", CNOT, rx, q) for q in STEANE_LOGICAL] + [("C", H, rx, 0), ("M", rx, None)]
+    ops += [("C", CNOT, q, rz) for q in STEANE_LOGICAL] + [("M", rz, None)]
+    for c, sup in zip(L["checks"], STEANE_CHECKS):
+        ops += [("C", CNOT, q, c) for q in sup] + [("M", c, None)]
+    # resolve the conditional correction: mask = bit of the magic measurement
+    out: List[Op] = []
+    n_meas = 0
+    for op in ops:
+        if op[0] == "M":
+            n_meas += 1
+        if op[0] == "QT":
+            out += [("Q", SDG, q, 0, 1 << (n_meas - 1)) for q in L["data"]]
+        else:
+            out.append(op)
+    return out
+
+
+def _gate_count(ops: Sequence[Op]) -> int:
+    return sum(1 for op in ops if op[0] != "K")
+
+
+def steane_variant(seed: int, min_len: int = 200, max_len: int = 2000, max_coherent: int = 12) -> List[Op]:
+    """One fault-injection variant of steane_base(): 1-3 single-qubit Pauli
+    errors (X, Y or Z) on uniform qubits at uniform positions, t_v uniform in
+    0..max_coherent coherent T or T-dagger faults on uniform data qubits at
+    uniform positions, padding with adjacent (g, g^-1) Clifford pairs on
+    uniform qubits to a length drawn uniform in [min_len, max_len] (ops other
+    than coalesces), and a uniform draw for every measurement."""
+    g = rng_for(seed)
+    base = steane_base()
+    n = STEANE_N
+    # insertion points: before base op i (i = len(base): at the end), never
+    # between an ("N", ...) and its ("K",)
+    pts = [i for i in range(len(base) + 1) if not (i < len(base) and base[i][0] == "K")]
+    buckets: List[List[Op]] = [[] for _ in range(len(base) + 1)]
+    count = _gate_count(base)
+
+    def insert(seq):
+        nonlocal count
+        buckets[pts[int(g.integers(len(pts)))]].extend(seq)
+        count += _gate_count(seq)
+
+    for _ in range(int(g.integers(1, 4))):
+        insert([("C", (X, Y, Z)[int(g.integers(3))], int(g.integers(n)), 0)])
+    for _ in range(int(g.integers(0, max_coherent + 1))):
+        insert([("N", (T, TDG)[int(g.integers(2))], int(g.integers(7)), 0, 0.0), ("K",)])
+    target = int(g.integers(min_len, max_len + 1))
+    n_pairs = max(0, (target - count + 1) // 2)
+    kinds = (H, S, SDG, X, Y, Z, CNOT, CZ, SWAP)
+    ks = g.integers(len(kinds), size=n_pairs)
+    qa = g.integers(n, size=n_pairs)
+    qb = g.integers(n - 1, size=n_pairs)
+    at = g.integers(len(pts), size=n_pairs)
+    for k_i, a, b, p in zip(ks.tolist(), qa.tolist(), qb.tolist(), at.tolist()):
+        k = kinds[k_i]
+        if k in TWO_QUBIT_CLIFFORD:
+            b = b + 1 if b >= a else b
+            buckets[pts[p]] += [("C", k, a, b), ("C", INVERSE_CLIFFORD[k], a, b)]
+        else:
+            buckets[pts[p]] += [("C", k, a, 0), ("C", INVERSE_CLIFFORD[k], a, 0)]
+    ops: List[Op] = []
+    for i in range(len(base) + 1):
+        ops.extend(buckets[i])
+        if i < len(base):
+            ops.append(base[i])
+    return [("M", op[1], float(g.random())) if op[0] == "M" else op for op in ops]
+
+
+def steane_campaign(n_variants: int = 4096, seed: int = 0, **kw) -> List[List[Op]]:
+    """n_variants seeded variants (variant v uses seed * 1_000_003 + v)."""
+    return [steane_variant(seed * 1_000_003 + v, **kw) for v in range(n_variants)]
+
+
 def count_ops(ops: Sequence[Op]):
-    c = {"C": 0, "N": 0, "K": 0, "M": 0}
+    c = {"C": 0, "N": 0, "K": 0, "M": 0, "Q": 0}
     for op in ops:
         c[op[0]] += 1
     return c

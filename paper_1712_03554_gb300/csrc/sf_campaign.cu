@@ -1,0 +1,731 @@
+// sf_campaign.cu -- batched simulation of many independent small circuits in
+// one persistent launch (up to 63 qubits, frames up to 8192 elements each).
+//
+// One CTA simulates one circuit at a time and pulls the next circuit from a
+// work counter.  Warp 0 keeps the circuit's tableau (M, D) in registers and
+// runs the tableau algebra (Table 2 conjugation, Invariant 1 repair, global
+// phase, branch and cofactor plans; Sec. III-IV); all eight warps run the
+// frame passes (affine phase-vector update, merged branching of diagonal
+// gates, cofactor split, measurement reductions, collapse) on the circuit's
+// frame, which sits in a per-CTA global workspace (L2-resident at these sizes)
+// with its phase-vector index in shared memory.  Outputs are compacted with
+// block scans and sums run in a fixed order, so a circuit's results do not
+// depend on which CTA ran it or what ran beside it.
+//
+// Measurement outcomes come from the draws in the program: outcome 1 iff the
+// draw u < p(1).  A conditional op applies a Clifford gate iff the parity of
+// (outcome bits & mask) is 1 (classically controlled correction).
+#include <algorithm>
+#include <string>
+
+#include "sf.h"
+#include "sf_warp.cuh"
+
+using namespace sfw;
+
+namespace {
+
+constexpr int kCT = 256;  // threads per CTA
+constexpr int kCampMaxCap = SF_CAMPAIGN_MAX_ELEMS;
+
+struct OpRec {
+    uint32_t kind, q0, q1, arg;
+    double param;
+};
+
+struct CampDev {
+    int n, ncirc;
+    unsigned cap;
+    double eps2;
+    const OpRec* ops;
+    const unsigned long long* off;
+    uint64_t* ws_sig;  // [gridDim][2][cap]
+    double2* ws_amp;   // [gridDim][2][cap]
+    unsigned* next;
+    unsigned long long* outcomes;
+    uint32_t* nmeas;
+    uint32_t* kfinal;
+    double* norm;
+    int32_t* cstatus;
+    uint64_t* ex_sig;  // [ncirc][cap] or null
+    double2* ex_amp;   // [ncirc][cap]
+    uint64_t* ex_tab;  // [ncirc][129]: x rows, z rows, r
+};
+
+struct Shared {
+    BrTab P;
+    CofTab C;
+    uint64_t at[64];          // columns of the composed affine map
+    uint64_t tab[16 * 16];    // 4-bit lookup tables of the affine map
+    uint64_t t;               // sign word of the affine map
+    uint64_t rmx[64], rmz[64], rdx[64], rdz[64];
+    uint32_t rde[64];
+    int32_t rpiv[64];
+    double red[2][kCT / 32];
+    unsigned wsum[kCT / 32];
+    Row stage[64];            // row permutation of the tableau reduction
+    unsigned long long obase, outcomes, oe;
+    double2 g;
+    double p[2];
+    unsigned k, kout, nmeas;
+    int cur, rx, status, circ;
+};
+
+__device__ __forceinline__ uint64_t hash1(uint64_t s) {
+    uint64_t v = s + 0x9E3779B97F4A7C15ull;
+    v ^= v >> 30;
+    v *= 0xBF58476D1CE4E5B9ull;
+    v ^= v >> 27;
+    v *= 0x94D049BB133111EBull;
+    v ^= v >> 31;
+    return v;
+}
+
+__device__ __forceinline__ unsigned slots_for(unsigned k) {
+    unsigned t = 64;
+    while (t < 2 * k) t <<= 1;
+    return t;
+}
+
+// index of the frame in buffer sig (k elements): slot = position + 1, 0 empty
+__device__ void build_index(uint32_t* idx, const uint64_t* sig, unsigned k) {
+    const unsigned T = slots_for(k);
+    for (unsigned s = threadIdx.x; s < T; s += blockDim.x) idx[s] = 0;
+    __syncthreads();
+    for (unsigned j = threadIdx.x; j < k; j += blockDim.x) {
+        unsigned slot = (unsigned)hash1(sig[j]) & (T - 1);
+        for (unsigned probe = 0; probe < T; probe++) {
+            if (atomicCAS(&idx[slot], 0u, j + 1) == 0u) break;
+            slot = (slot + 1) & (T - 1);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int find_index(const uint32_t* idx, const uint64_t* sig, unsigned k, uint64_t key) {
+    const unsigned T = slots_for(k);
+    unsigned slot = (unsigned)hash1(key) & (T - 1);
+    for (unsigned probe = 0; probe < T; probe++) {
+        const uint32_t p = idx[slot];
+        if (!p) return -1;
+        if (sig[p - 1] == key) return (int)(p - 1);
+        slot = (slot + 1) & (T - 1);
+    }
+    return -1;
+}
+
+// exclusive block scan of cnt (every thread calls); returns this thread's
+// offset and advances S.obase by the block total
+__device__ unsigned long long block_scan_advance(Shared& S, unsigned cnt) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned v = __shfl_up_sync(SF_FULL, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) S.wsum[wid] = incl;
+    __syncthreads();
+    const unsigned long long base = S.obase;
+    unsigned before = 0;
+    for (int i = 0; i < wid; i++) before += S.wsum[i];
+    const unsigned long long o = base + before + (incl - cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int i = 0; i < kCT / 32; i++) tot += S.wsum[i];
+        S.obase = base + tot;
+    }
+    __syncthreads();
+    return o;
+}
+
+// deterministic block sum of two doubles, result in S.p
+__device__ void block_sum2(Shared& S, double a, double b) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        a += __shfl_xor_sync(SF_FULL, a, off);
+        b += __shfl_xor_sync(SF_FULL, b, off);
+    }
+    if (lane == 0) {
+        S.red[0][wid] = a;
+        S.red[1][wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0;
+        for (int i = 0; i < kCT / 32; i++) {
+            x += S.red[0][i];
+            y += S.red[1][i];
+        }
+        S.p[0] = x;
+        S.p[1] = y;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double2 coef1(const BrTab& P, int g, uint64_t s) {
+    double2 cf = make_double2(0.0, 0.0);
+    for (int t = 0; t < P.nt[g]; t++) {
+        const double sg = (__popcll(P.v[g][t] & s) & 1) ? -1.0 : 1.0;
+        cf.x += sg * P.c[g][t].x;
+        cf.y += sg * P.c[g][t].y;
+    }
+    return cf;
+}
+
+__device__ __forceinline__ double2 cof_child1(const CofTab& C, uint64_t s, double2 a, int x, uint64_t& t) {
+    const int y = x ^ (__popcll(C.vq & s) & 1);
+    t = y ? C.tau1 : C.tau0;
+    int ip = 0;
+    uint64_t bits = s;
+    while (bits) {
+        const int h = __ffsll((long long)bits) - 1;
+        bits &= bits - 1;
+        ip += (int)((C.eps0 >> h) & 1) + 2 * (int)((C.eps1 >> h) & 1) + 2 * (__popcll(C.v[h] & t) & 1);
+        t ^= C.u[h];
+    }
+    return ipow_mul(cmul(C.kap[y], a), ip & 3);
+}
+
+// canonical-convention phase of D^sigma phi_0(M) (anchor convention), i-power
+__device__ int export_phase(const Shared& S, int n, uint64_t s) {
+    const int rx = S.rx;
+    uint64_t b = 0;
+    for (int h = rx; h < n; h++)
+        if ((s >> h) & 1) b ^= 1ull << (S.rpiv[h] - n);
+    for (int R = 0; R < rx; R++)
+        if ((b >> S.rpiv[R]) & 1) b ^= S.rmx[R];
+    uint64_t qx = 0, qz = 0;
+    int qe = 0;
+    uint64_t bits = s;
+    while (bits) {
+        const int h = __ffsll((long long)bits) - 1;
+        bits &= bits - 1;
+        pmul1(qx, qz, qe, S.rdx[h], S.rdz[h], (int)S.rde[h]);
+    }
+    const uint64_t w = b ^ qx;
+    uint64_t px = 0, pz = 0;
+    int pe = 0;
+    for (int R = 0; R < rx; R++)
+        if ((w >> S.rpiv[R]) & 1) pmul1(px, pz, pe, S.rmx[R], S.rmz[R], 0);
+    if (px != w) return -1;
+    return (qe + __popcll(qx & qz) + 2 * __popcll(qz & w) + pe + __popcll(px & pz)) & 3;
+}
+
+__global__ void __launch_bounds__(kCT) k_campaign(CampDev D) {
+    extern __shared__ uint32_t idx[];  // [slots_for(cap)]
+    __shared__ Shared S;
+    const int n = D.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* sigb[2] = {D.ws_sig + (size_t)blockIdx.x * 2 * D.cap, D.ws_sig + ((size_t)blockIdx.x * 2 + 1) * D.cap};
+    double2* ampb[2] = {D.ws_amp + (size_t)blockIdx.x * 2 * D.cap, D.ws_amp + ((size_t)blockIdx.x * 2 + 1) * D.cap};
+    Row r[2];
+    const double rs2 = 0.70710678118654752440;
+    for (;;) {
+        if (threadIdx.x == 0) S.circ = (int)atomicAdd(D.next, 1u);
+        __syncthreads();
+        const int ci = S.circ;
+        if (ci >= D.ncirc) break;
+        // |0...0>: M = Z_h, D = X_h, one element (sigma = 0, a = 1)
+        if (warp == 0) {
+            for (int hf = 0; hf < 2; hf++) {
+                const int row = lane + 32 * hf;
+                r[hf].mx = 0;
+                r[hf].mz = row < n ? 1ull << row : 0;
+                r[hf].dx = row < n ? 1ull << row : 0;
+                r[hf].dz = 0;
+                r[hf].de = 0;
+                r[hf].piv = row < n ? n + row : 0x7fffffff;
+                r[hf].A = row < n ? 1ull << row : 0;
+                r[hf].t0 = r[hf].t1 = 0;
+            }
+        }
+        if (threadIdx.x == 0) {
+            S.k = 1;
+            S.cur = 0;
+            S.rx = 0;
+            S.status = 0;
+            S.outcomes = 0;
+            S.nmeas = 0;
+            S.g = make_double2(1.0, 0.0);
+            sigb[0][0] = 0;
+            ampb[0][0] = make_double2(1.0, 0.0);
+        }
+        __syncthreads();
+        build_index(idx, sigb[0], 1);
+        const unsigned long long o0 = D.off[ci], o1 = D.off[ci + 1];
+        unsigned long long oi = o0;
+        while (oi < o1 && S.status == 0) {
+            const OpRec op0 = D.ops[oi];
+            uint32_t kind = op0.kind;
+            bool cond_false = false;
+            if (kind == SF_OP_COND) {
+                if (op0.arg > 8) {
+                    if (threadIdx.x == 0) S.status = SF_EINVAL;
+                    __syncthreads();
+                    break;
+                }
+                const uint64_t mask = (uint64_t)__double_as_longlong(op0.param);
+                cond_false = !(__popcll(S.outcomes & mask) & 1);
+                kind = op0.arg;
+            }
+            if (cond_false) {  // conditional gate not taken
+                oi++;
+                continue;
+            }
+            if (kind <= 8) {
+                // a run of consecutive Clifford gates (a conditional gate runs alone);
+                // warp 0 walks it with the next record prefetched, lane 0 publishes its end
+                if (warp == 0) {
+                    for (int hf = 0; hf < 2; hf++) {
+                        const int row = lane + 32 * hf;
+                        r[hf].A = row < n ? 1ull << row : 0;
+                        r[hf].t0 = 0;
+                    }
+                    int rx = S.rx;
+                    double2 g = S.g;
+                    int bad = 0;
+                    unsigned long long gi = oi;
+                    OpRec op = op0;
+                    const bool single = op0.kind == SF_OP_COND;
+                    for (;;) {
+                        OpRec nop = op;
+                        bool more = false;
+                        if (!single && gi + 1 < o1) {
+                            nop = D.ops[gi + 1];
+                            more = nop.kind <= 8;
+                        }
+                        gi++;
+                        const int gk = (int)(op.kind == SF_OP_COND ? op.arg : op.kind);
+                        const bool two = gk >= 6;
+                        const int q0 = (int)op.q0, q1 = two ? (int)op.q1 : 0;
+                        if (gk > 8 || q0 >= n || (two && (q1 >= n || q1 == q0))) {
+                            bad = 1;
+                            break;
+                        }
+                        int yq = -1;
+                        double2 num = make_double2(1.0, 0.0);
+                        if (gk == 0) {
+                            const int cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
+                            if (cq != 2) {
+                                const double2 cv = cq < 0 ? make_double2(0.0, 0.0) : ipow_mul(make_double2(1.0, 0.0), cq);
+                                num = make_double2((1.0 + cv.x) * rs2, cv.y * rs2);
+                            } else {
+                                yq = q0;
+                                num = make_double2(2.0 * rs2, 0.0);
+                            }
+                        } else if (gk == 3) {
+                            yq = q0;
+                        } else if (gk == 4) {
+                            yq = q0;
+                            num = make_double2(0.0, 1.0);
+                        }
+                        const int r_old = rx;
+                        for (int hf = 0; hf < 2; hf++) {
+                            const int row = lane + 32 * hf;
+                            if (row < n) {
+                                const uint32_t f = (uint32_t)conj1(gk, q0, q1, r[hf].mx, r[hf].mz);
+                                r[hf].t0 ^= f;
+                                r[hf].t1 = f;
+                                const int fd = conj1(gk, q0, q1, r[hf].dx, r[hf].dz);
+                                r[hf].de = (r[hf].de + 2u * (uint32_t)fd) & 3u;
+                            } else {
+                                r[hf].t1 = 0;
+                            }
+                        }
+                        // Pauli gates flip signs only: M keeps its bits and stays in RREF
+                        if (gk < 3 || gk > 5) rx = warp_rref(r, n, S.stage);
+                        const int dq = rx < 0 ? -1 : warp_amp_phi(r, n, rx, true, yq >= 0 ? (1ull << yq) : 0ull);
+                        if (dq < 0) {
+                            bad = 2;
+                            break;
+                        }
+                        double2 om = ipow_mul(num, (4 - dq) & 3);
+                        const int dr = rx - r_old;
+                        const double sc = dr == 0 ? 1.0 : (dr > 0 ? 1.41421356237309504880 : rs2);
+                        om.x *= sc;
+                        om.y *= sc;
+                        g = cmul(g, om);
+                        if (!more) break;
+                        op = nop;
+                    }
+                    for (int j = 0; j < n; j++) {
+                        const unsigned b0 = __ballot_sync(SF_FULL, lane < n && ((r[0].A >> j) & 1));
+                        const unsigned b1 = __ballot_sync(SF_FULL, lane + 32 < n && ((r[1].A >> j) & 1));
+                        if (lane == 0) S.at[j] = (uint64_t)b0 | ((uint64_t)b1 << 32);
+                    }
+                    const unsigned t0 = __ballot_sync(SF_FULL, lane < n && r[0].t0);
+                    const unsigned t1 = __ballot_sync(SF_FULL, lane + 32 < n && r[1].t0);
+                    if (lane == 0) {
+                        S.t = (uint64_t)t0 | ((uint64_t)t1 << 32);
+                        S.rx = rx;
+                        S.g = g;
+                        S.oe = gi;
+                        if (bad) S.status = bad == 1 ? SF_EINVAL : SF_EINTERNAL;
+                    }
+                }
+                __syncthreads();
+                if (S.status) break;
+                // sigma' = A sigma ^ t on every element, 4-bit table lookups
+                const int nc = (n + 3) >> 2;
+                for (int e = threadIdx.x; e < nc * 16; e += blockDim.x) {
+                    const int v = e & 15, c = e >> 4;
+                    uint64_t acc = 0;
+                    for (int b = 0; b < 4; b++)
+                        if (((v >> b) & 1) && 4 * c + b < n) acc ^= S.at[4 * c + b];
+                    S.tab[e] = acc;
+                }
+                __syncthreads();
+                uint64_t* sg = sigb[S.cur];
+                const uint64_t tw = S.t;
+                for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
+                    const uint64_t s = sg[j];
+                    uint64_t o = tw;
+                    for (int c = 0; c < nc; c++) o ^= S.tab[c * 16 + ((s >> (4 * c)) & 15)];
+                    sg[j] = o;
+                }
+                __syncthreads();
+                build_index(idx, sg, S.k);
+                oi = S.oe;
+                continue;
+            }
+            if (kind >= 16 && kind <= 19) {
+                // diagonal gate, merged: owner thread computes each output (Sec. IV)
+                const uint32_t gk = kind - 16;
+                const int q0 = (int)op0.q0, q1 = (int)op0.q1;
+                if (q0 >= n || (gk == 3 && (q1 >= n || q1 == q0))) {
+                    if (threadIdx.x == 0) S.status = SF_EINVAL;
+                    __syncthreads();
+                    break;
+                }
+                if (warp == 0) warp_branch_plan_regs(r, n, gk, q0, gk == 3 ? q1 : 0, op0.param, S.P);
+                __syncthreads();
+                const int ng = S.P.ng;
+                if (S.P.bad || (unsigned long long)ng * S.k > D.cap) {
+                    if (threadIdx.x == 0) S.status = S.P.bad ? SF_EINTERNAL : SF_ECAPACITY;
+                    __syncthreads();
+                    break;
+                }
+                const int ib = S.cur, ob = S.cur ^ 1;
+                const uint64_t* si = sigb[ib];
+                const double2* ai = ampb[ib];
+                const unsigned k = S.k;
+                if (threadIdx.x == 0) S.obase = 0;
+                __syncthreads();
+                for (unsigned base = 0; base < k; base += blockDim.x) {
+                    const unsigned j = base + threadIdx.x;
+                    const bool act = j < k;
+                    uint64_t s = 0;
+                    double2 a = make_double2(0.0, 0.0);
+                    int id[4] = {act ? (int)j : -1, -1, -1, -1};
+                    if (act) {
+                        s = si[j];
+                        a = ai[j];
+                        for (int g = 1; g < ng; g++) id[g] = find_index(idx, si, k, s ^ S.P.u[g]);
+                    }
+                    double2 amps[4];
+                    unsigned keepm = 0;
+                    for (int g = 0; g < ng; g++) {
+                        bool own = act;
+                        for (int g2 = 0; g2 < g; g2++) own &= id[S.P.xidx[g][g2]] < 0;
+                        double2 amp = make_double2(0.0, 0.0);
+                        if (own) {
+                            for (int g2 = 0; g2 < ng; g2++) {
+                                const int m = S.P.xidx[g][g2];
+                                if (id[m] < 0) continue;
+                                const double2 ap = m == 0 ? a : ai[id[m]];
+                                const double2 cc = cmul(coef1(S.P, g2, s ^ S.P.u[m]), ap);
+                                amp.x += cc.x;
+                                amp.y += cc.y;
+                            }
+                        }
+                        amps[g] = amp;
+                        if (own && amp.x * amp.x + amp.y * amp.y >= D.eps2) keepm |= 1u << g;
+                    }
+                    unsigned long long o = block_scan_advance(S, __popc(keepm));
+                    for (int g = 0; g < ng; g++) {
+                        if (!((keepm >> g) & 1u)) continue;
+                        sigb[ob][o] = s ^ S.P.u[g];
+                        ampb[ob][o] = amps[g];
+                        o++;
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    S.k = (unsigned)S.obase;
+                    S.cur = ob;
+                }
+                __syncthreads();
+                build_index(idx, sigb[S.cur], S.k);
+                oi++;
+                continue;
+            }
+            if (kind == SF_OP_MEASURE) {
+                const int q = (int)op0.q0;
+                if (q >= n || S.nmeas >= 64) {
+                    if (threadIdx.x == 0) S.status = SF_EINVAL;
+                    __syncthreads();
+                    break;
+                }
+                if (warp == 0) {
+                    const int rx = warp_measure_prep(r, n, S.rx, q, S.C, S.stage);
+                    if (lane == 0) S.rx = rx;
+                }
+                __syncthreads();
+                if (S.C.bad || (S.C.random && 2ull * S.k > D.cap)) {
+                    if (threadIdx.x == 0) S.status = S.C.bad ? SF_EINTERNAL : SF_ECAPACITY;
+                    __syncthreads();
+                    break;
+                }
+                if (S.C.random) {
+                    // cofactor split merged: s and s ^ uq share their two children
+                    const int ib = S.cur, ob = S.cur ^ 1;
+                    const uint64_t* si = sigb[ib];
+                    const double2* ai = ampb[ib];
+                    const unsigned k = S.k;
+                    if (threadIdx.x == 0) S.obase = 0;
+                    __syncthreads();
+                    for (unsigned base = 0; base < k; base += blockDim.x) {
+                        const unsigned j = base + threadIdx.x;
+                        const bool act = j < k;
+                        uint64_t s = 0, p = 0, t[2] = {0, 0};
+                        double2 a = make_double2(0.0, 0.0), ap = a, cc[2] = {a, a};
+                        int l = -1;
+                        bool own = false;
+                        if (act) {
+                            s = si[j];
+                            a = ai[j];
+                            p = s ^ S.C.uq;
+                            l = find_index(idx, si, k, p);
+                            own = l < 0 || s < p;
+                            if (l >= 0) ap = ai[l];
+                        }
+                        unsigned keepm = 0;
+                        for (int x = 0; x < 2; x++) {
+                            if (!own) continue;
+                            double2 c = cof_child1(S.C, s, a, x, t[x]);
+                            if (l >= 0) {
+                                uint64_t t2;
+                                const double2 c2 = cof_child1(S.C, p, ap, x, t2);
+                                c.x += c2.x;
+                                c.y += c2.y;
+                            }
+                            cc[x] = c;
+                            if (c.x * c.x + c.y * c.y >= 1e-24) keepm |= 1u << x;
+                        }
+                        unsigned long long o = block_scan_advance(S, __popc(keepm));
+                        for (int x = 0; x < 2; x++) {
+                            if (!((keepm >> x) & 1u)) continue;
+                            sigb[ob][o] = t[x];
+                            ampb[ob][o] = cc[x];
+                            o++;
+                        }
+                    }
+                    if (threadIdx.x == 0) {
+                        S.k = (unsigned)S.obase;
+                        S.cur = ob;
+                    }
+                    __syncthreads();
+                }
+                // probabilities of the two outcomes (Sec. IV), fixed summation order
+                const int rq = S.C.rq;
+                {
+                    double p0 = 0.0, p1 = 0.0;
+                    const uint64_t* sg = sigb[S.cur];
+                    const double2* am = ampb[S.cur];
+                    for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
+                        const double m = am[j].x * am[j].x + am[j].y * am[j].y;
+                        if ((sg[j] >> rq) & 1) p1 += m;
+                        else p0 += m;
+                    }
+                    block_sum2(S, p0, p1);
+                }
+                const int xo = op0.param < S.p[1] ? 1 : 0;
+                if (!(S.p[xo] > 0.0)) {
+                    if (threadIdx.x == 0) S.status = SF_ESTATE;
+                    __syncthreads();
+                    break;
+                }
+                const double scale = 1.0 / sqrt(S.p[xo]);
+                // collapse onto the outcome
+                {
+                    const int ib = S.cur, ob = S.cur ^ 1;
+                    const unsigned k = S.k;
+                    if (threadIdx.x == 0) S.obase = 0;
+                    __syncthreads();
+                    for (unsigned base = 0; base < k; base += blockDim.x) {
+                        const unsigned j = base + threadIdx.x;
+                        const bool keep = j < k && (int)((sigb[ib][j] >> rq) & 1) == xo;
+                        const unsigned long long o = block_scan_advance(S, keep ? 1u : 0u);
+                        if (keep) {
+                            sigb[ob][o] = sigb[ib][j];
+                            double2 a = ampb[ib][j];
+                            a.x *= scale;
+                            a.y *= scale;
+                            ampb[ob][o] = a;
+                        }
+                    }
+                    if (threadIdx.x == 0) {
+                        S.k = (unsigned)S.obase;
+                        S.cur = ob;
+                        if (xo) S.outcomes |= 1ull << S.nmeas;
+                        S.nmeas++;
+                    }
+                    __syncthreads();
+                }
+                build_index(idx, sigb[S.cur], S.k);
+                oi++;
+                continue;
+            }
+            if (threadIdx.x == 0) S.status = SF_EINVAL;  // unknown op
+            __syncthreads();
+        }
+        __syncthreads();
+        // results
+        double nr = 0.0;
+        for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
+            const double2 a = ampb[S.cur][j];
+            nr += a.x * a.x + a.y * a.y;
+        }
+        block_sum2(S, nr, 0.0);
+        if (threadIdx.x == 0) {
+            D.outcomes[ci] = S.outcomes;
+            D.nmeas[ci] = S.nmeas;
+            D.kfinal[ci] = S.k;
+            D.norm[ci] = S.p[0];
+            D.cstatus[ci] = S.status;
+        }
+        if (D.ex_sig) {
+            // canonical export: tableau rows and amplitudes in the anchor convention
+            if (warp == 0) {
+                for (int hf = 0; hf < 2; hf++) {
+                    const int row = lane + 32 * hf;
+                    if (row < 64) {
+                        S.rmx[row] = r[hf].mx;
+                        S.rmz[row] = r[hf].mz;
+                        S.rdx[row] = r[hf].dx;
+                        S.rdz[row] = r[hf].dz;
+                        S.rde[row] = r[hf].de;
+                        S.rpiv[row] = r[hf].piv;
+                    }
+                }
+            }
+            __syncthreads();
+            uint64_t* xt = D.ex_tab + (size_t)ci * 129;
+            for (int h = threadIdx.x; h < 64; h += blockDim.x) {
+                xt[h] = h < n ? S.rmx[h] : 0;
+                xt[64 + h] = h < n ? S.rmz[h] : 0;
+            }
+            if (threadIdx.x == 0) xt[128] = (uint64_t)S.rx;
+            const double2 g = S.g;
+            for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
+                const uint64_t s = sigb[S.cur][j];
+                const int ip = export_phase(S, n, s);
+                D.ex_sig[(size_t)ci * D.cap + j] = s;
+                D.ex_amp[(size_t)ci * D.cap + j] = ip < 0 ? make_double2(NAN, NAN)
+                                                             : ipow_mul(cmul(g, ampb[S.cur][j]), ip);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// shared-memory index for frames of up to cap elements (slots_for(cap) slots)
+size_t index_bytes(unsigned cap) {
+    size_t t = 64;
+    while (t < 2 * (size_t)cap) t <<= 1;
+    return t * sizeof(uint32_t);
+}
+
+}  // namespace
+
+struct sf_campaign_s {
+    int n = 0;
+    unsigned cap = 0;
+    int nblk = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t* ws_sig = nullptr;
+    double2* ws_amp = nullptr;
+    unsigned* next = nullptr;
+};
+
+extern "C" {
+
+sf_status sf_campaign_create(uint32_t n_qubits, uint32_t max_elems, void* cuda_stream, sf_campaign* out) {
+    if (!out) return SF_EINVAL;
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 63 || max_elems < 1 || max_elems > kCampMaxCap) return SF_EINVAL;
+    sf_campaign c = new (std::nothrow) sf_campaign_s();
+    if (!c) return SF_ENOMEM;
+    c->n = (int)n_qubits;
+    c->cap = max_elems;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, sms = 0, per_sm = 0;
+    const size_t smem = index_bytes(max_elems);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k_campaign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_campaign, kCT, smem) != cudaSuccess) {
+        delete c;
+        return SF_ECUDA;
+    }
+    c->nblk = std::max(1, sms * std::max(1, per_sm));
+    const size_t ne = (size_t)c->nblk * 2 * max_elems;
+    if (cudaMalloc(&c->ws_sig, ne * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&c->ws_amp, ne * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->next, sizeof(unsigned)) != cudaSuccess) {
+        sf_campaign_destroy(c);
+        return SF_ENOMEM;
+    }
+    *out = c;
+    return SF_OK;
+}
+
+sf_status sf_campaign_destroy(sf_campaign c) {
+    if (!c) return SF_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    if (c->ws_sig) cudaFree(c->ws_sig);
+    if (c->ws_amp) cudaFree(c->ws_amp);
+    if (c->next) cudaFree(c->next);
+    delete c;
+    return SF_OK;
+}
+
+sf_status sf_campaign_run(sf_campaign c, const sf_op* dev_ops, const uint64_t* dev_offsets, uint32_t n_circuits,
+                          double drop_eps, uint64_t* dev_outcomes, uint32_t* dev_n_meas, uint32_t* dev_k_final,
+                          double* dev_norm, int32_t* dev_status, uint64_t* dev_export_sigma,
+                          double* dev_export_amp, uint64_t* dev_export_tableau) {
+    if (!c || !dev_ops || !dev_offsets || !dev_outcomes || !dev_n_meas || !dev_k_final || !dev_norm ||
+        !dev_status || !(drop_eps >= 0.0))
+        return SF_EINVAL;
+    if ((dev_export_sigma != nullptr) != (dev_export_amp != nullptr) ||
+        (dev_export_sigma != nullptr) != (dev_export_tableau != nullptr))
+        return SF_EINVAL;
+    if (n_circuits == 0) return SF_OK;
+    CampDev D;
+    D.n = c->n;
+    D.ncirc = (int)n_circuits;
+    D.cap = c->cap;
+    D.eps2 = drop_eps * drop_eps;
+    D.ops = reinterpret_cast<const OpRec*>(dev_ops);
+    D.off = reinterpret_cast<const unsigned long long*>(dev_offsets);
+    D.ws_sig = c->ws_sig;
+    D.ws_amp = c->ws_amp;
+    D.next = c->next;
+    D.outcomes = reinterpret_cast<unsigned long long*>(dev_outcomes);
+    D.nmeas = dev_n_meas;
+    D.kfinal = dev_k_final;
+    D.norm = dev_norm;
+    D.cstatus = dev_status;
+    D.ex_sig = dev_export_sigma;
+    D.ex_amp = reinterpret_cast<double2*>(dev_export_amp);
+    D.ex_tab = dev_export_tableau;
+    if (cudaMemsetAsync(c->next, 0, sizeof(unsigned), c->stream) != cudaSuccess) return SF_ECUDA;
+    const size_t smem = index_bytes(c->cap);
+    k_campaign<<<c->nblk, kCT, smem, c->stream>>>(D);
+    return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
+uint32_t sf_campaign_ctas(sf_campaign c) { return c ? (uint32_t)c->nblk : 0u; }
+
+}  // extern "C"

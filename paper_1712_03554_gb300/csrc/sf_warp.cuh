@@ -1,0 +1,542 @@
+// sf_warp.cuh -- single-warp tableau primitives for n <= 63 (one 64-bit word
+// per row half): lane L holds tableau rows L and L + 32 in registers.  Used by
+// the single-warp Clifford kernel and by the batched campaign engine.
+#pragma once
+#include "sf_device.cuh"
+
+namespace sfw {
+
+struct Row {
+    uint64_t mx, mz, dx, dz, A;
+    uint32_t de, t0, t1;
+    int piv;
+};
+
+__device__ __forceinline__ int lam1(uint64_t x1, uint64_t z1, uint64_t x2, uint64_t z2) {
+    return (__popcll(x1 & z1) + __popcll(x2 & z2) + 2 * __popcll(z1 & x2) - __popcll((x1 ^ x2) & (z1 ^ z2))) & 3;
+}
+
+// (x, z, e) <- (x, z, e) * (x2, z2, e2)
+__device__ __forceinline__ void pmul1(uint64_t& x, uint64_t& z, int& e, uint64_t x2, uint64_t z2, int e2) {
+    const int l = lam1(x, z, x2, z2);
+    x ^= x2;
+    z ^= z2;
+    e = (e + e2 + l) & 3;
+}
+
+// product of commuting Pauli operators over the warp, result in every lane
+__device__ __forceinline__ void warp_prod(uint64_t& x, uint64_t& z, int& e) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const uint64_t ox = __shfl_xor_sync(SF_FULL, x, off);
+        const uint64_t oz = __shfl_xor_sync(SF_FULL, z, off);
+        const int oe = __shfl_xor_sync(SF_FULL, e, off);
+        pmul1(x, z, e, ox, oz, oe);
+    }
+}
+
+// Table 2 conjugation of one row held in registers; returns the sign flip
+__device__ __forceinline__ int conj1(int kind, int q0, int q1, uint64_t& x, uint64_t& z) {
+    const uint64_t m0 = 1ull << q0;
+    const int xa = (int)((x >> q0) & 1), za = (int)((z >> q0) & 1);
+    int f = 0;
+    switch (kind) {
+        case 0: f = xa & za; if (xa != za) { x ^= m0; z ^= m0; } break;
+        case 1: f = xa & za; if (xa) z ^= m0; break;
+        case 2: f = xa & (za ^ 1); if (xa) z ^= m0; break;
+        case 3: f = za; break;
+        case 4: f = xa ^ za; break;
+        case 5: f = xa; break;
+        default: {
+            const uint64_t m1 = 1ull << q1;
+            const int xb = (int)((x >> q1) & 1), zb = (int)((z >> q1) & 1);
+            if (kind == 6) {
+                f = xa & zb & (xb ^ za ^ 1);
+                if (xa) x ^= m1;
+                if (zb) z ^= m0;
+            } else if (kind == 7) {
+                f = xa & xb & (za ^ zb);
+                if (xa) z ^= m1;
+                if (xb) z ^= m0;
+            } else {
+                if (xa != xb) { x ^= m0 | m1; }
+                if (za != zb) { z ^= m0 | m1; }
+            }
+        }
+    }
+    return f;
+}
+
+// every field of row `row` (held by lane row & 31, half row >> 5) in every lane
+__device__ __forceinline__ Row fetch_row(const Row* r, int row) {
+    const int src = row & 31, half = row >> 5;
+    Row o;
+    o.mx = __shfl_sync(SF_FULL, half ? r[1].mx : r[0].mx, src);
+    o.mz = __shfl_sync(SF_FULL, half ? r[1].mz : r[0].mz, src);
+    o.dx = __shfl_sync(SF_FULL, half ? r[1].dx : r[0].dx, src);
+    o.dz = __shfl_sync(SF_FULL, half ? r[1].dz : r[0].dz, src);
+    o.A = __shfl_sync(SF_FULL, half ? r[1].A : r[0].A, src);
+    o.de = __shfl_sync(SF_FULL, half ? r[1].de : r[0].de, src);
+    o.t0 = __shfl_sync(SF_FULL, half ? r[1].t0 : r[0].t0, src);
+    o.t1 = __shfl_sync(SF_FULL, half ? r[1].t1 : r[0].t1, src);
+    o.piv = __shfl_sync(SF_FULL, half ? r[1].piv : r[0].piv, src);
+    return o;
+}
+
+__device__ __forceinline__ int colbit(const Row& a, int c, int n) {
+    return c < n ? (int)((a.mx >> c) & 1) : (int)((a.mz >> (c - n)) & 1);
+}
+
+// <y| D^tau phi_0(M)> 2^{r/2} as an i-power, -1 if zero (tau = t1 bits, or none)
+__device__ __forceinline__ int warp_amp_phi_sel(const Row* r, int n, int rx, int tau_sel, uint64_t y);
+__device__ __forceinline__ int warp_amp_phi(const Row* r, int n, int rx, bool use_tau, uint64_t y) {
+    return warp_amp_phi_sel(r, n, rx, use_tau ? 2 : 0, y);
+}
+// tau_sel: 0 none, 1 the t0 bits, 2 the t1 bits
+__device__ __forceinline__ int warp_amp_phi_sel(const Row* r, int n, int rx, int tau_sel, uint64_t y) {
+    const int lane = threadIdx.x & 31;
+    uint64_t qx = 0, qz = 0;
+    int qe = 0;
+    for (int hf = 0; hf < 2; hf++) {
+        const int row = lane + 32 * hf;
+        const uint32_t tb = tau_sel == 1 ? r[hf].t0 : (tau_sel == 2 ? r[hf].t1 : 0u);
+        if (row < n && tb) pmul1(qx, qz, qe, r[hf].dx, r[hf].dz, (int)r[hf].de);
+    }
+    warp_prod(qx, qz, qe);
+    const uint64_t w = y ^ qx;
+    uint64_t px = 0, pz = 0;
+    int pe = 0;
+    for (int hf = 0; hf < 2; hf++) {
+        const int row = lane + 32 * hf;
+        if (row < rx && ((w >> r[hf].piv) & 1)) pmul1(px, pz, pe, r[hf].mx, r[hf].mz, 0);
+    }
+    warp_prod(px, pz, pe);
+    if (px != w) return -1;
+    return (qe + __popcll(qx & qz) + 2 * __popcll(qz & w) + pe + __popcll(px & pz)) & 3;
+}
+
+// Gauss-Jordan from column `start` (rows with pivot < start keep theirs), with
+// the dual destabilizer updates and the affine-map / sign-vector tracking of
+// the block version.  Returns r.
+static __device__ int warp_gj(Row* r, int n, int start) {
+    const int lane = threadIdx.x & 31;
+    int nxt = __popc(__ballot_sync(SF_FULL, lane < n && r[0].piv < start)) +
+              __popc(__ballot_sync(SF_FULL, lane + 32 < n && r[1].piv < start));
+    for (int c = start; c < 2 * n && nxt < n; c++) {
+        const unsigned a0 = __ballot_sync(SF_FULL, lane < n && colbit(r[0], c, n));
+        const unsigned a1 = __ballot_sync(SF_FULL, lane + 32 < n && colbit(r[1], c, n));
+        const uint64_t all = (uint64_t)a0 | ((uint64_t)a1 << 32);
+        const uint64_t mask = all & (~0ull << nxt);  // candidate rows: not yet pivots
+        if (!mask) continue;
+        const int p = __ffsll((long long)mask) - 1;
+        if (p == nxt && all == (1ull << nxt)) {  // already reduced: the row keeps its pivot
+            if (lane == (nxt & 31)) r[nxt >> 5].piv = c;
+            nxt++;
+            continue;
+        }
+        if (p != nxt) {
+            const Row rp = fetch_row(r, p), rn = fetch_row(r, nxt);
+            if (lane == (p & 31)) r[p >> 5] = rn;
+            if (lane == (nxt & 31)) r[nxt >> 5] = rp;
+        }
+        const Row pv = fetch_row(r, nxt);
+        uint64_t dx = 0, dz = 0;
+        int de = 0;
+        bool any = false;
+        for (int hf = 0; hf < 2; hf++) {
+            const int row = lane + 32 * hf;
+            if (row < n && row != nxt && colbit(r[hf], c, n)) {
+                const uint32_t cb = (uint32_t)(lam1(r[hf].mx, r[hf].mz, pv.mx, pv.mz) >> 1) & 1u;
+                r[hf].mx ^= pv.mx;
+                r[hf].mz ^= pv.mz;
+                r[hf].A ^= pv.A;
+                r[hf].t0 ^= pv.t0 ^ cb;
+                r[hf].t1 ^= pv.t1 ^ cb;
+                pmul1(dx, dz, de, r[hf].dx, r[hf].dz, (int)r[hf].de);
+                any = true;
+            }
+        }
+        if (__any_sync(SF_FULL, any)) {
+            warp_prod(dx, dz, de);
+            if (lane == (nxt & 31)) {
+                Row& t = r[nxt >> 5];
+                uint64_t x = t.dx, z = t.dz;
+                int e = (int)t.de;
+                pmul1(x, z, e, dx, dz, de);
+                t.dx = x;
+                t.dz = z;
+                t.de = (uint32_t)e;
+            }
+        }
+        if (lane == (nxt & 31)) r[nxt >> 5].piv = c;
+        nxt++;
+    }
+    return __popc(__ballot_sync(SF_FULL, lane < n && r[0].piv < n)) +
+           __popc(__ballot_sync(SF_FULL, lane + 32 < n && r[1].piv < n));
+}
+
+
+// ---- Invariant 1 repair without row movement --------------------------------
+// The same row reduction with the rows left in place while pivots are chosen:
+// every unassigned row whose leading column holds no other 1 in the whole
+// tableau becomes that column's pivot at once (Gauss-Jordan would reach it
+// with nothing to eliminate, whatever the order), and only columns that hold
+// several 1s take an elimination step (pivot = lowest-index unassigned row
+// leading there; every other row with that bit gets M_h <- M_h M_p, the dual
+// D_p <- D_p D_h, and the affine / sign tracking).  A final permutation sorts
+// the rows by pivot.  The canonical M is the unique RREF of the row space;
+// the destabilizers may differ from a reduction that swaps rows, which
+// changes the internal labels but not the state any element stands for.
+// `stage` is 64 rows of shared memory owned by the calling warp.  Returns r,
+// or -1 if a row has no bits left (dependent rows: a broken tableau).
+__device__ __forceinline__ int lead_col(uint64_t mx, uint64_t mz, int n) {
+    if (mx) return __ffsll((long long)mx) - 1;
+    if (mz) return n + __ffsll((long long)mz) - 1;
+    return 0x7fffffff;
+}
+
+__device__ __forceinline__ uint64_t warp_or64(uint64_t v) {
+    const unsigned lo = __reduce_or_sync(SF_FULL, (unsigned)v);
+    const unsigned hi = __reduce_or_sync(SF_FULL, (unsigned)(v >> 32));
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+// column c as a bit of the (x part, z part) pair
+__device__ __forceinline__ void col_bit(int c, int n, uint64_t& bx, uint64_t& bz) {
+    bx = c < n ? 1ull << c : 0ull;
+    bz = (c >= n && c < 2 * n) ? 1ull << (c - n) : 0ull;
+}
+
+__device__ __forceinline__ bool col_in(int c, int n, uint64_t sx, uint64_t sz) {
+    return c < n ? ((sx >> c) & 1) : ((sz >> (c - n)) & 1);
+}
+
+__device__ __forceinline__ void elim_row(Row& a, const Row& pv, int c, int n, uint64_t& dx, uint64_t& dz, int& de,
+                                         bool& any) {
+    if (!col_in(c, n, a.mx, a.mz)) return;
+    const uint32_t cb = (uint32_t)(lam1(a.mx, a.mz, pv.mx, pv.mz) >> 1) & 1u;
+    a.mx ^= pv.mx;
+    a.mz ^= pv.mz;
+    a.A ^= pv.A;
+    a.t0 ^= pv.t0 ^ cb;
+    a.t1 ^= pv.t1 ^ cb;
+    pmul1(dx, dz, de, a.dx, a.dz, (int)a.de);
+    any = true;
+}
+
+__device__ __forceinline__ void take_pivot(Row& t, int c, bool with_d, uint64_t dx, uint64_t dz, int de) {
+    if (with_d) {
+        uint64_t x = t.dx, z = t.dz;
+        int e = (int)t.de;
+        pmul1(x, z, e, dx, dz, de);
+        t.dx = x;
+        t.dz = z;
+        t.de = (uint32_t)e;
+    }
+    t.piv = c;
+}
+
+__device__ __forceinline__ int warp_rref(Row* r, int n, Row* stage) {
+    const int lane = threadIdx.x & 31;
+    constexpr int INF = 0x7fffffff;
+    const bool v0 = lane < n, v1 = lane + 32 < n;
+    bool asg0 = false, asg1 = false;
+    for (int it = 0; it < 64; it++) {
+        const int l0 = v0 ? (asg0 ? r[0].piv : lead_col(r[0].mx, r[0].mz, n)) : INF;
+        const int l1 = v1 ? (asg1 ? r[1].piv : lead_col(r[1].mx, r[1].mz, n)) : INF;
+        // bits other than each row's lead, and the leads of each half
+        uint64_t b0x, b0z, b1x, b1z;
+        col_bit(l0, n, b0x, b0z);
+        col_bit(l1, n, b1x, b1z);
+        const uint64_t nx = (v0 ? r[0].mx & ~b0x : 0ull) | (v1 ? r[1].mx & ~b1x : 0ull);
+        const uint64_t nz = (v0 ? r[0].mz & ~b0z : 0ull) | (v1 ? r[1].mz & ~b1z : 0ull);
+        const uint64_t dirty_x = warp_or64(nx), dirty_z = warp_or64(nz);
+        const uint64_t cross_x = warp_or64(b0x) & warp_or64(b1x);
+        const uint64_t cross_z = warp_or64(b0z) & warp_or64(b1z);
+        const unsigned m0 = __match_any_sync(SF_FULL, l0), m1 = __match_any_sync(SF_FULL, l1);
+        const bool c0 = v0 && !asg0 && l0 != INF && __popc(m0) == 1 &&
+                        !col_in(l0, n, dirty_x | cross_x, dirty_z | cross_z);
+        const bool c1 = v1 && !asg1 && l1 != INF && __popc(m1) == 1 &&
+                        !col_in(l1, n, dirty_x | cross_x, dirty_z | cross_z);
+        if (c0) { asg0 = true; r[0].piv = l0; }
+        if (c1) { asg1 = true; r[1].piv = l1; }
+        const int u0 = (v0 && !asg0) ? l0 : INF, u1 = (v1 && !asg1) ? l1 : INF;
+        const int c = __reduce_min_sync(SF_FULL, min(u0, u1));
+        if (c == INF) break;
+        // one elimination step at column c
+        const uint64_t cand = (uint64_t)__ballot_sync(SF_FULL, u0 == c) | ((uint64_t)__ballot_sync(SF_FULL, u1 == c) << 32);
+        const int p = __ffsll((long long)cand) - 1;
+        const Row pv = fetch_row(r, p);
+        uint64_t dx = 0, dz = 0;
+        int de = 0;
+        bool any = false;
+        if (v0 && lane != p) elim_row(r[0], pv, c, n, dx, dz, de, any);
+        if (v1 && lane + 32 != p) elim_row(r[1], pv, c, n, dx, dz, de, any);
+        const bool with_d = __any_sync(SF_FULL, any);
+        if (with_d) warp_prod(dx, dz, de);
+        if (lane == (p & 31)) {
+            if (p < 32) { take_pivot(r[0], c, with_d, dx, dz, de); asg0 = true; }
+            else { take_pivot(r[1], c, with_d, dx, dz, de); asg1 = true; }
+        }
+    }
+    if (__any_sync(SF_FULL, (v0 && !asg0) || (v1 && !asg1))) return -1;
+    // sort by pivot: rank = number of pivots in smaller columns
+    uint64_t p0x, p0z, p1x, p1z;
+    col_bit(v0 ? r[0].piv : INF, n, p0x, p0z);
+    col_bit(v1 ? r[1].piv : INF, n, p1x, p1z);
+    const uint64_t PX = warp_or64(p0x | p1x), PZ = warp_or64(p0z | p1z);
+    const int rx = __popcll(PX);
+    auto rank = [&](int pc) {
+        return pc < n ? __popcll(PX & ((1ull << pc) - 1)) : rx + __popcll(PZ & ((1ull << (pc - n)) - 1));
+    };
+    const int k0 = v0 ? rank(r[0].piv) : lane, k1 = v1 ? rank(r[1].piv) : lane + 32;
+    if (__any_sync(SF_FULL, k0 != lane || k1 != lane + 32)) {
+        if (v0) stage[k0] = r[0];
+        if (v1) stage[k1] = r[1];
+        __syncwarp();
+        if (v0) r[0] = stage[lane];
+        if (v1) r[1] = stage[lane + 32];
+        __syncwarp();
+    }
+    return rx;
+}
+
+// ---- cofactor planning (COFACTOR, Sec. III) with the rows in registers -------
+// The same construction as the block kernel k_measure_prep: if q is random,
+// rows anticommuting with Z_q are multiplied by the first such row i (dual
+// D_i <- D_i D_h), destabilizers anticommuting with Z_q take a factor M_i,
+// D_i <- M_i, M_i <- Z_q, Gauss-Jordan; then kappa_y, tau_y and, for every old
+// destabilizer, D_h = eps_h D'^{u'_h} M'^{v'_h}.
+struct CofTab {
+    uint64_t u[64], v[64];
+    uint64_t eps0, eps1, tau0, tau1, vq, uq;
+    double2 kap[2];
+    int rq, random, bad;
+};
+
+__device__ __forceinline__ int symp1(uint64_t ax, uint64_t az, uint64_t bx, uint64_t bz) {
+    return (__popcll(ax & bz) + __popcll(az & bx)) & 1;
+}
+
+// lane 0 writes C; returns the new X-block size
+__device__ __forceinline__ int warp_measure_prep(Row* r, int n, int rx, int q, CofTab& C, Row* stage) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t qm = 1ull << q;
+    bool uh[2];
+    for (int hf = 0; hf < 2; hf++) uh[hf] = (lane + 32 * hf < n) && (r[hf].mx & qm);
+    const uint64_t umask = (uint64_t)__ballot_sync(SF_FULL, uh[0]) | ((uint64_t)__ballot_sync(SF_FULL, uh[1]) << 32);
+    if (!umask) {
+        // deterministic: Z_q is a canonical Z-block row
+        int rq = -1;
+        for (int hf = 0; hf < 2; hf++) {
+            const int row = lane + 32 * hf;
+            if (row < n && row >= rx && r[hf].piv == n + q && r[hf].mx == 0 && r[hf].mz == qm) rq = row;
+        }
+        for (int off = 16; off; off >>= 1) rq = max(rq, __shfl_xor_sync(SF_FULL, rq, off));
+        if (lane == 0) { C.random = 0; C.rq = rq; C.bad = rq < 0; }
+        return rx;
+    }
+    const int i = __ffsll((long long)umask) - 1;
+    const Row ri = fetch_row(r, i);
+    const int num1 = __popcll(ri.mx & ri.mz) & 3;
+    const uint64_t w1 = ri.mx;
+    const uint64_t vq = (uint64_t)__ballot_sync(SF_FULL, lane < n && (r[0].dx & qm)) |
+                        ((uint64_t)__ballot_sync(SF_FULL, lane + 32 < n && (r[1].dx & qm)) << 32);
+    uint64_t d0x[2], d0z[2];
+    uint32_t d0e[2];
+    for (int hf = 0; hf < 2; hf++) {
+        d0x[hf] = r[hf].dx;
+        d0z[hf] = r[hf].dz;
+        d0e[hf] = r[hf].de;
+        r[hf].t0 = 0;
+        r[hf].t1 = 0;
+    }
+    // rows anticommuting with Z_q (other than i) <- row * M_i; dual on D_i
+    uint64_t px = 0, pz = 0;
+    int pe = 0;
+    bool any = false;
+    for (int hf = 0; hf < 2; hf++) {
+        const int row = lane + 32 * hf;
+        if (uh[hf] && row != i) {
+            const uint32_t cb = (uint32_t)(lam1(r[hf].mx, r[hf].mz, ri.mx, ri.mz) >> 1) & 1u;
+            r[hf].mx ^= ri.mx;
+            r[hf].mz ^= ri.mz;
+            r[hf].t0 = cb;
+            r[hf].t1 = cb;
+            pmul1(px, pz, pe, r[hf].dx, r[hf].dz, (int)r[hf].de);
+            any = true;
+        }
+    }
+    if (__any_sync(SF_FULL, any)) {
+        warp_prod(px, pz, pe);
+        if (lane == (i & 31)) {
+            if (i < 32) take_pivot(r[0], r[0].piv, true, px, pz, pe);
+            else take_pivot(r[1], r[1].piv, true, px, pz, pe);
+        }
+    }
+    // destabilizers anticommuting with Z_q take a factor M_i (commutes with them)
+    for (int hf = 0; hf < 2; hf++) {
+        const int row = lane + 32 * hf;
+        if (row < n && row != i && (r[hf].dx & qm)) {
+            uint64_t x = r[hf].dx, z = r[hf].dz;
+            int e = (int)r[hf].de;
+            pmul1(x, z, e, ri.mx, ri.mz, 0);
+            r[hf].dx = x;
+            r[hf].dz = z;
+            r[hf].de = (uint32_t)e;
+        }
+    }
+#pragma unroll
+    for (int hf = 0; hf < 2; hf++) {
+        if (lane + 32 * hf == i) {
+            r[hf].dx = ri.mx;
+            r[hf].dz = ri.mz;
+            r[hf].de = 0;
+            r[hf].mx = 0;
+            r[hf].mz = qm;
+            r[hf].t0 = 0;
+            r[hf].t1 = 1;
+        }
+        r[hf].piv = 0x7fffffff;
+    }
+    const int rx2 = warp_rref(r, n, stage);
+    const int den0 = warp_amp_phi_sel(r, n, rx2, 1, 0ull);
+    const int den1 = warp_amp_phi_sel(r, n, rx2, 2, w1);
+    const uint64_t tau0 = (uint64_t)__ballot_sync(SF_FULL, lane < n && r[0].t0) |
+                          ((uint64_t)__ballot_sync(SF_FULL, lane + 32 < n && r[1].t0) << 32);
+    const uint64_t tau1 = (uint64_t)__ballot_sync(SF_FULL, lane < n && r[0].t1) |
+                          ((uint64_t)__ballot_sync(SF_FULL, lane + 32 < n && r[1].t1) << 32);
+    const double sc = rx2 == rx ? 1.0 : (rx2 > rx ? 1.41421356237309504880 : 0.70710678118654752440);
+    // tables of the old destabilizers in the new basis
+    uint64_t eps0 = 0, eps1 = 0;
+    int bad = (den0 < 0 || den1 < 0 || rx2 < 0) ? 1 : 0;
+    for (int hh = 0; hh < n; hh++) {
+        const int src = hh & 31, half = hh >> 5;
+        const uint64_t ox = __shfl_sync(SF_FULL, half ? d0x[1] : d0x[0], src);
+        const uint64_t oz = __shfl_sync(SF_FULL, half ? d0z[1] : d0z[0], src);
+        const int oe = (int)__shfl_sync(SF_FULL, half ? d0e[1] : d0e[0], src);
+        bool ub[2], vb[2];
+        uint64_t cx = 0, cz = 0;
+        int ce = 0;
+        for (int hf = 0; hf < 2; hf++) {
+            const int row = lane + 32 * hf;
+            ub[hf] = row < n && symp1(ox, oz, r[hf].mx, r[hf].mz);
+            vb[hf] = row < n && symp1(ox, oz, r[hf].dx, r[hf].dz);
+            if (ub[hf]) pmul1(cx, cz, ce, r[hf].dx, r[hf].dz, (int)r[hf].de);
+            if (vb[hf]) pmul1(cx, cz, ce, r[hf].mx, r[hf].mz, 0);
+        }
+        const uint64_t um = (uint64_t)__ballot_sync(SF_FULL, ub[0]) | ((uint64_t)__ballot_sync(SF_FULL, ub[1]) << 32);
+        const uint64_t vm = (uint64_t)__ballot_sync(SF_FULL, vb[0]) | ((uint64_t)__ballot_sync(SF_FULL, vb[1]) << 32);
+        warp_prod(cx, cz, ce);
+        if (cx != ox || cz != oz) bad = 1;
+        const int epsq = (oe - ce + 4) & 3;
+        if (epsq & 1) eps0 |= 1ull << hh;
+        if (epsq & 2) eps1 |= 1ull << hh;
+        if (lane == 0) {
+            C.u[hh] = um;
+            C.v[hh] = vm;
+        }
+    }
+    int rq = -1;
+    for (int hf = 0; hf < 2; hf++) {
+        const int row = lane + 32 * hf;
+        if (row < n && row >= rx2 && r[hf].piv == n + q) rq = row;
+    }
+    for (int off = 16; off; off >>= 1) rq = max(rq, __shfl_xor_sync(SF_FULL, rq, off));
+    if (lane == 0) {
+        C.random = 1;
+        C.rq = rq;
+        C.bad = bad | (rq < 0);
+        C.eps0 = eps0;
+        C.eps1 = eps1;
+        C.tau0 = tau0;
+        C.tau1 = tau1;
+        C.vq = vq;
+        C.uq = umask;
+        C.kap[0] = ipow_mul(make_double2(sc, 0.0), (4 - den0) & 3);
+        C.kap[1] = ipow_mul(make_double2(sc, 0.0), (num1 + 4 - den1) & 3);
+    }
+    return rx2;
+}
+
+// ---- plan of a diagonal gate (Sec. IV) with the rows in registers ---------------
+// Terms c_j Z^{w_j}; Z^w = eps D^u M^v; terms grouped by u (group 0: u = 0).
+struct BrTab {
+    int ng, bad;
+    int nt[4];
+    uint64_t u[4];
+    uint64_t v[4][4];
+    double2 c[4][4];
+    int xidx[4][4];
+};
+
+__device__ __forceinline__ void warp_branch_plan_regs(const Row* r, int n, uint32_t kind, int q0, int q1, double theta,
+                                             BrTab& P) {
+    const int lane = threadIdx.x & 31;
+    double th = theta;
+    if (kind == 0) th = 0.78539816339744830962;
+    if (kind == 1) th = -0.78539816339744830962;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    int nt;
+    uint64_t wz[4];
+    double2 cf[4];
+    if (kind <= 2) {
+        nt = 2;
+        wz[0] = 0; cf[0] = make_double2((1.0 + cs) * 0.5, sn * 0.5);
+        wz[1] = 1ull << q0; cf[1] = make_double2((1.0 - cs) * 0.5, -sn * 0.5);
+    } else {
+        nt = 4;
+        const double2 dd = make_double2((cs - 1.0) * 0.25, sn * 0.25);
+        wz[0] = 0; cf[0] = make_double2(1.0 + dd.x, dd.y);
+        wz[1] = 1ull << q0; cf[1] = make_double2(-dd.x, -dd.y);
+        wz[2] = 1ull << q1; cf[2] = make_double2(-dd.x, -dd.y);
+        wz[3] = (1ull << q0) | (1ull << q1); cf[3] = dd;
+    }
+    uint64_t um[4], vm[4];
+    int epsq[4], bad = 0;
+    for (int j = 0; j < nt; j++) {
+        uint64_t cx = 0, cz = 0;
+        int ce = 0;
+        bool ub[2], vb[2];
+        for (int hf = 0; hf < 2; hf++) {
+            const int row = lane + 32 * hf;
+            ub[hf] = row < n && (__popcll(r[hf].mx & wz[j]) & 1);
+            vb[hf] = row < n && (__popcll(r[hf].dx & wz[j]) & 1);
+            if (ub[hf]) pmul1(cx, cz, ce, r[hf].dx, r[hf].dz, (int)r[hf].de);
+            if (vb[hf]) pmul1(cx, cz, ce, r[hf].mx, r[hf].mz, 0);
+        }
+        um[j] = (uint64_t)__ballot_sync(SF_FULL, ub[0]) | ((uint64_t)__ballot_sync(SF_FULL, ub[1]) << 32);
+        vm[j] = (uint64_t)__ballot_sync(SF_FULL, vb[0]) | ((uint64_t)__ballot_sync(SF_FULL, vb[1]) << 32);
+        warp_prod(cx, cz, ce);
+        if (cx != 0 || cz != wz[j]) bad = 1;
+        epsq[j] = (4 - ce) & 3;
+    }
+    if (lane != 0) return;
+    int gid[4], ng = 0;
+    for (int j = 0; j < nt; j++) {
+        int found = -1;
+        for (int j2 = 0; j2 < j; j2++)
+            if (um[j2] == um[j]) { found = gid[j2]; break; }
+        gid[j] = found >= 0 ? found : ng++;
+    }
+    P.ng = ng;
+    for (int g = 0; g < ng; g++) P.nt[g] = 0;
+    for (int j = 0; j < nt; j++) {
+        const int g = gid[j], t = P.nt[g]++;
+        P.u[g] = um[j];
+        P.v[g][t] = vm[j];
+        P.c[g][t] = ipow_mul(cf[j], epsq[j]);
+    }
+    for (int g = 0; g < ng; g++)
+        for (int g2 = 0; g2 < ng; g2++) {
+            int m = -1;
+            for (int g3 = 0; g3 < ng; g3++)
+                if ((P.u[g] ^ P.u[g2]) == P.u[g3]) { m = g3; break; }
+            if (m < 0) bad = 1;
+            P.xidx[g][g2] = m < 0 ? 0 : m;
+        }
+    if (P.u[0] != 0) bad = 1;
+    P.bad = bad;
+}
+}  // namespace sfw

@@ -75,6 +75,10 @@ def load(build: bool = True) -> C.CDLL:
         "sf_last_error": ([H], C.c_char_p),
         "sf_coalesce_noalloc": ([C.c_void_p, C.c_void_p, u64, u32, dbl, C.c_void_p, C.c_void_p, P64, C.c_void_p],
                                 st),
+        "sf_campaign_create": ([u32, u32, C.c_void_p, C.POINTER(C.c_void_p)], st),
+        "sf_campaign_destroy": ([H], st),
+        "sf_campaign_run": ([H, C.c_void_p, C.c_void_p, u32, dbl] + [C.c_void_p] * 8, st),
+        "sf_campaign_ctas": ([H], u32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -98,6 +102,133 @@ def coalesce_noalloc(sigma_in: int, amp_in: int, k_in: int, n_words: int, drop_e
     if code != SF_OK:
         raise SFError(code, "sf_coalesce_noalloc failed")
     return int(k.value)
+
+
+CAMPAIGN_MAX_ELEMS = 16384
+OP_DIAG, OP_MEASURE, OP_COND = 16, 32, 33
+SF_OP_DTYPE = np.dtype([("kind", "<u4"), ("q0", "<u4"), ("q1", "<u4"), ("arg", "<u4"), ("param", "<f8")])
+
+
+def encode_program(circuits) -> Tuple[np.ndarray, np.ndarray]:
+    """sf_op records and offsets for a list of circuits in the op vocabulary of
+    circuits.py: ("C", kind, q0, q1) Clifford gate; ("N", kind, q0, q1, theta)
+    diagonal gate (the campaign engine always merges, so a following ("K",) is
+    implied and skipped); ("M", q, u) measurement with draw u; ("Q", kind, q0,
+    q1, mask) Clifford gate applied iff parity(outcomes & mask) = 1."""
+    recs, offs = [], [0]
+    for ops in circuits:
+        for op in ops:
+            t = op[0]
+            if t == "C":
+                recs.append((op[1], op[2], op[3], 0, 0.0))
+            elif t == "N":
+                recs.append((OP_DIAG + op[1], op[2], op[3], 0, float(op[4])))
+            elif t == "K":
+                continue
+            elif t == "M":
+                if op[2] is None:
+                    raise ValueError("a campaign measurement needs a draw u")
+                recs.append((OP_MEASURE, op[1], 0, 0, float(op[2])))
+            elif t == "Q":
+                mask = np.array([op[4]], dtype=np.uint64).view(np.float64)[0]
+                recs.append((OP_COND, op[2], op[3], op[1], mask))
+            else:
+                raise ValueError(f"unknown op {op!r}")
+        offs.append(len(recs))
+    return np.array(recs, dtype=SF_OP_DTYPE), np.array(offs, dtype=np.uint64)
+
+
+class Campaign:
+    """Batched engine: many circuits of n <= 63 qubits in one persistent
+    launch (sf_campaign_* in include/sf.h).  Device buffers come from torch."""
+
+    def __init__(self, n: int, max_elems: int, stream=None):
+        self.lib = load()
+        self.n, self.cap = int(n), int(max_elems)
+        self._stream = stream
+        sh = int(stream.cuda_stream) if stream is not None else _current_stream_handle()
+        self._sh = sh
+        h = C.c_void_p()
+        code = self.lib.sf_campaign_create(self.n, self.cap, C.c_void_p(sh), C.byref(h))
+        if code != SF_OK:
+            raise SFError(code, "sf_campaign_create failed")
+        self.h = h
+
+    def ctas(self) -> int:
+        return int(self.lib.sf_campaign_ctas(self.h))
+
+    def upload(self, circuits):
+        """Encode and copy a program to the device: (ops, offsets, n_circuits)."""
+        import torch
+        recs, offs = encode_program(circuits)
+        if len(recs) == 0:  # the ABI wants a valid ops pointer even when every circuit is empty
+            recs = np.zeros(1, dtype=SF_OP_DTYPE)
+        ops = torch.from_numpy(recs.view(np.uint8).copy()).to("cuda")
+        off = torch.from_numpy(offs.view(np.int64).copy()).to("cuda")
+        return ops, off, len(offs) - 1
+
+    def outputs(self, nc: int, export: bool = False):
+        import torch
+        dev = "cuda"
+        out = {"outcomes": torch.zeros(nc, dtype=torch.int64, device=dev),
+               "n_meas": torch.zeros(nc, dtype=torch.int32, device=dev),
+               "k_final": torch.zeros(nc, dtype=torch.int32, device=dev),
+               "norm": torch.zeros(nc, dtype=torch.float64, device=dev),
+               "status": torch.zeros(nc, dtype=torch.int32, device=dev)}
+        if export:
+            out["sigma"] = torch.zeros(nc * self.cap, dtype=torch.int64, device=dev)
+            out["amp"] = torch.zeros(nc * self.cap * 2, dtype=torch.float64, device=dev)
+            out["tableau"] = torch.zeros(nc * 129, dtype=torch.int64, device=dev)
+        return out
+
+    def launch(self, ops, off, nc: int, drop_eps: float, out) -> None:
+        """Asynchronous sf_campaign_run on uploaded buffers (see upload/outputs)."""
+        ex = [out[k].data_ptr() if k in out else None for k in ("sigma", "amp", "tableau")]
+        code = self.lib.sf_campaign_run(self.h, C.c_void_p(ops.data_ptr()), C.c_void_p(off.data_ptr()), nc,
+                                        float(drop_eps), C.c_void_p(out["outcomes"].data_ptr()),
+                                        C.c_void_p(out["n_meas"].data_ptr()), C.c_void_p(out["k_final"].data_ptr()),
+                                        C.c_void_p(out["norm"].data_ptr()), C.c_void_p(out["status"].data_ptr()),
+                                        *[C.c_void_p(p) for p in ex])
+        if code != SF_OK:
+            raise SFError(code, "sf_campaign_run failed")
+
+    def run(self, circuits, drop_eps: float = 1e-12, export: bool = False):
+        """Run a list of circuits; returns numpy results per circuit and, with
+        export, each final frame as (x rows, z rows, r, sigma, amp) with the
+        elements sorted by phase vector."""
+        import torch
+        ops, off, nc = self.upload(circuits)
+        out = self.outputs(nc, export)
+        self.launch(ops, off, nc, drop_eps, out)
+        if self._stream is not None:
+            self._stream.synchronize()
+        else:
+            torch.cuda.synchronize()
+        res = {k: out[k].cpu().numpy() for k in ("outcomes", "n_meas", "k_final", "norm", "status")}
+        res["outcomes"] = res["outcomes"].view(np.uint64)
+        if export:
+            sig = out["sigma"].cpu().numpy().view(np.uint64).reshape(nc, self.cap)
+            amp = out["amp"].cpu().numpy().reshape(nc, self.cap, 2)
+            tab = out["tableau"].cpu().numpy().view(np.uint64).reshape(nc, 129)
+            frames = []
+            for c in range(nc):
+                k = int(res["k_final"][c])
+                order = np.argsort(sig[c, :k], kind="stable")
+                frames.append((tab[c, :self.n].copy(), tab[c, 64:64 + self.n].copy(), int(tab[c, 128]),
+                               sig[c, :k][order].copy(), amp[c, :k, 0][order] + 1j * amp[c, :k, 1][order]))
+            res["frames"] = frames
+        return res
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sf_campaign_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _current_stream_handle() -> int:

@@ -1,0 +1,184 @@
+"""Parity of the batched campaign engine (sf_campaign_*, one persistent launch
+for many circuits) with the CPU oracle, with the one-circuit GPU path, and
+with itself when a circuit runs alone instead of in a batch.
+
+Tableau and phase vectors bit for bit; amplitudes within 1e-10 (global phase
+included); measurement outcomes exactly (both sides decide u < p(1) in FP64)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_03554_gb300 import circuits as c
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def sfm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1712_03554_gb300 import sf
+    sf.load()
+    return sf
+
+
+def oracle_run(n, ops):
+    o = oracle.FrameOracle(n)
+    res = c.run(o, ops)
+    bits = 0
+    for m, r in enumerate(res):
+        bits |= r[3] << m
+    return o, bits, len(res)
+
+
+def check_against_oracle(res, i, n, ops):
+    o, bits, nm = oracle_run(n, ops)
+    assert res["status"][i] == 0, (i, res["status"][i])
+    assert int(res["outcomes"][i]) == bits, (i, bin(int(res["outcomes"][i])), bin(bits))
+    assert res["n_meas"][i] == nm
+    x, z, r, sig, amp = res["frames"][i]
+    ox, oz, orr = o.tableau()
+    assert r == orr
+    assert np.array_equal(x, ox[:, 0]) and np.array_equal(z, oz[:, 0]), "tableau differs"
+    os_, oa = o.frame()
+    assert res["k_final"][i] == len(os_)
+    assert np.array_equal(sig, os_[:, 0]), "phase vectors differ"
+    if len(oa):
+        assert np.max(np.abs(amp - oa)) <= TOL
+    assert abs(res["norm"][i] - np.sum(np.abs(oa) ** 2)) <= TOL
+
+
+def test_steane_variants_vs_oracle(sfm):
+    circuits = c.steane_campaign(48, seed=1)
+    eng = sfm.Campaign(c.STEANE_N, 8192)
+    res = eng.run(circuits, export=True)
+    for i, ops in enumerate(circuits):
+        check_against_oracle(res, i, c.STEANE_N, ops)
+    eng.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 8, 31, 32, 33, 63])
+def test_random_clifford_t_vs_oracle(sfm, n):
+    """All nine Clifford kinds, T/T-dagger/PHASE on one qubit and CPHASE on
+    pairs, measurements with draws and conditional gates, across word-boundary
+    qubit counts."""
+    g = c.rng_for(1000 + n)
+    circuits = []
+    for v in range(6):
+        ops = c.random_clifford(n, 150, seed=97 * n + v, kinds=tuple(range(9)) if n >= 2 else (0, 1, 2, 3, 4, 5))
+        out = []
+        n_meas = 0
+        for op in ops:
+            out.append(op)
+            r = g.random()
+            if r < 0.03:
+                out += [("N", int(g.integers(3)), int(g.integers(n)), 0, float(g.uniform(-3, 3))), ("K",)]
+            elif r < 0.045 and n >= 2:
+                a, b = (int(x) for x in g.choice(n, size=2, replace=False))
+                out += [("N", c.CPHASE, a, b, float(g.uniform(-3, 3))), ("K",)]
+            elif r < 0.10:
+                out.append(("M", int(g.integers(n)), float(g.random())))
+                n_meas += 1
+            elif r < 0.12 and n_meas:
+                out.append(("Q", int(g.integers(6)), int(g.integers(n)), 0, int(g.integers(1, 1 << n_meas))))
+        circuits.append(out)
+    eng = sfm.Campaign(n, sfm.CAMPAIGN_MAX_ELEMS)
+    res = eng.run(circuits, export=True)
+    for i, ops in enumerate(circuits):
+        check_against_oracle(res, i, n, ops)
+    eng.close()
+
+
+def test_qft_vs_oracle(sfm):
+    """QFT on 10 qubits from random basis states: frames grow to hundreds of
+    elements through merged controlled phases."""
+    circuits = []
+    for s in range(4):
+        x, ops = c.qft_random_input(10, seed=s)
+        circuits.append(ops)
+    eng = sfm.Campaign(10, 4096)
+    res = eng.run(circuits, export=True)
+    for i, ops in enumerate(circuits):
+        check_against_oracle(res, i, 10, ops)
+    assert max(res["k_final"]) >= 256
+    eng.close()
+
+
+def test_alone_equals_batched(sfm):
+    """A circuit's results do not depend on what runs beside it: bit-identical
+    outputs and exported frames alone and inside a batch of 256."""
+    circuits = c.steane_campaign(256, seed=2)
+    eng = sfm.Campaign(c.STEANE_N, 8192)
+    full = eng.run(circuits, export=True)
+    for i in (0, 17, 255):
+        one = eng.run([circuits[i]], export=True)
+        for key in ("outcomes", "n_meas", "k_final", "norm", "status"):
+            assert one[key][0] == full[key][i], key
+        for a, b in zip(one["frames"][0], full["frames"][i]):
+            assert np.array_equal(np.asarray(a), np.asarray(b))
+    eng.close()
+
+
+def test_campaign_vs_single_circuit_path(sfm):
+    """The campaign and the one-circuit library path (sf_create ... per
+    circuit) give the same outcomes and frames."""
+    circuits = c.steane_campaign(6, seed=3)
+    eng = sfm.Campaign(c.STEANE_N, 8192)
+    res = eng.run(circuits, export=True)
+    for i, ops in enumerate(circuits):
+        f = sfm.Frame(c.STEANE_N, 1 << 14)
+        rr = c.run(f, ops)
+        bits = sum(r[3] << m for m, r in enumerate(rr))
+        assert int(res["outcomes"][i]) == bits
+        gx, gz, gr = f.tableau()
+        x, z, r, sig, amp = res["frames"][i]
+        assert gr == r and np.array_equal(gx[:, 0], x) and np.array_equal(gz[:, 0], z)
+        gs, ga = f.frame()
+        assert np.array_equal(gs[:, 0], sig)
+        assert np.max(np.abs(ga - amp)) <= TOL
+        f.close()
+    eng.close()
+
+
+def test_statuses_and_edge_cases(sfm):
+    """Per-circuit errors stop that circuit only; an empty circuit is |0..0>."""
+    n = 6
+    plus3 = [("C", c.H, q, 0) for q in range(3)] + [x for q in range(3) for x in (("N", c.T, q, 0, 0.0), ("K",))]
+    circuits = [
+        [],                                          # empty: one element, norm 1
+        [("C", c.H, 0, 0), ("C", c.CNOT, 0, 9)],     # qubit out of range
+        plus3,                                       # 8 elements > max_elems 4
+        [("C", c.H, 0, 0), ("C", c.CNOT, 0, 0)],     # q0 == q1
+        [("C", c.X, 0, 0), ("M", 0, 0.5), ("M", 0, 0.5)],
+        [("C", c.H, 1, 0), ("N", c.T, 1, 0, 0.0), ("K",)],
+    ]
+    eng = sfm.Campaign(n, 4)
+    res = eng.run(circuits, export=True)
+    assert list(res["status"]) == [0, sfm.SF_EINVAL, sfm.SF_ECAPACITY, sfm.SF_EINVAL, 0, 0]
+    assert res["k_final"][0] == 1 and abs(res["norm"][0] - 1) < 1e-15
+    assert int(res["outcomes"][4]) == 0b11 and res["n_meas"][4] == 2
+    assert res["k_final"][5] == 2
+    # the draw decides between p(1) and p(0): u just below and above p(1) = 1/2
+    h = [("C", c.H, 2, 0), ("M", 2, 0.4999999), ("C", c.H, 3, 0), ("M", 3, 0.5000001)]
+    r2 = eng.run([h])
+    assert int(r2["outcomes"][0]) == 0b01
+    # a conditional gate must be a Clifford kind
+    ops, off, nc = eng.upload([[("C", c.H, 0, 0)]])
+    rec = ops.cpu().numpy().view(sfm.SF_OP_DTYPE).copy()
+    rec["kind"][0], rec["arg"][0] = sfm.OP_COND, 20
+    rec["param"][0] = np.array([1], dtype=np.uint64).view(np.float64)[0]
+    import torch
+    ops = torch.from_numpy(rec.view(np.uint8)).to("cuda")
+    out = eng.outputs(1)
+    eng.launch(ops, off, 1, 1e-12, out)
+    torch.cuda.synchronize()
+    assert int(out["status"][0]) == sfm.SF_EINVAL
+    # zero circuits: nothing to do
+    eng.launch(ops, off, 0, 1e-12, out)
+    eng.close()
+    with pytest.raises(sfm.SFError):
+        sfm.Campaign(64, 16)
+    with pytest.raises(sfm.SFError):
+        sfm.Campaign(8, sfm.CAMPAIGN_MAX_ELEMS + 1)
