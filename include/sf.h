@@ -267,8 +267,9 @@ typedef struct sf_campaign_s* sf_campaign;
 
 /* Engine for circuits on n_qubits (1..63) whose frames never exceed
  * max_elems (1..SF_CAMPAIGN_MAX_ELEMS) elements, on cuda_stream.  Allocates a
- * workspace of about (#CTAs x max_elems x 48) bytes, #CTAs = SMs x resident
- * CTAs per SM.  Synchronises. */
+ * workspace of about (#CTAs x max_elems x 56) bytes, #CTAs = SMs x resident
+ * CTAs per SM of the launch shape with the most (see sf_campaign_set_shape).
+ * Synchronises. */
 sf_status sf_campaign_create(uint32_t n_qubits, uint32_t max_elems, void* cuda_stream, sf_campaign* out);
 
 /* Waits for the engine's stream and frees the workspace. */
@@ -288,15 +289,37 @@ sf_status sf_campaign_destroy(sf_campaign c);
  * (one word), dev_export_amp[2 * (c * max_elems + j) + {0, 1}] for
  * j < k_final, in the frame's order (not sorted), and dev_export_tableau[c * 129 + {0..63, 64..127, 128}] = the x
  * words, z words of the canonical rows and the X-block size r.  All three or
- * none.  Results do not depend on the number of CTAs or the order in which
- * circuits are run.  Asynchronous (one memset and one kernel on the stream). */
+ * none.  Results do not depend on the number of CTAs, on the order in which
+ * circuits are run or on the other circuits of the batch.  Asynchronous (one
+ * memset and one kernel on the stream). */
 sf_status sf_campaign_run(sf_campaign c, const sf_op* dev_ops, const uint64_t* dev_offsets, uint32_t n_circuits,
                           double drop_eps, uint64_t* dev_outcomes, uint32_t* dev_n_meas, uint32_t* dev_k_final,
                           double* dev_norm, int32_t* dev_status, uint64_t* dev_export_sigma,
                           double* dev_export_amp, uint64_t* dev_export_tableau);
 
-/* Number of CTAs of the engine's persistent launch. */
+/* Number of CTAs of the engine's persistent launch in its current shape. */
 uint32_t sf_campaign_ctas(sf_campaign c);
+
+/* Shape of the persistent launch: threads per circuit (32, 64, 128 or 256)
+ * and where each CTA keeps the hash index of its frame's phase vectors
+ * (smem_index = 1: shared memory, fastest probes, fewer CTAs per SM for large
+ * max_elems; 0: a per-CTA slice of global memory).  Small threads-per-circuit
+ * values run more circuits side by side (the tableau work of a circuit is one
+ * warp's); large ones spread big frames over more threads.  For a given shape
+ * a circuit's results do not depend on the rest of the batch; across shapes
+ * the probability and norm sums are added in a different order, so amplitudes
+ * may differ in the last bits.  SF_EINVAL for an unknown shape or one that cannot be
+ * resident on this GPU.  The default is 64 threads, index in shared memory
+ * when it needs at most 32 KB. */
+sf_status sf_campaign_set_shape(sf_campaign c, uint32_t threads_per_circuit, uint32_t smem_index);
+sf_status sf_campaign_get_shape(sf_campaign c, uint32_t* threads_per_circuit, uint32_t* smem_index, uint32_t* ctas);
+
+/* Autotuner: runs the given program (device pointers as for sf_campaign_run)
+ * once untimed and `reps` (1..16) times timed in every shape, keeps the
+ * fastest, and writes its mean time per run to *best_ms (nullable).  Uses
+ * temporary device buffers for the outputs.  Synchronises. */
+sf_status sf_campaign_autotune(sf_campaign c, const sf_op* dev_ops, const uint64_t* dev_offsets,
+                               uint32_t n_circuits, double drop_eps, uint32_t reps, float* best_ms);
 
 #ifdef __cplusplus
 }

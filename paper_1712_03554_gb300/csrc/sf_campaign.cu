@@ -25,7 +25,7 @@ using namespace sfw;
 
 namespace {
 
-constexpr int kCT = 256;  // threads per CTA
+constexpr int kMaxWarps = 8;  // threads per circuit: 32, 64, 128 or 256
 constexpr int kCampMaxCap = SF_CAMPAIGN_MAX_ELEMS;
 
 struct OpRec {
@@ -41,6 +41,8 @@ struct CampDev {
     const unsigned long long* off;
     uint64_t* ws_sig;  // [gridDim][2][cap]
     double2* ws_amp;   // [gridDim][2][cap]
+    uint32_t* ws_idx;  // [gridDim][islots] when the index lives in global memory
+    unsigned islots;
     unsigned* next;
     unsigned long long* outcomes;
     uint32_t* nmeas;
@@ -61,8 +63,8 @@ struct Shared {
     uint64_t rmx[64], rmz[64], rdx[64], rdz[64];
     uint32_t rde[64];
     int32_t rpiv[64];
-    double red[2][kCT / 32];
-    unsigned wsum[kCT / 32];
+    double red[2][kMaxWarps];
+    unsigned wsum[kMaxWarps];
     Row stage[64];            // row permutation of the tableau reduction
     unsigned long long obase, outcomes, oe;
     double2 g;
@@ -70,6 +72,31 @@ struct Shared {
     unsigned k, kout, nmeas;
     int cur, rx, status, circ;
 };
+
+// program records: warp 0 walks a run of Clifford gates through a window of
+// 32 records per register set (lane L holds record base + L), the next window
+// loading while the current one is used
+__device__ __forceinline__ OpRec load_rec(const OpRec* ops, unsigned long long i, unsigned long long end) {
+    OpRec o;
+    if (i < end) {
+        o = ops[i];
+    } else {
+        o.kind = 0xffffffffu;
+        o.q0 = o.q1 = o.arg = 0;
+        o.param = 0.0;
+    }
+    return o;
+}
+
+__device__ __forceinline__ OpRec shfl_rec(const OpRec& w, int src) {
+    OpRec o;
+    o.kind = __shfl_sync(SF_FULL, w.kind, src);
+    o.q0 = __shfl_sync(SF_FULL, w.q0, src);
+    o.q1 = __shfl_sync(SF_FULL, w.q1, src);
+    o.arg = __shfl_sync(SF_FULL, w.arg, src);
+    o.param = __shfl_sync(SF_FULL, w.param, src);
+    return o;
+}
 
 __device__ __forceinline__ uint64_t hash1(uint64_t s) {
     uint64_t v = s + 0x9E3779B97F4A7C15ull;
@@ -133,7 +160,7 @@ __device__ unsigned long long block_scan_advance(Shared& S, unsigned cnt) {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned tot = 0;
-        for (int i = 0; i < kCT / 32; i++) tot += S.wsum[i];
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) tot += S.wsum[i];
         S.obase = base + tot;
     }
     __syncthreads();
@@ -155,7 +182,7 @@ __device__ void block_sum2(Shared& S, double a, double b) {
     __syncthreads();
     if (threadIdx.x == 0) {
         double x = 0, y = 0;
-        for (int i = 0; i < kCT / 32; i++) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
             x += S.red[0][i];
             y += S.red[1][i];
         }
@@ -214,9 +241,13 @@ __device__ int export_phase(const Shared& S, int n, uint64_t s) {
     return (qe + __popcll(qx & qz) + 2 * __popcll(qz & w) + pe + __popcll(px & pz)) & 3;
 }
 
-__global__ void __launch_bounds__(kCT) k_campaign(CampDev D) {
-    extern __shared__ uint32_t idx[];  // [slots_for(cap)]
+// CT threads per circuit; GIDX: the phase-vector index in a per-CTA slice of
+// global memory (L2-resident) instead of shared memory, for more CTAs per SM
+template <int CT, bool GIDX>
+__global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
+    extern __shared__ uint32_t smem_idx[];  // [slots_for(cap)] unless GIDX
     __shared__ Shared S;
+    uint32_t* idx = GIDX ? D.ws_idx + (size_t)blockIdx.x * D.islots : smem_idx;
     const int n = D.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t* sigb[2] = {D.ws_sig + (size_t)blockIdx.x * 2 * D.cap, D.ws_sig + ((size_t)blockIdx.x * 2 + 1) * D.cap};
     double2* ampb[2] = {D.ws_amp + (size_t)blockIdx.x * 2 * D.cap, D.ws_amp + ((size_t)blockIdx.x * 2 + 1) * D.cap};
@@ -276,7 +307,7 @@ __global__ void __launch_bounds__(kCT) k_campaign(CampDev D) {
             }
             if (kind <= 8) {
                 // a run of consecutive Clifford gates (a conditional gate runs alone);
-                // warp 0 walks it with the next record prefetched, lane 0 publishes its end
+                // warp 0 walks it through the record window, lane 0 publishes its end
                 if (warp == 0) {
                     for (int hf = 0; hf < 2; hf++) {
                         const int row = lane + 32 * hf;
@@ -286,16 +317,16 @@ __global__ void __launch_bounds__(kCT) k_campaign(CampDev D) {
                     int rx = S.rx;
                     double2 g = S.g;
                     int bad = 0;
-                    unsigned long long gi = oi;
-                    OpRec op = op0;
+                    unsigned long long gi = oi, wb = oi;
+                    OpRec w0 = load_rec(D.ops, wb + lane, o1), w1 = load_rec(D.ops, wb + 32 + lane, o1);
                     const bool single = op0.kind == SF_OP_COND;
                     for (;;) {
-                        OpRec nop = op;
-                        bool more = false;
-                        if (!single && gi + 1 < o1) {
-                            nop = D.ops[gi + 1];
-                            more = nop.kind <= 8;
+                        if (gi - wb >= 32) {
+                            wb += 32;
+                            w0 = w1;
+                            w1 = load_rec(D.ops, wb + 32 + lane, o1);
                         }
+                        const OpRec op = shfl_rec(w0, (int)(gi - wb));
                         gi++;
                         const int gk = (int)(op.kind == SF_OP_COND ? op.arg : op.kind);
                         const bool two = gk >= 6;
@@ -347,8 +378,11 @@ __global__ void __launch_bounds__(kCT) k_campaign(CampDev D) {
                         om.x *= sc;
                         om.y *= sc;
                         g = cmul(g, om);
-                        if (!more) break;
-                        op = nop;
+                        if (single || gi >= o1) break;
+                        const unsigned long long d = gi - wb;  // 1..32
+                        const uint32_t nk = d < 32 ? __shfl_sync(SF_FULL, w0.kind, (int)d)
+                                                   : __shfl_sync(SF_FULL, w1.kind, 0);
+                        if (nk > 8) break;
                     }
                     for (int j = 0; j < n; j++) {
                         const unsigned b0 = __ballot_sync(SF_FULL, lane < n && ((r[0].A >> j) & 1));
@@ -630,11 +664,22 @@ __global__ void __launch_bounds__(kCT) k_campaign(CampDev D) {
     }
 }
 
-// shared-memory index for frames of up to cap elements (slots_for(cap) slots)
-size_t index_bytes(unsigned cap) {
+// index for frames of up to cap elements (slots_for(cap) slots)
+size_t index_slots_for(unsigned cap) {
     size_t t = 64;
     while (t < 2 * (size_t)cap) t <<= 1;
-    return t * sizeof(uint32_t);
+    return t;
+}
+
+using CampKernel = void (*)(CampDev);
+constexpr int kShapes = 8;  // threads 32 << (i >> 1), index in global memory iff i odd
+const CampKernel kKernels[kShapes] = {k_campaign<32, false>,  k_campaign<32, true>,  k_campaign<64, false>,
+                                      k_campaign<64, true>,   k_campaign<128, false>, k_campaign<128, true>,
+                                      k_campaign<256, false>, k_campaign<256, true>};
+
+int shape_index(uint32_t threads, bool smem_index) {
+    int i = threads == 32 ? 0 : threads == 64 ? 2 : threads == 128 ? 4 : threads == 256 ? 6 : -1;
+    return i < 0 ? -1 : i + (smem_index ? 0 : 1);
 }
 
 }  // namespace
@@ -642,12 +687,51 @@ size_t index_bytes(unsigned cap) {
 struct sf_campaign_s {
     int n = 0;
     unsigned cap = 0;
-    int nblk = 0;
     cudaStream_t stream = nullptr;
+    int shape = 0;
+    int nblk_of[kShapes] = {};
+    size_t smem_of[kShapes] = {};
+    int max_nblk = 0;
+    unsigned islots = 0;
     uint64_t* ws_sig = nullptr;
     double2* ws_amp = nullptr;
+    uint32_t* ws_idx = nullptr;
     unsigned* next = nullptr;
 };
+
+namespace {
+
+sf_status launch_campaign(sf_campaign c, int shape, const sf_op* dev_ops, const uint64_t* dev_offsets,
+                          uint32_t n_circuits, double drop_eps, uint64_t* dev_outcomes, uint32_t* dev_n_meas,
+                          uint32_t* dev_k_final, double* dev_norm, int32_t* dev_status, uint64_t* ex_sig,
+                          double* ex_amp, uint64_t* ex_tab) {
+    CampDev D;
+    D.n = c->n;
+    D.ncirc = (int)n_circuits;
+    D.cap = c->cap;
+    D.eps2 = drop_eps * drop_eps;
+    D.ops = reinterpret_cast<const OpRec*>(dev_ops);
+    D.off = reinterpret_cast<const unsigned long long*>(dev_offsets);
+    D.ws_sig = c->ws_sig;
+    D.ws_amp = c->ws_amp;
+    D.ws_idx = c->ws_idx;
+    D.islots = c->islots;
+    D.next = c->next;
+    D.outcomes = reinterpret_cast<unsigned long long*>(dev_outcomes);
+    D.nmeas = dev_n_meas;
+    D.kfinal = dev_k_final;
+    D.norm = dev_norm;
+    D.cstatus = dev_status;
+    D.ex_sig = ex_sig;
+    D.ex_amp = reinterpret_cast<double2*>(ex_amp);
+    D.ex_tab = ex_tab;
+    if (cudaMemsetAsync(c->next, 0, sizeof(unsigned), c->stream) != cudaSuccess) return SF_ECUDA;
+    const int threads = 32 << (shape >> 1);
+    kKernels[shape]<<<c->nblk_of[shape], threads, c->smem_of[shape], c->stream>>>(D);
+    return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -660,22 +744,44 @@ sf_status sf_campaign_create(uint32_t n_qubits, uint32_t max_elems, void* cuda_s
     c->n = (int)n_qubits;
     c->cap = max_elems;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
-    int dev = 0, sms = 0, per_sm = 0;
-    const size_t smem = index_bytes(max_elems);
+    c->islots = (unsigned)index_slots_for(max_elems);
+    int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaFuncSetAttribute(k_campaign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_campaign, kCT, smem) != cudaSuccess) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete c;
         return SF_ECUDA;
     }
-    c->nblk = std::max(1, sms * std::max(1, per_sm));
-    const size_t ne = (size_t)c->nblk * 2 * max_elems;
-    if (cudaMalloc(&c->ws_sig, ne * sizeof(uint64_t)) != cudaSuccess ||
+    // CTAs of each shape: SMs x resident CTAs per SM (registers, shared memory)
+    for (int i = 0; i < kShapes; i++) {
+        const bool gidx = i & 1;
+        const size_t smem = gidx ? 0 : c->islots * sizeof(uint32_t);
+        int per_sm = 0;
+        if (cudaFuncSetAttribute(kKernels[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kKernels[i], 32 << (i >> 1), smem) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 0;
+        }
+        c->smem_of[i] = smem;
+        c->nblk_of[i] = sms * per_sm;
+        c->max_nblk = std::max(c->max_nblk, c->nblk_of[i]);
+    }
+    // default shape: 64 threads per circuit, index in shared memory while it
+    // leaves room for several CTAs per SM
+    c->shape = shape_index(64, c->islots * sizeof(uint32_t) <= 32768);
+    if (c->nblk_of[c->shape] == 0) {
+        c->shape = -1;
+        for (int i = 0; i < kShapes; i++)
+            if (c->nblk_of[i] > 0) { c->shape = i; break; }
+    }
+    const size_t ne = (size_t)c->max_nblk * 2 * max_elems;
+    if (c->shape < 0 || cudaMalloc(&c->ws_sig, ne * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&c->ws_amp, ne * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->ws_idx, (size_t)c->max_nblk * c->islots * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->next, sizeof(unsigned)) != cudaSuccess) {
+        const bool nomem = c->shape >= 0;
         sf_campaign_destroy(c);
-        return SF_ENOMEM;
+        return nomem ? SF_ENOMEM : SF_ECUDA;
     }
     *out = c;
     return SF_OK;
@@ -686,6 +792,7 @@ sf_status sf_campaign_destroy(sf_campaign c) {
     cudaStreamSynchronize(c->stream);
     if (c->ws_sig) cudaFree(c->ws_sig);
     if (c->ws_amp) cudaFree(c->ws_amp);
+    if (c->ws_idx) cudaFree(c->ws_idx);
     if (c->next) cudaFree(c->next);
     delete c;
     return SF_OK;
@@ -702,30 +809,83 @@ sf_status sf_campaign_run(sf_campaign c, const sf_op* dev_ops, const uint64_t* d
         (dev_export_sigma != nullptr) != (dev_export_tableau != nullptr))
         return SF_EINVAL;
     if (n_circuits == 0) return SF_OK;
-    CampDev D;
-    D.n = c->n;
-    D.ncirc = (int)n_circuits;
-    D.cap = c->cap;
-    D.eps2 = drop_eps * drop_eps;
-    D.ops = reinterpret_cast<const OpRec*>(dev_ops);
-    D.off = reinterpret_cast<const unsigned long long*>(dev_offsets);
-    D.ws_sig = c->ws_sig;
-    D.ws_amp = c->ws_amp;
-    D.next = c->next;
-    D.outcomes = reinterpret_cast<unsigned long long*>(dev_outcomes);
-    D.nmeas = dev_n_meas;
-    D.kfinal = dev_k_final;
-    D.norm = dev_norm;
-    D.cstatus = dev_status;
-    D.ex_sig = dev_export_sigma;
-    D.ex_amp = reinterpret_cast<double2*>(dev_export_amp);
-    D.ex_tab = dev_export_tableau;
-    if (cudaMemsetAsync(c->next, 0, sizeof(unsigned), c->stream) != cudaSuccess) return SF_ECUDA;
-    const size_t smem = index_bytes(c->cap);
-    k_campaign<<<c->nblk, kCT, smem, c->stream>>>(D);
-    return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA;
+    return launch_campaign(c, c->shape, dev_ops, dev_offsets, n_circuits, drop_eps, dev_outcomes, dev_n_meas,
+                           dev_k_final, dev_norm, dev_status, dev_export_sigma, dev_export_amp, dev_export_tableau);
 }
 
-uint32_t sf_campaign_ctas(sf_campaign c) { return c ? (uint32_t)c->nblk : 0u; }
+uint32_t sf_campaign_ctas(sf_campaign c) { return c ? (uint32_t)c->nblk_of[c->shape] : 0u; }
+
+sf_status sf_campaign_set_shape(sf_campaign c, uint32_t threads_per_circuit, uint32_t smem_index) {
+    if (!c) return SF_EINVAL;
+    const int i = shape_index(threads_per_circuit, smem_index != 0);
+    if (i < 0 || c->nblk_of[i] == 0) return SF_EINVAL;
+    c->shape = i;
+    return SF_OK;
+}
+
+sf_status sf_campaign_get_shape(sf_campaign c, uint32_t* threads_per_circuit, uint32_t* smem_index,
+                                uint32_t* ctas) {
+    if (!c) return SF_EINVAL;
+    if (threads_per_circuit) *threads_per_circuit = 32u << (c->shape >> 1);
+    if (smem_index) *smem_index = (c->shape & 1) ? 0u : 1u;
+    if (ctas) *ctas = (uint32_t)c->nblk_of[c->shape];
+    return SF_OK;
+}
+
+sf_status sf_campaign_autotune(sf_campaign c, const sf_op* dev_ops, const uint64_t* dev_offsets,
+                               uint32_t n_circuits, double drop_eps, uint32_t reps, float* best_ms) {
+    if (!c || !dev_ops || !dev_offsets || !(drop_eps >= 0.0) || n_circuits == 0) return SF_EINVAL;
+    reps = std::max(1u, std::min(reps, 16u));
+    uint64_t* outc = nullptr;
+    uint32_t *nm = nullptr, *kf = nullptr;
+    double* nr = nullptr;
+    int32_t* st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sf_status res = SF_OK;
+    if (cudaMalloc(&outc, n_circuits * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&nm, n_circuits * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&kf, n_circuits * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&nr, n_circuits * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&st, n_circuits * sizeof(int32_t)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        res = SF_ENOMEM;
+    }
+    int best = -1;
+    float best_t = 0.f;
+    for (int i = 0; i < kShapes && res == SF_OK; i++) {
+        if (c->nblk_of[i] == 0) continue;
+        // one untimed launch, then the mean of reps timed launches
+        res = launch_campaign(c, i, dev_ops, dev_offsets, n_circuits, drop_eps, outc, nm, kf, nr, st, nullptr,
+                              nullptr, nullptr);
+        if (res != SF_OK) break;
+        cudaEventRecord(e0, c->stream);
+        for (uint32_t k = 0; k < reps && res == SF_OK; k++)
+            res = launch_campaign(c, i, dev_ops, dev_offsets, n_circuits, drop_eps, outc, nm, kf, nr, st, nullptr,
+                                  nullptr, nullptr);
+        cudaEventRecord(e1, c->stream);
+        float ms = 0.f;
+        if (res != SF_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            res = SF_ECUDA;
+            break;
+        }
+        ms /= (float)reps;
+        if (best < 0 || ms < best_t) {
+            best = i;
+            best_t = ms;
+        }
+    }
+    if (res == SF_OK && best >= 0) {
+        c->shape = best;
+        if (best_ms) *best_ms = best_t;
+    }
+    if (outc) cudaFree(outc);
+    if (nm) cudaFree(nm);
+    if (kf) cudaFree(kf);
+    if (nr) cudaFree(nr);
+    if (st) cudaFree(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return res;
+}
 
 }  // extern "C"

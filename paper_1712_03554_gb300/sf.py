@@ -79,6 +79,9 @@ def load(build: bool = True) -> C.CDLL:
         "sf_campaign_destroy": ([H], st),
         "sf_campaign_run": ([H, C.c_void_p, C.c_void_p, u32, dbl] + [C.c_void_p] * 8, st),
         "sf_campaign_ctas": ([H], u32),
+        "sf_campaign_set_shape": ([H, u32, u32], st),
+        "sf_campaign_get_shape": ([H, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)], st),
+        "sf_campaign_autotune": ([H, C.c_void_p, C.c_void_p, u32, dbl, u32, C.POINTER(C.c_float)], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -156,6 +159,26 @@ class Campaign:
 
     def ctas(self) -> int:
         return int(self.lib.sf_campaign_ctas(self.h))
+
+    def set_shape(self, threads_per_circuit: int, smem_index: bool) -> None:
+        code = self.lib.sf_campaign_set_shape(self.h, int(threads_per_circuit), 1 if smem_index else 0)
+        if code != SF_OK:
+            raise SFError(code, "sf_campaign_set_shape failed")
+
+    def shape(self) -> Tuple[int, bool, int]:
+        """(threads per circuit, index in shared memory, CTAs)."""
+        t, sm, n = C.c_uint32(), C.c_uint32(), C.c_uint32()
+        self.lib.sf_campaign_get_shape(self.h, C.byref(t), C.byref(sm), C.byref(n))
+        return int(t.value), bool(sm.value), int(n.value)
+
+    def autotune(self, ops, off, nc: int, drop_eps: float = 1e-12, reps: int = 2) -> float:
+        """sf_campaign_autotune on an uploaded program; returns the best ms per run."""
+        ms = C.c_float()
+        code = self.lib.sf_campaign_autotune(self.h, C.c_void_p(ops.data_ptr()), C.c_void_p(off.data_ptr()), nc,
+                                             float(drop_eps), int(reps), C.byref(ms))
+        if code != SF_OK:
+            raise SFError(code, "sf_campaign_autotune failed")
+        return float(ms.value)
 
     def upload(self, circuits):
         """Encode and copy a program to the device: (ops, offsets, n_circuits)."""

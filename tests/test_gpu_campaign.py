@@ -182,3 +182,37 @@ def test_statuses_and_edge_cases(sfm):
         sfm.Campaign(64, 16)
     with pytest.raises(sfm.SFError):
         sfm.Campaign(8, sfm.CAMPAIGN_MAX_ELEMS + 1)
+
+
+def test_shapes_agree_and_autotune(sfm):
+    """Every launch shape (threads per circuit x index placement) gives the
+    same outcomes, frame sizes and phase vectors, and amplitudes equal up to
+    the rounding of the probability sums; the autotuner keeps a valid shape."""
+    circuits = c.steane_campaign(64, seed=4) + [c.qft_random_input(8, seed=9)[1]]
+    eng = sfm.Campaign(c.STEANE_N, 4096)
+    ref = None
+    for threads in (32, 64, 128, 256):
+        for smem in (True, False):
+            try:
+                eng.set_shape(threads, smem)
+            except sfm.SFError:
+                continue
+            assert eng.shape()[:2] == (threads, smem)
+            res = eng.run(circuits, export=True)
+            assert not res["status"].any()
+            if ref is None:
+                ref = res
+                continue
+            for key in ("outcomes", "n_meas", "k_final"):
+                assert np.array_equal(res[key], ref[key]), (threads, smem, key)
+            assert np.max(np.abs(res["norm"] - ref["norm"])) <= 1e-12
+            for fa, fb in zip(res["frames"], ref["frames"]):
+                assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1]) and fa[2] == fb[2]
+                assert np.array_equal(fa[3], fb[3])
+                assert np.max(np.abs(fa[4] - fb[4]), initial=0.0) <= 1e-12
+    ops, off, nc = eng.upload(circuits)
+    ms = eng.autotune(ops, off, nc, reps=1)
+    assert ms > 0
+    res = eng.run(circuits)
+    assert np.array_equal(res["outcomes"], ref["outcomes"])
+    eng.close()
