@@ -216,9 +216,10 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     SfDev& d = h->d;
     d.n = (int)n_qubits;
-    // words per phase vector: a power of two with at least one bit to spare
-    // above qubit n-1 (the slot table marks empty keys with that bit)
-    d.W = pow2_at_least((int)(n_qubits / 64) + 1);
+    // words per phase vector: a power of two >= ceil(n/64); with one word, bit
+    // 63 stays free (the slot table marks empty one-word keys with all ones),
+    // so n = 64 takes two
+    d.W = n_qubits <= 63 ? 1 : std::max(2, pow2_at_least((int)((n_qubits + 63) / 64)));
     d.NT = std::max(32, (int)((n_qubits + 31) / 32) * 32);
     d.cap = max_elems;
     int dev = 0, sms = 0;

@@ -75,8 +75,8 @@ struct SfDev {
     unsigned long long* ocnt;  // output counter of the merge kernels
 };
 
-// An empty slot key: phase vectors never set bit 63 of their last word
-// (the word count W leaves at least one spare bit above qubit n-1).
+// An empty one-word slot key: with W = 1 (n <= 63) phase vectors never set
+// bit 63.  Wider keys mark their slots through a separate state word.
 #define SF_EMPTY_KEY 0xffffffffffffffffull
 
 // ---- plan layout (in 64-bit words) ---------------------------------------

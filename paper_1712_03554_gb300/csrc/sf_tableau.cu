@@ -1,8 +1,8 @@
 // sf_tableau.cu -- single-CTA kernels that work on the shared tableau:
 //   * k_clifford:      ROTATE(F, U) on M and D for a batch of Clifford gates
-//                      (Table 2 conjugation, Invariant 1 repair by Gauss-Jordan
-//                      from the first touched column, global-phase update by
-//                      the five-step rule of Sec. III evaluated once per gate),
+//                      (Table 2 conjugation, Invariant 1 repair by a row
+//                      reduction that only works on dirty columns, global-phase
+//                      update by the five-step rule of Sec. III once per gate),
 //                      emitting the composed affine map sigma' = A sigma ^ t that
 //                      k_affine applies to every phase vector.
 //   * k_measure_prep:  deterministic/random test of a qubit and, if random, the
@@ -50,6 +50,7 @@ struct Scratch {
     Pauli<W> red[kMaxWarps + 1];
     int wmin[2][kMaxWarps];
     uint64_t y[W], y2[W], words[5][W];
+    uint64_t occ1[2 * W], occ2[2 * W];  // columns holding >= 1 / >= 2 ones (x words, then z words)
     int iv[8];
     double dv[8];
 };
@@ -194,82 +195,186 @@ __device__ __forceinline__ int conj_row(int kind, int q0, int q1, uint64_t* X, u
     return f;
 }
 
-// Gauss-Jordan elimination to the canonical RREF over columns >= start, rows
-// whose pivot is < start keeping theirs.  Every row operation M_h <- M_h M_i is
-// mirrored as D_i <- D_i D_h (so D stays a destabilizer set and
-// D^sigma = D'^{A sigma} exactly), as A_h ^= A_i on the composed affine map
-// (if TRACK_A), and as t_h ^= t_i ^ c (c = sign bit of the row product) on the
-// sign vectors t0/t1.  Returns r.
+// ---- Invariant 1 repair without row movement (CTA version) -----------------
+// The reduction of the warp kernel at block scale: rows stay in place while
+// pivots are chosen; every unassigned row whose leading column holds no other
+// 1 in the tableau takes it as pivot at once (Gauss-Jordan would reach it with
+// nothing to eliminate, in any order); otherwise the smallest leading column c
+// among unassigned rows takes one elimination step with the lowest-index
+// unassigned row leading there as pivot p: every other row with bit c gets
+// M_h <- M_h M_p, mirrored as D_p <- D_p D_h, A_h ^= A_p and t_h ^= t_p ^ c.
+// A final permutation sorts the rows by pivot.  Each gate dirties a few
+// columns, so a gate costs a few block-wide passes instead of one barrier
+// round per column.  Returns r, or -1 if a row has no bits (dependent rows).
+template <int W>
+__device__ __forceinline__ int row_lead(const Ws<W>& T, int NT, int h, int n) {
+#pragma unroll 1
+    for (int w = 0; w < W; w++) {
+        const uint64_t v = T.mx[w * NT + h];
+        if (v) return 64 * w + __ffsll((long long)v) - 1;
+    }
+#pragma unroll 1
+    for (int w = 0; w < W; w++) {
+        const uint64_t v = T.mz[w * NT + h];
+        if (v) return n + 64 * w + __ffsll((long long)v) - 1;
+    }
+    return 0x7fffffff;
+}
+
+__device__ __forceinline__ bool col_set(const uint64_t* occ, int W, int c, int n) {
+    const int wi = c < n ? (c >> 6) : W + ((c - n) >> 6);
+    const int b = c < n ? (c & 63) : ((c - n) & 63);
+    return (occ[wi] >> b) & 1;
+}
+
+// S.occ1 / S.occ2: columns with at least one / at least two ones over all rows
+template <int W>
+__device__ void cta_occupancy(const Ws<W>& T, int NT, Scratch<W>& S) {
+    const int h = threadIdx.x, lane = h & 31;
+    if (h < 2 * W) { S.occ1[h] = 0; S.occ2[h] = 0; }
+    __syncthreads();
+#pragma unroll 1
+    for (int w = 0; w < 2 * W; w++) {
+        uint64_t o = w < W ? T.mx[w * NT + h] : T.mz[(w - W) * NT + h];
+        if (!__any_sync(SF_FULL, o != 0)) continue;
+        uint64_t m = 0;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const uint64_t oo = __shfl_xor_sync(SF_FULL, o, off);
+            const uint64_t om = __shfl_xor_sync(SF_FULL, m, off);
+            m |= om | (o & oo);
+            o |= oo;
+        }
+        if (lane == 0 && o) {
+            const unsigned long long prev = atomicOr(reinterpret_cast<unsigned long long*>(&S.occ1[w]), o);
+            if (m | (prev & o)) atomicOr(reinterpret_cast<unsigned long long*>(&S.occ2[w]), m | (prev & o));
+        }
+    }
+    __syncthreads();
+}
+
+// move row fields so that row h goes to position dst (a permutation)
+template <int W>
+__device__ void cta_permute64(uint64_t* F, uint64_t* tmp, int NT, int h, int n, int dst) {
+    if (h < n) {
+#pragma unroll 1
+        for (int w = 0; w < W; w++) tmp[w * NT + dst] = F[w * NT + h];
+    }
+    __syncthreads();
+    if (h < n) {
+#pragma unroll 1
+        for (int w = 0; w < W; w++) F[w * NT + h] = tmp[w * NT + h];
+    }
+    __syncthreads();
+}
+
+__device__ void cta_permute32(uint32_t* F, uint32_t* tmp, int h, int n, int dst) {
+    if (h < n) tmp[dst] = F[h];
+    __syncthreads();
+    if (h < n) F[h] = tmp[h];
+    __syncthreads();
+}
+
 template <int W, bool TRACK_A>
-__device__ int cta_gj(const Ws<W>& T, int n, int NT, int start, Scratch<W>& S) {
+__device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
     const int h = threadIdx.x, lane = h & 31, wid = h >> 5, nw = NT >> 5;
-    int nxt = __syncthreads_count(h < n && T.piv[h] < start);
-    int par = 0;
-    for (int c = start; c < 2 * n && nxt < n; c++) {
+    constexpr int INF = 0x7fffffff;
+    bool asg = false;
+    for (int it = 0; it <= n; it++) {
+        cta_occupancy<W>(T, NT, S);
+        const int l = (h < n && !asg) ? row_lead<W>(T, NT, h, n) : INF;
+        if (l != INF && !col_set(S.occ2, W, l, n)) {
+            asg = true;
+            T.piv[h] = l;
+        }
+        // smallest leading column of the unassigned rows; lowest row index on ties
+        const int key = (h < n && !asg && l != INF) ? ((l << 10) | h) : INF;
+        const int wk = __reduce_min_sync(SF_FULL, key);
+        if (lane == 0) S.wmin[0][wid] = wk;
+        __syncthreads();
+        int kmin = INF;
+        for (int i = 0; i < nw; i++) kmin = min(kmin, S.wmin[0][i]);
+        const int none_left = __syncthreads_and(asg || h >= n);
+        if (kmin == INF) {
+            if (!none_left) return -1;  // an unassigned row without bits
+            break;
+        }
+        const int c = kmin >> 10, p = kmin & 1023;
+        // elimination step at column c with pivot row p
         const uint64_t* plane = c < n ? T.mx : T.mz;
         const int cc = c < n ? c : c - n;
-        const int cwo = (cc >> 6) * NT, cb = cc & 63;
-        const bool cand = (h < n) && (h >= nxt) && ((plane[cwo + h] >> cb) & 1);
-        const unsigned bal = __ballot_sync(SF_FULL, cand);
-        if (lane == 0) S.wmin[par][wid] = bal ? (wid * 32 + __ffs(bal) - 1) : 0x7fffffff;
-        __syncthreads();
-        int p = 0x7fffffff;
-        for (int i = 0; i < nw; i++) p = min(p, S.wmin[par][i]);
-        par ^= 1;
-        if (p == 0x7fffffff) continue;
-        if (p != nxt) {
-            if (h < W) {
-                const int a = h * NT + p, b = h * NT + nxt;
-                uint64_t t;
-                t = T.mx[a]; T.mx[a] = T.mx[b]; T.mx[b] = t;
-                t = T.mz[a]; T.mz[a] = T.mz[b]; T.mz[b] = t;
-                t = T.dx[a]; T.dx[a] = T.dx[b]; T.dx[b] = t;
-                t = T.dz[a]; T.dz[a] = T.dz[b]; T.dz[b] = t;
-                if (TRACK_A) { t = T.A[a]; T.A[a] = T.A[b]; T.A[b] = t; }
-            } else if (h == W) {
-                uint32_t u;
-                u = T.de[p]; T.de[p] = T.de[nxt]; T.de[nxt] = u;
-                u = T.t0[p]; T.t0[p] = T.t0[nxt]; T.t0[nxt] = u;
-                u = T.t1[p]; T.t1[p] = T.t1[nxt]; T.t1[nxt] = u;
-            }
-            __syncthreads();
-        }
-        const int i = nxt;
-        const bool el = (h < n) && (h != i) && ((plane[cwo + h] >> cb) & 1);
+        const bool el = (h < n) && (h != p) && ((plane[(cc >> 6) * NT + h] >> (cc & 63)) & 1);
         if (el) {
             uint64_t xh[W], zh[W], xi[W], zi[W];
 #pragma unroll
             for (int w = 0; w < W; w++) {
                 xh[w] = T.mx[w * NT + h]; zh[w] = T.mz[w * NT + h];
-                xi[w] = T.mx[w * NT + i]; zi[w] = T.mz[w * NT + i];
+                xi[w] = T.mx[w * NT + p]; zi[w] = T.mz[w * NT + p];
             }
             const uint32_t cbit = (uint32_t)(pauli_lambda<W>(xh, zh, xi, zi) >> 1) & 1u;
 #pragma unroll
             for (int w = 0; w < W; w++) {
                 T.mx[w * NT + h] = xh[w] ^ xi[w];
                 T.mz[w * NT + h] = zh[w] ^ zi[w];
-                if (TRACK_A) T.A[w * NT + h] ^= T.A[w * NT + i];
+                if (TRACK_A) T.A[w * NT + h] ^= T.A[w * NT + p];
             }
-            T.t0[h] ^= T.t0[i] ^ cbit;
-            T.t1[h] ^= T.t1[i] ^ cbit;
+            T.t0[h] ^= T.t0[p] ^ cbit;
+            T.t1[h] ^= T.t1[p] ^ cbit;
         }
         if (__syncthreads_or(el)) {
             Pauli<W> v;
             pauli_id<W>(v);
             if (el) load_d<W>(T, NT, h, v);
             cta_product<W>(v, S);
-            if (h == 0) {
+            if (h == p) {
                 Pauli<W> di;
-                load_d<W>(T, NT, i, di);
+                load_d<W>(T, NT, p, di);
                 pauli_mul<W>(di, v);
-                store_d<W>(T, NT, i, di);
+                store_d<W>(T, NT, p, di);
             }
         }
-        if (h == 0) T.piv[i] = c;
-        nxt++;
+        if (h == p) {
+            asg = true;
+            T.piv[p] = c;
+        }
         __syncthreads();
     }
-    return __syncthreads_count(h < n && T.piv[h] < n);
+    // sort by pivot: rank = number of pivots in smaller columns
+    if (h < 2 * W) S.occ1[h] = 0;
+    __syncthreads();
+    const int pv = h < n ? T.piv[h] : INF;
+    if (h < n) {
+        const int wi = pv < n ? (pv >> 6) : W + ((pv - n) >> 6);
+        const int b = pv < n ? (pv & 63) : ((pv - n) & 63);
+        atomicOr(reinterpret_cast<unsigned long long*>(&S.occ1[wi]), 1ull << b);
+    }
+    __syncthreads();
+    int rank = h, rx = 0;
+#pragma unroll 1
+    for (int w = 0; w < W; w++) rx += __popcll(S.occ1[w]);
+    if (h < n) {
+        const int wi = pv < n ? (pv >> 6) : W + ((pv - n) >> 6);
+        const int b = pv < n ? (pv & 63) : ((pv - n) & 63);
+        rank = __popcll(S.occ1[wi] & ((1ull << b) - 1));
+#pragma unroll 1
+        for (int w = 0; w < wi; w++) rank += __popcll(S.occ1[w]);
+    }
+    if (__syncthreads_or(rank != h)) {
+        // scratch: the Clifford kernel has d0x/d0e free, the measurement kernel
+        // (which keeps the old destabilizers there) has A free
+        uint64_t* t64 = TRACK_A ? T.d0x : T.A;
+        uint32_t* t32 = TRACK_A ? T.d0e : reinterpret_cast<uint32_t*>(T.A);
+        cta_permute64<W>(T.mx, t64, NT, h, n, rank);
+        cta_permute64<W>(T.mz, t64, NT, h, n, rank);
+        cta_permute64<W>(T.dx, t64, NT, h, n, rank);
+        cta_permute64<W>(T.dz, t64, NT, h, n, rank);
+        if (TRACK_A) cta_permute64<W>(T.A, t64, NT, h, n, rank);
+        cta_permute32(T.de, t32, h, n, rank);
+        cta_permute32(T.t0, t32, h, n, rank);
+        cta_permute32(T.t1, t32, h, n, rank);
+        cta_permute32(reinterpret_cast<uint32_t*>(T.piv), t32, h, n, rank);
+    }
+    return rx;
 }
 
 template <int W>
@@ -363,8 +468,12 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
             T.t1[h] = 0;
         }
         __syncthreads();
-        const int start = two ? min(q0, q1) : q0;
-        r = cta_gj<W, true>(T, n, NT, start, S);
+        // Pauli gates flip signs only: M keeps its bits and stays in RREF
+        if (kind < 3 || kind > 5) r = cta_rref<W, true>(T, n, NT, S);
+        if (r < 0) {
+            if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 9u);
+            return;
+        }
         // denominator: <y| D'^{t1} phi_0(M')>
         if (h < W) S.y[h] = (yq >= 0 && h == (yq >> 6)) ? (1ull << (yq & 63)) : 0ull;
         __syncthreads();
@@ -518,7 +627,11 @@ __global__ void __launch_bounds__(1024) k_measure_prep(SfDev d, uint32_t q, int 
     }
     T.piv[h] = 0x7fffffff;
     __syncthreads();
-    const int r = cta_gj<W, false>(T, n, NT, 0, S);
+    const int r = cta_rref<W, false>(T, n, NT, S);
+    if (r < 0) {
+        if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 10u);
+        return;
+    }
     const int den0 = cta_amp_phi<W>(T, n, NT, r, T.t0, S.y, S);
     const int den1 = cta_amp_phi<W>(T, n, NT, r, T.t1, S.y2, S);
     if (den0 < 0 || den1 < 0) {

@@ -1,9 +1,10 @@
 // sf_tableau_warp.cu -- the Clifford tableau kernel (ROTATE(F, U) on M and D,
 // Invariant 1 repair, global-phase update; Sec. III, Table 2) for n <= 63,
 // run by a single warp.  Lane L keeps tableau rows L and L + 32 in registers;
-// the pivot search is two ballots, row swaps and the pivot broadcast are
-// shuffles, and the destabilizer products of the dual row operations are warp
-// butterflies -- no shared memory and no block barrier.  Same results, bit for
+// the reduction (sfw::warp_rref) accepts clean leading columns with warp
+// reductions, pivots are broadcast by shuffles, the destabilizer products of
+// the dual row operations are warp butterflies, and one shared-memory
+// permutation sorts the rows.  Same algorithm, and the same results bit for
 // bit, as the block kernel of sf_tableau.cu.
 #include "sf_warp.cuh"
 
@@ -11,6 +12,7 @@ namespace {
 using namespace sfw;
 
 __global__ void __launch_bounds__(32) k_clifford_warp(SfDev d, const sf_gate_rec* gates, int ng, int buf) {
+    __shared__ Row stage[64];
     if (*d.status) return;
     const int n = d.n, lane = threadIdx.x;
     Row r[2];
@@ -69,8 +71,9 @@ __global__ void __launch_bounds__(32) k_clifford_warp(SfDev d, const sf_gate_rec
                 r[hf].t1 = 0;
             }
         }
-        rx = warp_gj(r, n, two ? min(q0, q1) : q0);
-        const int dq = warp_amp_phi(r, n, rx, true, yq >= 0 ? (1ull << yq) : 0ull);
+        // Pauli gates flip signs only: M keeps its bits and stays in RREF
+        if (kind < 3 || kind > 5) rx = warp_rref(r, n, stage);
+        const int dq = rx < 0 ? -1 : warp_amp_phi(r, n, rx, true, yq >= 0 ? (1ull << yq) : 0ull);
         if (dq < 0) {
             if (lane == 0) set_status(d.status, SF_ST_INTERNAL, buf, 8u);
             return;

@@ -115,67 +115,6 @@ __device__ __forceinline__ int warp_amp_phi_sel(const Row* r, int n, int rx, int
     return (qe + __popcll(qx & qz) + 2 * __popcll(qz & w) + pe + __popcll(px & pz)) & 3;
 }
 
-// Gauss-Jordan from column `start` (rows with pivot < start keep theirs), with
-// the dual destabilizer updates and the affine-map / sign-vector tracking of
-// the block version.  Returns r.
-static __device__ int warp_gj(Row* r, int n, int start) {
-    const int lane = threadIdx.x & 31;
-    int nxt = __popc(__ballot_sync(SF_FULL, lane < n && r[0].piv < start)) +
-              __popc(__ballot_sync(SF_FULL, lane + 32 < n && r[1].piv < start));
-    for (int c = start; c < 2 * n && nxt < n; c++) {
-        const unsigned a0 = __ballot_sync(SF_FULL, lane < n && colbit(r[0], c, n));
-        const unsigned a1 = __ballot_sync(SF_FULL, lane + 32 < n && colbit(r[1], c, n));
-        const uint64_t all = (uint64_t)a0 | ((uint64_t)a1 << 32);
-        const uint64_t mask = all & (~0ull << nxt);  // candidate rows: not yet pivots
-        if (!mask) continue;
-        const int p = __ffsll((long long)mask) - 1;
-        if (p == nxt && all == (1ull << nxt)) {  // already reduced: the row keeps its pivot
-            if (lane == (nxt & 31)) r[nxt >> 5].piv = c;
-            nxt++;
-            continue;
-        }
-        if (p != nxt) {
-            const Row rp = fetch_row(r, p), rn = fetch_row(r, nxt);
-            if (lane == (p & 31)) r[p >> 5] = rn;
-            if (lane == (nxt & 31)) r[nxt >> 5] = rp;
-        }
-        const Row pv = fetch_row(r, nxt);
-        uint64_t dx = 0, dz = 0;
-        int de = 0;
-        bool any = false;
-        for (int hf = 0; hf < 2; hf++) {
-            const int row = lane + 32 * hf;
-            if (row < n && row != nxt && colbit(r[hf], c, n)) {
-                const uint32_t cb = (uint32_t)(lam1(r[hf].mx, r[hf].mz, pv.mx, pv.mz) >> 1) & 1u;
-                r[hf].mx ^= pv.mx;
-                r[hf].mz ^= pv.mz;
-                r[hf].A ^= pv.A;
-                r[hf].t0 ^= pv.t0 ^ cb;
-                r[hf].t1 ^= pv.t1 ^ cb;
-                pmul1(dx, dz, de, r[hf].dx, r[hf].dz, (int)r[hf].de);
-                any = true;
-            }
-        }
-        if (__any_sync(SF_FULL, any)) {
-            warp_prod(dx, dz, de);
-            if (lane == (nxt & 31)) {
-                Row& t = r[nxt >> 5];
-                uint64_t x = t.dx, z = t.dz;
-                int e = (int)t.de;
-                pmul1(x, z, e, dx, dz, de);
-                t.dx = x;
-                t.dz = z;
-                t.de = (uint32_t)e;
-            }
-        }
-        if (lane == (nxt & 31)) r[nxt >> 5].piv = c;
-        nxt++;
-    }
-    return __popc(__ballot_sync(SF_FULL, lane < n && r[0].piv < n)) +
-           __popc(__ballot_sync(SF_FULL, lane + 32 < n && r[1].piv < n));
-}
-
-
 // ---- Invariant 1 repair without row movement --------------------------------
 // The same row reduction with the rows left in place while pivots are chosen:
 // every unassigned row whose leading column holds no other 1 in the whole
@@ -186,7 +125,8 @@ static __device__ int warp_gj(Row* r, int n, int start) {
 // D_p <- D_p D_h, and the affine / sign tracking).  A final permutation sorts
 // the rows by pivot.  The canonical M is the unique RREF of the row space;
 // the destabilizers may differ from a reduction that swaps rows, which
-// changes the internal labels but not the state any element stands for.
+// changes the internal labels but not the state any element stands for.  The
+// block kernel of sf_tableau.cu runs the same algorithm.
 // `stage` is 64 rows of shared memory owned by the calling warp.  Returns r,
 // or -1 if a row has no bits left (dependent rows: a broken tableau).
 __device__ __forceinline__ int lead_col(uint64_t mx, uint64_t mz, int n) {

@@ -82,7 +82,9 @@ def test_random_clifford_t_n8_amplitudes_vs_dense(sfm, seed):
     assert np.max(np.abs(amps - d.state())) <= TOL
 
 
-@pytest.mark.parametrize("n,seed", [(3, 0), (6, 1), (7, 2), (12, 3), (33, 4), (64, 5), (65, 6), (100, 7)])
+@pytest.mark.parametrize("n,seed", [(3, 0), (6, 1), (7, 2), (12, 3), (33, 4), (64, 5), (65, 6), (100, 7),
+                                    (127, 8), (128, 9), (129, 10), (256, 11), (257, 12), (513, 13),
+                                    (1000, 14), (1024, 15)])
 def test_all_kinds_mixed(sfm, n, seed):
     """All nine Clifford kinds, single and batched, with T, T-dagger, phase and
     controlled-phase gates interleaved; n spans one and several words."""
@@ -189,6 +191,22 @@ def test_cuccaro_7bit_sampling(sfm):
 def test_measurement_parity(sfm, seed):
     n = 8
     ops = c.random_clifford_t(n, 120, 4, seed) + c.cuccaro_sample_ops(3, seed)[:n]
+    g, o = run_both(sfm, n, ops, cap=1 << 10)
+    frames_equal(g, o)
+
+
+@pytest.mark.parametrize("n,seed", [(64, 0), (130, 1), (300, 2), (1024, 3)])
+def test_measurement_wide(sfm, n, seed):
+    """Random and deterministic measurements with collapse on multi-word
+    tableaux up to the largest n, interleaved with Clifford and T gates."""
+    g0 = c.rng_for(2000 + seed)
+    ops = []
+    for blk in range(5):
+        ops += c.random_clifford(n, 30, seed * 10 + blk, kinds=(c.H, c.S, c.CNOT, c.CZ, c.SWAP))
+        q = int(g0.integers(n))
+        ops += [("C", c.H, q, 0), ("N", c.T, q, 0, 0.0), ("K",)]
+        for _ in range(2):
+            ops.append(("M", int(g0.integers(n)), float(g0.random())))
     g, o = run_both(sfm, n, ops, cap=1 << 10)
     frames_equal(g, o)
 
