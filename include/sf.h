@@ -80,6 +80,10 @@ enum { SF_T = 0,      /* diag(1, e^{i pi/4}) on q0 */
  * tableau.  Synchronises. */
 sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf_handle* out);
 
+/* Device bytes that sf_create(n_qubits, max_elems, ...) allocates (0 for
+ * arguments sf_create rejects).  For admission control. */
+uint64_t sf_footprint_bytes(uint32_t n_qubits, uint64_t max_elems);
+
 /* Free all device and host memory of the handle.  Synchronises. */
 sf_status sf_destroy(sf_handle h);
 
@@ -320,6 +324,69 @@ sf_status sf_campaign_get_shape(sf_campaign c, uint32_t* threads_per_circuit, ui
  * temporary device buffers for the outputs.  Synchronises. */
 sf_status sf_campaign_autotune(sf_campaign c, const sf_op* dev_ops, const uint64_t* dev_offsets,
                                uint32_t n_circuits, double drop_eps, uint32_t reps, float* best_ms);
+
+/* ---- Serving: continuous batching of circuits over resident frames ---------
+ * A request is one circuit: qubit count, frame capacity, an sf_op program
+ * (the record kinds of the campaign engine: Clifford gates, merged diagonal
+ * gates, measurements with caller draws, conditional Clifford gates) and up to
+ * SF_SERVER_MAX_PROBES basis states whose amplitudes <x|Psi> are returned.
+ * sf_server_submit queues it and returns at once.  Up to max_active requests
+ * run at a time, each on its own host worker and CUDA stream with its frame
+ * resident on the device from the first gate batch to the last; a queued
+ * request is admitted as soon as a slot is free and its device footprint
+ * (sf_footprint_bytes) fits in the HBM budget next to what the slots hold, in
+ * arrival order except that a request that does not fit may be passed by later
+ * ones (at most 8 times).  Slots keep their frame handle for the next request
+ * of the same qubit count and no larger capacity.  Results are the ones
+ * sf_create ... sf_apply_* ... sf_amplitude give for the circuit alone. */
+#define SF_SERVER_MAX_PROBES 4
+
+typedef struct {
+    uint32_t n_qubits;      /* 1..1024 */
+    uint32_t n_probes;      /* 0..SF_SERVER_MAX_PROBES */
+    uint64_t max_elems;     /* frame capacity, as for sf_create */
+    double drop_eps;        /* merge threshold of every diagonal gate */
+    const sf_op* ops;       /* host, n_ops records; copied by sf_server_submit */
+    uint64_t n_ops;
+    const uint64_t* probes; /* host, n_probes x ceil(n_qubits/64) words; copied */
+} sf_request;
+
+typedef struct {
+    uint64_t id;
+    int32_t status;         /* sf_status of the run */
+    uint32_t n_meas;
+    uint64_t outcomes;      /* bit m = outcome of measurement m */
+    uint64_t k_final;       /* final frame size */
+    double t_submit, t_start, t_done;  /* seconds on the server clock */
+    uint32_t n_probes;
+    uint32_t pad;
+    double amp[2 * SF_SERVER_MAX_PROBES];  /* (re, im) of <probe_p|Psi> */
+} sf_result;
+
+typedef struct {
+    uint32_t queued, active;
+    uint64_t bytes_in_use, submitted, completed;
+} sf_server_stats;
+
+typedef struct sf_server_s* sf_server;
+
+/* max_active (1..256) slots on the current device, HBM budget in bytes for
+ * the frames the slots hold.  Starts the workers. */
+sf_status sf_server_create(uint64_t hbm_budget_bytes, uint32_t max_active, sf_server* out);
+/* Queue a request (thread-safe, does not wait); *id (nullable) receives its
+ * id.  SF_ENOMEM if its footprint exceeds the whole budget. */
+sf_status sf_server_submit(sf_server s, const sf_request* r, uint64_t* id);
+/* Move up to max_results completed results (in completion order) to out;
+ * returns how many.  Does not wait. */
+uint32_t sf_server_poll(sf_server s, sf_result* out, uint32_t max_results);
+/* Wait until every submitted request has completed (timeout_s < 0: no limit;
+ * SF_ETIMEOUT when it runs out). */
+sf_status sf_server_wait(sf_server s, double timeout_s);
+sf_status sf_server_stats_get(sf_server s, sf_server_stats* st);
+/* Seconds since sf_server_create: the clock of t_submit / t_start / t_done. */
+double sf_server_clock(sf_server s);
+/* Stop the workers after their current request and free every frame. */
+sf_status sf_server_destroy(sf_server s);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libsf.so")
-SOURCES = ["sf_tableau.cu", "sf_tableau_warp.cu", "sf_frame.cu", "sf_api.cu", "sf_noalloc.cu", "sf_campaign.cu"]
+SOURCES = ["sf_tableau.cu", "sf_tableau_warp.cu", "sf_frame.cu", "sf_api.cu", "sf_noalloc.cu", "sf_campaign.cu",
+           "sf_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 
@@ -44,7 +45,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         os.makedirs(BUILD, exist_ok=True)
         os.makedirs(LIBDIR, exist_ok=True)
         cc = nvcc()
-        common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+        common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
+                         "-I", INCLUDE, "-I", CSRC]
         common += list(extra_flags)
         procs = []
         objs = []
@@ -63,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         if errors:
             raise RuntimeError("nvcc failed: " + "; ".join(errors))
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"])
+        subprocess.check_call([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static", "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

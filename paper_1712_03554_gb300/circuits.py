@@ -429,6 +429,56 @@ def steane_campaign(n_variants: int = 4096, seed: int = 0, **kw) -> List[List[Op
     return [steane_variant(seed * 1_000_003 + v, **kw) for v in range(n_variants)]
 
 
+# ---- workload 5: a Poisson stream of served circuits ---------------------------------
+SERVING_QUBITS = (16, 64, 256, 1024)
+
+
+def serving_circuit(seed: int, n: int, n_cliff: int, n_t: int) -> List[Op]:
+    """Random Clifford+T circuit: n_cliff gates uniform over {H, S, CNOT} (one-
+    qubit targets and ordered CNOT pairs uniform), n_t T gates at uniform
+    positions on uniform qubits, each followed by a coalesce."""
+    g = rng_for(seed)
+    kinds = g.integers(3, size=n_cliff)
+    qa = g.integers(n, size=n_cliff)
+    qb = g.integers(max(n - 1, 1), size=n_cliff)
+    ops: List[Op] = []
+    for k, a, b in zip(kinds.tolist(), qa.tolist(), qb.tolist()):
+        if k == 2 and n > 1:
+            ops.append(("C", CNOT, a, b + 1 if b >= a else b))
+        else:
+            ops.append(("C", (H, S, H)[k], a, 0))
+    t_pos = sorted(g.choice(n_cliff + 1, size=n_t, replace=True).tolist(), reverse=True)
+    t_q = g.integers(n, size=n_t).tolist()
+    for p, q in zip(t_pos, t_q):
+        ops[p:p] = [("N", T, q, 0, 0.0), ("K",)]
+    return ops
+
+
+def serving_stream(n_requests: int, rate_hz: float, seed: int = 0, qubits: Sequence[int] = SERVING_QUBITS,
+                   cliff_range=(1000, 100000), max_t: int = 20, n_probes: int = 4):
+    """A seeded Poisson stream of requests: exponential inter-arrival times of
+    mean 1/rate_hz; n uniform over `qubits`; the Clifford count log-uniform in
+    cliff_range; the T count uniform in 0..max_t; frame capacity
+    2^min(T, n + 1, 20) (each T at most doubles the frame, and a frame on n
+    qubits holds at most 2^n elements before a branch doubles it); probes:
+    |0...0> and uniform basis states.  Returns dicts with arrival (s), n, ops,
+    max_elems, probes."""
+    g = rng_for(seed)
+    t = 0.0
+    out = []
+    lo, hi = math.log(cliff_range[0]), math.log(cliff_range[1])
+    for i in range(n_requests):
+        t += float(g.exponential(1.0 / rate_hz))
+        n = int(qubits[int(g.integers(len(qubits)))])
+        n_cliff = int(round(math.exp(g.uniform(lo, hi))))
+        n_t = int(g.integers(0, max_t + 1))
+        probes = [0] + [int(x) for x in (int(g.integers(1 << 62)) for _ in range(n_probes - 1))]
+        probes = [p & ((1 << n) - 1) for p in probes]
+        out.append({"arrival": t, "n": n, "ops": serving_circuit(seed * 7919 + i, n, n_cliff, n_t),
+                    "max_elems": 1 << min(n_t, n + 1, 20), "probes": probes})
+    return out
+
+
 def count_ops(ops: Sequence[Op]):
     c = {"C": 0, "N": 0, "K": 0, "M": 0, "Q": 0}
     for op in ops:

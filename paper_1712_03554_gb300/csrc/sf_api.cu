@@ -69,15 +69,73 @@ int pow2_at_least(int v) {
     return p;
 }
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// handle's stream): creating or destroying a handle, or growing its gate
+// buffer, never waits for kernels of other handles, so handles driven from
+// several host threads overlap on the GPU.  Freed blocks stay in the device's
+// default pool (release threshold raised once per process) for the next handle.
+void keep_pool_memory() {
+    static const bool once = [] {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        return true;
+    }();
+    (void)once;
+}
+
 template <typename T>
 cudaError_t dalloc(sf_handle h, T** p, size_t count) {
     void* v = nullptr;
-    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    cudaError_t e = cudaMallocAsync(&v, std::max<size_t>(count, 1) * sizeof(T), h->stream);
     if (e == cudaSuccess) {
         h->dallocs.push_back(v);
         *p = static_cast<T*>(v);
     }
     return e;
+}
+
+// Pinned host buffers come from a process-wide pool of power-of-two blocks that
+// are never returned to the driver (freeing pinned memory synchronises the
+// whole device).
+std::mutex g_pin_mu;
+std::vector<std::vector<void*>> g_pin_free(64);
+
+int pin_class(size_t bytes) {
+    int c = 6;
+    while ((size_t(1) << c) < bytes) c++;
+    return c;
+}
+
+cudaError_t pinned_alloc(void** p, size_t bytes) {
+    const int c = pin_class(bytes);
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pin_free[c].empty()) {
+            *p = g_pin_free[c].back();
+            g_pin_free[c].pop_back();
+            return cudaSuccess;
+        }
+    }
+    return cudaMallocHost(p, size_t(1) << c);
+}
+
+template <typename T>
+cudaError_t pinned_alloc_n(T** p, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = pinned_alloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    *p = static_cast<T*>(v);
+    return e;
+}
+
+template <typename T>
+void pinned_free(T* p, size_t count) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free[pin_class(std::max<size_t>(count, 1) * sizeof(T))].push_back(static_cast<void*>(p));
 }
 
 const char* status_text(uint32_t code) {
@@ -211,6 +269,7 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     if (max_elems < 1 || max_elems > (1ull << 31)) return fail(nullptr, SF_EINVAL, "max_elems must be in [1, 2^31]");
     sf_handle h = new (std::nothrow) sf_frame_s();
     if (!h) return fail(nullptr, SF_ENOMEM, "host allocation failed");
+    keep_pool_memory();
     h->n = n_qubits;
     h->Wabi = (int)((n_qubits + 63) / 64);
     h->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -279,12 +338,12 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     if (wsb > 200 * 1024) SF_ALLOC(h->gws, (wsb + 7) / 8);
 #undef SF_ALLOC
     h->hstage_cap = 256;
-    if (cudaMallocHost(&h->hstage, h->hstage_cap * sizeof(sf_gate_rec)) != cudaSuccess ||
-        cudaMallocHost(&h->hy, W * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMallocHost(&h->hk, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&h->hstatus, sizeof(uint32_t)) != cudaSuccess ||
-        cudaMallocHost(&h->hout, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&h->hmeta, 4 * sizeof(int32_t)) != cudaSuccess ||
+    if (pinned_alloc_n(&h->hstage, h->hstage_cap) != cudaSuccess ||
+        pinned_alloc_n(&h->hy, W) != cudaSuccess ||
+        pinned_alloc_n(&h->hk, 2) != cudaSuccess ||
+        pinned_alloc_n(&h->hstatus, 1) != cudaSuccess ||
+        pinned_alloc_n(&h->hout, 8) != cudaSuccess ||
+        pinned_alloc_n(&h->hmeta, 4) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
         sf_destroy(h);
         return fail(nullptr, SF_ENOMEM, "pinned host allocation failed");
@@ -318,14 +377,15 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
 
 sf_status sf_destroy(sf_handle h) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
-    if (h->stream || true) cudaStreamSynchronize(h->stream);
-    for (void* p : h->dallocs) cudaFree(p);
-    if (h->hstage) cudaFreeHost(h->hstage);
-    if (h->hy) cudaFreeHost(h->hy);
-    if (h->hk) cudaFreeHost(h->hk);
-    if (h->hstatus) cudaFreeHost(h->hstatus);
-    if (h->hout) cudaFreeHost(h->hout);
-    if (h->hmeta) cudaFreeHost(h->hmeta);
+    cudaStreamSynchronize(h->stream);  // pending copies may still use the pinned buffers
+    for (void* p : h->dallocs) cudaFreeAsync(p, h->stream);
+    cudaStreamSynchronize(h->stream);
+    pinned_free(h->hstage, h->hstage_cap);
+    pinned_free(h->hy, (size_t)h->d.W);
+    pinned_free(h->hk, 2);
+    pinned_free(h->hstatus, 1);
+    pinned_free(h->hout, 8);
+    pinned_free(h->hmeta, 4);
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -352,22 +412,21 @@ sf_status sf_apply_clifford(sf_handle h, const sf_gate* gates, uint64_t n_gates)
     // the previous staging copy must have left the pinned buffer
     SF_CK(h, cudaEventSynchronize(h->stage_ev));
     if (n_gates > h->hstage_cap) {
-        cudaFreeHost(h->hstage);
+        pinned_free(h->hstage, h->hstage_cap);
         h->hstage = nullptr;
         size_t c = h->hstage_cap;
         while (c < n_gates) c *= 2;
-        SF_CK(h, cudaMallocHost(&h->hstage, c * sizeof(sf_gate_rec)));
+        SF_CK(h, pinned_alloc_n(&h->hstage, c));
         h->hstage_cap = c;
     }
-    if (n_gates > h->dgates_cap) {
-        SF_CK(h, cudaStreamSynchronize(h->stream));
+    if (n_gates > h->dgates_cap) {  // stream-ordered: earlier launches still read the old buffer
         size_t c = h->dgates_cap;
         while (c < n_gates) c *= 2;
         sf_gate_rec* p = nullptr;
-        SF_CK(h, cudaMalloc(&p, c * sizeof(sf_gate_rec)));
+        SF_CK(h, cudaMallocAsync(&p, c * sizeof(sf_gate_rec), h->stream));
         auto it = std::find(h->dallocs.begin(), h->dallocs.end(), (void*)h->dgates);
         if (it != h->dallocs.end()) {
-            cudaFree(*it);
+            cudaFreeAsync(*it, h->stream);
             *it = p;
         }
         h->dgates = p;
@@ -509,9 +568,10 @@ sf_status sf_get_tableau(sf_handle h, uint64_t* x, uint64_t* z, uint32_t* n_xblo
     const size_t n = h->n, W = h->d.W;
     std::vector<uint64_t> bx(W * n), bz(W * n);
     int32_t r = 0;
-    SF_CK(h, cudaMemcpy(bx.data(), h->d.mx, W * n * 8, cudaMemcpyDeviceToHost));
-    SF_CK(h, cudaMemcpy(bz.data(), h->d.mz, W * n * 8, cudaMemcpyDeviceToHost));
-    SF_CK(h, cudaMemcpy(&r, h->d.meta, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    SF_CK(h, cudaMemcpyAsync(bx.data(), h->d.mx, W * n * 8, cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaMemcpyAsync(bz.data(), h->d.mz, W * n * 8, cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaMemcpyAsync(&r, h->d.meta, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaStreamSynchronize(h->stream));
     for (size_t row = 0; row < n; row++)
         for (int w = 0; w < h->Wabi; w++) {
             x[row * h->Wabi + w] = bx[w * n + row];
@@ -538,8 +598,9 @@ sf_status sf_get_frame(sf_handle h, uint64_t* sigma, double* amp, uint64_t capac
     const size_t W = h->d.W;
     std::vector<uint64_t> xs(kk * W);
     std::vector<double> xa(2 * kk);
-    SF_CK(h, cudaMemcpy(xs.data(), h->d.sig[stage], kk * W * 8, cudaMemcpyDeviceToHost));
-    SF_CK(h, cudaMemcpy(xa.data(), h->d.amp[stage], kk * 16, cudaMemcpyDeviceToHost));
+    SF_CK(h, cudaMemcpyAsync(xs.data(), h->d.sig[stage], kk * W * 8, cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaMemcpyAsync(xa.data(), h->d.amp[stage], kk * 16, cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaStreamSynchronize(h->stream));
     std::vector<uint64_t> idx(kk);
     std::iota(idx.begin(), idx.end(), 0ull);
     std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) {
@@ -582,10 +643,11 @@ sf_status sf_get_internal(sf_handle h, uint64_t* dx, uint64_t* dz, uint32_t* de,
     if (st) return st;
     const size_t n = h->n, W = h->d.W;
     std::vector<uint64_t> bx(W * n), bz(W * n);
-    SF_CK(h, cudaMemcpy(bx.data(), h->d.dx, W * n * 8, cudaMemcpyDeviceToHost));
-    SF_CK(h, cudaMemcpy(bz.data(), h->d.dz, W * n * 8, cudaMemcpyDeviceToHost));
-    SF_CK(h, cudaMemcpy(de, h->d.de, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-    SF_CK(h, cudaMemcpy(g, h->d.g, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    SF_CK(h, cudaMemcpyAsync(bx.data(), h->d.dx, W * n * 8, cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaMemcpyAsync(bz.data(), h->d.dz, W * n * 8, cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaMemcpyAsync(de, h->d.de, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaMemcpyAsync(g, h->d.g, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaStreamSynchronize(h->stream));
     for (size_t row = 0; row < n; row++)
         for (int w = 0; w < h->Wabi; w++) {
             dx[row * h->Wabi + w] = bx[w * n + row];
@@ -615,6 +677,27 @@ sf_status sf_kernel_time(sf_handle h, double* total_ms, uint64_t* launches) {
     *total_ms = tot;
     *launches = h->ev_used;
     return SF_OK;
+}
+
+uint64_t sf_footprint_bytes(uint32_t n_qubits, uint64_t max_elems) {
+    if (n_qubits < 1 || n_qubits > SF_MAX_N || max_elems < 1) return 0;
+    const uint64_t n = n_qubits, cap = max_elems;
+    const uint64_t W = n <= 63 ? 1 : (uint64_t)std::max(2, pow2_at_least((int)((n + 63) / 64)));
+    const uint64_t NT = std::max<uint64_t>(32, (n + 31) / 32 * 32);
+    uint64_t slots = 1024, icap = 64;
+    while (slots < 2 * cap) slots <<= 1;
+    while (icap < 2 * cap) icap <<= 1;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t b = 8 * 4 * W * n + 8 * n                 // tableau rows, signs, pivots
+                 + 2 * (8 * W + 16) * cap               // two frame buffers
+                 + 8 * plan_words((int)n, (int)W)       // plan
+                 + (W > 1 ? 4 * slots : 0) + (8 * W + 16) * slots  // slot table
+                 + 2 * 8 * (W + 1) * icap               // phase-vector indexes
+                 + 32 * (uint64_t)std::max(1, sms) * 4 + 8 * W + 16 * 256 + 4096;
+    const size_t wsb = sf_tableau_smem_bytes((int)n, (int)W, (int)NT);
+    if (wsb > 200 * 1024) b += (wsb + 7) / 8 * 8;
+    return b;
 }
 
 const char* sf_last_error(sf_handle h) {

@@ -1031,11 +1031,10 @@ void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s) {
     }
     const size_t sm = sf_affine_smem_bytes(d.n, d.W);
     SF_DISPATCH(d.W, {
-        static bool attr = false;
-        if (!attr && sm > 48 * 1024) {
-            cudaFuncSetAttribute(k_affine<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
+        // once per kernel, thread-safe (handles may be driven from several host threads)
+        static const bool attr = cudaFuncSetAttribute(k_affine<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      200 * 1024) == cudaSuccess;
+        (void)attr;
         k_affine<WW><<<d.nblk, kThreads, sm, s>>>(d, buf);
     });
 }

@@ -74,14 +74,21 @@ __device__ __forceinline__ void store_d(const Ws<W>& T, int NT, int h, const Pau
     T.de[h] = (uint32_t)p.e;
 }
 
+// v <- v * (v of lane ^ off), one word at a time (no second operand held)
 template <int W>
-__device__ __forceinline__ void shfl_pauli(const Pauli<W>& v, Pauli<W>& o, int off) {
+__device__ __forceinline__ void shfl_mul(Pauli<W>& v, int off) {
+    const int oe = __shfl_xor_sync(SF_FULL, v.e, off);
+    int l = 0;
 #pragma unroll
     for (int w = 0; w < W; w++) {
-        o.x[w] = __shfl_xor_sync(SF_FULL, v.x[w], off);
-        o.z[w] = __shfl_xor_sync(SF_FULL, v.z[w], off);
+        const uint64_t ox = __shfl_xor_sync(SF_FULL, v.x[w], off);
+        const uint64_t oz = __shfl_xor_sync(SF_FULL, v.z[w], off);
+        l += __popcll(v.x[w] & v.z[w]) + __popcll(ox & oz) + 2 * __popcll(v.z[w] & ox) -
+             __popcll((v.x[w] ^ ox) & (v.z[w] ^ oz));
+        v.x[w] ^= ox;
+        v.z[w] ^= oz;
     }
-    o.e = __shfl_xor_sync(SF_FULL, v.e, off);
+    v.e = (v.e + oe + l) & 3;
 }
 
 // Product over all threads of the block of commuting Pauli operators; every
@@ -90,25 +97,16 @@ template <int W>
 __device__ void cta_product(Pauli<W>& v, Scratch<W>& S) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        Pauli<W> o;
-        shfl_pauli<W>(v, o, off);
-        pauli_mul<W>(v, o);
-    }
+    for (int off = 16; off; off >>= 1) shfl_mul<W>(v, off);
     __syncthreads();
     if (lane == 0) S.red[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        Pauli<W> u;
-        if (lane < nw) u = S.red[lane];
-        else pauli_id<W>(u);
+        if (lane < nw) v = S.red[lane];
+        else pauli_id<W>(v);
 #pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            Pauli<W> o;
-            shfl_pauli<W>(u, o, off);
-            pauli_mul<W>(u, o);
-        }
-        if (lane == 0) S.red[kMaxWarps] = u;
+        for (int off = 16; off; off >>= 1) shfl_mul<W>(v, off);
+        if (lane == 0) S.red[kMaxWarps] = v;
     }
     __syncthreads();
     v = S.red[kMaxWarps];
@@ -138,6 +136,7 @@ __device__ int cta_amp_phi(const Ws<W>& T, int n, int NT, int r, const uint32_t*
     uint64_t wv[W];
 #pragma unroll
     for (int w = 0; w < W; w++) wv[w] = y[w] ^ q.x[w];
+    const int qa = q.e + popc_and<W>(q.x, q.z) + 2 * popc_and<W>(q.z, wv);
     Pauli<W> p;
     pauli_id<W>(p);
     if (h < r) {
@@ -149,8 +148,7 @@ __device__ int cta_amp_phi(const Ws<W>& T, int n, int NT, int r, const uint32_t*
 #pragma unroll
     for (int w = 0; w < W; w++) ok &= (p.x[w] == wv[w]);
     if (!ok) return -1;
-    int tot = q.e + popc_and<W>(q.x, q.z) + 2 * popc_and<W>(q.z, wv) + p.e + popc_and<W>(p.x, p.z);
-    return tot & 3;
+    return (qa + p.e + popc_and<W>(p.x, p.z)) & 3;
 }
 
 // Conjugate one row (x, z planes, word-major) by a Clifford gate; returns the
@@ -200,9 +198,10 @@ __device__ __forceinline__ int conj_row(int kind, int q0, int q1, uint64_t* X, u
 // pivots are chosen; every unassigned row whose leading column holds no other
 // 1 in the tableau takes it as pivot at once (Gauss-Jordan would reach it with
 // nothing to eliminate, in any order); otherwise the smallest leading column c
-// among unassigned rows takes one elimination step with the lowest-index
-// unassigned row leading there as pivot p: every other row with bit c gets
-// M_h <- M_h M_p, mirrored as D_p <- D_p D_h, A_h ^= A_p and t_h ^= t_p ^ c.
+// among unassigned rows takes one elimination step, its pivot p being the
+// unassigned row leading at c whose next 1 lies furthest right: every other
+// row with bit c gets M_h <- M_h M_p, mirrored as D_p <- D_p D_h, A_h ^= A_p
+// and t_h ^= t_p ^ c.
 // A final permutation sorts the rows by pivot.  Each gate dirties a few
 // columns, so a gate costs a few block-wide passes instead of one barrier
 // round per column.  Returns r, or -1 if a row has no bits (dependent rows).
@@ -216,6 +215,26 @@ __device__ __forceinline__ int row_lead(const Ws<W>& T, int NT, int h, int n) {
 #pragma unroll 1
     for (int w = 0; w < W; w++) {
         const uint64_t v = T.mz[w * NT + h];
+        if (v) return n + 64 * w + __ffsll((long long)v) - 1;
+    }
+    return 0x7fffffff;
+}
+
+// first 1 of row h after column c (columns x_0..x_{n-1}, z_0..z_{n-1})
+template <int W>
+__device__ __forceinline__ int row_next_lead(const Ws<W>& T, int NT, int h, int n, int c) {
+#pragma unroll 1
+    for (int w = 0; w < W; w++) {
+        uint64_t v = T.mx[w * NT + h];
+        if (c < n && (c >> 6) == w) v &= ~(1ull << (c & 63));
+        if (c < n && (c >> 6) > w) v = 0;
+        if (v) return 64 * w + __ffsll((long long)v) - 1;
+    }
+#pragma unroll 1
+    for (int w = 0; w < W; w++) {
+        uint64_t v = T.mz[w * NT + h];
+        if (c >= n && ((c - n) >> 6) == w) v &= ~(1ull << ((c - n) & 63));
+        if (c >= n && ((c - n) >> 6) > w) v = 0;
         if (v) return n + 64 * w + __ffsll((long long)v) - 1;
     }
     return 0x7fffffff;
@@ -287,35 +306,50 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
             asg = true;
             T.piv[h] = l;
         }
-        // smallest leading column of the unassigned rows; lowest row index on ties
-        const int key = (h < n && !asg && l != INF) ? ((l << 10) | h) : INF;
-        const int wk = __reduce_min_sync(SF_FULL, key);
-        if (lane == 0) S.wmin[0][wid] = wk;
+        // smallest leading column c of the unassigned rows, then the pivot among
+        // the rows leading at c: the one whose next 1 lies furthest right (no
+        // further 1: best), lowest row index on ties -- the other candidates then
+        // keep their own next 1 as lead and no chain of steps follows
+        const int lk = (h < n && !asg && l != INF) ? l : INF;
+        const int wl = __reduce_min_sync(SF_FULL, lk);
+        if (lane == 0) S.wmin[0][wid] = wl;
         __syncthreads();
-        int kmin = INF;
-        for (int i = 0; i < nw; i++) kmin = min(kmin, S.wmin[0][i]);
+        int c = INF;
+        for (int i = 0; i < nw; i++) c = min(c, S.wmin[0][i]);
         const int none_left = __syncthreads_and(asg || h >= n);
-        if (kmin == INF) {
+        if (c == INF) {
             if (!none_left) return -1;  // an unassigned row without bits
             break;
         }
-        const int c = kmin >> 10, p = kmin & 1023;
+        unsigned pk = 0xffffffffu;
+        if (lk == c) {
+            const int nl = row_next_lead<W>(T, NT, h, n, c);
+            pk = ((nl == INF ? 0u : (unsigned)(2047 - nl)) << 10) | (unsigned)h;
+        }
+        const unsigned wp = __reduce_min_sync(SF_FULL, pk);
+        if (lane == 0) S.wmin[1][wid] = (int)wp;
+        __syncthreads();
+        unsigned pmin = 0xffffffffu;
+        for (int i = 0; i < nw; i++) pmin = min(pmin, (unsigned)S.wmin[1][i]);
+        const int p = (int)(pmin & 1023u);
         // elimination step at column c with pivot row p
         const uint64_t* plane = c < n ? T.mx : T.mz;
         const int cc = c < n ? c : c - n;
         const bool el = (h < n) && (h != p) && ((plane[(cc >> 6) * NT + h] >> (cc & 63)) & 1);
         if (el) {
-            uint64_t xh[W], zh[W], xi[W], zi[W];
-#pragma unroll
+            // sign bit of the row product, then the row update, one word at a time
+            int lam = 0;
+#pragma unroll 4
             for (int w = 0; w < W; w++) {
-                xh[w] = T.mx[w * NT + h]; zh[w] = T.mz[w * NT + h];
-                xi[w] = T.mx[w * NT + p]; zi[w] = T.mz[w * NT + p];
+                const uint64_t xh = T.mx[w * NT + h], zh = T.mz[w * NT + h];
+                const uint64_t xi = T.mx[w * NT + p], zi = T.mz[w * NT + p];
+                lam += __popcll(xh & zh) + __popcll(xi & zi) + 2 * __popcll(zh & xi) - __popcll((xh ^ xi) & (zh ^ zi));
             }
-            const uint32_t cbit = (uint32_t)(pauli_lambda<W>(xh, zh, xi, zi) >> 1) & 1u;
-#pragma unroll
+            const uint32_t cbit = (uint32_t)((lam & 3) >> 1) & 1u;
+#pragma unroll 4
             for (int w = 0; w < W; w++) {
-                T.mx[w * NT + h] = xh[w] ^ xi[w];
-                T.mz[w * NT + h] = zh[w] ^ zi[w];
+                T.mx[w * NT + h] ^= T.mx[w * NT + p];
+                T.mz[w * NT + h] ^= T.mz[w * NT + p];
                 if (TRACK_A) T.A[w * NT + h] ^= T.A[w * NT + p];
             }
             T.t0[h] ^= T.t0[p] ^ cbit;
@@ -787,11 +821,10 @@ uint64_t* pick_ws(const SfDev& d, K kern, size_t& smem, uint64_t* gws, int which
     const size_t need = ws_bytes<W>(d.NT);
     if (need <= 200 * 1024) {
         smem = need;
-        static int attr_bytes = 48 * 1024;
-        if ((int)need > attr_bytes) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr_bytes = 200 * 1024;
-        }
+        // once per kernel, thread-safe (handles may be driven from several host threads)
+        static const bool attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      200 * 1024) == cudaSuccess;
+        (void)attr;
         return nullptr;
     }
     smem = 0;

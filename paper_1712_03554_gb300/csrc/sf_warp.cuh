@@ -176,6 +176,16 @@ __device__ __forceinline__ void take_pivot(Row& t, int c, bool with_d, uint64_t 
     t.piv = c;
 }
 
+// pivot preference among the rows leading at column c: the next 1 after c
+// furthest right first (no further 1: best), then the lowest row index
+__device__ __forceinline__ unsigned pivot_key(const Row& a, int c, int n, int row) {
+    uint64_t bx, bz;
+    col_bit(c, n, bx, bz);
+    const int nl = lead_col(a.mx & ~bx, a.mz & ~bz, n);
+    const unsigned rank = nl == 0x7fffffff ? 0u : (unsigned)(2047 - nl);
+    return (rank << 6) | (unsigned)row;
+}
+
 __device__ __forceinline__ int warp_rref(Row* r, int n, Row* stage) {
     const int lane = threadIdx.x & 31;
     constexpr int INF = 0x7fffffff;
@@ -203,9 +213,13 @@ __device__ __forceinline__ int warp_rref(Row* r, int n, Row* stage) {
         const int u0 = (v0 && !asg0) ? l0 : INF, u1 = (v1 && !asg1) ? l1 : INF;
         const int c = __reduce_min_sync(SF_FULL, min(u0, u1));
         if (c == INF) break;
-        // one elimination step at column c
-        const uint64_t cand = (uint64_t)__ballot_sync(SF_FULL, u0 == c) | ((uint64_t)__ballot_sync(SF_FULL, u1 == c) << 32);
-        const int p = __ffsll((long long)cand) - 1;
+        // one elimination step at column c; pivot: the candidate whose next 1
+        // after c lies furthest right (lowest row index on ties), so that the
+        // other candidates keep their own next 1 as lead and no chain of steps
+        // follows
+        const unsigned k0 = u0 == c ? pivot_key(r[0], c, n, lane) : 0xffffffffu;
+        const unsigned k1 = u1 == c ? pivot_key(r[1], c, n, lane + 32) : 0xffffffffu;
+        const int p = (int)(__reduce_min_sync(SF_FULL, min(k0, k1)) & 63u);
         const Row pv = fetch_row(r, p);
         uint64_t dx = 0, dz = 0;
         int de = 0;

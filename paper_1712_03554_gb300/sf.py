@@ -79,6 +79,14 @@ def load(build: bool = True) -> C.CDLL:
         "sf_campaign_destroy": ([H], st),
         "sf_campaign_run": ([H, C.c_void_p, C.c_void_p, u32, dbl] + [C.c_void_p] * 8, st),
         "sf_campaign_ctas": ([H], u32),
+        "sf_footprint_bytes": ([u32, u64], u64),
+        "sf_server_create": ([u64, u32, C.POINTER(C.c_void_p)], st),
+        "sf_server_submit": ([H, C.c_void_p, C.POINTER(C.c_uint64)], st),
+        "sf_server_poll": ([H, C.c_void_p, u32], u32),
+        "sf_server_wait": ([H, dbl], st),
+        "sf_server_stats_get": ([H, C.c_void_p], st),
+        "sf_server_clock": ([H], dbl),
+        "sf_server_destroy": ([H], st),
         "sf_campaign_set_shape": ([H, u32, u32], st),
         "sf_campaign_get_shape": ([H, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)], st),
         "sf_campaign_autotune": ([H, C.c_void_p, C.c_void_p, u32, dbl, u32, C.POINTER(C.c_float)], st),
@@ -245,6 +253,95 @@ class Campaign:
     def close(self):
         if getattr(self, "h", None):
             self.lib.sf_campaign_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SERVER_MAX_PROBES = 4
+
+
+class sf_request(C.Structure):
+    _fields_ = [("n_qubits", C.c_uint32), ("n_probes", C.c_uint32), ("max_elems", C.c_uint64),
+                ("drop_eps", C.c_double), ("ops", C.c_void_p), ("n_ops", C.c_uint64), ("probes", C.c_void_p)]
+
+
+class sf_result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int32), ("n_meas", C.c_uint32), ("outcomes", C.c_uint64),
+                ("k_final", C.c_uint64), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double), ("n_probes", C.c_uint32), ("pad", C.c_uint32),
+                ("amp", C.c_double * (2 * SERVER_MAX_PROBES))]
+
+
+class sf_server_stats(C.Structure):
+    _fields_ = [("queued", C.c_uint32), ("active", C.c_uint32), ("bytes_in_use", C.c_uint64),
+                ("submitted", C.c_uint64), ("completed", C.c_uint64)]
+
+
+def footprint_bytes(n: int, max_elems: int) -> int:
+    return int(load().sf_footprint_bytes(int(n), int(max_elems)))
+
+
+class Server:
+    """Continuous-batching request loop (sf_server_* in include/sf.h): circuits
+    are admitted by HBM footprint onto max_active slots, each with its own
+    stream and resident frame."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int):
+        self.lib = load()
+        h = C.c_void_p()
+        code = self.lib.sf_server_create(int(hbm_budget_bytes), int(max_active), C.byref(h))
+        if code != SF_OK:
+            raise SFError(code, "sf_server_create failed")
+        self.h = h
+
+    def submit(self, n: int, ops, max_elems: int, probes: Sequence[int] = (), drop_eps: float = 1e-12) -> int:
+        """Queue one circuit (ops in the vocabulary of circuits.py, or sf_op
+        records); returns its id."""
+        recs = ops if isinstance(ops, np.ndarray) else encode_program([ops])[0]
+        recs = np.ascontiguousarray(recs, dtype=SF_OP_DTYPE)
+        W = (int(n) + 63) // 64
+        pw = np.concatenate([int_to_words(int(x), W) for x in probes]) if len(probes) else np.zeros(1, np.uint64)
+        req = sf_request(int(n), len(probes), int(max_elems), float(drop_eps),
+                         recs.ctypes.data if len(recs) else None, len(recs), pw.ctypes.data)
+        rid = C.c_uint64()
+        code = self.lib.sf_server_submit(self.h, C.byref(req), C.byref(rid))
+        if code != SF_OK:
+            raise SFError(code, "sf_server_submit failed")
+        return int(rid.value)
+
+    def poll(self, max_results: int = 4096):
+        buf = (sf_result * max_results)()
+        k = self.lib.sf_server_poll(self.h, buf, max_results)
+        out = []
+        for r in buf[:k]:
+            out.append({"id": int(r.id), "status": int(r.status), "n_meas": int(r.n_meas),
+                        "outcomes": int(r.outcomes), "k_final": int(r.k_final), "t_submit": r.t_submit,
+                        "t_start": r.t_start, "t_done": r.t_done,
+                        "amps": [complex(r.amp[2 * p], r.amp[2 * p + 1]) for p in range(r.n_probes)]})
+        return out
+
+    def wait(self, timeout: float = -1.0) -> None:
+        code = self.lib.sf_server_wait(self.h, float(timeout))
+        if code != SF_OK:
+            raise SFError(code, "sf_server_wait")
+
+    def stats(self):
+        st = sf_server_stats()
+        self.lib.sf_server_stats_get(self.h, C.byref(st))
+        return {"queued": st.queued, "active": st.active, "bytes_in_use": st.bytes_in_use,
+                "submitted": st.submitted, "completed": st.completed}
+
+    def clock(self) -> float:
+        return float(self.lib.sf_server_clock(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sf_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -131,3 +131,26 @@ def test_encode_program_fields():
     assert tuple(rec[4])[:2] == (sf.OP_DIAG + c.T, 0)
     with pytest.raises(ValueError):
         sf.encode_program([[("M", 0, None)]])
+
+
+def test_serving_stream_recipe():
+    st = c.serving_stream(40, 10.0, seed=3)
+    arr = [r["arrival"] for r in st]
+    assert all(b > a for a, b in zip(arr, arr[1:]))
+    assert {r["n"] for r in st} <= set(c.SERVING_QUBITS)
+    for r in st:
+        n_c = sum(1 for op in r["ops"] if op[0] == "C")
+        n_t = sum(1 for op in r["ops"] if op[0] == "N")
+        assert 1000 <= n_c <= 100000 and 0 <= n_t <= 20
+        assert r["max_elems"] == 1 << min(n_t, r["n"] + 1, 20)
+        assert r["probes"][0] == 0 and all(0 <= p < (1 << r["n"]) for p in r["probes"])
+    assert c.serving_stream(5, 1.0, seed=1)[3]["ops"] == c.serving_stream(5, 1.0, seed=1)[3]["ops"]
+
+
+def test_server_abi_struct_layouts():
+    import ctypes
+    from paper_1712_03554_gb300 import sf
+    assert ctypes.sizeof(sf.sf_request) == 48
+    assert ctypes.sizeof(sf.sf_result) == 128
+    assert ctypes.sizeof(sf.sf_server_stats) == 32
+    assert sf.SF_OP_DTYPE.itemsize == 24
