@@ -47,10 +47,12 @@ __device__ Ws<W> carve(uint64_t* base, int NT) {
 
 template <int W>
 struct Scratch {
-    Pauli<W> red[kMaxWarps + 1];
     int wmin[2][kMaxWarps];
     uint64_t y[W], y2[W], words[5][W];
     uint64_t occ1[2 * W], occ2[2 * W];  // columns holding >= 1 / >= 2 ones (x words, then z words)
+    uint64_t wx[kMaxWarps][W], wz[kMaxWarps][W], wp[kMaxWarps][W];  // per-warp word totals of a product
+    uint64_t px[W], pz[W], qx[W], qz[W], wv[W];                    // product results, amplitude point
+    int pe, qe, ired[kMaxWarps];
     int iv[8];
     double dv[8];
 };
@@ -74,42 +76,75 @@ __device__ __forceinline__ void store_d(const Ws<W>& T, int NT, int h, const Pau
     T.de[h] = (uint32_t)p.e;
 }
 
-// v <- v * (v of lane ^ off), one word at a time (no second operand held)
-template <int W>
-__device__ __forceinline__ void shfl_mul(Pauli<W>& v, int off) {
-    const int oe = __shfl_xor_sync(SF_FULL, v.e, off);
-    int l = 0;
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-        const uint64_t ox = __shfl_xor_sync(SF_FULL, v.x[w], off);
-        const uint64_t oz = __shfl_xor_sync(SF_FULL, v.z[w], off);
-        l += __popcll(v.x[w] & v.z[w]) + __popcll(ox & oz) + 2 * __popcll(v.z[w] & ox) -
-             __popcll((v.x[w] ^ ox) & (v.z[w] ^ oz));
-        v.x[w] ^= ox;
-        v.z[w] ^= oz;
-    }
-    v.e = (v.e + oe + l) & 3;
+__device__ __forceinline__ uint64_t warp_xor64(uint64_t v) {
+    const unsigned lo = __reduce_xor_sync(SF_FULL, (unsigned)v);
+    const unsigned hi = __reduce_xor_sync(SF_FULL, (unsigned)(v >> 32));
+    return (uint64_t)lo | ((uint64_t)hi << 32);
 }
 
-// Product over all threads of the block of commuting Pauli operators; every
-// thread receives the result.  Commuting factors make the order irrelevant.
+// Ordered product, in row order, of the rows h with sel (Pauli i^{E_h} P(X_h,
+// Z_h) from word-major planes; E null: phase 0) -- word by word, with no
+// per-thread Pauli in registers.  The product P_1 ... P_m is
+//   i^e P(X, Z),  X = xor x_i,  Z = xor z_i,
+//   e = sum_i (e_i + |x_i & z_i|) + 2 sum_{i<j} |z_i & x_j| - |X & Z|  (mod 4)
+// (Table 1 applied factor by factor); the ordered cross term takes a prefix
+// xor of z along the rows: in-warp by a shuffle scan per word, across warps
+// through the per-warp totals.  Results in ox / oz / *oe (shared), visible to
+// every thread on return.
 template <int W>
-__device__ void cta_product(Pauli<W>& v, Scratch<W>& S) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ void cta_rows_product(const uint64_t* X, const uint64_t* Z, const uint32_t* E, int NT, bool sel,
+                                 Scratch<W>& S, uint64_t* ox, uint64_t* oz, int* oe) {
+    const int h = threadIdx.x, lane = h & 31, wid = h >> 5, nw = blockDim.x >> 5;
+    int acc = (sel && E) ? (int)E[h] : 0;
+    int par = 0;
+#pragma unroll 1
+    for (int w = 0; w < W; w++) {
+        const uint64_t x = sel ? X[w * NT + h] : 0ull;
+        const uint64_t z = sel ? Z[w * NT + h] : 0ull;
+        acc += __popcll(x & z);
+        uint64_t inc = z;
 #pragma unroll
-    for (int off = 16; off; off >>= 1) shfl_mul<W>(v, off);
-    __syncthreads();
-    if (lane == 0) S.red[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        if (lane < nw) v = S.red[lane];
-        else pauli_id<W>(v);
-#pragma unroll
-        for (int off = 16; off; off >>= 1) shfl_mul<W>(v, off);
-        if (lane == 0) S.red[kMaxWarps] = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t t = __shfl_up_sync(SF_FULL, inc, off);
+            if (lane >= off) inc ^= t;
+        }
+        par ^= __popcll((inc ^ z) & x) & 1;
+        const uint64_t xt = warp_xor64(x);
+        if (lane == 31) S.wz[wid][w] = inc;
+        if (lane == 0) S.wx[wid][w] = xt;
     }
     __syncthreads();
-    v = S.red[kMaxWarps];
+    // xor of the z totals of the earlier warps, per warp and word
+    for (int t = h; t < nw * W; t += blockDim.x) {
+        const int v = t / W, w = t % W;
+        uint64_t a = 0;
+        for (int u = 0; u < v; u++) a ^= S.wz[u][w];
+        S.wp[v][w] = a;
+    }
+    __syncthreads();
+    if (sel) {
+#pragma unroll 1
+        for (int w = 0; w < W; w++) par ^= __popcll(S.wp[wid][w] & X[w * NT + h]) & 1;
+    }
+    const int tot = __reduce_add_sync(SF_FULL, (acc + 2 * par) & 3);
+    if (lane == 0) S.ired[wid] = tot;
+    if (h < W) {
+        uint64_t a = 0, b = 0;
+        for (int v = 0; v < nw; v++) {
+            a ^= S.wx[v][h];
+            b ^= S.wz[v][h];
+        }
+        ox[h] = a;
+        oz[h] = b;
+    }
+    __syncthreads();
+    if (h == 0) {
+        int e = 0;
+        for (int v = 0; v < nw; v++) e += S.ired[v];
+        for (int w = 0; w < W; w++) e -= __popcll(ox[w] & oz[w]);
+        *oe = e & 3;
+    }
+    __syncthreads();
 }
 
 // OR a per-thread bit (thread h -> bit h) into words[W] (must be zeroed).
@@ -125,30 +160,35 @@ __device__ void cta_bits(bool b, uint64_t* words) {
 
 // <y| D^tau phi_0(M)> * 2^{r/2} as an i-power (0..3), or -1 when it is zero.
 // tau: per-row bits (nullptr = all zero).  y: W words in shared memory.
+// With Q = prod_{tau_h} D_h = i^{q} P(qx, qz): D^tau phi_0 = Q phi_0, whose
+// amplitude at y is the phi_0 amplitude at w = y ^ qx times i^{q + |qx qz| +
+// 2 |qz w|}; phi_0 has support on the row span of the X block, and at w it is
+// i^{|px pz|} 2^{-r/2} for the product P of the X-block rows picked by the
+// pivot bits of w (zero unless px = w).
 template <int W>
 __device__ int cta_amp_phi(const Ws<W>& T, int n, int NT, int r, const uint32_t* tau, const uint64_t* y,
                            Scratch<W>& S) {
     const int h = threadIdx.x;
-    Pauli<W> q;
-    pauli_id<W>(q);
-    if (tau && h < n && tau[h]) load_d<W>(T, NT, h, q);
-    cta_product<W>(q, S);
-    uint64_t wv[W];
-#pragma unroll
-    for (int w = 0; w < W; w++) wv[w] = y[w] ^ q.x[w];
-    const int qa = q.e + popc_and<W>(q.x, q.z) + 2 * popc_and<W>(q.z, wv);
-    Pauli<W> p;
-    pauli_id<W>(p);
+    cta_rows_product<W>(T.dx, T.dz, T.de, NT, tau && h < n && tau[h], S, S.qx, S.qz, &S.qe);
+    if (h < W) S.wv[h] = y[h] ^ S.qx[h];  // w
+    __syncthreads();
+    const uint64_t* wv = S.wv;
+    bool sel = false;
     if (h < r) {
-        int pv = T.piv[h];
-        if ((wv[pv >> 6] >> (pv & 63)) & 1) load_m<W>(T, NT, h, p);
+        const int pv = T.piv[h];
+        sel = (wv[pv >> 6] >> (pv & 63)) & 1;
     }
-    cta_product<W>(p, S);
+    cta_rows_product<W>(T.mx, T.mz, nullptr, NT, sel, S, S.px, S.pz, &S.pe);
     bool ok = true;
-#pragma unroll
-    for (int w = 0; w < W; w++) ok &= (p.x[w] == wv[w]);
+    int tot = S.qe + S.pe;
+#pragma unroll 1
+    for (int w = 0; w < W; w++) {
+        ok &= (S.px[w] == wv[w]);
+        tot += __popcll(S.qx[w] & S.qz[w]) + 2 * __popcll(S.qz[w] & wv[w]) + __popcll(S.px[w] & S.pz[w]);
+    }
+    __syncthreads();  // the scratch words are reused by the next call
     if (!ok) return -1;
-    return (qa + p.e + popc_and<W>(p.x, p.z)) & 3;
+    return tot & 3;
 }
 
 // Conjugate one row (x, z planes, word-major) by a Clifford gate; returns the
@@ -356,15 +396,20 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
             T.t1[h] ^= T.t1[p] ^ cbit;
         }
         if (__syncthreads_or(el)) {
-            Pauli<W> v;
-            pauli_id<W>(v);
-            if (el) load_d<W>(T, NT, h, v);
-            cta_product<W>(v, S);
+            // D_p <- D_p * prod_{eliminated h} D_h
+            cta_rows_product<W>(T.dx, T.dz, T.de, NT, el, S, S.qx, S.qz, &S.qe);
             if (h == p) {
-                Pauli<W> di;
-                load_d<W>(T, NT, p, di);
-                pauli_mul<W>(di, v);
-                store_d<W>(T, NT, p, di);
+                int lam = 0;
+#pragma unroll 1
+                for (int w = 0; w < W; w++) {
+                    const uint64_t ax = T.dx[w * NT + p], az = T.dz[w * NT + p];
+                    const uint64_t bx = S.qx[w], bz = S.qz[w];
+                    lam += __popcll(ax & az) + __popcll(bx & bz) + 2 * __popcll(az & bx) -
+                           __popcll((ax ^ bx) & (az ^ bz));
+                    T.dx[w * NT + p] = ax ^ bx;
+                    T.dz[w * NT + p] = az ^ bz;
+                }
+                T.de[p] = (T.de[p] + (uint32_t)S.qe + (uint32_t)lam) & 3u;
             }
         }
         if (h == p) {
@@ -630,15 +675,19 @@ __global__ void __launch_bounds__(1024) k_measure_prep(SfDev d, uint32_t q, int 
         T.t1[h] = cbit;
     }
     if (__syncthreads_or(el)) {
-        Pauli<W> v;
-        pauli_id<W>(v);
-        if (el) load_d<W>(T, NT, h, v);
-        cta_product<W>(v, S);
+        // D_i <- D_i * prod_{el} D_h
+        cta_rows_product<W>(T.dx, T.dz, T.de, NT, el, S, S.qx, S.qz, &S.qe);
         if (h == 0) {
-            Pauli<W> di;
-            load_d<W>(T, NT, i, di);
-            pauli_mul<W>(di, v);
-            store_d<W>(T, NT, i, di);
+            int lam = 0;
+#pragma unroll 1
+            for (int w = 0; w < W; w++) {
+                const uint64_t ax = T.dx[w * NT + i], az = T.dz[w * NT + i];
+                const uint64_t bx = S.qx[w], bz = S.qz[w];
+                lam += __popcll(ax & az) + __popcll(bx & bz) + 2 * __popcll(az & bx) - __popcll((ax ^ bx) & (az ^ bz));
+                T.dx[w * NT + i] = ax ^ bx;
+                T.dz[w * NT + i] = az ^ bz;
+            }
+            T.de[i] = (T.de[i] + (uint32_t)S.qe + (uint32_t)lam) & 3u;
         }
         __syncthreads();
     }
@@ -706,28 +755,33 @@ __global__ void __launch_bounds__(1024) k_measure_prep(SfDev d, uint32_t q, int 
         for (int w = 0; w < W; w++) { ox[w] = T.d0x[w * NT + hh]; oz[w] = T.d0z[w * NT + hh]; }
         const int oe = (int)T.d0e[hh];
         bool ub = false, vb = false;
-        Pauli<W> p;
-        pauli_id<W>(p);
         if (h < n) {
             ub = (popc_and<W>(ox, me.z) + popc_and<W>(oz, me.x)) & 1;
             vb = (popc_and<W>(ox, de.z) + popc_and<W>(oz, de.x)) & 1;
-            if (ub) p = de;
-            if (vb) pauli_mul<W>(p, me);
         }
         if (h < W) { S.words[1][h] = 0; S.words[2][h] = 0; }
         __syncthreads();
         cta_bits<W>(ub, S.words[1]);
         cta_bits<W>(vb, S.words[2]);
-        cta_product<W>(p, S);
+        // prod_h D'_h^{u_h} M'_h^{v_h} = (prod_u D'_h)(prod_v M'_h): a D'_h and an
+        // M'_k anticommute only for h = k, and that pair is never swapped
+        cta_rows_product<W>(T.dx, T.dz, T.de, NT, ub, S, S.qx, S.qz, &S.qe);
+        cta_rows_product<W>(T.mx, T.mz, nullptr, NT, vb, S, S.px, S.pz, &S.pe);
         if (h < W) {
             pl[cf_u(n, W) + (size_t)hh * W + h] = S.words[1][h];
             pl[cf_v(n, W) + (size_t)hh * W + h] = S.words[2][h];
         }
         if (h == 0) {
             bool ok = true;
-#pragma unroll
-            for (int w = 0; w < W; w++) ok &= (p.x[w] == ox[w]) && (p.z[w] == oz[w]);
-            const int epsq = (oe - p.e + 4) & 3;
+            int lam = 0;
+#pragma unroll 1
+            for (int w = 0; w < W; w++) {
+                const uint64_t ax = S.qx[w], az = S.qz[w], bx = S.px[w], bz = S.pz[w];
+                lam += __popcll(ax & az) + __popcll(bx & bz) + 2 * __popcll(az & bx) - __popcll((ax ^ bx) & (az ^ bz));
+                ok &= ((ax ^ bx) == ox[w]) && ((az ^ bz) == oz[w]);
+            }
+            const int pe = (S.qe + S.pe + lam) & 3;
+            const int epsq = (oe - pe + 4) & 3;
             if (!ok) set_status(d.status, SF_ST_INTERNAL, buf, 5u);
             if (epsq & 1) S.words[3][hh >> 6] |= 1ull << (hh & 63);
             if (epsq & 2) S.y[hh >> 6] |= 1ull << (hh & 63);
