@@ -16,6 +16,13 @@ gate arrays, host->device copies and result reads inside the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
+Two more measurements ride on the same JSON line (rank 0): "batched", the
+Steane fault-injection campaign (4096 variants in one persistent launch, shape
+picked by the library's autotuner) against the one-circuit path, and
+"served", a seeded Poisson stream of random Clifford+T circuits through the
+continuous-batching server against the same stream one at a time, with
+p50/p99 latency.
+
 Multi-GPU: one process per GPU (torchrun), each rank simulates its own QFT
 instance (different seed); no data-path collective ("weak" scaling).
 """
@@ -325,6 +332,119 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# Batched campaign: the Steane [[7,1,3]] fault-injection workload, every
+# variant in one persistent launch, against the one-circuit library path.
+CAMPAIGN_WORKLOAD = ("Steane [[7,1,3]] encode + 3 flagged syndrome rounds + logical T by magic-state "
+                     "injection on 49 qubits; per variant 1-3 Pauli errors, 0-12 coherent T/T-dagger "
+                     "faults, 200-2000 ops, seeded draws for 42 measurements")
+
+
+def campaign_leg(sfm, torch, n_variants: int, plain_sample: int = 16):
+    t0 = time.perf_counter()
+    circuits = c.steane_campaign(n_variants, seed=0)
+    recs, offs = sfm.encode_program(circuits)
+    prep_s = time.perf_counter() - t0
+    eng = sfm.Campaign(c.STEANE_N, 4096)
+    nc = len(circuits)
+    ops = torch.from_numpy(recs.view(np.uint8).copy()).cuda()
+    off = torch.from_numpy(offs.view(np.int64).copy()).cuda()
+    out = eng.outputs(nc)
+    eng.autotune(ops, off, nc, reps=2)
+    threads, smem_index, ctas = eng.shape()
+    eng.launch(ops, off, nc, DROP_EPS, out)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        eng.launch(ops, off, nc, DROP_EPS, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    status = out["status"].cpu().numpy()
+    # end to end: program from pinned host memory, results back to the host
+    h_ops = torch.from_numpy(recs.view(np.uint8).copy()).pin_memory()
+    h_off = torch.from_numpy(offs.view(np.int64).copy()).pin_memory()
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    e2e = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ops.copy_(h_ops, non_blocking=True)
+        off.copy_(h_off, non_blocking=True)
+        eng.launch(ops, off, nc, DROP_EPS, out)
+        for k in out:
+            h_out[k].copy_(out[k], non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e.append(e0.elapsed_time(e1))
+    eng.close()
+    # the plain path: one circuit at a time through the one-circuit library calls
+    t0 = time.perf_counter()
+    for ops_v in circuits[:plain_sample]:
+        f = sfm.Frame(c.STEANE_N, 4096)
+        c.run(f, ops_v)
+        f.sync()
+        f.close()
+    plain_s = time.perf_counter() - t0
+    med = statistics.median(ms)
+    return {"workload": CAMPAIGN_WORKLOAD, "circuits": nc, "ops": int(len(recs)),
+            "circuits_per_s": nc / (med * 1e-3), "ops_per_s": len(recs) / (med * 1e-3), "ms": med,
+            "e2e_circuits_per_s": nc / (statistics.median(e2e) * 1e-3),
+            "e2e_h2d_bytes": int(recs.nbytes + offs.nbytes),
+            "shape": {"threads_per_circuit": threads, "index_in_shared_memory": smem_index, "ctas": ctas,
+                      "chosen_by": "sf_campaign_autotune"},
+            "plain_circuits_per_s": plain_sample / plain_s,
+            "plain_sample": f"first {plain_sample} variants, one at a time through sf_create/sf_apply_*/sf_measure",
+            "speedup_vs_plain": (nc / (med * 1e-3)) / (plain_sample / plain_s),
+            "circuits_failed": int((status != 0).sum()), "host_prep_s": prep_s}
+
+
+# Serving: a seeded Poisson stream of random Clifford+T circuits admitted by
+# HBM footprint (continuous batching) against the same stream one at a time.
+SERVING_WORKLOAD = ("Poisson stream of random Clifford+T circuits, n uniform in {16,64,256,1024}, "
+                    "1e3-1e5 Clifford gates (log-uniform), 0-20 T gates, frames up to 2^20 elements")
+
+
+def _run_stream(sfm, stream, recs, slots, budget):
+    srv = sfm.Server(budget, slots)
+    t0 = srv.clock()
+    ids = []
+    for r, rc in zip(stream, recs):
+        while srv.clock() - t0 < r["arrival"]:
+            time.sleep(0.0002)
+        ids.append(srv.submit(r["n"], rc, r["max_elems"], r["probes"]))
+    srv.wait(900.0)
+    res = {x["id"]: x for x in srv.poll()}
+    srv.close()
+    out = [res[i] for i in ids]
+    lat = np.array([x["t_done"] - x["t_submit"] for x in out])
+    span = max(x["t_done"] for x in out) - min(x["t_submit"] for x in out)
+    return out, {"circuits_per_s": len(out) / span, "p50_latency_s": float(np.percentile(lat, 50)),
+                 "p99_latency_s": float(np.percentile(lat, 99)), "span_s": span,
+                 "failed": int(sum(x["status"] != 0 for x in out))}
+
+
+def serving_leg(sfm, n_requests: int, rate_hz: float, slots: int, budget_gb: int = 64):
+    stream = c.serving_stream(n_requests, rate_hz, seed=0)
+    recs = [sfm.encode_program([r["ops"]])[0] for r in stream]
+    budget = budget_gb << 30
+    served, s_stats = _run_stream(sfm, stream, recs, slots, budget)
+    alone, p_stats = _run_stream(sfm, stream, recs, 1, budget)
+    # element order inside a frame follows CTA scheduling, so amplitude sums may
+    # differ in the last bits between runs: compare within the 1e-10 tolerance
+    diff = max((abs(x - y) for a, b in zip(served, alone) for x, y in zip(a["amps"], b["amps"])), default=0.0)
+    same = all(a["status"] == b["status"] and a["k_final"] == b["k_final"] for a, b in zip(served, alone)) \
+        and diff <= 1e-10
+    gates = sum(len(r) for r in recs)
+    return {"workload": SERVING_WORKLOAD, "requests": n_requests, "arrival_rate_hz": rate_hz,
+            "gates_total": int(gates), "max_active": slots, "hbm_budget_gb": budget_gb,
+            "served": s_stats, "plain_one_at_a_time": p_stats,
+            "speedup_circuits_per_s": s_stats["circuits_per_s"] / p_stats["circuits_per_s"],
+            "results_same_alone_and_mixed": same, "max_amp_diff_alone_vs_mixed": diff}
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,6 +454,12 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-campaign", action="store_true", help="skip the batched-campaign leg")
+    ap.add_argument("--campaign-variants", type=int, default=4096)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serving-requests", type=int, default=32)
+    ap.add_argument("--serving-rate", type=float, default=8.0)
+    ap.add_argument("--serving-slots", type=int, default=32)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -571,6 +697,9 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(n, plan, y, updates)
+    batched = None if args.no_campaign else campaign_leg(sf, torch, args.campaign_variants)
+    served = None if args.no_serving else serving_leg(sf, args.serving_requests, args.serving_rate,
+                                                      args.serving_slots)
 
     out = {
         "impl": "gb300", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -589,6 +718,8 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": int(launches_total),
+        "batched": batched,
+        "served": served,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:

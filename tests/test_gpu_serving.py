@@ -80,14 +80,16 @@ def test_results_match_oracle(sfm):
 
 def test_alone_equals_mixed(sfm):
     """One slot (each request alone on the GPU) and eight slots (requests
-    overlapping on the GPU) give bit-identical results."""
+    overlapping on the GPU) give the same results: frame sizes and outcomes
+    exactly, amplitudes within 1e-10 (element order inside a frame follows CTA
+    scheduling, so sums may differ in the last bits)."""
     reqs = small_stream(3, count=16)
     alone = run_server(sfm, reqs, max_active=1)
     mixed = run_server(sfm, reqs, max_active=8)
     for a, m in zip(alone, mixed):
         assert a["status"] == m["status"] == 0
         assert a["k_final"] == m["k_final"] and a["outcomes"] == m["outcomes"]
-        assert a["amps"] == m["amps"]
+        assert np.max(np.abs(np.array(a["amps"]) - np.array(m["amps"]))) <= TOL
     # the mix really overlapped: some request started before another finished
     spans = sorted((m["t_start"], m["t_done"]) for m in mixed)
     assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
