@@ -403,7 +403,8 @@ def campaign_leg(sfm, torch, n_variants: int, plain_sample: int = 16):
 # Serving: a seeded Poisson stream of random Clifford+T circuits admitted by
 # HBM footprint (continuous batching) against the same stream one at a time.
 SERVING_WORKLOAD = ("Poisson stream of random Clifford+T circuits, n uniform in {16,64,256,1024}, "
-                    "1e3-1e5 Clifford gates (log-uniform), 0-20 T gates, frames up to 2^20 elements")
+                    "1e3-1e5 Clifford gates (log-uniform), 0-20 T gates, frames up to 2^20 elements, "
+                    "then 8 measurements with seeded draws; amplitudes of 4 basis states returned")
 
 
 def _run_stream(sfm, stream, recs, slots, budget):
@@ -425,7 +426,7 @@ def _run_stream(sfm, stream, recs, slots, budget):
                  "failed": int(sum(x["status"] != 0 for x in out))}
 
 
-def serving_leg(sfm, n_requests: int, rate_hz: float, slots: int, budget_gb: int = 64):
+def serving_leg(sfm, n_requests: int, rate_hz: float, slots: int, budget_gb: int = 96):
     stream = c.serving_stream(n_requests, rate_hz, seed=0)
     recs = [sfm.encode_program([r["ops"]])[0] for r in stream]
     budget = budget_gb << 30

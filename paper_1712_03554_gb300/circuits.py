@@ -455,7 +455,7 @@ def serving_circuit(seed: int, n: int, n_cliff: int, n_t: int) -> List[Op]:
 
 
 def serving_stream(n_requests: int, rate_hz: float, seed: int = 0, qubits: Sequence[int] = SERVING_QUBITS,
-                   cliff_range=(1000, 100000), max_t: int = 20, n_probes: int = 4):
+                   cliff_range=(1000, 100000), max_t: int = 20, n_probes: int = 4, n_measure: int = 8):
     """A seeded Poisson stream of requests: exponential inter-arrival times of
     mean 1/rate_hz; n uniform over `qubits`; the Clifford count log-uniform in
     cliff_range; the T count uniform in 0..max_t; frame capacity
@@ -474,8 +474,11 @@ def serving_stream(n_requests: int, rate_hz: float, seed: int = 0, qubits: Seque
         n_t = int(g.integers(0, max_t + 1))
         probes = [0] + [int(x) for x in (int(g.integers(1 << 62)) for _ in range(n_probes - 1))]
         probes = [p & ((1 << n) - 1) for p in probes]
-        out.append({"arrival": t, "n": n, "ops": serving_circuit(seed * 7919 + i, n, n_cliff, n_t),
-                    "max_elems": 1 << min(n_t, n + 1, 20), "probes": probes})
+        ops = serving_circuit(seed * 7919 + i, n, n_cliff, n_t)
+        mq = g.choice(n, size=min(n_measure, n), replace=False).tolist()
+        ops += [("M", int(q), float(g.random())) for q in mq]
+        out.append({"arrival": t, "n": n, "ops": ops,
+                    "max_elems": 1 << min(n_t + 1, n + 1, 21), "probes": probes})
     return out
 
 

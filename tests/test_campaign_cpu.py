@@ -142,7 +142,8 @@ def test_serving_stream_recipe():
         n_c = sum(1 for op in r["ops"] if op[0] == "C")
         n_t = sum(1 for op in r["ops"] if op[0] == "N")
         assert 1000 <= n_c <= 100000 and 0 <= n_t <= 20
-        assert r["max_elems"] == 1 << min(n_t, r["n"] + 1, 20)
+        assert r["max_elems"] == 1 << min(n_t + 1, r["n"] + 1, 21)
+        assert [op[0] for op in r["ops"][-8:]] == ["M"] * 8 and len({op[1] for op in r["ops"][-8:]}) == 8
         assert r["probes"][0] == 0 and all(0 <= p < (1 << r["n"]) for p in r["probes"])
     assert c.serving_stream(5, 1.0, seed=1)[3]["ops"] == c.serving_stream(5, 1.0, seed=1)[3]["ops"]
 
