@@ -9,6 +9,9 @@ amplitudes read and written; index and hash tables are not counted).
   python -m paper_1712_03554_gb300.kernel_bench throughput 16 20 24
   python -m paper_1712_03554_gb300.kernel_bench latency
   python -m paper_1712_03554_gb300.kernel_bench merge-case 20   (a short run for ncu captures)
+  python -m paper_1712_03554_gb300.kernel_bench qft-step        (one eager QFT n=20 step, the bench's circuit)
+  python -m paper_1712_03554_gb300.kernel_bench campaign-case 64 (one campaign launch, 32 threads, global index)
+  python -m paper_1712_03554_gb300.kernel_bench clifford-case 1024 (one Clifford batch of 200 gates at n)
 """
 from __future__ import annotations
 
@@ -60,7 +63,7 @@ def throughput(ms_list):
             f.apply_nonclifford_coalesce(c.TDG, m, 0, 0.0, 1e-12)
         ms = timed(f, "branch_merge", tt, 3)
         res["branch_merge_us"] = ms * 1e3
-        res["branch_merge_GBs"] = E * 3 * k / 2 / (ms * 1e-3) / 1e9  # (k in + 2k out, 2k in + k out) / 2
+        res["branch_merge_GBs"] = E * 3 * k / (ms * 1e-3) / 1e9  # per launch: k in + 2k out, or 2k in + k out
 
         def br():
             f.apply_nonclifford(c.T, m, 0, 0.0)
@@ -112,6 +115,39 @@ def merge_case(m):
     print("k", f.size())
 
 
+def qft_step(seed=0):
+    """The bench's step eagerly: QFT n = 20 on a seeded random basis state with
+    merged branching, then the probabilities of qubit 0 and one amplitude."""
+    x, ops = c.qft_random_input(20, seed)
+    f = frame_of(20, 0, 1 << 21)
+    f.reset()
+    c.run(f, ops)
+    f.measure(0, -1)
+    f.amplitude(x)
+    f.sync()
+    print("k", f.size())
+
+
+def campaign_case(nv=64):
+    """One launch of the campaign kernel on nv Steane variants."""
+    eng = sf.Campaign(c.STEANE_N, 4096)
+    eng.set_shape(32, False)
+    res = eng.run(c.steane_campaign(nv, seed=0))
+    print("ok", int((res["status"] != 0).sum()) == 0, "ctas", eng.ctas())
+
+
+def clifford_case(n=1024, gates=200):
+    """One Clifford batch of random H/S/CNOT gates on a scrambled tableau."""
+    ops = c.random_clifford(n, 4000 + gates, seed=n, kinds=(c.H, c.S, c.CNOT))
+    g = [(op[1], op[2], op[3]) for op in ops]
+    f = sf.Frame(n, 64)
+    f.apply_clifford(g[:4000])
+    f.sync()
+    f.apply_clifford(g[4000:])
+    f.sync()
+    print("r", f.tableau()[2])
+
+
 if __name__ == "__main__":
     mode = sys.argv[1] if len(sys.argv) > 1 else "throughput"
     args = [int(a) for a in sys.argv[2:]]
@@ -121,5 +157,11 @@ if __name__ == "__main__":
         latency()
     elif mode == "merge-case":
         merge_case(args[0] if args else 20)
+    elif mode == "qft-step":
+        qft_step()
+    elif mode == "campaign-case":
+        campaign_case(args[0] if args else 64)
+    elif mode == "clifford-case":
+        clifford_case(args[0] if args else 1024)
     else:
         raise SystemExit(f"unknown mode {mode}")
