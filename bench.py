@@ -103,7 +103,72 @@ def bytes_model(W: int, n: int = N_QUBITS):
         "prob": lambda kin, kout: 24 * kin,
         "amplitude": lambda kin, kout: e * kin,
         "reduce": lambda kin, kout: 0,
+        "segment": lambda kin, kout: kin,  # recorded as the summed bytes of the ops it runs
     }
+
+
+def plan_records(sfm, plan):
+    """sf_op records of a plan made of Clifford batches and merged diagonal gates
+    (one record per gate), and the record index at which each plan entry starts."""
+    recs, starts = [], []
+    for op in plan:
+        starts.append(len(recs))
+        if op[0] == "C":
+            recs += [(g[0], g[1], g[2], 0, 0.0) for g in op[1]]
+        elif op[0] == "NK":
+            recs.append((sfm.OP_DIAG + op[1], op[2], op[3], 0, float(op[4])))
+        else:
+            break
+    starts.append(len(recs))
+    return np.array(recs, dtype=sfm.SF_OP_DTYPE), starts
+
+
+def choose_program_prefix(sfm, torch, n, plan, y, stream, candidates=(256, 512, 1024, 2048, 4096)):
+    """The single-CTA program (sf_apply_program) runs the first plan entries while
+    the frame is small; pick its frame limit by timing the eager step for each
+    candidate (and without it).  Returns (max_frame, plan entries, records, the
+    device records)."""
+    recs, starts = plan_records(sfm, plan)
+    d_all = torch.from_numpy(recs.view(np.uint8).copy()).cuda()
+    consumed = torch.zeros(1, dtype=torch.int64, device="cuda")
+    fr = sfm.Frame(n, MAX_ELEMS, stream=stream)
+
+    def run(mf, p, m):
+        with torch.cuda.stream(stream):
+            fr.reset()
+            if m:
+                fr.apply_program_device(d_all.data_ptr(), m, DROP_EPS, 0, 0, mf)
+            for op in plan[p:]:
+                if op[0] == "C":
+                    fr.apply_clifford(op[1])
+                elif op[0] == "NK":
+                    fr.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], DROP_EPS)
+        fr.measure(0, -1)
+        fr.amplitude(y)
+
+    best = None
+    for mf in (0,) + tuple(candidates):
+        p = m = 0
+        if mf:
+            with torch.cuda.stream(stream):
+                fr.reset()
+                fr.apply_program_device(d_all.data_ptr(), len(recs), DROP_EPS, consumed.data_ptr(), 0, mf)
+            fr.sync()
+            m = int(consumed.item())
+            p = max(i for i in range(len(starts)) if starts[i] <= m)
+            m = starts[p]
+        run(mf, p, m)
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            run(mf, p, m)
+            ts.append(time.perf_counter() - t0)
+        t = statistics.median(ts)
+        if best is None or t < best[0]:
+            best = (t, mf, p, m)
+    fr.close()
+    _, mf, p, m = best
+    return mf, p, m, d_all
 
 
 def instrumented_pass(sfm, n, plan, y):
@@ -117,12 +182,14 @@ def instrumented_pass(sfm, n, plan, y):
     k = 1
     peak = 1
     indexed = True  # the index of the current frame is valid (see sf_api.cu)
-    for op in plan:
+    ops_rec = []  # (plan index, class, kin, kout) of every launch of the captured part
+    for pi, op in enumerate(plan):
         if op[0] == "C":
             f.apply_clifford(op[1])
             updates += len(op[1]) * k
             rec["affine"].append((k, k))
             rec["clifford"].append((k, k))
+            ops_rec += [(pi, "affine", k, k), (pi, "clifford", k, k)]
             indexed = False
         elif op[0] == "NK":
             f.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], DROP_EPS)
@@ -131,7 +198,9 @@ def instrumented_pass(sfm, n, plan, y):
             coal_elems += k
             if not indexed:
                 rec["index"].append((k, k))
+                ops_rec.append((pi, "index", k, k))
             rec["branch_merge"].append((k, kout))
+            ops_rec.append((pi, "branch_merge", k, kout))
             indexed = True
             k = kout
         elif op[0] == "N":
@@ -151,6 +220,14 @@ def instrumented_pass(sfm, n, plan, y):
         peak = max(peak, k)
     # the captured (graph) part ends here; the tail is measured eagerly
     graph_rec = {cls: list(v) for cls, v in rec.items()}
+    k_before = [1]  # frame size before each plan entry
+    kk = 1
+    for pi, op in enumerate(plan):
+        k_before.append(kk)
+        for (pj, cls, a, b) in ops_rec:
+            if pj == pi and cls == "branch_merge":
+                kk = b
+    k_before = k_before[1:]
     # measurement of qubit 0 (cofactor + coalesce + probabilities)
     kin = k
     f.measure(0, -1)
@@ -166,7 +243,7 @@ def instrumented_pass(sfm, n, plan, y):
     rec["amplitude"].append((km, km))
     peak = max(peak, 2 * kin)
     f.close()
-    return updates, coal_elems, rec, graph_rec, peak, W
+    return updates, coal_elems, rec, graph_rec, peak, W, ops_rec, k_before
 
 
 def measured_peak_gbs():
@@ -455,6 +532,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-program", action="store_true", help="no single-CTA program for the small-frame prefix")
     ap.add_argument("--no-campaign", action="store_true", help="skip the batched-campaign leg")
     ap.add_argument("--campaign-variants", type=int, default=4096)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
@@ -483,14 +561,31 @@ def main():
     seed = args.seed + rank
     n = N_QUBITS
     x, plan, y = build_plan(n, seed)
-    updates, coal_elems, rec, graph_rec, peak, W = instrumented_pass(sf, n, plan, y)
+    updates, coal_elems, rec, graph_rec, peak, W, ops_rec, k_before = instrumented_pass(sf, n, plan, y)
     model = bytes_model(W, n)
 
     stream = torch.cuda.Stream()
+    # the first plan entries run as one single-CTA program while the frame is small
+    max_frame, p_pre, m_pre, d_prog = (0, 0, 0, None) if args.no_program else \
+        choose_program_prefix(sf, torch, n, plan, y, stream)
+    if p_pre:
+        graph_rec = {cls: [] for cls in graph_rec}
+        seg_bytes = 0
+        for (pi, cls, a, b) in ops_rec:
+            if pi < p_pre:
+                seg_bytes += model[cls](a, b)
+            else:
+                graph_rec[cls].append((a, b))
+        graph_rec["segment"] = [(seg_bytes, 0)]
+        # the program leaves no index: the first merged branch after it builds one
+        if p_pre < len(plan) and plan[p_pre][0] == "NK" and \
+                not any(pi == p_pre and cls == "index" for (pi, cls, a, b) in ops_rec):
+            kk = k_before[p_pre]
+            graph_rec["index"].insert(0, (kk, kk))
     frame = sf.Frame(n, MAX_ELEMS, stream=stream)
     # device-resident gate lists for the graph path
     dev_lists = []
-    for op in plan:
+    for op in plan[p_pre:]:
         if op[0] == "C":
             arr = np.array([[g[0], g[1], g[2], 0] for g in op[1]], dtype=np.uint32)
             t = torch.from_numpy(arr.view(np.int32)).cuda()
@@ -499,8 +594,10 @@ def main():
 
     def async_part(fr):
         fr.reset()
+        if m_pre:
+            fr.apply_program_device(d_prog.data_ptr(), m_pre, DROP_EPS, 0, 0, max_frame)
         di = 0
-        for op in plan:
+        for op in plan[p_pre:]:
             if op[0] == "C":
                 fr.apply_clifford_device(dev_lists[di].data_ptr(), dev_lists[di].shape[0])
                 di += 1
@@ -536,12 +633,16 @@ def main():
     # captured part of the step (where the timed event pairs live)
     graph_classes = [cls for cls in per_class if graph_rec.get(cls)] or list(per_class)
     dominant = max(graph_classes, key=per_class.get)
+    # the streaming kernel with the largest time, when the dominant class is the
+    # latency-bound single-CTA program: its roofline is reported beside
+    hbm_classes = [cls for cls in graph_classes if cls not in ("segment", "clifford")]
+    second = max(hbm_classes, key=per_class.get) if dominant == "segment" and hbm_classes else None
 
     # capture the asynchronous part in CUDA graphs: `graph` for the timed steps,
     # `tgraph` (the same launches with the dominant class bracketed by CUDA
     # events) for the roofline measurement
     use_graph = not args.no_graph
-    graph = tgraph = None
+    graph = tgraph = tgraph2 = None
     token = 0
     if use_graph:
         try:
@@ -566,7 +667,7 @@ def main():
                     raise RuntimeError("graph replay differs from the eager step")
         except Exception as exc:  # fall back to eager launches from the host
             print(f"# graph capture unavailable ({exc}); timing eager launches", file=sys.stderr)
-            graph = tgraph = None
+            graph = tgraph = tgraph2 = None
     if graph is None:
         frame.time_kernel(dominant)
 
@@ -622,21 +723,46 @@ def main():
                 ms, cnt = frame.kernel_time()
                 dom_ms += ms
                 dom_launches += cnt
+        sec_ms, sec_launches = 0.0, 0
+        if second is not None and tgraph is not None:
+            # captured only now: the timing event pairs of a handle are one pool
+            frame.time_kernel(second)
+            async_part(frame)
+            tail(frame)
+            frame.time_kernel(second)
+            tgraph2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(tgraph2, stream=stream):
+                async_part(frame)
+            frame.time_kernel(-1)
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                step(tgraph2)
+                ms, cnt = frame.kernel_time()
+                sec_ms += ms
+                sec_launches += cnt
     clocks = clk.summary()
     # graph replays do not pass through the host launch counter: add the captured kernels
     launches_total = launches_timed  # launched from the host inside the timed steps
     if graph is not None:
-        launches_total += graph_launch_count(plan) * args.steps  # graph replays of the timed steps
+        launches_total += graph_launch_count(plan[p_pre:], start_indexed=not m_pre,
+                                             extra=1 if m_pre else 0) * args.steps  # graph replays
     ms_step = float(np.mean(step_ms))
 
     # e2e: the public API with host gate arrays, eager launches
     e2e_frame = sf.Frame(n, MAX_ELEMS, stream=stream)
-    h2d = 16 * sum(len(op[1]) for op in plan if op[0] == "C") + 8 * e2e_frame.W
+    h2d = 16 * sum(len(op[1]) for op in plan[p_pre:] if op[0] == "C") + 8 * e2e_frame.W + 24 * m_pre
     d2h = 16 + 16
+    if m_pre:
+        h_prog = torch.from_numpy(plan_records(sf, plan)[0][:m_pre].view(np.uint8).copy()).pin_memory()
+        d_prog_e2e = torch.empty_like(h_prog, device="cuda")
 
     def e2e_step():
         e2e_frame.reset()
-        for op in plan:
+        if m_pre:  # the program's records from pinned host memory, then one launch
+            d_prog_e2e.copy_(h_prog, non_blocking=True)
+            e2e_frame.apply_program_device(d_prog_e2e.data_ptr(), m_pre, DROP_EPS, 0, 0, max_frame)
+        for op in plan[p_pre:]:
             if op[0] == "C":
                 e2e_frame.apply_clifford(op[1])
             elif op[0] == "NK":
@@ -692,6 +818,19 @@ def main():
                 "frac": achieved / peak_gbs, "peak_source": peak_src, "traffic": ncu_traffic(dominant),
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_ms * 1e3,
                 "launches_timed": dom_launches}
+    if dominant == "segment":
+        roofline["note"] = ("the dominant kernel is the single-CTA program that runs the small-frame prefix of "
+                            "the step: a serial chain of latency-bound ops, so its HBM fraction is near zero by "
+                            "design; roofline_streaming gives the streaming kernel with the largest time")
+    roofline_streaming = None
+    if second is not None and sec_launches:
+        b2 = sum(model[second](a, b) for a, b in graph_rec[second]) / max(1, len(graph_rec[second]))
+        t2 = sec_ms / sec_launches
+        a2 = b2 / (t2 * 1e-3) / 1e9
+        roofline_streaming = {"bound": "hbm", "kernel": second, "achieved": a2, "peak": peak_gbs, "unit": "GB/s",
+                              "frac": a2 / peak_gbs, "peak_source": peak_src, "traffic": ncu_traffic(second),
+                              "algorithmic_bytes_per_launch": b2, "avg_launch_us": t2 * 1e3,
+                              "launches_timed": sec_launches}
     step_share = {k: round(v / max(1e-9, sum(per_class.values())), 4) for k, v in
                   sorted(per_class.items(), key=lambda kv: -kv[1])}
 
@@ -710,11 +849,14 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between steps (512 MiB write)", "cuda_graph": graph is not None,
                    "updates_per_step": updates, "coalesce_elems_per_step": coal_elems,
+                   "program_prefix": {"plan_entries": p_pre, "records": m_pre, "max_frame": max_frame,
+                                      "of_plan_entries": len(plan), "chosen_by": "eager step timing sweep"},
                    "coalesce_elems_per_s": coal_elems * world / (max_ms * 1e-3), "frame_peak": peak,
                    "wall_s_timed_region": wall},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": max_e2e},
         "roofline": roofline,
+        "roofline_streaming": roofline_streaming,
         "kernel_time_share_eager_step": step_share,
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -729,13 +871,13 @@ def main():
     return 0
 
 
-def graph_launch_count(plan) -> int:
-    """Kernels in the captured part of a step: reset, 2 per Clifford batch
-    (tableau + affine), 1 per unmerged branch, 2 per generic coalesce (insert +
-    compact), 1 per merged branch plus an index build when the previous op
-    left the frame unindexed."""
-    cnt = 1
-    indexed = True
+def graph_launch_count(plan, start_indexed: bool = True, extra: int = 0) -> int:
+    """Kernels in the captured part of a step: reset, the program kernel if any
+    (extra), 2 per Clifford batch (tableau + affine), 1 per unmerged branch, 2
+    per generic coalesce (insert + compact), 1 per merged branch plus an index
+    build when the previous op left the frame unindexed."""
+    cnt = 1 + extra
+    indexed = start_indexed
     for op in plan:
         cnt += {"C": 2, "N": 1, "K": 2, "NK": 1}[op[0]]
         if op[0] == "NK" and not indexed:

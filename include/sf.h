@@ -167,7 +167,9 @@ enum { SF_K_CLIFFORD = 0,      /* tableau update of a Clifford batch (single CTA
        SF_K_COFACTOR = 8,      /* cofactor split merged through the index */
        SF_K_PROB = 9, SF_K_REDUCE = 10, SF_K_AMP_PREP = 11, SF_K_AMPLITUDE = 12,
        SF_K_FILTER = 13,       /* collapse */
-       SF_K_EXPORT = 14, SF_K_RESET = 15, SF_K_COUNT_CLASSES = 16 };
+       SF_K_EXPORT = 14, SF_K_RESET = 15,
+       SF_K_SEGMENT = 16,      /* sf_apply_program (single CTA) */
+       SF_K_COUNT_CLASSES = 17 };
 
 /* Number of CUDA kernels this handle has launched since it was created. */
 uint64_t sf_kernel_launches(sf_handle h);
@@ -266,6 +268,36 @@ typedef struct {
     uint32_t kind, q0, q1, arg;
     double param; /* angle, draw, or mask bits (memcpy of a uint64_t) */
 } sf_op;
+
+/* Largest frame sf_apply_program works on. */
+#define SF_SEGMENT_MAX_ELEMS 16384u
+
+/* A program of sf_op records (the record kinds above:
+ * Clifford gates, merged diagonal gates, measurements with caller draws,
+ * conditional Clifford gates; Sec. III-IV) applied to this handle's frame in
+ * ONE launch of a single-CTA kernel, for handles with n_qubits <= 63: the
+ * tableau is held in one warp's registers and the frame, while it has at most
+ * L = min(max_frame, max_elems, SF_SEGMENT_MAX_ELEMS) elements (max_frame 0:
+ * no extra limit), is branched, merged, cofactored and collapsed in place with
+ * a shared-memory index.  This replaces one or more grid-wide launches per op
+ * while the frame is small; the same frame results as the per-op calls
+ * (amplitudes to rounding).  One CTA is faster than the grid-wide kernels only
+ * for small frames (a few hundred elements on GB300), hence max_frame.
+ *
+ * dev_ops: n_ops records in device memory (valid until the stream reaches the
+ * call).  The records are checked first (qubits, kinds, at most 64
+ * measurements); a bad record fails the call (SF_EINVAL, deferred) with the
+ * frame untouched.  The run stops at an op boundary before a diagonal gate or
+ * random measurement whose intermediate frame could exceed L.
+ * With dev_consumed (device, one uint64) non-NULL the number of records applied
+ * is written there and stopping early is not an error: continue with the
+ * per-op calls from that record.  With dev_consumed NULL, stopping early is
+ * reported as SF_ECAPACITY (deferred), the frame then holding the state after
+ * the records that were applied.  dev_meas (device, two uint64, nullable)
+ * receives the outcome bits of the program's measurements and their count.
+ * Outcomes follow the draw rule of the campaign engine.  Asynchronous. */
+sf_status sf_apply_program(sf_handle h, const sf_op* dev_ops, uint64_t n_ops, double drop_eps,
+                           uint64_t max_frame, uint64_t* dev_consumed, uint64_t* dev_meas);
 
 typedef struct sf_campaign_s* sf_campaign;
 

@@ -238,15 +238,16 @@ def cuccaro_sample_ops(nbits: int, seed: int) -> List[Op]:
 
 
 # ---- driver ------------------------------------------------------------------------
-def run(sim, ops: Sequence[Op], drop_eps: float = 1e-12, batch_cliffords: bool = True):
+def run(sim, ops: Sequence[Op], drop_eps: float = 1e-12, batch_cliffords: bool = True,
+        outcome_bits: int = 0, n_drawn: int = 0):
     """Walk ops against sim.  Consecutive Clifford gates are passed as one batch;
     a non-Clifford gate directly followed by a coalesce goes to
     sim.apply_nonclifford_coalesce when sim has it.  Returns the list of
-    (q, p0, p1, outcome) for every measurement."""
+    (q, p0, p1, outcome) for every measurement.  outcome_bits / n_drawn carry
+    the outcomes of measurements already made on sim (for conditional gates)
+    when a circuit is continued from the middle."""
     pending: List[Tuple[int, int, int]] = []
     results = []
-    outcome_bits = 0
-    n_drawn = 0
 
     def flush():
         if pending:

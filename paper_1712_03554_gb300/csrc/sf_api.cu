@@ -480,6 +480,29 @@ sf_status sf_apply_nonclifford_coalesce(sf_handle h, uint32_t kind, uint32_t q0,
     return SF_OK;
 }
 
+sf_status sf_apply_program(sf_handle h, const sf_op* dev_ops, uint64_t n_ops, double drop_eps,
+                           uint64_t max_frame, uint64_t* dev_consumed, uint64_t* dev_meas) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (h->d.W != 1) return fail(h, SF_EINVAL, "sf_apply_program needs n_qubits <= 63");
+    if (n_ops && !dev_ops) return fail(h, SF_EINVAL, "dev_ops is NULL");
+    if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");
+    if (n_ops == 0) {
+        if (dev_consumed) SF_CK(h, cudaMemsetAsync(dev_consumed, 0, sizeof(uint64_t), h->stream));
+        if (dev_meas) SF_CK(h, cudaMemsetAsync(dev_meas, 0, 2 * sizeof(uint64_t), h->stream));
+        return SF_OK;
+    }
+    uint64_t lim = std::min<uint64_t>(h->d.cap, SF_SEGMENT_MAX_ELEMS);
+    if (max_frame) lim = std::min<uint64_t>(lim, max_frame);
+    const unsigned seg_cap = (unsigned)lim;
+    SF_LAUNCH(h, SF_K_SEGMENT,
+              sf_launch_segment(h->d, dev_ops, n_ops, drop_eps * drop_eps, seg_cap, h->cur,
+                                reinterpret_cast<unsigned long long*>(dev_consumed),
+                                reinterpret_cast<unsigned long long*>(dev_meas), h->stream));
+    // the kernel leaves the frame in the current buffer; neither index is valid now
+    h->idx_ok[0] = h->idx_ok[1] = false;
+    return SF_OK;
+}
+
 sf_status sf_coalesce(sf_handle h, double drop_eps, uint64_t* out_size) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
     if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");

@@ -25,7 +25,7 @@ using namespace sfw;
 
 namespace {
 
-constexpr int kMaxWarps = 8;  // threads per circuit: 32, 64, 128 or 256
+constexpr int kMaxWarps = 16;  // threads per circuit: 32..256 (campaign), 512 (program segment)
 constexpr int kCampMaxCap = SF_CAMPAIGN_MAX_ELEMS;
 
 struct OpRec {
@@ -70,7 +70,7 @@ struct Shared {
     double2 g;
     double p[2];
     unsigned k, kout, nmeas;
-    int cur, rx, status, circ;
+    int cur, rx, status, circ, rnd;
 };
 
 // program records: warp 0 walks a run of Clifford gates through a window of
@@ -241,6 +241,362 @@ __device__ int export_phase(const Shared& S, int n, uint64_t s) {
     return (qe + __popcll(qx & qz) + 2 * __popcll(qz & w) + pe + __popcll(px & pz)) & 3;
 }
 
+// Runs program records [o0, o1) on one circuit's state: S (frame size, buffer,
+// X-block size, global phase, status, outcomes), the tableau rows in warp 0's
+// registers r, the two frame buffers sigb/ampb and the index idx of the current
+// buffer (valid on entry and on return).  Every thread of the block calls it.
+// Exceeding cap is an error (SF_ECAPACITY in S.status); with stop_cap > 0 the
+// run instead stops, at an op boundary and without error, before a diagonal
+// gate or random measurement whose intermediate frame could exceed stop_cap.
+// Returns the index of the first record not applied.
+__device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, uint64_t* const* sigb,
+                                                      double2* const* ampb, uint32_t* idx, const OpRec* ops,
+                                                      unsigned long long o0, unsigned long long o1, unsigned cap,
+                                                      double eps2, unsigned stop_cap) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double rs2 = 0.70710678118654752440;
+unsigned long long oi = o0;
+while (oi < o1 && S.status == 0) {
+        const OpRec op0 = ops[oi];
+        uint32_t kind = op0.kind;
+        bool cond_false = false;
+        if (kind == SF_OP_COND) {
+            if (op0.arg > 8) {
+                if (threadIdx.x == 0) S.status = SF_EINVAL;
+                __syncthreads();
+                break;
+            }
+            const uint64_t mask = (uint64_t)__double_as_longlong(op0.param);
+            cond_false = !(__popcll(S.outcomes & mask) & 1);
+            kind = op0.arg;
+        }
+        if (cond_false) {  // conditional gate not taken
+            oi++;
+            continue;
+        }
+        if (kind <= 8) {
+            // a run of consecutive Clifford gates (a conditional gate runs alone);
+            // warp 0 walks it through the record window, lane 0 publishes its end
+            if (warp == 0) {
+                for (int hf = 0; hf < 2; hf++) {
+                    const int row = lane + 32 * hf;
+                    r[hf].A = row < n ? 1ull << row : 0;
+                    r[hf].t0 = 0;
+                }
+                int rx = S.rx;
+                double2 g = S.g;
+                int bad = 0;
+                unsigned long long gi = oi, wb = oi;
+                OpRec w0 = load_rec(ops, wb + lane, o1), w1 = load_rec(ops, wb + 32 + lane, o1);
+                const bool single = op0.kind == SF_OP_COND;
+                for (;;) {
+                    if (gi - wb >= 32) {
+                        wb += 32;
+                        w0 = w1;
+                        w1 = load_rec(ops, wb + 32 + lane, o1);
+                    }
+                    const OpRec op = shfl_rec(w0, (int)(gi - wb));
+                    gi++;
+                    const int gk = (int)(op.kind == SF_OP_COND ? op.arg : op.kind);
+                    const bool two = gk >= 6;
+                    const int q0 = (int)op.q0, q1 = two ? (int)op.q1 : 0;
+                    if (gk > 8 || q0 >= n || (two && (q1 >= n || q1 == q0))) {
+                        bad = 1;
+                        break;
+                    }
+                    int yq = -1;
+                    double2 num = make_double2(1.0, 0.0);
+                    if (gk == 0) {
+                        const int cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
+                        if (cq != 2) {
+                            const double2 cv = cq < 0 ? make_double2(0.0, 0.0) : ipow_mul(make_double2(1.0, 0.0), cq);
+                            num = make_double2((1.0 + cv.x) * rs2, cv.y * rs2);
+                        } else {
+                            yq = q0;
+                            num = make_double2(2.0 * rs2, 0.0);
+                        }
+                    } else if (gk == 3) {
+                        yq = q0;
+                    } else if (gk == 4) {
+                        yq = q0;
+                        num = make_double2(0.0, 1.0);
+                    }
+                    const int r_old = rx;
+                    for (int hf = 0; hf < 2; hf++) {
+                        const int row = lane + 32 * hf;
+                        if (row < n) {
+                            const uint32_t f = (uint32_t)conj1(gk, q0, q1, r[hf].mx, r[hf].mz);
+                            r[hf].t0 ^= f;
+                            r[hf].t1 = f;
+                            const int fd = conj1(gk, q0, q1, r[hf].dx, r[hf].dz);
+                            r[hf].de = (r[hf].de + 2u * (uint32_t)fd) & 3u;
+                        } else {
+                            r[hf].t1 = 0;
+                        }
+                    }
+                    // Pauli gates flip signs only: M keeps its bits and stays in RREF
+                    if (gk < 3 || gk > 5) rx = warp_rref(r, n, S.stage);
+                    const int dq = rx < 0 ? -1 : warp_amp_phi(r, n, rx, true, yq >= 0 ? (1ull << yq) : 0ull);
+                    if (dq < 0) {
+                        bad = 2;
+                        break;
+                    }
+                    double2 om = ipow_mul(num, (4 - dq) & 3);
+                    const int dr = rx - r_old;
+                    const double sc = dr == 0 ? 1.0 : (dr > 0 ? 1.41421356237309504880 : rs2);
+                    om.x *= sc;
+                    om.y *= sc;
+                    g = cmul(g, om);
+                    if (single || gi >= o1) break;
+                    const unsigned long long d = gi - wb;  // 1..32
+                    const uint32_t nk = d < 32 ? __shfl_sync(SF_FULL, w0.kind, (int)d)
+                                               : __shfl_sync(SF_FULL, w1.kind, 0);
+                    if (nk > 8) break;
+                }
+                for (int j = 0; j < n; j++) {
+                    const unsigned b0 = __ballot_sync(SF_FULL, lane < n && ((r[0].A >> j) & 1));
+                    const unsigned b1 = __ballot_sync(SF_FULL, lane + 32 < n && ((r[1].A >> j) & 1));
+                    if (lane == 0) S.at[j] = (uint64_t)b0 | ((uint64_t)b1 << 32);
+                }
+                const unsigned t0 = __ballot_sync(SF_FULL, lane < n && r[0].t0);
+                const unsigned t1 = __ballot_sync(SF_FULL, lane + 32 < n && r[1].t0);
+                if (lane == 0) {
+                    S.t = (uint64_t)t0 | ((uint64_t)t1 << 32);
+                    S.rx = rx;
+                    S.g = g;
+                    S.oe = gi;
+                    if (bad) S.status = bad == 1 ? SF_EINVAL : SF_EINTERNAL;
+                }
+            }
+            __syncthreads();
+            if (S.status) break;
+            // sigma' = A sigma ^ t on every element, 4-bit table lookups
+            const int nc = (n + 3) >> 2;
+            for (int e = threadIdx.x; e < nc * 16; e += blockDim.x) {
+                const int v = e & 15, c = e >> 4;
+                uint64_t acc = 0;
+                for (int b = 0; b < 4; b++)
+                    if (((v >> b) & 1) && 4 * c + b < n) acc ^= S.at[4 * c + b];
+                S.tab[e] = acc;
+            }
+            __syncthreads();
+            uint64_t* sg = sigb[S.cur];
+            const uint64_t tw = S.t;
+            for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
+                const uint64_t s = sg[j];
+                uint64_t o = tw;
+                for (int c = 0; c < nc; c++) o ^= S.tab[c * 16 + ((s >> (4 * c)) & 15)];
+                sg[j] = o;
+            }
+            __syncthreads();
+            build_index(idx, sg, S.k);
+            oi = S.oe;
+            continue;
+        }
+        if (kind >= 16 && kind <= 19) {
+            // diagonal gate, merged: owner thread computes each output (Sec. IV)
+            const uint32_t gk = kind - 16;
+            const int q0 = (int)op0.q0, q1 = (int)op0.q1;
+            if (q0 >= n || (gk == 3 && (q1 >= n || q1 == q0))) {
+                if (threadIdx.x == 0) S.status = SF_EINVAL;
+                __syncthreads();
+                break;
+            }
+            if (warp == 0) warp_branch_plan_regs(r, n, gk, q0, gk == 3 ? q1 : 0, op0.param, S.P);
+            __syncthreads();
+            const int ng = S.P.ng;
+            if (stop_cap && !S.P.bad && (unsigned long long)ng * S.k > stop_cap) break;  // stop before this op
+            if (S.P.bad || (unsigned long long)ng * S.k > cap) {
+                if (threadIdx.x == 0) S.status = S.P.bad ? SF_EINTERNAL : SF_ECAPACITY;
+                __syncthreads();
+                break;
+            }
+            const int ib = S.cur, ob = S.cur ^ 1;
+            const uint64_t* si = sigb[ib];
+            const double2* ai = ampb[ib];
+            const unsigned k = S.k;
+            if (threadIdx.x == 0) S.obase = 0;
+            __syncthreads();
+            for (unsigned base = 0; base < k; base += blockDim.x) {
+                const unsigned j = base + threadIdx.x;
+                const bool act = j < k;
+                uint64_t s = 0;
+                double2 a = make_double2(0.0, 0.0);
+                int id[4] = {act ? (int)j : -1, -1, -1, -1};
+                if (act) {
+                    s = si[j];
+                    a = ai[j];
+                    for (int g = 1; g < ng; g++) id[g] = find_index(idx, si, k, s ^ S.P.u[g]);
+                }
+                double2 amps[4];
+                unsigned keepm = 0;
+                for (int g = 0; g < ng; g++) {
+                    bool own = act;
+                    for (int g2 = 0; g2 < g; g2++) own &= id[S.P.xidx[g][g2]] < 0;
+                    double2 amp = make_double2(0.0, 0.0);
+                    if (own) {
+                        for (int g2 = 0; g2 < ng; g2++) {
+                            const int m = S.P.xidx[g][g2];
+                            if (id[m] < 0) continue;
+                            const double2 ap = m == 0 ? a : ai[id[m]];
+                            const double2 cc = cmul(coef1(S.P, g2, s ^ S.P.u[m]), ap);
+                            amp.x += cc.x;
+                            amp.y += cc.y;
+                        }
+                    }
+                    amps[g] = amp;
+                    if (own && amp.x * amp.x + amp.y * amp.y >= eps2) keepm |= 1u << g;
+                }
+                unsigned long long o = block_scan_advance(S, __popc(keepm));
+                for (int g = 0; g < ng; g++) {
+                    if (!((keepm >> g) & 1u)) continue;
+                    sigb[ob][o] = s ^ S.P.u[g];
+                    ampb[ob][o] = amps[g];
+                    o++;
+                }
+            }
+            if (threadIdx.x == 0) {
+                S.k = (unsigned)S.obase;
+                S.cur = ob;
+            }
+            __syncthreads();
+            build_index(idx, sigb[S.cur], S.k);
+            oi++;
+            continue;
+        }
+        if (kind == SF_OP_MEASURE) {
+            const int q = (int)op0.q0;
+            if (q >= n || S.nmeas >= 64) {
+                if (threadIdx.x == 0) S.status = SF_EINVAL;
+                __syncthreads();
+                break;
+            }
+            if (stop_cap) {  // stop before a random measurement whose cofactor could exceed stop_cap
+                if (warp == 0) {
+                    const bool x0 = lane < n && ((r[0].mx >> q) & 1), x1 = lane + 32 < n && ((r[1].mx >> q) & 1);
+                    const bool rnd = __any_sync(SF_FULL, x0 || x1);
+                    if (lane == 0) S.rnd = rnd ? 1 : 0;
+                }
+                __syncthreads();
+                if (S.rnd && 2ull * S.k > stop_cap) break;
+            }
+            if (warp == 0) {
+                const int rx = warp_measure_prep(r, n, S.rx, q, S.C, S.stage);
+                if (lane == 0) S.rx = rx;
+            }
+            __syncthreads();
+            if (S.C.bad || (S.C.random && 2ull * S.k > cap)) {
+                if (threadIdx.x == 0) S.status = S.C.bad ? SF_EINTERNAL : SF_ECAPACITY;
+                __syncthreads();
+                break;
+            }
+            if (S.C.random) {
+                // cofactor split merged: s and s ^ uq share their two children
+                const int ib = S.cur, ob = S.cur ^ 1;
+                const uint64_t* si = sigb[ib];
+                const double2* ai = ampb[ib];
+                const unsigned k = S.k;
+                if (threadIdx.x == 0) S.obase = 0;
+                __syncthreads();
+                for (unsigned base = 0; base < k; base += blockDim.x) {
+                    const unsigned j = base + threadIdx.x;
+                    const bool act = j < k;
+                    uint64_t s = 0, p = 0, t[2] = {0, 0};
+                    double2 a = make_double2(0.0, 0.0), ap = a, cc[2] = {a, a};
+                    int l = -1;
+                    bool own = false;
+                    if (act) {
+                        s = si[j];
+                        a = ai[j];
+                        p = s ^ S.C.uq;
+                        l = find_index(idx, si, k, p);
+                        own = l < 0 || s < p;
+                        if (l >= 0) ap = ai[l];
+                    }
+                    unsigned keepm = 0;
+                    for (int x = 0; x < 2; x++) {
+                        if (!own) continue;
+                        double2 c = cof_child1(S.C, s, a, x, t[x]);
+                        if (l >= 0) {
+                            uint64_t t2;
+                            const double2 c2 = cof_child1(S.C, p, ap, x, t2);
+                            c.x += c2.x;
+                            c.y += c2.y;
+                        }
+                        cc[x] = c;
+                        if (c.x * c.x + c.y * c.y >= 1e-24) keepm |= 1u << x;
+                    }
+                    unsigned long long o = block_scan_advance(S, __popc(keepm));
+                    for (int x = 0; x < 2; x++) {
+                        if (!((keepm >> x) & 1u)) continue;
+                        sigb[ob][o] = t[x];
+                        ampb[ob][o] = cc[x];
+                        o++;
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    S.k = (unsigned)S.obase;
+                    S.cur = ob;
+                }
+                __syncthreads();
+            }
+            // probabilities of the two outcomes (Sec. IV), fixed summation order
+            const int rq = S.C.rq;
+            {
+                double p0 = 0.0, p1 = 0.0;
+                const uint64_t* sg = sigb[S.cur];
+                const double2* am = ampb[S.cur];
+                for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
+                    const double m = am[j].x * am[j].x + am[j].y * am[j].y;
+                    if ((sg[j] >> rq) & 1) p1 += m;
+                    else p0 += m;
+                }
+                block_sum2(S, p0, p1);
+            }
+            const int xo = op0.param < S.p[1] ? 1 : 0;
+            if (!(S.p[xo] > 0.0)) {
+                if (threadIdx.x == 0) S.status = SF_ESTATE;
+                __syncthreads();
+                break;
+            }
+            const double scale = 1.0 / sqrt(S.p[xo]);
+            // collapse onto the outcome
+            {
+                const int ib = S.cur, ob = S.cur ^ 1;
+                const unsigned k = S.k;
+                if (threadIdx.x == 0) S.obase = 0;
+                __syncthreads();
+                for (unsigned base = 0; base < k; base += blockDim.x) {
+                    const unsigned j = base + threadIdx.x;
+                    const bool keep = j < k && (int)((sigb[ib][j] >> rq) & 1) == xo;
+                    const unsigned long long o = block_scan_advance(S, keep ? 1u : 0u);
+                    if (keep) {
+                        sigb[ob][o] = sigb[ib][j];
+                        double2 a = ampb[ib][j];
+                        a.x *= scale;
+                        a.y *= scale;
+                        ampb[ob][o] = a;
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    S.k = (unsigned)S.obase;
+                    S.cur = ob;
+                    if (xo) S.outcomes |= 1ull << S.nmeas;
+                    S.nmeas++;
+                }
+                __syncthreads();
+            }
+            build_index(idx, sigb[S.cur], S.k);
+            oi++;
+            continue;
+        }
+        if (threadIdx.x == 0) S.status = SF_EINVAL;  // unknown op
+        __syncthreads();
+    }
+    __syncthreads();
+    return oi;
+}
+
 // CT threads per circuit; GIDX: the phase-vector index in a per-CTA slice of
 // global memory (L2-resident) instead of shared memory, for more CTAs per SM
 template <int CT, bool GIDX>
@@ -252,7 +608,6 @@ __global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
     uint64_t* sigb[2] = {D.ws_sig + (size_t)blockIdx.x * 2 * D.cap, D.ws_sig + ((size_t)blockIdx.x * 2 + 1) * D.cap};
     double2* ampb[2] = {D.ws_amp + (size_t)blockIdx.x * 2 * D.cap, D.ws_amp + ((size_t)blockIdx.x * 2 + 1) * D.cap};
     Row r[2];
-    const double rs2 = 0.70710678118654752440;
     for (;;) {
         if (threadIdx.x == 0) S.circ = (int)atomicAdd(D.next, 1u);
         __syncthreads();
@@ -285,335 +640,7 @@ __global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
         }
         __syncthreads();
         build_index(idx, sigb[0], 1);
-        const unsigned long long o0 = D.off[ci], o1 = D.off[ci + 1];
-        unsigned long long oi = o0;
-        while (oi < o1 && S.status == 0) {
-            const OpRec op0 = D.ops[oi];
-            uint32_t kind = op0.kind;
-            bool cond_false = false;
-            if (kind == SF_OP_COND) {
-                if (op0.arg > 8) {
-                    if (threadIdx.x == 0) S.status = SF_EINVAL;
-                    __syncthreads();
-                    break;
-                }
-                const uint64_t mask = (uint64_t)__double_as_longlong(op0.param);
-                cond_false = !(__popcll(S.outcomes & mask) & 1);
-                kind = op0.arg;
-            }
-            if (cond_false) {  // conditional gate not taken
-                oi++;
-                continue;
-            }
-            if (kind <= 8) {
-                // a run of consecutive Clifford gates (a conditional gate runs alone);
-                // warp 0 walks it through the record window, lane 0 publishes its end
-                if (warp == 0) {
-                    for (int hf = 0; hf < 2; hf++) {
-                        const int row = lane + 32 * hf;
-                        r[hf].A = row < n ? 1ull << row : 0;
-                        r[hf].t0 = 0;
-                    }
-                    int rx = S.rx;
-                    double2 g = S.g;
-                    int bad = 0;
-                    unsigned long long gi = oi, wb = oi;
-                    OpRec w0 = load_rec(D.ops, wb + lane, o1), w1 = load_rec(D.ops, wb + 32 + lane, o1);
-                    const bool single = op0.kind == SF_OP_COND;
-                    for (;;) {
-                        if (gi - wb >= 32) {
-                            wb += 32;
-                            w0 = w1;
-                            w1 = load_rec(D.ops, wb + 32 + lane, o1);
-                        }
-                        const OpRec op = shfl_rec(w0, (int)(gi - wb));
-                        gi++;
-                        const int gk = (int)(op.kind == SF_OP_COND ? op.arg : op.kind);
-                        const bool two = gk >= 6;
-                        const int q0 = (int)op.q0, q1 = two ? (int)op.q1 : 0;
-                        if (gk > 8 || q0 >= n || (two && (q1 >= n || q1 == q0))) {
-                            bad = 1;
-                            break;
-                        }
-                        int yq = -1;
-                        double2 num = make_double2(1.0, 0.0);
-                        if (gk == 0) {
-                            const int cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
-                            if (cq != 2) {
-                                const double2 cv = cq < 0 ? make_double2(0.0, 0.0) : ipow_mul(make_double2(1.0, 0.0), cq);
-                                num = make_double2((1.0 + cv.x) * rs2, cv.y * rs2);
-                            } else {
-                                yq = q0;
-                                num = make_double2(2.0 * rs2, 0.0);
-                            }
-                        } else if (gk == 3) {
-                            yq = q0;
-                        } else if (gk == 4) {
-                            yq = q0;
-                            num = make_double2(0.0, 1.0);
-                        }
-                        const int r_old = rx;
-                        for (int hf = 0; hf < 2; hf++) {
-                            const int row = lane + 32 * hf;
-                            if (row < n) {
-                                const uint32_t f = (uint32_t)conj1(gk, q0, q1, r[hf].mx, r[hf].mz);
-                                r[hf].t0 ^= f;
-                                r[hf].t1 = f;
-                                const int fd = conj1(gk, q0, q1, r[hf].dx, r[hf].dz);
-                                r[hf].de = (r[hf].de + 2u * (uint32_t)fd) & 3u;
-                            } else {
-                                r[hf].t1 = 0;
-                            }
-                        }
-                        // Pauli gates flip signs only: M keeps its bits and stays in RREF
-                        if (gk < 3 || gk > 5) rx = warp_rref(r, n, S.stage);
-                        const int dq = rx < 0 ? -1 : warp_amp_phi(r, n, rx, true, yq >= 0 ? (1ull << yq) : 0ull);
-                        if (dq < 0) {
-                            bad = 2;
-                            break;
-                        }
-                        double2 om = ipow_mul(num, (4 - dq) & 3);
-                        const int dr = rx - r_old;
-                        const double sc = dr == 0 ? 1.0 : (dr > 0 ? 1.41421356237309504880 : rs2);
-                        om.x *= sc;
-                        om.y *= sc;
-                        g = cmul(g, om);
-                        if (single || gi >= o1) break;
-                        const unsigned long long d = gi - wb;  // 1..32
-                        const uint32_t nk = d < 32 ? __shfl_sync(SF_FULL, w0.kind, (int)d)
-                                                   : __shfl_sync(SF_FULL, w1.kind, 0);
-                        if (nk > 8) break;
-                    }
-                    for (int j = 0; j < n; j++) {
-                        const unsigned b0 = __ballot_sync(SF_FULL, lane < n && ((r[0].A >> j) & 1));
-                        const unsigned b1 = __ballot_sync(SF_FULL, lane + 32 < n && ((r[1].A >> j) & 1));
-                        if (lane == 0) S.at[j] = (uint64_t)b0 | ((uint64_t)b1 << 32);
-                    }
-                    const unsigned t0 = __ballot_sync(SF_FULL, lane < n && r[0].t0);
-                    const unsigned t1 = __ballot_sync(SF_FULL, lane + 32 < n && r[1].t0);
-                    if (lane == 0) {
-                        S.t = (uint64_t)t0 | ((uint64_t)t1 << 32);
-                        S.rx = rx;
-                        S.g = g;
-                        S.oe = gi;
-                        if (bad) S.status = bad == 1 ? SF_EINVAL : SF_EINTERNAL;
-                    }
-                }
-                __syncthreads();
-                if (S.status) break;
-                // sigma' = A sigma ^ t on every element, 4-bit table lookups
-                const int nc = (n + 3) >> 2;
-                for (int e = threadIdx.x; e < nc * 16; e += blockDim.x) {
-                    const int v = e & 15, c = e >> 4;
-                    uint64_t acc = 0;
-                    for (int b = 0; b < 4; b++)
-                        if (((v >> b) & 1) && 4 * c + b < n) acc ^= S.at[4 * c + b];
-                    S.tab[e] = acc;
-                }
-                __syncthreads();
-                uint64_t* sg = sigb[S.cur];
-                const uint64_t tw = S.t;
-                for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
-                    const uint64_t s = sg[j];
-                    uint64_t o = tw;
-                    for (int c = 0; c < nc; c++) o ^= S.tab[c * 16 + ((s >> (4 * c)) & 15)];
-                    sg[j] = o;
-                }
-                __syncthreads();
-                build_index(idx, sg, S.k);
-                oi = S.oe;
-                continue;
-            }
-            if (kind >= 16 && kind <= 19) {
-                // diagonal gate, merged: owner thread computes each output (Sec. IV)
-                const uint32_t gk = kind - 16;
-                const int q0 = (int)op0.q0, q1 = (int)op0.q1;
-                if (q0 >= n || (gk == 3 && (q1 >= n || q1 == q0))) {
-                    if (threadIdx.x == 0) S.status = SF_EINVAL;
-                    __syncthreads();
-                    break;
-                }
-                if (warp == 0) warp_branch_plan_regs(r, n, gk, q0, gk == 3 ? q1 : 0, op0.param, S.P);
-                __syncthreads();
-                const int ng = S.P.ng;
-                if (S.P.bad || (unsigned long long)ng * S.k > D.cap) {
-                    if (threadIdx.x == 0) S.status = S.P.bad ? SF_EINTERNAL : SF_ECAPACITY;
-                    __syncthreads();
-                    break;
-                }
-                const int ib = S.cur, ob = S.cur ^ 1;
-                const uint64_t* si = sigb[ib];
-                const double2* ai = ampb[ib];
-                const unsigned k = S.k;
-                if (threadIdx.x == 0) S.obase = 0;
-                __syncthreads();
-                for (unsigned base = 0; base < k; base += blockDim.x) {
-                    const unsigned j = base + threadIdx.x;
-                    const bool act = j < k;
-                    uint64_t s = 0;
-                    double2 a = make_double2(0.0, 0.0);
-                    int id[4] = {act ? (int)j : -1, -1, -1, -1};
-                    if (act) {
-                        s = si[j];
-                        a = ai[j];
-                        for (int g = 1; g < ng; g++) id[g] = find_index(idx, si, k, s ^ S.P.u[g]);
-                    }
-                    double2 amps[4];
-                    unsigned keepm = 0;
-                    for (int g = 0; g < ng; g++) {
-                        bool own = act;
-                        for (int g2 = 0; g2 < g; g2++) own &= id[S.P.xidx[g][g2]] < 0;
-                        double2 amp = make_double2(0.0, 0.0);
-                        if (own) {
-                            for (int g2 = 0; g2 < ng; g2++) {
-                                const int m = S.P.xidx[g][g2];
-                                if (id[m] < 0) continue;
-                                const double2 ap = m == 0 ? a : ai[id[m]];
-                                const double2 cc = cmul(coef1(S.P, g2, s ^ S.P.u[m]), ap);
-                                amp.x += cc.x;
-                                amp.y += cc.y;
-                            }
-                        }
-                        amps[g] = amp;
-                        if (own && amp.x * amp.x + amp.y * amp.y >= D.eps2) keepm |= 1u << g;
-                    }
-                    unsigned long long o = block_scan_advance(S, __popc(keepm));
-                    for (int g = 0; g < ng; g++) {
-                        if (!((keepm >> g) & 1u)) continue;
-                        sigb[ob][o] = s ^ S.P.u[g];
-                        ampb[ob][o] = amps[g];
-                        o++;
-                    }
-                }
-                if (threadIdx.x == 0) {
-                    S.k = (unsigned)S.obase;
-                    S.cur = ob;
-                }
-                __syncthreads();
-                build_index(idx, sigb[S.cur], S.k);
-                oi++;
-                continue;
-            }
-            if (kind == SF_OP_MEASURE) {
-                const int q = (int)op0.q0;
-                if (q >= n || S.nmeas >= 64) {
-                    if (threadIdx.x == 0) S.status = SF_EINVAL;
-                    __syncthreads();
-                    break;
-                }
-                if (warp == 0) {
-                    const int rx = warp_measure_prep(r, n, S.rx, q, S.C, S.stage);
-                    if (lane == 0) S.rx = rx;
-                }
-                __syncthreads();
-                if (S.C.bad || (S.C.random && 2ull * S.k > D.cap)) {
-                    if (threadIdx.x == 0) S.status = S.C.bad ? SF_EINTERNAL : SF_ECAPACITY;
-                    __syncthreads();
-                    break;
-                }
-                if (S.C.random) {
-                    // cofactor split merged: s and s ^ uq share their two children
-                    const int ib = S.cur, ob = S.cur ^ 1;
-                    const uint64_t* si = sigb[ib];
-                    const double2* ai = ampb[ib];
-                    const unsigned k = S.k;
-                    if (threadIdx.x == 0) S.obase = 0;
-                    __syncthreads();
-                    for (unsigned base = 0; base < k; base += blockDim.x) {
-                        const unsigned j = base + threadIdx.x;
-                        const bool act = j < k;
-                        uint64_t s = 0, p = 0, t[2] = {0, 0};
-                        double2 a = make_double2(0.0, 0.0), ap = a, cc[2] = {a, a};
-                        int l = -1;
-                        bool own = false;
-                        if (act) {
-                            s = si[j];
-                            a = ai[j];
-                            p = s ^ S.C.uq;
-                            l = find_index(idx, si, k, p);
-                            own = l < 0 || s < p;
-                            if (l >= 0) ap = ai[l];
-                        }
-                        unsigned keepm = 0;
-                        for (int x = 0; x < 2; x++) {
-                            if (!own) continue;
-                            double2 c = cof_child1(S.C, s, a, x, t[x]);
-                            if (l >= 0) {
-                                uint64_t t2;
-                                const double2 c2 = cof_child1(S.C, p, ap, x, t2);
-                                c.x += c2.x;
-                                c.y += c2.y;
-                            }
-                            cc[x] = c;
-                            if (c.x * c.x + c.y * c.y >= 1e-24) keepm |= 1u << x;
-                        }
-                        unsigned long long o = block_scan_advance(S, __popc(keepm));
-                        for (int x = 0; x < 2; x++) {
-                            if (!((keepm >> x) & 1u)) continue;
-                            sigb[ob][o] = t[x];
-                            ampb[ob][o] = cc[x];
-                            o++;
-                        }
-                    }
-                    if (threadIdx.x == 0) {
-                        S.k = (unsigned)S.obase;
-                        S.cur = ob;
-                    }
-                    __syncthreads();
-                }
-                // probabilities of the two outcomes (Sec. IV), fixed summation order
-                const int rq = S.C.rq;
-                {
-                    double p0 = 0.0, p1 = 0.0;
-                    const uint64_t* sg = sigb[S.cur];
-                    const double2* am = ampb[S.cur];
-                    for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
-                        const double m = am[j].x * am[j].x + am[j].y * am[j].y;
-                        if ((sg[j] >> rq) & 1) p1 += m;
-                        else p0 += m;
-                    }
-                    block_sum2(S, p0, p1);
-                }
-                const int xo = op0.param < S.p[1] ? 1 : 0;
-                if (!(S.p[xo] > 0.0)) {
-                    if (threadIdx.x == 0) S.status = SF_ESTATE;
-                    __syncthreads();
-                    break;
-                }
-                const double scale = 1.0 / sqrt(S.p[xo]);
-                // collapse onto the outcome
-                {
-                    const int ib = S.cur, ob = S.cur ^ 1;
-                    const unsigned k = S.k;
-                    if (threadIdx.x == 0) S.obase = 0;
-                    __syncthreads();
-                    for (unsigned base = 0; base < k; base += blockDim.x) {
-                        const unsigned j = base + threadIdx.x;
-                        const bool keep = j < k && (int)((sigb[ib][j] >> rq) & 1) == xo;
-                        const unsigned long long o = block_scan_advance(S, keep ? 1u : 0u);
-                        if (keep) {
-                            sigb[ob][o] = sigb[ib][j];
-                            double2 a = ampb[ib][j];
-                            a.x *= scale;
-                            a.y *= scale;
-                            ampb[ob][o] = a;
-                        }
-                    }
-                    if (threadIdx.x == 0) {
-                        S.k = (unsigned)S.obase;
-                        S.cur = ob;
-                        if (xo) S.outcomes |= 1ull << S.nmeas;
-                        S.nmeas++;
-                    }
-                    __syncthreads();
-                }
-                build_index(idx, sigb[S.cur], S.k);
-                oi++;
-                continue;
-            }
-            if (threadIdx.x == 0) S.status = SF_EINVAL;  // unknown op
-            __syncthreads();
-        }
+        run_ops(S, r, n, sigb, ampb, idx, D.ops, D.off[ci], D.off[ci + 1], D.cap, D.eps2, 0u);
         __syncthreads();
         // results
         double nr = 0.0;
@@ -664,6 +691,108 @@ __global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
     }
 }
 
+// ---- a program on one handle's frame while it is small (sf_apply_program) ----
+// The circuit engine above, run by one CTA on a frame handle's own state: the
+// tableau rows are loaded into warp 0's registers, the handle's two frame
+// buffers are used in place, the index lives in shared memory.  The program is
+// checked before anything is touched; the run stops at an op boundary before
+// a diagonal gate or random measurement whose intermediate frame could exceed
+// seg_cap; the frame is left in buffer `cur` and the tableau, X-block size and
+// global phase are written back.
+constexpr int kSegThreads = 512;
+
+__global__ void __launch_bounds__(kSegThreads) k_segment(SfDev d, const OpRec* ops, unsigned long long n_ops,
+                                                        double eps2, unsigned seg_cap, int cur,
+                                                        unsigned long long* consumed, unsigned long long* out_meas) {
+    extern __shared__ uint32_t idx[];  // [slots_for(seg_cap)]
+    __shared__ Shared S;
+    if (*(volatile uint32_t*)d.status) return;
+    const int n = d.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) S.nmeas = 0;
+    __syncthreads();
+    bool bad = false;
+    unsigned nm = 0;
+    for (unsigned long long i = threadIdx.x; i < n_ops; i += blockDim.x) {
+        const OpRec o = ops[i];
+        const uint32_t k = o.kind == SF_OP_COND ? o.arg : o.kind;
+        const bool two = (k >= 6 && k <= 8) || k == 19;
+        bool ok = o.q0 < (uint32_t)n && (!two || (o.q1 < (uint32_t)n && o.q1 != o.q0));
+        if (o.kind == SF_OP_COND) ok &= o.arg <= 8;
+        else if (k == SF_OP_MEASURE) nm++;
+        else ok &= k <= 8 || (k >= 16 && k <= 19);
+        bad |= !ok;
+    }
+    if (nm) atomicAdd(&S.nmeas, nm);
+    bad = __syncthreads_or(bad) != 0;
+    if (bad || S.nmeas > 64) {
+        if (threadIdx.x == 0) set_status(d.status, 1u, cur, 30u);  // SF_EINVAL: bad record
+        return;
+    }
+    Row r[2];
+    if (warp == 0) {
+        for (int hf = 0; hf < 2; hf++) {
+            const int row = lane + 32 * hf;
+            const bool in = row < n;
+            r[hf].mx = in ? d.mx[row] : 0;
+            r[hf].mz = in ? d.mz[row] : 0;
+            r[hf].dx = in ? d.dx[row] : 0;
+            r[hf].dz = in ? d.dz[row] : 0;
+            r[hf].de = in ? d.de[row] : 0;
+            r[hf].piv = in ? d.piv[row] : 0x7fffffff;
+            r[hf].A = in ? 1ull << row : 0;
+            r[hf].t0 = r[hf].t1 = 0;
+        }
+    }
+    uint64_t* const sigb[2] = {d.sig[cur], d.sig[cur ^ 1]};
+    double2* const ampb[2] = {d.amp[cur], d.amp[cur ^ 1]};
+    if (threadIdx.x == 0) {
+        S.k = (unsigned)d.kcnt[cur];
+        S.cur = 0;
+        S.rx = d.meta[0];
+        S.g = *d.g;
+        S.status = 0;
+        S.outcomes = 0;
+        S.nmeas = 0;
+    }
+    __syncthreads();
+    unsigned long long done = 0;
+    if (S.k <= seg_cap) {
+        build_index(idx, sigb[0], S.k);
+        done = run_ops(S, r, n, sigb, ampb, idx, ops, 0, n_ops, seg_cap, eps2, seg_cap);
+    }
+    if (S.cur == 1) {
+        for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
+            sigb[0][j] = sigb[1][j];
+            ampb[0][j] = ampb[1][j];
+        }
+    }
+    if (warp == 0) {
+        for (int hf = 0; hf < 2; hf++) {
+            const int row = lane + 32 * hf;
+            if (row < n) {
+                d.mx[row] = r[hf].mx;
+                d.mz[row] = r[hf].mz;
+                d.dx[row] = r[hf].dx;
+                d.dz[row] = r[hf].dz;
+                d.de[row] = r[hf].de;
+                d.piv[row] = r[hf].piv;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        d.meta[0] = S.rx;
+        *d.g = S.g;
+        d.kcnt[cur] = S.k;
+        if (consumed) *consumed = done;
+        if (out_meas) {
+            out_meas[0] = S.outcomes;
+            out_meas[1] = S.nmeas;
+        }
+        if (S.status) set_status(d.status, (uint32_t)S.status, cur, 31u);
+        else if (!consumed && done < n_ops) set_status(d.status, SF_ST_CAPACITY, cur, 32u);
+    }
+}
+
 // index for frames of up to cap elements (slots_for(cap) slots)
 size_t index_slots_for(unsigned cap) {
     size_t t = 64;
@@ -683,6 +812,18 @@ int shape_index(uint32_t threads, bool smem_index) {
 }
 
 }  // namespace
+
+size_t sf_segment_smem_bytes(unsigned seg_cap) { return index_slots_for(seg_cap) * sizeof(uint32_t); }
+
+void sf_launch_segment(const SfDev& d, const void* ops, unsigned long long n_ops, double eps2, unsigned seg_cap,
+                       int cur, unsigned long long* consumed, unsigned long long* out_meas, cudaStream_t s) {
+    // once per process, thread-safe
+    static const bool attr = cudaFuncSetAttribute(k_segment, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  200 * 1024) == cudaSuccess;
+    (void)attr;
+    k_segment<<<1, kSegThreads, sf_segment_smem_bytes(seg_cap), s>>>(
+        d, reinterpret_cast<const OpRec*>(ops), n_ops, eps2, seg_cap, cur, consumed, out_meas);
+}
 
 struct sf_campaign_s {
     int n = 0;

@@ -297,6 +297,10 @@ void sf_launch_clifford(const SfDev& d, const void* dev_gates, int ngates, int b
 void sf_launch_clifford_warp(const SfDev& d, const void* dev_gates, int ngates, int buf, cudaStream_t s);
 void sf_launch_measure_prep(const SfDev& d, uint32_t q, int buf, uint64_t* gws, cudaStream_t s);
 void sf_launch_amp_prep(const SfDev& d, const uint64_t* dev_y, cudaStream_t s);
+// one handle's program in a single-CTA launch while the frame is small (W = 1)
+void sf_launch_segment(const SfDev& d, const void* ops, unsigned long long n_ops, double eps2, unsigned seg_cap,
+                       int cur, unsigned long long* consumed, unsigned long long* out_meas, cudaStream_t s);
+size_t sf_segment_smem_bytes(unsigned seg_cap);
 size_t sf_tableau_smem_bytes(int n, int W, int NT);
 
 void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s);

@@ -18,7 +18,7 @@ from . import _build
 SF_OK, SF_EINVAL, SF_ENOMEM, SF_ECAPACITY, SF_ECUDA, SF_ETIMEOUT, SF_ESTATE, SF_EINTERNAL = range(8)
 # kernel classes (SF_K_* in include/sf.h)
 KERNEL_CLASSES = ["clifford", "affine", "branch", "branch_merge", "insert", "compact", "index", "measure_prep",
-                  "cofactor", "prob", "reduce", "amp_prep", "amplitude", "filter", "export", "reset"]
+                  "cofactor", "prob", "reduce", "amp_prep", "amplitude", "filter", "export", "reset", "segment"]
 STATUS_NAMES = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOMEM", 3: "SF_ECAPACITY", 4: "SF_ECUDA",
                 5: "SF_ETIMEOUT", 6: "SF_ESTATE", 7: "SF_EINTERNAL"}
 
@@ -58,6 +58,7 @@ def load(build: bool = True) -> C.CDLL:
         "sf_apply_clifford_device": ([H, C.c_void_p, u64], st),
         "sf_apply_nonclifford": ([H, u32, u32, u32, dbl], st),
         "sf_apply_nonclifford_coalesce": ([H, u32, u32, u32, dbl, dbl], st),
+        "sf_apply_program": ([H, C.c_void_p, u64, dbl, u64, C.c_void_p, C.c_void_p], st),
         "sf_coalesce": ([H, dbl, P64], st),
         "sf_measure": ([H, u32, C.c_int32, PD, PD], st),
         "sf_amplitude": ([H, P64, PD, PD], st),
@@ -426,6 +427,37 @@ class Frame:
     def apply_nonclifford_coalesce(self, kind: int, q0: int, q1: int = 0, theta: float = 0.0,
                                    eps: float = 1e-12) -> None:
         self._check(self.lib.sf_apply_nonclifford_coalesce(self.h, kind, q0, q1, float(theta), float(eps)), self.h)
+
+    def apply_program_device(self, dev_ops: int, n_ops: int, eps: float = 1e-12, dev_consumed: int = 0,
+                             dev_meas: int = 0, max_frame: int = 0) -> None:
+        """sf_apply_program on device pointers (ints; 0 for NULL)."""
+        self._check(self.lib.sf_apply_program(self.h, C.c_void_p(dev_ops or None), int(n_ops), float(eps),
+                                              int(max_frame), C.c_void_p(dev_consumed or None),
+                                              C.c_void_p(dev_meas or None)), self.h)
+
+    def apply_program(self, ops, eps: float = 1e-12, max_frame: int = 0):
+        """Apply ops (the vocabulary of circuits.py) through sf_apply_program
+        while the frame is small.  Returns (i, outcome_bits, n_meas): ops[:i]
+        were applied (i counts op tuples, a coalesce after a diagonal gate
+        included); continue with the per-op calls from ops[i]."""
+        import torch
+        recs, _ = encode_program([ops])
+        if len(recs) == 0:
+            return len(ops), 0, 0
+        d_ops = torch.from_numpy(recs.view(np.uint8).copy()).cuda()
+        out = torch.zeros(3, dtype=torch.int64, device="cuda")
+        self.apply_program_device(d_ops.data_ptr(), len(recs), eps, out.data_ptr(), out.data_ptr() + 8, max_frame)
+        self.sync()
+        consumed, bits, nm = (int(v) for v in out.cpu().numpy().view(np.uint64))
+        # record index -> op index ("K" right after "N" belongs to it; lone "K" has no record)
+        i, r = 0, 0
+        while i < len(ops) and r < consumed:
+            if ops[i][0] != "K":
+                r += 1
+            i += 1
+        while i < len(ops) and ops[i][0] == "K":
+            i += 1
+        return i, bits, nm
 
     def coalesce(self, eps: float = 1e-12, sync: bool = False) -> Optional[int]:
         if sync:
