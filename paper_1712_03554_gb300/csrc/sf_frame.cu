@@ -280,17 +280,22 @@ __device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uin
         wq[2][0] = (int)q1; wq[2][1] = -1; cf[2] = make_double2(-dd.x, -dd.y);
         wq[3][0] = (int)q0; wq[3][1] = (int)q1; cf[3] = dd;
     }
-    uint64_t um[SF_BR_MAXT][W], vm[SF_BR_MAXT][W], wz[SF_BR_MAXT][W];
+    uint64_t um[SF_BR_MAXT][W], vm[SF_BR_MAXT][W], wz[SF_BR_MAXT][W], odd[W];
     int epsq[SF_BR_MAXT];
     int bad = 0;
     Pauli<W> p[SF_BR_MAXT];
+    // the identity term needs no pass; for CR the Z_c Z_t term follows from the other two
+    bool skip[SF_BR_MAXT];
     for (int j = 0; j < nt; j++) {
 #pragma unroll
         for (int w = 0; w < W; w++) { wz[j][w] = 0; um[j][w] = 0; vm[j][w] = 0; }
         for (int a = 0; a < 2; a++)
             if (wq[j][a] >= 0) wz[j][wq[j][a] >> 6] ^= 1ull << (wq[j][a] & 63);
         pauli_id<W>(p[j]);
+        skip[j] = wq[j][0] < 0 || (kind == 3 && j == 3);
     }
+#pragma unroll
+    for (int w = 0; w < W; w++) odd[w] = 0;
     // each row is read once for all terms: u_h = [Z^w anticommutes with M_h],
     // v_h = [Z^w anticommutes with D_h], contribution D_h^{u_h} M_h^{v_h}
     for (int h = lane; h < n; h += 32) {
@@ -304,7 +309,9 @@ __device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uin
         }
         mh.e = 0;
         dh.e = (int)__ldg(&d.de[h]);
+        if (dh.e & 1) odd[h >> 6] |= 1ull << (h & 63);
         for (int j = 0; j < nt; j++) {
+            if (skip[j]) continue;
             const bool ub = popc_and<W>(mh.x, wz[j]) & 1;
             const bool vb = popc_and<W>(dh.x, wz[j]) & 1;
             if (ub) {
@@ -318,6 +325,7 @@ __device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uin
         }
     }
     for (int j = 0; j < nt; j++) {
+        if (skip[j]) continue;
         warp_pauli_product<W>(p[j]);
 #pragma unroll
         for (int w = 0; w < W; w++) {
@@ -326,6 +334,21 @@ __device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uin
             if (p[j].x[w] != 0 || p[j].z[w] != wz[j][w]) bad = 1;
         }
         epsq[j] = (4 - p[j].e) & 3;
+    }
+    epsq[0] = 0;  // identity: u = v = 0 (zeroed above)
+    if (kind == 3) {
+        // Z^{w1} Z^{w2} = eps1 eps2 D^{u1} M^{v1} D^{u2} M^{v2}: moving M^{v1} past D^{u2}
+        // gives (-1)^{|v1 & u2|}; D^{u1} D^{u2} = D^{u1^u2} times the squares of the
+        // shared destabilizers (-1 for an odd i-power)
+        int par = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            odd[w] = warp_or(odd[w]);
+            um[3][w] = um[1][w] ^ um[2][w];
+            vm[3][w] = vm[1][w] ^ vm[2][w];
+            par += __popcll(vm[1][w] & um[2][w]) + __popcll(um[1][w] & um[2][w] & odd[w]);
+        }
+        epsq[3] = (epsq[1] + epsq[2] + 2 * par) & 3;
     }
     if (lane != 0) return;
     int gid[SF_BR_MAXT];

@@ -450,6 +450,23 @@ __device__ __forceinline__ void warp_branch_plan_regs(const Row* r, int n, uint3
     uint64_t um[4], vm[4];
     int epsq[4], bad = 0;
     for (int j = 0; j < nt; j++) {
+        if (wz[j] == 0) {  // the identity term: u = v = 0, eps = 1
+            um[j] = vm[j] = 0;
+            epsq[j] = 0;
+            continue;
+        }
+        if (kind == 3 && j == 3) {
+            // Z_c Z_t from the two one-qubit terms: Z^{w1} Z^{w2} = eps1 eps2 D^{u1} M^{v1} D^{u2} M^{v2};
+            // moving M^{v1} past D^{u2} gives (-1)^{|v1 & u2|}, D^{u1} D^{u2} = D^{u1^u2} up to the
+            // squares of the shared destabilizers (-1 for an odd i-power)
+            const unsigned o0 = __ballot_sync(SF_FULL, lane < n && (r[0].de & 1u));
+            const unsigned o1 = __ballot_sync(SF_FULL, lane + 32 < n && (r[1].de & 1u));
+            const uint64_t odd = (uint64_t)o0 | ((uint64_t)o1 << 32);
+            um[3] = um[1] ^ um[2];
+            vm[3] = vm[1] ^ vm[2];
+            epsq[3] = (epsq[1] + epsq[2] + 2 * (__popcll(vm[1] & um[2]) + __popcll(um[1] & um[2] & odd))) & 3;
+            continue;
+        }
         uint64_t cx = 0, cz = 0;
         int ce = 0;
         bool ub[2], vb[2];
