@@ -9,7 +9,7 @@ amplitudes read and written; index and hash tables are not counted).
   python -m paper_1712_03554_gb300.kernel_bench throughput 16 20 24
   python -m paper_1712_03554_gb300.kernel_bench latency
   python -m paper_1712_03554_gb300.kernel_bench merge-case 20   (a short run for ncu captures)
-  python -m paper_1712_03554_gb300.kernel_bench qft-step        (one eager QFT n=20 step, the bench's circuit)
+  python -m paper_1712_03554_gb300.kernel_bench qft-step [max_frame] (one eager QFT n=20 step, the bench's circuit)
   python -m paper_1712_03554_gb300.kernel_bench campaign-case 64 (one campaign launch, 32 threads, global index)
   python -m paper_1712_03554_gb300.kernel_bench clifford-case 1024 (one Clifford batch of 200 gates at n)
 """
@@ -115,13 +115,16 @@ def merge_case(m):
     print("k", f.size())
 
 
-def qft_step(seed=0):
-    """The bench's step eagerly: QFT n = 20 on a seeded random basis state with
-    merged branching, then the probabilities of qubit 0 and one amplitude."""
+def qft_step(seed=0, max_frame=2048):
+    """The bench's step eagerly: QFT n = 20 on a seeded random basis state, the
+    small-frame prefix as one sf_apply_program launch (frame limit max_frame,
+    0: none), the rest with merged branching, then the probabilities of qubit 0
+    and one amplitude."""
     x, ops = c.qft_random_input(20, seed)
     f = frame_of(20, 0, 1 << 21)
     f.reset()
-    c.run(f, ops)
+    i = f.apply_program(ops, max_frame=max_frame)[0] if max_frame else 0
+    c.run(f, ops[i:])
     f.measure(0, -1)
     f.amplitude(x)
     f.sync()
@@ -158,7 +161,7 @@ if __name__ == "__main__":
     elif mode == "merge-case":
         merge_case(args[0] if args else 20)
     elif mode == "qft-step":
-        qft_step()
+        qft_step(max_frame=args[0] if args else 2048)
     elif mode == "campaign-case":
         campaign_case(args[0] if args else 64)
     elif mode == "clifford-case":
