@@ -57,6 +57,8 @@ def _load():
         lib.of_nonclifford.argtypes = [vp, u32, u32, u32, C.c_double]
         lib.of_coalesce.argtypes = [vp, C.c_double, szp]
         lib.of_measure.argtypes = [vp, u32, C.c_int, dp, dp]
+        lib.of_toffoli_cofactor.argtypes = [vp, u32, u32, u32]
+        lib.of_cr_cofactor.argtypes = [vp, u32, u32, C.c_double]
         lib.of_amplitude.argtypes = [vp, u64p, dp, dp]
         lib.of_get_tableau.argtypes = [vp, u64p, u64p, C.POINTER(C.c_uint32)]
         lib.of_get_frame.argtypes = [vp, u64p, dp, C.c_size_t, szp]
@@ -129,6 +131,14 @@ class FrameOracle:
         k = C.c_size_t()
         self._chk(self.lib.of_coalesce(self.h, float(eps), C.byref(k)), "coalesce")
         return k.value
+
+    def apply_toffoli_cofactor(self, c1, c2, t):
+        """TOF by cofactors (Eq. 2)."""
+        self._chk(self.lib.of_toffoli_cofactor(self.h, c1, c2, t), "toffoli")
+
+    def apply_cr_cofactor(self, c, t, alpha):
+        """R(alpha)_{ct} by cofactors (Eq. 3)."""
+        self._chk(self.lib.of_cr_cofactor(self.h, c, t, float(alpha)), "cr")
 
     def measure(self, q, collapse=-1):
         p0, p1 = C.c_double(), C.c_double()

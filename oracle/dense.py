@@ -88,6 +88,17 @@ class DenseOracle:
             raise ValueError(kind)
         self.psi = np.where(mask, self.psi * ph, self.psi)
 
+    def apply_toffoli_cofactor(self, c1, c2, t):
+        """The Toffoli gate itself (its definition: flip bit t where bits c1 and
+        c2 are 1), the dense counterpart of the cofactor-based frame update."""
+        both = (((self.idx >> c1) & 1) & ((self.idx >> c2) & 1)) == 1
+        src = np.where(both, self.idx ^ (1 << t), self.idx)
+        self.psi = self.psi[src]
+
+    def apply_cr_cofactor(self, c, t, alpha):
+        """R(alpha)_{ct} by its definition: e^{i alpha} where bits c and t are 1."""
+        self.apply_nonclifford(3, c, t, alpha)
+
     def coalesce(self, eps=1e-12):
         return None
 

@@ -32,6 +32,9 @@
  *   - COFACTOR (Sec. III) for random-outcome measurements: the measurement
  *     update of Sec. II-B forced to each outcome, children weighted by the
  *     five-step phase rule with U = the projector.
+ *   - Toffoli and controlled-R(alpha) by cofactors (Eq. 2 and Eq. 3): COFACTOR
+ *     on the two qubits, then X_t (or the phase e^{i alpha}) applied to the
+ *     states of the 11 cofactor only.
  *   - Coalescing = the set semantics of Def. 1: sort, merge equal phase
  *     vectors, drop |a| < eps.
  */
@@ -581,12 +584,12 @@ static int find_zq_row(const ofr* f, int q) {
     return -1;
 }
 
-/* COFACTOR(F, q) for a random qubit (Sec. III), then the measurement sum of
- * Sec. IV; collapse keeps the consistent states and renormalises.           */
-int of_measure(void* hh, uint32_t q, int collapse, double* p0, double* p1) {
-    ofr* f = (ofr*)hh;
+/* COFACTOR(F, q) (Sec. III): if q is random in M, the measurement update of
+ * Sec. II-B forced to each outcome, every element split into its two
+ * cofactors weighted by the five-step phase rule, then merged.  Afterwards
+ * Z_q is a canonical row of M.                                               */
+static int cofactor(ofr* f, uint32_t q) {
     int n = f->n, W = f->W;
-    if ((int)q >= n || collapse < -1 || collapse > 1) return OF_EINVAL;
     int piv_row = -1;
     for (int h = 0; h < n; h++)
         if (getb(f->x + (size_t)h * W, (int)q)) { piv_row = h; break; }
@@ -636,6 +639,17 @@ int of_measure(void* hh, uint32_t q, int collapse, double* p0, double* p1) {
         free_tableau(old);
         merge_frame(f, OF_MEASURE_EPS);
     }
+    return OF_OK;
+}
+
+/* COFACTOR(F, q), then the measurement sum of Sec. IV; collapse keeps the
+ * consistent states and renormalises.                                       */
+int of_measure(void* hh, uint32_t q, int collapse, double* p0, double* p1) {
+    ofr* f = (ofr*)hh;
+    int W = f->W;
+    if ((int)q >= f->n || collapse < -1 || collapse > 1) return OF_EINVAL;
+    int st = cofactor(f, q);
+    if (st) return st;
     int R = find_zq_row(f, (int)q);
     if (R < 0) return OF_ESTATE;
     double pr[2] = {0.0, 0.0};
@@ -656,6 +670,74 @@ int of_measure(void* hh, uint32_t q, int collapse, double* p0, double* p1) {
             out++;
         }
         f->k = out;
+    }
+    return OF_OK;
+}
+
+/* TOF_{c1 c2 t} by cofactors (Eq. 2 and its three steps): COFACTOR on c1
+ * and c2, so that M holds the rows Z_c1 (index u) and Z_c2 (index v); then X_t
+ * is applied to the states of the c1 c2 = 11 cofactor, the elements whose
+ * phase vector is -1 at both u and v.  A Pauli gate leaves M unchanged, so X_t
+ * acts on each such state as a frame rotation of that state alone: its
+ * phase vector takes the sign flips of the rows that anticommute with X_t and
+ * its amplitude the five-step phase factor.  The 11 class maps onto itself
+ * (X_t commutes with Z_c1 and Z_c2), so no phase vectors collide.           */
+int of_toffoli_cofactor(void* hh, uint32_t c1, uint32_t c2, uint32_t t) {
+    ofr* f = (ofr*)hh;
+    int n = f->n, W = f->W;
+    if ((int)c1 >= n || (int)c2 >= n || (int)t >= n || c1 == c2 || c1 == t || c2 == t) return OF_EINVAL;
+    int st = cofactor(f, c1);
+    if (!st) st = cofactor(f, c2);
+    if (st) return st;
+    int u = find_zq_row(f, (int)c1), v = find_zq_row(f, (int)c2);
+    if (u < 0 || v < 0) return OF_ESTATE;
+    uint64_t* flip = (uint64_t*)calloc(W, 8);
+    for (int h = 0; h < n; h++) {
+        int l = lit_of(f->x + (size_t)h * W, f->z + (size_t)h * W, (int)t), dummy = 0;
+        if (ot_conjugate(3, &l, &dummy)) flipb(flip, h);
+    }
+    cplx U[4][4];
+    int nq;
+    gate_matrix(3, U, &nq);
+    uint64_t* s = (uint64_t*)malloc(8 * W);
+    uint64_t* b = (uint64_t*)malloc(8 * W);
+    uint64_t* y = (uint64_t*)malloc(8 * W);
+    double scale = pow(2.0, 0.5 * f->r);
+    for (size_t j = 0; j < f->k; j++) {
+        uint64_t* sj = f->sig + j * W;
+        if (!getb(sj, u) || !getb(sj, v)) continue;
+        for (int w = 0; w < W; w++) s[w] = sj[w] ^ flip[w];
+        anchor(f, s, b);
+        int lo = getb(b, (int)t);
+        cplx om = 0.0;
+        for (int li = 0; li < 2; li++) {
+            if (U[lo][li] == 0.0) continue;
+            memcpy(y, b, 8 * W);
+            setb(y, (int)t, li);
+            om += U[lo][li] * amp_at(f, sj, y);
+        }
+        memcpy(sj, s, 8 * W);
+        f->a[j] *= om * scale;
+    }
+    free(s); free(b); free(y); free(flip);
+    return OF_OK;
+}
+
+/* R(alpha)_{ct} by cofactors (Eq. 3): COFACTOR on c and t, then the states of
+ * the ct = 11 cofactor take the factor e^{i alpha}.                          */
+int of_cr_cofactor(void* hh, uint32_t c, uint32_t t, double alpha) {
+    ofr* f = (ofr*)hh;
+    int W = f->W;
+    if ((int)c >= f->n || (int)t >= f->n || c == t) return OF_EINVAL;
+    int st = cofactor(f, c);
+    if (!st) st = cofactor(f, t);
+    if (st) return st;
+    int u = find_zq_row(f, (int)c), v = find_zq_row(f, (int)t);
+    if (u < 0 || v < 0) return OF_ESTATE;
+    const cplx ph = cexp(I * alpha);
+    for (size_t j = 0; j < f->k; j++) {
+        const uint64_t* sj = f->sig + j * W;
+        if (getb(sj, u) && getb(sj, v)) f->a[j] *= ph;
     }
     return OF_OK;
 }

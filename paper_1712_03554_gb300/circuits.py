@@ -13,6 +13,9 @@ Op encoding (one tuple per op):
   ("M", q, u)                      measure qubit q; outcome = 1 if u < p(1) else 0
                                    (u is a seeded uniform draw, or None for
                                    "probabilities only")
+  ("T3", c1, c2, t)                Toffoli by cofactors (Eq. 2): COFACTOR on c1, c2,
+                                   X_t on the 11 cofactor
+  ("CR", c, t, alpha)              controlled-R(alpha) by cofactors (Eq. 3)
   ("Q", kind, q0, q1, mask)        classically controlled Clifford gate: applied
                                    iff the parity of (outcome bits & mask) is 1,
                                    bit m = outcome of the m-th drawn measurement
@@ -196,10 +199,11 @@ def cuccaro_classical_ops(nbits: int):
 
 
 def cuccaro(nbits: int, superpose: bool = True, a_val: int = 0, b_val: int = 0,
-            coalesce: bool = True) -> List[Op]:
-    """Cuccaro adder with every Toffoli as Clifford+7T.  With superpose=True the
-    inputs are H on every a and b qubit (the paper's benchmark, Sec. VI);
-    otherwise X gates load the basis inputs a_val, b_val."""
+            coalesce: bool = True, toffoli: str = "clifford_t") -> List[Op]:
+    """Cuccaro adder with every Toffoli as Clifford+7T (toffoli="clifford_t") or
+    applied directly by cofactors, Eq. 2 (toffoli="cofactor").  With
+    superpose=True the inputs are H on every a and b qubit (the paper's
+    benchmark, Sec. VI); otherwise X gates load the basis inputs a_val, b_val."""
     anc, a, b, z = cuccaro_layout(nbits)
     ops: List[Op] = []
     if superpose:
@@ -210,6 +214,8 @@ def cuccaro(nbits: int, superpose: bool = True, a_val: int = 0, b_val: int = 0,
     for rec in cuccaro_classical_ops(nbits):
         if rec[0] == "cnot":
             ops.append(("C", CNOT, rec[1], rec[2]))
+        elif toffoli == "cofactor":
+            ops.append(("T3", rec[1], rec[2], rec[3]))
         else:
             ops += toffoli_clifford_t(rec[1], rec[2], rec[3])
     return with_coalesce_after_nonclifford(ops) if coalesce else ops
@@ -287,6 +293,12 @@ def run(sim, ops: Sequence[Op], drop_eps: float = 1e-12, batch_cliffords: bool =
                 results.append((q, p0, p1, x))
                 outcome_bits |= x << n_drawn
                 n_drawn += 1
+        elif tag == "T3":
+            flush()
+            sim.apply_toffoli_cofactor(op[1], op[2], op[3])
+        elif tag == "CR":
+            flush()
+            sim.apply_cr_cofactor(op[1], op[2], op[3])
         elif tag == "Q":
             if bin(outcome_bits & op[4]).count("1") & 1:
                 pending.append((op[1], op[2], op[3]))
@@ -484,7 +496,7 @@ def serving_stream(n_requests: int, rate_hz: float, seed: int = 0, qubits: Seque
 
 
 def count_ops(ops: Sequence[Op]):
-    c = {"C": 0, "N": 0, "K": 0, "M": 0, "Q": 0}
+    c = {"C": 0, "N": 0, "K": 0, "M": 0, "Q": 0, "T3": 0, "CR": 0}
     for op in ops:
         c[op[0]] += 1
     return c

@@ -310,3 +310,70 @@ def test_planted_sign_error_is_caught():
     for s, a in zip(sig[:, 0], amp2):
         psi += a * stabilizer_state_by_projection(n, x[:, 0], z[:, 0], int(s))
     assert not np.allclose(psi, d.state(), atol=1e-9)
+
+
+# ---- Toffoli and controlled-R(alpha) by cofactors (Eq. 2, Eq. 3) -----------------
+def _dense_prefix(n, seed):
+    ops = c.random_clifford_t(n, 40, 3, seed, t_kinds=(c.T, c.TDG))
+    f, d = oracle.FrameOracle(n), DenseOracle(n)
+    c.run(f, ops)
+    c.run(d, ops)
+    return f, d
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_cofactor_toffoli_is_the_toffoli(seed):
+    """After Eq. 2 on a random Clifford+T state, the frame (expanded by
+    projectors, independently of the oracle's amplitude code) is the dense
+    state with the Toffoli permutation applied, global phase included; M holds
+    Z_c1 and Z_c2 as rows and stays in RREF; a second Toffoli restores the
+    state."""
+    n = 5
+    g = c.rng_for(500 + seed)
+    c1, c2, t = (int(x) for x in g.choice(n, size=3, replace=False))
+    f, d = _dense_prefix(n, seed)
+    before = d.state()
+    f.apply_toffoli_cofactor(c1, c2, t)
+    d.apply_toffoli_cofactor(c1, c2, t)
+    assert np.allclose(_expand_by_projection(f, n), d.state(), atol=1e-12)
+    assert f.is_rref()
+    x, z, r = f.tableau()
+    rows = {(int(x[h, 0]), int(z[h, 0])) for h in range(n)}
+    assert (0, 1 << c1) in rows and (0, 1 << c2) in rows
+    f.apply_toffoli_cofactor(c1, c2, t)
+    assert np.allclose(_expand_by_projection(f, n), before, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_cofactor_cr_is_the_controlled_phase(seed):
+    n = 5
+    g = c.rng_for(700 + seed)
+    ct, tt = (int(x) for x in g.choice(n, size=2, replace=False))
+    alpha = float(g.uniform(-3, 3))
+    f, d = _dense_prefix(n, seed)
+    f.apply_cr_cofactor(ct, tt, alpha)
+    d.apply_nonclifford(c.CPHASE, ct, tt, alpha)
+    assert np.allclose(_expand_by_projection(f, n), d.state(), atol=1e-12)
+    assert f.is_rref()
+
+
+def test_cofactor_toffoli_on_basis_states_and_cuccaro():
+    """Classical inputs: the Toffoli truth table with a single-element frame;
+    the Cuccaro adder with direct Toffolis adds, and on the equal superposition
+    equals the 7T-decomposed adder's state."""
+    for a_in in range(8):
+        f = oracle.FrameOracle(3)
+        f.apply_clifford([(c.X, q, 0) for q in range(3) if (a_in >> q) & 1])
+        f.apply_toffoli_cofactor(0, 1, 2)
+        want = a_in ^ (4 if (a_in & 3) == 3 else 0)
+        assert f.size() == 1 and abs(f.amplitude(want) - 1) < 1e-12
+    nb = 3
+    for av, bv in ((3, 5), (7, 7), (0, 6)):
+        f = oracle.FrameOracle(2 * nb + 2)
+        c.run(f, c.cuccaro(nb, False, av, bv, toffoli="cofactor"))
+        assert abs(f.amplitude(c.cuccaro_reference(nb, av, bv)) - 1) < 1e-12
+    f = oracle.FrameOracle(2 * nb + 2)
+    c.run(f, c.cuccaro(nb, True, toffoli="cofactor"))
+    d = DenseOracle(2 * nb + 2)
+    c.run(d, c.cuccaro(nb, True))
+    assert np.allclose([f.amplitude(y) for y in range(1 << (2 * nb + 2))], d.state(), atol=1e-12)
