@@ -117,6 +117,21 @@ sf_status sf_apply_nonclifford(sf_handle h, uint32_t kind, uint32_t q0, uint32_t
 sf_status sf_apply_nonclifford_coalesce(sf_handle h, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
                                         double drop_eps);
 
+/* TOF_{c1 c2 t} by cofactors (Eq. 2): COFACTOR on c1 and c2 (Sec. III; the
+ * frame may double twice, merged as in sf_measure), after which M holds the
+ * rows Z_c1 and Z_c2, then X_t applied to the states of the c1 c2 = 11
+ * cofactor (the elements whose sign is -1 at both rows): each such phase
+ * vector takes the sign flips of the rows that anticommute with X_t, with the
+ * exact phase factor, and the amplitude stays in place.  The same state as the
+ * Clifford+T decomposition, in fewer passes; M then differs (it holds Z_c1 and
+ * Z_c2), so frames are compared after the same sequence of operations.
+ * Distinct qubits < n_qubits.  Synchronises (twice, inside the cofactors). */
+sf_status sf_apply_toffoli(sf_handle h, uint32_t c1, uint32_t c2, uint32_t t);
+
+/* R(alpha)_{ct} by cofactors (Eq. 3): COFACTOR on c and t, then the states of
+ * the ct = 11 cofactor take the factor e^{i alpha}.  Synchronises. */
+sf_status sf_apply_cr_cofactor(sf_handle h, uint32_t c, uint32_t t, double alpha);
+
 /* Merge elements with equal phase vectors (summing amplitudes) and drop those
  * with |a| < drop_eps (Def. 1: the phase vectors of a frame are distinct).
  * If out_size is non-NULL the new frame size is written there and the call
@@ -169,7 +184,8 @@ enum { SF_K_CLIFFORD = 0,      /* tableau update of a Clifford batch (single CTA
        SF_K_FILTER = 13,       /* collapse */
        SF_K_EXPORT = 14, SF_K_RESET = 15,
        SF_K_SEGMENT = 16,      /* sf_apply_program (single CTA) */
-       SF_K_COUNT_CLASSES = 17 };
+       SF_K_COND = 17,         /* the 11-cofactor step of sf_apply_toffoli / sf_apply_cr_cofactor */
+       SF_K_COUNT_CLASSES = 18 };
 
 /* Number of CUDA kernels this handle has launched since it was created. */
 uint64_t sf_kernel_launches(sf_handle h);

@@ -519,9 +519,10 @@ sf_status sf_coalesce(sf_handle h, double drop_eps, uint64_t* out_size) {
     return SF_OK;
 }
 
-sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, double* p1) {
-    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
-    if (q >= h->n || collapse_to < -1 || collapse_to > 1) return fail(h, SF_EINVAL, "bad measurement arguments");
+// COFACTOR(F, q) (Sec. III): the tableau update and, if q is random, the
+// merged split of every element into its two cofactors.  Synchronises (the
+// host learns whether q was random).
+static sf_status cofactor_q(sf_handle h, uint32_t q) {
     SF_LAUNCH(h, SF_K_MEASURE_PREP, sf_launch_measure_prep(h->d, q, h->cur, h->gws, h->stream));
     SF_CK(h, cudaMemcpyAsync(h->hmeta, h->d.meta, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     sf_status st = sync_check(h);
@@ -533,6 +534,36 @@ sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, d
         h->cur ^= 1;
         h->idx_ok[h->cur] = true;
     }
+    return SF_OK;
+}
+
+sf_status sf_apply_toffoli(sf_handle h, uint32_t c1, uint32_t c2, uint32_t t) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (c1 >= h->n || c2 >= h->n || t >= h->n || c1 == c2 || c1 == t || c2 == t)
+        return fail(h, SF_EINVAL, "bad Toffoli qubits");
+    sf_status st = cofactor_q(h, c1);
+    if (!st) st = cofactor_q(h, c2);
+    if (st) return st;
+    SF_LAUNCH(h, SF_K_COND, sf_launch_cond(h->d, h->cur, 0, (int)c1, (int)c2, (int)t, 0.0, h->stream));
+    h->idx_ok[h->cur] = false;  // phase vectors changed
+    return SF_OK;
+}
+
+sf_status sf_apply_cr_cofactor(sf_handle h, uint32_t c, uint32_t t, double alpha) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (c >= h->n || t >= h->n || c == t) return fail(h, SF_EINVAL, "bad controlled-phase qubits");
+    sf_status st = cofactor_q(h, c);
+    if (!st) st = cofactor_q(h, t);
+    if (st) return st;
+    SF_LAUNCH(h, SF_K_COND, sf_launch_cond(h->d, h->cur, 1, (int)c, (int)t, 0, alpha, h->stream));
+    return SF_OK;  // phase vectors unchanged: the index stays valid
+}
+
+sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, double* p1) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (q >= h->n || collapse_to < -1 || collapse_to > 1) return fail(h, SF_EINVAL, "bad measurement arguments");
+    sf_status st = cofactor_q(h, q);
+    if (st) return st;
     SF_LAUNCH(h, SF_K_PROB, sf_launch_prob(h->d, h->cur, h->stream));
     SF_LAUNCH(h, SF_K_REDUCE, sf_launch_reduce_final(h->d, 0, h->stream));
     SF_CK(h, cudaMemcpyAsync(h->hout, h->d.out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

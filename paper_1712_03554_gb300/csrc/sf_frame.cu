@@ -9,6 +9,7 @@
 //   k_compact     COALESCE in the set sense of Def. 1: emit every slot with
 //                 |a| >= eps and leave the table empty
 //   k_filter      collapse after a measurement
+//   k_cond        Toffoli / controlled-R(alpha) on the 11 cofactor (Eq. 2, Eq. 3)
 //   k_prob        measurement probabilities (Sec. IV, measuring F)
 //   k_amplitude   <y|Psi> (Observation 1)
 //   k_export      canonical-convention amplitudes for export
@@ -626,6 +627,115 @@ __global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, doub
 
 // keep the elements whose sign of row meta[1] is x, scaled by 1/sqrt(p_x)
 // (collapse after a measurement); kcnt[out_buf] must be zero on entry
+// ---------------------------------------------------------------------------
+// Toffoli and controlled-R(alpha) by cofactors (Eq. 2, Eq. 3), the step after
+// COFACTOR on the two qubits: the rows of M equal to Z_c1 and Z_c2 select the
+// elements of the 11 cofactor (sigma bit 1 at both).  kind 0: X_t = eps D^u M^v
+// (u_h = [X_t anticommutes with M_h], v_h = [X_t anticommutes with D_h]) maps
+// such an element in place to sigma ^ u with the factor eps (-1)^{v.sigma};
+// the class maps onto itself, so no two elements meet.  kind 1: the amplitude
+// takes e^{i alpha}.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_cond(SfDev d, int buf, int kind, int c1, int c2, int t,
+                                                   double alpha) {
+    __shared__ int rows[2], epsq, bad;
+    __shared__ uint64_t ux[W], vx[W];
+    if (*d.status) return;
+    const int n = d.n, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        rows[0] = rows[1] = 0x7fffffff;
+        bad = 0;
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < n; h += blockDim.x) {
+        for (int which = 0; which < 2; which++) {
+            const int q = which ? c2 : c1;
+            bool eq = true;
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                eq &= d.mx[w * n + h] == 0ull;
+                eq &= d.mz[w * n + h] == (((q >> 6) == w) ? (1ull << (q & 63)) : 0ull);
+            }
+            if (eq) atomicMin(&rows[which], h);
+        }
+    }
+    if (kind == 0 && threadIdx.x < 32) {
+        // X_t in the basis (M, D): one warp pass over the rows
+        uint64_t um[W], vm[W];
+        Pauli<W> p;
+        pauli_id<W>(p);
+#pragma unroll
+        for (int w = 0; w < W; w++) um[w] = vm[w] = 0;
+        const int tw = t >> 6;
+        const uint64_t tb = 1ull << (t & 63);
+        for (int h = lane; h < n; h += 32) {
+            const bool ub = (d.mz[tw * n + h] & tb) != 0;
+            const bool vb = (d.dz[tw * n + h] & tb) != 0;
+            if (ub) {
+                Pauli<W> dh;
+#pragma unroll
+                for (int w = 0; w < W; w++) { dh.x[w] = d.dx[w * n + h]; dh.z[w] = d.dz[w * n + h]; }
+                dh.e = (int)d.de[h];
+                pauli_mul<W>(p, dh);
+                um[h >> 6] |= 1ull << (h & 63);
+            }
+            if (vb) {
+                Pauli<W> mh;
+#pragma unroll
+                for (int w = 0; w < W; w++) { mh.x[w] = d.mx[w * n + h]; mh.z[w] = d.mz[w * n + h]; }
+                mh.e = 0;
+                pauli_mul<W>(p, mh);
+                vm[h >> 6] |= 1ull << (h & 63);
+            }
+        }
+        warp_pauli_product<W>(p);
+        bool ok = true;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            um[w] = warp_or(um[w]);
+            vm[w] = warp_or(vm[w]);
+            ok &= p.x[w] == (w == tw ? tb : 0ull) && p.z[w] == 0ull;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int w = 0; w < W; w++) { ux[w] = um[w]; vx[w] = vm[w]; }
+            epsq = (4 - p.e) & 3;
+            bad = ok ? 0 : 1;
+        }
+    }
+    __syncthreads();
+    if (rows[0] == 0x7fffffff || rows[1] == 0x7fffffff || bad) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, buf, 28u);
+        return;
+    }
+    const int ru = rows[0], rv = rows[1];
+    double sn = 0.0, cs = 1.0;
+    if (kind == 1) sincos(alpha, &sn, &cs);
+    const unsigned long long k = d.kcnt[buf];
+    const uint64_t cap = d.cap;
+    uint64_t* S = d.sig[buf];
+    double2* A = d.amp[buf];
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        uint64_t s[W];
+        load_sig<W>(S, cap, j, s);
+        if (!((s[ru >> 6] >> (ru & 63)) & 1) || !((s[rv >> 6] >> (rv & 63)) & 1)) continue;
+        double2 a = A[j];
+        if (kind == 0) {
+            uint64_t vv[W];
+#pragma unroll
+            for (int w = 0; w < W; w++) vv[w] = vx[w];
+            a = ipow_mul(a, epsq + 2 * (popc_and<W>(vv, s) & 1));
+#pragma unroll
+            for (int w = 0; w < W; w++) s[w] ^= ux[w];
+            store_sig<W>(S, cap, j, s);
+        } else {
+            a = cmul(a, make_double2(cs, sn));
+        }
+        A[j] = a;
+    }
+}
+
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_filter(SfDev d, int x, int in_buf, int out_buf) {
     if (*d.status) return;
@@ -1087,6 +1197,10 @@ void sf_launch_build_index(const SfDev& d, int buf, cudaStream_t s) {
 
 void sf_launch_compact(const SfDev& d, double eps, int out_buf, cudaStream_t s) {
     SF_DISPATCH(d.W, k_compact<WW><<<d.nblk, kThreads, 0, s>>>(d, out_buf, eps * eps));
+}
+
+void sf_launch_cond(const SfDev& d, int buf, int kind, int c1, int c2, int t, double alpha, cudaStream_t s) {
+    SF_DISPATCH(d.W, k_cond<WW><<<d.nblk, kThreads, 0, s>>>(d, buf, kind, c1, c2, t, alpha));
 }
 
 void sf_launch_filter(const SfDev& d, int x, int in_buf, int out_buf, cudaStream_t s) {

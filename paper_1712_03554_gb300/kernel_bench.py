@@ -12,6 +12,7 @@ amplitudes read and written; index and hash tables are not counted).
   python -m paper_1712_03554_gb300.kernel_bench qft-step [max_frame] (one eager QFT n=20 step, the bench's circuit)
   python -m paper_1712_03554_gb300.kernel_bench campaign-case 64 (one campaign launch, 32 threads, global index)
   python -m paper_1712_03554_gb300.kernel_bench clifford-case 1024 (one Clifford batch of 200 gates at n)
+  python -m paper_1712_03554_gb300.kernel_bench cuccaro 5 6 7   (adder: Toffoli by cofactors vs Clifford+7T)
 """
 from __future__ import annotations
 
@@ -151,6 +152,31 @@ def clifford_case(n=1024, gates=200):
     print("r", f.tableau()[2])
 
 
+def cuccaro_compare(nbs=(5, 6, 7)):
+    """The Cuccaro adder on the equal superposition with every Toffoli applied
+    by cofactors (Eq. 2) and as Clifford+7T: wall time of the whole circuit
+    (median of 3 after a warm-up) and the final frame size."""
+    for nb in nbs:
+        n = 2 * nb + 2
+        row = {"nbits": nb, "qubits": n}
+        for how in ("cofactor", "clifford_t"):
+            ops = c.cuccaro(nb, True, toffoli=how)
+            f = sf.Frame(n, 1 << min(2 * nb + 4, 24))
+            ts = []
+            for rep in range(4):
+                f.reset()
+                f.sync()
+                t0 = time.perf_counter()
+                c.run(f, ops)
+                f.sync()
+                ts.append(time.perf_counter() - t0)
+            row[how + "_ms"] = sorted(ts[1:])[1] * 1e3
+            row[how + "_frame"] = f.size()
+            f.close()
+        row["speedup"] = row["clifford_t_ms"] / row["cofactor_ms"]
+        print(json.dumps(row), flush=True)
+
+
 if __name__ == "__main__":
     mode = sys.argv[1] if len(sys.argv) > 1 else "throughput"
     args = [int(a) for a in sys.argv[2:]]
@@ -164,6 +190,8 @@ if __name__ == "__main__":
         qft_step(max_frame=args[0] if args else 2048)
     elif mode == "campaign-case":
         campaign_case(args[0] if args else 64)
+    elif mode == "cuccaro":
+        cuccaro_compare(args or [5, 6, 7])
     elif mode == "clifford-case":
         clifford_case(args[0] if args else 1024)
     else:

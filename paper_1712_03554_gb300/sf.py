@@ -18,7 +18,8 @@ from . import _build
 SF_OK, SF_EINVAL, SF_ENOMEM, SF_ECAPACITY, SF_ECUDA, SF_ETIMEOUT, SF_ESTATE, SF_EINTERNAL = range(8)
 # kernel classes (SF_K_* in include/sf.h)
 KERNEL_CLASSES = ["clifford", "affine", "branch", "branch_merge", "insert", "compact", "index", "measure_prep",
-                  "cofactor", "prob", "reduce", "amp_prep", "amplitude", "filter", "export", "reset", "segment"]
+                  "cofactor", "prob", "reduce", "amp_prep", "amplitude", "filter", "export", "reset", "segment",
+                  "cond"]
 STATUS_NAMES = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOMEM", 3: "SF_ECAPACITY", 4: "SF_ECUDA",
                 5: "SF_ETIMEOUT", 6: "SF_ESTATE", 7: "SF_EINTERNAL"}
 
@@ -59,6 +60,8 @@ def load(build: bool = True) -> C.CDLL:
         "sf_apply_nonclifford": ([H, u32, u32, u32, dbl], st),
         "sf_apply_nonclifford_coalesce": ([H, u32, u32, u32, dbl, dbl], st),
         "sf_apply_program": ([H, C.c_void_p, u64, dbl, u64, C.c_void_p, C.c_void_p], st),
+        "sf_apply_toffoli": ([H, u32, u32, u32], st),
+        "sf_apply_cr_cofactor": ([H, u32, u32, dbl], st),
         "sf_coalesce": ([H, dbl, P64], st),
         "sf_measure": ([H, u32, C.c_int32, PD, PD], st),
         "sf_amplitude": ([H, P64, PD, PD], st),
@@ -427,6 +430,14 @@ class Frame:
     def apply_nonclifford_coalesce(self, kind: int, q0: int, q1: int = 0, theta: float = 0.0,
                                    eps: float = 1e-12) -> None:
         self._check(self.lib.sf_apply_nonclifford_coalesce(self.h, kind, q0, q1, float(theta), float(eps)), self.h)
+
+    def apply_toffoli_cofactor(self, c1: int, c2: int, t: int) -> None:
+        """sf_apply_toffoli: TOF by cofactors (Eq. 2)."""
+        self._check(self.lib.sf_apply_toffoli(self.h, int(c1), int(c2), int(t)), self.h)
+
+    def apply_cr_cofactor(self, c: int, t: int, alpha: float) -> None:
+        """sf_apply_cr_cofactor: R(alpha)_{ct} by cofactors (Eq. 3)."""
+        self._check(self.lib.sf_apply_cr_cofactor(self.h, int(c), int(t), float(alpha)), self.h)
 
     def apply_program_device(self, dev_ops: int, n_ops: int, eps: float = 1e-12, dev_consumed: int = 0,
                              dev_meas: int = 0, max_frame: int = 0) -> None:
