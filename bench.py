@@ -790,15 +790,7 @@ def main():
     e2e_ms_step = float(np.mean(e2e_ms))
 
     # whole-job aggregation
-    tot_updates = updates
-    max_ms = ms_step
-    max_e2e = e2e_ms_step
-    if dist is not None:
-        t = torch.tensor([float(updates), ms_step, e2e_ms_step], dtype=torch.float64, device="cuda")
-        tu = t.clone()
-        dist.all_reduce(tu[:1], op=dist.ReduceOp.SUM)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.MAX)
-        tot_updates, max_ms, max_e2e = float(tu[0]), float(t[1]), float(t[2])
+    tot_updates, max_ms, max_e2e = aggregate_ranks(dist, updates, ms_step, e2e_ms_step, "cuda")
     value = tot_updates / (max_ms * 1e-3)
     e2e_value = tot_updates / (max_e2e * 1e-3)
 
@@ -869,6 +861,20 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def aggregate_ranks(dist, updates: float, ms_step: float, e2e_ms_step: float, device: str):
+    """Whole-job figures of a weak-scaling run: every rank simulates its own
+    instance, so the updates add up and the step time is the slowest rank's.
+    dist is torch.distributed (None for one process)."""
+    if dist is None:
+        return float(updates), float(ms_step), float(e2e_ms_step)
+    import torch
+    t = torch.tensor([float(updates), ms_step, e2e_ms_step], dtype=torch.float64, device=device)
+    tu = t.clone()
+    dist.all_reduce(tu[:1], op=dist.ReduceOp.SUM)
+    dist.all_reduce(t[1:], op=dist.ReduceOp.MAX)
+    return float(tu[0]), float(t[1]), float(t[2])
 
 
 def graph_launch_count(plan, start_indexed: bool = True, extra: int = 0) -> int:
