@@ -56,6 +56,7 @@ struct CampDev {
 
 struct Shared {
     BrTab P;
+    double2 ctab[4][16];      // group coefficient of the plan per sign pattern
     CofTab C;
     uint64_t at[64];          // columns of the composed affine map
     uint64_t tab[16 * 16];    // 4-bit lookup tables of the affine map
@@ -66,6 +67,8 @@ struct Shared {
     double red[2][kMaxWarps];
     unsigned wsum[kMaxWarps];
     Row stage[64];            // row permutation of the tableau reduction
+    double2 eth[32];          // e^{i theta} of records tbase .. tbase + 31
+    unsigned long long tbase;
     unsigned long long obase, outcomes, oe;
     double2 g;
     double p[2];
@@ -192,16 +195,6 @@ __device__ void block_sum2(Shared& S, double a, double b) {
     __syncthreads();
 }
 
-__device__ __forceinline__ double2 coef1(const BrTab& P, int g, uint64_t s) {
-    double2 cf = make_double2(0.0, 0.0);
-    for (int t = 0; t < P.nt[g]; t++) {
-        const double sg = (__popcll(P.v[g][t] & s) & 1) ? -1.0 : 1.0;
-        cf.x += sg * P.c[g][t].x;
-        cf.y += sg * P.c[g][t].y;
-    }
-    return cf;
-}
-
 __device__ __forceinline__ double2 cof_child1(const CofTab& C, uint64_t s, double2 a, int x, uint64_t& t) {
     const int y = x ^ (__popcll(C.vq & s) & 1);
     t = y ? C.tau1 : C.tau0;
@@ -254,7 +247,6 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                                                       unsigned long long o0, unsigned long long o1, unsigned cap,
                                                       double eps2, unsigned stop_cap) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double rs2 = 0.70710678118654752440;
 unsigned long long oi = o0;
 while (oi < o1 && S.status == 0) {
         const OpRec op0 = ops[oi];
@@ -284,7 +276,7 @@ while (oi < o1 && S.status == 0) {
                     r[hf].t0 = 0;
                 }
                 int rx = S.rx;
-                double2 g = S.g;
+                int ga = 0, gb = 0;  // the run's phase factor omega^ga sqrt(2)^gb
                 int bad = 0;
                 unsigned long long gi = oi, wb = oi;
                 OpRec w0 = load_rec(ops, wb + lane, o1), w1 = load_rec(ops, wb + 32 + lane, o1);
@@ -304,23 +296,15 @@ while (oi < o1 && S.status == 0) {
                         bad = 1;
                         break;
                     }
-                    int yq = -1;
-                    double2 num = make_double2(1.0, 0.0);
+                    int yq = -1, cq = -1;
                     if (gk == 0) {
-                        const int cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
-                        if (cq != 2) {
-                            const double2 cv = cq < 0 ? make_double2(0.0, 0.0) : ipow_mul(make_double2(1.0, 0.0), cq);
-                            num = make_double2((1.0 + cv.x) * rs2, cv.y * rs2);
-                        } else {
-                            yq = q0;
-                            num = make_double2(2.0 * rs2, 0.0);
-                        }
-                    } else if (gk == 3) {
+                        cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
+                        if (cq == 2) yq = q0;
+                    } else if (gk == 3 || gk == 4) {
                         yq = q0;
-                    } else if (gk == 4) {
-                        yq = q0;
-                        num = make_double2(0.0, 1.0);
                     }
+                    int na, nb;
+                    cliff_num_exp(gk, cq, na, nb);
                     const int r_old = rx;
                     for (int hf = 0; hf < 2; hf++) {
                         const int row = lane + 32 * hf;
@@ -341,12 +325,9 @@ while (oi < o1 && S.status == 0) {
                         bad = 2;
                         break;
                     }
-                    double2 om = ipow_mul(num, (4 - dq) & 3);
                     const int dr = rx - r_old;
-                    const double sc = dr == 0 ? 1.0 : (dr > 0 ? 1.41421356237309504880 : rs2);
-                    om.x *= sc;
-                    om.y *= sc;
-                    g = cmul(g, om);
+                    ga = (ga + na + 2 * ((4 - dq) & 3)) & 7;
+                    gb += nb + (dr > 0) - (dr < 0);
                     if (single || gi >= o1) break;
                     const unsigned long long d = gi - wb;  // 1..32
                     const uint32_t nk = d < 32 ? __shfl_sync(SF_FULL, w0.kind, (int)d)
@@ -363,7 +344,7 @@ while (oi < o1 && S.status == 0) {
                 if (lane == 0) {
                     S.t = (uint64_t)t0 | ((uint64_t)t1 << 32);
                     S.rx = rx;
-                    S.g = g;
+                    S.g = cmul(S.g, cliff_factor(ga, gb));
                     S.oe = gi;
                     if (bad) S.status = bad == 1 ? SF_EINVAL : SF_EINTERNAL;
                 }
@@ -402,7 +383,36 @@ while (oi < o1 && S.status == 0) {
                 __syncthreads();
                 break;
             }
-            if (warp == 0) warp_branch_plan_regs(r, n, gk, q0, gk == 3 ? q1 : 0, op0.param, S.P);
+            if (warp == 0) {
+                // T and T-dagger take e^{+-i pi/4}; the angles of the other diagonal
+                // records are evaluated 32 records at a time, one per lane, so the
+                // narrow double-precision pipe runs one sincos per window
+                double2 eth = make_double2(0.70710678118654752440, gk == 0 ? 0.70710678118654752440
+                                                                            : -0.70710678118654752440);
+                if (gk >= 2) {
+                    if (oi < S.tbase || oi - S.tbase >= 32) {
+                        const unsigned long long ri = oi + lane;
+                        double th = 0.0;
+                        if (ri < o1) {
+                            const OpRec o = ops[ri];
+                            if (o.kind == SF_OP_DIAG + 2 || o.kind == SF_OP_DIAG + 3) th = o.param;
+                        }
+                        double sn, cs;
+                        sincos(th, &sn, &cs);
+                        __syncwarp();
+                        S.eth[lane] = make_double2(cs, sn);
+                        if (lane == 0) S.tbase = oi;
+                        __syncwarp();
+                    }
+                    eth = S.eth[oi - S.tbase];
+                }
+                warp_branch_plan_regs(r, n, gk, q0, gk == 3 ? q1 : 0, eth, S.P);
+                __syncwarp();
+                for (int e = lane; e < 64; e += 32) {
+                    const int g = e >> 4, p = e & 15;
+                    if (!S.P.bad && g < S.P.ng && p < (1 << S.P.nt[g])) S.ctab[g][p] = coef_pattern(S.P.c[g], S.P.nt[g], p);
+                }
+            }
             __syncthreads();
             const int ng = S.P.ng;
             if (stop_cap && !S.P.bad && (unsigned long long)ng * S.k > stop_cap) break;  // stop before this op
@@ -412,6 +422,7 @@ while (oi < o1 && S.status == 0) {
                 break;
             }
             const int ib = S.cur, ob = S.cur ^ 1;
+            const unsigned long long kb = keep_bits(eps2);
             const uint64_t* si = sigb[ib];
             const double2* ai = ampb[ib];
             const unsigned k = S.k;
@@ -439,13 +450,14 @@ while (oi < o1 && S.status == 0) {
                             const int m = S.P.xidx[g][g2];
                             if (id[m] < 0) continue;
                             const double2 ap = m == 0 ? a : ai[id[m]];
-                            const double2 cc = cmul(coef1(S.P, g2, s ^ S.P.u[m]), ap);
-                            amp.x += cc.x;
-                            amp.y += cc.y;
+                            const uint64_t px = s ^ S.P.u[m];
+                            int pat = 0;
+                            for (int t = 0; t < S.P.nt[g2]; t++) pat |= (__popcll(S.P.v[g2][t] & px) & 1) << t;
+                            cmul_acc(amp, S.ctab[g2][pat], ap);
                         }
                     }
                     amps[g] = amp;
-                    if (own && amp.x * amp.x + amp.y * amp.y >= eps2) keepm |= 1u << g;
+                    if (own && amp_kept(amp, kb, eps2)) keepm |= 1u << g;
                 }
                 unsigned long long o = block_scan_advance(S, __popc(keepm));
                 for (int g = 0; g < ng; g++) {
@@ -634,6 +646,7 @@ __global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
             S.status = 0;
             S.outcomes = 0;
             S.nmeas = 0;
+            S.tbase = ~0ull;
             S.g = make_double2(1.0, 0.0);
             sigb[0][0] = 0;
             ampb[0][0] = make_double2(1.0, 0.0);
@@ -753,6 +766,7 @@ __global__ void __launch_bounds__(kSegThreads) k_segment(SfDev d, const OpRec* o
         S.status = 0;
         S.outcomes = 0;
         S.nmeas = 0;
+        S.tbase = ~0ull;
     }
     __syncthreads();
     unsigned long long done = 0;

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #define SF_MAX_W 16
 #define SF_MAX_N 1024
 #define SF_FULL 0xffffffffu
@@ -157,6 +159,77 @@ __device__ __forceinline__ double2 ipow_mul(double2 a, int k) {  // a * i^k
         case 2: return make_double2(-a.x, -a.y);
         default: return make_double2(a.y, -a.x);
     }
+}
+
+// e^{i theta} of diagonal gate kind (T, T-dagger: theta = +-pi/4), computed
+// once on the host for a launch from the host: the double-precision pipe of an
+// SM is narrow, and every CTA would otherwise evaluate the same sincos
+inline double2 sf_phase_host(uint32_t kind, double theta) {
+    const double th = kind == 0 ? 0.78539816339744830962 : (kind == 1 ? -0.78539816339744830962 : theta);
+    return make_double2(std::cos(th), std::sin(th));
+}
+
+// Double-precision work runs on a narrow pipe, so the per-element kernels keep
+// it to the multiply-adds of the amplitudes.
+__device__ __forceinline__ double dneg_if(double x, bool neg) {  // sign flip without the FP64 pipe
+    return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)neg << 63));
+}
+// coefficient sum_t (-1)^{bit t of p} c_t of a group of nt diagonal-gate
+// terms, added in the order t = 0, 1, ... (the per-element sum of the terms
+// for the sign pattern p)
+__device__ __forceinline__ double2 coef_pattern(const double2* c, int nt, int p) {
+    double2 cf = make_double2(dneg_if(c[0].x, p & 1), dneg_if(c[0].y, p & 1));
+    for (int t = 1; t < nt; t++) {
+        const bool ng = (p >> t) & 1;
+        cf.x += dneg_if(c[t].x, ng);
+        cf.y += dneg_if(c[t].y, ng);
+    }
+    return cf;
+}
+// acc += c * a
+__device__ __forceinline__ void cmul_acc(double2& acc, double2 c, double2 a) {
+    acc.x = fma(c.x, a.x, acc.x);
+    acc.x = fma(-c.y, a.y, acc.x);
+    acc.y = fma(c.x, a.y, acc.y);
+    acc.y = fma(c.y, a.x, acc.y);
+}
+// drop rule |a|^2 >= eps2: keep_bits is a power of two no smaller than
+// sqrt(eps2) (from the exponent of eps2), so an amplitude whose larger
+// component reaches it is kept on integer compares alone (rounding is monotone)
+__device__ __forceinline__ unsigned long long keep_bits(double eps2) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(eps2);
+    if (b == 0) return 0;
+    const int e = (int)(b >> 52) - 1023;  // eps2 < 2^{e+1}
+    return (unsigned long long)(((e + 2) >> 1) + 1023) << 52;
+}
+__device__ __forceinline__ bool amp_kept(double2 a, unsigned long long kb, double eps2) {
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(a.x) & 0x7fffffffffffffffull;
+    const unsigned long long by = (unsigned long long)__double_as_longlong(a.y) & 0x7fffffffffffffffull;
+    if ((bx > by ? bx : by) >= kb) return true;
+    return a.x * a.x + a.y * a.y >= eps2;
+}
+
+// Every Clifford gate multiplies the global factor by omega^a sqrt(2)^b
+// (omega = e^{i pi/4}, a mod 8, b an integer): a run of gates keeps the two
+// exponents in integers and touches the double-precision factor once.
+// Numerator of the phase rule of gate kind as omega^a sqrt(2)^b; cq is the
+// i-power of the Hadamard numerator (2: the Y-point form, negative: zero).
+__device__ __forceinline__ void cliff_num_exp(int kind, int cq, int& a, int& b) {
+    a = 0;
+    b = 0;
+    if (kind == 0) {
+        if (cq == 0 || cq == 2) b = 1;  // 2 / sqrt(2)
+        else if (cq < 0) b = -1;        // 1 / sqrt(2)
+        else a = cq == 1 ? 1 : 7;       // (1 + i) / sqrt(2), (1 - i) / sqrt(2)
+    } else if (kind == 4) {
+        a = 2;  // i
+    }
+}
+__device__ __forceinline__ double2 cliff_factor(int a, int b) {
+    double m = ldexp(1.0, b >> 1);
+    if (b & 1) m *= 1.41421356237309504880;
+    const double h = m * 0.70710678118654752440;
+    return ipow_mul((a & 1) ? make_double2(h, h) : make_double2(m, 0.0), (a >> 1) & 3);
 }
 
 // code | buffer << 8 | site << 16 (site identifies the failing check)

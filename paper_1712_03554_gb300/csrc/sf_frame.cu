@@ -258,14 +258,10 @@ __device__ __forceinline__ uint64_t warp_or(uint64_t v) {
 
 // called by the 32 lanes of one warp; lane 0 writes P
 template <int W>
-__device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
+__device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double2 eth,
                                  BrPlan<W>& P) {
     const int lane = threadIdx.x & 31, n = d.n;
-    double th = theta;
-    if (kind == 0) th = 0.78539816339744830962;
-    if (kind == 1) th = -0.78539816339744830962;
-    double sn, cs;
-    sincos(th, &sn, &cs);
+    const double cs = eth.x, sn = eth.y;  // e^{i theta}
     int nt;
     int wq[SF_BR_MAXT][2];
     double2 cf[SF_BR_MAXT];
@@ -391,11 +387,11 @@ __device__ __forceinline__ double2 group_coef(const BrPlan<W>& P, int g, const u
 // children of a diagonal gate written out unmerged: child g of element j at
 // g * k + j
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_branch(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
+__global__ void __launch_bounds__(kThreads) k_branch(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1, double2 eth,
                                                      int in_buf, int out_buf) {
     __shared__ BrPlan<W> P;
     if (*d.status) return;
-    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, theta, P);
+    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, eth, P);
     __syncthreads();
     if (P.bad) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 23u);
@@ -601,7 +597,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, doub
                     d.tkey[i] = SF_EMPTY_KEY;
                 }
                 d.tacc[i] = make_double2(0.0, 0.0);
-                keep = a.x * a.x + a.y * a.y >= eps2;
+                keep = amp_kept(a, keep_bits(eps2), eps2);
             }
         }
         const unsigned bal = __ballot_sync(SF_FULL, keep);
@@ -637,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, doub
 // takes e^{i alpha}.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_cond(SfDev d, int buf, int kind, int c1, int c2, int t,
-                                                   double alpha) {
+                                                   double2 ealpha) {  // e^{i alpha} (kind 1)
     __shared__ int rows[2], epsq, bad;
     __shared__ uint64_t ux[W], vx[W];
     if (*d.status) return;
@@ -709,8 +705,7 @@ __global__ void __launch_bounds__(kThreads) k_cond(SfDev d, int buf, int kind, i
         return;
     }
     const int ru = rows[0], rv = rows[1];
-    double sn = 0.0, cs = 1.0;
-    if (kind == 1) sincos(alpha, &sn, &cs);
+    const double cs = ealpha.x, sn = ealpha.y;
     const unsigned long long k = d.kcnt[buf];
     const uint64_t cap = d.cap;
     uint64_t* S = d.sig[buf];
@@ -817,9 +812,10 @@ __global__ void __launch_bounds__(kThreads) k_build_index(SfDev d, int b) {
 // in a fixed order.  No amplitude atomics; the output frame is indexed.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1,
-                                                           double theta, double eps2, int in_buf, int out_buf) {
+                                                           double2 eth, double eps2, int in_buf, int out_buf) {
     __shared__ BrPlan<W> P;
     __shared__ int xidx[SF_BR_MAXG][SF_BR_MAXG];
+    __shared__ double2 ctab[SF_BR_MAXG][1 << SF_BR_MAXT];  // group coefficient per sign pattern
     __shared__ unsigned int wsum[kThreads / 32];
     __shared__ unsigned long long bbase;
     if (*d.status) return;
@@ -837,7 +833,7 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
         }
         return;
     }
-    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, theta, P);
+    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, eth, P);
     __syncthreads();
     if (threadIdx.x == 0) {
         int bad = P.bad;
@@ -854,6 +850,9 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
             }
         for (int w = 0; w < W; w++) bad |= (P.u[0][w] != 0);
         P.bad = bad;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + SF_BR_MAXG * (1 << SF_BR_MAXT)) {
+        const int e = threadIdx.x - 32, g = e >> SF_BR_MAXT, p = e & ((1 << SF_BR_MAXT) - 1);
+        if (!P.bad && g < P.ng && p < (1 << P.nt[g])) ctab[g][p] = coef_pattern(P.c[g], P.nt[g], p);
     }
     __syncthreads();
     if (P.bad) {
@@ -875,6 +874,7 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
     uint64_t* So = d.sig[out_buf];
     double2* Ao = d.amp[out_buf];
     const uint64_t cap = d.cap;
+    const unsigned long long kb = keep_bits(eps2);
     bool ok = tag_in != 0;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < k; base += stride) {
         const unsigned long long j = base + threadIdx.x;
@@ -911,13 +911,13 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
 #pragma unroll
                     for (int w = 0; w < W; w++) px[w] = s[w] ^ P.u[m][w];
                     const double2 ap = m == 0 ? a : Ai[idx[m]];
-                    const double2 c = cmul(group_coef<W>(P, g2, px), ap);
-                    amp.x += c.x;
-                    amp.y += c.y;
+                    int pat = 0;
+                    for (int t = 0; t < P.nt[g2]; t++) pat |= (popc_and<W>(P.v[g2][t], px) & 1) << t;
+                    cmul_acc(amp, ctab[g2][pat], ap);
                 }
             }
             amps[g] = amp;
-            if (own && (amp.x * amp.x + amp.y * amp.y >= eps2)) keepm |= 1u << g;
+            if (own && amp_kept(amp, kb, eps2)) keepm |= 1u << g;
         }
         // one reservation per iteration for all kept outputs of the block
         unsigned long long o = block_out_range(d.ocnt, __popc(keepm), wsum, &bbase);
@@ -981,6 +981,7 @@ __global__ void __launch_bounds__(kThreads) k_cof_merge(SfDev d, double eps2, in
     double2* Ao = d.amp[out_buf];
     const uint64_t cap = d.cap;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long kb = keep_bits(eps2);
     bool ok = tag_in != 0;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < k; base += stride) {
         const unsigned long long j = base + threadIdx.x;
@@ -1017,7 +1018,7 @@ __global__ void __launch_bounds__(kThreads) k_cof_merge(SfDev d, double eps2, in
                 }
             }
             cc[x] = c;
-            if (own && (c.x * c.x + c.y * c.y >= eps2)) keepm |= 1u << x;
+            if (own && amp_kept(c, kb, eps2)) keepm |= 1u << x;
         }
         unsigned long long o = block_out_range(d.ocnt, __popc(keepm), wsum, &bbase);
         for (int x = 0; x < 2; x++) {
@@ -1174,7 +1175,8 @@ void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s) {
 
 void sf_launch_branch(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
                       int out_buf, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_branch<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, theta, in_buf, out_buf));
+    const double2 eth = sf_phase_host(kind, theta);
+    SF_DISPATCH(d.W, k_branch<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, eth, in_buf, out_buf));
 }
 
 void sf_launch_insert(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
@@ -1183,8 +1185,8 @@ void sf_launch_insert(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
 
 void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, double eps,
                             int in_buf, int out_buf, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_branch_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, theta, eps * eps, in_buf,
-                                                                    out_buf));
+    const double2 eth = sf_phase_host(kind, theta);
+    SF_DISPATCH(d.W, k_branch_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, eth, eps * eps, in_buf, out_buf));
 }
 
 void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
@@ -1200,7 +1202,8 @@ void sf_launch_compact(const SfDev& d, double eps, int out_buf, cudaStream_t s) 
 }
 
 void sf_launch_cond(const SfDev& d, int buf, int kind, int c1, int c2, int t, double alpha, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_cond<WW><<<d.nblk, kThreads, 0, s>>>(d, buf, kind, c1, c2, t, alpha));
+    const double2 ea = kind == 1 ? make_double2(std::cos(alpha), std::sin(alpha)) : make_double2(1.0, 0.0);
+    SF_DISPATCH(d.W, k_cond<WW><<<d.nblk, kThreads, 0, s>>>(d, buf, kind, c1, c2, t, ea));
 }
 
 void sf_launch_filter(const SfDev& d, int x, int in_buf, int out_buf, cudaStream_t s) {

@@ -489,8 +489,6 @@ __device__ void store_tableau(const SfDev& d, const Ws<W>& T, int r) {
     if (h == 0) d.meta[0] = r;
 }
 
-__device__ __forceinline__ double2 ipow_c(int k) { return ipow_mul(make_double2(1.0, 0.0), k); }
-
 // ---------------------------------------------------------------------------
 template <int W>
 __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* gates, int ng, int buf,
@@ -504,9 +502,8 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
 #pragma unroll
     for (int w = 0; w < W; w++) T.A[w * NT + h] = (h < n && (h >> 6) == w) ? (1ull << (h & 63)) : 0ull;
     int r = d.meta[0];
-    double2 g = *d.g;
+    int ga = 0, gb = 0;  // the run's phase factor omega^ga sqrt(2)^gb
     __syncthreads();
-    const double rs2 = 0.70710678118654752440;
     for (int gi = 0; gi < ng; gi++) {
         const uint32_t ukind = gates[gi].kind, uq0 = gates[gi].q0, uq1 = gates[gi].q1;
         const bool two = ukind >= 6;
@@ -516,25 +513,17 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
         }
         const int kind = (int)ukind, q0 = (int)uq0, q1 = two ? (int)uq1 : 0;
         // numerator of the phase rule: a point y with <y|U phi_0(M)> != 0, in units of 2^{-r/2}
-        int yq = -1;
-        double2 num = make_double2(1.0, 0.0);
+        int yq = -1, cq = -1;
         if (kind == 0) {
             if (h < W) S.y[h] = (h == (q0 >> 6)) ? (1ull << (q0 & 63)) : 0ull;
             __syncthreads();
-            const int cq = cta_amp_phi<W>(T, n, NT, r, nullptr, S.y, S);
-            if (cq != 2) {
-                double2 cv = cq < 0 ? make_double2(0.0, 0.0) : ipow_c(cq);
-                num = make_double2((1.0 + cv.x) * rs2, cv.y * rs2);
-            } else {
-                yq = q0;
-                num = make_double2(2.0 * rs2, 0.0);
-            }
-        } else if (kind == 3) {
+            cq = cta_amp_phi<W>(T, n, NT, r, nullptr, S.y, S);
+            if (cq == 2) yq = q0;
+        } else if (kind == 3 || kind == 4) {
             yq = q0;
-        } else if (kind == 4) {
-            yq = q0;
-            num = make_double2(0.0, 1.0);
         }
+        int na, nb;
+        cliff_num_exp(kind, cq, na, nb);
         const int r_old = r;
         // conjugate all rows; sign flips of M go to t0 (composed) and t1 (this gate)
         if (h < n) {
@@ -561,16 +550,13 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
             if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 1u);
             return;
         }
-        double2 om = ipow_mul(num, (4 - dq) & 3);
         const int dr = r - r_old;
-        const double sc = dr == 0 ? 1.0 : (dr > 0 ? 1.41421356237309504880 : rs2);
-        om.x *= sc;
-        om.y *= sc;
-        g = cmul(g, om);
+        ga = (ga + na + 2 * ((4 - dq) & 3)) & 7;
+        gb += nb + (dr > 0) - (dr < 0);
         __syncthreads();
     }
     store_tableau<W>(d, T, r);
-    if (h == 0) *d.g = g;
+    if (h == 0) *d.g = cmul(*d.g, cliff_factor(ga, gb));
     // emit the affine map: columns of A (column j = image of e_j) and t as bit words
     uint64_t* AT = T.d0x;  // free in this kernel; W*NT >= n*W words
     for (int e = h; e < n * W; e += NT) AT[e] = 0;

@@ -30,8 +30,7 @@ __global__ void __launch_bounds__(32) k_clifford_warp(SfDev d, const sf_gate_rec
         r[hf].t1 = 0;
     }
     int rx = d.meta[0];
-    double2 g = *d.g;
-    const double rs2 = 0.70710678118654752440;
+    int ga = 0, gb = 0;  // the run's phase factor omega^ga sqrt(2)^gb
     for (int gi = 0; gi < ng; gi++) {
         const uint32_t ukind = gates[gi].kind, uq0 = gates[gi].q0, uq1 = gates[gi].q1;
         const bool two = ukind >= 6;
@@ -41,23 +40,15 @@ __global__ void __launch_bounds__(32) k_clifford_warp(SfDev d, const sf_gate_rec
         }
         const int kind = (int)ukind, q0 = (int)uq0, q1 = two ? (int)uq1 : 0;
         // numerator of the phase rule (see the block kernel)
-        int yq = -1;
-        double2 num = make_double2(1.0, 0.0);
+        int yq = -1, cq = -1;
         if (kind == 0) {
-            const int cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
-            if (cq != 2) {
-                const double2 cv = cq < 0 ? make_double2(0.0, 0.0) : ipow_mul(make_double2(1.0, 0.0), cq);
-                num = make_double2((1.0 + cv.x) * rs2, cv.y * rs2);
-            } else {
-                yq = q0;
-                num = make_double2(2.0 * rs2, 0.0);
-            }
-        } else if (kind == 3) {
+            cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
+            if (cq == 2) yq = q0;
+        } else if (kind == 3 || kind == 4) {
             yq = q0;
-        } else if (kind == 4) {
-            yq = q0;
-            num = make_double2(0.0, 1.0);
         }
+        int na, nb;
+        cliff_num_exp(kind, cq, na, nb);
         const int r_old = rx;
         for (int hf = 0; hf < 2; hf++) {
             const int row = lane + 32 * hf;
@@ -78,12 +69,9 @@ __global__ void __launch_bounds__(32) k_clifford_warp(SfDev d, const sf_gate_rec
             if (lane == 0) set_status(d.status, SF_ST_INTERNAL, buf, 8u);
             return;
         }
-        double2 om = ipow_mul(num, (4 - dq) & 3);
         const int dr = rx - r_old;
-        const double sc = dr == 0 ? 1.0 : (dr > 0 ? 1.41421356237309504880 : rs2);
-        om.x *= sc;
-        om.y *= sc;
-        g = cmul(g, om);
+        ga = (ga + na + 2 * ((4 - dq) & 3)) & 7;
+        gb += nb + (dr > 0) - (dr < 0);
     }
     for (int hf = 0; hf < 2; hf++) {
         const int row = lane + 32 * hf;
@@ -98,7 +86,7 @@ __global__ void __launch_bounds__(32) k_clifford_warp(SfDev d, const sf_gate_rec
     }
     if (lane == 0) {
         d.meta[0] = rx;
-        *d.g = g;
+        *d.g = cmul(*d.g, cliff_factor(ga, gb));
     }
     // affine map: column j of A (image of e_j) and the sign word t
     uint64_t* AT = d.plan + plan_AT(n, 1);

@@ -424,14 +424,11 @@ struct BrTab {
     int xidx[4][4];
 };
 
-__device__ __forceinline__ void warp_branch_plan_regs(const Row* r, int n, uint32_t kind, int q0, int q1, double theta,
+// eth = e^{i theta}
+__device__ __forceinline__ void warp_branch_plan_regs(const Row* r, int n, uint32_t kind, int q0, int q1, double2 eth,
                                              BrTab& P) {
     const int lane = threadIdx.x & 31;
-    double th = theta;
-    if (kind == 0) th = 0.78539816339744830962;
-    if (kind == 1) th = -0.78539816339744830962;
-    double sn, cs;
-    sincos(th, &sn, &cs);
+    const double cs = eth.x, sn = eth.y;
     int nt;
     uint64_t wz[4];
     double2 cf[4];
