@@ -56,7 +56,7 @@ struct CampDev {
 
 struct Shared {
     BrTab P;
-    double2 ctab[4][16];      // group coefficient of the plan per sign pattern
+    double2 ctab[4][16];      // group coefficient of the plan per sign pattern (half table)
     CofTab C;
     uint64_t at[64];          // columns of the composed affine map
     uint64_t tab[16 * 16];    // 4-bit lookup tables of the affine map
@@ -67,8 +67,9 @@ struct Shared {
     double red[2][kMaxWarps];
     unsigned wsum[kMaxWarps];
     Row stage[64];            // row permutation of the tableau reduction
-    double2 eth[32];          // e^{i theta} of records tbase .. tbase + 31
+    SfTerms ecf[32];          // terms of the diagonal records tbase .. tbase + 31
     unsigned long long tbase;
+    unsigned long long pbase, pend;  // records with a plan in the batch
     unsigned long long obase, outcomes, oe;
     double2 g;
     double p[2];
@@ -245,7 +246,8 @@ __device__ int export_phase(const Shared& S, int n, uint64_t s) {
 __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, uint64_t* const* sigb,
                                                       double2* const* ampb, uint32_t* idx, const OpRec* ops,
                                                       unsigned long long o0, unsigned long long o1, unsigned cap,
-                                                      double eps2, unsigned stop_cap) {
+                                                      double eps2, unsigned stop_cap, BrTab* pb,
+                                                      double2 (*cb)[4][16], int nbm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 unsigned long long oi = o0;
 while (oi < o1 && S.status == 0) {
@@ -383,41 +385,87 @@ while (oi < o1 && S.status == 0) {
                 __syncthreads();
                 break;
             }
-            if (warp == 0) {
-                // T and T-dagger take e^{+-i pi/4}; the angles of the other diagonal
-                // records are evaluated 32 records at a time, one per lane, so the
-                // narrow double-precision pipe runs one sincos per window
-                double2 eth = make_double2(0.70710678118654752440, gk == 0 ? 0.70710678118654752440
-                                                                            : -0.70710678118654752440);
-                if (gk >= 2) {
-                    if (oi < S.tbase || oi - S.tbase >= 32) {
+            if (oi < S.pbase || oi >= S.pend) {
+                // plans of the run of diagonal records from oi (at most nbm): the
+                // tableau does not change within it, so warp w plans record oi + w
+                if (warp == 0) {
+                    int nb = 1;
+                    if (nbm > 1) {
                         const unsigned long long ri = oi + lane;
+                        bool dg = false;
+                        if (ri < o1) {
+                            const uint32_t kk = ops[ri].kind;
+                            dg = kk >= SF_OP_DIAG && kk <= SF_OP_DIAG + 3;
+                        }
+                        const unsigned bl = __ballot_sync(SF_FULL, dg);
+                        nb = bl == SF_FULL ? 32 : __ffs(~bl) - 1;
+                        nb = nb < nbm ? nb : nbm;
+                        nb = nb < 1 ? 1 : nb;
+                    }
+                    // the terms of the diagonal records, 32 records at a time (one per
+                    // lane), so the narrow double-precision pipe runs one sincos per window
+                    if (oi < S.tbase || oi + nb > S.tbase + 32) {
+                        const unsigned long long ri = oi + lane;
+                        uint32_t rk = 0;
                         double th = 0.0;
                         if (ri < o1) {
                             const OpRec o = ops[ri];
-                            if (o.kind == SF_OP_DIAG + 2 || o.kind == SF_OP_DIAG + 3) th = o.param;
+                            if (o.kind >= SF_OP_DIAG && o.kind <= SF_OP_DIAG + 3) {
+                                rk = o.kind - SF_OP_DIAG;
+                                th = rk == 0 ? 0.78539816339744830962 : (rk == 1 ? -0.78539816339744830962 : o.param);
+                            }
                         }
                         double sn, cs;
                         sincos(th, &sn, &cs);
+                        const SfTerms T = diag_terms(rk, cs, sn);
                         __syncwarp();
-                        S.eth[lane] = make_double2(cs, sn);
+                        S.ecf[lane] = T;
                         if (lane == 0) S.tbase = oi;
-                        __syncwarp();
                     }
-                    eth = S.eth[oi - S.tbase];
+                    if (nb > 1) {
+                        for (int hf = 0; hf < 2; hf++) {
+                            const int row = lane + 32 * hf;
+                            S.rmx[row] = r[hf].mx;
+                            S.rmz[row] = r[hf].mz;
+                            S.rdx[row] = r[hf].dx;
+                            S.rdz[row] = r[hf].dz;
+                            S.rde[row] = r[hf].de;
+                        }
+                    }
+                    if (lane == 0) {
+                        S.pbase = oi;
+                        S.pend = oi + nb;
+                    }
                 }
-                warp_branch_plan_regs(r, n, gk, q0, gk == 3 ? q1 : 0, eth, S.P);
-                __syncwarp();
-                for (int e = lane; e < 64; e += 32) {
-                    const int g = e >> 4, p = e & 15;
-                    if (!S.P.bad && g < S.P.ng && p < (1 << S.P.nt[g])) S.ctab[g][p] = coef_pattern(S.P.c[g], S.P.nt[g], p);
+                __syncthreads();
+                const int nb = (int)(S.pend - S.pbase);
+                if (warp < nb) {
+                    if (warp != 0) {
+                        for (int hf = 0; hf < 2; hf++) {
+                            const int row = lane + 32 * hf;
+                            r[hf].mx = S.rmx[row];
+                            r[hf].mz = S.rmz[row];
+                            r[hf].dx = S.rdx[row];
+                            r[hf].dz = S.rdz[row];
+                            r[hf].de = S.rde[row];
+                        }
+                    }
+                    const OpRec o = warp == 0 ? op0 : ops[oi + warp];
+                    const uint32_t wk = o.kind - SF_OP_DIAG;
+                    // a bad record is planned as a one-qubit gate on qubit 0 and
+                    // rejected when the run reaches it
+                    const bool okr = (int)o.q0 < n && (wk != 3 || ((int)o.q1 < n && o.q1 != o.q0));
+                    warp_branch_plan_regs(r, n, okr ? wk : 2u, okr ? (int)o.q0 : 0, okr && wk == 3 ? (int)o.q1 : 0,
+                                          S.ecf[oi + warp - S.tbase].c, pb[warp], cb[warp]);
                 }
             }
+            const BrTab& P = pb[oi - S.pbase];
+            double2(*const ctab)[16] = cb[oi - S.pbase];
             __syncthreads();
-            const int ng = S.P.ng;
-            if (stop_cap && !S.P.bad && (unsigned long long)ng * S.k > stop_cap) break;  // stop before this op
-            if (S.P.bad || (unsigned long long)ng * S.k > cap) {
-                if (threadIdx.x == 0) S.status = S.P.bad ? SF_EINTERNAL : SF_ECAPACITY;
+            const int ng = P.ng;
+            if (stop_cap && !P.bad && (unsigned long long)ng * S.k > stop_cap) break;  // stop before this op
+            if (P.bad || (unsigned long long)ng * S.k > cap) {
+                if (threadIdx.x == 0) S.status = P.bad ? SF_EINTERNAL : SF_ECAPACITY;
                 __syncthreads();
                 break;
             }
@@ -437,23 +485,27 @@ while (oi < o1 && S.status == 0) {
                 if (act) {
                     s = si[j];
                     a = ai[j];
-                    for (int g = 1; g < ng; g++) id[g] = find_index(idx, si, k, s ^ S.P.u[g]);
+                    for (int g = 1; g < ng; g++) id[g] = find_index(idx, si, k, s ^ P.u[g]);
                 }
                 double2 amps[4];
                 unsigned keepm = 0;
                 for (int g = 0; g < ng; g++) {
                     bool own = act;
-                    for (int g2 = 0; g2 < g; g2++) own &= id[S.P.xidx[g][g2]] < 0;
+                    for (int g2 = 0; g2 < g; g2++) own &= id[P.xidx[g][g2]] < 0;
                     double2 amp = make_double2(0.0, 0.0);
                     if (own) {
                         for (int g2 = 0; g2 < ng; g2++) {
-                            const int m = S.P.xidx[g][g2];
+                            const int m = P.xidx[g][g2];
                             if (id[m] < 0) continue;
                             const double2 ap = m == 0 ? a : ai[id[m]];
-                            const uint64_t px = s ^ S.P.u[m];
+                            const uint64_t px = s ^ P.u[m];
+                            const int ntg = P.nt[g2];
                             int pat = 0;
-                            for (int t = 0; t < S.P.nt[g2]; t++) pat |= (__popcll(S.P.v[g2][t] & px) & 1) << t;
-                            cmul_acc(amp, S.ctab[g2][pat], ap);
+                            for (int t = 0; t < ntg; t++) pat |= (__popcll(P.v[g2][t] & px) & 1) << t;
+                            // the half table holds the patterns with the last term's bit clear
+                            const bool neg = (pat >> (ntg - 1)) & 1;
+                            const double2 cc = ctab[g2][neg ? pat ^ ((1 << ntg) - 1) : pat];
+                            cmul_acc(amp, make_double2(dneg_if(cc.x, neg), dneg_if(cc.y, neg)), ap);
                         }
                     }
                     amps[g] = amp;
@@ -462,7 +514,7 @@ while (oi < o1 && S.status == 0) {
                 unsigned long long o = block_scan_advance(S, __popc(keepm));
                 for (int g = 0; g < ng; g++) {
                     if (!((keepm >> g) & 1u)) continue;
-                    sigb[ob][o] = s ^ S.P.u[g];
+                    sigb[ob][o] = s ^ P.u[g];
                     ampb[ob][o] = amps[g];
                     o++;
                 }
@@ -647,13 +699,14 @@ __global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
             S.outcomes = 0;
             S.nmeas = 0;
             S.tbase = ~0ull;
+            S.pbase = S.pend = 0;
             S.g = make_double2(1.0, 0.0);
             sigb[0][0] = 0;
             ampb[0][0] = make_double2(1.0, 0.0);
         }
         __syncthreads();
         build_index(idx, sigb[0], 1);
-        run_ops(S, r, n, sigb, ampb, idx, D.ops, D.off[ci], D.off[ci + 1], D.cap, D.eps2, 0u);
+        run_ops(S, r, n, sigb, ampb, idx, D.ops, D.off[ci], D.off[ci + 1], D.cap, D.eps2, 0u, &S.P, &S.ctab, 1);
         __syncthreads();
         // results
         double nr = 0.0;
@@ -713,11 +766,15 @@ __global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
 // seg_cap; the frame is left in buffer `cur` and the tableau, X-block size and
 // global phase are written back.
 constexpr int kSegThreads = 512;
+// frames of up to this many elements stay in shared memory (96 KB for the two buffers)
+constexpr unsigned kSegSmemElems = 2048;
 
 __global__ void __launch_bounds__(kSegThreads) k_segment(SfDev d, const OpRec* ops, unsigned long long n_ops,
                                                         double eps2, unsigned seg_cap, int cur,
                                                         unsigned long long* consumed, unsigned long long* out_meas) {
-    extern __shared__ uint32_t idx[];  // [slots_for(seg_cap)]
+    // [slots_for(seg_cap)] index slots, then (seg_cap <= kSegSmemElems) the two
+    // frame buffers: 2 x seg_cap phase vectors, 2 x seg_cap amplitudes
+    extern __shared__ uint32_t idx[];
     __shared__ Shared S;
     if (*(volatile uint32_t*)d.status) return;
     const int n = d.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -756,8 +813,16 @@ __global__ void __launch_bounds__(kSegThreads) k_segment(SfDev d, const OpRec* o
             r[hf].t0 = r[hf].t1 = 0;
         }
     }
-    uint64_t* const sigb[2] = {d.sig[cur], d.sig[cur ^ 1]};
-    double2* const ampb[2] = {d.amp[cur], d.amp[cur ^ 1]};
+    // small frames live in shared memory for the whole program
+    const bool in_smem = seg_cap <= kSegSmemElems;
+    uint64_t* const fs = reinterpret_cast<uint64_t*>(idx + slots_for(seg_cap));
+    double2* const fa = reinterpret_cast<double2*>(fs + 2 * (size_t)seg_cap);
+    // then the plans of a run of diagonal records, one per warp
+    BrTab* const pbs = reinterpret_cast<BrTab*>(in_smem ? reinterpret_cast<char*>(fa + 2 * (size_t)seg_cap)
+                                                         : reinterpret_cast<char*>(fs));
+    double2(*const cbs)[4][16] = reinterpret_cast<double2(*)[4][16]>(pbs + kSegThreads / 32);
+    uint64_t* const sigb[2] = {in_smem ? fs : d.sig[cur], in_smem ? fs + seg_cap : d.sig[cur ^ 1]};
+    double2* const ampb[2] = {in_smem ? fa : d.amp[cur], in_smem ? fa + seg_cap : d.amp[cur ^ 1]};
     if (threadIdx.x == 0) {
         S.k = (unsigned)d.kcnt[cur];
         S.cur = 0;
@@ -767,17 +832,28 @@ __global__ void __launch_bounds__(kSegThreads) k_segment(SfDev d, const OpRec* o
         S.outcomes = 0;
         S.nmeas = 0;
         S.tbase = ~0ull;
+        S.pbase = S.pend = 0;
     }
     __syncthreads();
     unsigned long long done = 0;
-    if (S.k <= seg_cap) {
+    const bool runs = S.k <= seg_cap;
+    if (runs) {
+        if (in_smem) {
+            for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
+                fs[j] = d.sig[cur][j];
+                fa[j] = d.amp[cur][j];
+            }
+            __syncthreads();
+        }
         build_index(idx, sigb[0], S.k);
-        done = run_ops(S, r, n, sigb, ampb, idx, ops, 0, n_ops, seg_cap, eps2, seg_cap);
+        done = run_ops(S, r, n, sigb, ampb, idx, ops, 0, n_ops, seg_cap, eps2, seg_cap, pbs, cbs, kSegThreads / 32);
     }
-    if (S.cur == 1) {
+    if (runs && (in_smem || S.cur == 1)) {
+        const uint64_t* fsig = sigb[S.cur];
+        const double2* famp = ampb[S.cur];
         for (unsigned j = threadIdx.x; j < S.k; j += blockDim.x) {
-            sigb[0][j] = sigb[1][j];
-            ampb[0][j] = ampb[1][j];
+            d.sig[cur][j] = fsig[j];
+            d.amp[cur][j] = famp[j];
         }
     }
     if (warp == 0) {
@@ -827,7 +903,11 @@ int shape_index(uint32_t threads, bool smem_index) {
 
 }  // namespace
 
-size_t sf_segment_smem_bytes(unsigned seg_cap) { return index_slots_for(seg_cap) * sizeof(uint32_t); }
+size_t sf_segment_smem_bytes(unsigned seg_cap) {
+    return index_slots_for(seg_cap) * sizeof(uint32_t) +
+           (seg_cap <= kSegSmemElems ? 2 * (size_t)seg_cap * (sizeof(uint64_t) + sizeof(double2)) : 0) +
+           (kSegThreads / 32) * (sizeof(BrTab) + 4 * 16 * sizeof(double2));
+}
 
 void sf_launch_segment(const SfDev& d, const void* ops, unsigned long long n_ops, double eps2, unsigned seg_cap,
                        int cur, unsigned long long* consumed, unsigned long long* out_meas, cudaStream_t s) {

@@ -152,28 +152,49 @@ __device__ __forceinline__ int popc_and(const uint64_t* a, const uint64_t* b) {
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+__device__ __forceinline__ double dneg_if(double x, bool neg) {  // sign flip on the integer pipe
+    return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)neg << 63));
+}
 __device__ __forceinline__ double2 ipow_mul(double2 a, int k) {  // a * i^k
     switch (k & 3) {
         case 0: return a;
-        case 1: return make_double2(-a.y, a.x);
-        case 2: return make_double2(-a.x, -a.y);
-        default: return make_double2(a.y, -a.x);
+        case 1: return make_double2(dneg_if(a.y, true), a.x);
+        case 2: return make_double2(dneg_if(a.x, true), dneg_if(a.y, true));
+        default: return make_double2(a.y, dneg_if(a.x, true));
     }
 }
 
-// e^{i theta} of diagonal gate kind (T, T-dagger: theta = +-pi/4), computed
-// once on the host for a launch from the host: the double-precision pipe of an
-// SM is narrow, and every CTA would otherwise evaluate the same sincos
-inline double2 sf_phase_host(uint32_t kind, double theta) {
+// Terms of diagonal gate kind as sum_j c_j Z^{w_j} (Sec. IV), from
+// e^{i theta} = cs + i sn (T, T-dagger: theta = +-pi/4).  Kinds 0-2:
+// P(theta) = (1 + e^{i theta})/2 I + (1 - e^{i theta})/2 Z_q0, terms I, Z_q0.
+// Kind 3: CR(theta) = I + (e^{i theta} - 1)(I - Z_c - Z_t + Z_c Z_t)/4, terms
+// I, Z_c, Z_t, Z_c Z_t.
+struct SfTerms {
+    double2 c[4];
+};
+__host__ __device__ inline SfTerms diag_terms(uint32_t kind, double cs, double sn) {
+    SfTerms T;
+    if (kind <= 2) {
+        T.c[0] = make_double2((1.0 + cs) * 0.5, sn * 0.5);
+        T.c[1] = make_double2((1.0 - cs) * 0.5, -sn * 0.5);
+        T.c[2] = T.c[3] = make_double2(0.0, 0.0);
+    } else {
+        const double2 dd = make_double2((cs - 1.0) * 0.25, sn * 0.25);
+        T.c[0] = make_double2(1.0 + dd.x, dd.y);
+        T.c[1] = T.c[2] = make_double2(-dd.x, -dd.y);
+        T.c[3] = dd;
+    }
+    return T;
+}
+// computed once on the host for a launch from the host: the double-precision
+// pipe of an SM is narrow, and every CTA would otherwise evaluate them
+inline SfTerms diag_terms_host(uint32_t kind, double theta) {
     const double th = kind == 0 ? 0.78539816339744830962 : (kind == 1 ? -0.78539816339744830962 : theta);
-    return make_double2(std::cos(th), std::sin(th));
+    return diag_terms(kind, std::cos(th), std::sin(th));
 }
 
 // Double-precision work runs on a narrow pipe, so the per-element kernels keep
 // it to the multiply-adds of the amplitudes.
-__device__ __forceinline__ double dneg_if(double x, bool neg) {  // sign flip without the FP64 pipe
-    return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)neg << 63));
-}
 // coefficient sum_t (-1)^{bit t of p} c_t of a group of nt diagonal-gate
 // terms, added in the order t = 0, 1, ... (the per-element sum of the terms
 // for the sign pattern p)

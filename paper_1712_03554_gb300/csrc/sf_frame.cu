@@ -258,24 +258,23 @@ __device__ __forceinline__ uint64_t warp_or(uint64_t v) {
 
 // called by the 32 lanes of one warp; lane 0 writes P
 template <int W>
-__device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double2 eth,
+// tm: the term coefficients of the gate (diag_terms)
+__device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, const SfTerms& tm,
                                  BrPlan<W>& P) {
     const int lane = threadIdx.x & 31, n = d.n;
-    const double cs = eth.x, sn = eth.y;  // e^{i theta}
+    const double2* cf = tm.c;
     int nt;
     int wq[SF_BR_MAXT][2];
-    double2 cf[SF_BR_MAXT];
-    if (kind <= 2) {  // P(theta) = (1 + e^{i theta})/2 I + (1 - e^{i theta})/2 Z_q0
+    if (kind <= 2) {  // terms I, Z_q0
         nt = 2;
-        wq[0][0] = -1; wq[0][1] = -1; cf[0] = make_double2((1.0 + cs) * 0.5, sn * 0.5);
-        wq[1][0] = (int)q0; wq[1][1] = -1; cf[1] = make_double2((1.0 - cs) * 0.5, -sn * 0.5);
-    } else {  // CR(theta) = I + (e^{i theta} - 1)(I - Z_c - Z_t + Z_c Z_t)/4
+        wq[0][0] = -1; wq[0][1] = -1;
+        wq[1][0] = (int)q0; wq[1][1] = -1;
+    } else {  // terms I, Z_c, Z_t, Z_c Z_t
         nt = 4;
-        const double2 dd = make_double2((cs - 1.0) * 0.25, sn * 0.25);
-        wq[0][0] = -1; wq[0][1] = -1; cf[0] = make_double2(1.0 + dd.x, dd.y);
-        wq[1][0] = (int)q0; wq[1][1] = -1; cf[1] = make_double2(-dd.x, -dd.y);
-        wq[2][0] = (int)q1; wq[2][1] = -1; cf[2] = make_double2(-dd.x, -dd.y);
-        wq[3][0] = (int)q0; wq[3][1] = (int)q1; cf[3] = dd;
+        wq[0][0] = -1; wq[0][1] = -1;
+        wq[1][0] = (int)q0; wq[1][1] = -1;
+        wq[2][0] = (int)q1; wq[2][1] = -1;
+        wq[3][0] = (int)q0; wq[3][1] = (int)q1;
     }
     uint64_t um[SF_BR_MAXT][W], vm[SF_BR_MAXT][W], wz[SF_BR_MAXT][W], odd[W];
     int epsq[SF_BR_MAXT];
@@ -387,11 +386,11 @@ __device__ __forceinline__ double2 group_coef(const BrPlan<W>& P, int g, const u
 // children of a diagonal gate written out unmerged: child g of element j at
 // g * k + j
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_branch(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1, double2 eth,
+__global__ void __launch_bounds__(kThreads) k_branch(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1, SfTerms tm,
                                                      int in_buf, int out_buf) {
     __shared__ BrPlan<W> P;
     if (*d.status) return;
-    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, eth, P);
+    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, tm, P);
     __syncthreads();
     if (P.bad) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 23u);
@@ -812,7 +811,7 @@ __global__ void __launch_bounds__(kThreads) k_build_index(SfDev d, int b) {
 // in a fixed order.  No amplitude atomics; the output frame is indexed.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1,
-                                                           double2 eth, double eps2, int in_buf, int out_buf) {
+                                                           SfTerms tm, double eps2, int in_buf, int out_buf) {
     __shared__ BrPlan<W> P;
     __shared__ int xidx[SF_BR_MAXG][SF_BR_MAXG];
     __shared__ double2 ctab[SF_BR_MAXG][1 << SF_BR_MAXT];  // group coefficient per sign pattern
@@ -833,29 +832,30 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
         }
         return;
     }
-    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, eth, P);
+    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, tm, P);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int bad = P.bad;
-        for (int g = 0; g < P.ng; g++)
-            for (int g2 = 0; g2 < P.ng; g2++) {
-                int m = -1;
-                for (int g3 = 0; g3 < P.ng; g3++) {
-                    bool eq = true;
-                    for (int w = 0; w < W; w++) eq &= (P.u[g][w] ^ P.u[g2][w]) == P.u[g3][w];
-                    if (eq) { m = g3; break; }
-                }
-                if (m < 0) bad = 1;
-                xidx[g][g2] = m < 0 ? 0 : m;
+    // xidx[g][g2]: the group whose u is u_g ^ u_g2 (threads 0-15, one entry
+    // each); threads 32-95: the coefficient of each group per sign pattern
+    int bad = 0;
+    if (threadIdx.x < SF_BR_MAXG * SF_BR_MAXG) {
+        const int g = threadIdx.x / SF_BR_MAXG, g2 = threadIdx.x % SF_BR_MAXG;
+        if (g < P.ng && g2 < P.ng) {
+            int m = -1;
+            for (int g3 = 0; g3 < P.ng && m < 0; g3++) {
+                bool eq = true;
+                for (int w = 0; w < W; w++) eq &= (P.u[g][w] ^ P.u[g2][w]) == P.u[g3][w];
+                if (eq) m = g3;
             }
-        for (int w = 0; w < W; w++) bad |= (P.u[0][w] != 0);
-        P.bad = bad;
+            bad = m < 0;
+            xidx[g][g2] = m < 0 ? 0 : m;
+        }
+        if (threadIdx.x == 0)
+            for (int w = 0; w < W; w++) bad |= (P.u[0][w] != 0);
     } else if (threadIdx.x >= 32 && threadIdx.x < 32 + SF_BR_MAXG * (1 << SF_BR_MAXT)) {
         const int e = threadIdx.x - 32, g = e >> SF_BR_MAXT, p = e & ((1 << SF_BR_MAXT) - 1);
         if (!P.bad && g < P.ng && p < (1 << P.nt[g])) ctab[g][p] = coef_pattern(P.c[g], P.nt[g], p);
     }
-    __syncthreads();
-    if (P.bad) {
+    if (__syncthreads_or(bad) || P.bad) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 26u);
         return;
     }
@@ -1175,8 +1175,8 @@ void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s) {
 
 void sf_launch_branch(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
                       int out_buf, cudaStream_t s) {
-    const double2 eth = sf_phase_host(kind, theta);
-    SF_DISPATCH(d.W, k_branch<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, eth, in_buf, out_buf));
+    const SfTerms tm = diag_terms_host(kind, theta);
+    SF_DISPATCH(d.W, k_branch<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, tm, in_buf, out_buf));
 }
 
 void sf_launch_insert(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
@@ -1185,8 +1185,8 @@ void sf_launch_insert(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
 
 void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, double eps,
                             int in_buf, int out_buf, cudaStream_t s) {
-    const double2 eth = sf_phase_host(kind, theta);
-    SF_DISPATCH(d.W, k_branch_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, eth, eps * eps, in_buf, out_buf));
+    const SfTerms tm = diag_terms_host(kind, theta);
+    SF_DISPATCH(d.W, k_branch_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, tm, eps * eps, in_buf, out_buf));
 }
 
 void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {

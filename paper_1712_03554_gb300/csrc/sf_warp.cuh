@@ -424,87 +424,181 @@ struct BrTab {
     int xidx[4][4];
 };
 
-// eth = e^{i theta}
-__device__ __forceinline__ void warp_branch_plan_regs(const Row* r, int n, uint32_t kind, int q0, int q1, double2 eth,
-                                             BrTab& P) {
+// cf: the nt term coefficients of the gate (diag_terms).  Every lane derives
+// the groups from warp-uniform values; the lanes split the writes of P and of
+// the coefficient table.  ctab[g][p] holds sum_t (-1)^{bit t of p} c_t for
+// the patterns p of group g whose last-term bit is clear (terms in order); the
+// other half are their negations.  A double-precision instruction costs the
+// same pipe time for one lane as for 32, so the table takes one add per extra
+// term of the largest group, all lanes at once.
+__device__ __forceinline__ void warp_branch_plan_regs(const Row* r, int n, uint32_t kind, int q0, int q1,
+                                                      const double2* cf, BrTab& P, double2 (*ctab)[16]) {
     const int lane = threadIdx.x & 31;
-    const double cs = eth.x, sn = eth.y;
-    int nt;
+    const int nt = kind <= 2 ? 2 : 4;
     uint64_t wz[4];
-    double2 cf[4];
-    if (kind <= 2) {
-        nt = 2;
-        wz[0] = 0; cf[0] = make_double2((1.0 + cs) * 0.5, sn * 0.5);
-        wz[1] = 1ull << q0; cf[1] = make_double2((1.0 - cs) * 0.5, -sn * 0.5);
-    } else {
-        nt = 4;
-        const double2 dd = make_double2((cs - 1.0) * 0.25, sn * 0.25);
-        wz[0] = 0; cf[0] = make_double2(1.0 + dd.x, dd.y);
-        wz[1] = 1ull << q0; cf[1] = make_double2(-dd.x, -dd.y);
-        wz[2] = 1ull << q1; cf[2] = make_double2(-dd.x, -dd.y);
-        wz[3] = (1ull << q0) | (1ull << q1); cf[3] = dd;
+    wz[0] = 0;
+    wz[1] = 1ull << q0;
+    wz[2] = kind == 3 ? 1ull << q1 : 0;
+    wz[3] = wz[1] | wz[2];
+    // Z^{w_j} = eps_j D^{u_j} M^{v_j} for the one-qubit terms j = 1, 2, both
+    // decompositions interleaved (u_h = [Z^w anticommutes with M_h],
+    // v_h = [Z^w anticommutes with D_h], product of D_h^{u_h} M_h^{v_h})
+    uint64_t cx[2] = {0, 0}, cz[2] = {0, 0};
+    int ce[2] = {0, 0};
+    bool ub[2][2], vb[2][2];
+#pragma unroll
+    for (int hf = 0; hf < 2; hf++) {
+        const int row = lane + 32 * hf;
+        const uint64_t mx = r[hf].mx, mz = r[hf].mz, dx = r[hf].dx, dz = r[hf].dz;
+        const int de = (int)r[hf].de;
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            const uint64_t w = wz[1 + a];
+            ub[a][hf] = row < n && (__popcll(mx & w) & 1);
+            vb[a][hf] = row < n && (__popcll(dx & w) & 1);
+            if (ub[a][hf]) pmul1(cx[a], cz[a], ce[a], dx, dz, de);
+            if (vb[a][hf]) pmul1(cx[a], cz[a], ce[a], mx, mz, 0);
+        }
     }
     uint64_t um[4], vm[4];
     int epsq[4], bad = 0;
-    for (int j = 0; j < nt; j++) {
-        if (wz[j] == 0) {  // the identity term: u = v = 0, eps = 1
-            um[j] = vm[j] = 0;
-            epsq[j] = 0;
-            continue;
-        }
-        if (kind == 3 && j == 3) {
-            // Z_c Z_t from the two one-qubit terms: Z^{w1} Z^{w2} = eps1 eps2 D^{u1} M^{v1} D^{u2} M^{v2};
-            // moving M^{v1} past D^{u2} gives (-1)^{|v1 & u2|}, D^{u1} D^{u2} = D^{u1^u2} up to the
-            // squares of the shared destabilizers (-1 for an odd i-power)
-            const unsigned o0 = __ballot_sync(SF_FULL, lane < n && (r[0].de & 1u));
-            const unsigned o1 = __ballot_sync(SF_FULL, lane + 32 < n && (r[1].de & 1u));
-            const uint64_t odd = (uint64_t)o0 | ((uint64_t)o1 << 32);
-            um[3] = um[1] ^ um[2];
-            vm[3] = vm[1] ^ vm[2];
-            epsq[3] = (epsq[1] + epsq[2] + 2 * (__popcll(vm[1] & um[2]) + __popcll(um[1] & um[2] & odd))) & 3;
-            continue;
-        }
-        uint64_t cx = 0, cz = 0;
-        int ce = 0;
-        bool ub[2], vb[2];
-        for (int hf = 0; hf < 2; hf++) {
-            const int row = lane + 32 * hf;
-            ub[hf] = row < n && (__popcll(r[hf].mx & wz[j]) & 1);
-            vb[hf] = row < n && (__popcll(r[hf].dx & wz[j]) & 1);
-            if (ub[hf]) pmul1(cx, cz, ce, r[hf].dx, r[hf].dz, (int)r[hf].de);
-            if (vb[hf]) pmul1(cx, cz, ce, r[hf].mx, r[hf].mz, 0);
-        }
-        um[j] = (uint64_t)__ballot_sync(SF_FULL, ub[0]) | ((uint64_t)__ballot_sync(SF_FULL, ub[1]) << 32);
-        vm[j] = (uint64_t)__ballot_sync(SF_FULL, vb[0]) | ((uint64_t)__ballot_sync(SF_FULL, vb[1]) << 32);
-        warp_prod(cx, cz, ce);
-        if (cx != 0 || cz != wz[j]) bad = 1;
-        epsq[j] = (4 - ce) & 3;
+    um[0] = vm[0] = 0;
+    epsq[0] = 0;  // the identity term: u = v = 0, eps = 1
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        um[1 + a] = (uint64_t)__ballot_sync(SF_FULL, ub[a][0]) | ((uint64_t)__ballot_sync(SF_FULL, ub[a][1]) << 32);
+        vm[1 + a] = (uint64_t)__ballot_sync(SF_FULL, vb[a][0]) | ((uint64_t)__ballot_sync(SF_FULL, vb[a][1]) << 32);
     }
-    if (lane != 0) return;
-    int gid[4], ng = 0;
-    for (int j = 0; j < nt; j++) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        uint64_t ox[2], oz[2];
+        int oe[2];
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            ox[a] = __shfl_xor_sync(SF_FULL, cx[a], off);
+            oz[a] = __shfl_xor_sync(SF_FULL, cz[a], off);
+            oe[a] = __shfl_xor_sync(SF_FULL, ce[a], off);
+        }
+#pragma unroll
+        for (int a = 0; a < 2; a++) pmul1(cx[a], cz[a], ce[a], ox[a], oz[a], oe[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        if (cx[a] != 0 || cz[a] != wz[1 + a]) bad = 1;
+        epsq[1 + a] = (4 - ce[a]) & 3;
+    }
+    if (kind == 3) {
+        // Z_c Z_t from the two one-qubit terms: Z^{w1} Z^{w2} = eps1 eps2 D^{u1} M^{v1} D^{u2} M^{v2};
+        // moving M^{v1} past D^{u2} gives (-1)^{|v1 & u2|}, D^{u1} D^{u2} = D^{u1^u2} up to the
+        // squares of the shared destabilizers (-1 for an odd i-power)
+        const unsigned o0 = __ballot_sync(SF_FULL, lane < n && (r[0].de & 1u));
+        const unsigned o1 = __ballot_sync(SF_FULL, lane + 32 < n && (r[1].de & 1u));
+        const uint64_t odd = (uint64_t)o0 | ((uint64_t)o1 << 32);
+        um[3] = um[1] ^ um[2];
+        vm[3] = vm[1] ^ vm[2];
+        epsq[3] = (epsq[1] + epsq[2] + 2 * (__popcll(vm[1] & um[2]) + __popcll(um[1] & um[2] & odd))) & 3;
+    } else {  // one-qubit gate: terms 0 and 1 only
+        um[2] = um[3] = vm[2] = vm[3] = 0;
+        epsq[2] = epsq[3] = 0;
+    }
+    // groups by u in order of first appearance (group 0: the identity term)
+    int gid[4], tpos[4], gnt[4] = {0, 0, 0, 0}, ng = 0;
+    uint64_t gu[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        gid[j] = -1;
+        tpos[j] = 0;
+        if (j >= nt) continue;
         int found = -1;
+#pragma unroll
         for (int j2 = 0; j2 < j; j2++)
-            if (um[j2] == um[j]) { found = gid[j2]; break; }
-        gid[j] = found >= 0 ? found : ng++;
+            if (found < 0 && um[j2] == um[j]) found = gid[j2];
+        if (found < 0) {
+            found = ng;
+#pragma unroll
+            for (int g = 0; g < 4; g++)
+                if (g == ng) gu[g] = um[j];
+            ng++;
+        }
+        gid[j] = found;
+#pragma unroll
+        for (int g = 0; g < 4; g++)
+            if (g == found) tpos[j] = gnt[g]++;
     }
-    P.ng = ng;
-    for (int g = 0; g < ng; g++) P.nt[g] = 0;
-    for (int j = 0; j < nt; j++) {
-        const int g = gid[j], t = P.nt[g]++;
-        P.u[g] = um[j];
-        P.v[g][t] = vm[j];
-        P.c[g][t] = ipow_mul(cf[j], epsq[j]);
-    }
-    for (int g = 0; g < ng; g++)
-        for (int g2 = 0; g2 < ng; g2++) {
+    // P.xidx[g][g2] = the group whose u is u_g ^ u_g2 (lanes 0-15)
+    {
+        const int g = lane >> 2, g2 = lane & 3;
+        uint64_t ug = 0, ug2 = 0;
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            if (x == g) ug = gu[x];
+            if (x == g2) ug2 = gu[x];
+        }
+        bool miss = false;
+        if (lane < 16 && g < ng && g2 < ng) {
             int m = -1;
-            for (int g3 = 0; g3 < ng; g3++)
-                if ((P.u[g] ^ P.u[g2]) == P.u[g3]) { m = g3; break; }
-            if (m < 0) bad = 1;
+#pragma unroll
+            for (int g3 = 3; g3 >= 0; g3--)
+                if (g3 < ng && (ug ^ ug2) == gu[g3]) m = g3;
+            miss = m < 0;
             P.xidx[g][g2] = m < 0 ? 0 : m;
         }
-    if (P.u[0] != 0) bad = 1;
-    P.bad = bad;
+        if (__any_sync(SF_FULL, miss)) bad = 1;
+    }
+    // term coefficients c_j i^{eps_j} (sign flips and swaps only)
+    double2 ct[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) ct[j] = j < nt ? ipow_mul(cf[j], epsq[j]) : make_double2(0.0, 0.0);
+    // table: lane 2q + comp takes component comp of the q-th half-table entry
+    // (groups in order, 2^{nt_g - 1} entries each)
+    {
+        const int q = lane >> 1;
+        const bool comp = lane & 1;
+        int g = -1, pp = 0, base = 0, gn = 0;
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            const int sz = x < ng ? 1 << (gnt[x] - 1) : 0;
+            if (g < 0 && q < base + sz) {
+                g = x;
+                pp = q - base;
+                gn = gnt[x];
+            }
+            base += sz;
+        }
+        // the terms of group g in order, signed by pattern pp
+        double val[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (gid[j] != g || g < 0) continue;
+            const double x = comp ? ct[j].y : ct[j].x;
+#pragma unroll
+            for (int t = 0; t < 4; t++)
+                if (t == tpos[j]) val[t] = dneg_if(x, (pp >> t) & 1);
+        }
+        int maxn = 0;
+#pragma unroll
+        for (int x = 0; x < 4; x++) maxn = gnt[x] > maxn ? gnt[x] : maxn;
+        double acc = val[0];
+        if (maxn > 1) acc += gn > 1 ? val[1] : 0.0;
+        if (maxn > 2) acc += gn > 2 ? val[2] : 0.0;
+        if (maxn > 3) acc += gn > 3 ? val[3] : 0.0;
+        if (g >= 0) reinterpret_cast<double*>(&ctab[g][pp])[comp] = acc;
+    }
+    // the rest of P, one field per lane
+    if (lane < 4) {
+        P.nt[lane] = gnt[lane];
+        P.u[lane] = gu[lane];
+    } else if (lane < 20) {
+        const int g = (lane - 4) >> 2, t = (lane - 4) & 3;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (gid[j] == g && tpos[j] == t) {
+                P.v[g][t] = vm[j];
+                P.c[g][t] = ct[j];
+            }
+    } else if (lane == 20) {
+        P.ng = ng;
+        P.bad = bad | (gu[0] != 0);
+    }
 }
 }  // namespace sfw
