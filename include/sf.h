@@ -185,7 +185,8 @@ enum { SF_K_CLIFFORD = 0,      /* tableau update of a Clifford batch (single CTA
        SF_K_EXPORT = 14, SF_K_RESET = 15,
        SF_K_SEGMENT = 16,      /* sf_apply_program (single CTA) */
        SF_K_COND = 17,         /* the 11-cofactor step of sf_apply_toffoli / sf_apply_cr_cofactor */
-       SF_K_COUNT_CLASSES = 18 };
+       SF_K_GPROG = 18,        /* sf_apply_program_grid (one cooperative launch) */
+       SF_K_COUNT_CLASSES = 19 };
 
 /* Number of CUDA kernels this handle has launched since it was created. */
 uint64_t sf_kernel_launches(sf_handle h);
@@ -314,6 +315,33 @@ typedef struct {
  * Outcomes follow the draw rule of the campaign engine.  Asynchronous. */
 sf_status sf_apply_program(sf_handle h, const sf_op* dev_ops, uint64_t n_ops, double drop_eps,
                            uint64_t max_frame, uint64_t* dev_consumed, uint64_t* dev_meas);
+
+/* A program of Clifford and diagonal sf_op records (kinds 0..8 and 16..19;
+ * ROTATE and merged branching, Sec. III-IV) applied to this handle's frame, of
+ * any size up to max_elems, in ONE cooperative launch over the whole GPU, for
+ * handles with n_qubits <= 63.  One persistent CTA per SM walks the records;
+ * a Clifford run is applied to the tableau by one warp and to the phase
+ * vectors by every CTA (with a fresh index), a run of diagonal records is
+ * planned at once (one CTA per record) and then merged record by record, and
+ * grid barriers separate the phases.  This replaces the per-op launches (a
+ * tableau kernel, an affine pass and an index rebuild per Clifford run, a
+ * merge kernel per diagonal gate) with the same frame results as the per-op
+ * calls (amplitudes to rounding).
+ *
+ * dev_ops: n_ops records in device memory (valid until the stream reaches the
+ * call).  The records are checked first (qubits and kinds; measurement and
+ * conditional records are accepted); a bad record fails the call (SF_EINVAL,
+ * deferred) with the frame untouched.  The run stops before the first
+ * measurement or conditional record; dev_consumed (device, one uint64,
+ * nullable) receives the number of records applied, so the caller continues
+ * with the per-op calls from there.  A frame that would exceed max_elems fails
+ * the call (SF_ECAPACITY, deferred), the frame holding the state before the
+ * failing record.  A grid barrier that waits for more than about a second
+ * fails the call with SF_ETIMEOUT (deferred).  The frame ends in the handle's
+ * current buffer with its index built.  Asynchronous; two calls on the same
+ * handle are ordered by its stream. */
+sf_status sf_apply_program_grid(sf_handle h, const sf_op* dev_ops, uint64_t n_ops, double drop_eps,
+                                uint64_t* dev_consumed);
 
 typedef struct sf_campaign_s* sf_campaign;
 

@@ -198,6 +198,7 @@ sf_status sync_check(sf_handle h) {
         SF_CK(h, cudaMemsetAsync(h->d.status, 0, sizeof(uint32_t), h->stream));
         SF_CK(h, cudaMemsetAsync(h->d.done, 0, sizeof(unsigned int), h->stream));
         SF_CK(h, cudaMemsetAsync(h->d.ocnt, 0, sizeof(unsigned long long), h->stream));
+        if (h->d.gp) SF_CK(h, sf_gprog_reset(h->d, h->stream));
         sf_status cs = clean_table(h);
         if (cs) return cs;
         SF_CK(h, cudaStreamSynchronize(h->stream));
@@ -331,6 +332,7 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     SF_ALLOC(d.ipend, 1);
     SF_ALLOC(d.red, 4 * (size_t)d.nblk);
     SF_ALLOC(d.out, 8);
+    if (W == 1) SF_ALLOC(d.gp, sf_gprog_work_words());
     SF_ALLOC(h->dy, W);
     h->dgates_cap = 256;
     SF_ALLOC(h->dgates, h->dgates_cap);
@@ -354,6 +356,7 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     cudaMemsetAsync(d.isize, 0, 2 * sizeof(unsigned long long), h->stream);
     cudaMemsetAsync(d.done, 0, sizeof(unsigned int), h->stream);
     cudaMemsetAsync(d.ocnt, 0, sizeof(unsigned long long), h->stream);
+    if (d.gp) cudaMemsetAsync(d.gp, 0, sf_gprog_work_words() * sizeof(uint64_t), h->stream);
     if (clean_table(h) != SF_OK) {
         sf_destroy(h);
         return fail(nullptr, SF_ECUDA, "table initialisation failed");
@@ -500,6 +503,29 @@ sf_status sf_apply_program(sf_handle h, const sf_op* dev_ops, uint64_t n_ops, do
                                 reinterpret_cast<unsigned long long*>(dev_meas), h->stream));
     // the kernel leaves the frame in the current buffer; neither index is valid now
     h->idx_ok[0] = h->idx_ok[1] = false;
+    return SF_OK;
+}
+
+sf_status sf_apply_program_grid(sf_handle h, const sf_op* dev_ops, uint64_t n_ops, double drop_eps,
+                                uint64_t* dev_consumed) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (h->d.W != 1) return fail(h, SF_EINVAL, "sf_apply_program_grid needs n_qubits <= 63");
+    if (n_ops && !dev_ops) return fail(h, SF_EINVAL, "dev_ops is NULL");
+    if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");
+    if (n_ops == 0) {
+        if (dev_consumed) SF_CK(h, cudaMemsetAsync(dev_consumed, 0, sizeof(uint64_t), h->stream));
+        return SF_OK;
+    }
+    sf_status st = need_index(h, h->cur);
+    if (st) return st;
+    cudaError_t ge = cudaSuccess;
+    SF_LAUNCH(h, SF_K_GPROG,
+              ge = sf_launch_gprog(h->d, dev_ops, n_ops, drop_eps * drop_eps, h->cur,
+                                   reinterpret_cast<unsigned long long*>(dev_consumed), h->stream));
+    if (ge != cudaSuccess) return cuda_fail(h, ge, "grid program launch");
+    // the frame ends in the current buffer with its index; the other index is stale
+    h->idx_ok[h->cur] = true;
+    h->idx_ok[h->cur ^ 1] = false;
     return SF_OK;
 }
 

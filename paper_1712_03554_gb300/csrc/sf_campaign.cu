@@ -28,11 +28,6 @@ namespace {
 constexpr int kMaxWarps = 16;  // threads per circuit: 32..256 (campaign), 512 (program segment)
 constexpr int kCampMaxCap = SF_CAMPAIGN_MAX_ELEMS;
 
-struct OpRec {
-    uint32_t kind, q0, q1, arg;
-    double param;
-};
-
 struct CampDev {
     int n, ncirc;
     unsigned cap;
@@ -298,38 +293,10 @@ while (oi < o1 && S.status == 0) {
                         bad = 1;
                         break;
                     }
-                    int yq = -1, cq = -1;
-                    if (gk == 0) {
-                        cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
-                        if (cq == 2) yq = q0;
-                    } else if (gk == 3 || gk == 4) {
-                        yq = q0;
-                    }
-                    int na, nb;
-                    cliff_num_exp(gk, cq, na, nb);
-                    const int r_old = rx;
-                    for (int hf = 0; hf < 2; hf++) {
-                        const int row = lane + 32 * hf;
-                        if (row < n) {
-                            const uint32_t f = (uint32_t)conj1(gk, q0, q1, r[hf].mx, r[hf].mz);
-                            r[hf].t0 ^= f;
-                            r[hf].t1 = f;
-                            const int fd = conj1(gk, q0, q1, r[hf].dx, r[hf].dz);
-                            r[hf].de = (r[hf].de + 2u * (uint32_t)fd) & 3u;
-                        } else {
-                            r[hf].t1 = 0;
-                        }
-                    }
-                    // Pauli gates flip signs only: M keeps its bits and stays in RREF
-                    if (gk < 3 || gk > 5) rx = warp_rref(r, n, S.stage);
-                    const int dq = rx < 0 ? -1 : warp_amp_phi(r, n, rx, true, yq >= 0 ? (1ull << yq) : 0ull);
-                    if (dq < 0) {
+                    if (!warp_clifford_gate(r, n, rx, gk, q0, q1, S.stage, ga, gb)) {
                         bad = 2;
                         break;
                     }
-                    const int dr = rx - r_old;
-                    ga = (ga + na + 2 * ((4 - dq) & 3)) & 7;
-                    gb += nb + (dr > 0) - (dr < 0);
                     if (single || gi >= o1) break;
                     const unsigned long long d = gi - wb;  // 1..32
                     const uint32_t nk = d < 32 ? __shfl_sync(SF_FULL, w0.kind, (int)d)

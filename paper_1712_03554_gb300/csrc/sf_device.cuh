@@ -75,6 +75,14 @@ struct SfDev {
     unsigned int* done;        // CTAs finished (last-CTA publication of tags and counts)
     unsigned long long* ipend; // index size chosen by CTA 0, published by the last CTA
     unsigned long long* ocnt;  // output counter of the merge kernels
+    uint64_t* gp;              // workspace of the grid program (n <= 63 only)
+};
+
+// one program record (the layout of sf_op): kind, qubits, conditional-gate
+// kind or parameter bits
+struct OpRec {
+    uint32_t kind, q0, q1, arg;
+    double param;
 };
 
 // An empty one-word slot key: with W = 1 (n <= 63) phase vectors never set
@@ -261,9 +269,12 @@ __device__ __forceinline__ void set_status(uint32_t* st, uint32_t code, int buf,
 // ---- frame index ---------------------------------------------------------------
 __device__ __forceinline__ uint32_t next_tag(uint32_t t) { return (t % 0x7ffffffeu) + 1u; }
 
+// slots of an index for k keys: load factor at most 1/4 (1/2 for frames above
+// half the capacity), which keeps the longest linear-probe chain of a pass --
+// every probe a dependent L2 round trip -- short
 __host__ __device__ inline unsigned long long index_slots(unsigned long long k, unsigned long long icap) {
     unsigned long long t = 64;
-    while (t < 2 * k && t < icap) t <<= 1;
+    while (t < 4 * k && t < icap) t <<= 1;
     return t < icap ? t : icap;
 }
 
@@ -395,6 +406,10 @@ void sf_launch_amp_prep(const SfDev& d, const uint64_t* dev_y, cudaStream_t s);
 void sf_launch_segment(const SfDev& d, const void* ops, unsigned long long n_ops, double eps2, unsigned seg_cap,
                        int cur, unsigned long long* consumed, unsigned long long* out_meas, cudaStream_t s);
 size_t sf_segment_smem_bytes(unsigned seg_cap);
+size_t sf_gprog_work_words();
+cudaError_t sf_gprog_reset(const SfDev& d, cudaStream_t s);
+cudaError_t sf_launch_gprog(const SfDev& d, const void* ops, unsigned long long n_ops, double eps2, int cur,
+                            unsigned long long* consumed, cudaStream_t s);
 size_t sf_tableau_smem_bytes(int n, int W, int NT);
 
 void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s);

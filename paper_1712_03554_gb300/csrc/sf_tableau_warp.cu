@@ -39,39 +39,10 @@ __global__ void __launch_bounds__(32) k_clifford_warp(SfDev d, const sf_gate_rec
             return;
         }
         const int kind = (int)ukind, q0 = (int)uq0, q1 = two ? (int)uq1 : 0;
-        // numerator of the phase rule (see the block kernel)
-        int yq = -1, cq = -1;
-        if (kind == 0) {
-            cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
-            if (cq == 2) yq = q0;
-        } else if (kind == 3 || kind == 4) {
-            yq = q0;
-        }
-        int na, nb;
-        cliff_num_exp(kind, cq, na, nb);
-        const int r_old = rx;
-        for (int hf = 0; hf < 2; hf++) {
-            const int row = lane + 32 * hf;
-            if (row < n) {
-                const uint32_t f = (uint32_t)conj1(kind, q0, q1, r[hf].mx, r[hf].mz);
-                r[hf].t0 ^= f;
-                r[hf].t1 = f;
-                const int fd = conj1(kind, q0, q1, r[hf].dx, r[hf].dz);
-                r[hf].de = (r[hf].de + 2u * (uint32_t)fd) & 3u;
-            } else {
-                r[hf].t1 = 0;
-            }
-        }
-        // Pauli gates flip signs only: M keeps its bits and stays in RREF
-        if (kind < 3 || kind > 5) rx = warp_rref(r, n, stage);
-        const int dq = rx < 0 ? -1 : warp_amp_phi(r, n, rx, true, yq >= 0 ? (1ull << yq) : 0ull);
-        if (dq < 0) {
+        if (!warp_clifford_gate(r, n, rx, kind, q0, q1, stage, ga, gb)) {
             if (lane == 0) set_status(d.status, SF_ST_INTERNAL, buf, 8u);
             return;
         }
-        const int dr = rx - r_old;
-        ga = (ga + na + 2 * ((4 - dq) & 3)) & 7;
-        gb += nb + (dr > 0) - (dr < 0);
     }
     for (int hf = 0; hf < 2; hf++) {
         const int row = lane + 32 * hf;

@@ -413,6 +413,48 @@ __device__ __forceinline__ int warp_measure_prep(Row* r, int n, int rx, int q, C
     return rx2;
 }
 
+// One Clifford gate on the rows in registers (ROTATE, Sec. III, Table 2):
+// conjugate M and D (sign flips of M to t0, composed, and t1, this gate),
+// restore Invariant 1, and multiply the run's phase factor omega^ga sqrt(2)^gb
+// by the gate's.  rx is the X-block size.  Returns false if the phase rule
+// finds no point (an internal error).
+__device__ __forceinline__ bool warp_clifford_gate(Row* r, int n, int& rx, int kind, int q0, int q1, Row* stage,
+                                                   int& ga, int& gb) {
+    const int lane = threadIdx.x & 31;
+    // numerator of the phase rule: a point y with <y|U phi_0(M)> != 0
+    int yq = -1, cq = -1;
+    if (kind == 0) {
+        cq = warp_amp_phi(r, n, rx, false, 1ull << q0);
+        if (cq == 2) yq = q0;
+    } else if (kind == 3 || kind == 4) {
+        yq = q0;
+    }
+    int na, nb;
+    cliff_num_exp(kind, cq, na, nb);
+    const int r_old = rx;
+    for (int hf = 0; hf < 2; hf++) {
+        const int row = lane + 32 * hf;
+        if (row < n) {
+            const uint32_t f = (uint32_t)conj1(kind, q0, q1, r[hf].mx, r[hf].mz);
+            r[hf].t0 ^= f;
+            r[hf].t1 = f;
+            const int fd = conj1(kind, q0, q1, r[hf].dx, r[hf].dz);
+            r[hf].de = (r[hf].de + 2u * (uint32_t)fd) & 3u;
+        } else {
+            r[hf].t1 = 0;
+        }
+    }
+    // Pauli gates flip signs only: M keeps its bits and stays in RREF
+    if (kind < 3 || kind > 5) rx = warp_rref(r, n, stage);
+    // denominator: <y| D'^{t1} phi_0(M')>
+    const int dq = rx < 0 ? -1 : warp_amp_phi(r, n, rx, true, yq >= 0 ? (1ull << yq) : 0ull);
+    if (dq < 0) return false;
+    const int dr = rx - r_old;
+    ga = (ga + na + 2 * ((4 - dq) & 3)) & 7;
+    gb += nb + (dr > 0) - (dr < 0);
+    return true;
+}
+
 // ---- plan of a diagonal gate (Sec. IV) with the rows in registers ---------------
 // Terms c_j Z^{w_j}; Z^w = eps D^u M^v; terms grouped by u (group 0: u = 0).
 struct BrTab {

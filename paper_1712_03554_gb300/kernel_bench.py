@@ -10,6 +10,7 @@ amplitudes read and written; index and hash tables are not counted).
   python -m paper_1712_03554_gb300.kernel_bench latency
   python -m paper_1712_03554_gb300.kernel_bench merge-case 20   (a short run for ncu captures)
   python -m paper_1712_03554_gb300.kernel_bench qft-step [max_frame] (one eager QFT n=20 step, the bench's circuit)
+  python -m paper_1712_03554_gb300.kernel_bench qft-grid          (QFT n=20: per-op vs grid program, wall per pass)
   python -m paper_1712_03554_gb300.kernel_bench campaign-case 64 (one campaign launch, 32 threads, global index)
   python -m paper_1712_03554_gb300.kernel_bench clifford-case 1024 (one Clifford batch of 200 gates at n)
   python -m paper_1712_03554_gb300.kernel_bench cuccaro 5 6 7   (adder: Toffoli by cofactors vs Clifford+7T)
@@ -19,6 +20,8 @@ from __future__ import annotations
 import json
 import sys
 import time
+
+import numpy as np
 
 from . import circuits as c
 from . import sf
@@ -132,6 +135,46 @@ def qft_step(seed=0, max_frame=2048):
     print("k", f.size())
 
 
+def qft_grid(reps=5):
+    """QFT n = 20 (the bench's circuit) three ways, wall time per pass after a
+    warm-up (median of reps): the small-frame prefix in the single-CTA program
+    and the rest per op; the prefix and the rest in the grid program; all of
+    it in the grid program.  Then one frame check against the closed form."""
+    import torch
+    x, ops = c.qft_random_input(20, 0)
+    f = frame_of(20, 0, 1 << 21)
+    f.reset()
+    i = f.apply_program(ops, max_frame=2048)[0]
+    recs_a, _ = sf.encode_program([ops[:i]])
+    recs_b, _ = sf.encode_program([ops[i:]])
+    recs_all, _ = sf.encode_program([ops])
+    dev = {k: torch.from_numpy(v.view(np.uint8).copy()).cuda() for k, v in
+           (("a", recs_a), ("b", recs_b), ("all", recs_all))}
+    n_rec = {"a": len(recs_a), "b": len(recs_b), "all": len(recs_all)}
+    res = {}
+    for mode in ("prefix+per-op", "prefix+grid", "grid"):
+        ts = []
+        for rep in range(reps + 1):
+            f.reset()
+            f.sync()
+            t0 = time.perf_counter()
+            if mode == "grid":
+                f.apply_program_grid_device(dev["all"].data_ptr(), n_rec["all"])
+            else:
+                f.apply_program_device(dev["a"].data_ptr(), n_rec["a"], 1e-12, 0, 0, 2048)
+                if mode == "prefix+grid":
+                    f.apply_program_grid_device(dev["b"].data_ptr(), n_rec["b"])
+                else:
+                    c.run(f, ops[i:])
+            f.sync()
+            ts.append(time.perf_counter() - t0)
+        res[mode + "_ms"] = round(sorted(ts[1:])[len(ts[1:]) // 2] * 1e3, 3)
+        res[mode + "_k"] = f.size()
+        y = 12345
+        res[mode + "_amp_err"] = abs(f.amplitude(y) - c.qft_expected_amplitude(20, x, y))
+    print(json.dumps(res), flush=True)
+
+
 def campaign_case(nv=64):
     """One launch of the campaign kernel on nv Steane variants."""
     eng = sf.Campaign(c.STEANE_N, 4096)
@@ -188,6 +231,8 @@ if __name__ == "__main__":
         merge_case(args[0] if args else 20)
     elif mode == "qft-step":
         qft_step(max_frame=args[0] if args else 2048)
+    elif mode == "qft-grid":
+        qft_grid()
     elif mode == "campaign-case":
         campaign_case(args[0] if args else 64)
     elif mode == "cuccaro":

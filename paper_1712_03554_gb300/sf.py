@@ -19,7 +19,7 @@ SF_OK, SF_EINVAL, SF_ENOMEM, SF_ECAPACITY, SF_ECUDA, SF_ETIMEOUT, SF_ESTATE, SF_
 # kernel classes (SF_K_* in include/sf.h)
 KERNEL_CLASSES = ["clifford", "affine", "branch", "branch_merge", "insert", "compact", "index", "measure_prep",
                   "cofactor", "prob", "reduce", "amp_prep", "amplitude", "filter", "export", "reset", "segment",
-                  "cond"]
+                  "cond", "gprog"]
 STATUS_NAMES = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOMEM", 3: "SF_ECAPACITY", 4: "SF_ECUDA",
                 5: "SF_ETIMEOUT", 6: "SF_ESTATE", 7: "SF_EINTERNAL"}
 
@@ -38,6 +38,19 @@ class sf_gate(C.Structure):
 
 def library_path() -> str:
     return _build.LIB
+
+
+def _ops_consumed(ops, consumed: int) -> int:
+    """Op index after `consumed` program records: a "K" right after "N"
+    belongs to it, a lone "K" has no record."""
+    i, r = 0, 0
+    while i < len(ops) and r < consumed:
+        if ops[i][0] != "K":
+            r += 1
+        i += 1
+    while i < len(ops) and ops[i][0] == "K":
+        i += 1
+    return i
 
 
 def load(build: bool = True) -> C.CDLL:
@@ -60,6 +73,7 @@ def load(build: bool = True) -> C.CDLL:
         "sf_apply_nonclifford": ([H, u32, u32, u32, dbl], st),
         "sf_apply_nonclifford_coalesce": ([H, u32, u32, u32, dbl, dbl], st),
         "sf_apply_program": ([H, C.c_void_p, u64, dbl, u64, C.c_void_p, C.c_void_p], st),
+        "sf_apply_program_grid": ([H, C.c_void_p, u64, dbl, C.c_void_p], st),
         "sf_apply_toffoli": ([H, u32, u32, u32], st),
         "sf_apply_cr_cofactor": ([H, u32, u32, dbl], st),
         "sf_coalesce": ([H, dbl, P64], st),
@@ -460,15 +474,26 @@ class Frame:
         self.apply_program_device(d_ops.data_ptr(), len(recs), eps, out.data_ptr(), out.data_ptr() + 8, max_frame)
         self.sync()
         consumed, bits, nm = (int(v) for v in out.cpu().numpy().view(np.uint64))
-        # record index -> op index ("K" right after "N" belongs to it; lone "K" has no record)
-        i, r = 0, 0
-        while i < len(ops) and r < consumed:
-            if ops[i][0] != "K":
-                r += 1
-            i += 1
-        while i < len(ops) and ops[i][0] == "K":
-            i += 1
-        return i, bits, nm
+        return _ops_consumed(ops, consumed), bits, nm
+
+    def apply_program_grid_device(self, dev_ops: int, n_ops: int, eps: float = 1e-12, dev_consumed: int = 0) -> None:
+        """sf_apply_program_grid on device pointers (ints; 0 for NULL)."""
+        self._check(self.lib.sf_apply_program_grid(self.h, C.c_void_p(dev_ops or None), int(n_ops), float(eps),
+                                                   C.c_void_p(dev_consumed or None)), self.h)
+
+    def apply_program_grid(self, ops, eps: float = 1e-12) -> int:
+        """Apply ops through sf_apply_program_grid (one cooperative launch)
+        up to the first measurement or conditional gate.  Returns i: ops[:i]
+        were applied; continue with the per-op calls from ops[i]."""
+        import torch
+        recs, _ = encode_program([ops])
+        if len(recs) == 0:
+            return len(ops)
+        d_ops = torch.from_numpy(recs.view(np.uint8).copy()).cuda()
+        out = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.apply_program_grid_device(d_ops.data_ptr(), len(recs), eps, out.data_ptr())
+        self.sync()
+        return _ops_consumed(ops, int(out.cpu().numpy().view(np.uint64)[0]))
 
     def coalesce(self, eps: float = 1e-12, sync: bool = False) -> Optional[int]:
         if sync:
