@@ -104,6 +104,7 @@ def bytes_model(W: int, n: int = N_QUBITS):
         "amplitude": lambda kin, kout: e * kin,
         "reduce": lambda kin, kout: 0,
         "segment": lambda kin, kout: kin,  # recorded as the summed bytes of the ops it runs
+        "gprog": lambda kin, kout: kin,    # the same for the grid program
     }
 
 
@@ -123,11 +124,12 @@ def plan_records(sfm, plan):
     return np.array(recs, dtype=sfm.SF_OP_DTYPE), starts
 
 
-def choose_program_prefix(sfm, torch, n, plan, y, stream, candidates=(256, 512, 1024, 2048, 4096)):
+def choose_program_prefix(sfm, torch, n, plan, y, stream, candidates=(256, 512, 1024, 2048, 4096), grid=True):
     """The single-CTA program (sf_apply_program) runs the first plan entries while
-    the frame is small; pick its frame limit by timing the eager step for each
-    candidate (and without it).  Returns (max_frame, plan entries, records, the
-    device records)."""
+    the frame is small, the rest runs in the grid program (sf_apply_program_grid;
+    with grid=False, per op); pick the single-CTA frame limit by timing the eager
+    step for each candidate (and without it).  Returns (max_frame, plan entries,
+    records, the device records of the whole plan, their number)."""
     recs, starts = plan_records(sfm, plan)
     d_all = torch.from_numpy(recs.view(np.uint8).copy()).cuda()
     consumed = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -138,11 +140,15 @@ def choose_program_prefix(sfm, torch, n, plan, y, stream, candidates=(256, 512, 
             fr.reset()
             if m:
                 fr.apply_program_device(d_all.data_ptr(), m, DROP_EPS, 0, 0, mf)
-            for op in plan[p:]:
-                if op[0] == "C":
-                    fr.apply_clifford(op[1])
-                elif op[0] == "NK":
-                    fr.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], DROP_EPS)
+            if grid:
+                if len(recs) > m:
+                    fr.apply_program_grid_device(d_all.data_ptr() + recs.itemsize * m, len(recs) - m, DROP_EPS)
+            else:
+                for op in plan[p:]:
+                    if op[0] == "C":
+                        fr.apply_clifford(op[1])
+                    elif op[0] == "NK":
+                        fr.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], DROP_EPS)
         fr.measure(0, -1)
         fr.amplitude(y)
 
@@ -168,7 +174,7 @@ def choose_program_prefix(sfm, torch, n, plan, y, stream, candidates=(256, 512, 
             best = (t, mf, p, m)
     fr.close()
     _, mf, p, m = best
-    return mf, p, m, d_all
+    return mf, p, m, d_all, len(recs)
 
 
 def instrumented_pass(sfm, n, plan, y):
@@ -533,6 +539,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-program", action="store_true", help="no single-CTA program for the small-frame prefix")
+    ap.add_argument("--no-grid-program", action="store_true",
+                    help="per-op launches after the prefix instead of the grid program")
     ap.add_argument("--no-campaign", action="store_true", help="skip the batched-campaign leg")
     ap.add_argument("--campaign-variants", type=int, default=4096)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
@@ -565,27 +573,36 @@ def main():
     model = bytes_model(W, n)
 
     stream = torch.cuda.Stream()
-    # the first plan entries run as one single-CTA program while the frame is small
-    max_frame, p_pre, m_pre, d_prog = (0, 0, 0, None) if args.no_program else \
-        choose_program_prefix(sf, torch, n, plan, y, stream)
-    if p_pre:
+    use_grid = not args.no_grid_program
+    # the first plan entries run as one single-CTA program while the frame is
+    # small, the rest as one grid program (or per op)
+    cands = () if args.no_program else (256, 512, 1024, 2048, 4096)
+    max_frame, p_pre, m_pre, d_prog, n_rec = choose_program_prefix(sf, torch, n, plan, y, stream, cands,
+                                                                    grid=use_grid)
+    if p_pre or use_grid:
         graph_rec = {cls: [] for cls in graph_rec}
-        seg_bytes = 0
+        seg_bytes = gp_bytes = 0
         for (pi, cls, a, b) in ops_rec:
             if pi < p_pre:
                 seg_bytes += model[cls](a, b)
+            elif use_grid:
+                gp_bytes += model[cls](a, b)
             else:
                 graph_rec[cls].append((a, b))
-        graph_rec["segment"] = [(seg_bytes, 0)]
-        # the program leaves no index: the first merged branch after it builds one
-        if p_pre < len(plan) and plan[p_pre][0] == "NK" and \
-                not any(pi == p_pre and cls == "index" for (pi, cls, a, b) in ops_rec):
+        if p_pre:
+            graph_rec["segment"] = [(seg_bytes, 0)]
+        if use_grid and n_rec > m_pre:
+            graph_rec["gprog"] = [(gp_bytes, 0)]
+        # the single-CTA program leaves no index: the grid program, or the first
+        # merged branch after it, builds one
+        if p_pre and p_pre < len(plan) and (use_grid or (plan[p_pre][0] == "NK" and not any(
+                pi == p_pre and cls == "index" for (pi, cls, a, b) in ops_rec))):
             kk = k_before[p_pre]
             graph_rec["index"].insert(0, (kk, kk))
     frame = sf.Frame(n, MAX_ELEMS, stream=stream)
     # device-resident gate lists for the graph path
     dev_lists = []
-    for op in plan[p_pre:]:
+    for op in ([] if use_grid else plan[p_pre:]):
         if op[0] == "C":
             arr = np.array([[g[0], g[1], g[2], 0] for g in op[1]], dtype=np.uint32)
             t = torch.from_numpy(arr.view(np.int32)).cuda()
@@ -596,6 +613,10 @@ def main():
         fr.reset()
         if m_pre:
             fr.apply_program_device(d_prog.data_ptr(), m_pre, DROP_EPS, 0, 0, max_frame)
+        if use_grid:
+            if n_rec > m_pre:
+                fr.apply_program_grid_device(d_prog.data_ptr() + 24 * m_pre, n_rec - m_pre, DROP_EPS)
+            return
         di = 0
         for op in plan[p_pre:]:
             if op[0] == "C":
@@ -633,10 +654,13 @@ def main():
     # captured part of the step (where the timed event pairs live)
     graph_classes = [cls for cls in per_class if graph_rec.get(cls)] or list(per_class)
     dominant = max(graph_classes, key=per_class.get)
-    # the streaming kernel with the largest time, when the dominant class is the
-    # latency-bound single-CTA program: its roofline is reported beside
-    hbm_classes = [cls for cls in graph_classes if cls not in ("segment", "clifford")]
-    second = max(hbm_classes, key=per_class.get) if dominant == "segment" and hbm_classes else None
+    # the streaming kernel with the largest time, when the dominant class is a
+    # latency-bound program kernel: its roofline is reported beside (a class of
+    # the eager tail is timed on the tail's launches)
+    streaming = ("affine", "branch", "branch_merge", "insert", "compact", "index", "cofactor", "prob", "amplitude")
+    hbm_classes = [cls for cls in streaming if per_class.get(cls, 0) > 0 and rec.get(cls)]
+    second = max(hbm_classes, key=per_class.get) if dominant in ("segment", "gprog") and hbm_classes else None
+    second_in_graph = second is not None and bool(graph_rec.get(second))
 
     # capture the asynchronous part in CUDA graphs: `graph` for the timed steps,
     # `tgraph` (the same launches with the dominant class bracketed by CUDA
@@ -724,7 +748,24 @@ def main():
                 dom_ms += ms
                 dom_launches += cnt
         sec_ms, sec_launches = 0.0, 0
-        if second is not None and tgraph is not None:
+        if second is not None and not second_in_graph:
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                frame.time_kernel(second)  # brackets this class's launches from here on
+                if graph is not None:
+                    with torch.cuda.stream(stream):
+                        graph.replay()
+                    frame.set_host_state(token)
+                else:
+                    with torch.cuda.stream(stream):
+                        async_part(frame)
+                tail(frame)
+                ms, cnt = frame.kernel_time()
+                sec_ms += ms
+                sec_launches += cnt
+            frame.time_kernel(-1)
+        elif second is not None and tgraph is not None:
             # captured only now: the timing event pairs of a handle are one pool
             frame.time_kernel(second)
             async_part(frame)
@@ -744,24 +785,33 @@ def main():
     clocks = clk.summary()
     # graph replays do not pass through the host launch counter: add the captured kernels
     launches_total = launches_timed  # launched from the host inside the timed steps
-    if graph is not None:
+    if graph is not None and use_grid:  # reset, program kernels, the index build between them
+        launches_total += (1 + (2 if m_pre else 0) + (1 if n_rec > m_pre else 0)) * args.steps
+    elif graph is not None:
         launches_total += graph_launch_count(plan[p_pre:], start_indexed=not m_pre,
                                              extra=1 if m_pre else 0) * args.steps  # graph replays
     ms_step = float(np.mean(step_ms))
 
     # e2e: the public API with host gate arrays, eager launches
     e2e_frame = sf.Frame(n, MAX_ELEMS, stream=stream)
-    h2d = 16 * sum(len(op[1]) for op in plan[p_pre:] if op[0] == "C") + 8 * e2e_frame.W + 24 * m_pre
+    m_host = n_rec if use_grid else m_pre  # records copied from the host each step
+    h2d = (0 if use_grid else 16 * sum(len(op[1]) for op in plan[p_pre:] if op[0] == "C")) + \
+        8 * e2e_frame.W + 24 * m_host
     d2h = 16 + 16
-    if m_pre:
-        h_prog = torch.from_numpy(plan_records(sf, plan)[0][:m_pre].view(np.uint8).copy()).pin_memory()
+    if m_host:
+        h_prog = torch.from_numpy(plan_records(sf, plan)[0][:m_host].view(np.uint8).copy()).pin_memory()
         d_prog_e2e = torch.empty_like(h_prog, device="cuda")
 
     def e2e_step():
         e2e_frame.reset()
-        if m_pre:  # the program's records from pinned host memory, then one launch
+        if m_host:  # the programs' records from pinned host memory, then one launch each
             d_prog_e2e.copy_(h_prog, non_blocking=True)
+        if m_pre:
             e2e_frame.apply_program_device(d_prog_e2e.data_ptr(), m_pre, DROP_EPS, 0, 0, max_frame)
+        if use_grid:
+            if n_rec > m_pre:
+                e2e_frame.apply_program_grid_device(d_prog_e2e.data_ptr() + 24 * m_pre, n_rec - m_pre, DROP_EPS)
+            return e2e_frame.measure(0, -1), e2e_frame.amplitude(y)
         for op in plan[p_pre:]:
             if op[0] == "C":
                 e2e_frame.apply_clifford(op[1])
@@ -810,13 +860,16 @@ def main():
                 "frac": achieved / peak_gbs, "peak_source": peak_src, "traffic": ncu_traffic(dominant),
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_ms * 1e3,
                 "launches_timed": dom_launches}
-    if dominant == "segment":
-        roofline["note"] = ("the dominant kernel is the single-CTA program that runs the small-frame prefix of "
-                            "the step: a serial chain of latency-bound ops, so its HBM fraction is near zero by "
-                            "design; roofline_streaming gives the streaming kernel with the largest time")
+    if dominant in ("segment", "gprog"):
+        roofline["note"] = ("the dominant kernel is a program kernel (the single-CTA small-frame prefix, or the "
+                            "grid program that runs the rest of the circuit with grid barriers between its "
+                            "passes): a serial chain of latency-bound passes whose achieved bandwidth is the "
+                            "summed algorithmic bytes of its ops over its time; roofline_streaming gives the "
+                            "streaming kernel with the largest time")
     roofline_streaming = None
     if second is not None and sec_launches:
-        b2 = sum(model[second](a, b) for a, b in graph_rec[second]) / max(1, len(graph_rec[second]))
+        src = graph_rec if second_in_graph else rec
+        b2 = sum(model[second](a, b) for a, b in src[second]) / max(1, len(src[second]))
         t2 = sec_ms / sec_launches
         a2 = b2 / (t2 * 1e-3) / 1e9
         roofline_streaming = {"bound": "hbm", "kernel": second, "achieved": a2, "peak": peak_gbs, "unit": "GB/s",
@@ -843,6 +896,7 @@ def main():
                    "updates_per_step": updates, "coalesce_elems_per_step": coal_elems,
                    "program_prefix": {"plan_entries": p_pre, "records": m_pre, "max_frame": max_frame,
                                       "of_plan_entries": len(plan), "chosen_by": "eager step timing sweep"},
+                   "grid_program": {"records": n_rec - m_pre} if use_grid else None,
                    "coalesce_elems_per_s": coal_elems * world / (max_ms * 1e-3), "frame_peak": peak,
                    "wall_s_timed_region": wall},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

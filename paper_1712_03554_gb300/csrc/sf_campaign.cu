@@ -64,7 +64,6 @@ struct Shared {
     Row stage[64];            // row permutation of the tableau reduction
     SfTerms ecf[32];          // terms of the diagonal records tbase .. tbase + 31
     unsigned long long tbase;
-    unsigned long long pbase, pend;  // records with a plan in the batch
     unsigned long long obase, outcomes, oe;
     double2 g;
     double p[2];
@@ -244,8 +243,9 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                                                       double eps2, unsigned stop_cap, BrTab* pb,
                                                       double2 (*cb)[4][16], int nbm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-unsigned long long oi = o0;
-while (oi < o1 && S.status == 0) {
+    unsigned long long oi = o0;
+    unsigned long long pbase = 0, pend = 0;  // records planned in the current batch (the same in every thread)
+    while (oi < o1 && S.status == 0) {
         const OpRec op0 = ops[oi];
         uint32_t kind = op0.kind;
         bool cond_false = false;
@@ -352,23 +352,27 @@ while (oi < o1 && S.status == 0) {
                 __syncthreads();
                 break;
             }
-            if (oi < S.pbase || oi >= S.pend) {
+            if (oi < pbase || oi >= pend) {
                 // plans of the run of diagonal records from oi (at most nbm): the
-                // tableau does not change within it, so warp w plans record oi + w
-                if (warp == 0) {
-                    int nb = 1;
-                    if (nbm > 1) {
-                        const unsigned long long ri = oi + lane;
-                        bool dg = false;
-                        if (ri < o1) {
-                            const uint32_t kk = ops[ri].kind;
-                            dg = kk >= SF_OP_DIAG && kk <= SF_OP_DIAG + 3;
-                        }
-                        const unsigned bl = __ballot_sync(SF_FULL, dg);
-                        nb = bl == SF_FULL ? 32 : __ffs(~bl) - 1;
-                        nb = nb < nbm ? nb : nbm;
-                        nb = nb < 1 ? 1 : nb;
+                // tableau does not change within it, so warp w plans record oi + w.
+                // Every warp counts the run itself, so the batch bounds agree in all
+                // threads without a barrier.
+                int nb = 1;
+                if (nbm > 1) {
+                    const unsigned long long ri = oi + lane;
+                    bool dg = false;
+                    if (ri < o1) {
+                        const uint32_t kk = ops[ri].kind;
+                        dg = kk >= SF_OP_DIAG && kk <= SF_OP_DIAG + 3;
                     }
+                    const unsigned bl = __ballot_sync(SF_FULL, dg);
+                    nb = bl == SF_FULL ? 32 : __ffs(~bl) - 1;
+                    nb = nb < nbm ? nb : nbm;
+                    nb = nb < 1 ? 1 : nb;
+                }
+                pbase = oi;
+                pend = oi + nb;
+                if (warp == 0) {
                     // the terms of the diagonal records, 32 records at a time (one per
                     // lane), so the narrow double-precision pipe runs one sincos per window
                     if (oi < S.tbase || oi + nb > S.tbase + 32) {
@@ -399,13 +403,8 @@ while (oi < o1 && S.status == 0) {
                             S.rde[row] = r[hf].de;
                         }
                     }
-                    if (lane == 0) {
-                        S.pbase = oi;
-                        S.pend = oi + nb;
-                    }
                 }
                 __syncthreads();
-                const int nb = (int)(S.pend - S.pbase);
                 if (warp < nb) {
                     if (warp != 0) {
                         for (int hf = 0; hf < 2; hf++) {
@@ -426,8 +425,8 @@ while (oi < o1 && S.status == 0) {
                                           S.ecf[oi + warp - S.tbase].c, pb[warp], cb[warp]);
                 }
             }
-            const BrTab& P = pb[oi - S.pbase];
-            double2(*const ctab)[16] = cb[oi - S.pbase];
+            const BrTab& P = pb[oi - pbase];
+            double2(*const ctab)[16] = cb[oi - pbase];
             __syncthreads();
             const int ng = P.ng;
             if (stop_cap && !P.bad && (unsigned long long)ng * S.k > stop_cap) break;  // stop before this op
@@ -666,7 +665,6 @@ __global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
             S.outcomes = 0;
             S.nmeas = 0;
             S.tbase = ~0ull;
-            S.pbase = S.pend = 0;
             S.g = make_double2(1.0, 0.0);
             sigb[0][0] = 0;
             ampb[0][0] = make_double2(1.0, 0.0);
@@ -799,7 +797,6 @@ __global__ void __launch_bounds__(kSegThreads) k_segment(SfDev d, const OpRec* o
         S.outcomes = 0;
         S.nmeas = 0;
         S.tbase = ~0ull;
-        S.pbase = S.pend = 0;
     }
     __syncthreads();
     unsigned long long done = 0;

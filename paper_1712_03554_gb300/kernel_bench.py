@@ -122,13 +122,13 @@ def merge_case(m):
 def qft_step(seed=0, max_frame=2048):
     """The bench's step eagerly: QFT n = 20 on a seeded random basis state, the
     small-frame prefix as one sf_apply_program launch (frame limit max_frame,
-    0: none), the rest with merged branching, then the probabilities of qubit 0
-    and one amplitude."""
+    0: none), the rest as one sf_apply_program_grid launch, then the
+    probabilities of qubit 0 and one amplitude."""
     x, ops = c.qft_random_input(20, seed)
     f = frame_of(20, 0, 1 << 21)
     f.reset()
     i = f.apply_program(ops, max_frame=max_frame)[0] if max_frame else 0
-    c.run(f, ops[i:])
+    f.apply_program_grid(ops[i:])
     f.measure(0, -1)
     f.amplitude(x)
     f.sync()
