@@ -245,6 +245,8 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long oi = o0;
     unsigned long long pbase = 0, pend = 0;  // records planned in the current batch (the same in every thread)
+    bool have_u = false;  // the frame is closed under the mask cu (s in F => s ^ cu in F)
+    uint64_t cu = 0;
     while (oi < o1 && S.status == 0) {
         const OpRec op0 = ops[oi];
         uint32_t kind = op0.kind;
@@ -340,6 +342,7 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
             }
             __syncthreads();
             build_index(idx, sg, S.k);
+            have_u = false;
             oi = S.oe;
             continue;
         }
@@ -425,9 +428,68 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                                           S.ecf[oi + warp - S.tbase].c, pb[warp], cb[warp]);
                 }
             }
-            const BrTab& P = pb[oi - pbase];
-            double2(*const ctab)[16] = cb[oi - pbase];
             __syncthreads();
+            // the longest run of planned records from oi that one in-place pass takes:
+            // one-group gates (a phase per element) and two-group gates whose second
+            // mask is the one the frame is closed under (each pair {s, s ^ u} maps
+            // onto itself: phase vectors, positions and the index stay)
+            const int t = (int)(oi - pbase);
+            int t2 = t;
+            bool pairs = false;
+            while (t2 < (int)(pend - pbase) && !pb[t2].bad) {
+                const BrTab& Q = pb[t2];
+                if (Q.ng == 1 || (Q.ng == 2 && have_u && Q.u[1] == cu)) {
+                    pairs |= Q.ng == 2;
+                    t2++;
+                } else {
+                    break;
+                }
+            }
+            const unsigned long long kb = keep_bits(eps2);
+            if (t2 > t) {
+                // the element with the smaller phase vector of each pair applies the
+                // run's gates to both amplitudes: the per-gate sums, in the same order
+                const unsigned k = S.k;
+                const uint64_t* si = sigb[S.cur];
+                double2* ai = ampb[S.cur];
+                bool drop = false, miss = false;
+                const auto plan = [&](int r2) { return PlanRef{&pb[r2], cb[r2]}; };
+                const auto find = [&](uint64_t key) { return (long long)find_index(idx, si, k, key); };
+                for (unsigned base = 64u * warp; base < k; base += 64u * (blockDim.x >> 5))
+                    inplace_run_warp<false>(si, ai, base, k, pairs, cu, t, t2, plan, find, kb, eps2, drop, miss);
+                if (__syncthreads_or(miss)) {  // the frame was not closed after all
+                    if (threadIdx.x == 0) S.status = SF_EINTERNAL;
+                    __syncthreads();
+                    break;
+                }
+                oi += t2 - t;
+                if (!__syncthreads_or(drop)) continue;
+                // amplitudes fell below the threshold: compact the frame
+                const int ib = S.cur, ob = S.cur ^ 1;
+                if (threadIdx.x == 0) S.obase = 0;
+                __syncthreads();
+                for (unsigned base = 0; base < k; base += blockDim.x) {
+                    const unsigned j = base + threadIdx.x;
+                    const bool act = j < k;
+                    const double2 a = act ? ampb[ib][j] : make_double2(0.0, 0.0);
+                    const bool keep = act && amp_kept(a, kb, eps2);
+                    const unsigned long long o = block_scan_advance(S, keep ? 1u : 0u);
+                    if (keep) {
+                        sigb[ob][o] = sigb[ib][j];
+                        ampb[ob][o] = a;
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    S.k = (unsigned)S.obase;
+                    S.cur = ob;
+                }
+                __syncthreads();
+                build_index(idx, sigb[S.cur], S.k);
+                have_u = false;
+                continue;
+            }
+            const BrTab& P = pb[t];
+            double2(*const ctab)[16] = cb[t];
             const int ng = P.ng;
             if (stop_cap && !P.bad && (unsigned long long)ng * S.k > stop_cap) break;  // stop before this op
             if (P.bad || (unsigned long long)ng * S.k > cap) {
@@ -436,12 +498,12 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                 break;
             }
             const int ib = S.cur, ob = S.cur ^ 1;
-            const unsigned long long kb = keep_bits(eps2);
             const uint64_t* si = sigb[ib];
             const double2* ai = ampb[ib];
             const unsigned k = S.k;
             if (threadIdx.x == 0) S.obase = 0;
             __syncthreads();
+            bool drop = false;
             for (unsigned base = 0; base < k; base += blockDim.x) {
                 const unsigned j = base + threadIdx.x;
                 const bool act = j < k;
@@ -464,18 +526,12 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                             const int m = P.xidx[g][g2];
                             if (id[m] < 0) continue;
                             const double2 ap = m == 0 ? a : ai[id[m]];
-                            const uint64_t px = s ^ P.u[m];
-                            const int ntg = P.nt[g2];
-                            int pat = 0;
-                            for (int t = 0; t < ntg; t++) pat |= (__popcll(P.v[g2][t] & px) & 1) << t;
-                            // the half table holds the patterns with the last term's bit clear
-                            const bool neg = (pat >> (ntg - 1)) & 1;
-                            const double2 cc = ctab[g2][neg ? pat ^ ((1 << ntg) - 1) : pat];
-                            cmul_acc(amp, make_double2(dneg_if(cc.x, neg), dneg_if(cc.y, neg)), ap);
+                            cmul_acc(amp, half_coef(P, ctab, g2, s ^ P.u[m]), ap);
                         }
                     }
                     amps[g] = amp;
                     if (own && amp_kept(amp, kb, eps2)) keepm |= 1u << g;
+                    else if (own) drop = true;
                 }
                 unsigned long long o = block_scan_advance(S, __popc(keepm));
                 for (int g = 0; g < ng; g++) {
@@ -485,6 +541,11 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                     o++;
                 }
             }
+            // no output dropped: every parent s gave s ^ u_g for all g, so the new
+            // frame is closed under the gate's masks
+            const bool dropped = __syncthreads_or(drop);
+            have_u = !dropped && ng == 2;
+            cu = P.u[1];
             if (threadIdx.x == 0) {
                 S.k = (unsigned)S.obase;
                 S.cur = ob;
@@ -617,6 +678,7 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                 __syncthreads();
             }
             build_index(idx, sigb[S.cur], S.k);
+            have_u = false;
             oi++;
             continue;
         }

@@ -217,16 +217,7 @@ __device__ void gp_plan(const SfDev& d, const OpRec& o, GpPlan& sp, GpPlan* out)
     for (int i = lane; i < (int)(sizeof(GpPlan) / 8); i += 32) dst[i] = src[i];
 }
 
-// coefficient of group g of a plan for parent phase vector x (half table and sign)
-__device__ __forceinline__ double2 gp_coef(const GpPlan& Q, int g, uint64_t x) {
-    const int ntg = Q.P.nt[g];
-    int pat = 0;
-    for (int t = 0; t < ntg; t++) pat |= (__popcll(Q.P.v[g][t] & x) & 1) << t;
-    // the half table holds the patterns with the last term's bit clear
-    const bool neg = (pat >> (ntg - 1)) & 1;
-    const double2 cc = Q.ctab[g][neg ? pat ^ ((1 << ntg) - 1) : pat];
-    return make_double2(dneg_if(cc.x, neg), dneg_if(cc.y, neg));
-}
+__device__ __forceinline__ double2 gp_coef(const GpPlan& Q, int g, uint64_t x) { return half_coef(Q.P, Q.ctab, g, x); }
 
 // elements [lo, hi) of CTA b: contiguous chunks, whole warps, all CTAs busy
 __device__ __forceinline__ void gp_chunk(unsigned long long k, unsigned long long& lo, unsigned long long& hi) {
@@ -381,35 +372,15 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 double2* A = d.amp[cur];
                 unsigned long long lo, hi;
                 gp_chunk(k, lo, hi);
-                bool drop = false;
-                for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-                    const uint64_t s0 = __ldcg(&S[j]), s1 = s0 ^ cu;
-                    long long q = -1;
-                    if (pairs) {
-                        if (s1 < s0) continue;
-                        q = gp_find(d, cur, isz[cur], tag[cur], s1);
-                        if (q < 0) {  // the frame is not closed after all
-                            set_status(d.status, SF_ST_INTERNAL, cur, 47u);
-                            gp_fail(w);
-                            continue;
-                        }
-                    }
-                    double2 a0 = __ldcg(&A[j]), a1 = q >= 0 ? __ldcg(&A[q]) : make_double2(0.0, 0.0);
-                    for (int r = t; r < t2; r++) {
-                        const GpPlan& Q = spl[r];
-                        double2 n0 = make_double2(0.0, 0.0), n1 = make_double2(0.0, 0.0);
-                        cmul_acc(n0, gp_coef(Q, 0, s0), a0);
-                        if (pairs) {
-                            if (Q.P.ng == 2) cmul_acc(n0, gp_coef(Q, 1, s1), a1);
-                            cmul_acc(n1, gp_coef(Q, 0, s1), a1);
-                            if (Q.P.ng == 2) cmul_acc(n1, gp_coef(Q, 1, s0), a0);
-                        }
-                        a0 = n0;
-                        a1 = n1;
-                    }
-                    A[j] = a0;
-                    if (q >= 0) A[q] = a1;
-                    drop |= !amp_kept(a0, kb, eps2) || (q >= 0 && !amp_kept(a1, kb, eps2));
+                bool drop = false, miss = false;
+                const auto plan = [&](int r) { return PlanRef{&spl[r].P, spl[r].ctab}; };
+                const int c_ = cur;
+                const auto find = [&](uint64_t key) { return gp_find(d, c_, isz[c_], tag[c_], key); };
+                for (unsigned long long base = lo + 64ull * warp; base < hi; base += 64ull * (blockDim.x >> 5))
+                    inplace_run_warp<true>(S, A, base, hi, pairs, cu, t, t2, plan, find, kb, eps2, drop, miss);
+                if (miss) {  // the frame is not closed after all
+                    set_status(d.status, SF_ST_INTERNAL, cur, 47u);
+                    gp_fail(w);
                 }
                 if (__syncthreads_or(drop) && threadIdx.x == 0) gp_dropped(w);
                 if (!gp_barrier(w, gen, d.status, cur)) return bail();

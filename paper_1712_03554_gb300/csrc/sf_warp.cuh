@@ -466,6 +466,83 @@ struct BrTab {
     int xidx[4][4];
 };
 
+// coefficient of group g of a plan for parent phase vector x: the sign
+// pattern of the group's terms, looked up in the half table (patterns with
+// the last term's bit set are the negations of their complements)
+__device__ __forceinline__ double2 half_coef(const BrTab& P, const double2 (*ctab)[16], int g, uint64_t x) {
+    const int ntg = P.nt[g];
+    int pat = 0;
+    for (int t = 0; t < ntg; t++) pat |= (__popcll(P.v[g][t] & x) & 1) << t;
+    const bool neg = (pat >> (ntg - 1)) & 1;
+    const double2 cc = ctab[g][neg ? pat ^ ((1 << ntg) - 1) : pat];
+    return make_double2(dneg_if(cc.x, neg), dneg_if(cc.y, neg));
+}
+
+// One warp's share of an in-place run of diagonal gates (plan(r) for r in
+// [r0, r1) gives the gate's BrTab and half table) on the elements [base,
+// base + 64) of a frame of hi elements: with pairs, each pair {s, s ^ cu}
+// is carried by its element with the smaller phase vector, and those owners
+// are packed onto consecutive lanes first, so no lane idles through the FP64
+// pipe (a double-precision instruction costs the same for 1 lane as for 32).
+// find(key) is the position of a phase vector, kL2: the frame is read through
+// L2 (written by other CTAs of the launch).  Sets drop if a result is below
+// the threshold, miss if a partner is absent.
+template <bool kL2, class Plan, class Find>
+__device__ __forceinline__ void inplace_run_warp(const uint64_t* S, double2* A, unsigned long long base,
+                                                 unsigned long long hi, bool pairs, uint64_t cu, int r0, int r1,
+                                                 Plan plan, Find find, unsigned long long kb, double eps2, bool& drop,
+                                                 bool& miss) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long ja = base + lane, jb = base + 32 + lane;
+    uint64_t sa = 0, sb = 0;
+    if (ja < hi) sa = kL2 ? __ldcg(&S[ja]) : S[ja];
+    if (jb < hi) sb = kL2 ? __ldcg(&S[jb]) : S[jb];
+    const bool oa = ja < hi && (!pairs || (sa ^ cu) > sa), ob = jb < hi && (!pairs || (sb ^ cu) > sb);
+    const unsigned ma = __ballot_sync(SF_FULL, oa), mb = __ballot_sync(SF_FULL, ob);
+    const int na = __popc(ma), cnt = na + __popc(mb);
+    // lane l takes the l-th owner of the 64 elements
+    unsigned m = lane < na ? ma : mb;
+    for (int i = lane < na ? lane : lane - na; i > 0 && m; i--) m &= m - 1;
+    const int src = m ? __ffs(m) - 1 : 0;
+    const uint64_t s_a = __shfl_sync(SF_FULL, sa, src), s_b = __shfl_sync(SF_FULL, sb, src);
+    if (lane >= cnt) return;
+    const bool second = lane >= na;
+    const uint64_t s0 = second ? s_b : s_a, s1 = s0 ^ cu;
+    const unsigned long long j = base + (second ? 32 : 0) + src;
+    long long q = -1;
+    if (pairs) {
+        q = find(s1);
+        if (q < 0) {
+            miss = true;
+            return;
+        }
+    }
+    double2 a0 = kL2 ? __ldcg(&A[j]) : A[j];
+    double2 a1 = make_double2(0.0, 0.0);
+    if (q >= 0) a1 = kL2 ? __ldcg(&A[q]) : A[q];
+    for (int r = r0; r < r1; r++) {
+        const BrTab& Q = *plan(r).P;
+        const double2(*ct)[16] = plan(r).ctab;
+        double2 n0 = make_double2(0.0, 0.0), n1 = make_double2(0.0, 0.0);
+        cmul_acc(n0, half_coef(Q, ct, 0, s0), a0);
+        if (pairs) {
+            if (Q.ng == 2) cmul_acc(n0, half_coef(Q, ct, 1, s1), a1);
+            cmul_acc(n1, half_coef(Q, ct, 0, s1), a1);
+            if (Q.ng == 2) cmul_acc(n1, half_coef(Q, ct, 1, s0), a0);
+        }
+        a0 = n0;
+        a1 = n1;
+    }
+    A[j] = a0;
+    if (q >= 0) A[q] = a1;
+    drop |= !amp_kept(a0, kb, eps2) || (q >= 0 && !amp_kept(a1, kb, eps2));
+}
+
+struct PlanRef {
+    const BrTab* P;
+    const double2 (*ctab)[16];
+};
+
 // cf: the nt term coefficients of the gate (diag_terms).  Every lane derives
 // the groups from warp-uniform values; the lanes split the writes of P and of
 // the coefficient table.  ctab[g][p] holds sum_t (-1)^{bit t of p} c_t for
