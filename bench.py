@@ -165,7 +165,7 @@ def choose_program_prefix(sfm, torch, n, plan, y, stream, candidates=(256, 512, 
             m = starts[p]
         run(mf, p, m)
         ts = []
-        for _ in range(3):
+        for _ in range(7):
             t0 = time.perf_counter()
             run(mf, p, m)
             ts.append(time.perf_counter() - t0)
