@@ -57,4 +57,6 @@ def test_invalid_args_without_gpu_are_rejected_on_the_host():
     assert lib.sf_create(2000, 16, None, ctypes.byref(h)) == sf.SF_EINVAL
     assert lib.sf_create(4, 0, None, ctypes.byref(h)) == sf.SF_EINVAL
     assert lib.sf_destroy(None) == sf.SF_EINVAL
+    assert lib.sf_apply_program(None, None, 0, 0.0, 0, None, None) == sf.SF_EINVAL
+    assert lib.sf_apply_program_grid(None, None, 0, 0.0, None) == sf.SF_EINVAL
     assert lib.sf_last_error(None)
