@@ -160,8 +160,16 @@ __device__ __forceinline__ int popc_and(const uint64_t* a, const uint64_t* b) {
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ double dneg_if(double x, bool neg) {  // sign flip on the integer pipe
-    return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)neg << 63));
+// sign flip on the integer pipe: the high word goes through registers by
+// explicit moves, so the flip is not turned back into an FP64 negation (an
+// FP64 instruction occupies the SM's narrow FP64 pipe)
+__device__ __forceinline__ double dneg_if(double x, bool neg) {
+    unsigned lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+    hi ^= (unsigned)neg << 31;
+    double r;
+    asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi));
+    return r;
 }
 __device__ __forceinline__ double2 ipow_mul(double2 a, int k) {  // a * i^k
     switch (k & 3) {

@@ -46,6 +46,7 @@ struct GpWork {
     unsigned int drop[3];        // an amplitude dropped in phase p: drop[p % 3]
     unsigned long long ocnt[3];  // output counters of consecutive merges, rotating
     unsigned long long oe;       // end of the current Clifford run
+    unsigned int npre;           // diagonal records after it already planned into plans[0 .. npre)
     uint64_t AT[64];             // affine map of the current Clifford run: column j = image of e_j
     uint64_t t;
     GpPlan plans[kGpPlans];
@@ -271,6 +272,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
     bool ok = true;
     bool have_u = false;  // the frame is closed under the mask cu (s in F => s ^ cu in F)
     uint64_t cu = 0;
+    unsigned npre = 0;    // records at oi planned by the last Clifford phase
     // on a failed check: the frame stays in buffer cur (its count and the
     // index tags go back for the host's error path), and the launch ends
     auto bail = [&]() {
@@ -285,9 +287,28 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
     while (oi < n_ops) {
         const uint32_t kind = ops[oi].kind;
         if (kind <= 8) {
-            // ---- Clifford run: tableau in one warp, then the affine pass with a fresh index
-            if (blockIdx.x == 0 && warp == 0) gp_clifford_run(d, w, ops, oi, n_ops, stage, cur);
+            // ---- Clifford run: tableau in one warp of CTA 0, whose other warps then plan
+            // the diagonal records that follow (one record each) in the same phase;
+            // then the affine pass with a fresh index
+            if (blockIdx.x == 0) {
+                if (warp == 0) gp_clifford_run(d, w, ops, oi, n_ops, stage, cur);
+                __syncthreads();
+                const unsigned long long oe = __ldcg(&w->oe);
+                const unsigned long long ri = oe + lane;
+                bool dg = false;
+                if (ri < n_ops) {
+                    const uint32_t kk = ops[ri].kind;
+                    dg = kk >= SF_OP_DIAG && kk <= SF_OP_DIAG + 3;
+                }
+                const unsigned bl = __ballot_sync(SF_FULL, dg);
+                int np = bl == SF_FULL ? 32 : __ffs(~bl) - 1;
+                np = np < (int)(blockDim.x >> 5) ? np : (int)(blockDim.x >> 5);
+                if (*(volatile uint32_t*)d.status) np = 0;
+                if (warp < np) gp_plan(d, ops[oe + warp], spl[warp], &w->plans[warp]);
+                if (threadIdx.x == 0) w->npre = (unsigned)np;
+            }
             if (!gp_barrier(w, gen, d.status, cur)) return bail();
+            npre = __ldcg(&w->npre);
             const int nc = (n + 3) >> 2;
             for (int e = threadIdx.x; e < nc * 16; e += blockDim.x) {
                 const int v = e & 15, c = e >> 4;
@@ -324,7 +345,11 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             continue;
         }
         if (kind < SF_OP_DIAG || kind > SF_OP_DIAG + 3) break;  // measurement or conditional gate
-        // ---- diagonal run: all plans first, then one merge per record
+        // ---- diagonal run: all plans first (unless the Clifford phase made them),
+        // then one merge per record
+        int nb = (int)npre;
+        npre = 0;
+        if (nb == 0) {
         if (warp == 0) {
             const unsigned long long ri = oi + lane;
             bool dg = false;
@@ -338,9 +363,10 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             if (lane == 0) s_nb = nb < (int)gridDim.x ? nb : (int)gridDim.x;
         }
         __syncthreads();
-        const int nb = s_nb;
+        nb = s_nb;
         if ((int)blockIdx.x < nb && warp == 0) gp_plan(d, ops[oi + blockIdx.x], sp, &w->plans[blockIdx.x]);
         if (!gp_barrier(w, gen, d.status, cur)) return bail();
+        }
         {
             const uint64_t* src = reinterpret_cast<const uint64_t*>(w->plans);
             uint64_t* dst = reinterpret_cast<uint64_t*>(spl);
