@@ -49,6 +49,7 @@ struct GpWork {
     unsigned int npre;           // diagonal records after it already planned into plans[0 .. npre)
     uint64_t AT[64];             // affine map of the current Clifford run: column j = image of e_j
     uint64_t t;
+    uint64_t Ainv[64];           // rows of the inverse of its linear part
     GpPlan plans[kGpPlans];
 };
 
@@ -123,7 +124,7 @@ __device__ __forceinline__ long long gp_find(const SfDev& d, int b, unsigned lon
 // tableau in registers, written back with the X-block size and global phase;
 // the composed affine map goes to the workspace, the run's end to w->oe.
 __device__ void gp_clifford_run(const SfDev& d, GpWork* w, const OpRec* ops, unsigned long long oi,
-                                unsigned long long o1, Row* stage, int buf) {
+                                unsigned long long o1, Row* stage, uint64_t* arows, int buf) {
     const int n = d.n, lane = threadIdx.x & 31;
     Row r[2];
     for (int hf = 0; hf < 2; hf++) {
@@ -183,6 +184,9 @@ __device__ void gp_clifford_run(const SfDev& d, GpWork* w, const OpRec* ops, uns
         const unsigned b1 = __ballot_sync(SF_FULL, lane + 32 < n && ((r[1].A >> j) & 1));
         if (lane == 0) w->AT[j] = (uint64_t)b0 | ((uint64_t)b1 << 32);
     }
+    // rows of A, inverted next while other warps plan
+    for (int hf = 0; hf < 2; hf++)
+        if (lane + 32 * hf < n) arows[lane + 32 * hf] = r[hf].A;
     const unsigned t0 = __ballot_sync(SF_FULL, lane < n && r[0].t0);
     const unsigned t1 = __ballot_sync(SF_FULL, lane + 32 < n && r[1].t0);
     if (lane == 0) {
@@ -218,8 +222,6 @@ __device__ void gp_plan(const SfDev& d, const OpRec& o, GpPlan& sp, GpPlan* out)
     for (int i = lane; i < (int)(sizeof(GpPlan) / 8); i += 32) dst[i] = src[i];
 }
 
-__device__ __forceinline__ double2 gp_coef(const GpPlan& Q, int g, uint64_t x) { return half_coef(Q.P, Q.ctab, g, x); }
-
 // elements [lo, hi) of CTA b: contiguous chunks, whole warps, all CTAs busy
 __device__ __forceinline__ void gp_chunk(unsigned long long k, unsigned long long& lo, unsigned long long& hi) {
     const unsigned long long per = ((k + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
@@ -231,6 +233,8 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                                                       double eps2, int cur0, unsigned long long* consumed) {
     extern __shared__ GpPlan spl[];  // [kGpPlans]: the plans of the current diagonal run
     __shared__ GpPlan sp;            // scratch of the planning warp
+    __shared__ BrTab pm;             // a plan moved to the coordinates before a pending affine map
+    __shared__ uint64_t s_ainv[64], s_at[64];
     __shared__ uint64_t tab[16 * 16];
     __shared__ Row stage[64];
     __shared__ unsigned int wsum[kGpThreads / 32];
@@ -273,6 +277,50 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
     bool have_u = false;  // the frame is closed under the mask cu (s in F => s ^ cu in F)
     uint64_t cu = 0;
     unsigned npre = 0;    // records at oi planned by the last Clifford phase
+    // The last Clifford run's map sigma' = A sigma ^ t is not yet applied to the
+    // phase vectors (the tableau is already new); the next merge applies it.
+    bool aff = false;
+    const int nc = (n + 3) >> 2;
+    uint64_t tw = 0;
+    // 4-bit lookup tables of the pending map (columns of A from the workspace)
+    auto affine_tables = [&]() {
+        for (int e = threadIdx.x; e < nc * 16; e += blockDim.x) {
+            const int v = e & 15, c = e >> 4;
+            uint64_t acc = 0;
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+                if (((v >> b) & 1) && 4 * c + b < n) acc ^= __ldcg(&w->AT[4 * c + b]);
+            tab[e] = acc;
+        }
+        tw = __ldcg(&w->t);
+        __syncthreads();
+    };
+    auto affine_of = [&](uint64_t x) {
+        uint64_t o = tw;
+        for (int c = 0; c < nc; c++) o ^= tab[c * 16 + ((x >> (4 * c)) & 15)];
+        return o;
+    };
+    // the map applied to every phase vector, which go into a fresh index
+    auto affine_pass = [&]() {
+        affine_tables();
+        const uint32_t tg = next_tag(tag[cur]);
+        const unsigned long long T = index_slots(k, d.icap);
+        uint64_t* S = d.sig[cur];
+        unsigned long long lo, hi;
+        gp_chunk(k, lo, hi);
+        for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+            const uint64_t o = affine_of(__ldcg(&S[j]));
+            S[j] = o;
+            ok &= index_insert<1>(d, cur, T, tg, &o, (uint32_t)j);
+        }
+        tag[cur] = tg;
+        isz[cur] = T;
+        if (!ok) {
+            set_status(d.status, SF_ST_TIMEOUT, cur, 43u);  // index full
+            gp_fail(w);
+        }
+        aff = false;
+    };
     // on a failed check: the frame stays in buffer cur (its count and the
     // index tags go back for the host's error path), and the launch ends
     auto bail = [&]() {
@@ -291,8 +339,19 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             // the diagonal records that follow (one record each) in the same phase;
             // then the affine pass with a fresh index
             if (blockIdx.x == 0) {
-                if (warp == 0) gp_clifford_run(d, w, ops, oi, n_ops, stage, cur);
+                if (warp == 0) gp_clifford_run(d, w, ops, oi, n_ops, stage, s_ainv, cur);
                 __syncthreads();
+                if (warp == 0) {
+                    // rows of A^-1, for a merge that reads the phase vectors before the map
+                    const uint64_t av[2] = {lane < n ? s_ainv[lane] : 0, lane + 32 < n ? s_ainv[lane + 32] : 0};
+                    uint64_t iv[2];
+                    if (!warp_gf2_inverse(av, n, iv) && lane == 0) {
+                        set_status(d.status, SF_ST_INTERNAL, cur, 49u);
+                        gp_fail(w);
+                    }
+                    for (int hf = 0; hf < 2; hf++)
+                        if (lane + 32 * hf < n) w->Ainv[lane + 32 * hf] = iv[hf];
+                }
                 const unsigned long long oe = __ldcg(&w->oe);
                 const unsigned long long ri = oe + lane;
                 bool dg = false;
@@ -302,46 +361,24 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 }
                 const unsigned bl = __ballot_sync(SF_FULL, dg);
                 int np = bl == SF_FULL ? 32 : __ffs(~bl) - 1;
-                np = np < (int)(blockDim.x >> 5) ? np : (int)(blockDim.x >> 5);
+                np = np < (int)(blockDim.x >> 5) - 1 ? np : (int)(blockDim.x >> 5) - 1;
                 if (*(volatile uint32_t*)d.status) np = 0;
-                if (warp < np) gp_plan(d, ops[oe + warp], spl[warp], &w->plans[warp]);
+                if (warp >= 1 && warp - 1 < np) gp_plan(d, ops[oe + warp - 1], spl[warp - 1], &w->plans[warp - 1]);
                 if (threadIdx.x == 0) w->npre = (unsigned)np;
             }
             if (!gp_barrier(w, gen, d.status, cur)) return bail();
             npre = __ldcg(&w->npre);
-            const int nc = (n + 3) >> 2;
-            for (int e = threadIdx.x; e < nc * 16; e += blockDim.x) {
-                const int v = e & 15, c = e >> 4;
-                uint64_t acc = 0;
-#pragma unroll
-                for (int b = 0; b < 4; b++)
-                    if (((v >> b) & 1) && 4 * c + b < n) acc ^= __ldcg(&w->AT[4 * c + b]);
-                tab[e] = acc;
-            }
-            const uint64_t tw = __ldcg(&w->t);
-            const unsigned long long oe = __ldcg(&w->oe);
-            __syncthreads();
-            const uint32_t tg = next_tag(tag[cur]);
-            const unsigned long long T = index_slots(k, d.icap);
-            uint64_t* S = d.sig[cur];
-            unsigned long long lo, hi;
-            gp_chunk(k, lo, hi);
-            for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-                const uint64_t s = __ldcg(&S[j]);
-                uint64_t o = tw;
-                for (int c = 0; c < nc; c++) o ^= tab[c * 16 + ((s >> (4 * c)) & 15)];
-                S[j] = o;
-                ok &= index_insert<1>(d, cur, T, tg, &o, (uint32_t)j);
-            }
-            tag[cur] = tg;
-            isz[cur] = T;
-            if (!ok) {
-                set_status(d.status, SF_ST_TIMEOUT, cur, 43u);  // index full
-                gp_fail(w);
-            }
-            if (!gp_barrier(w, gen, d.status, cur)) return bail();
             have_u = false;
-            oi = oe;
+            oi = __ldcg(&w->oe);
+            // a following merge of two or more groups reads the phase vectors before
+            // the map (partners at A^-1 u, sign patterns from A^T v); otherwise the
+            // map is applied now
+            if (npre > 0 && !__ldcg(&w->plans[0].P.bad) && __ldcg(&w->plans[0].P.ng) >= 2) {
+                aff = true;
+                continue;
+            }
+            affine_pass();
+            if (!gp_barrier(w, gen, d.status, cur)) return bail();
             continue;
         }
         if (kind < SF_OP_DIAG || kind > SF_OP_DIAG + 3) break;  // measurement or conditional gate
@@ -449,14 +486,51 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 continue;
             }
             // ---- merge of record t into the other buffer
-            const BrTab& P = spl[t].P;
-            const GpPlan& Q = spl[t];
-            const int ng = P.ng;
-            if (P.bad || (unsigned long long)ng * k > d.cap) {
+            const BrTab& P0 = spl[t].P;  // the plan in the tableau's coordinates
+            const int ng = P0.ng;
+            if (P0.bad || (unsigned long long)ng * k > d.cap) {
                 if (blockIdx.x == 0 && threadIdx.x == 0)
-                    set_status(d.status, P.bad ? SF_ST_INTERNAL : SF_ST_CAPACITY, cur, P.bad ? 44u : 0u);
+                    set_status(d.status, P0.bad ? SF_ST_INTERNAL : SF_ST_CAPACITY, cur, P0.bad ? 44u : 0u);
+                if (aff) affine_pass();  // the frame must match the tableau when the launch ends
                 return bail();
             }
+            if (aff) {
+                // the phase vectors are still those before the map sigma' = A sigma ^ t:
+                // partners at A^-1 u, sign patterns from A^T v flipped by parity(v & t);
+                // outputs are written in the new coordinates
+                affine_tables();
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    s_ainv[i] = __ldcg(&w->Ainv[i]);
+                    s_at[i] = __ldcg(&w->AT[i]);
+                }
+                {
+                    const uint64_t* src = reinterpret_cast<const uint64_t*>(&P0);
+                    uint64_t* dst = reinterpret_cast<uint64_t*>(&pm);
+                    for (int i = threadIdx.x; i < (int)(sizeof(BrTab) / 8); i += blockDim.x) dst[i] = src[i];
+                }
+                __syncthreads();
+                const int tid = threadIdx.x;
+                if (tid < ng) {  // u'_g = A^-1 u_g
+                    uint64_t x = 0;
+                    for (int i = 0; i < n; i++) x |= (uint64_t)(__popcll(s_ainv[i] & P0.u[tid]) & 1) << i;
+                    pm.u[tid] = x;
+                } else if (tid >= 32 && tid < 48) {  // v' = A^T v
+                    const int g = (tid - 32) >> 2, tt = (tid - 32) & 3;
+                    if (g < ng && tt < P0.nt[g]) {
+                        uint64_t x = 0;
+                        for (int j = 0; j < n; j++) x |= (uint64_t)(__popcll(s_at[j] & P0.v[g][tt]) & 1) << j;
+                        pm.v[g][tt] = x;
+                    }
+                } else if (tid >= 64 && tid < 64 + ng) {  // the pattern bits flipped by t
+                    const int g = tid - 64;
+                    int f = 0;
+                    for (int tt = 0; tt < P0.nt[g]; tt++) f |= (__popcll(P0.v[g][tt] & tw) & 1) << tt;
+                    pm.fl[g] = f;
+                }
+                __syncthreads();
+            }
+            const BrTab& P = aff ? pm : P0;  // the plan in the frame's coordinates
+            const double2(*const ctab)[16] = spl[t].ctab;
             const int in = cur, out = cur ^ 1;
             const unsigned long long Tin = isz[in], Tout = index_slots((unsigned long long)ng * k, d.icap);
             const uint32_t tag_in = tag[in], tag_out = next_tag(tag[out]);
@@ -493,7 +567,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                             const int m = P.xidx[g][g2];
                             if (id[m] < 0) continue;
                             const double2 ap = m == 0 ? a : __ldcg(&Ai[id[m]]);
-                            cmul_acc(amp, gp_coef(Q, g2, s ^ P.u[m]), ap);
+                            cmul_acc(amp, half_coef(P, ctab, g2, s ^ P.u[m]), ap);
                         }
                     }
                     amps[g] = amp;
@@ -501,9 +575,10 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                     else if (own) drop = true;
                 }
                 unsigned long long o = block_out_range(ctr, __popc(keepm), wsum, &bbase);
+                const uint64_t sn = aff && act ? affine_of(s) : s;  // the parent in the new coordinates
                 for (int g = 0; g < ng; g++) {
                     if (!((keepm >> g) & 1u)) continue;
-                    const uint64_t tau = s ^ P.u[g];
+                    const uint64_t tau = sn ^ P0.u[g];
                     So[o] = tau;
                     Ao[o] = amps[g];
                     ok &= index_insert<1>(d, out, Tout, tag_out, &tau, (uint32_t)o);
@@ -524,10 +599,15 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             // no output dropped: every parent s gave s ^ u_g for all g, so the new
             // frame is closed under the gate's masks
             have_u = !s_drop && ng == 2;
-            cu = P.u[1];
+            cu = P0.u[1];
+            aff = false;
             t++;
         }
         oi += nb;
+    }
+    if (aff) {  // not reached in practice: a pending map always has a merge after it
+        affine_pass();
+        if (!gp_barrier(w, gen, d.status, cur)) return bail();
     }
     // the frame goes back to buffer cur0, indexed
     if (cur != cur0) {

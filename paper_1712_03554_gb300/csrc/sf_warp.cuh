@@ -413,6 +413,48 @@ __device__ __forceinline__ int warp_measure_prep(Row* r, int n, int rx, int q, C
     return rx2;
 }
 
+// Rows of the inverse of the GF(2) matrix whose rows are a[] (lane L: rows L
+// and L + 32 of n), by Gauss-Jordan elimination over the warp.  Returns false
+// if the matrix is singular.
+__device__ __forceinline__ bool warp_gf2_inverse(const uint64_t* a_in, int n, uint64_t* inv) {
+    const int lane = threadIdx.x & 31;
+    uint64_t a[2] = {a_in[0], a_in[1]};
+    uint64_t b[2] = {lane < n ? 1ull << lane : 0, lane + 32 < n ? 1ull << (lane + 32) : 0};
+    for (int c = 0; c < n; c++) {
+        // pivot: the first row p >= c with bit c set
+        const unsigned m0 = __ballot_sync(SF_FULL, lane >= c && lane < n && ((a[0] >> c) & 1));
+        const unsigned m1 = __ballot_sync(SF_FULL, lane + 32 >= c && lane + 32 < n && ((a[1] >> c) & 1));
+        if (!m0 && !m1) return false;
+        const int p = m0 ? __ffs(m0) - 1 : 32 + __ffs(m1) - 1;
+        const uint64_t pa0 = __shfl_sync(SF_FULL, a[0], p & 31), pa1 = __shfl_sync(SF_FULL, a[1], p & 31);
+        const uint64_t pb0 = __shfl_sync(SF_FULL, b[0], p & 31), pb1 = __shfl_sync(SF_FULL, b[1], p & 31);
+        const uint64_t ca0 = __shfl_sync(SF_FULL, a[0], c & 31), ca1 = __shfl_sync(SF_FULL, a[1], c & 31);
+        const uint64_t cb0 = __shfl_sync(SF_FULL, b[0], c & 31), cb1 = __shfl_sync(SF_FULL, b[1], c & 31);
+        const uint64_t pa = p < 32 ? pa0 : pa1, pb = p < 32 ? pb0 : pb1;
+        const uint64_t ca = c < 32 ? ca0 : ca1, cb = c < 32 ? cb0 : cb1;
+        for (int hf = 0; hf < 2; hf++) {
+            const int row = lane + 32 * hf;
+            if (row >= n) continue;
+            if (row == c) {  // rows c and p swap
+                a[hf] = pa;
+                b[hf] = pb;
+            } else {
+                if (row == p) {
+                    a[hf] = ca;
+                    b[hf] = cb;
+                }
+                if ((a[hf] >> c) & 1) {  // clear column c
+                    a[hf] ^= pa;
+                    b[hf] ^= pb;
+                }
+            }
+        }
+    }
+    inv[0] = b[0];
+    inv[1] = b[1];
+    return true;
+}
+
 // One Clifford gate on the rows in registers (ROTATE, Sec. III, Table 2):
 // conjugate M and D (sign flips of M to t0, composed, and t1, this gate),
 // restore Invariant 1, and multiply the run's phase factor omega^ga sqrt(2)^gb
@@ -460,6 +502,7 @@ __device__ __forceinline__ bool warp_clifford_gate(Row* r, int n, int& rx, int k
 struct BrTab {
     int ng, bad;
     int nt[4];
+    int fl[4];  // sign-pattern bits flipped for every element (0 unless the plan was moved to other coordinates)
     uint64_t u[4];
     uint64_t v[4][4];
     double2 c[4][4];
@@ -471,8 +514,8 @@ struct BrTab {
 // the last term's bit set are the negations of their complements)
 __device__ __forceinline__ double2 half_coef(const BrTab& P, const double2 (*ctab)[16], int g, uint64_t x) {
     const int ntg = P.nt[g];
-    int pat = 0;
-    for (int t = 0; t < ntg; t++) pat |= (__popcll(P.v[g][t] & x) & 1) << t;
+    int pat = P.fl[g];
+    for (int t = 0; t < ntg; t++) pat ^= (__popcll(P.v[g][t] & x) & 1) << t;
     const bool neg = (pat >> (ntg - 1)) & 1;
     const double2 cc = ctab[g][neg ? pat ^ ((1 << ntg) - 1) : pat];
     return make_double2(dneg_if(cc.x, neg), dneg_if(cc.y, neg));
@@ -706,6 +749,7 @@ __device__ __forceinline__ void warp_branch_plan_regs(const Row* r, int n, uint3
     // the rest of P, one field per lane
     if (lane < 4) {
         P.nt[lane] = gnt[lane];
+        P.fl[lane] = 0;
         P.u[lane] = gu[lane];
     } else if (lane < 20) {
         const int g = (lane - 4) >> 2, t = (lane - 4) & 3;
