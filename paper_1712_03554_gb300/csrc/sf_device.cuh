@@ -336,17 +336,25 @@ __device__ __forceinline__ long long index_find(const SfDev& d, int b, unsigned 
                                                 const uint64_t* key) {
     const uint64_t* sl = d.islot[b];
     unsigned long long slot = hash_sig<W>(key) & (T - 1);
+    if constexpr (W == 1) {
+        // four slots (64 bytes) per round trip, checked in probe order
+        const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sl);
+        for (unsigned long long probed = 0; probed < T;) {
+            const unsigned long long g0 = slot & ~3ull;
+            ulonglong2 v[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) v[i] = __ldg(s2 + g0 + i);
+            for (int i = (int)(slot & 3); i < 4; i++, probed++) {
+                if ((uint32_t)(v[i].x >> 32) != tag) return -1;
+                if (v[i].y == key[0]) return (long long)(uint32_t)v[i].x;
+            }
+            slot = (g0 + 4) & (T - 1);
+        }
+        return -1;
+    }
     for (unsigned long long probe = 0; probe < T; probe++) {
         const uint64_t* p = sl + slot * (W + 1);
-        uint64_t tv, k0;
-        if constexpr (W == 1) {
-            const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p));
-            tv = v.x;
-            k0 = v.y;
-        } else {
-            tv = __ldg(p);
-            k0 = __ldg(p + 1);
-        }
+        const uint64_t tv = __ldg(p), k0 = __ldg(p + 1);
         if ((uint32_t)(tv >> 32) != tag) return -1;
         bool eq = k0 == key[0];
 #pragma unroll

@@ -107,15 +107,22 @@ __device__ bool gp_barrier(GpWork* w, unsigned& gen, uint32_t* status, int buf) 
     return s_ok != 0;
 }
 
-// position of key in the index of buffer b (written in this launch), or -1
+// position of key in the index of buffer b (written in this launch), or -1.
+// Linear probing, read four slots (64 bytes) per round trip: the slots of an
+// aligned group are loaded together and checked in probe order.
 __device__ __forceinline__ long long gp_find(const SfDev& d, int b, unsigned long long T, uint32_t tag, uint64_t key) {
     const ulonglong2* sl = reinterpret_cast<const ulonglong2*>(d.islot[b]);
     unsigned long long slot = hash_sig<1>(&key) & (T - 1);
-    for (unsigned long long probe = 0; probe < T; probe++) {
-        const ulonglong2 v = __ldcg(sl + slot);
-        if ((uint32_t)(v.x >> 32) != tag) return -1;
-        if (v.y == key) return (long long)(uint32_t)v.x;
-        slot = (slot + 1) & (T - 1);
+    for (unsigned long long probed = 0; probed < T;) {
+        const unsigned long long g0 = slot & ~3ull;
+        ulonglong2 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) v[i] = __ldcg(sl + g0 + i);
+        for (int i = (int)(slot & 3); i < 4; i++, probed++) {
+            if ((uint32_t)(v[i].x >> 32) != tag) return -1;
+            if (v[i].y == key) return (long long)(uint32_t)v[i].x;
+        }
+        slot = (g0 + 4) & (T - 1);
     }
     return -1;
 }
