@@ -416,6 +416,7 @@ void sf_launch_clifford(const SfDev& d, const void* dev_gates, int ngates, int b
                         cudaStream_t s);
 // single-warp version for n <= 63 (W = 1)
 void sf_launch_clifford_warp(const SfDev& d, const void* dev_gates, int ngates, int buf, cudaStream_t s);
+void sf_launch_measure_prep_warp(const SfDev& d, uint32_t q, int buf, cudaStream_t s);
 void sf_launch_measure_prep(const SfDev& d, uint32_t q, int buf, uint64_t* gws, cudaStream_t s);
 void sf_launch_amp_prep(const SfDev& d, const uint64_t* dev_y, cudaStream_t s);
 // one handle's program in a single-CTA launch while the frame is small (W = 1)

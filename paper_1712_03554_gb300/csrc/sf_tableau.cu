@@ -909,6 +909,10 @@ void sf_launch_clifford(const SfDev& d, const void* dev_gates, int ngates, int b
 }
 
 void sf_launch_measure_prep(const SfDev& d, uint32_t q, int buf, uint64_t* gws, cudaStream_t s) {
+    if (d.W == 1) {  // n <= 63: one warp with the rows in registers
+        sf_launch_measure_prep_warp(d, q, buf, s);
+        return;
+    }
     SF_DISPATCH(d.W, {
         size_t sm;
         uint64_t* ws = pick_ws<WW>(d, k_measure_prep<WW>, sm, gws, 1);
