@@ -236,7 +236,11 @@ __device__ int export_phase(const Shared& S, int n, uint64_t s) {
 // Exceeding cap is an error (SF_ECAPACITY in S.status); with stop_cap > 0 the
 // run instead stops, at an op boundary and without error, before a diagonal
 // gate or random measurement whose intermediate frame could exceed stop_cap.
-// Returns the index of the first record not applied.
+// A run of up to nbm consecutive diagonal records is planned at once into
+// pb/cb (warp w plans record w); after a merge that drops nothing, the
+// following planned gates that keep the frame closed under its mask are
+// applied in place in one pass.  Returns the index of the first record not
+// applied.
 __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, uint64_t* const* sigb,
                                                       double2* const* ampb, uint32_t* idx, const OpRec* ops,
                                                       unsigned long long o0, unsigned long long o1, unsigned cap,
@@ -786,8 +790,10 @@ __global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
 
 // ---- a program on one handle's frame while it is small (sf_apply_program) ----
 // The circuit engine above, run by one CTA on a frame handle's own state: the
-// tableau rows are loaded into warp 0's registers, the handle's two frame
-// buffers are used in place, the index lives in shared memory.  The program is
+// tableau rows are loaded into warp 0's registers, frames of up to
+// kSegSmemElems elements are copied into shared memory (larger ones stay in the
+// handle's buffers), the index and the plans of a diagonal run live in shared
+// memory, 16 records planned at a time.  The program is
 // checked before anything is touched; the run stops at an op boundary before
 // a diagonal gate or random measurement whose intermediate frame could exceed
 // seg_cap; the frame is left in buffer `cur` and the tableau, X-block size and

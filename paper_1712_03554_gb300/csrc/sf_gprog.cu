@@ -8,15 +8,22 @@
 // grid barrier instead:
 //
 //   Clifford run   warp 0 of CTA 0 runs ROTATE on the tableau in registers
-//                  (Sec. III, Table 2) and publishes the affine map of the run;
-//                  barrier; every CTA applies sigma' = A sigma ^ t to its
-//                  elements and inserts them into a fresh index; barrier.
-//   diagonal run   the run's records are planned at once, CTA c planning
-//                  record c (Sec. IV: Z^w = eps D^u M^v per term, grouped by u,
-//                  half table of group coefficients); barrier; then per record
-//                  every CTA merges its share of the elements into the other
-//                  buffer (owner rule, outputs reserved with one atomic per
-//                  block, inserted into the output index); barrier.
+//                  (Sec. III, Table 2) and publishes the run's affine map
+//                  sigma' = A sigma ^ t; while it inverts A, the other warps of
+//                  CTA 0 plan the diagonal records that follow (one each);
+//                  barrier.  The map itself is applied by the next merge
+//                  (partners at A^-1 u, sign patterns from A^T v); any other
+//                  follower gets a pass that rewrites and re-indexes the
+//                  phase vectors first.
+//   diagonal run   records not planned yet are planned at once, CTA c
+//                  planning record c (Sec. IV: Z^w = eps D^u M^v per term,
+//                  grouped by u, half table of group coefficients); barrier;
+//                  then per record every CTA merges its share of the elements
+//                  into the other buffer (owner rule, outputs reserved with one
+//                  atomic per block, inserted into the output index); barrier.
+//                  Once a merge drops nothing the frame is closed under its
+//                  mask, and the following gates that keep it closed are
+//                  applied in place to each pair's amplitudes in one pass.
 //
 // A measurement or conditional record ends the program (the caller continues
 // per op).  Data written inside the launch by other CTAs is read through L2
@@ -38,8 +45,8 @@ struct GpPlan {
     double2 ctab[4][16];
 };
 
-// device workspace, zeroed at handle creation; err and ocnt are cleared
-// before every launch
+// device workspace, zeroed at handle creation; err, drop and ocnt are
+// cleared before every launch
 struct GpWork {
     unsigned int bar_count, bar_gen;
     unsigned int err[3];         // a failed check in phase p (between barriers p and p + 1): err[p % 3]
