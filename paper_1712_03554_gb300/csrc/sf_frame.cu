@@ -1077,19 +1077,82 @@ __global__ void __launch_bounds__(kThreads) k_amplitude(SfDev d, int buf) {
     for (int w = 0; w < W; w++) { y[w] = d.plan[o + w]; zm[w] = d.plan[o + W + w]; ze[w] = d.plan[o + 2 * W + w]; }
     const unsigned long long k = d.kcnt[buf];
     double acc[2] = {0.0, 0.0};
-    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        uint64_t s[W];
-        load_sig<W>(d.sig[buf], d.cap, j, s);
-        bool match = true;
+    if constexpr (W == 1) {
+        // The two Pauli products of elem_amp_phi by 4-bit chunks, tabulated once
+        // per CTA: DT[c][v] = the product of D_h over the set bits h = 4c + b of v,
+        // MT[c][v] = the product of M_R over the X-block rows R = 4c + b < r
+        // selected by v (both in increasing index, as the per-bit loops multiply)
+        __shared__ Pauli<1> DT[16][16], MT[16][16];
+        __shared__ int pv[64];
+        const int nc = (n + 3) >> 2, rc = (r + 3) >> 2;
+        for (int e = threadIdx.x; e < 16 * 16; e += blockDim.x) {
+            const int c = e >> 4, v = e & 15;
+            Pauli<1> a, b;
+            pauli_id<1>(a);
+            pauli_id<1>(b);
+            for (int bb = 0; bb < 4; bb++) {
+                const int h = 4 * c + bb;
+                if (!((v >> bb) & 1)) continue;
+                if (h < n) {
+                    Pauli<1> dh;
+                    dh.x[0] = __ldg(&d.dx[h]);
+                    dh.z[0] = __ldg(&d.dz[h]);
+                    dh.e = (int)__ldg(&d.de[h]);
+                    pauli_mul<1>(a, dh);
+                }
+                if (h < r) {
+                    Pauli<1> m;
+                    m.x[0] = __ldg(&d.mx[h]);
+                    m.z[0] = __ldg(&d.mz[h]);
+                    m.e = 0;
+                    pauli_mul<1>(b, m);
+                }
+            }
+            DT[c][v] = a;
+            MT[c][v] = b;
+        }
+        for (int R = threadIdx.x; R < 64; R += blockDim.x) pv[R] = R < r ? (__ldg(&d.piv[R]) & 63) : 0;
+        __syncthreads();
+        for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
+             j += (unsigned long long)gridDim.x * blockDim.x) {
+            const uint64_t s = d.sig[buf][j];
+            if ((s & zm[0]) != ze[0]) continue;
+            Pauli<1> q;
+            pauli_id<1>(q);
+            for (int c = 0; c < nc; c++) pauli_mul<1>(q, DT[c][(s >> (4 * c)) & 15]);
+            const uint64_t wv = y[0] ^ q.x[0];
+            Pauli<1> p;
+            pauli_id<1>(p);
+            for (int c = 0; c < rc; c++) {
+                int v = 0;
+                for (int bb = 0; bb < 4; bb++) {
+                    const int R = 4 * c + bb;
+                    if (R < r) v |= (int)((wv >> pv[R]) & 1) << bb;
+                }
+                pauli_mul<1>(p, MT[c][v]);
+            }
+            if (p.x[0] != wv) continue;
+            const int ip = (q.e + __popcll(q.x[0] & q.z[0]) + 2 * __popcll(q.z[0] & wv) + p.e +
+                            __popcll(p.x[0] & p.z[0])) & 3;
+            const double2 c = ipow_mul(d.amp[buf][j], ip);
+            acc[0] += c.x;
+            acc[1] += c.y;
+        }
+    } else {
+        for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
+             j += (unsigned long long)gridDim.x * blockDim.x) {
+            uint64_t s[W];
+            load_sig<W>(d.sig[buf], d.cap, j, s);
+            bool match = true;
 #pragma unroll
-        for (int w = 0; w < W; w++) match &= ((s[w] & zm[w]) == ze[w]);
-        if (!match) continue;
-        const int ip = elem_amp_phi<W>(d, s, y, r);
-        if (ip < 0) continue;
-        const double2 c = ipow_mul(d.amp[buf][j], ip);
-        acc[0] += c.x;
-        acc[1] += c.y;
+            for (int w = 0; w < W; w++) match &= ((s[w] & zm[w]) == ze[w]);
+            if (!match) continue;
+            const int ip = elem_amp_phi<W>(d, s, y, r);
+            if (ip < 0) continue;
+            const double2 c = ipow_mul(d.amp[buf][j], ip);
+            acc[0] += c.x;
+            acc[1] += c.y;
+        }
     }
     block_sum<2>(acc, sh);
     if (threadIdx.x == 0) {
