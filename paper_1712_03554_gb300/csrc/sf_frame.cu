@@ -1176,7 +1176,9 @@ __global__ void k_reduce_final(SfDev d, int what) {
             d.out[0] = v[0];
             d.out[1] = v[1];
         } else {
-            const double sc = exp2(-0.5 * (double)d.meta[0]);
+            // 2^{-r/2} exactly: a power of two, times 1/sqrt(2) for odd r
+            const int r = d.meta[0];
+            const double sc = ldexp(1.0, -((r + 1) >> 1)) * ((r & 1) ? 1.41421356237309504880 : 1.0);
             const double2 c = cmul(*d.g, make_double2(v[0] * sc, v[1] * sc));
             d.out[2] = c.x;
             d.out[3] = c.y;
@@ -1277,7 +1279,8 @@ void sf_launch_prob(const SfDev& d, int buf, cudaStream_t s) {
     SF_DISPATCH(d.W, k_prob<WW><<<d.nblk, kThreads, 0, s>>>(d, buf));
 }
 
-void sf_launch_reduce_final(const SfDev& d, int what, cudaStream_t s) { k_reduce_final<<<1, 1024, 0, s>>>(d, what); }
+// 128 threads: one warp per SM sub-partition, whose FP64 pipe does the sums
+void sf_launch_reduce_final(const SfDev& d, int what, cudaStream_t s) { k_reduce_final<<<1, 128, 0, s>>>(d, what); }
 
 void sf_launch_amplitude(const SfDev& d, int buf, cudaStream_t s) {
     SF_DISPATCH(d.W, k_amplitude<WW><<<d.nblk, kThreads, 0, s>>>(d, buf));
