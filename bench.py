@@ -262,23 +262,48 @@ def measured_peak_gbs():
     return 6800.0, "fallback"
 
 
-def kernel_sources_hash() -> str:
+# the file that defines each timed kernel class; its hash (with every header it
+# includes) decides whether an ncu traffic figure still describes the kernel
+KERNEL_SOURCE = {"segment": "sf_campaign.cu", "gprog": "sf_gprog.cu", "clifford": "sf_tableau_warp.cu",
+                 "measure_prep": "sf_tableau_warp.cu", "reset": "sf_tableau.cu", "amp_prep": "sf_tableau.cu"}
+
+
+def kernel_sources_hash(cls: str) -> str:
+    """sha256 (16 hex digits) of the source file defining kernel class `cls`
+    and of the headers it includes, transitively (csrc/ and include/)."""
+    import re
+    dirs = [os.path.join(ROOT, "paper_1712_03554_gb300", "csrc"), os.path.join(ROOT, "include")]
+    todo, seen = [KERNEL_SOURCE.get(cls, "sf_frame.cu")], []
+    while todo:
+        fn = todo.pop(0)
+        if fn in seen:
+            continue
+        for d in dirs:
+            path = os.path.join(d, fn)
+            if os.path.exists(path):
+                seen.append(fn)
+                with open(path, encoding="utf-8") as fh:
+                    todo += re.findall(r'^#include "([^"]+)"', fh.read(), re.M)
+                break
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1712_03554_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, fn), "rb") as fh:
-            h.update(fh.read())
+    for fn in sorted(seen):
+        for d in dirs:
+            path = os.path.join(d, fn)
+            if os.path.exists(path):
+                with open(path, "rb") as fh:
+                    h.update(fn.encode() + b"\0" + fh.read())
+                break
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(cls: str):
     """DRAM bytes per launch of `cls` from the committed ncu summary, or None if
-    absent or taken on different kernel sources."""
+    absent or taken on different sources of that kernel."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             t = json.load(fh)
-        if t.get("sources") != kernel_sources_hash():
+        if t.get("sources", {}).get(cls) != kernel_sources_hash(cls):
             return None
         v = t.get("bytes_per_launch", {}).get(cls)
         return float(v) if v is not None else None
