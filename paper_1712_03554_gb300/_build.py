@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libsf.so")
 SOURCES = ["sf_tableau.cu", "sf_tableau_warp.cu", "sf_frame.cu", "sf_api.cu", "sf_noalloc.cu", "sf_campaign.cu",
-           "sf_gprog.cu", "sf_server.cu"]
+           "sf_gprog.cu", "sf_server.cu", "sf_multiframe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 

@@ -787,3 +787,417 @@ const char* sf_last_error(sf_handle h) {
 }
 
 }  // extern "C"
+
+// ---- multiframes (include/sf_multiframe.h, Sec. IV) ------------------------
+// A multiframe is a list of frame handles on one stream.  COALESCE of a frame
+// runs on the device (export of canonical amplitudes, then k_mf_pair); the
+// host reads the pairs, groups them by (e, d), copies the owners of each group
+// into a new frame with the same tableau (k_mf_gather), rotates it by
+// C = CNOT_{v1,v2} ... P^d_{v1} H_{v1} with the frame's own Clifford path, and
+// keeps the unpaired elements in the old frame.  Frames whose matrices are
+// equal are merged by exporting one and importing it into the other in that
+// frame's convention (k_mf_import), then coalescing (Def. 1).
+#include <map>
+
+#include "sf_multiframe.cuh"
+#include "sf_multiframe.h"
+
+struct sf_multiframe_s {
+    uint32_t n = 0;
+    uint64_t max_elems = 0;
+    uint32_t max_frames = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<sf_handle> all;     // every frame handle created (owned)
+    std::vector<sf_handle> frames;  // the multiframe, in list order
+    std::vector<sf_handle> spare;   // handles not in use, reused first
+    MfPair* dpairs = nullptr;
+    uint32_t* dkeep = nullptr;
+    uint32_t* didx = nullptr;
+    uint32_t* dcounts = nullptr;
+    std::string err;
+};
+
+namespace {
+
+constexpr int kMfKernelId = 1 << 20;  // multiframe kernels are counted, never timed by class
+constexpr double kMfTol = 1e-9;
+
+sf_status mf_fail(sf_multiframe m, sf_status code, const std::string& msg) {
+    if (m) m->err = msg;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_err = msg;
+    return code;
+}
+
+// a failed call on one of the frames: its message becomes the multiframe's
+sf_status mf_from(sf_multiframe m, sf_handle h, sf_status st) {
+    if (st != SF_OK) m->err = h ? h->err : std::string(sf_last_error(nullptr));
+    return st;
+}
+
+#define MF_TRY(m, h, call)                            \
+    do {                                              \
+        sf_status s_ = (call);                        \
+        if (s_ != SF_OK) return mf_from((m), (h), s_); \
+    } while (0)
+
+sf_status mf_new_frame(sf_multiframe m, sf_handle* out) {
+    if (!m->spare.empty()) {
+        *out = m->spare.back();
+        m->spare.pop_back();
+        return SF_OK;
+    }
+    if (m->all.size() >= m->max_frames) return mf_fail(m, SF_ECAPACITY, "multiframe would exceed max_frames");
+    sf_status st = sf_create(m->n, m->max_elems, m->stream, out);
+    if (st) return mf_fail(m, st, std::string("frame creation failed: ") + sf_last_error(nullptr));
+    m->all.push_back(*out);
+    return SF_OK;
+}
+
+// the full tableau state of src (matrix, destabilizers, pivots, X-block size,
+// global phase) copied into dst; same stream
+sf_status mf_copy_tableau(sf_handle dst, sf_handle src) {
+    const size_t n = src->n, W = src->d.W;
+    cudaStream_t s = src->stream;
+    const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+    SF_CK(dst, cudaMemcpyAsync(dst->d.mx, src->d.mx, W * n * sizeof(uint64_t), dd, s));
+    SF_CK(dst, cudaMemcpyAsync(dst->d.mz, src->d.mz, W * n * sizeof(uint64_t), dd, s));
+    SF_CK(dst, cudaMemcpyAsync(dst->d.dx, src->d.dx, W * n * sizeof(uint64_t), dd, s));
+    SF_CK(dst, cudaMemcpyAsync(dst->d.dz, src->d.dz, W * n * sizeof(uint64_t), dd, s));
+    SF_CK(dst, cudaMemcpyAsync(dst->d.de, src->d.de, n * sizeof(uint32_t), dd, s));
+    SF_CK(dst, cudaMemcpyAsync(dst->d.piv, src->d.piv, n * sizeof(int32_t), dd, s));
+    SF_CK(dst, cudaMemcpyAsync(dst->d.meta, src->d.meta, 4 * sizeof(int32_t), dd, s));
+    SF_CK(dst, cudaMemcpyAsync(dst->d.g, src->d.g, sizeof(double2), dd, s));
+    return SF_OK;
+}
+
+// unsigned rows of the matrix of h (one word each: x rows, then z rows)
+sf_status mf_matrix(sf_handle h, std::vector<uint64_t>& xz) {
+    const size_t n = h->n;
+    xz.resize(2 * n);
+    SF_CK(h, cudaMemcpyAsync(xz.data(), h->d.mx, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
+    SF_CK(h, cudaMemcpyAsync(xz.data() + n, h->d.mz, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
+    return sync_check(h);
+}
+
+// COALESCE(F): appends to `out` F with its unpaired elements (if any), then
+// one new frame per pair class (e, d) in ascending order; adds the pairs formed
+sf_status mf_coalesce_frame(sf_multiframe m, sf_handle F, std::vector<sf_handle>& out, uint64_t& pairs_formed) {
+    uint64_t k = 0;
+    MF_TRY(m, F, sf_size(F, &k));
+    if (k < 2) {
+        (k ? out : m->spare).push_back(F);
+        return SF_OK;
+    }
+    if (k > SF_MF_MAXK) return mf_fail(m, SF_ECAPACITY, "COALESCE takes frames of at most 8192 elements");
+    cudaStream_t s = m->stream;
+    const int stage = F->cur ^ 1;
+    MF_TRY(m, F, launch(F, kMfKernelId, "export", [&] { sf_launch_export(F->d, F->cur, stage, s); }));
+    F->idx_ok[stage] = false;
+    MF_TRY(m, F, launch(F, kMfKernelId, "k_mf_pair", [&] {
+               sf_launch_mf_pair(F->d, F->cur, stage, k, kMfTol, m->dpairs, m->dkeep, m->dcounts, s);
+           }));
+    uint32_t cnt[2] = {0, 0};
+    SF_CK(F, cudaMemcpyAsync(cnt, m->dcounts, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    MF_TRY(m, F, sync_check(F));
+    const uint32_t np = cnt[0], nk = cnt[1];
+    if (2ull * np + nk != k) return mf_fail(m, SF_EINTERNAL, "COALESCE lost elements");
+    if (np == 0) {
+        out.push_back(F);
+        return SF_OK;
+    }
+    std::vector<MfPair> pairs(np);
+    std::vector<uint32_t> keep(nk);
+    std::vector<uint64_t> xz;
+    SF_CK(F, cudaMemcpyAsync(pairs.data(), m->dpairs, np * sizeof(MfPair), cudaMemcpyDeviceToHost, s));
+    if (nk) SF_CK(F, cudaMemcpyAsync(keep.data(), m->dkeep, nk * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    MF_TRY(m, F, mf_matrix(F, xz));
+    pairs_formed += np;
+    std::map<std::pair<uint64_t, uint32_t>, std::vector<uint32_t>> cls;
+    for (const MfPair& p : pairs) cls[{p.e, p.d}].push_back(p.owner);
+    // owners of each class, then the unpaired elements, as one index list
+    std::vector<uint32_t> idx;
+    idx.reserve(k);
+    for (const auto& c : cls) idx.insert(idx.end(), c.second.begin(), c.second.end());
+    idx.insert(idx.end(), keep.begin(), keep.end());
+    SF_CK(F, cudaMemcpyAsync(m->didx, idx.data(), idx.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    std::vector<sf_handle> made;
+    size_t off = 0;
+    sf_status st = SF_OK;
+    for (const auto& c : cls) {
+        sf_handle G = nullptr;
+        st = mf_new_frame(m, &G);
+        if (st) break;
+        made.push_back(G);
+        st = mf_copy_tableau(G, F);
+        if (st) break;
+        const uint32_t cntc = (uint32_t)c.second.size();
+        st = launch(G, kMfKernelId, "k_mf_gather", [&] {
+            sf_launch_mf_gather(G->d, G->cur, F->d.sig[F->cur], F->d.amp[F->cur], m->didx + off, cntc, std::sqrt(2.0), s);
+        });
+        if (st) {
+            mf_from(m, G, st);
+            break;
+        }
+        G->idx_ok[0] = G->idx_ok[1] = false;
+        off += cntc;
+        // the qubits v_1 < ... < v_m of the Z_k-rows in e
+        std::vector<uint32_t> V;
+        for (uint64_t e = c.first.first; e; e &= e - 1) {
+            const int r = __builtin_ctzll(e);
+            V.push_back((uint32_t)__builtin_ctzll(xz[m->n + r]));
+        }
+        std::sort(V.begin(), V.end());
+        std::vector<sf_gate> gates;
+        gates.push_back(sf_gate{SF_H, V[0], 0, 0});
+        for (uint32_t t = 0; t < c.first.second; t++) gates.push_back(sf_gate{SF_S, V[0], 0, 0});
+        for (size_t i = 1; i < V.size(); i++) gates.push_back(sf_gate{SF_CNOT, V[0], V[i], 0});
+        st = sf_apply_clifford(G, gates.data(), gates.size());
+        if (st) {
+            mf_from(m, G, st);
+            break;
+        }
+    }
+    if (!st && nk) {
+        st = launch(F, kMfKernelId, "k_mf_gather", [&] {
+            sf_launch_mf_gather(F->d, F->cur ^ 1, F->d.sig[F->cur], F->d.amp[F->cur], m->didx + off, nk, 1.0, s);
+        });
+        if (st) mf_from(m, F, st);
+        F->cur ^= 1;
+        F->idx_ok[0] = F->idx_ok[1] = false;
+    }
+    // every handle stays reachable (list or spare), also after an error
+    (nk ? out : m->spare).push_back(F);
+    out.insert(out.end(), made.begin(), made.end());
+    cudaError_t e = cudaStreamSynchronize(s);  // idx is read by the copy above
+    if (st) return st;
+    if (e != cudaSuccess) return mf_fail(m, SF_ECUDA, std::string("COALESCE: ") + cudaGetErrorString(e));
+    return SF_OK;
+}
+
+// A16: frames with equal matrices merged into the first of them (union, then
+// Def. 1 coalescing with drop_eps); empty frames leave the list
+sf_status mf_merge(sf_multiframe m, double eps) {
+    std::vector<std::vector<uint64_t>> keys(m->frames.size());
+    for (size_t i = 0; i < m->frames.size(); i++) MF_TRY(m, m->frames[i], mf_matrix(m->frames[i], keys[i]));
+    std::map<std::vector<uint64_t>, size_t> first;
+    std::vector<std::vector<sf_handle>> groups;
+    for (size_t i = 0; i < m->frames.size(); i++) {
+        auto it = first.find(keys[i]);
+        if (it == first.end()) {
+            first.emplace(keys[i], groups.size());
+            groups.push_back({m->frames[i]});
+        } else {
+            groups[it->second].push_back(m->frames[i]);
+        }
+    }
+    std::vector<sf_handle> out;
+    sf_status st = SF_OK;
+    for (auto& g : groups) {
+        if (st) {  // after an error: keep the rest reachable, unmerged
+            out.insert(out.end(), g.begin(), g.end());
+            continue;
+        }
+        sf_handle dst = g[0];
+        uint64_t kd = 0;
+        st = mf_from(m, dst, sf_size(dst, &kd));
+        for (size_t i = 1; i < g.size() && !st; i++) {
+            sf_handle src = g[i];
+            uint64_t ks = 0;
+            st = mf_from(m, src, sf_size(src, &ks));
+            if (st) break;
+            if (kd + ks > m->max_elems) {
+                st = mf_fail(m, SF_ECAPACITY, "merged frame would exceed max_elems");
+                break;
+            }
+            if (ks) {
+                const int stage = src->cur ^ 1;
+                st = mf_from(m, src, launch(src, kMfKernelId, "export",
+                                            [&] { sf_launch_export(src->d, src->cur, stage, m->stream); }));
+                src->idx_ok[stage] = false;
+                if (st) break;
+                const uint64_t off = kd;
+                st = mf_from(m, dst, launch(dst, kMfKernelId, "k_mf_import", [&] {
+                                 sf_launch_mf_import(dst->d, dst->cur, off, src->d.sig[stage], src->d.amp[stage],
+                                                     (uint32_t)ks, m->stream);
+                             }));
+                dst->idx_ok[0] = dst->idx_ok[1] = false;
+                kd += ks;
+            }
+            m->spare.push_back(src);
+            g[i] = nullptr;
+        }
+        if (!st && g.size() > 1) st = mf_from(m, dst, sf_coalesce(dst, eps, &kd));
+        if (!st && kd == 0) m->spare.push_back(dst);
+        else out.push_back(dst);
+        for (size_t i = 1; i < g.size(); i++)
+            if (g[i]) out.push_back(g[i]);
+    }
+    m->frames.swap(out);
+    return st;
+}
+
+// merge, then COALESCE every frame and merge again until no pair forms
+sf_status mf_coalesce_all(sf_multiframe m, double eps) {
+    sf_status st = mf_merge(m, eps);
+    if (st) return st;
+    for (int iter = 0;; iter++) {
+        if (iter > (1 << 20)) return mf_fail(m, SF_EINTERNAL, "multiframe coalescing did not terminate");
+        std::vector<sf_handle> next;
+        uint64_t formed = 0;
+        size_t i = 0;
+        for (; i < m->frames.size() && !st; i++) st = mf_coalesce_frame(m, m->frames[i], next, formed);
+        next.insert(next.end(), m->frames.begin() + i, m->frames.end());
+        m->frames.swap(next);
+        if (st) return st;
+        st = mf_merge(m, eps);
+        if (st || formed == 0) return st;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+sf_status sf_mf_create(uint32_t n_qubits, uint64_t max_elems, uint32_t max_frames, void* cuda_stream,
+                       sf_multiframe* out) {
+    if (!out) return mf_fail(nullptr, SF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 63) return mf_fail(nullptr, SF_EINVAL, "multiframes take 1 to 63 qubits");
+    if (max_frames < 1) return mf_fail(nullptr, SF_EINVAL, "max_frames must be >= 1");
+    sf_multiframe m = new (std::nothrow) sf_multiframe_s();
+    if (!m) return mf_fail(nullptr, SF_ENOMEM, "host allocation failed");
+    m->n = n_qubits;
+    m->max_elems = max_elems;
+    m->max_frames = max_frames;
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    sf_handle F = nullptr;
+    sf_status st = mf_new_frame(m, &F);
+    if (st) {
+        const std::string msg = m->err;
+        sf_mf_destroy(m);
+        return mf_fail(nullptr, st, msg);
+    }
+    m->frames.push_back(F);
+    cudaError_t e = cudaMallocAsync(&m->dpairs, SF_MF_MAXK / 2 * sizeof(MfPair), m->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&m->dkeep, SF_MF_MAXK * sizeof(uint32_t), m->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&m->didx, SF_MF_MAXK * sizeof(uint32_t), m->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&m->dcounts, 2 * sizeof(uint32_t), m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) {
+        sf_mf_destroy(m);
+        return mf_fail(nullptr, SF_ENOMEM, "multiframe scratch allocation failed");
+    }
+    *out = m;
+    return SF_OK;
+}
+
+sf_status sf_mf_destroy(sf_multiframe m) {
+    if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    for (sf_handle h : m->all) sf_destroy(h);
+    for (void* p : {(void*)m->dpairs, (void*)m->dkeep, (void*)m->didx, (void*)m->dcounts})
+        if (p) cudaFreeAsync(p, m->stream);
+    cudaStreamSynchronize(m->stream);
+    delete m;
+    return SF_OK;
+}
+
+sf_status sf_mf_apply_clifford(sf_multiframe m, const sf_gate* gates, uint64_t n_gates) {
+    if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    for (sf_handle F : m->frames) MF_TRY(m, F, sf_apply_clifford(F, gates, n_gates));
+    return SF_OK;
+}
+
+sf_status sf_mf_apply_nonclifford(sf_multiframe m, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
+                                  double drop_eps) {
+    if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    std::vector<sf_handle> kept;
+    sf_status st = SF_OK;
+    for (size_t i = 0; i < m->frames.size(); i++) {
+        sf_handle F = m->frames[i];
+        uint64_t k = 1;
+        if (!st) st = mf_from(m, F, sf_apply_nonclifford_coalesce(F, kind, q0, q1, theta, drop_eps));
+        if (!st) st = mf_from(m, F, sf_size(F, &k));
+        (k || st ? kept : m->spare).push_back(F);
+    }
+    m->frames.swap(kept);
+    return st;
+}
+
+sf_status sf_mf_apply_toffoli(sf_multiframe m, uint32_t c1, uint32_t c2, uint32_t t, double drop_eps) {
+    if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    if (!(drop_eps >= 0.0)) return mf_fail(m, SF_EINVAL, "drop_eps must be >= 0");
+    for (sf_handle F : m->frames) {
+        MF_TRY(m, F, sf_apply_toffoli(F, c1, c2, t));
+        MF_TRY(m, F, sf_coalesce(F, drop_eps, nullptr));
+    }
+    return mf_coalesce_all(m, drop_eps);
+}
+
+sf_status sf_mf_apply_cr(sf_multiframe m, uint32_t c, uint32_t t, double alpha, double drop_eps) {
+    if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    if (!(drop_eps >= 0.0)) return mf_fail(m, SF_EINVAL, "drop_eps must be >= 0");
+    for (sf_handle F : m->frames) {
+        MF_TRY(m, F, sf_apply_cr_cofactor(F, c, t, alpha));
+        MF_TRY(m, F, sf_coalesce(F, drop_eps, nullptr));
+    }
+    return mf_coalesce_all(m, drop_eps);
+}
+
+sf_status sf_mf_count(sf_multiframe m, uint32_t* n_frames, uint64_t* n_states) {
+    if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    uint64_t tot = 0;
+    for (sf_handle F : m->frames) {
+        uint64_t k = 0;
+        MF_TRY(m, F, sf_size(F, &k));
+        tot += k;
+    }
+    if (n_frames) *n_frames = (uint32_t)m->frames.size();
+    if (n_states) *n_states = tot;
+    return SF_OK;
+}
+
+sf_status sf_mf_coalesce(sf_multiframe m, double drop_eps, uint32_t* n_frames, uint64_t* n_states) {
+    if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    if (!(drop_eps >= 0.0)) return mf_fail(m, SF_EINVAL, "drop_eps must be >= 0");
+    sf_status st = mf_coalesce_all(m, drop_eps);
+    if (st) return st;
+    return sf_mf_count(m, n_frames, n_states);
+}
+
+sf_status sf_mf_amplitude(sf_multiframe m, const uint64_t* x_bits, double* re, double* im) {
+    if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    if (!x_bits || !re || !im) return mf_fail(m, SF_EINVAL, "NULL argument");
+    double sr = 0.0, si = 0.0;
+    for (sf_handle F : m->frames) {
+        double a = 0.0, b = 0.0;
+        MF_TRY(m, F, sf_amplitude(F, x_bits, &a, &b));
+        sr += a;
+        si += b;
+    }
+    *re = sr;
+    *im = si;
+    return SF_OK;
+}
+
+sf_status sf_mf_frame(sf_multiframe m, uint32_t i, sf_handle* out) {
+    if (!m || !out) return mf_fail(m, SF_EINVAL, "NULL argument");
+    if (i >= m->frames.size()) return mf_fail(m, SF_EINVAL, "frame index out of range");
+    *out = m->frames[i];
+    return SF_OK;
+}
+
+uint64_t sf_mf_launches(sf_multiframe m) {
+    uint64_t t = 0;
+    if (m)
+        for (sf_handle h : m->all) t += h->launches;
+    return t;
+}
+
+const char* sf_mf_last_error(sf_multiframe m) {
+    if (m) return m->err.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    return g_err.c_str();
+}
+
+}  // extern "C"

@@ -14,6 +14,7 @@ amplitudes read and written; index and hash tables are not counted).
   python -m paper_1712_03554_gb300.kernel_bench campaign-case 64 (one campaign launch, 32 threads, global index)
   python -m paper_1712_03554_gb300.kernel_bench clifford-case 1024 (one Clifford batch of 200 gates at n)
   python -m paper_1712_03554_gb300.kernel_bench cuccaro 5 6 7   (adder: Toffoli by cofactors vs Clifford+7T)
+  python -m paper_1712_03554_gb300.kernel_bench cuccaro-mf 4 5 6 7 (adder: one frame vs a multiframe)
 """
 from __future__ import annotations
 
@@ -220,6 +221,46 @@ def cuccaro_compare(nbs=(5, 6, 7)):
         print(json.dumps(row), flush=True)
 
 
+def cuccaro_multiframe(nbs=(4, 5, 6, 7)):
+    """The Cuccaro adder on the equal superposition, Toffolis by cofactors
+    (Eq. 2), as one frame and as a multiframe (COALESCE and the merge of equal
+    matrices after every Toffoli, Sec. IV): wall time of the whole circuit
+    (median of 3 after a warm-up), final frames and states, kernel launches."""
+    for nb in nbs:
+        n = 2 * nb + 2
+        ops = c.cuccaro(nb, True, toffoli="cofactor", coalesce=False)
+        row = {"nbits": nb, "qubits": n}
+        ts = []
+        f = sf.Frame(n, 1 << min(2 * nb + 2, 24))
+        for rep in range(4):
+            f.reset()
+            f.sync()
+            l0 = f.kernel_launches()
+            t0 = time.perf_counter()
+            c.run(f, ops)
+            f.sync()
+            ts.append(time.perf_counter() - t0)
+        row["frame_ms"] = sorted(ts[1:])[1] * 1e3
+        row["frame_states"] = f.size()
+        row["frame_launches"] = f.kernel_launches() - l0
+        f.close()
+        ts = []
+        for rep in range(4):
+            mf = sf.MultiFrame(n, max_elems=4096, max_frames=8192)
+            mf.count()
+            l0 = mf.kernel_launches()
+            t0 = time.perf_counter()
+            c.run(mf, ops)
+            nf, ns = mf.count()
+            ts.append(time.perf_counter() - t0)
+            launches = mf.kernel_launches() - l0
+            mf.close()
+        row["multiframe_ms"] = sorted(ts[1:])[1] * 1e3
+        row["multiframe_frames"], row["multiframe_states"] = nf, ns
+        row["multiframe_launches"] = launches
+        print(json.dumps(row), flush=True)
+
+
 if __name__ == "__main__":
     mode = sys.argv[1] if len(sys.argv) > 1 else "throughput"
     args = [int(a) for a in sys.argv[2:]]
@@ -237,6 +278,8 @@ if __name__ == "__main__":
         campaign_case(args[0] if args else 64)
     elif mode == "cuccaro":
         cuccaro_compare(args or [5, 6, 7])
+    elif mode == "cuccaro-mf":
+        cuccaro_multiframe(args or [4, 5, 6, 7])
     elif mode == "clifford-case":
         clifford_case(args[0] if args else 1024)
     else:

@@ -108,6 +108,18 @@ def load(build: bool = True) -> C.CDLL:
         "sf_campaign_set_shape": ([H, u32, u32], st),
         "sf_campaign_get_shape": ([H, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)], st),
         "sf_campaign_autotune": ([H, C.c_void_p, C.c_void_p, u32, dbl, u32, C.POINTER(C.c_float)], st),
+        "sf_mf_create": ([u32, u64, u32, C.c_void_p, C.POINTER(C.c_void_p)], st),
+        "sf_mf_destroy": ([H], st),
+        "sf_mf_apply_clifford": ([H, C.POINTER(sf_gate), u64], st),
+        "sf_mf_apply_nonclifford": ([H, u32, u32, u32, dbl, dbl], st),
+        "sf_mf_apply_toffoli": ([H, u32, u32, u32, dbl], st),
+        "sf_mf_apply_cr": ([H, u32, u32, dbl, dbl], st),
+        "sf_mf_coalesce": ([H, dbl, C.POINTER(C.c_uint32), P64], st),
+        "sf_mf_count": ([H, C.POINTER(C.c_uint32), P64], st),
+        "sf_mf_amplitude": ([H, P64, PD, PD], st),
+        "sf_mf_frame": ([H, u32, C.POINTER(C.c_void_p)], st),
+        "sf_mf_launches": ([H], u64),
+        "sf_mf_last_error": ([H], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -410,7 +422,7 @@ class Frame:
 
     def close(self) -> None:
         h, self.h = getattr(self, "h", None), None
-        if h:
+        if h and getattr(self, "_owned", True):
             self.lib.sf_destroy(h)
 
     def __del__(self):
@@ -572,3 +584,93 @@ class Frame:
                                           amp.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(k)), self.h)
         k = int(k.value)
         return sig[:k].copy(), amp[:k, 0] + 1j * amp[:k, 1]
+
+
+class MultiFrame:
+    """A multiframe on the GPU (include/sf_multiframe.h, Sec. IV): frames with
+    different stabilizer matrices whose states sum to one state."""
+
+    def __init__(self, n: int, max_elems: int = 8192, max_frames: int = 4096, stream=None):
+        self.lib = load()
+        self.n = n
+        if stream is None:
+            sh = _current_stream_handle()
+        elif isinstance(stream, int):
+            sh = stream
+        else:
+            sh = int(stream.cuda_stream)
+        self.stream_handle = sh
+        h = C.c_void_p()
+        self._check(self.lib.sf_mf_create(n, max_elems, max_frames, C.c_void_p(sh), C.byref(h)), None)
+        self.h = h
+        self.max_elems = max_elems
+
+    def _check(self, code: int, h) -> None:
+        if code != SF_OK:
+            msg = self.lib.sf_mf_last_error(h)
+            raise SFError(code, msg.decode() if msg else "")
+
+    def close(self) -> None:
+        h, self.h = getattr(self, "h", None), None
+        if h:
+            self.lib.sf_mf_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_clifford(self, gates) -> None:
+        arr = (sf_gate * len(gates))(*[sf_gate(int(g[0]), int(g[1]), int(g[2]) if len(g) > 2 else 0, 0)
+                                         for g in gates])
+        self._check(self.lib.sf_mf_apply_clifford(self.h, arr, len(gates)), self.h)
+
+    def apply_nonclifford_coalesce(self, kind, q0, q1=0, theta=0.0, drop_eps=1e-12) -> None:
+        self._check(self.lib.sf_mf_apply_nonclifford(self.h, kind, q0, q1, float(theta), float(drop_eps)), self.h)
+
+    def apply_toffoli_cofactor(self, c1, c2, t, drop_eps=1e-12) -> None:
+        self._check(self.lib.sf_mf_apply_toffoli(self.h, c1, c2, t, float(drop_eps)), self.h)
+
+    def apply_cr_cofactor(self, c, t, alpha, drop_eps=1e-12) -> None:
+        self._check(self.lib.sf_mf_apply_cr(self.h, c, t, float(alpha), float(drop_eps)), self.h)
+
+    def coalesce(self, drop_eps=1e-12):
+        nf, ns = C.c_uint32(), C.c_uint64()
+        self._check(self.lib.sf_mf_coalesce(self.h, float(drop_eps), C.byref(nf), C.byref(ns)), self.h)
+        return int(nf.value), int(ns.value)
+
+    def count(self):
+        nf, ns = C.c_uint32(), C.c_uint64()
+        self._check(self.lib.sf_mf_count(self.h, C.byref(nf), C.byref(ns)), self.h)
+        return int(nf.value), int(ns.value)
+
+    def amplitude(self, x) -> complex:
+        xs = np.array([int(x)], dtype=np.uint64)
+        re, im = C.c_double(), C.c_double()
+        self._check(self.lib.sf_mf_amplitude(self.h, xs.ctypes.data_as(C.POINTER(C.c_uint64)), C.byref(re),
+                                             C.byref(im)), self.h)
+        return complex(re.value, im.value)
+
+    def frame(self, i: int) -> Frame:
+        """Frame i as a borrowed Frame (valid until the next call on the multiframe)."""
+        fh = C.c_void_p()
+        self._check(self.lib.sf_mf_frame(self.h, i, C.byref(fh)), self.h)
+        f = Frame.__new__(Frame)
+        f.lib, f.n, f.h, f.W, f.max_elems, f.stream_handle = self.lib, self.n, fh, 1, self.max_elems, self.stream_handle
+        f._owned = False
+        return f
+
+    def as_dict(self):
+        """{(x bytes, z bytes): {sigma: amplitude}} -- the multiframe as a set."""
+        out = {}
+        for i in range(self.count()[0]):
+            f = self.frame(i)
+            x, z, _ = f.tableau()
+            sig, amp = f.frame()
+            out[(x.tobytes(), z.tobytes())] = {int(row[0]): complex(a) for row, a in zip(sig, amp)}
+        return out
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.sf_mf_launches(self.h))
+
