@@ -789,10 +789,12 @@ const char* sf_last_error(sf_handle h) {
 }  // extern "C"
 
 // ---- multiframes (include/sf_multiframe.h, Sec. IV) ------------------------
-// A multiframe is a list of frame handles on one stream.  COALESCE of a frame
-// runs on the device (export of canonical amplitudes, then k_mf_pair); the
-// host reads the pairs, groups them by (e, d), copies the owners of each group
-// into a new frame with the same tableau (k_mf_gather), rotates it by
+// A multiframe is a list of frame handles on one stream.  Every operation runs
+// as phases over all frames: each phase enqueues the work of every frame and
+// its reads into pinned memory, then synchronises once.  COALESCE of a frame
+// runs on the device (export of canonical amplitudes, then k_mf_pair); the host
+// groups the pairs by (e, d), copies the owners of each group into a new frame
+// with the same tableau (k_mf_gather), rotates it by
 // C = CNOT_{v1,v2} ... P^d_{v1} H_{v1} with the frame's own Clifford path, and
 // keeps the unpaired elements in the old frame.  Frames whose matrices are
 // equal are merged by exporting one and importing it into the other in that
@@ -810,10 +812,20 @@ struct sf_multiframe_s {
     std::vector<sf_handle> all;     // every frame handle created (owned)
     std::vector<sf_handle> frames;  // the multiframe, in list order
     std::vector<sf_handle> spare;   // handles not in use, reused first
+    // one COALESCE round: per frame, its pairs and unpaired elements at the
+    // frame's element offset, two counts per frame, and the index lists
     MfPair* dpairs = nullptr;
     uint32_t* dkeep = nullptr;
-    uint32_t* didx = nullptr;
     uint32_t* dcounts = nullptr;
+    uint32_t* didx = nullptr;
+    size_t dpairs_cap = 0, dkeep_cap = 0, dcounts_cap = 0, didx_cap = 0;
+    // pinned mirrors, and the frames' matrices (2n words per frame)
+    MfPair* hpairs = nullptr;
+    uint32_t* hkeep = nullptr;
+    uint32_t* hcounts = nullptr;
+    uint32_t* hidx = nullptr;
+    uint64_t* hmat = nullptr;
+    size_t hpairs_cap = 0, hkeep_cap = 0, hcounts_cap = 0, hidx_cap = 0, hmat_cap = 0;
     std::string err;
 };
 
@@ -841,6 +853,40 @@ sf_status mf_from(sf_multiframe m, sf_handle h, sf_status st) {
         if (s_ != SF_OK) return mf_from((m), (h), s_); \
     } while (0)
 
+#define MF_CK(m, call)                                                                               \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return mf_fail((m), SF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+sf_status mf_grow_dev(sf_multiframe m, T** p, size_t& cap, size_t need) {
+    if (need <= cap) return SF_OK;
+    const size_t nc = std::max<size_t>(need, 2 * cap);
+    if (*p) cudaFreeAsync(*p, m->stream);
+    *p = nullptr;
+    cap = 0;
+    void* v = nullptr;
+    if (cudaMallocAsync(&v, nc * sizeof(T), m->stream) != cudaSuccess)
+        return mf_fail(m, SF_ENOMEM, "multiframe scratch allocation failed");
+    *p = static_cast<T*>(v);
+    cap = nc;
+    return SF_OK;
+}
+
+template <typename T>
+sf_status mf_grow_pin(sf_multiframe m, T** p, size_t& cap, size_t need) {
+    if (need <= cap) return SF_OK;
+    MF_CK(m, cudaStreamSynchronize(m->stream));  // no copy into the old buffer is in flight
+    const size_t nc = std::max<size_t>(need, 2 * cap);
+    if (*p) pinned_free(*p, cap);
+    *p = nullptr;
+    cap = 0;
+    if (pinned_alloc_n(p, nc) != cudaSuccess) return mf_fail(m, SF_ENOMEM, "pinned allocation failed");
+    cap = nc;
+    return SF_OK;
+}
+
 sf_status mf_new_frame(sf_multiframe m, sf_handle* out) {
     if (!m->spare.empty()) {
         *out = m->spare.back();
@@ -856,182 +902,274 @@ sf_status mf_new_frame(sf_multiframe m, sf_handle* out) {
 
 // the full tableau state of src (matrix, destabilizers, pivots, X-block size,
 // global phase) copied into dst; same stream
-sf_status mf_copy_tableau(sf_handle dst, sf_handle src) {
+sf_status mf_copy_tableau(sf_multiframe m, sf_handle dst, sf_handle src) {
     const size_t n = src->n, W = src->d.W;
-    cudaStream_t s = src->stream;
+    cudaStream_t s = m->stream;
     const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
-    SF_CK(dst, cudaMemcpyAsync(dst->d.mx, src->d.mx, W * n * sizeof(uint64_t), dd, s));
-    SF_CK(dst, cudaMemcpyAsync(dst->d.mz, src->d.mz, W * n * sizeof(uint64_t), dd, s));
-    SF_CK(dst, cudaMemcpyAsync(dst->d.dx, src->d.dx, W * n * sizeof(uint64_t), dd, s));
-    SF_CK(dst, cudaMemcpyAsync(dst->d.dz, src->d.dz, W * n * sizeof(uint64_t), dd, s));
-    SF_CK(dst, cudaMemcpyAsync(dst->d.de, src->d.de, n * sizeof(uint32_t), dd, s));
-    SF_CK(dst, cudaMemcpyAsync(dst->d.piv, src->d.piv, n * sizeof(int32_t), dd, s));
-    SF_CK(dst, cudaMemcpyAsync(dst->d.meta, src->d.meta, 4 * sizeof(int32_t), dd, s));
-    SF_CK(dst, cudaMemcpyAsync(dst->d.g, src->d.g, sizeof(double2), dd, s));
+    MF_CK(m, cudaMemcpyAsync(dst->d.mx, src->d.mx, W * n * sizeof(uint64_t), dd, s));
+    MF_CK(m, cudaMemcpyAsync(dst->d.mz, src->d.mz, W * n * sizeof(uint64_t), dd, s));
+    MF_CK(m, cudaMemcpyAsync(dst->d.dx, src->d.dx, W * n * sizeof(uint64_t), dd, s));
+    MF_CK(m, cudaMemcpyAsync(dst->d.dz, src->d.dz, W * n * sizeof(uint64_t), dd, s));
+    MF_CK(m, cudaMemcpyAsync(dst->d.de, src->d.de, n * sizeof(uint32_t), dd, s));
+    MF_CK(m, cudaMemcpyAsync(dst->d.piv, src->d.piv, n * sizeof(int32_t), dd, s));
+    MF_CK(m, cudaMemcpyAsync(dst->d.meta, src->d.meta, 4 * sizeof(int32_t), dd, s));
+    MF_CK(m, cudaMemcpyAsync(dst->d.g, src->d.g, sizeof(double2), dd, s));
     return SF_OK;
 }
 
-// unsigned rows of the matrix of h (one word each: x rows, then z rows)
-sf_status mf_matrix(sf_handle h, std::vector<uint64_t>& xz) {
-    const size_t n = h->n;
-    xz.resize(2 * n);
-    SF_CK(h, cudaMemcpyAsync(xz.data(), h->d.mx, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
-    SF_CK(h, cudaMemcpyAsync(xz.data() + n, h->d.mz, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
-    return sync_check(h);
+// Enqueue the status read of every frame of fs (with its size, and its matrix
+// into m->hmat when `matrices`), synchronise once, then report the first
+// device error through that frame's sync_check.  k[i]: size of fs[i].
+sf_status mf_read(sf_multiframe m, const std::vector<sf_handle>& fs, std::vector<uint64_t>& k, bool matrices) {
+    const size_t n = m->n;
+    if (matrices) {
+        sf_status st = mf_grow_pin(m, &m->hmat, m->hmat_cap, 2 * n * std::max<size_t>(fs.size(), 1));
+        if (st) return st;
+    }
+    const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+    for (size_t i = 0; i < fs.size(); i++) {
+        sf_handle F = fs[i];
+        MF_CK(m, cudaMemcpyAsync(F->hk, F->d.kcnt, 2 * sizeof(unsigned long long), d2h, m->stream));
+        MF_CK(m, cudaMemcpyAsync(F->hstatus, F->d.status, sizeof(uint32_t), d2h, m->stream));
+        if (matrices) {
+            MF_CK(m, cudaMemcpyAsync(m->hmat + 2 * n * i, F->d.mx, n * sizeof(uint64_t), d2h, m->stream));
+            MF_CK(m, cudaMemcpyAsync(m->hmat + 2 * n * i + n, F->d.mz, n * sizeof(uint64_t), d2h, m->stream));
+        }
+    }
+    MF_CK(m, cudaStreamSynchronize(m->stream));
+    k.resize(fs.size());
+    for (size_t i = 0; i < fs.size(); i++) {
+        if (*fs[i]->hstatus) MF_TRY(m, fs[i], sync_check(fs[i]));
+        k[i] = fs[i]->hk[fs[i]->cur];
+    }
+    return SF_OK;
 }
 
-// COALESCE(F): appends to `out` F with its unpaired elements (if any), then
-// one new frame per pair class (e, d) in ascending order; adds the pairs formed
-sf_status mf_coalesce_frame(sf_multiframe m, sf_handle F, std::vector<sf_handle>& out, uint64_t& pairs_formed) {
-    uint64_t k = 0;
-    MF_TRY(m, F, sf_size(F, &k));
-    if (k < 2) {
-        (k ? out : m->spare).push_back(F);
-        return SF_OK;
+// COFACTOR(F, q) of every frame (Sec. III), in two phases: the tableau update
+// and the random flag of every frame, one synchronisation, then the merged
+// split of the frames where q was random
+sf_status mf_cofactor_all(sf_multiframe m, uint32_t q) {
+    const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+    for (sf_handle F : m->frames) {
+        MF_TRY(m, F, launch(F, SF_K_MEASURE_PREP, "measure_prep",
+                            [&] { sf_launch_measure_prep(F->d, q, F->cur, F->gws, m->stream); }));
+        MF_CK(m, cudaMemcpyAsync(F->hmeta, F->d.meta, 4 * sizeof(int32_t), d2h, m->stream));
+        MF_CK(m, cudaMemcpyAsync(F->hstatus, F->d.status, sizeof(uint32_t), d2h, m->stream));
     }
-    if (k > SF_MF_MAXK) return mf_fail(m, SF_ECAPACITY, "COALESCE takes frames of at most 8192 elements");
-    cudaStream_t s = m->stream;
-    const int stage = F->cur ^ 1;
-    MF_TRY(m, F, launch(F, kMfKernelId, "export", [&] { sf_launch_export(F->d, F->cur, stage, s); }));
-    F->idx_ok[stage] = false;
-    MF_TRY(m, F, launch(F, kMfKernelId, "k_mf_pair", [&] {
-               sf_launch_mf_pair(F->d, F->cur, stage, k, kMfTol, m->dpairs, m->dkeep, m->dcounts, s);
-           }));
-    uint32_t cnt[2] = {0, 0};
-    SF_CK(F, cudaMemcpyAsync(cnt, m->dcounts, sizeof(cnt), cudaMemcpyDeviceToHost, s));
-    MF_TRY(m, F, sync_check(F));
-    const uint32_t np = cnt[0], nk = cnt[1];
-    if (2ull * np + nk != k) return mf_fail(m, SF_EINTERNAL, "COALESCE lost elements");
-    if (np == 0) {
-        out.push_back(F);
-        return SF_OK;
-    }
-    std::vector<MfPair> pairs(np);
-    std::vector<uint32_t> keep(nk);
-    std::vector<uint64_t> xz;
-    SF_CK(F, cudaMemcpyAsync(pairs.data(), m->dpairs, np * sizeof(MfPair), cudaMemcpyDeviceToHost, s));
-    if (nk) SF_CK(F, cudaMemcpyAsync(keep.data(), m->dkeep, nk * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    MF_TRY(m, F, mf_matrix(F, xz));
-    pairs_formed += np;
-    std::map<std::pair<uint64_t, uint32_t>, std::vector<uint32_t>> cls;
-    for (const MfPair& p : pairs) cls[{p.e, p.d}].push_back(p.owner);
-    // owners of each class, then the unpaired elements, as one index list
-    std::vector<uint32_t> idx;
-    idx.reserve(k);
-    for (const auto& c : cls) idx.insert(idx.end(), c.second.begin(), c.second.end());
-    idx.insert(idx.end(), keep.begin(), keep.end());
-    SF_CK(F, cudaMemcpyAsync(m->didx, idx.data(), idx.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
-    std::vector<sf_handle> made;
-    size_t off = 0;
-    sf_status st = SF_OK;
-    for (const auto& c : cls) {
-        sf_handle G = nullptr;
-        st = mf_new_frame(m, &G);
-        if (st) break;
-        made.push_back(G);
-        st = mf_copy_tableau(G, F);
-        if (st) break;
-        const uint32_t cntc = (uint32_t)c.second.size();
-        st = launch(G, kMfKernelId, "k_mf_gather", [&] {
-            sf_launch_mf_gather(G->d, G->cur, F->d.sig[F->cur], F->d.amp[F->cur], m->didx + off, cntc, std::sqrt(2.0), s);
-        });
-        if (st) {
-            mf_from(m, G, st);
-            break;
-        }
-        G->idx_ok[0] = G->idx_ok[1] = false;
-        off += cntc;
-        // the qubits v_1 < ... < v_m of the Z_k-rows in e
-        std::vector<uint32_t> V;
-        for (uint64_t e = c.first.first; e; e &= e - 1) {
-            const int r = __builtin_ctzll(e);
-            V.push_back((uint32_t)__builtin_ctzll(xz[m->n + r]));
-        }
-        std::sort(V.begin(), V.end());
-        std::vector<sf_gate> gates;
-        gates.push_back(sf_gate{SF_H, V[0], 0, 0});
-        for (uint32_t t = 0; t < c.first.second; t++) gates.push_back(sf_gate{SF_S, V[0], 0, 0});
-        for (size_t i = 1; i < V.size(); i++) gates.push_back(sf_gate{SF_CNOT, V[0], V[i], 0});
-        st = sf_apply_clifford(G, gates.data(), gates.size());
-        if (st) {
-            mf_from(m, G, st);
-            break;
-        }
-    }
-    if (!st && nk) {
-        st = launch(F, kMfKernelId, "k_mf_gather", [&] {
-            sf_launch_mf_gather(F->d, F->cur ^ 1, F->d.sig[F->cur], F->d.amp[F->cur], m->didx + off, nk, 1.0, s);
-        });
-        if (st) mf_from(m, F, st);
+    MF_CK(m, cudaStreamSynchronize(m->stream));
+    for (sf_handle F : m->frames) {
+        if (*F->hstatus) MF_TRY(m, F, sync_check(F));
+        if (!F->hmeta[2]) continue;
+        MF_TRY(m, F, need_index(F, F->cur));
+        MF_TRY(m, F, launch(F, SF_K_COFACTOR, "cof_merge",
+                            [&] { sf_launch_cof_merge(F->d, F->cur, F->cur ^ 1, m->stream); }));
         F->cur ^= 1;
-        F->idx_ok[0] = F->idx_ok[1] = false;
+        F->idx_ok[F->cur] = true;
     }
-    // every handle stays reachable (list or spare), also after an error
-    (nk ? out : m->spare).push_back(F);
-    out.insert(out.end(), made.begin(), made.end());
-    cudaError_t e = cudaStreamSynchronize(s);  // idx is read by the copy above
-    if (st) return st;
-    if (e != cudaSuccess) return mf_fail(m, SF_ECUDA, std::string("COALESCE: ") + cudaGetErrorString(e));
+    return SF_OK;
+}
+
+// Def. 1 coalescing of every frame (asynchronous)
+sf_status mf_coalesce_frames(sf_multiframe m, double eps) {
+    for (sf_handle F : m->frames) {
+        MF_TRY(m, F, merge_seq(F, eps, F->cur, F->cur ^ 1));
+        F->cur ^= 1;
+    }
     return SF_OK;
 }
 
 // A16: frames with equal matrices merged into the first of them (union, then
-// Def. 1 coalescing with drop_eps); empty frames leave the list
+// Def. 1 coalescing with eps); empty frames leave the list
 sf_status mf_merge(sf_multiframe m, double eps) {
-    std::vector<std::vector<uint64_t>> keys(m->frames.size());
-    for (size_t i = 0; i < m->frames.size(); i++) MF_TRY(m, m->frames[i], mf_matrix(m->frames[i], keys[i]));
+    std::vector<uint64_t> k;
+    sf_status st = mf_read(m, m->frames, k, true);
+    if (st) return st;
+    const size_t n = m->n;
     std::map<std::vector<uint64_t>, size_t> first;
-    std::vector<std::vector<sf_handle>> groups;
+    std::vector<std::vector<size_t>> groups;
     for (size_t i = 0; i < m->frames.size(); i++) {
-        auto it = first.find(keys[i]);
+        std::vector<uint64_t> key(m->hmat + 2 * n * i, m->hmat + 2 * n * (i + 1));
+        auto it = first.find(key);
         if (it == first.end()) {
-            first.emplace(keys[i], groups.size());
-            groups.push_back({m->frames[i]});
+            first.emplace(std::move(key), groups.size());
+            groups.push_back({i});
         } else {
-            groups[it->second].push_back(m->frames[i]);
+            groups[it->second].push_back(i);
         }
     }
-    std::vector<sf_handle> out;
-    sf_status st = SF_OK;
-    for (auto& g : groups) {
-        if (st) {  // after an error: keep the rest reachable, unmerged
-            out.insert(out.end(), g.begin(), g.end());
+    std::vector<sf_handle> out, merged;
+    for (const auto& g : groups) {
+        sf_handle dst = m->frames[g[0]];
+        if (g.size() == 1) {
+            (k[g[0]] ? out : m->spare).push_back(dst);
             continue;
         }
-        sf_handle dst = g[0];
-        uint64_t kd = 0;
-        st = mf_from(m, dst, sf_size(dst, &kd));
-        for (size_t i = 1; i < g.size() && !st; i++) {
-            sf_handle src = g[i];
-            uint64_t ks = 0;
-            st = mf_from(m, src, sf_size(src, &ks));
-            if (st) break;
-            if (kd + ks > m->max_elems) {
-                st = mf_fail(m, SF_ECAPACITY, "merged frame would exceed max_elems");
-                break;
-            }
-            if (ks) {
+        uint64_t kd = k[g[0]];
+        for (size_t i = 1; i < g.size(); i++) {
+            sf_handle src = m->frames[g[i]];
+            const uint64_t ks = k[g[i]];
+            if (!st && kd + ks > m->max_elems) st = mf_fail(m, SF_ECAPACITY, "merged frame would exceed max_elems");
+            if (!st && ks) {
                 const int stage = src->cur ^ 1;
                 st = mf_from(m, src, launch(src, kMfKernelId, "export",
                                             [&] { sf_launch_export(src->d, src->cur, stage, m->stream); }));
                 src->idx_ok[stage] = false;
-                if (st) break;
                 const uint64_t off = kd;
-                st = mf_from(m, dst, launch(dst, kMfKernelId, "k_mf_import", [&] {
-                                 sf_launch_mf_import(dst->d, dst->cur, off, src->d.sig[stage], src->d.amp[stage],
-                                                     (uint32_t)ks, m->stream);
-                             }));
+                if (!st)
+                    st = mf_from(m, dst, launch(dst, kMfKernelId, "k_mf_import", [&] {
+                                     sf_launch_mf_import(dst->d, dst->cur, off, src->d.sig[stage], src->d.amp[stage],
+                                                         (uint32_t)ks, m->stream);
+                                 }));
                 dst->idx_ok[0] = dst->idx_ok[1] = false;
                 kd += ks;
             }
-            m->spare.push_back(src);
-            g[i] = nullptr;
+            if (st) out.push_back(src);  // after an error every handle stays reachable
+            else m->spare.push_back(src);
         }
-        if (!st && g.size() > 1) st = mf_from(m, dst, sf_coalesce(dst, eps, &kd));
-        if (!st && kd == 0) m->spare.push_back(dst);
-        else out.push_back(dst);
-        for (size_t i = 1; i < g.size(); i++)
-            if (g[i]) out.push_back(g[i]);
+        if (!st) {
+            st = mf_from(m, dst, merge_seq(dst, eps, dst->cur, dst->cur ^ 1));
+            dst->cur ^= 1;
+        }
+        out.push_back(dst);
+        merged.push_back(dst);
+    }
+    m->frames.swap(out);
+    if (st || merged.empty()) return st;
+    // frames emptied by the drop threshold leave the list
+    st = mf_read(m, merged, k, false);
+    if (st) return st;
+    std::vector<sf_handle> kept;
+    for (sf_handle F : m->frames) {
+        const auto it = std::find(merged.begin(), merged.end(), F);
+        if (it != merged.end() && k[it - merged.begin()] == 0) m->spare.push_back(F);
+        else kept.push_back(F);
+    }
+    m->frames.swap(kept);
+    return SF_OK;
+}
+
+// One round of COALESCE over every frame; `formed`: the pairs found
+sf_status mf_coalesce_round(sf_multiframe m, uint64_t& formed) {
+    formed = 0;
+    std::vector<uint64_t> k;
+    sf_status st = mf_read(m, m->frames, k, true);
+    if (st) return st;
+    const size_t nf = m->frames.size(), n = m->n;
+    std::vector<size_t> part, off(nf, 0);
+    size_t total = 0;
+    for (size_t i = 0; i < nf; i++) {
+        if (k[i] < 2) continue;
+        if (k[i] > SF_MF_MAXK) return mf_fail(m, SF_ECAPACITY, "COALESCE takes frames of at most 8192 elements");
+        part.push_back(i);
+        off[i] = total;
+        total += k[i];
+    }
+    if (part.empty()) return SF_OK;
+    if ((st = mf_grow_dev(m, &m->dpairs, m->dpairs_cap, total)) || (st = mf_grow_dev(m, &m->dkeep, m->dkeep_cap, total)) ||
+        (st = mf_grow_dev(m, &m->dcounts, m->dcounts_cap, 2 * part.size())) ||
+        (st = mf_grow_dev(m, &m->didx, m->didx_cap, total)) ||
+        (st = mf_grow_pin(m, &m->hpairs, m->hpairs_cap, total)) || (st = mf_grow_pin(m, &m->hkeep, m->hkeep_cap, total)) ||
+        (st = mf_grow_pin(m, &m->hcounts, m->hcounts_cap, 2 * part.size())) ||
+        (st = mf_grow_pin(m, &m->hidx, m->hidx_cap, total)))
+        return st;
+    // phase 1: export and pairing of every frame of two or more elements
+    for (size_t j = 0; j < part.size(); j++) {
+        sf_handle F = m->frames[part[j]];
+        const int stage = F->cur ^ 1;
+        const uint64_t kk = k[part[j]], o = off[part[j]];
+        MF_TRY(m, F, launch(F, kMfKernelId, "export", [&] { sf_launch_export(F->d, F->cur, stage, m->stream); }));
+        F->idx_ok[stage] = false;
+        MF_TRY(m, F, launch(F, kMfKernelId, "k_mf_pair", [&] {
+                   sf_launch_mf_pair(F->d, F->cur, stage, kk, kMfTol, m->dpairs + o, m->dkeep + o, m->dcounts + 2 * j,
+                                     m->stream);
+               }));
+    }
+    MF_CK(m, cudaMemcpyAsync(m->hcounts, m->dcounts, 2 * part.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                             m->stream));
+    std::vector<sf_handle> chk;
+    for (size_t i : part) chk.push_back(m->frames[i]);
+    if ((st = mf_read(m, chk, k, false))) return st;  // statuses of the pairing; sizes unchanged
+    // phase 2: the pairs and unpaired elements of the frames that formed pairs
+    std::vector<size_t> paired;
+    for (size_t j = 0; j < part.size(); j++) {
+        const uint32_t np = m->hcounts[2 * j], nk = m->hcounts[2 * j + 1];
+        if (2ull * np + nk != k[j]) return mf_fail(m, SF_EINTERNAL, "COALESCE lost elements");
+        if (!np) continue;
+        formed += np;
+        paired.push_back(j);
+        const uint64_t o = off[part[j]];
+        MF_CK(m, cudaMemcpyAsync(m->hpairs + o, m->dpairs + o, np * sizeof(MfPair), cudaMemcpyDeviceToHost, m->stream));
+        if (nk)
+            MF_CK(m, cudaMemcpyAsync(m->hkeep + o, m->dkeep + o, nk * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                     m->stream));
+    }
+    if (paired.empty()) return SF_OK;
+    MF_CK(m, cudaStreamSynchronize(m->stream));
+    // per frame: owners of each class (e, d) in ascending order, then the unpaired
+    std::vector<std::map<std::pair<uint64_t, uint32_t>, std::vector<uint32_t>>> cls(paired.size());
+    for (size_t pi = 0; pi < paired.size(); pi++) {
+        const size_t j = paired[pi];
+        const uint64_t o = off[part[j]];
+        const uint32_t np = m->hcounts[2 * j], nk = m->hcounts[2 * j + 1];
+        for (uint32_t t = 0; t < np; t++) cls[pi][{m->hpairs[o + t].e, m->hpairs[o + t].d}].push_back(m->hpairs[o + t].owner);
+        uint64_t w = o;
+        for (const auto& c : cls[pi])
+            for (uint32_t x : c.second) m->hidx[w++] = x;
+        for (uint32_t t = 0; t < nk; t++) m->hidx[w++] = m->hkeep[o + t];
+    }
+    MF_CK(m, cudaMemcpyAsync(m->didx, m->hidx, total * sizeof(uint32_t), cudaMemcpyHostToDevice, m->stream));
+    // phase 3: new frames from the classes, unpaired elements kept in place
+    std::vector<std::vector<sf_handle>> made(nf);
+    std::vector<char> gone(nf, 0);
+    for (size_t pi = 0; pi < paired.size() && !st; pi++) {
+        const size_t j = paired[pi], fi = part[j];
+        sf_handle F = m->frames[fi];
+        const uint64_t o = off[fi];
+        const uint32_t nk = m->hcounts[2 * j + 1];
+        const uint64_t* mz = m->hmat + 2 * n * fi + n;
+        uint64_t pos = o;
+        for (const auto& c : cls[pi]) {
+            sf_handle G = nullptr;
+            if ((st = mf_new_frame(m, &G))) break;
+            made[fi].push_back(G);
+            if ((st = mf_copy_tableau(m, G, F))) break;
+            const uint32_t cnt = (uint32_t)c.second.size();
+            const uint32_t* ix = m->didx + pos;
+            st = mf_from(m, G, launch(G, kMfKernelId, "k_mf_gather", [&] {
+                             sf_launch_mf_gather(G->d, G->cur, F->d.sig[F->cur], F->d.amp[F->cur], ix, cnt,
+                                                 std::sqrt(2.0), m->stream);
+                         }));
+            if (st) break;
+            G->idx_ok[0] = G->idx_ok[1] = false;
+            pos += cnt;
+            // the qubits v_1 < ... < v_m of the Z_k-rows in e
+            std::vector<uint32_t> V;
+            for (uint64_t e = c.first.first; e; e &= e - 1) V.push_back((uint32_t)__builtin_ctzll(mz[__builtin_ctzll(e)]));
+            std::sort(V.begin(), V.end());
+            std::vector<sf_gate> gates;
+            gates.push_back(sf_gate{SF_H, V[0], 0, 0});
+            for (uint32_t t = 0; t < c.first.second; t++) gates.push_back(sf_gate{SF_S, V[0], 0, 0});
+            for (size_t i = 1; i < V.size(); i++) gates.push_back(sf_gate{SF_CNOT, V[0], V[i], 0});
+            if ((st = mf_from(m, G, sf_apply_clifford(G, gates.data(), gates.size())))) break;
+        }
+        if (st) break;
+        if (nk) {
+            const uint32_t* ix = m->didx + pos;
+            st = mf_from(m, F, launch(F, kMfKernelId, "k_mf_gather", [&] {
+                             sf_launch_mf_gather(F->d, F->cur ^ 1, F->d.sig[F->cur], F->d.amp[F->cur], ix, nk, 1.0,
+                                                 m->stream);
+                         }));
+            F->cur ^= 1;
+            F->idx_ok[0] = F->idx_ok[1] = false;
+        } else {
+            gone[fi] = 1;
+        }
+    }
+    // the list in order: each frame (unless all its elements paired), then its new frames
+    std::vector<sf_handle> out;
+    for (size_t i = 0; i < nf; i++) {
+        (gone[i] && !st ? m->spare : out).push_back(m->frames[i]);
+        out.insert(out.end(), made[i].begin(), made[i].end());
     }
     m->frames.swap(out);
     return st;
@@ -1040,19 +1178,24 @@ sf_status mf_merge(sf_multiframe m, double eps) {
 // merge, then COALESCE every frame and merge again until no pair forms
 sf_status mf_coalesce_all(sf_multiframe m, double eps) {
     sf_status st = mf_merge(m, eps);
-    if (st) return st;
-    for (int iter = 0;; iter++) {
+    for (int iter = 0; !st; iter++) {
         if (iter > (1 << 20)) return mf_fail(m, SF_EINTERNAL, "multiframe coalescing did not terminate");
-        std::vector<sf_handle> next;
         uint64_t formed = 0;
-        size_t i = 0;
-        for (; i < m->frames.size() && !st; i++) st = mf_coalesce_frame(m, m->frames[i], next, formed);
-        next.insert(next.end(), m->frames.begin() + i, m->frames.end());
-        m->frames.swap(next);
-        if (st) return st;
+        st = mf_coalesce_round(m, formed);
+        if (st || formed == 0) break;
         st = mf_merge(m, eps);
-        if (st || formed == 0) return st;
     }
+    return st;
+}
+
+sf_status mf_check_qubits(sf_multiframe m, std::initializer_list<uint32_t> qs) {
+    std::vector<uint32_t> v(qs);
+    for (size_t i = 0; i < v.size(); i++) {
+        if (v[i] >= m->n) return mf_fail(m, SF_EINVAL, "qubit out of range");
+        for (size_t j = 0; j < i; j++)
+            if (v[i] == v[j]) return mf_fail(m, SF_EINVAL, "repeated qubit");
+    }
+    return SF_OK;
 }
 
 }  // namespace
@@ -1079,15 +1222,6 @@ sf_status sf_mf_create(uint32_t n_qubits, uint64_t max_elems, uint32_t max_frame
         return mf_fail(nullptr, st, msg);
     }
     m->frames.push_back(F);
-    cudaError_t e = cudaMallocAsync(&m->dpairs, SF_MF_MAXK / 2 * sizeof(MfPair), m->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&m->dkeep, SF_MF_MAXK * sizeof(uint32_t), m->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&m->didx, SF_MF_MAXK * sizeof(uint32_t), m->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&m->dcounts, 2 * sizeof(uint32_t), m->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-    if (e != cudaSuccess) {
-        sf_mf_destroy(m);
-        return mf_fail(nullptr, SF_ENOMEM, "multiframe scratch allocation failed");
-    }
     *out = m;
     return SF_OK;
 }
@@ -1095,9 +1229,14 @@ sf_status sf_mf_create(uint32_t n_qubits, uint64_t max_elems, uint32_t max_frame
 sf_status sf_mf_destroy(sf_multiframe m) {
     if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
     for (sf_handle h : m->all) sf_destroy(h);
-    for (void* p : {(void*)m->dpairs, (void*)m->dkeep, (void*)m->didx, (void*)m->dcounts})
+    for (void* p : {(void*)m->dpairs, (void*)m->dkeep, (void*)m->dcounts, (void*)m->didx})
         if (p) cudaFreeAsync(p, m->stream);
     cudaStreamSynchronize(m->stream);
+    pinned_free(m->hpairs, m->hpairs_cap);
+    pinned_free(m->hkeep, m->hkeep_cap);
+    pinned_free(m->hcounts, m->hcounts_cap);
+    pinned_free(m->hidx, m->hidx_cap);
+    pinned_free(m->hmat, m->hmat_cap);
     delete m;
     return SF_OK;
 }
@@ -1111,47 +1250,56 @@ sf_status sf_mf_apply_clifford(sf_multiframe m, const sf_gate* gates, uint64_t n
 sf_status sf_mf_apply_nonclifford(sf_multiframe m, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
                                   double drop_eps) {
     if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    for (sf_handle F : m->frames)
+        MF_TRY(m, F, sf_apply_nonclifford_coalesce(F, kind, q0, q1, theta, drop_eps));
+    std::vector<uint64_t> k;
+    sf_status st = mf_read(m, m->frames, k, false);
+    if (st) return st;
     std::vector<sf_handle> kept;
-    sf_status st = SF_OK;
-    for (size_t i = 0; i < m->frames.size(); i++) {
-        sf_handle F = m->frames[i];
-        uint64_t k = 1;
-        if (!st) st = mf_from(m, F, sf_apply_nonclifford_coalesce(F, kind, q0, q1, theta, drop_eps));
-        if (!st) st = mf_from(m, F, sf_size(F, &k));
-        (k || st ? kept : m->spare).push_back(F);
-    }
+    for (size_t i = 0; i < m->frames.size(); i++) (k[i] ? kept : m->spare).push_back(m->frames[i]);
     m->frames.swap(kept);
-    return st;
+    return SF_OK;
 }
 
 sf_status sf_mf_apply_toffoli(sf_multiframe m, uint32_t c1, uint32_t c2, uint32_t t, double drop_eps) {
     if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
     if (!(drop_eps >= 0.0)) return mf_fail(m, SF_EINVAL, "drop_eps must be >= 0");
+    sf_status st = mf_check_qubits(m, {c1, c2, t});
+    if (!st) st = mf_cofactor_all(m, c1);
+    if (!st) st = mf_cofactor_all(m, c2);
+    if (st) return st;
     for (sf_handle F : m->frames) {
-        MF_TRY(m, F, sf_apply_toffoli(F, c1, c2, t));
-        MF_TRY(m, F, sf_coalesce(F, drop_eps, nullptr));
+        MF_TRY(m, F, launch(F, SF_K_COND, "cond", [&] {
+                   sf_launch_cond(F->d, F->cur, 0, (int)c1, (int)c2, (int)t, 0.0, m->stream);
+               }));
+        F->idx_ok[F->cur] = false;  // phase vectors changed
     }
+    if ((st = mf_coalesce_frames(m, drop_eps))) return st;
     return mf_coalesce_all(m, drop_eps);
 }
 
 sf_status sf_mf_apply_cr(sf_multiframe m, uint32_t c, uint32_t t, double alpha, double drop_eps) {
     if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
     if (!(drop_eps >= 0.0)) return mf_fail(m, SF_EINVAL, "drop_eps must be >= 0");
-    for (sf_handle F : m->frames) {
-        MF_TRY(m, F, sf_apply_cr_cofactor(F, c, t, alpha));
-        MF_TRY(m, F, sf_coalesce(F, drop_eps, nullptr));
-    }
+    sf_status st = mf_check_qubits(m, {c, t});
+    if (!st) st = mf_cofactor_all(m, c);
+    if (!st) st = mf_cofactor_all(m, t);
+    if (st) return st;
+    for (sf_handle F : m->frames)
+        MF_TRY(m, F, launch(F, SF_K_COND, "cond", [&] {
+                   sf_launch_cond(F->d, F->cur, 1, (int)c, (int)t, 0, alpha, m->stream);
+               }));
+    if ((st = mf_coalesce_frames(m, drop_eps))) return st;
     return mf_coalesce_all(m, drop_eps);
 }
 
 sf_status sf_mf_count(sf_multiframe m, uint32_t* n_frames, uint64_t* n_states) {
     if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
+    std::vector<uint64_t> k;
+    sf_status st = mf_read(m, m->frames, k, false);
+    if (st) return st;
     uint64_t tot = 0;
-    for (sf_handle F : m->frames) {
-        uint64_t k = 0;
-        MF_TRY(m, F, sf_size(F, &k));
-        tot += k;
-    }
+    for (uint64_t v : k) tot += v;
     if (n_frames) *n_frames = (uint32_t)m->frames.size();
     if (n_states) *n_states = tot;
     return SF_OK;
@@ -1165,15 +1313,26 @@ sf_status sf_mf_coalesce(sf_multiframe m, double drop_eps, uint32_t* n_frames, u
     return sf_mf_count(m, n_frames, n_states);
 }
 
+// <x|Psi>: the amplitude kernels of every frame, one synchronisation, the sum
 sf_status sf_mf_amplitude(sf_multiframe m, const uint64_t* x_bits, double* re, double* im) {
     if (!m) return mf_fail(nullptr, SF_EINVAL, "NULL multiframe");
     if (!x_bits || !re || !im) return mf_fail(m, SF_EINVAL, "NULL argument");
+    const uint64_t x = m->n == 64 ? x_bits[0] : x_bits[0] & ((1ull << m->n) - 1ull);
+    for (sf_handle F : m->frames) {
+        F->hy[0] = x;
+        MF_CK(m, cudaMemcpyAsync(F->dy, F->hy, sizeof(uint64_t), cudaMemcpyHostToDevice, m->stream));
+        MF_TRY(m, F, launch(F, SF_K_AMP_PREP, "amp_prep", [&] { sf_launch_amp_prep(F->d, F->dy, m->stream); }));
+        MF_TRY(m, F, launch(F, SF_K_AMPLITUDE, "amplitude", [&] { sf_launch_amplitude(F->d, F->cur, m->stream); }));
+        MF_TRY(m, F, launch(F, SF_K_REDUCE, "reduce", [&] { sf_launch_reduce_final(F->d, 1, m->stream); }));
+        MF_CK(m, cudaMemcpyAsync(F->hout, F->d.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    }
+    std::vector<uint64_t> k;
+    sf_status st = mf_read(m, m->frames, k, false);  // synchronises, reports device errors
+    if (st) return st;
     double sr = 0.0, si = 0.0;
     for (sf_handle F : m->frames) {
-        double a = 0.0, b = 0.0;
-        MF_TRY(m, F, sf_amplitude(F, x_bits, &a, &b));
-        sr += a;
-        si += b;
+        sr += F->hout[2];
+        si += F->hout[3];
     }
     *re = sr;
     *im = si;

@@ -143,7 +143,7 @@ def test_errors(sfm):
         g.apply_toffoli_cofactor(0, 1, 2)
     assert e.value.code == sfm.SF_ECAPACITY
     g.close()
-    # bad Toffoli qubits are reported by the frame and the multiframe stays usable
+    # bad Toffoli qubits are rejected and the multiframe stays usable
     g = sfm.MultiFrame(4, 64, 8)
     with pytest.raises(sfm.SFError) as e:
         g.apply_toffoli_cofactor(0, 0, 2)
