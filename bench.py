@@ -21,7 +21,9 @@ Steane fault-injection campaign (4096 variants in one persistent launch, shape
 picked by the library's autotuner) against the one-circuit path, and
 "served", a seeded Poisson stream of random Clifford+T circuits through the
 continuous-batching server against the same stream one at a time, with
-p50/p99 latency.
+p50/p99 latency.  "multiframe": the Cuccaro adder on the equal superposition
+(Toffolis by cofactors) as one frame and as a multiframe (Sec. IV), with the
+largest amplitude difference between the two on sampled basis states.
 
 Multi-GPU: one process per GPU (torchrun), each rank simulates its own QFT
 instance (different seed); no data-path collective ("weak" scaling).
@@ -553,6 +555,49 @@ def serving_leg(sfm, n_requests: int, rate_hz: float, slots: int, budget_gb: int
             "results_same_alone_and_mixed": same, "max_amp_diff_alone_vs_mixed": diff}
 
 
+# Multiframes (Sec. IV): the same adder state as one frame and as a list of
+# frames built by COALESCE and the merge of equal matrices.
+def multiframe_leg(sfm, nb: int = 6, reps: int = 3):
+    try:
+        ops = c.cuccaro(nb, True, toffoli="cofactor", coalesce=False)
+        n = 2 * nb + 2
+        f = sfm.Frame(n, 1 << min(2 * nb + 2, 24))
+        ts = []
+        for _ in range(reps + 1):
+            f.reset()
+            f.sync()
+            t0 = time.perf_counter()
+            c.run(f, ops)
+            f.sync()
+            ts.append(time.perf_counter() - t0)
+        frame_ms = statistics.median(ts[1:]) * 1e3
+        ts, mf = [], None
+        for _ in range(reps + 1):
+            if mf is not None:
+                mf.close()
+            mf = sfm.MultiFrame(n, 4096, 8192)
+            mf.count()
+            t0 = time.perf_counter()
+            c.run(mf, ops)
+            frames, states = mf.count()
+            ts.append(time.perf_counter() - t0)
+        mf_ms = statistics.median(ts[1:]) * 1e3
+        ys = [int(y) for y in c.rng_for(7).integers(1 << n, size=8)]
+        diff = max(abs(mf.amplitude(y) - f.amplitude(y)) for y in ys)
+        out = {"workload": f"Cuccaro adder, {nb}-bit, equal superposition of both inputs, Toffolis by cofactors "
+                           f"(Eq. 2), {n} qubits",
+               "single_frame": {"states": f.size(), "ms": frame_ms},
+               "multiframe": {"frames": frames, "states": states, "ms": mf_ms},
+               "state_ratio": f.size() / max(states, 1), "time_ratio": mf_ms / frame_ms,
+               "max_amp_diff_single_vs_multi": diff, "same_state": diff <= 1e-10,
+               "timing": f"wall time of the whole circuit, median of {reps} after one warm-up"}
+        mf.close()
+        f.close()
+        return out
+    except Exception as e:  # the headline line must not depend on this leg
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -569,6 +614,7 @@ def main():
     ap.add_argument("--no-campaign", action="store_true", help="skip the batched-campaign leg")
     ap.add_argument("--campaign-variants", type=int, default=4096)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-multiframe", action="store_true", help="skip the multiframe leg")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--serving-rate", type=float, default=8.0)
     ap.add_argument("--serving-slots", type=int, default=32)
@@ -910,6 +956,7 @@ def main():
     batched = None if args.no_campaign else campaign_leg(sf, torch, args.campaign_variants)
     served = None if args.no_serving else serving_leg(sf, args.serving_requests, args.serving_rate,
                                                       args.serving_slots)
+    multiframe = None if args.no_multiframe else multiframe_leg(sf)
 
     out = {
         "impl": "gb300", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -934,6 +981,7 @@ def main():
         "gpu_launches": int(launches_total),
         "batched": batched,
         "served": served,
+        "multiframe": multiframe,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:
