@@ -11,10 +11,13 @@ no code with the CUDA library.
                   of diagonal non-Clifford gates, COFACTOR for measurement.
   DenseOracle  -- numpy state vector (the "array of complex amplitudes"
                   check the paper uses in Sec. VI), n <= 22.
+  multiframe   -- MultiFrameOracle: lists of FrameOracle frames, COALESCE into
+                  new frames and the merge of equal matrices (Sec. IV).
 
-Pins (tests/test_oracle_*.py) tie both to Tables 1 and 2, the paper's worked
-examples (Ex. 1, Ex. 2, the P|1> = i|1> example of Sec. II-B), closed forms
-(QFT, GHZ, Cuccaro addition) and brute force over every phase vector at n <= 6.
+Pins (tests/test_oracle_*.py) tie them to Tables 1 and 2, the paper's worked
+examples (Ex. 1, Ex. 2, the P|1> = i|1> example of Sec. II-B, the COALESCE
+example of Sec. IV), closed forms (QFT, GHZ, Cuccaro addition) and brute force
+over every phase vector at n <= 6.
 """
 from __future__ import annotations
 
