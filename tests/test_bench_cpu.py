@@ -41,6 +41,8 @@ def test_hash_ignores_unrelated_sources(tree):
 
 def test_traffic_is_null_once_the_kernel_changed(tree):
     t = json.loads((tree / "profiles" / "traffic.json").read_text())
+    t["sources"] = {cls: bench.kernel_sources_hash(cls) for cls in t["bytes_per_launch"]}
+    (tree / "profiles" / "traffic.json").write_text(json.dumps(t))
     for cls, v in t["bytes_per_launch"].items():
         assert bench.ncu_traffic(cls) == float(v), cls
     frame = tree / "paper_1712_03554_gb300" / "csrc" / "sf_frame.cu"
