@@ -25,7 +25,9 @@
  *
  * Errors are sf_status codes; no call throws.  A failed call leaves the
  * multiframe in an unspecified but destroyable state.  Calls synchronise the
- * stream unless stated otherwise.  Not thread-safe per multiframe.
+ * stream unless stated otherwise; an operation over all frames enqueues every
+ * frame's work and synchronises once per phase.  Not thread-safe per
+ * multiframe.
  */
 #ifndef SF_MULTIFRAME_H
 #define SF_MULTIFRAME_H
@@ -47,12 +49,14 @@ sf_status sf_mf_create(uint32_t n_qubits, uint64_t max_elems, uint32_t max_frame
                        sf_multiframe* out);
 sf_status sf_mf_destroy(sf_multiframe m);
 
-/* Clifford gates on every frame (host array, sf_apply_clifford per frame). */
+/* Clifford gates on every frame (host array, sf_apply_clifford per frame).
+ * Asynchronous; an invalid gate fails with SF_EINVAL before any frame changes
+ * only if it is invalid for the first frame (all frames share n). */
 sf_status sf_mf_apply_clifford(sf_multiframe m, const sf_gate* gates, uint64_t n_gates);
 
 /* A diagonal non-Clifford gate (sf_nonclifford_kind) branched and coalesced
- * (Def. 1) in every frame; frames left empty are dropped.  No multiframe
- * coalescing. */
+ * (Def. 1) in every frame; frames left empty are dropped (one
+ * synchronisation).  No multiframe coalescing. */
 sf_status sf_mf_apply_nonclifford(sf_multiframe m, uint32_t kind, uint32_t q0, uint32_t q1, double theta,
                                   double drop_eps);
 
