@@ -50,8 +50,8 @@ sf_status sf_mf_create(uint32_t n_qubits, uint64_t max_elems, uint32_t max_frame
 sf_status sf_mf_destroy(sf_multiframe m);
 
 /* Clifford gates on every frame (host array, sf_apply_clifford per frame).
- * Asynchronous; an invalid gate fails with SF_EINVAL before any frame changes
- * only if it is invalid for the first frame (all frames share n). */
+ * Asynchronous.  An invalid gate fails with SF_EINVAL before any frame
+ * changes: every frame has the same n, so the first frame rejects it. */
 sf_status sf_mf_apply_clifford(sf_multiframe m, const sf_gate* gates, uint64_t n_gates);
 
 /* A diagonal non-Clifford gate (sf_nonclifford_kind) branched and coalesced
