@@ -182,3 +182,22 @@ def test_planted_mistakes_are_caught(monkeypatch):
     mf = build()
     mf.coalesce()
     assert not ok(mf)
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_one_coalesce_halves_a_fully_paired_frame(n):
+    """Sec. IV: the multiframe COALESCE generates holds half the phase vectors
+    of its input when every element has a candidate partner.  H on every
+    qubit, P(pi/2) branched on each, H again: one frame of 2^n elements over
+    Z_k-rows only, with amplitude ratios that are powers of i."""
+    mf = mfo.MultiFrameOracle(n)
+    mf.apply_clifford([(c.H, q, 0) for q in range(n)])
+    for q in range(n):
+        mf.apply_nonclifford_coalesce(c.PHASE, q, 0, math.pi / 2)
+    mf.apply_clifford([(c.H, q, 0) for q in range(n)])
+    (F,) = mf.frames
+    x, z, _ = F.tableau()
+    assert len(mfo.zk_rows(x, z)) == n and F.size() == 1 << n
+    out, pairs = mfo.coalesce_frame(F)
+    assert pairs == 1 << (n - 1)
+    assert sum(G.size() for G in out) == 1 << (n - 1)
