@@ -214,19 +214,25 @@ sf_status sf_get_internal(sf_handle h, uint64_t* dx, uint64_t* dz, uint32_t* de,
 #define SF_COALESCE_NOALLOC_MAX_ELEMS 65536u
 
 /* Coalescing of caller-owned device buffers that allocates nothing.  The paper
- * has no counterpart: it is an addition for callers that cannot allocate
- * device memory where they merge a frame -- code running while its stream is
- * captured into a CUDA graph (cudaMalloc is not allowed there), frameworks
- * whose device memory belongs to their own caching pool, and serving loops
- * that plan all memory up front.
+ * has no counterpart: it is an addition for callers that must not allocate
+ * device memory where they merge a frame -- frameworks whose device memory
+ * belongs to their own caching pool (little is free outside it, so an extra
+ * cudaMalloc may fail, and cudaMalloc/cudaFree may synchronise the device),
+ * and serving loops that budget all device memory up front and must not fail
+ * half way through a request on an allocation.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.
  *
  * sigma_in: k_in phase vectors of n_words (1..16) 64-bit words each,
  * row-major (element j at [j*n_words, j*n_words+n_words)); amp_in: k_in FP64
  * complex amplitudes (re, im).  Both are device pointers.  Elements with equal
  * phase vectors are merged by summing their amplitudes, and merged elements
- * with |a| < drop_eps are dropped.  The survivors are written to sigma_out /
- * amp_out (device, same layouts, room for k_in elements) in the order of their
- * first occurrence, and their number to *k_out (host).
+ * with |a| < drop_eps are dropped.  Each group is represented by its first
+ * element (the smallest input index); the survivors are written to sigma_out /
+ * amp_out (device, same layouts, room for k_in elements) in input order, and
+ * their number to *k_out (host).  A group's amplitudes are summed with device
+ * atomics in an order that depends on scheduling, so two calls on the same
+ * input can differ in the last bits of a merged amplitude (far below 1e-10
+ * for unit-norm frames).
  *
  * Limits and behaviour: k_in must not exceed SF_COALESCE_NOALLOC_MAX_ELEMS
  * (SF_EINVAL otherwise).  The hash table and accumulators are one fixed
@@ -234,9 +240,10 @@ sf_status sf_get_internal(sf_handle h, uint64_t* dx, uint64_t* dz, uint32_t* de,
  * until the process exits; it is shared by all calls on a device and is
  * cleared by each call before use, so calls whose work overlaps on the GPU
  * (different streams or host threads) race and must be ordered by the caller.
- * The first call on each device looks up the array's device address; make that
- * first call before any stream capture.  Runs on cuda_stream (a cudaStream_t)
- * and synchronises it. */
+ * The first call on each device looks up the array's device address (with that
+ * device current) and keeps it; after cudaDeviceReset on that device the
+ * entry point must not be called again.  Runs on cuda_stream (a cudaStream_t)
+ * and synchronises it to read the output count. */
 sf_status sf_coalesce_noalloc(const uint64_t* sigma_in, const double* amp_in, uint64_t k_in, uint32_t n_words,
                               double drop_eps, uint64_t* sigma_out, double* amp_out, uint64_t* k_out,
                               void* cuda_stream);

@@ -9,6 +9,8 @@ no code with the CUDA library.
                   Gauss-Jordan RREF after every gate (Invariant 1), the
                   five-step global-phase rule of Sec. III per element, branching
                   of diagonal non-Clifford gates, COFACTOR for measurement.
+                  set_threads(t) splits its per-element loops into t ranges
+                  run by t threads (Sec. V); the default is sequential.
   DenseOracle  -- numpy state vector (the "array of complex amplitudes"
                   check the paper uses in Sec. VI), n <= 22.
   multiframe   -- MultiFrameOracle: lists of FrameOracle frames, COALESCE into
@@ -42,7 +44,8 @@ def build(force: bool = False) -> str:
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm",
+                                   "-lpthread"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -70,6 +73,8 @@ def _load():
         lib.of_set_state.argtypes = [vp, u64p, u64p, u64p, dp, C.c_size_t]
         lib.of_basis_amp.argtypes = [vp, u64p, u64p, dp, dp]
         lib.of_is_rref.argtypes = [vp]
+        lib.of_set_threads.restype = C.c_int
+        lib.of_set_threads.argtypes = [C.c_int]
         lib.ot_pauli_mult.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int)]
         lib.ot_conjugate.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = lib
@@ -189,6 +194,13 @@ class FrameOracle:
 
     def is_rref(self) -> bool:
         return bool(self.lib.of_is_rref(self.h))
+
+
+def set_threads(t: int) -> int:
+    """Number of element ranges (threads) the per-element loops of every
+    FrameOracle are split into (Sec. V); 1, the default, runs them
+    sequentially.  Returns the value in effect."""
+    return int(_load().of_set_threads(int(t)))
 
 
 def pauli_mult(a: int, b: int):

@@ -40,6 +40,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -47,6 +48,58 @@
 typedef double complex cplx;
 
 enum { OF_OK = 0, OF_EINVAL = 1, OF_ENOMEM = 2, OF_ECAPACITY = 3, OF_ESTATE = 6 };
+
+/* ---- element ranges (Sec. V) -----------------------------------------------
+ * The per-element loops of ROTATE, branching, COFACTOR and the amplitude sum
+ * touch each phase vector independently.  Sec. V runs them by splitting the
+ * phase vectors into equal consecutive ranges, one thread per range, joined
+ * before the operation returns; of_set_threads chooses the number of ranges
+ * (default 1: plain sequential loops).  Every element is computed by the same
+ * code either way, so frames are identical; sums over the frame are added per
+ * range and then range by range.                                              */
+#define OF_MAX_THREADS 256
+static int g_threads = 1;
+
+int of_set_threads(int t) {
+    g_threads = t < 1 ? 1 : (t > OF_MAX_THREADS ? OF_MAX_THREADS : t);
+    return g_threads;
+}
+
+typedef void (*range_fn)(void* ctx, size_t lo, size_t hi, int part);
+typedef struct { range_fn fn; void* ctx; size_t lo, hi; int part; } range_job;
+
+static void* range_run(void* p) {
+    range_job* j = (range_job*)p;
+    j->fn(j->ctx, j->lo, j->hi, j->part);
+    return NULL;
+}
+
+/* fn over [0, k) in at most g_threads consecutive ranges; returns the number
+ * of ranges used (range i is part i) */
+static int for_ranges(size_t k, range_fn fn, void* ctx) {
+    int T = g_threads;
+    if ((size_t)T > k) T = k ? (int)k : 1;
+    if (T <= 1) {
+        fn(ctx, 0, k, 0);
+        return 1;
+    }
+    range_job jobs[OF_MAX_THREADS];
+    pthread_t th[OF_MAX_THREADS];
+    int started[OF_MAX_THREADS];
+    size_t per = (k + T - 1) / T;
+    for (int t = 0; t < T; t++) {
+        size_t lo = (size_t)t * per, hi = lo + per;
+        jobs[t].fn = fn; jobs[t].ctx = ctx; jobs[t].part = t;
+        jobs[t].lo = lo < k ? lo : k;
+        jobs[t].hi = hi < k ? hi : k;
+        started[t] = t > 0 && pthread_create(&th[t], NULL, range_run, &jobs[t]) == 0;
+    }
+    for (int t = 0; t < T; t++)
+        if (!started[t]) range_run(&jobs[t]);
+    for (int t = 1; t < T; t++)
+        if (started[t]) pthread_join(th[t], NULL);
+    return T;
+}
 
 /* literals: (x<<1)|z  ->  I=0, Z=1, X=2, Y=3 */
 enum { LI = 0, LZ = 1, LX = 2, LY = 3 };
@@ -403,6 +456,48 @@ static ofr* clone_tableau(const ofr* f) {
 }
 static void free_tableau(ofr* g) { free(g->x); free(g->z); free(g->piv); free(g); }
 
+/* Steps of the five-step phase rule (Sec. III) for elements [lo, hi) of a
+ * ROTATE: sign flips and the recorded row operations give sigma', the new
+ * anchor b'*(sigma') is mapped back through U^dagger and read on the old M. */
+typedef struct {
+    ofr* f;
+    const ofr* old;
+    const gprog* prog;
+    const uint64_t* flip;
+    int q0, q1, two, nq;
+    cplx U[4][4];
+    double scale;
+} rot_ctx;
+
+static void rotate_range(void* vctx, size_t lo_j, size_t hi_j, int part) {
+    (void)part;
+    rot_ctx* cx = (rot_ctx*)vctx;
+    ofr* f = cx->f;
+    int W = f->W, q0 = cx->q0, q1 = cx->q1, two = cx->two;
+    uint64_t* s = (uint64_t*)malloc(8 * W);
+    uint64_t* b = (uint64_t*)malloc(8 * W);
+    uint64_t* y = (uint64_t*)malloc(8 * W);
+    for (size_t j = lo_j; j < hi_j; j++) {
+        uint64_t* sj = f->sig + j * W;
+        for (int w = 0; w < W; w++) s[w] = sj[w] ^ cx->flip[w];
+        replay(cx->prog, s);
+        anchor(f, s, b); /* new anchor b'*(sigma') on the new M */
+        int lo = getb(b, q0) | (two ? getb(b, q1) << 1 : 0);
+        cplx om = 0.0;
+        for (int li = 0; li < (1 << cx->nq); li++) {
+            if (cx->U[lo][li] == 0.0) continue;
+            memcpy(y, b, 8 * W);
+            setb(y, q0, li & 1);
+            if (two) setb(y, q1, (li >> 1) & 1);
+            om += cx->U[lo][li] * amp_at(cx->old, sj, y);
+        }
+        om *= cx->scale;
+        memcpy(sj, s, 8 * W);
+        f->a[j] *= om;
+    }
+    free(s); free(b); free(y);
+}
+
 /* ROTATE(F, U) for one Clifford gate (Sec. III). */
 static int clifford_one(ofr* f, int kind, int q0, int q1) {
     int n = f->n, W = f->W, two = (kind >= 6);
@@ -421,32 +516,13 @@ static int clifford_one(ofr* f, int kind, int q0, int q1) {
     }
     gprog prog = {0};
     if (gauss_jordan(f, &prog) != 0) { free(flip); free_tableau(old); return OF_ESTATE; }
-    cplx U[4][4];
-    int nq;
-    gate_matrix(kind, U, &nq);
-    uint64_t* s = (uint64_t*)malloc(8 * W);
-    uint64_t* b = (uint64_t*)malloc(8 * W);
-    uint64_t* y = (uint64_t*)malloc(8 * W);
-    double scale = pow(2.0, 0.5 * f->r);
-    for (size_t j = 0; j < f->k; j++) {
-        uint64_t* sj = f->sig + j * W;
-        for (int w = 0; w < W; w++) s[w] = sj[w] ^ flip[w];
-        replay(&prog, s);
-        anchor(f, s, b); /* new anchor b'*(sigma') on the new M */
-        int lo = getb(b, q0) | (two ? getb(b, q1) << 1 : 0);
-        cplx om = 0.0;
-        for (int li = 0; li < (1 << nq); li++) {
-            if (U[lo][li] == 0.0) continue;
-            memcpy(y, b, 8 * W);
-            setb(y, q0, li & 1);
-            if (two) setb(y, q1, (li >> 1) & 1);
-            om += U[lo][li] * amp_at(old, sj, y);
-        }
-        om *= scale;
-        memcpy(sj, s, 8 * W);
-        f->a[j] *= om;
-    }
-    free(s); free(b); free(y); free(flip); free(prog.v);
+    rot_ctx cx;
+    cx.f = f; cx.old = old; cx.prog = &prog; cx.flip = flip;
+    cx.q0 = q0; cx.q1 = q1; cx.two = two;
+    gate_matrix(kind, cx.U, &cx.nq);
+    cx.scale = pow(2.0, 0.5 * f->r);
+    for_ranges(f->k, rotate_range, &cx);
+    free(flip); free(prog.v);
     free_tableau(old);
     return OF_OK;
 }
@@ -505,20 +581,38 @@ static void merge_frame(ofr* f, double eps) {
 }
 
 /* one term c * Z^w applied to every element, children appended to dst */
+typedef struct {
+    const ofr* f;
+    const uint64_t *w, *m;
+    cplx c;
+    uint64_t* dsig;
+    cplx* da;
+} term_ctx;
+
+static void term_range(void* vctx, size_t lo, size_t hi, int part) {
+    (void)part;
+    term_ctx* cx = (term_ctx*)vctx;
+    const ofr* f = cx->f;
+    int W = f->W;
+    uint64_t* b = (uint64_t*)malloc(8 * W);
+    for (size_t j = lo; j < hi; j++) {
+        const uint64_t* s = f->sig + j * W;
+        anchor(f, s, b);
+        int p = popc_and(W, b, cx->w) & 1;
+        for (int t = 0; t < W; t++) cx->dsig[j * W + t] = s[t] ^ cx->m[t];
+        cx->da[j] = cx->c * (p ? -1.0 : 1.0) * f->a[j];
+    }
+    free(b);
+}
+
 static void branch_term(const ofr* f, const uint64_t* w, cplx c, uint64_t* dsig, cplx* da) {
     int W = f->W, n = f->n;
     uint64_t* m = (uint64_t*)calloc(W, 8);
-    uint64_t* b = (uint64_t*)malloc(8 * W);
     for (int h = 0; h < n; h++)
         if (popc_and(W, f->x + (size_t)h * W, w) & 1) flipb(m, h);
-    for (size_t j = 0; j < f->k; j++) {
-        const uint64_t* s = f->sig + j * W;
-        anchor(f, s, b);
-        int p = popc_and(W, b, w) & 1;
-        for (int t = 0; t < W; t++) dsig[j * W + t] = s[t] ^ m[t];
-        da[j] = c * (p ? -1.0 : 1.0) * f->a[j];
-    }
-    free(m); free(b);
+    term_ctx cx = {f, w, m, c, dsig, da};
+    for_ranges(f->k, term_range, &cx);
+    free(m);
 }
 
 /* P(theta)_t = alpha I + beta Z_t (Sec. IV, T gate as a cofactor sum) */
@@ -584,6 +678,47 @@ static int find_zq_row(const ofr* f, int q) {
     return -1;
 }
 
+/* the two cofactors of elements [lo, hi): child x of element j goes to slot
+ * 2j + x (valid[2j + x] = 1 when its weight is nonzero) */
+typedef struct {
+    ofr* f;
+    const ofr* old;
+    const gprog* prog;
+    const uint64_t* anti;
+    const int* cb;
+    int piv_row, q;
+    double scale;
+    uint64_t* nsig;
+    cplx* na;
+    unsigned char* valid;
+} cof_ctx;
+
+static void cof_range(void* vctx, size_t lo, size_t hi, int part) {
+    (void)part;
+    cof_ctx* cx = (cof_ctx*)vctx;
+    ofr* f = cx->f;
+    int n = f->n, W = f->W;
+    uint64_t* s = (uint64_t*)malloc(8 * W);
+    uint64_t* b = (uint64_t*)malloc(8 * W);
+    for (size_t j = lo; j < hi; j++) {
+        const uint64_t* sj = f->sig + j * W;
+        for (int x = 0; x < 2; x++) {
+            memcpy(s, sj, 8 * W);
+            for (int h = 0; h < n; h++)
+                if (getb(cx->anti, h) && (getb(sj, cx->piv_row) ^ cx->cb[h])) flipb(s, h);
+            setb(s, cx->piv_row, x);
+            replay(cx->prog, s);
+            anchor(f, s, b);
+            cplx om = (getb(b, cx->q) == x) ? amp_at(cx->old, sj, b) * cx->scale : 0.0;
+            if (om == 0.0) continue;
+            memcpy(cx->nsig + (2 * j + x) * W, s, 8 * W);
+            cx->na[2 * j + x] = f->a[j] * om;
+            cx->valid[2 * j + x] = 1;
+        }
+    }
+    free(s); free(b);
+}
+
 /* COFACTOR(F, q) (Sec. III): if q is random in M, the measurement update of
  * Sec. II-B forced to each outcome, every element split into its two
  * cofactors weighted by the five-step phase rule, then merged.  Afterwards
@@ -611,31 +746,28 @@ static int cofactor(ofr* f, uint32_t q) {
         size_t k = f->k;
         uint64_t* nsig = (uint64_t*)malloc(2 * k * 8 * W + 8);
         cplx* na = (cplx*)malloc(2 * k * sizeof(cplx) + 16);
-        uint64_t* s = (uint64_t*)malloc(8 * W);
-        uint64_t* b = (uint64_t*)malloc(8 * W);
-        double scale = pow(2.0, 0.5 * f->r);
+        cof_ctx cx;
+        cx.f = f; cx.old = old; cx.prog = &prog; cx.anti = anti; cx.cb = cb;
+        cx.piv_row = piv_row; cx.q = (int)q; cx.scale = pow(2.0, 0.5 * f->r);
+        cx.nsig = nsig; cx.na = na;
+        cx.valid = (unsigned char*)calloc(2 * k + 1, 1);
+        for_ranges(k, cof_range, &cx);
+        /* children in element order, as one sequential pass would append them */
         size_t out = 0;
-        for (size_t j = 0; j < k; j++) {
-            const uint64_t* sj = f->sig + j * W;
-            for (int x = 0; x < 2; x++) {
-                memcpy(s, sj, 8 * W);
-                for (int h = 0; h < n; h++)
-                    if (getb(anti, h) && (getb(sj, piv_row) ^ cb[h])) flipb(s, h);
-                setb(s, piv_row, x);
-                replay(&prog, s);
-                anchor(f, s, b);
-                cplx om = (getb(b, (int)q) == x) ? amp_at(old, sj, b) * scale : 0.0;
-                if (om == 0.0) continue;
-                memcpy(nsig + out * W, s, 8 * W);
-                na[out] = f->a[j] * om;
-                out++;
+        for (size_t c = 0; c < 2 * k; c++) {
+            if (!cx.valid[c]) continue;
+            if (out != c) {
+                memmove(nsig + out * W, nsig + c * W, 8 * W);
+                na[out] = na[c];
             }
+            out++;
         }
+        free(cx.valid);
         if (reserve(f, out)) return OF_ENOMEM;
         memcpy(f->sig, nsig, out * 8 * W);
         memcpy(f->a, na, out * sizeof(cplx));
         f->k = out;
-        free(nsig); free(na); free(s); free(b); free(anti); free(cb); free(prog.v);
+        free(nsig); free(na); free(anti); free(cb); free(prog.v);
         free_tableau(old);
         merge_frame(f, OF_MEASURE_EPS);
     }
@@ -742,10 +874,27 @@ int of_cr_cofactor(void* hh, uint32_t c, uint32_t t, double alpha) {
     return OF_OK;
 }
 
+/* <y|Psi> summed over elements [lo, hi) (Observation 1 per element) */
+typedef struct {
+    const ofr* f;
+    const uint64_t* y;
+    cplx part[OF_MAX_THREADS];
+} amp_ctx;
+
+static void amp_range(void* vctx, size_t lo, size_t hi, int part) {
+    amp_ctx* cx = (amp_ctx*)vctx;
+    cplx acc = 0.0;
+    for (size_t j = lo; j < hi; j++) acc += cx->f->a[j] * amp_at(cx->f, cx->f->sig + j * cx->f->W, cx->y);
+    cx->part[part] = acc;
+}
+
 int of_amplitude(void* hh, const uint64_t* y, double* re, double* im) {
     ofr* f = (ofr*)hh;
+    amp_ctx cx;
+    cx.f = f; cx.y = y;
+    int T = for_ranges(f->k, amp_range, &cx);
     cplx acc = 0.0;
-    for (size_t j = 0; j < f->k; j++) acc += f->a[j] * amp_at(f, f->sig + j * f->W, y);
+    for (int t = 0; t < T; t++) acc += cx.part[t];
     *re = creal(acc);
     *im = cimag(acc);
     return OF_OK;

@@ -1,21 +1,26 @@
 // sf_noalloc.cu -- sf_coalesce_noalloc: coalescing of caller-owned device
 // buffers with no allocation at all.
 //
-// Who needs it: code that must merge a frame at a point where it cannot
-// allocate device memory -- while a stream is being captured into a CUDA graph
-// (cudaMalloc is not allowed there), inside a framework whose device memory
-// belongs to its own caching pool (an extra cudaMalloc behind its back
-// fragments that pool and may synchronise the device), or in a serving loop
-// that plans all of its memory up front and cannot pay for an allocation on
-// the request path.  The caller passes the input and output arrays; the
-// hash table, the representative indices and the amplitude accumulators live
-// in one file-scope __device__ array of fixed size, so the number of input
-// elements is capped.
+// Who needs it: callers that must not allocate device memory where they merge
+// a frame.  A framework that owns the device memory through its own caching
+// pool leaves little free memory outside that pool, so an extra cudaMalloc
+// behind its back may fail, and cudaMalloc/cudaFree can synchronise the
+// device; a serving loop that budgets all device memory up front must not
+// fail half way through a request on an allocation.  The caller passes the
+// input and output arrays; the hash table, the representative indices and the
+// amplitude accumulators live in one file-scope __device__ array of fixed
+// size, so the number of input elements is capped.
 //
 // The scratch array is shared by every call on a device and keeps the
 // previous call's contents: each call clears what it relies on before use.
 // Calls whose kernels overlap on the GPU (two streams, or two host threads)
 // race on the scratch; callers must order them.
+//
+// Output order: each group of equal phase vectors is represented by its first
+// input element (the smallest index, found with atomicMin after the slots are
+// claimed), and representatives are written in input order.  The amplitudes of
+// a group are summed with atomics, in an order that depends on scheduling, so
+// two calls on the same input may differ in the last bits of a merged sum.
 #include <mutex>
 
 #include "sf.h"
@@ -92,9 +97,9 @@ __global__ void k_na_init(uint32_t* base, const double2* amp_in, uint64_t k) {
     }
 }
 
-// find or claim the slot of each phase vector; duplicates add their amplitude
-// to the first element that claimed the slot
-__global__ void k_na_insert(uint32_t* base, const uint64_t* sig_in, const double2* amp_in, uint64_t k, int nw) {
+// find or claim the slot of each phase vector; the slot ends up holding the
+// smallest input index of its group, and rep[j] the slot of element j
+__global__ void k_na_insert(uint32_t* base, const uint64_t* sig_in, uint64_t k, int nw) {
     const NaPtrs p = na_ptrs(base);
     const uint32_t T = table_slots(k);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -102,22 +107,37 @@ __global__ void k_na_insert(uint32_t* base, const uint64_t* sig_in, const double
         uint64_t s[SF_MAX_W];
         for (int w = 0; w < nw; w++) s[w] = sig_in[j * nw + w];
         uint32_t slot = (uint32_t)(na_hash(s, nw) & (T - 1));
-        uint32_t rep = kEmptySlot;
+        uint32_t found = kEmptySlot;
         for (uint32_t probe = 0; probe < T; probe++) {
             uint32_t cur = p.slots[slot];
             if (cur == kEmptySlot) {
                 cur = atomicCAS(&p.slots[slot], kEmptySlot, (uint32_t)j);
-                if (cur == kEmptySlot) { rep = (uint32_t)j; break; }
+                if (cur == kEmptySlot) { found = slot; break; }
             }
+            // any member of a group has the group's phase vector, so the slot
+            // may be lowered by atomicMin while others compare against it
             bool eq = true;
             for (int w = 0; w < nw; w++) eq &= (sig_in[(uint64_t)cur * nw + w] == s[w]);
-            if (eq) { rep = cur; break; }
+            if (eq) { found = slot; break; }
             slot = (slot + 1) & (T - 1);
         }
-        if (rep == kEmptySlot) {
-            atomicExch(p.flag, 1u);
-            rep = (uint32_t)j;
+        if (found == kEmptySlot) {
+            atomicExch(p.flag, 1u);  // table full: cannot happen with 2k slots, reported if it does
+        } else {
+            atomicMin(&p.slots[found], (uint32_t)j);
         }
+        p.rep[j] = found;
+    }
+}
+
+// representative of each element (its group's smallest index); the others add
+// their amplitude to it
+__global__ void k_na_link(uint32_t* base, const double2* amp_in, uint64_t k) {
+    const NaPtrs p = na_ptrs(base);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < k; j += stride) {
+        const uint32_t slot = p.rep[j];
+        const uint32_t rep = slot == kEmptySlot ? (uint32_t)j : p.slots[slot];
         p.rep[j] = rep;
         if (rep != (uint32_t)j) {
             const double2 a = amp_in[j];
@@ -169,7 +189,10 @@ std::mutex g_na_mu;
 uint32_t* g_na_addr[SF_NOALLOC_MAX_DEVICES] = {};
 
 // Device address of the scratch array for the current device, looked up once
-// per device (the symbol's host-side name is not a device address).
+// per device with that device current (the symbol's host-side name is not a
+// device address).  The address belongs to the device's primary context, so a
+// process that resets the device (cudaDeviceReset) must not call
+// sf_coalesce_noalloc on it afterwards.
 sf_status na_scratch(uint32_t** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SF_NOALLOC_MAX_DEVICES) return SF_ECUDA;
@@ -199,7 +222,8 @@ extern "C" sf_status sf_coalesce_noalloc(const uint64_t* sigma_in, const double*
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const double2* ain = reinterpret_cast<const double2*>(amp_in);
     k_na_init<<<kNaBlocks, kNaThreads, 0, s>>>(base, ain, k_in);
-    k_na_insert<<<kNaBlocks, kNaThreads, 0, s>>>(base, sigma_in, ain, k_in, (int)n_words);
+    k_na_insert<<<kNaBlocks, kNaThreads, 0, s>>>(base, sigma_in, k_in, (int)n_words);
+    k_na_link<<<kNaBlocks, kNaThreads, 0, s>>>(base, ain, k_in);
     k_na_compact<<<1, 1024, 0, s>>>(base, sigma_in, k_in, (int)n_words, drop_eps * drop_eps, sigma_out,
                                     reinterpret_cast<double2*>(amp_out));
     if (cudaGetLastError() != cudaSuccess) return SF_ECUDA;
