@@ -758,6 +758,15 @@ def main():
     with torch.cuda.stream(stream):
         async_part(frame)
     p_ref, a_ref = tail(frame)
+    # the grid program counts the element bytes its passes read and write (each
+    # pass once); that is its algorithmic traffic, not the per-op sum above
+    gp_moved = None
+    if use_grid and n_rec > m_pre:
+        with torch.cuda.stream(stream):
+            async_part(frame)
+        gp_moved = frame.grid_program_bytes()
+        tail(frame)
+        graph_rec["gprog"] = [(gp_moved, 0)]
 
     # per-class device time of one eager step -> dominant kernel class
     per_class = {}
@@ -905,45 +914,25 @@ def main():
     clocks = clk.summary()
     # graph replays do not pass through the host launch counter: add the captured kernels
     launches_total = launches_timed  # launched from the host inside the timed steps
-    if graph is not None and use_grid:  # reset, program kernels, the index build between them
-        launches_total += (1 + (2 if m_pre else 0) + (1 if n_rec > m_pre else 0)) * args.steps
+    if graph is not None and use_grid:  # reset and the program kernels
+        launches_total += (1 + (1 if m_pre else 0) + (1 if n_rec > m_pre else 0)) * args.steps
     elif graph is not None:
         launches_total += graph_launch_count(plan[p_pre:], start_indexed=not m_pre,
                                              extra=1 if m_pre else 0) * args.steps  # graph replays
     ms_step = float(np.mean(step_ms))
 
-    # e2e: the public API with host gate arrays, eager launches
+    # e2e: the public API with host buffers -- the QFT's records from host
+    # memory in one sf_run_program call (the library copies them), then the
+    # measurement and the amplitude, each reading its result back
     e2e_frame = sf.Frame(n, MAX_ELEMS, stream=stream)
-    m_host = n_rec if use_grid else m_pre  # records copied from the host each step
-    h2d = (0 if use_grid else 16 * sum(len(op[1]) for op in plan[p_pre:] if op[0] == "C")) + \
-        8 * e2e_frame.W + 24 * m_host
+    h_recs = plan_records(sf, plan)[0]
+    h2d = int(h_recs.nbytes) + 8 * e2e_frame.W
     d2h = 16 + 16
-    if m_host:
-        h_prog = torch.from_numpy(plan_records(sf, plan)[0][:m_host].view(np.uint8).copy()).pin_memory()
-        d_prog_e2e = torch.empty_like(h_prog, device="cuda")
 
     def e2e_step():
         e2e_frame.reset()
-        if m_host:  # the programs' records from pinned host memory, then one launch each
-            d_prog_e2e.copy_(h_prog, non_blocking=True)
-        if m_pre:
-            e2e_frame.apply_program_device(d_prog_e2e.data_ptr(), m_pre, DROP_EPS, 0, 0, max_frame)
-        if use_grid:
-            if n_rec > m_pre:
-                e2e_frame.apply_program_grid_device(d_prog_e2e.data_ptr() + 24 * m_pre, n_rec - m_pre, DROP_EPS)
-            return e2e_frame.measure(0, -1), e2e_frame.amplitude(y)
-        for op in plan[p_pre:]:
-            if op[0] == "C":
-                e2e_frame.apply_clifford(op[1])
-            elif op[0] == "NK":
-                e2e_frame.apply_nonclifford_coalesce(op[1], op[2], op[3], op[4], DROP_EPS)
-            elif op[0] == "N":
-                e2e_frame.apply_nonclifford(op[1], op[2], op[3], op[4])
-            elif op[0] == "K":
-                e2e_frame.coalesce(DROP_EPS)
-        p = e2e_frame.measure(0, -1)
-        a = e2e_frame.amplitude(y)
-        return p, a
+        e2e_frame.run_program_records(h_recs, DROP_EPS)
+        return e2e_frame.measure(0, -1), e2e_frame.amplitude(y)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -955,7 +944,7 @@ def main():
             t0 = time.perf_counter()
             p_e, a_e = e2e_step()
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    if abs(a_e - a_ref) > 1e-10:
+    if abs(a_e - a_ref) > 1e-10 or abs(p_e[0] - p_ref[0]) > 1e-10:
         raise RuntimeError("e2e result differs from the device path")
     e2e_ms_step = float(np.mean(e2e_ms))
 
@@ -980,6 +969,10 @@ def main():
                 "frac": achieved / peak_gbs, "peak_source": peak_src, "traffic": ncu_traffic(dominant),
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_ms * 1e3,
                 "launches_timed": dom_launches}
+    if dominant == "gprog" and gp_moved is not None:
+        roofline["bytes_model"] = ("the grid program's own count of element bytes (8 per phase-vector word, 16 per "
+                                   "amplitude) read and written by its passes, each pass once (sf_grid_program_bytes)")
+        roofline["per_op_equivalent_bytes"] = gp_bytes if (p_pre or use_grid) else None
     if dominant in ("segment", "gprog"):
         roofline["note"] = ("the dominant kernel is a program kernel (the single-CTA small-frame prefix, or the "
                             "grid program that runs the rest of the circuit with grid barriers between its "
@@ -1021,7 +1014,9 @@ def main():
                    "coalesce_elems_per_s": coal_elems * world / (max_ms * 1e-3), "frame_peak": peak,
                    "wall_s_timed_region": wall},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": max_e2e},
+                "ms_per_step": max_e2e,
+                "path": "sf_reset; sf_run_program (the QFT's sf_op records from host memory, copied by the library); "
+                        "sf_measure(0, -1); sf_amplitude -- results read back every step"},
         "roofline": roofline,
         "roofline_streaming": roofline_streaming,
         "kernel_time_share_eager_step": step_share,

@@ -249,7 +249,8 @@ sf_status sf_coalesce_noalloc(const uint64_t* sigma_in, const double* amp_in, ui
                               void* cuda_stream);
 
 /* Host-side bookkeeping of the handle: which of its two frame buffers holds
- * the current frame and which buffers carry a valid phase-vector index.  A
+ * the current frame, which buffers carry a valid phase-vector index, and what
+ * the grid program may assume about the frame's phase vectors.  A
  * CUDA graph captured from this handle's stream replays device work only, so
  * read the token right after the capture ends and restore it with
  * sf_set_host_state after every replay, before the next call on the handle. */
@@ -326,14 +327,17 @@ sf_status sf_apply_program(sf_handle h, const sf_op* dev_ops, uint64_t n_ops, do
 /* A program of Clifford and diagonal sf_op records (kinds 0..8 and 16..19;
  * ROTATE and merged branching, Sec. III-IV) applied to this handle's frame, of
  * any size up to max_elems, in ONE cooperative launch over the whole GPU, for
- * handles with n_qubits <= 63.  One persistent CTA per SM walks the records;
- * a Clifford run is applied to the tableau by one warp and to the phase
- * vectors by every CTA (with a fresh index), a run of diagonal records is
- * planned at once (one CTA per record) and then merged record by record, and
- * grid barriers separate the phases.  This replaces the per-op launches (a
- * tableau kernel, an affine pass and an index rebuild per Clifford run, a
- * merge kernel per diagonal gate) with the same frame results as the per-op
- * calls (amplitudes to rounding).
+ * handles with n_qubits <= 63.  One persistent CTA per SM walks the records; a
+ * Clifford run is applied to the tableau by one warp, a run of diagonal
+ * records is planned at once (one CTA per record), and the records are then
+ * applied in passes over the frame separated by grid barriers.  A diagonal
+ * gate whose anticommutation mask is not spanned by the differences of the
+ * frame's phase vectors has no partners: its elements write both children in
+ * place, and the following gates that keep those pairs are applied in the same
+ * pass; other gates are merged through the phase-vector index as in
+ * sf_apply_nonclifford_coalesce.  The same frame results as the per-op calls
+ * (amplitudes to rounding; an amplitude between 0 and drop_eps inside a pass
+ * is kept to the pass's end, a difference of at most drop_eps).
  *
  * dev_ops: n_ops records in device memory (valid until the stream reaches the
  * call).  The records are checked first (qubits and kinds; measurement and
@@ -343,12 +347,65 @@ sf_status sf_apply_program(sf_handle h, const sf_op* dev_ops, uint64_t n_ops, do
  * nullable) receives the number of records applied, so the caller continues
  * with the per-op calls from there.  A frame that would exceed max_elems fails
  * the call (SF_ECAPACITY, deferred), the frame holding the state before the
- * failing record.  A grid barrier that waits for more than about a second
- * fails the call with SF_ETIMEOUT (deferred).  The frame ends in the handle's
- * current buffer with its index built.  Asynchronous; two calls on the same
- * handle are ordered by its stream. */
+ * failing record.  A grid barrier that waits longer than the handle's wait
+ * limit (sf_set_wait_limit) fails the call with SF_ETIMEOUT (deferred); the
+ * tableau and frame are then unspecified until sf_reset.  The frame ends in
+ * the handle's current buffer.  Asynchronous; two calls on the same handle are
+ * ordered by its stream. */
 sf_status sf_apply_program_grid(sf_handle h, const sf_op* dev_ops, uint64_t n_ops, double drop_eps,
                                 uint64_t* dev_consumed);
+
+/* A whole program of sf_op records (every kind above: Clifford gates, merged
+ * diagonal gates, measurements with caller draws, conditional Clifford gates;
+ * Sec. III-IV) from HOST memory, run on this handle.  The records are checked
+ * first (SF_EINVAL, nothing applied, for a bad record or more than 64
+ * measurements).  For n_qubits <= 63 the library copies them to the device
+ * once (through a pinned staging buffer of the handle) and runs each stretch
+ * of Clifford and diagonal records as one sf_apply_program_grid launch;
+ * otherwise it applies them with the per-op calls.  A measurement is made as
+ * in the campaign engine: outcome 1 iff the record's draw (param) is below
+ * p(1), then the frame is collapsed onto it; a conditional gate applies iff
+ * the parity of (outcome bits & mask) is 1.  outcomes / n_meas (host,
+ * nullable) receive the outcome bits (bit m = measurement m) and their number.
+ * Synchronises at each measurement (the draw needs p(1)); otherwise
+ * asynchronous, with deferred device errors as for the calls it makes. */
+sf_status sf_run_program(sf_handle h, const sf_op* ops, uint64_t n_ops, double drop_eps, uint64_t* outcomes,
+                         uint32_t* n_meas);
+
+/* Bytes of phase vectors (8 per word) and amplitudes (16) that the passes of
+ * the last sf_apply_program_grid launch on this handle read and wrote, each
+ * pass counted once: a branch pass reads its k elements and writes 2k, an
+ * in-place pass reads k and writes back the amplitudes (and the phase vectors
+ * when it applies a Clifford map), a merge reads its input and writes its
+ * output, an index build reads the phase vectors; index slots are not
+ * counted.  For roofline figures.  Synchronises. */
+sf_status sf_grid_program_bytes(sf_handle h, uint64_t* bytes);
+
+/* Tracing of the grid program, for performance analysis.  With on != 0 the
+ * next sf_apply_program_grid launches of this handle time each phase (the
+ * stretch between two grid barriers) with the GPU's global nanosecond timer.
+ * sf_grid_program_trace writes up to cap records of 13 words for the last
+ * traced launch, one per phase in order, and their number to *n: what ran
+ * (low 4 bits: 3 branch pass along a new direction, 4 in-place pass, 5
+ * merge, 6 compaction, 7 index build, 8 Clifford map pass, 10 record check;
+ * bits 4..7: records in the pass, mod 16; bits 8..: elements), the time CTA 0
+ * began the phase, the time it reached the barrier, the time the last CTA
+ * reached it, that CTA's index, then 8 checkpoint times of CTA 0 inside the
+ * phase (0 where not reached): Clifford run start and end, planning end, hull
+ * update end, pass start, Clifford-map tables end, element loop end, and the
+ * time the kept-children counts of the previous pass were read after its
+ * barrier.  Synchronises. */
+sf_status sf_set_trace(sf_handle h, int32_t on);
+sf_status sf_grid_program_trace(sf_handle h, uint64_t* rec, uint32_t cap, uint32_t* n);
+
+/* Bounded device waits: a grid barrier of sf_apply_program_grid polls at most
+ * `polls` times, about 100 ns apart, before the launch gives up with
+ * SF_ETIMEOUT (every CTA leaves at its next barrier; no kernel waits without
+ * bound).  The default, SF_WAIT_LIMIT_DEFAULT, is about 0.1 s of waiting; a
+ * small value makes a barrier run out on purpose, for tests of the timeout
+ * path.  Takes effect at the next launch. */
+#define SF_WAIT_LIMIT_DEFAULT 1048576u
+sf_status sf_set_wait_limit(sf_handle h, uint32_t polls);
 
 typedef struct sf_campaign_s* sf_campaign;
 

@@ -166,6 +166,34 @@ def qft_expected_amplitude(n: int, x: int, y: int) -> complex:
 
 
 # ---- workload 3: Cuccaro ripple-carry adder -------------------------------------------
+def stage_circuit(n: int, seed: int, stages: int, per_stage: int) -> List[Op]:
+    """Stages shaped like the QFT's: X on random qubits, then per stage H on a
+    fresh target t and a run of controlled phases onto t from random other
+    qubits (angles pi/2, pi, pi/4, -pi/2, 2 pi/3: exact zeros when a control
+    is |0>, cancellations when angles add up to multiples of 2 pi), T and
+    T-dagger on t, and one-qubit phases on random qubits.  Each stage branches
+    along a new direction; controls from earlier stages make merges whose
+    partners already exist."""
+    g = rng_for(seed)
+    ops: List[Op] = [("C", X, q, 0) for q in range(n) if g.random() < 0.5]
+    for s in range(stages):
+        t = s % n
+        ops.append(("C", H, t, 0))
+        for _ in range(per_stage):
+            r = g.random()
+            if r < 0.6:
+                ctl = int(g.integers(n - 1))
+                ctl += ctl >= t
+                th = float(g.choice([np.pi / 2, np.pi, np.pi / 4, -np.pi / 2, 2 * np.pi / 3]))
+                ops += [("N", CPHASE, ctl, t, th), ("K",)]
+            elif r < 0.8:
+                ops += [("N", T if g.random() < 0.5 else TDG, t, 0, 0.0), ("K",)]
+            else:
+                q = int(g.integers(n))
+                ops += [("N", PHASE, q, 0, float(g.uniform(-3, 3))), ("K",)]
+    return ops
+
+
 def cuccaro_layout(nbits: int):
     """Qubit 0 = ancilla (carry-in), then interleaved b_i, a_i for i = 0..nbits-1,
     then the carry-out z.  Returns (anc, a[], b[], z)."""

@@ -25,6 +25,13 @@ struct sf_frame_s {
     size_t dgates_cap = 0;
     sf_gate_rec* hstage = nullptr;
     size_t hstage_cap = 0;
+    double2* dtrig = nullptr;   // e^{i theta} scratch of the grid program, one per record
+    size_t dtrig_cap = 0;
+    OpRec* dops = nullptr;      // program records copied by sf_run_program
+    size_t dops_cap = 0;
+    OpRec* hops = nullptr;      // their pinned staging buffer
+    size_t hops_cap = 0;
+    cudaEvent_t ops_ev = nullptr;  // the last copy out of hops
     cudaEvent_t stage_ev = nullptr;
     uint64_t* dy = nullptr;
     uint64_t* hy = nullptr;
@@ -35,6 +42,12 @@ struct sf_frame_s {
     std::vector<void*> dallocs;
     std::string err;
     bool idx_ok[2] = {false, false};  // buffer b has a valid phase-vector index
+    // what the grid program may assume about the hull of the frame (the span of
+    // the differences of its phase vectors): 0 nothing, 1 the constraints its
+    // last launch left in its workspace, 2 the frame is one element
+    int hull = 2;
+    uint32_t wait_limit = SF_WAIT_LIMIT_DEFAULT;
+    int trace = 0;  // grid program launches record per-phase times
     uint64_t launches = 0;
     int time_id = -1;
     std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
@@ -175,6 +188,21 @@ sf_status launch(sf_handle h, int id, const char* what, F&& fn) {
     if (e != cudaSuccess) return cuda_fail(h, e, what);
     if (timed) cudaEventRecordWithFlags(e1, h->stream, rec_flags);
     h->launches++;
+    // a kernel that moves phase vectors to other coordinates or adds new ones
+    // invalidates what the grid program knows about the frame's hull; subsets
+    // of the frame (coalescing, collapse) keep it valid
+    switch (id) {
+        case SF_K_CLIFFORD:
+        case SF_K_AFFINE:
+            if (h->hull != 2) h->hull = 0;  // one element stays one element
+            break;
+        case SF_K_RESET: case SF_K_GPROG: case SF_K_INDEX: case SF_K_INSERT: case SF_K_COMPACT: case SF_K_FILTER:
+        case SF_K_PROB: case SF_K_REDUCE: case SF_K_AMP_PREP: case SF_K_AMPLITUDE: case SF_K_EXPORT:
+        case SF_K_MEASURE_PREP:
+            break;
+        default:
+            h->hull = 0;
+    }
     return SF_OK;
 }
 
@@ -195,6 +223,7 @@ sf_status sync_check(sf_handle h) {
     if (st) {
         h->cur = (int)((st >> 8) & 1u);
         h->idx_ok[0] = h->idx_ok[1] = false;
+        h->hull = 0;
         SF_CK(h, cudaMemsetAsync(h->d.status, 0, sizeof(uint32_t), h->stream));
         SF_CK(h, cudaMemsetAsync(h->d.done, 0, sizeof(unsigned int), h->stream));
         SF_CK(h, cudaMemsetAsync(h->d.ocnt, 0, sizeof(unsigned long long), h->stream));
@@ -256,6 +285,27 @@ sf_status run_clifford(sf_handle h, const sf_gate_rec* dev, uint64_t ng) {
         SF_LAUNCH(h, SF_K_AFFINE, sf_launch_affine(h->d, h->cur, h->stream));
     }
     h->idx_ok[h->cur] = false;  // phase vectors changed; the index is rebuilt when needed
+    return SF_OK;
+}
+
+// a device buffer of the handle that grows stream-ordered (earlier launches may
+// still read the old one)
+template <typename T>
+sf_status grow_dev(sf_handle h, T** p, size_t& cap, size_t need) {
+    if (need <= cap && *p) return SF_OK;
+    size_t c = cap ? cap : 256;
+    while (c < need) c *= 2;
+    void* v = nullptr;
+    SF_CK(h, cudaMallocAsync(&v, c * sizeof(T), h->stream));
+    auto it = std::find(h->dallocs.begin(), h->dallocs.end(), (void*)*p);
+    if (*p && it != h->dallocs.end()) {
+        cudaFreeAsync(*it, h->stream);
+        *it = v;
+    } else {
+        h->dallocs.push_back(v);
+    }
+    *p = static_cast<T*>(v);
+    cap = c;
     return SF_OK;
 }
 
@@ -389,6 +439,8 @@ sf_status sf_destroy(sf_handle h) {
     pinned_free(h->hstatus, 1);
     pinned_free(h->hout, 8);
     pinned_free(h->hmeta, 4);
+    pinned_free(h->hops, h->hops_cap);
+    if (h->ops_ev) cudaEventDestroy(h->ops_ev);
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -401,6 +453,7 @@ sf_status sf_reset(sf_handle h) {
     SF_LAUNCH(h, SF_K_RESET, sf_launch_reset(h->d, 0, h->stream));
     h->idx_ok[0] = true;
     h->idx_ok[1] = false;
+    h->hull = 2;
     return SF_OK;
 }
 
@@ -516,16 +569,156 @@ sf_status sf_apply_program_grid(sf_handle h, const sf_op* dev_ops, uint64_t n_op
         if (dev_consumed) SF_CK(h, cudaMemsetAsync(dev_consumed, 0, sizeof(uint64_t), h->stream));
         return SF_OK;
     }
-    sf_status st = need_index(h, h->cur);
-    if (st) return st;
+    sf_status gs = grow_dev(h, &h->dtrig, h->dtrig_cap, n_ops);
+    if (gs) return gs;
     cudaError_t ge = cudaSuccess;
     SF_LAUNCH(h, SF_K_GPROG,
-              ge = sf_launch_gprog(h->d, dev_ops, n_ops, drop_eps * drop_eps, h->cur,
+              ge = sf_launch_gprog(h->d, dev_ops, n_ops, drop_eps * drop_eps, h->cur, h->idx_ok[h->cur] ? 1 : 0,
+                                   h->hull, h->wait_limit, h->trace, h->dtrig,
                                    reinterpret_cast<unsigned long long*>(dev_consumed), h->stream));
     if (ge != cudaSuccess) return cuda_fail(h, ge, "grid program launch");
-    // the frame ends in the current buffer with its index; the other index is stale
-    h->idx_ok[h->cur] = true;
-    h->idx_ok[h->cur ^ 1] = false;
+    // the frame ends in the current buffer, without an index; the kernel keeps
+    // the hull in its workspace when it started from a known one
+    h->idx_ok[0] = h->idx_ok[1] = false;
+    h->hull = h->hull ? 1 : 0;
+    return SF_OK;
+}
+
+sf_status sf_run_program(sf_handle h, const sf_op* ops, uint64_t n_ops, double drop_eps, uint64_t* outcomes,
+                         uint32_t* n_meas) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (n_ops && !ops) return fail(h, SF_EINVAL, "ops is NULL");
+    if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");
+    uint32_t nm = 0;
+    for (uint64_t i = 0; i < n_ops; i++) {
+        const sf_op& o = ops[i];
+        const uint32_t k = o.kind == SF_OP_COND ? o.arg : o.kind;
+        const bool two = (k >= SF_CNOT && k <= SF_SWAP) || k == SF_OP_DIAG + SF_CPHASE;
+        bool ok = o.q0 < h->n && (!two || (o.q1 < h->n && o.q1 != o.q0));
+        if (o.kind == SF_OP_COND) ok &= o.arg <= SF_SWAP;
+        else ok &= k <= SF_SWAP || (k >= SF_OP_DIAG && k <= SF_OP_DIAG + SF_CPHASE) || k == SF_OP_MEASURE;
+        if (!ok) return fail(h, SF_EINVAL, "bad program record " + std::to_string(i));
+        nm += o.kind == SF_OP_MEASURE;
+    }
+    if (nm > 64) return fail(h, SF_EINVAL, "more than 64 measurements");
+    const bool grid = h->d.W == 1 && h->d.gp;
+    if (grid && n_ops) {
+        // the records go to the device once, through the pinned staging buffer
+        if (!h->ops_ev) SF_CK(h, cudaEventCreateWithFlags(&h->ops_ev, cudaEventDisableTiming));
+        SF_CK(h, cudaEventSynchronize(h->ops_ev));  // the previous copy has left the staging buffer
+        if (n_ops > h->hops_cap) {
+            pinned_free(h->hops, h->hops_cap);
+            h->hops = nullptr;
+            size_t c = h->hops_cap ? h->hops_cap : 256;
+            while (c < n_ops) c *= 2;
+            SF_CK(h, pinned_alloc_n(&h->hops, c));
+            h->hops_cap = c;
+        }
+        sf_status gs = grow_dev(h, &h->dops, h->dops_cap, n_ops);
+        if (gs) return gs;
+        std::memcpy(h->hops, ops, n_ops * sizeof(OpRec));
+        SF_CK(h, cudaMemcpyAsync(h->dops, h->hops, n_ops * sizeof(OpRec), cudaMemcpyHostToDevice, h->stream));
+        SF_CK(h, cudaEventRecord(h->ops_ev, h->stream));
+    }
+    uint64_t bits = 0;
+    uint32_t done_m = 0;
+    std::vector<sf_gate> gates;
+    auto flush = [&]() -> sf_status {
+        if (gates.empty()) return SF_OK;
+        sf_status st = sf_apply_clifford(h, gates.data(), gates.size());
+        gates.clear();
+        return st;
+    };
+    uint64_t i = 0;
+    while (i < n_ops) {
+        const sf_op& o = ops[i];
+        if (o.kind <= SF_SWAP || (o.kind >= SF_OP_DIAG && o.kind <= SF_OP_DIAG + SF_CPHASE)) {
+            uint64_t j = i;
+            while (j < n_ops && (ops[j].kind <= SF_SWAP ||
+                                 (ops[j].kind >= SF_OP_DIAG && ops[j].kind <= SF_OP_DIAG + SF_CPHASE)))
+                j++;
+            if (grid) {
+                sf_status st = flush();
+                if (!st) st = sf_apply_program_grid(h, reinterpret_cast<const sf_op*>(h->dops + i), j - i, drop_eps,
+                                                    nullptr);
+                if (st) return st;
+            } else {
+                for (uint64_t r = i; r < j; r++) {
+                    const sf_op& q = ops[r];
+                    if (q.kind <= SF_SWAP) {
+                        gates.push_back(sf_gate{q.kind, q.q0, q.q1, 0u});
+                        continue;
+                    }
+                    sf_status st = flush();
+                    if (!st) st = sf_apply_nonclifford_coalesce(h, q.kind - SF_OP_DIAG, q.q0, q.q1, q.param, drop_eps);
+                    if (st) return st;
+                }
+            }
+            i = j;
+            continue;
+        }
+        if (o.kind == SF_OP_COND) {
+            uint64_t mask;
+            std::memcpy(&mask, &o.param, sizeof(mask));
+            if (__builtin_popcountll(bits & mask) & 1) gates.push_back(sf_gate{o.arg, o.q0, o.q1, 0u});
+            i++;
+            continue;
+        }
+        // measurement: outcome 1 iff the caller's draw is below p(1), then collapse
+        sf_status st = flush();
+        double p0 = 0.0, p1 = 0.0;
+        if (!st) st = sf_measure(h, o.q0, -1, &p0, &p1);
+        const int x = o.param < p1 ? 1 : 0;
+        if (!st) st = sf_measure(h, o.q0, x, nullptr, nullptr);
+        if (st) return st;
+        if (x) bits |= 1ull << done_m;
+        done_m++;
+        i++;
+    }
+    sf_status st = flush();
+    if (st) return st;
+    if (outcomes) *outcomes = bits;
+    if (n_meas) *n_meas = done_m;
+    return SF_OK;
+}
+
+sf_status sf_grid_program_bytes(sf_handle h, uint64_t* bytes) {
+    if (!h || !bytes) return fail(h, SF_EINVAL, "NULL argument");
+    if (!h->d.gp) return fail(h, SF_EINVAL, "no grid program on this handle (n_qubits > 63)");
+    SF_CK(h, sf_gprog_moved(h->d, h->hk, h->stream));
+    sf_status st = sync_check(h);
+    if (st) return st;
+    *bytes = h->hk[0];
+    return SF_OK;
+}
+
+sf_status sf_set_trace(sf_handle h, int32_t on) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    h->trace = on ? 1 : 0;
+    return SF_OK;
+}
+
+sf_status sf_grid_program_trace(sf_handle h, uint64_t* rec, uint32_t cap, uint32_t* n) {
+    if (!h || !n || (cap && !rec)) return fail(h, SF_EINVAL, "NULL argument");
+    if (!h->d.gp) return fail(h, SF_EINVAL, "no grid program on this handle (n_qubits > 63)");
+    sf_status st = sync_check(h);
+    if (st) return st;
+    unsigned m = 0;
+    std::vector<uint64_t> base((size_t)cap * 5), marks((size_t)cap * 8);
+    SF_CK(h, sf_gprog_trace(h->d, base.data(), cap, &m, h->stream));
+    SF_CK(h, sf_gprog_marks(h->d, marks.data(), m, h->stream));
+    SF_CK(h, cudaStreamSynchronize(h->stream));
+    for (unsigned i = 0; i < m; i++) {
+        std::memcpy(rec + 13 * (size_t)i, base.data() + 5 * (size_t)i, 5 * sizeof(uint64_t));
+        std::memcpy(rec + 13 * (size_t)i + 5, marks.data() + 8 * (size_t)i, 8 * sizeof(uint64_t));
+    }
+    *n = m;
+    return SF_OK;
+}
+
+sf_status sf_set_wait_limit(sf_handle h, uint32_t polls) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    h->wait_limit = polls;
     return SF_OK;
 }
 
@@ -703,15 +896,17 @@ uint32_t sf_words(sf_handle h) { return h ? (uint32_t)h->Wabi : 0u; }
 
 uint32_t sf_host_state(sf_handle h) {
     if (!h) return 0u;
-    return (uint32_t)h->cur | ((uint32_t)h->idx_ok[0] << 1) | ((uint32_t)h->idx_ok[1] << 2);
+    return (uint32_t)h->cur | ((uint32_t)h->idx_ok[0] << 1) | ((uint32_t)h->idx_ok[1] << 2) |
+           ((uint32_t)h->hull << 3);
 }
 
 sf_status sf_set_host_state(sf_handle h, uint32_t token) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
-    if (token > 7u) return fail(h, SF_EINVAL, "invalid host-state token");
+    if (token > 31u || (token >> 3) > 2u) return fail(h, SF_EINVAL, "invalid host-state token");
     h->cur = (int)(token & 1u);
     h->idx_ok[0] = (token >> 1) & 1u;
     h->idx_ok[1] = (token >> 2) & 1u;
+    h->hull = (int)(token >> 3);
     return SF_OK;
 }
 

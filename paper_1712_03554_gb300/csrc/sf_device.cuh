@@ -425,8 +425,16 @@ void sf_launch_segment(const SfDev& d, const void* ops, unsigned long long n_ops
 size_t sf_segment_smem_bytes(unsigned seg_cap);
 size_t sf_gprog_work_words();
 cudaError_t sf_gprog_reset(const SfDev& d, cudaStream_t s);
+cudaError_t sf_gprog_moved(const SfDev& d, unsigned long long* host, cudaStream_t s);
+// hull_state: 0 unknown, 1 kept in the workspace by the last launch, 2 the
+// frame is one element; spin_limit: polls of a grid barrier before it gives
+// up; trace: record per-phase times in the workspace; trig: n_ops entries of
+// scratch for e^{i theta} of the diagonal records
 cudaError_t sf_launch_gprog(const SfDev& d, const void* ops, unsigned long long n_ops, double eps2, int cur,
+                            int idx_ok, int hull_state, unsigned spin_limit, int trace, double2* trig,
                             unsigned long long* consumed, cudaStream_t s);
+cudaError_t sf_gprog_trace(const SfDev& d, uint64_t* host, unsigned cap, unsigned* n, cudaStream_t s);
+cudaError_t sf_gprog_marks(const SfDev& d, uint64_t* host, unsigned m, cudaStream_t s);
 size_t sf_tableau_smem_bytes(int n, int W, int NT);
 
 void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s);

@@ -11,24 +11,36 @@
 //                  (Sec. III, Table 2) and publishes the run's affine map
 //                  sigma' = A sigma ^ t; while it inverts A, the other warps of
 //                  CTA 0 plan the diagonal records that follow (one each);
-//                  barrier.  The map itself is applied by the next merge
-//                  (partners at A^-1 u, sign patterns from A^T v); any other
-//                  follower gets a pass that rewrites and re-indexes the
-//                  phase vectors first.
+//                  barrier.  The map itself is applied by the next pass over
+//                  the elements.
 //   diagonal run   records not planned yet are planned at once, CTA c
 //                  planning record c (Sec. IV: Z^w = eps D^u M^v per term,
 //                  grouped by u, half table of group coefficients); barrier;
-//                  then per record every CTA merges its share of the elements
-//                  into the other buffer (owner rule, outputs reserved with one
-//                  atomic per block, inserted into the output index); barrier.
-//                  Once a merge drops nothing the frame is closed under its
-//                  mask, and the following gates that keep it closed are
-//                  applied in place to each pair's amplitudes in one pass.
+//                  then the records are applied in passes over the frame.
+//
+// Passes over the frame.  Every CTA keeps the frame's linear hull -- the span
+// of the differences of its phase vectors -- as parity constraints (c . d = 0
+// for every difference d), updated identically in every CTA: a Clifford map
+// moves them, a branch along a new direction adds it.  A diagonal gate whose
+// two groups differ by a mask u outside the hull has no partners in the frame
+// (s ^ u is never a phase vector of it): each element writes its two children
+// in place, s at its own position j and s ^ u at j + k, with no index and no
+// atomics, and the records that follow and keep each pair {s, s ^ u} (a phase
+// per element, or the same mask) are applied to the pair in the same pass.
+// The directions of such passes and their strides are remembered while no
+// element moves, so later gates along them find each partner by position.
+// Gates whose masks lie in the hull go through the phase-vector index: each
+// element looks up its partners, one thread owns each output and the outputs
+// are reserved with one atomic per block (merge), or, when the frame is
+// closed under the mask, the pair is updated in place.  The index is built
+// only when a pass needs it.
 //
 // A measurement or conditional record ends the program (the caller continues
 // per op).  Data written inside the launch by other CTAs is read through L2
 // (ld.global.cg), never through the non-coherent or L1 paths.  Every barrier
 // wait is bounded: on expiry the kernel sets SF_ST_TIMEOUT and returns.
+#include <algorithm>
+
 #include "sf.h"
 #include "sf_warp.cuh"
 
@@ -38,26 +50,42 @@ namespace {
 
 constexpr int kGpThreads = 512;
 constexpr int kGpPlans = 32;              // diagonal records planned per batch
-constexpr unsigned kGpSpinLimit = 1u << 20;  // barrier polls (100 ns apart) before giving up
+constexpr int kGpTrace = 512;             // phases recorded by a traced launch
 
 struct GpPlan {
     BrTab P;
     double2 ctab[4][16];
 };
 
-// device workspace, zeroed at handle creation; err, drop and ocnt are
-// cleared before every launch
+// device workspace, zeroed at handle creation; err, drop, ocnt, fk and moved
+// are cleared before every launch
 struct GpWork {
     unsigned int bar_count, bar_gen;
     unsigned int err[3];         // a failed check in phase p (between barriers p and p + 1): err[p % 3]
     unsigned int drop[3];        // an amplitude dropped in phase p: drop[p % 3]
     unsigned long long ocnt[3];  // output counters of consecutive merges, rotating
-    unsigned long long oe;       // end of the current Clifford run
-    unsigned int npre;           // diagonal records after it already planned into plans[0 .. npre)
-    uint64_t AT[64];             // affine map of the current Clifford run: column j = image of e_j
-    uint64_t t;
-    uint64_t Ainv[64];           // rows of the inverse of its linear part
-    GpPlan plans[kGpPlans];
+    unsigned long long fk[3][2]; // children kept by consecutive in-place branch passes (s, s ^ u), rotating
+    unsigned long long moved;    // element bytes read and written by this launch's passes
+    unsigned long long cleared_end;
+    uint64_t hull[64];           // the frame's hull constraints at the end of the last launch
+    uint64_t hbasis[64];         // and directions spanning the hull
+    unsigned int nhb;
+    unsigned int ntrace;         // phases recorded by the last traced launch
+    // per phase of a traced launch: what ran (code | elements << 8), CTA 0's
+    // start and arrival time, the last arrival's time and CTA (ns, %globaltimer)
+    uint64_t trace[kGpTrace][5];
+    uint64_t marks[kGpTrace][8];  // checkpoints inside each traced phase (CTA 0)
+};
+
+// The tableau of the launch.  Every CTA keeps its own copy in shared memory
+// and applies the same Clifford runs to it (the work is deterministic, so the
+// copies agree); CTA 0 writes it back at the end.
+struct GpTab {
+    uint64_t mx[64], mz[64], dx[64], dz[64];
+    uint32_t de[64];
+    int piv[64];
+    int rx;       // X-block size
+    double2 g;    // global phase
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -66,8 +94,32 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-__shared__ unsigned s_phase;  // phase of the grid program this CTA is in
-__shared__ int s_drop;        // an amplitude was dropped in the phase that ended at the last barrier
+__shared__ unsigned s_phase;   // phase of the grid program this CTA is in
+__shared__ int s_drop;         // an amplitude was dropped in the phase that ended at the last barrier
+__shared__ unsigned s_spin;    // barrier polls before giving up
+__shared__ int s_trace;        // record per-phase times
+__shared__ unsigned s_gen0;    // barrier generation at launch start
+__shared__ uint64_t s_tstart;  // CTA 0: when the current phase started
+__shared__ uint64_t s_code;    // CTA 0: what the current phase runs
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// checkpoint i of the current phase (traced launches, CTA 0, one thread)
+__device__ __forceinline__ void gp_mark(GpWork* w, int i) {
+    if (s_trace && blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned ti = s_phase - s_gen0;
+        if (ti < (unsigned)kGpTrace) w->marks[ti][i] = gtimer();
+    }
+}
+
+// the phase about to end ran `code` over k elements (traced launches, CTA 0)
+__device__ __forceinline__ void gp_phase(int code, unsigned long long k) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s_code = (uint64_t)code | ((uint64_t)k << 8);
+}
 
 // a failed check of this CTA: every CTA stops at the next barrier
 __device__ __forceinline__ void gp_fail(GpWork* w) { atomicExch(&w->err[s_phase % 3], 1u); }
@@ -76,10 +128,11 @@ __device__ __forceinline__ void gp_dropped(GpWork* w) { atomicExch(&w->drop[s_ph
 
 // Grid barrier: every CTA passes the same sequence of barriers.  Thread 0
 // arrives with one atomic; the last arrival resets the count and bumps the
-// generation, the others poll it with a bound.  Returns false in every
-// thread of every CTA if a check failed in the phase that ends here, and in
-// the CTA whose wait ran out.  The error word of a phase is cleared two
-// phases ahead, once every CTA has read it.
+// generation, the others poll it, at most s_spin times.  Returns false in
+// every thread of every CTA if a check failed in the phase that ends here, and
+// in the CTA whose wait ran out (which also fails the phase, so that a CTA
+// still passing this barrier stops at its next one).  The error word of a
+// phase is cleared two phases ahead, once every CTA has read it.
 __device__ bool gp_barrier(GpWork* w, unsigned& gen, uint32_t* status, int buf) {
     __shared__ int s_ok;
     __syncthreads();
@@ -87,22 +140,40 @@ __device__ bool gp_barrier(GpWork* w, unsigned& gen, uint32_t* status, int buf) 
         __threadfence();
         const unsigned g = gen;
         int ok = 1;
+        const uint64_t t_arr = s_trace ? gtimer() : 0;
+        const unsigned ti = g - s_gen0;
+        if (s_trace && blockIdx.x == 0 && ti < (unsigned)kGpTrace) {
+            w->trace[ti][0] = s_code;
+            w->trace[ti][1] = s_tstart;
+            w->trace[ti][2] = t_arr;
+        }
         if (atomicAdd(&w->bar_count, 1u) == gridDim.x - 1) {
+            if (s_trace && ti < (unsigned)kGpTrace) {
+                w->trace[ti][3] = t_arr;
+                w->trace[ti][4] = blockIdx.x;
+            }
             w->bar_count = 0;
             __threadfence();
             atomicExch(&w->bar_gen, g + 1);
         } else {
             unsigned spins = 0;
             while (ld_acquire(&w->bar_gen) == g) {
-                if (++spins > kGpSpinLimit) {
+                if (++spins > s_spin) {
                     ok = 0;
                     break;
                 }
                 __nanosleep(100);
             }
         }
+        if (s_trace && blockIdx.x == 0) {
+            s_tstart = gtimer();
+            s_code = 0;
+        }
         __threadfence();
-        if (!ok) set_status(status, SF_ST_TIMEOUT, buf, 40u);
+        if (!ok) {
+            set_status(status, SF_ST_TIMEOUT, buf, 40u);
+            atomicExch(&w->err[g % 3], 1u);
+        }
         if (__ldcg(&w->err[g % 3])) ok = 0;
         s_drop = __ldcg(&w->drop[g % 3]) != 0;
         if (blockIdx.x == 0) w->err[(g + 2) % 3] = w->drop[(g + 2) % 3] = 0;
@@ -112,6 +183,33 @@ __device__ bool gp_barrier(GpWork* w, unsigned& gen, uint32_t* status, int buf) 
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// ---- the frame's hull (span of the differences of its phase vectors) ------------
+// kept as up to 64 parity constraints c (c . d = 0 for every difference d);
+// zero constraints say nothing.  All of a CTA's threads read the same values.
+
+// u lies outside the hull: some constraint has odd parity with it (per warp, no sync)
+__device__ __forceinline__ bool hull_fresh(const uint64_t* hc, uint64_t u) {
+    const int lane = threadIdx.x & 31;
+    const bool odd = (__popcll(hc[lane] & u) & 1) | (__popcll(hc[lane + 32] & u) & 1);
+    return __any_sync(SF_FULL, odd);
+}
+
+// the hull grows by u (warp 0; the caller synchronises the block afterwards):
+// one constraint with odd parity is added to the other odd ones and dropped
+__device__ __forceinline__ void hull_add(uint64_t* hc, uint64_t u) {
+    const int lane = threadIdx.x & 31;
+    uint64_t c0 = hc[lane], c1 = hc[lane + 32];
+    const bool o0 = __popcll(c0 & u) & 1, o1 = __popcll(c1 & u) & 1;
+    const unsigned b0 = __ballot_sync(SF_FULL, o0), b1 = __ballot_sync(SF_FULL, o1);
+    if (!(b0 | b1)) return;
+    const int p = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+    const uint64_t cp = __shfl_sync(SF_FULL, p < 32 ? c0 : c1, p & 31);
+    if (o0) c0 ^= cp;
+    if (o1) c1 ^= cp;
+    hc[lane] = c0;
+    hc[lane + 32] = c1;
 }
 
 // position of key in the index of buffer b (written in this launch), or -1.
@@ -134,29 +232,33 @@ __device__ __forceinline__ long long gp_find(const SfDev& d, int b, unsigned lon
     return -1;
 }
 
-// ROTATE over the run of Clifford records from oi (warp 0 of CTA 0): the
-// tableau in registers, written back with the X-block size and global phase;
-// the composed affine map goes to the workspace, the run's end to w->oe.
-__device__ void gp_clifford_run(const SfDev& d, GpWork* w, const OpRec* ops, unsigned long long oi,
-                                unsigned long long o1, Row* stage, uint64_t* arows, int buf) {
-    const int n = d.n, lane = threadIdx.x & 31;
+// ROTATE over the run of Clifford records from oi (warp 0 of a CTA) on the
+// CTA's tableau: the rows in registers, written back with the X-block size and
+// global phase.  The composed affine map sigma' = A sigma ^ t goes to at
+// (column j = image of e_j) and *t, the rows of A to arows; returns the run's
+// end, or ~0 if a tableau check failed.
+__device__ unsigned long long gp_clifford_run(GpTab& T, const OpRec* ops, unsigned long long oi,
+                                              unsigned long long o1, int n, Row* stage, uint64_t* at,
+                                              uint64_t* arows, uint64_t* t_out) {
+    const int lane = threadIdx.x & 31;
     Row r[2];
     for (int hf = 0; hf < 2; hf++) {
         const int row = lane + 32 * hf;
         const bool in = row < n;
-        r[hf].mx = in ? __ldcg(&d.mx[row]) : 0;
-        r[hf].mz = in ? __ldcg(&d.mz[row]) : 0;
-        r[hf].dx = in ? __ldcg(&d.dx[row]) : 0;
-        r[hf].dz = in ? __ldcg(&d.dz[row]) : 0;
-        r[hf].de = in ? __ldcg(&d.de[row]) : 0;
-        r[hf].piv = in ? __ldcg(&d.piv[row]) : 0x7fffffff;
+        r[hf].mx = in ? T.mx[row] : 0;
+        r[hf].mz = in ? T.mz[row] : 0;
+        r[hf].dx = in ? T.dx[row] : 0;
+        r[hf].dz = in ? T.dz[row] : 0;
+        r[hf].de = in ? T.de[row] : 0;
+        r[hf].piv = in ? T.piv[row] : 0x7fffffff;
         r[hf].A = in ? (1ull << row) : 0;
         r[hf].t0 = 0;
         r[hf].t1 = 0;
     }
-    int rx = __ldcg(&d.meta[0]);
+    int rx = T.rx;
     int ga = 0, gb = 0;  // the run's phase factor omega^ga sqrt(2)^gb
     unsigned long long gi = oi;
+    bool good = true;
     // records are read 32 at a time, lane L holding record wb + L
     unsigned long long wb = gi;
     OpRec wr;
@@ -174,10 +276,7 @@ __device__ void gp_clifford_run(const SfDev& d, GpWork* w, const OpRec* ops, uns
         const int q0 = (int)__shfl_sync(SF_FULL, wr.q0, src);
         const int q1 = kind >= 6 ? (int)__shfl_sync(SF_FULL, wr.q1, src) : 0;
         if (!warp_clifford_gate(r, n, rx, (int)kind, q0, q1, stage, ga, gb)) {
-            if (lane == 0) {
-                set_status(d.status, SF_ST_INTERNAL, buf, 41u);
-                gp_fail(w);
-            }
+            good = false;
             break;
         }
         gi++;
@@ -185,55 +284,62 @@ __device__ void gp_clifford_run(const SfDev& d, GpWork* w, const OpRec* ops, uns
     for (int hf = 0; hf < 2; hf++) {
         const int row = lane + 32 * hf;
         if (row < n) {
-            d.mx[row] = r[hf].mx;
-            d.mz[row] = r[hf].mz;
-            d.dx[row] = r[hf].dx;
-            d.dz[row] = r[hf].dz;
-            d.de[row] = r[hf].de;
-            d.piv[row] = r[hf].piv;
+            T.mx[row] = r[hf].mx;
+            T.mz[row] = r[hf].mz;
+            T.dx[row] = r[hf].dx;
+            T.dz[row] = r[hf].dz;
+            T.de[row] = r[hf].de;
+            T.piv[row] = r[hf].piv;
+            arows[row] = r[hf].A;
         }
     }
     for (int j = 0; j < n; j++) {
         const unsigned b0 = __ballot_sync(SF_FULL, lane < n && ((r[0].A >> j) & 1));
         const unsigned b1 = __ballot_sync(SF_FULL, lane + 32 < n && ((r[1].A >> j) & 1));
-        if (lane == 0) w->AT[j] = (uint64_t)b0 | ((uint64_t)b1 << 32);
+        if (lane == 0) at[j] = (uint64_t)b0 | ((uint64_t)b1 << 32);
     }
-    // rows of A, inverted next while other warps plan
-    for (int hf = 0; hf < 2; hf++)
-        if (lane + 32 * hf < n) arows[lane + 32 * hf] = r[hf].A;
     const unsigned t0 = __ballot_sync(SF_FULL, lane < n && r[0].t0);
     const unsigned t1 = __ballot_sync(SF_FULL, lane + 32 < n && r[1].t0);
     if (lane == 0) {
-        w->t = (uint64_t)t0 | ((uint64_t)t1 << 32);
-        d.meta[0] = rx;
-        *d.g = cmul(*d.g, cliff_factor(ga, gb));
-        w->oe = gi;
+        *t_out = (uint64_t)t0 | ((uint64_t)t1 << 32);
+        T.rx = rx;
+        T.g = cmul(T.g, cliff_factor(ga, gb));
     }
+    __syncwarp();
+    return good ? gi : ~0ull;
 }
 
-// Plan of diagonal record o (warp 0 of one CTA) into the workspace.
-__device__ void gp_plan(const SfDev& d, const OpRec& o, GpPlan& sp, GpPlan* out) {
-    const int n = d.n, lane = threadIdx.x & 31;
+// Plan of diagonal record o (one warp) from the CTA's tableau, with its
+// e^{i theta} = cs + i sn from the launch's table
+__device__ void gp_plan(const GpTab& T, int n, const OpRec& o, double2 trig, GpPlan& out) {
+    const int lane = threadIdx.x & 31;
     Row r[2];
     for (int hf = 0; hf < 2; hf++) {
         const int row = lane + 32 * hf;
         const bool in = row < n;
-        r[hf].mx = in ? __ldcg(&d.mx[row]) : 0;
-        r[hf].mz = in ? __ldcg(&d.mz[row]) : 0;
-        r[hf].dx = in ? __ldcg(&d.dx[row]) : 0;
-        r[hf].dz = in ? __ldcg(&d.dz[row]) : 0;
-        r[hf].de = in ? __ldcg(&d.de[row]) : 0;
+        r[hf].mx = in ? T.mx[row] : 0;
+        r[hf].mz = in ? T.mz[row] : 0;
+        r[hf].dx = in ? T.dx[row] : 0;
+        r[hf].dz = in ? T.dz[row] : 0;
+        r[hf].de = in ? T.de[row] : 0;
     }
     const uint32_t kind = o.kind - SF_OP_DIAG;
-    const double th = kind == 0 ? 0.78539816339744830962 : (kind == 1 ? -0.78539816339744830962 : o.param);
-    double sn, cs;
-    sincos(th, &sn, &cs);
-    const SfTerms T = diag_terms(kind, cs, sn);
-    warp_branch_plan_regs(r, n, kind, (int)o.q0, kind == 3 ? (int)o.q1 : 0, T.c, sp.P, sp.ctab);
+    const SfTerms Tm = diag_terms(kind, trig.x, trig.y);
+    warp_branch_plan_regs(r, n, kind, (int)o.q0, kind == 3 ? (int)o.q1 : 0, Tm.c, out.P, out.ctab);
     __syncwarp();
-    const uint64_t* src = reinterpret_cast<const uint64_t*>(&sp);
-    uint64_t* dst = reinterpret_cast<uint64_t*>(out);
-    for (int i = lane; i < (int)(sizeof(GpPlan) / 8); i += 32) dst[i] = src[i];
+}
+
+// number of consecutive diagonal records from ri, at most kGpPlans (every lane)
+__device__ __forceinline__ int diag_count(const OpRec* ops, unsigned long long ri, unsigned long long n_ops) {
+    const int lane = threadIdx.x & 31;
+    bool dg = false;
+    if (ri + lane < n_ops) {
+        const uint32_t kk = ops[ri + lane].kind;
+        dg = kk >= SF_OP_DIAG && kk <= SF_OP_DIAG + 3;
+    }
+    const unsigned bl = __ballot_sync(SF_FULL, dg);
+    const int nb = bl == SF_FULL ? 32 : __ffs(~bl) - 1;
+    return nb < kGpPlans ? nb : kGpPlans;
 }
 
 // elements [lo, hi) of CTA b: contiguous chunks, whole warps, all CTAs busy
@@ -243,23 +349,160 @@ __device__ __forceinline__ void gp_chunk(unsigned long long k, unsigned long lon
     hi = min(k, lo + per);
 }
 
+// One record r of an in-place run applied to the pair (s0, a0), (s1, a1) with
+// s1 = s0 ^ u (u the mask of its second group, if it has one): each output
+// sums its own group-0 term and its partner's group-1 term, in that order (the
+// order of the per-gate merge).  A missing partner enters with a1 = 0.
+// Without kPairs only (s0, a0) is updated (every record has one group).
+template <bool kPairs>
+__device__ __forceinline__ void pair_step(const GpPlan& pl, uint64_t s0, uint64_t s1, double2& a0, double2& a1) {
+    const BrTab& Q = pl.P;
+    double2 n0 = make_double2(0.0, 0.0);
+    cmul_acc(n0, half_coef(Q, pl.ctab, 0, s0), a0);
+    if (kPairs) {
+        double2 n1 = make_double2(0.0, 0.0);
+        if (Q.ng == 2) cmul_acc(n0, half_coef(Q, pl.ctab, 1, s1), a1);
+        cmul_acc(n1, half_coef(Q, pl.ctab, 0, s1), a1);
+        if (Q.ng == 2) cmul_acc(n1, half_coef(Q, pl.ctab, 1, s0), a0);
+        a1 = n1;
+    }
+    a0 = n0;
+}
+
+// ---- runs whose coefficients do not depend on the element ------------------------
+// A term's sign pattern bit parity(v . s) is the same for every phase vector s
+// of the frame when v is orthogonal to every direction of the hull (the
+// differences of the frame's phase vectors).  When that holds for every term
+// of every record of a run, each record acts on the pair (s, s ^ u) through one
+// 2x2 matrix for the whole frame, and the run is their product, formed once by
+// a warp as a tree (5 levels instead of one dependent step per record); each
+// element then takes a single 2x2 product.
+
+struct Cm2 {  // 2x2 complex matrix (a0', a1') = M (a0, a1)
+    double2 m00, m01, m10, m11;
+};
+
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a * b + c
+    double2 r;
+    r.x = fma(a.x, b.x, c.x);
+    r.x = fma(-a.y, b.y, r.x);
+    r.y = fma(a.x, b.y, c.y);
+    r.y = fma(a.y, b.x, r.y);
+    return r;
+}
+__device__ __forceinline__ double2 cprod(double2 a, double2 b) { return cfma(a, b, make_double2(0.0, 0.0)); }
+
+__device__ __forceinline__ Cm2 cm2_mul(const Cm2& x, const Cm2& y) {  // x * y
+    Cm2 r;
+    r.m00 = cfma(x.m01, y.m10, cprod(x.m00, y.m00));
+    r.m01 = cfma(x.m01, y.m11, cprod(x.m00, y.m01));
+    r.m10 = cfma(x.m11, y.m10, cprod(x.m10, y.m00));
+    r.m11 = cfma(x.m11, y.m11, cprod(x.m10, y.m01));
+    return r;
+}
+
+__device__ __forceinline__ double2 shfl_down_c(double2 v, int off) {
+    return make_double2(__shfl_down_sync(SF_FULL, v.x, off), __shfl_down_sync(SF_FULL, v.y, off));
+}
+
+// Warp 0: if every term of records [r0, r1) (at most 32) is orthogonal to the
+// hull directions hb[0 .. nhb), the product of their pair matrices at
+// (s0, s0 ^ u) into *out and true (every lane); otherwise false.
+__device__ bool uniform_run(const GpPlan* spl, int r0, int r1, const uint64_t* hb, int nhb, uint64_t s0, uint64_t u,
+                            Cm2* out) {
+    const int lane = threadIdx.x & 31;
+    const int r = r0 + lane;
+    bool uni = true;
+    Cm2 M;
+    M.m00 = M.m11 = make_double2(1.0, 0.0);
+    M.m01 = M.m10 = make_double2(0.0, 0.0);
+    if (r < r1) {
+        const BrTab& Q = spl[r].P;
+        for (int g = 0; g < Q.ng && uni; g++)
+            for (int t = 0; t < Q.nt[g] && uni; t++)
+                for (int i = 0; i < nhb; i++)
+                    if (__popcll(Q.v[g][t] & hb[i]) & 1) {
+                        uni = false;
+                        break;
+                    }
+        const uint64_t s1 = s0 ^ u;
+        M.m00 = half_coef(Q, spl[r].ctab, 0, s0);
+        M.m11 = half_coef(Q, spl[r].ctab, 0, s1);
+        if (Q.ng == 2) {
+            M.m01 = half_coef(Q, spl[r].ctab, 1, s1);
+            M.m10 = half_coef(Q, spl[r].ctab, 1, s0);
+        }
+    }
+    if (!__all_sync(SF_FULL, uni)) return false;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        Cm2 o;
+        o.m00 = shfl_down_c(M.m00, off);
+        o.m01 = shfl_down_c(M.m01, off);
+        o.m10 = shfl_down_c(M.m10, off);
+        o.m11 = shfl_down_c(M.m11, off);
+        if ((lane & (2 * off - 1)) == 0) M = cm2_mul(o, M);  // later records on the left
+    }
+    if (lane == 0) *out = M;
+    __syncwarp();
+    return true;
+}
+
+// kept-children counts of a warp added to the pass's counters
+__device__ __forceinline__ void add_counts(unsigned long long* ctr, unsigned c0, unsigned c1) {
+    c0 = __reduce_add_sync(SF_FULL, c0);
+    c1 = __reduce_add_sync(SF_FULL, c1);
+    if ((threadIdx.x & 31) == 0) {
+        if (c0) atomicAdd(&ctr[0], (unsigned long long)c0);
+        if (c1) atomicAdd(&ctr[1], (unsigned long long)c1);
+    }
+}
+
+// hull_state: 0 nothing known about the frame's hull, 1 the constraints in
+// w->hull hold, 2 the frame is one element (the hull is {0}).  idx_ok0: the
+// index of buffer cur0 is valid.
 __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const OpRec* ops, unsigned long long n_ops,
-                                                      double eps2, int cur0, unsigned long long* consumed) {
+                                                      double eps2, int cur0, int idx_ok0, int hull_state,
+                                                      unsigned spin_limit, int trace, double2* trig,
+                                                      unsigned long long* consumed) {
     extern __shared__ GpPlan spl[];  // [kGpPlans]: the plans of the current diagonal run
-    __shared__ GpPlan sp;            // scratch of the planning warp
     __shared__ BrTab pm;             // a plan moved to the coordinates before a pending affine map
+    __shared__ GpTab s_tab;          // this CTA's copy of the tableau
+    // the last Clifford run's map: columns of A, rows of A^-1 (first the rows of A), t
     __shared__ uint64_t s_ainv[64], s_at[64];
+    __shared__ uint64_t s_t;
+    __shared__ unsigned long long s_oe;
     __shared__ uint64_t tab[16 * 16];
     __shared__ Row stage[64];
     __shared__ unsigned int wsum[kGpThreads / 32];
     __shared__ unsigned long long bbase;
-    __shared__ int s_nb;
+    __shared__ int s_inv_ok;
+    __shared__ uint64_t s_hc[64];            // hull constraints
+    __shared__ uint64_t s_hb[64];            // directions spanning the hull
+    __shared__ int s_nhb;
+    __shared__ Cm2 s_comp;                   // product of a run's pair matrices
+    __shared__ int s_uni;                    // ... valid for the current pass
+    __shared__ uint64_t s_ref;               // a phase vector of the frame (new coordinates)
+    __shared__ uint64_t s_pu[64];            // directions whose partners are found by position ...
+    __shared__ unsigned long long s_pk[64];  // ... and their strides
     if (*(volatile uint32_t*)d.status) return;
     const int n = d.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned gen = 0;
     if (threadIdx.x == 0) {
         gen = ld_acquire(&w->bar_gen);
         s_phase = gen;
+        s_spin = spin_limit;
+        s_trace = trace;
+        s_gen0 = gen;
+        s_tstart = trace ? gtimer() : 0;
+        s_code = 0;
+    }
+    if (threadIdx.x < 64) {
+        const int i = threadIdx.x;
+        s_hc[i] = hull_state == 2 ? (i < n ? 1ull << i : 0ull) : (hull_state == 1 ? __ldcg(&w->hull[i]) : 0ull);
+        // nothing known: every unit vector may be a direction of the hull
+        s_hb[i] = hull_state == 1 ? __ldcg(&w->hbasis[i]) : (hull_state == 0 && i < n ? 1ull << i : 0ull);
+        if (i == 0) s_nhb = hull_state == 1 ? (int)__ldcg(&w->nhb) : (hull_state == 0 ? n : 0);
     }
     __syncthreads();
     // every record is checked before anything is touched
@@ -274,28 +517,60 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             if (o.kind == SF_OP_COND) ok &= o.arg <= 8;
             else ok &= k <= 8 || (k >= SF_OP_DIAG && k <= SF_OP_DIAG + 3) || k == SF_OP_MEASURE;
             bad |= !ok;
+            // e^{i theta} of every diagonal record, computed once here, spread over
+            // the grid (the double-precision pipe of one SM is narrow)
+            if (ok && o.kind >= SF_OP_DIAG && o.kind <= SF_OP_DIAG + 3) {
+                const uint32_t kd = o.kind - SF_OP_DIAG;
+                const double th = kd == 0 ? 0.78539816339744830962 : (kd == 1 ? -0.78539816339744830962 : o.param);
+                double sn, cs;
+                sincos(th, &sn, &cs);
+                trig[i] = make_double2(cs, sn);
+            }
         }
         if (__syncthreads_or(bad) && threadIdx.x == 0) {
             set_status(d.status, 1u, cur0, 42u);  // SF_EINVAL: bad record
             gp_fail(w);
         }
+        gp_phase(10, n_ops);
         if (!gp_barrier(w, gen, d.status, cur0)) return;
     }
+    for (int row = threadIdx.x; row < n; row += blockDim.x) {
+        s_tab.mx[row] = __ldcg(&d.mx[row]);
+        s_tab.mz[row] = __ldcg(&d.mz[row]);
+        s_tab.dx[row] = __ldcg(&d.dx[row]);
+        s_tab.dz[row] = __ldcg(&d.dz[row]);
+        s_tab.de[row] = __ldcg(&d.de[row]);
+        s_tab.piv[row] = __ldcg(&d.piv[row]);
+    }
+    if (threadIdx.x == 0) {
+        s_tab.rx = __ldcg(&d.meta[0]);
+        s_tab.g = __ldcg(d.g);
+    }
+    __syncthreads();
     int cur = cur0;
     unsigned long long k = d.kcnt[cur0];
     uint32_t tag[2] = {d.itag[0], d.itag[1]};
     unsigned long long isz[2] = {d.isize[0], d.isize[1]};
+    bool ivalid[2] = {false, false};  // the index of buffer b describes its current contents
+    ivalid[cur0] = idx_ok0 != 0;
     unsigned long long oi = 0;
-    unsigned nmerge = 0;
+    unsigned nmerge = 0, nfresh = 0;
+    int npos = 0;         // entries of s_pu / s_pk
     bool ok = true;
     bool have_u = false;  // the frame is closed under the mask cu (s in F => s ^ cu in F)
     uint64_t cu = 0;
     unsigned npre = 0;    // records at oi planned by the last Clifford phase
     // The last Clifford run's map sigma' = A sigma ^ t is not yet applied to the
-    // phase vectors (the tableau is already new); the next merge applies it.
+    // phase vectors (the tableau is already new); the next pass over the
+    // elements applies it.  The hull and the positional directions are kept in
+    // the new coordinates from the Clifford phase on.
     bool aff = false;
     const int nc = (n + 3) >> 2;
     uint64_t tw = 0;
+    // element bytes of a pass (phase vector 8 B, amplitude 16 B), counted once
+    auto account = [&](unsigned long long bytes) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) w->moved += bytes;
+    };
     // 4-bit lookup tables of the pending map (columns of A from the workspace)
     auto affine_tables = [&]() {
         for (int e = threadIdx.x; e < nc * 16; e += blockDim.x) {
@@ -303,10 +578,10 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             uint64_t acc = 0;
 #pragma unroll
             for (int b = 0; b < 4; b++)
-                if (((v >> b) & 1) && 4 * c + b < n) acc ^= __ldcg(&w->AT[4 * c + b]);
+                if (((v >> b) & 1) && 4 * c + b < n) acc ^= s_at[4 * c + b];
             tab[e] = acc;
         }
-        tw = __ldcg(&w->t);
+        tw = s_t;
         __syncthreads();
     };
     auto affine_of = [&](uint64_t x) {
@@ -314,34 +589,159 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
         for (int c = 0; c < nc; c++) o ^= tab[c * 16 + ((x >> (4 * c)) & 15)];
         return o;
     };
-    // the map applied to every phase vector, which go into a fresh index
+    // the map applied to every phase vector in place (positions unchanged)
     auto affine_pass = [&]() {
         affine_tables();
-        const uint32_t tg = next_tag(tag[cur]);
-        const unsigned long long T = index_slots(k, d.icap);
         uint64_t* S = d.sig[cur];
         unsigned long long lo, hi;
         gp_chunk(k, lo, hi);
-        for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-            const uint64_t o = affine_of(__ldcg(&S[j]));
-            S[j] = o;
-            ok &= index_insert<1>(d, cur, T, tg, &o, (uint32_t)j);
+        for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x) S[j] = affine_of(__ldcg(&S[j]));
+        ivalid[cur] = false;
+        aff = false;
+        account(16 * k);
+    };
+    // the Clifford run's map moves the hull constraints (c -> A^-T c: the XOR of
+    // the rows of A^-1 that c selects) and the positional directions (u -> A u)
+    auto move_hull = [&]() {
+        uint64_t hc = 0, pu = 0;
+        const int i = threadIdx.x;
+        if (i < 64) {
+            const uint64_t c = s_hc[i];
+            for (int h = 0; h < n; h++)
+                if ((c >> h) & 1) hc ^= s_ainv[h];
+            if (i < npos) {
+                const uint64_t u = s_pu[i];
+                for (int j = 0; j < n; j++)
+                    if ((u >> j) & 1) pu ^= s_at[j];
+            }
         }
-        tag[cur] = tg;
-        isz[cur] = T;
+        uint64_t hb = 0;
+        if (i < s_nhb) {
+            const uint64_t u = s_hb[i];
+            for (int j = 0; j < n; j++)
+                if ((u >> j) & 1) hb ^= s_at[j];
+        }
+        __syncthreads();
+        if (i < 64) {
+            s_hc[i] = hc;
+            if (i < npos) s_pu[i] = pu;
+            if (i < s_nhb) s_hb[i] = hb;
+        }
+        __syncthreads();
+    };
+    // the hull grows by u (warp 0; the caller synchronises the block): a new
+    // direction joins the basis and removes one constraint
+    auto hull_grow = [&](uint64_t u) {
+        if (warp != 0) return;
+        if (!hull_fresh(s_hc, u)) return;
+        hull_add(s_hc, u);
+        if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = u;
+        __syncwarp();
+    };
+    // records [r0, r1) with frame-independent coefficients multiplied into
+    // s_comp (runs of three records or more, frames of one element or more);
+    // the pending map is applied to the reference phase vector when aff is set
+    // (its tables built).  Every thread learns whether it worked.
+    auto compose = [&](int r0, int r1, uint64_t u) {
+        if (threadIdx.x == 0) {
+            const uint64_t s = k ? __ldcg(&d.sig[cur][0]) : 0;
+            s_ref = aff ? affine_of(s) : s;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const bool uni = k && r1 - r0 >= 3 && uniform_run(spl, r0, r1, s_hb, s_nhb, s_ref, u, &s_comp);
+            if (lane == 0) s_uni = uni;
+        }
+        __syncthreads();
+        return s_uni != 0;
+    };
+    // stride of a direction with positional partners, or 0
+    auto pos_stride = [&](uint64_t u) {
+        unsigned long long st = 0;
+        for (int i = 0; i < npos; i++)
+            if (s_pu[i] == u) st = s_pk[i];
+        return st;
+    };
+    // the index of buffer b, built from its phase vectors as they are stored
+    auto build_index = [&](int b) {
+        const uint32_t tg = next_tag(tag[b]);
+        const unsigned long long T = index_slots(k, d.icap);
+        unsigned long long lo, hi;
+        gp_chunk(k, lo, hi);
+        for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+            const uint64_t s = __ldcg(&d.sig[b][j]);
+            ok &= index_insert<1>(d, b, T, tg, &s, (uint32_t)j);
+        }
+        tag[b] = tg;
+        isz[b] = T;
+        ivalid[b] = true;
+        account(8 * k);
+        gp_phase(7, k);
         if (!ok) {
-            set_status(d.status, SF_ST_TIMEOUT, cur, 43u);  // index full
+            set_status(d.status, SF_ST_TIMEOUT, b, 43u);  // index full
             gp_fail(w);
         }
-        aff = false;
+        return gp_barrier(w, gen, d.status, b);
+    };
+    // the elements of positions [0, m) of buffer cur with |a| >= eps, compacted
+    // into the other buffer (order of the reservations)
+    auto compact = [&](unsigned long long m, bool& moved) {
+        const int in = cur, out = cur ^ 1;
+        unsigned long long* ctr = &w->ocnt[nmerge % 3];
+        if (blockIdx.x == 0 && threadIdx.x == 0) w->ocnt[(nmerge + 1) % 3] = 0;
+        const unsigned long long kb = keep_bits(eps2);
+        unsigned long long lo, hi;
+        gp_chunk(m, lo, hi);
+        for (unsigned long long base = lo; base < hi; base += blockDim.x) {
+            const unsigned long long j = base + threadIdx.x;
+            const bool act = j < hi;
+            uint64_t s0 = 0;
+            double2 a = make_double2(0.0, 0.0);
+            if (act) {
+                s0 = __ldcg(&d.sig[in][j]);
+                a = __ldcg(&d.amp[in][j]);
+            }
+            const bool keep = act && amp_kept(a, kb, eps2);
+            const unsigned long long o = block_out_range(ctr, keep ? 1u : 0u, wsum, &bbase);
+            if (keep) {
+                d.sig[out][o] = s0;
+                d.amp[out][o] = a;
+            }
+        }
+        gp_phase(6, m);
+        moved = gp_barrier(w, gen, d.status, in);
+        k = __ldcg(ctr);
+        account(24 * (m + k));
+        cur = out;
+        ivalid[out] = false;
+        nmerge++;
+        have_u = false;
+        npos = 0;
     };
     // on a failed check: the frame stays in buffer cur (its count and the
     // index tags go back for the host's error path), and the launch ends
+    // the tableau of the launch back to the handle (CTA 0)
+    auto store_tableau = [&]() {
+        if (blockIdx.x != 0) return;
+        for (int row = threadIdx.x; row < n; row += blockDim.x) {
+            d.mx[row] = s_tab.mx[row];
+            d.mz[row] = s_tab.mz[row];
+            d.dx[row] = s_tab.dx[row];
+            d.dz[row] = s_tab.dz[row];
+            d.de[row] = s_tab.de[row];
+            d.piv[row] = s_tab.piv[row];
+        }
+        if (threadIdx.x == 0) {
+            d.meta[0] = s_tab.rx;
+            *d.g = s_tab.g;
+        }
+    };
     auto bail = [&]() {
+        store_tableau();
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             d.kcnt[cur] = k;
             for (int b = 0; b < 2; b++) {
-                d.itag[b] = tag[b];
+                d.itag[b] = ivalid[b] ? tag[b] : next_tag(tag[b]);
                 d.isize[b] = isz[b];
             }
         }
@@ -349,174 +749,277 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
     while (oi < n_ops) {
         const uint32_t kind = ops[oi].kind;
         if (kind <= 8) {
-            // ---- Clifford run: tableau in one warp of CTA 0, whose other warps then plan
-            // the diagonal records that follow (one record each) in the same phase;
-            // then the affine pass with a fresh index
-            if (blockIdx.x == 0) {
-                if (warp == 0) gp_clifford_run(d, w, ops, oi, n_ops, stage, s_ainv, cur);
-                __syncthreads();
-                if (warp == 0) {
-                    // rows of A^-1, for a merge that reads the phase vectors before the map
-                    const uint64_t av[2] = {lane < n ? s_ainv[lane] : 0, lane + 32 < n ? s_ainv[lane + 32] : 0};
-                    uint64_t iv[2];
-                    if (!warp_gf2_inverse(av, n, iv) && lane == 0) {
-                        set_status(d.status, SF_ST_INTERNAL, cur, 49u);
-                        gp_fail(w);
-                    }
-                    for (int hf = 0; hf < 2; hf++)
-                        if (lane + 32 * hf < n) w->Ainv[lane + 32 * hf] = iv[hf];
-                }
-                const unsigned long long oe = __ldcg(&w->oe);
-                const unsigned long long ri = oe + lane;
-                bool dg = false;
-                if (ri < n_ops) {
-                    const uint32_t kk = ops[ri].kind;
-                    dg = kk >= SF_OP_DIAG && kk <= SF_OP_DIAG + 3;
-                }
-                const unsigned bl = __ballot_sync(SF_FULL, dg);
-                int np = bl == SF_FULL ? 32 : __ffs(~bl) - 1;
-                np = np < (int)(blockDim.x >> 5) - 1 ? np : (int)(blockDim.x >> 5) - 1;
-                if (*(volatile uint32_t*)d.status) np = 0;
-                if (warp >= 1 && warp - 1 < np) gp_plan(d, ops[oe + warp - 1], spl[warp - 1], &w->plans[warp - 1]);
-                if (threadIdx.x == 0) w->npre = (unsigned)np;
+            // ---- Clifford run: every CTA applies it to its own tableau (one warp),
+            // then inverts the map (that warp) while its other warps plan the
+            // diagonal records that follow; no grid barrier, no global traffic
+            gp_mark(w, 0);
+            if (warp == 0) {
+                const unsigned long long oe = gp_clifford_run(s_tab, ops, oi, n_ops, n, stage, s_at, s_ainv, &s_t);
+                if (lane == 0) s_oe = oe;
             }
-            if (!gp_barrier(w, gen, d.status, cur)) return bail();
-            npre = __ldcg(&w->npre);
+            __syncthreads();
+            gp_mark(w, 1);
+            const unsigned long long oe = s_oe;
+            if (oe == ~0ull) {  // a tableau check failed (in every CTA alike)
+                if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, cur, 41u);
+                return bail();
+            }
+            const int np = diag_count(ops, oe, n_ops);
+            if (warp == 0) {
+                // rows of A^-1: for a merge that reads the phase vectors before the map,
+                // and for the hull constraints
+                const uint64_t av[2] = {lane < n ? s_ainv[lane] : 0, lane + 32 < n ? s_ainv[lane + 32] : 0};
+                uint64_t iv[2];
+                const bool inv_ok = warp_gf2_inverse(av, n, iv);
+                __syncwarp();
+                for (int hf = 0; hf < 2; hf++)
+                    if (lane + 32 * hf < n) s_ainv[lane + 32 * hf] = iv[hf];
+                if (lane == 0) s_inv_ok = inv_ok;
+            } else {
+                for (int r = warp - 1; r < np; r += (int)(blockDim.x >> 5) - 1)
+                    gp_plan(s_tab, n, ops[oe + r], __ldcg(&trig[oe + r]), spl[r]);
+            }
+            __syncthreads();
+            if (!s_inv_ok) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, cur, 49u);
+                return bail();
+            }
+            gp_mark(w, 2);
+            npre = (unsigned)np;
             have_u = false;
-            oi = __ldcg(&w->oe);
-            // a following merge of two or more groups reads the phase vectors before
-            // the map (partners at A^-1 u, sign patterns from A^T v); otherwise the
-            // map is applied now
-            if (npre > 0 && !__ldcg(&w->plans[0].P.bad) && __ldcg(&w->plans[0].P.ng) >= 2) {
-                aff = true;
-                continue;
-            }
-            affine_pass();
-            if (!gp_barrier(w, gen, d.status, cur)) return bail();
+            oi = oe;
+            aff = true;
+            move_hull();
+            gp_mark(w, 3);
             continue;
         }
         if (kind < SF_OP_DIAG || kind > SF_OP_DIAG + 3) break;  // measurement or conditional gate
         // ---- diagonal run: all plans first (unless the Clifford phase made them),
-        // then one merge per record
+        // then the records in passes over the frame
         int nb = (int)npre;
         npre = 0;
-        if (nb == 0) {
-        if (warp == 0) {
-            const unsigned long long ri = oi + lane;
-            bool dg = false;
-            if (ri < n_ops) {
-                const uint32_t kk = ops[ri].kind;
-                dg = kk >= SF_OP_DIAG && kk <= SF_OP_DIAG + 3;
-            }
-            const unsigned bl = __ballot_sync(SF_FULL, dg);
-            int nb = bl == SF_FULL ? 32 : __ffs(~bl) - 1;
-            nb = nb < kGpPlans ? nb : kGpPlans;
-            if (lane == 0) s_nb = nb < (int)gridDim.x ? nb : (int)gridDim.x;
+        if (nb == 0) {  // every CTA plans the batch itself, one warp per record
+            nb = diag_count(ops, oi, n_ops);
+            for (int r = warp; r < nb; r += (int)(blockDim.x >> 5))
+                gp_plan(s_tab, n, ops[oi + r], __ldcg(&trig[oi + r]), spl[r]);
+            __syncthreads();
         }
-        __syncthreads();
-        nb = s_nb;
-        if ((int)blockIdx.x < nb && warp == 0) gp_plan(d, ops[oi + blockIdx.x], sp, &w->plans[blockIdx.x]);
-        if (!gp_barrier(w, gen, d.status, cur)) return bail();
-        }
-        {
-            const uint64_t* src = reinterpret_cast<const uint64_t*>(w->plans);
-            uint64_t* dst = reinterpret_cast<uint64_t*>(spl);
-            for (int i = threadIdx.x; i < nb * (int)(sizeof(GpPlan) / 8); i += blockDim.x) dst[i] = __ldcg(&src[i]);
-        }
-        __syncthreads();
         int t = 0;
         while (t < nb) {
-            // the longest run from t that one in-place pass takes: one-group gates
-            // (a phase per element) and two-group gates whose second mask is the one
-            // the frame is closed under (each pair {s, s ^ u} maps onto itself)
+            const BrTab& P0 = spl[t].P;  // the plan in the tableau's coordinates
+            const int ng = P0.ng;
+            if (P0.bad) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, cur, 44u);
+                if (aff) affine_pass();  // the frame must match the tableau when the launch ends
+                return bail();
+            }
+            const unsigned long long kb = keep_bits(eps2);
+            // ---- a branch along a direction outside the hull: no element has a
+            // partner, so each writes its two children in place (s at j, s ^ u at
+            // j + k); the following records that keep every pair are applied to it
+            // in the same pass
+            if (ng == 2 && hull_fresh(s_hc, P0.u[1])) {
+                const uint64_t u = P0.u[1];
+                int t2 = t + 1;
+                while (t2 < nb && !spl[t2].P.bad &&
+                       (spl[t2].P.ng == 1 || (spl[t2].P.ng == 2 && spl[t2].P.u[1] == u)))
+                    t2++;
+                if (2 * k > d.cap) {
+                    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_CAPACITY, cur, 0u);
+                    if (aff) affine_pass();
+                    return bail();
+                }
+                gp_mark(w, 4);
+                if (aff) affine_tables();
+                const bool uni = compose(t, t2, u);
+                const Cm2 cm = s_comp;
+                gp_mark(w, 5);
+                unsigned long long* fk = w->fk[nfresh % 3];
+                if (blockIdx.x == 0 && threadIdx.x == 0) w->fk[(nfresh + 1) % 3][0] = w->fk[(nfresh + 1) % 3][1] = 0;
+                uint64_t* S = d.sig[cur];
+                double2* A = d.amp[cur];
+                unsigned long long lo, hi;
+                gp_chunk(k, lo, hi);
+                unsigned c0 = 0, c1 = 0;
+                for (unsigned long long base = lo; base < hi; base += blockDim.x) {
+                    const unsigned long long j = base + threadIdx.x;
+                    if (j < hi) {
+                        const uint64_t s = __ldcg(&S[j]);
+                        double2 a0 = __ldcg(&A[j]), a1 = make_double2(0.0, 0.0);
+                        const uint64_t s0 = aff ? affine_of(s) : s, s1 = s0 ^ u;
+                        if (uni) {
+                            a1 = cprod(cm.m10, a0);
+                            a0 = cprod(cm.m00, a0);
+                        } else {
+                            for (int r = t; r < t2; r++) pair_step<true>(spl[r], s0, s1, a0, a1);
+                        }
+                        S[j] = s0;
+                        A[j] = a0;
+                        S[j + k] = s1;
+                        A[j + k] = a1;
+                        c0 += amp_kept(a0, kb, eps2);
+                        c1 += amp_kept(a1, kb, eps2);
+                    }
+                }
+                gp_mark(w, 6);
+                add_counts(fk, c0, c1);
+                gp_phase(3 | ((t2 - t) << 4), k);
+                if (!gp_barrier(w, gen, d.status, cur)) return bail();
+                const unsigned long long K0 = __ldcg(&fk[0]), K1 = __ldcg(&fk[1]);
+                gp_mark(w, 7);
+                account(72 * k);
+                aff = false;
+                nfresh++;
+                ivalid[cur] = false;
+                t = t2;
+                if (K0 == k && K1 == k) {  // every child kept: the frame doubles
+                    hull_grow(u);
+                    if (threadIdx.x == 0 && npos < 64) {
+                        s_pu[npos] = u;
+                        s_pk[npos] = k;
+                    }
+                    npos = npos < 64 ? npos + 1 : npos;
+                    __syncthreads();
+                    k *= 2;
+                    have_u = true;
+                    cu = u;
+                } else if (K0 == k && K1 == 0) {  // the mask's children all vanished: same positions
+                    have_u = false;
+                } else {
+                    hull_grow(u);
+                    __syncthreads();
+                    bool moved = true;
+                    compact(2 * k, moved);
+                    if (!moved) return bail();
+                }
+                continue;
+            }
+            // ---- in-place run: one-group records (a phase per element) and two-group
+            // records whose mask the frame is closed under (each pair {s, s ^ u} maps
+            // onto itself); phase vectors and positions stay
             int t2 = t;
             bool pairs = false;
+            uint64_t pu = 0;
             while (t2 < nb && !spl[t2].P.bad) {
                 const BrTab& Q = spl[t2].P;
-                if (Q.ng == 1 || (Q.ng == 2 && have_u && Q.u[1] == cu)) {
-                    pairs |= Q.ng == 2;
+                if (Q.ng == 1) {
+                    t2++;
+                } else if (Q.ng == 2 && (pairs ? Q.u[1] == pu
+                                               : ((have_u && Q.u[1] == cu) || pos_stride(Q.u[1]) != 0))) {
+                    pairs = true;
+                    pu = Q.u[1];
                     t2++;
                 } else {
                     break;
                 }
             }
             if (t2 > t) {
-                // ---- in-place run: the element with the smaller phase vector of each pair
-                // applies the run's gates to both amplitudes (same sums, same order, as
-                // the per-gate merge); phase vectors, positions and the index stay
-                const unsigned long long kb = keep_bits(eps2);
-                const uint64_t* S = d.sig[cur];
-                double2* A = d.amp[cur];
-                unsigned long long lo, hi;
-                gp_chunk(k, lo, hi);
+                const unsigned long long st = pairs ? pos_stride(pu) : 0;
                 bool drop = false, miss = false;
-                const auto plan = [&](int r) { return PlanRef{&spl[r].P, spl[r].ctab}; };
-                const int c_ = cur;
-                const auto find = [&](uint64_t key) { return gp_find(d, c_, isz[c_], tag[c_], key); };
-                for (unsigned long long base = lo + 64ull * warp; base < hi; base += 64ull * (blockDim.x >> 5))
-                    inplace_run_warp<true>(S, A, base, hi, pairs, cu, t, t2, plan, find, kb, eps2, drop, miss);
+                if (st && k % (2 * st)) {  // positions no longer pair up: a bookkeeping fault
+                    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, cur, 50u);
+                    if (aff) affine_pass();
+                    return bail();
+                }
+                const bool wrote_sig = aff && (!pairs || st);
+                if (!pairs || st) {
+                    // partners by position (or none): the pending map is applied on the way
+                    if (aff) affine_tables();
+                    const bool uni = compose(t, t2, pairs ? pu : 0);
+                    const Cm2 cm = s_comp;
+                    uint64_t* S = d.sig[cur];
+                    double2* A = d.amp[cur];
+                    const unsigned long long items = pairs ? k / 2 : k;
+                    unsigned long long lo, hi;
+                    gp_chunk(items, lo, hi);
+                    for (unsigned long long m = lo + threadIdx.x; m < hi; m += blockDim.x) {
+                        unsigned long long p0 = m, p1 = 0;
+                        if (pairs) {
+                            const unsigned long long b = m / st;
+                            p0 = m + b * st;  // 2 b st + (m - b st)
+                            p1 = p0 + st;
+                        }
+                        uint64_t s0 = __ldcg(&S[p0]);
+                        uint64_t s1 = pairs ? __ldcg(&S[p1]) : 0;
+                        if (aff) {
+                            s0 = affine_of(s0);
+                            if (pairs) s1 = affine_of(s1);
+                        }
+                        if (pairs && s1 != (s0 ^ pu)) {
+                            miss = true;
+                            continue;
+                        }
+                        double2 a0 = __ldcg(&A[p0]);
+                        double2 a1 = pairs ? __ldcg(&A[p1]) : make_double2(0.0, 0.0);
+                        if (uni) {
+                            const double2 b0 = cfma(cm.m01, a1, cprod(cm.m00, a0));
+                            a1 = cfma(cm.m11, a1, cprod(cm.m10, a0));
+                            a0 = b0;
+                        } else if (pairs) {
+                            for (int r = t; r < t2; r++) pair_step<true>(spl[r], s0, s1, a0, a1);
+                        } else {
+                            for (int r = t; r < t2; r++) pair_step<false>(spl[r], s0, s1, a0, a1);
+                        }
+                        if (aff) S[p0] = s0;
+                        A[p0] = a0;
+                        drop |= !amp_kept(a0, kb, eps2);
+                        if (pairs) {
+                            if (aff) S[p1] = s1;
+                            A[p1] = a1;
+                            drop |= !amp_kept(a1, kb, eps2);
+                        }
+                    }
+                    if (aff) {
+                        ivalid[cur] = false;
+                        aff = false;
+                    }
+                } else {
+                    // partners through the index (the frame was closed under pu by a merge,
+                    // which left its index; no map is pending then)
+                    if (aff) {
+                        affine_pass();
+                        gp_phase(8, k);
+                        if (!gp_barrier(w, gen, d.status, cur)) return bail();
+                    }
+                    if (!ivalid[cur] && !build_index(cur)) return bail();
+                    const uint64_t* S = d.sig[cur];
+                    double2* A = d.amp[cur];
+                    unsigned long long lo, hi;
+                    gp_chunk(k, lo, hi);
+                    const auto plan = [&](int r) { return PlanRef{&spl[r].P, spl[r].ctab}; };
+                    const int c_ = cur;
+                    const auto find = [&](uint64_t key) { return gp_find(d, c_, isz[c_], tag[c_], key); };
+                    for (unsigned long long base = lo + 64ull * warp; base < hi; base += 64ull * (blockDim.x >> 5))
+                        inplace_run_warp<true>(S, A, base, hi, true, pu, t, t2, plan, find, kb, eps2, drop, miss);
+                }
                 if (miss) {  // the frame is not closed after all
                     set_status(d.status, SF_ST_INTERNAL, cur, 47u);
                     gp_fail(w);
                 }
                 if (__syncthreads_or(drop) && threadIdx.x == 0) gp_dropped(w);
+                gp_phase(4 | ((t2 - t) << 4), k);
                 if (!gp_barrier(w, gen, d.status, cur)) return bail();
+                account(40 * k + (wrote_sig ? 8 * k : 0));
                 t = t2;
                 if (!s_drop) continue;
                 // ---- amplitudes fell below the threshold: compact the frame
-                const int in = cur, out = cur ^ 1;
-                const unsigned long long Tout = index_slots(k, d.icap);
-                const uint32_t tag_out = next_tag(tag[out]);
-                unsigned long long* ctr = &w->ocnt[nmerge % 3];
-                if (blockIdx.x == 0 && threadIdx.x == 0) w->ocnt[(nmerge + 1) % 3] = 0;
-                for (unsigned long long base = lo; base < hi; base += blockDim.x) {
-                    const unsigned long long j = base + threadIdx.x;
-                    const bool act = j < hi;
-                    uint64_t s0 = 0;
-                    double2 a = make_double2(0.0, 0.0);
-                    if (act) {
-                        s0 = __ldcg(&d.sig[in][j]);
-                        a = __ldcg(&d.amp[in][j]);
-                    }
-                    const bool keep = act && amp_kept(a, kb, eps2);
-                    const unsigned long long o = block_out_range(ctr, keep ? 1u : 0u, wsum, &bbase);
-                    if (keep) {
-                        d.sig[out][o] = s0;
-                        d.amp[out][o] = a;
-                        ok &= index_insert<1>(d, out, Tout, tag_out, &s0, (uint32_t)o);
-                    }
-                }
-                if (!ok) {
-                    set_status(d.status, SF_ST_TIMEOUT, in, 48u);  // index full
-                    gp_fail(w);
-                }
-                if (!gp_barrier(w, gen, d.status, in)) return bail();
-                k = __ldcg(ctr);
-                cur = out;
-                tag[out] = tag_out;
-                isz[out] = Tout;
-                nmerge++;
-                have_u = false;
+                bool moved = true;
+                compact(k, moved);
+                if (!moved) return bail();
                 continue;
             }
-            // ---- merge of record t into the other buffer
-            const BrTab& P0 = spl[t].P;  // the plan in the tableau's coordinates
-            const int ng = P0.ng;
-            if (P0.bad || (unsigned long long)ng * k > d.cap) {
-                if (blockIdx.x == 0 && threadIdx.x == 0)
-                    set_status(d.status, P0.bad ? SF_ST_INTERNAL : SF_ST_CAPACITY, cur, P0.bad ? 44u : 0u);
-                if (aff) affine_pass();  // the frame must match the tableau when the launch ends
+            // ---- merge of record t into the other buffer through the input's index
+            if ((unsigned long long)ng * k > d.cap) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_CAPACITY, cur, 0u);
+                if (aff) affine_pass();
                 return bail();
             }
+            if (!ivalid[cur] && !build_index(cur)) return bail();
             if (aff) {
                 // the phase vectors are still those before the map sigma' = A sigma ^ t:
                 // partners at A^-1 u, sign patterns from A^T v flipped by parity(v & t);
                 // outputs are written in the new coordinates
                 affine_tables();
-                for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    s_ainv[i] = __ldcg(&w->Ainv[i]);
-                    s_at[i] = __ldcg(&w->AT[i]);
-                }
                 {
                     const uint64_t* src = reinterpret_cast<const uint64_t*>(&P0);
                     uint64_t* dst = reinterpret_cast<uint64_t*>(&pm);
@@ -551,7 +1054,6 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             unsigned long long* ctr = &w->ocnt[nmerge % 3];
             // the counter of the next merge was last read before the previous barrier
             if (blockIdx.x == 0 && threadIdx.x == 0) w->ocnt[(nmerge + 1) % 3] = 0;
-            const unsigned long long kb = keep_bits(eps2);
             const uint64_t* Si = d.sig[in];
             const double2* Ai = d.amp[in];
             uint64_t* So = d.sig[out];
@@ -604,12 +1106,18 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 gp_fail(w);
             }
             if (__syncthreads_or(drop) && threadIdx.x == 0) gp_dropped(w);
+            for (int g = 1; g < ng; g++) hull_grow(P0.u[g]);  // directions new to the hull
+            gp_phase(5, k);
             if (!gp_barrier(w, gen, d.status, in)) return bail();
+            account(24 * k);
             k = __ldcg(ctr);
+            account(24 * k);
             cur = out;
             tag[out] = tag_out;
             isz[out] = Tout;
+            ivalid[out] = true;
             nmerge++;
+            npos = 0;  // outputs sit where their reservations put them
             // no output dropped: every parent s gave s ^ u_g for all g, so the new
             // frame is closed under the gate's masks
             have_u = !s_drop && ng == 2;
@@ -619,33 +1127,38 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
         }
         oi += nb;
     }
-    if (aff) {  // not reached in practice: a pending map always has a merge after it
+    if (aff) {  // a Clifford run at the end of the program
         affine_pass();
+        gp_phase(8, k);
         if (!gp_barrier(w, gen, d.status, cur)) return bail();
     }
-    // the frame goes back to buffer cur0, indexed
+    // the frame goes back to buffer cur0 (without an index)
     if (cur != cur0) {
-        const uint32_t tg = next_tag(tag[cur0]);
-        const unsigned long long T = index_slots(k, d.icap);
         unsigned long long lo, hi;
         gp_chunk(k, lo, hi);
         for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-            const uint64_t s = __ldcg(&d.sig[cur][j]);
-            d.sig[cur0][j] = s;
+            d.sig[cur0][j] = __ldcg(&d.sig[cur][j]);
             d.amp[cur0][j] = __ldcg(&d.amp[cur][j]);
-            ok &= index_insert<1>(d, cur0, T, tg, &s, (uint32_t)j);
         }
-        if (!ok) set_status(d.status, SF_ST_TIMEOUT, cur0, 46u);
-        tag[cur0] = tg;
-        isz[cur0] = T;
+        ivalid[cur0] = false;
+        account(48 * k);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        d.kcnt[cur0] = k;
-        d.itag[cur0] = tag[cur0];
-        d.isize[cur0] = isz[cur0];
-        d.itag[cur0 ^ 1] = tag[cur0 ^ 1];  // stale, but its tag must not repeat
-        d.isize[cur0 ^ 1] = isz[cur0 ^ 1];
-        if (consumed) *consumed = oi;
+    store_tableau();
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < 64 && hull_state != 0) {
+            w->hull[threadIdx.x] = s_hc[threadIdx.x];
+            w->hbasis[threadIdx.x] = s_hb[threadIdx.x];
+            if (threadIdx.x == 0) w->nhb = (unsigned)s_nhb;
+        }
+        if (threadIdx.x == 0) {
+            d.kcnt[cur0] = k;
+            for (int b = 0; b < 2; b++) {  // an index that went stale gets a tag it never had
+                d.itag[b] = ivalid[b] ? tag[b] : next_tag(tag[b]);
+                d.isize[b] = isz[b];
+            }
+            if (consumed) *consumed = oi;
+            if (trace) w->ntrace = gen - s_gen0;
+        }
     }
 }
 
@@ -656,7 +1169,33 @@ size_t sf_gprog_work_words() { return (sizeof(GpWork) + 7) / 8; }
 // clears the per-launch words of the workspace (stream-ordered)
 cudaError_t sf_gprog_clear(const SfDev& d, cudaStream_t s) {
     GpWork* w = reinterpret_cast<GpWork*>(d.gp);
-    return cudaMemsetAsync(&w->err[0], 0, offsetof(GpWork, oe) - offsetof(GpWork, err), s);
+    return cudaMemsetAsync(&w->err[0], 0, offsetof(GpWork, cleared_end) - offsetof(GpWork, err), s);
+}
+
+// element bytes moved by the last launch (stream-ordered copy into *host)
+cudaError_t sf_gprog_moved(const SfDev& d, unsigned long long* host, cudaStream_t s) {
+    GpWork* w = reinterpret_cast<GpWork*>(d.gp);
+    return cudaMemcpyAsync(host, &w->moved, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+}
+
+// checkpoints inside the phases of the last traced launch (8 per phase)
+cudaError_t sf_gprog_marks(const SfDev& d, uint64_t* host, unsigned m, cudaStream_t s) {
+    GpWork* w = reinterpret_cast<GpWork*>(d.gp);
+    m = std::min(m, (unsigned)kGpTrace);
+    return m ? cudaMemcpyAsync(host, &w->marks[0][0], m * 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s)
+             : cudaSuccess;
+}
+
+// the phase records of the last traced launch (stream-ordered copies)
+cudaError_t sf_gprog_trace(const SfDev& d, uint64_t* host, unsigned cap, unsigned* n, cudaStream_t s) {
+    GpWork* w = reinterpret_cast<GpWork*>(d.gp);
+    cudaError_t e = cudaMemcpyAsync(n, &w->ntrace, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    const unsigned m = std::min(std::min(*n, cap), (unsigned)kGpTrace);
+    *n = m;
+    return m ? cudaMemcpyAsync(host, &w->trace[0][0], m * 5 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s)
+             : cudaSuccess;
 }
 
 // resets the barrier after a launch that gave up waiting
@@ -665,6 +1204,7 @@ cudaError_t sf_gprog_reset(const SfDev& d, cudaStream_t s) {
 }
 
 cudaError_t sf_launch_gprog(const SfDev& d, const void* ops, unsigned long long n_ops, double eps2, int cur,
+                            int idx_ok, int hull_state, unsigned spin_limit, int trace, double2* trig,
                             unsigned long long* consumed, cudaStream_t s) {
     static int grid = 0;  // one CTA per SM, all resident (checked once per process)
     if (grid == 0) {
@@ -692,5 +1232,5 @@ cudaError_t sf_launch_gprog(const SfDev& d, const void* ops, unsigned long long 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_gprog, d, reinterpret_cast<GpWork*>(d.gp), reinterpret_cast<const OpRec*>(ops),
-                              n_ops, eps2, cur, consumed);
+                              n_ops, eps2, cur, idx_ok, hull_state, spin_limit, trace, trig, consumed);
 }

@@ -527,6 +527,8 @@ __device__ __forceinline__ double2 half_coef(const BrTab& P, const double2 (*cta
 // is carried by its element with the smaller phase vector, and those owners
 // are packed onto consecutive lanes first, so no lane idles through the FP64
 // pipe (a double-precision instruction costs the same for 1 lane as for 32).
+// A window can hold up to 64 owners (the partners of its elements may sit in
+// other windows), so the owners are taken 32 at a time.
 // find(key) is the position of a phase vector, kL2: the frame is read through
 // L2 (written by other CTAs of the launch).  Sets drop if a result is below
 // the threshold, miss if a partner is absent.
@@ -543,42 +545,45 @@ __device__ __forceinline__ void inplace_run_warp(const uint64_t* S, double2* A, 
     const bool oa = ja < hi && (!pairs || (sa ^ cu) > sa), ob = jb < hi && (!pairs || (sb ^ cu) > sb);
     const unsigned ma = __ballot_sync(SF_FULL, oa), mb = __ballot_sync(SF_FULL, ob);
     const int na = __popc(ma), cnt = na + __popc(mb);
-    // lane l takes the l-th owner of the 64 elements
-    unsigned m = lane < na ? ma : mb;
-    for (int i = lane < na ? lane : lane - na; i > 0 && m; i--) m &= m - 1;
-    const int src = m ? __ffs(m) - 1 : 0;
-    const uint64_t s_a = __shfl_sync(SF_FULL, sa, src), s_b = __shfl_sync(SF_FULL, sb, src);
-    if (lane >= cnt) return;
-    const bool second = lane >= na;
-    const uint64_t s0 = second ? s_b : s_a, s1 = s0 ^ cu;
-    const unsigned long long j = base + (second ? 32 : 0) + src;
-    long long q = -1;
-    if (pairs) {
-        q = find(s1);
-        if (q < 0) {
-            miss = true;
-            return;
-        }
-    }
-    double2 a0 = kL2 ? __ldcg(&A[j]) : A[j];
-    double2 a1 = make_double2(0.0, 0.0);
-    if (q >= 0) a1 = kL2 ? __ldcg(&A[q]) : A[q];
-    for (int r = r0; r < r1; r++) {
-        const BrTab& Q = *plan(r).P;
-        const double2(*ct)[16] = plan(r).ctab;
-        double2 n0 = make_double2(0.0, 0.0), n1 = make_double2(0.0, 0.0);
-        cmul_acc(n0, half_coef(Q, ct, 0, s0), a0);
+    for (int first = 0; first < cnt; first += 32) {
+        // lane l takes owner first + l of the 64 elements
+        const int l = first + lane;
+        unsigned m = l < na ? ma : mb;
+        for (int i = l < na ? l : l - na; i > 0 && m; i--) m &= m - 1;
+        const int src = m ? __ffs(m) - 1 : 0;
+        const uint64_t s_a = __shfl_sync(SF_FULL, sa, src), s_b = __shfl_sync(SF_FULL, sb, src);
+        if (l >= cnt) continue;
+        const bool second = l >= na;
+        const uint64_t s0 = second ? s_b : s_a, s1 = s0 ^ cu;
+        const unsigned long long j = base + (second ? 32 : 0) + src;
+        long long q = -1;
         if (pairs) {
-            if (Q.ng == 2) cmul_acc(n0, half_coef(Q, ct, 1, s1), a1);
-            cmul_acc(n1, half_coef(Q, ct, 0, s1), a1);
-            if (Q.ng == 2) cmul_acc(n1, half_coef(Q, ct, 1, s0), a0);
+            q = find(s1);
+            if (q < 0) {
+                miss = true;
+                continue;
+            }
         }
-        a0 = n0;
-        a1 = n1;
+        double2 a0 = kL2 ? __ldcg(&A[j]) : A[j];
+        double2 a1 = make_double2(0.0, 0.0);
+        if (q >= 0) a1 = kL2 ? __ldcg(&A[q]) : A[q];
+        for (int r = r0; r < r1; r++) {
+            const BrTab& Q = *plan(r).P;
+            const double2(*ct)[16] = plan(r).ctab;
+            double2 n0 = make_double2(0.0, 0.0), n1 = make_double2(0.0, 0.0);
+            cmul_acc(n0, half_coef(Q, ct, 0, s0), a0);
+            if (pairs) {
+                if (Q.ng == 2) cmul_acc(n0, half_coef(Q, ct, 1, s1), a1);
+                cmul_acc(n1, half_coef(Q, ct, 0, s1), a1);
+                if (Q.ng == 2) cmul_acc(n1, half_coef(Q, ct, 1, s0), a0);
+            }
+            a0 = n0;
+            a1 = n1;
+        }
+        A[j] = a0;
+        if (q >= 0) A[q] = a1;
+        drop |= !amp_kept(a0, kb, eps2) || (q >= 0 && !amp_kept(a1, kb, eps2));
     }
-    A[j] = a0;
-    if (q >= 0) A[q] = a1;
-    drop |= !amp_kept(a0, kb, eps2) || (q >= 0 && !amp_kept(a1, kb, eps2));
 }
 
 struct PlanRef {

@@ -11,6 +11,7 @@ amplitudes read and written; index and hash tables are not counted).
   python -m paper_1712_03554_gb300.kernel_bench merge-case 20   (a short run for ncu captures)
   python -m paper_1712_03554_gb300.kernel_bench qft-step [max_frame] (one eager QFT n=20 step, the bench's circuit)
   python -m paper_1712_03554_gb300.kernel_bench qft-grid          (QFT n=20: per-op vs grid program, wall per pass)
+  python -m paper_1712_03554_gb300.kernel_bench qft-trace         (QFT n=20 in the grid program: time per phase)
   python -m paper_1712_03554_gb300.kernel_bench campaign-case 64 (one campaign launch, 32 threads, global index)
   python -m paper_1712_03554_gb300.kernel_bench clifford-case 1024 (one Clifford batch of 200 gates at n)
   python -m paper_1712_03554_gb300.kernel_bench cuccaro 5 6 7   (adder: Toffoli by cofactors vs Clifford+7T)
@@ -176,6 +177,51 @@ def qft_grid(reps=5):
     print(json.dumps(res), flush=True)
 
 
+PHASE_NAMES = {1: "clifford", 2: "plan", 3: "branch", 4: "in-place", 5: "merge", 6: "compact", 7: "index",
+               8: "map", 10: "check"}
+
+
+def qft_trace(seed=0, reps=3):
+    """QFT n = 20 (the bench's circuit) as one grid program launch with per-phase
+    tracing (sf_set_trace): each phase's kind, records, elements, CTA 0's own
+    work, and the wait for the last CTA; summed by kind.  Times in us from the
+    GPU's global timer (the last of reps launches after a warm-up)."""
+    import torch
+    x, ops = c.qft_random_input(20, seed)
+    recs, _ = sf.encode_program([ops])
+    d = torch.from_numpy(recs.view(np.uint8).copy()).cuda()
+    f = sf.Frame(20, 1 << 21)
+    f.set_trace(True)
+    for _ in range(reps + 1):
+        f.reset()
+        f.apply_program_grid_device(d.data_ptr(), len(recs))
+        f.sync()
+    tr = f.grid_program_trace().astype(np.int64)
+    rows, by_kind = [], {}
+    mark_names = ("cliff_start", "cliff_end", "plan_end", "hull_end", "pass_start", "map_tables_end", "loop_end",
+                  "prev_pass_counts_read")
+    for i, rec in enumerate(tr):
+        code, t0, arr0, last, who = (int(v) for v in rec[:5])
+        kind = PHASE_NAMES.get(code & 15, str(code & 15))
+        nrec, k = (code >> 4) & 15, code >> 8
+        end = max(arr0, last)
+        row = {"i": i, "kind": kind, "records_mod16": nrec, "k": k, "phase_us": (end - t0) / 1e3,
+               "cta0_us": (arr0 - t0) / 1e3, "last_after_cta0_us": (last - arr0) / 1e3, "last_cta": who}
+        marks = {nm: round((int(v) - t0) / 1e3, 3) for nm, v in zip(mark_names, rec[5:]) if int(v) >= t0 > 0}
+        row["marks_us_from_start"] = marks
+        rows.append(row)
+        agg = by_kind.setdefault(kind, {"phases": 0, "us": 0.0})
+        agg["phases"] += 1
+        agg["us"] += row["phase_us"]
+    total = (max(int(tr[-1][2]), int(tr[-1][3])) - int(tr[0][1])) / 1e3 if len(tr) else 0.0
+    print(json.dumps({"phases": len(rows), "total_us": total, "by_kind": by_kind,
+                      "moved_bytes": f.grid_program_bytes()}), flush=True)
+    for r in rows:
+        print(json.dumps(r), flush=True)
+    y = 12345
+    print(json.dumps({"amp_err": abs(f.amplitude(y) - c.qft_expected_amplitude(20, x, y))}), flush=True)
+
+
 def campaign_case(nv=64):
     """One launch of the campaign kernel on nv Steane variants."""
     eng = sf.Campaign(c.STEANE_N, 4096)
@@ -274,6 +320,8 @@ if __name__ == "__main__":
         qft_step(max_frame=args[0] if args else 2048)
     elif mode == "qft-grid":
         qft_grid()
+    elif mode == "qft-trace":
+        qft_trace(args[0] if args else 0)
     elif mode == "campaign-case":
         campaign_case(args[0] if args else 64)
     elif mode == "cuccaro":

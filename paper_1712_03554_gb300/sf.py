@@ -74,6 +74,11 @@ def load(build: bool = True) -> C.CDLL:
         "sf_apply_nonclifford_coalesce": ([H, u32, u32, u32, dbl, dbl], st),
         "sf_apply_program": ([H, C.c_void_p, u64, dbl, u64, C.c_void_p, C.c_void_p], st),
         "sf_apply_program_grid": ([H, C.c_void_p, u64, dbl, C.c_void_p], st),
+        "sf_run_program": ([H, C.c_void_p, u64, dbl, P64, C.POINTER(C.c_uint32)], st),
+        "sf_set_wait_limit": ([H, u32], st),
+        "sf_grid_program_bytes": ([H, P64], st),
+        "sf_set_trace": ([H, C.c_int32], st),
+        "sf_grid_program_trace": ([H, P64, u32, C.POINTER(C.c_uint32)], st),
         "sf_apply_toffoli": ([H, u32, u32, u32], st),
         "sf_apply_cr_cofactor": ([H, u32, u32, dbl], st),
         "sf_coalesce": ([H, dbl, P64], st),
@@ -130,6 +135,7 @@ def load(build: bool = True) -> C.CDLL:
 
 
 COALESCE_NOALLOC_MAX_ELEMS = 65536
+WAIT_LIMIT_DEFAULT = 1048576
 
 
 def coalesce_noalloc(sigma_in: int, amp_in: int, k_in: int, n_words: int, drop_eps: float, sigma_out: int,
@@ -546,6 +552,42 @@ class Frame:
                                              de.ctypes.data_as(C.POINTER(C.c_uint32)),
                                              g.ctypes.data_as(C.POINTER(C.c_double))), self.h)
         return dx, dz, de, complex(g[0], g[1])
+
+    def run_program_records(self, recs: np.ndarray, eps: float = 1e-12) -> Tuple[int, int]:
+        """sf_run_program on an array of sf_op records in host memory (the
+        library copies them); returns (outcome bits, number of measurements)."""
+        recs = np.ascontiguousarray(recs)
+        bits, nm = C.c_uint64(), C.c_uint32()
+        self._check(self.lib.sf_run_program(self.h, recs.ctypes.data_as(C.c_void_p), len(recs), float(eps),
+                                            C.byref(bits), C.byref(nm)), self.h)
+        return int(bits.value), int(nm.value)
+
+    def run_program(self, ops, eps: float = 1e-12) -> Tuple[int, int]:
+        """The ops (circuits.py vocabulary) as one sf_run_program call."""
+        recs, _ = encode_program([ops])
+        return self.run_program_records(recs, eps)
+
+    def grid_program_bytes(self) -> int:
+        """sf_grid_program_bytes: element bytes moved by the last grid program launch."""
+        b = C.c_uint64()
+        self._check(self.lib.sf_grid_program_bytes(self.h, C.byref(b)), self.h)
+        return int(b.value)
+
+    def set_trace(self, on: bool) -> None:
+        """sf_set_trace: record per-phase times of the next grid program launches."""
+        self._check(self.lib.sf_set_trace(self.h, 1 if on else 0), self.h)
+
+    def grid_program_trace(self) -> np.ndarray:
+        """sf_grid_program_trace: (phases, 13) uint64 records of the last traced launch."""
+        buf = np.zeros((512, 13), dtype=np.uint64)
+        n = C.c_uint32()
+        self._check(self.lib.sf_grid_program_trace(self.h, buf.ctypes.data_as(C.POINTER(C.c_uint64)), 512,
+                                                   C.byref(n)), self.h)
+        return buf[:n.value].copy()
+
+    def set_wait_limit(self, polls: int) -> None:
+        """sf_set_wait_limit: barrier polls of the grid program before it gives up."""
+        self._check(self.lib.sf_set_wait_limit(self.h, int(polls)), self.h)
 
     def host_state(self) -> int:
         """Token of the host-side bookkeeping (restore it after replaying a graph)."""

@@ -216,3 +216,20 @@ def test_shapes_agree_and_autotune(sfm):
     res = eng.run(circuits)
     assert np.array_equal(res["outcomes"], ref["outcomes"])
     eng.close()
+
+
+@pytest.mark.parametrize("threads", [32, 64, 256])
+def test_stage_circuits_vs_oracle(sfm, threads):
+    """Stages that branch along new directions, then controlled phases from
+    earlier stages' qubits (merges whose partners already exist, after which
+    pairs are scattered through the frame) followed by gates that keep the
+    pairs: every in-place run must reach the owners of a 64-element window
+    beyond its first 32."""
+    n = 12
+    circuits = [c.stage_circuit(n, 4400 + s, stages=10, per_stage=24) for s in range(4)]
+    eng = sfm.Campaign(n, sfm.CAMPAIGN_MAX_ELEMS)
+    eng.set_shape(threads, 0)
+    res = eng.run(circuits, export=True)
+    for i, ops in enumerate(circuits):
+        check_against_oracle(res, i, n, ops)
+    eng.close()

@@ -143,3 +143,18 @@ def test_exact_mode_and_errors(sfm):
         w.apply_program_device(d_ops.data_ptr(), len(recs))
     for x in (f, g, h, w):
         x.close()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_program_stage_circuits(sfm, seed):
+    """The single-CTA program on stage circuits (new-direction branches, merges
+    whose partners exist, in-place runs over scattered pairs), then the per-op
+    calls once the frame outgrows it; against the oracle."""
+    n = 14
+    ops = c.stage_circuit(n, 5100 + seed, stages=12, per_stage=30)
+    f, i, _ = run_program_then_ops(sfm, n, ops, 1 << 18, max_frame=16384)
+    assert i > len(ops) // 4
+    o = oracle.FrameOracle(n)
+    c.run(o, ops)
+    frames_equal(f, o)
+    f.close()

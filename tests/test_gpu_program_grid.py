@@ -204,3 +204,101 @@ def test_grid_program_errors(sfm):
         w.apply_program_grid_device(d2.data_ptr(), len(recs2))
     for x in (f, g, w):
         x.close()
+
+
+def _forget_hull(f):
+    """A diagonal gate of angle 0 (the identity) through the per-op path: the
+    state is unchanged, and the handle no longer vouches for the frame's hull,
+    so the grid program that follows merges every branch through the index."""
+    f.apply_nonclifford_coalesce(c.PHASE, 0, 0, 0.0, 1e-12)
+
+
+@pytest.mark.parametrize("n,seed", [(6, 10), (12, 11), (20, 12), (40, 13), (63, 14)])
+@pytest.mark.parametrize("known", [True, False])
+def test_grid_program_with_and_without_hull(sfm, n, seed, known):
+    """Branches along directions new to the frame run as in-place passes when the
+    hull is known (from the reset) and as index merges when it is not; both
+    equal the oracle."""
+    ops = clifford_diag_circuit(n, 5000 + seed, length=400, p_diag=0.2)
+    f = sfm.Frame(n, 1 << 18)
+    if not known:
+        _forget_hull(f)
+    i = f.apply_program_grid(ops)
+    assert i == len(ops)
+    o = oracle.FrameOracle(n)
+    c.run(o, ops)
+    frames_equal(f, o)
+    f.close()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_grid_program_stage_passes(sfm, seed):
+    """Stages that branch along new directions, runs that keep the pairs (found
+    by position), uniform and partial drops, more stages than one plan batch
+    holds; against the oracle."""
+    n = 16
+    ops = c.stage_circuit(n, 700 + seed, stages=14, per_stage=40)
+    f = sfm.Frame(n, 1 << 18)
+    assert f.apply_program_grid(ops) == len(ops)
+    o = oracle.FrameOracle(n)
+    c.run(o, ops)
+    frames_equal(f, o)
+    f.close()
+
+
+@pytest.mark.parametrize("n,seed", [(10, 0), (30, 1), (63, 2), (70, 3), (200, 4)])
+def test_run_program_from_host_records(sfm, n, seed):
+    """sf_run_program: the whole circuit (Clifford gates, diagonal gates,
+    measurements with draws, conditional gates) from host records, through the
+    grid program (n <= 63) or the per-op calls, against the oracle."""
+    ops = clifford_diag_circuit(n, 9000 + seed, length=250, with_meas=True)
+    ops += [("M", (3 * seed) % n, 0.37)]
+    f = sfm.Frame(n, 1 << 16)
+    bits, nm = f.run_program(ops)
+    o = oracle.FrameOracle(n)
+    res = c.run(o, ops)
+    assert nm == len(res)
+    assert bits == sum(r[3] << i for i, r in enumerate(res))
+    frames_equal(f, o)
+    f.close()
+
+
+def test_run_program_conditional_gates(sfm):
+    """Conditional Clifford gates after two measurements, through
+    sf_run_program, against the oracle walking the same ops."""
+    n = 5
+    ops = [("C", c.H, 0, 0), ("C", c.H, 1, 0), ("N", c.T, 0, 0, 0.0), ("K",), ("M", 0, 0.9), ("M", 1, 0.1),
+           ("Q", c.X, 2, 0, 0b11), ("Q", c.H, 3, 0, 0b01), ("N", c.T, 3, 0, 0.0), ("K",), ("M", 3, 0.6)]
+    f = sfm.Frame(n, 1 << 10)
+    bits, nm = f.run_program(ops)
+    o = oracle.FrameOracle(n)
+    res = c.run(o, ops)
+    assert nm == 3 and bits == sum(r[3] << i for i, r in enumerate(res))
+    frames_equal(f, o)
+    f.close()
+
+
+def test_grid_barrier_timeout_is_reported_and_the_handle_recovers(sfm):
+    """A wait limit of zero polls makes the first grid barrier run out: the call
+    reports SF_ETIMEOUT at the next synchronising call (every CTA leaves at a
+    barrier, none waits without bound), and after a reset with the default
+    limit the same program gives the oracle's frame."""
+    n = 20
+    x, ops = c.qft_random_input(n, 3)
+    f = sfm.Frame(n, 1 << 21)
+    f.set_wait_limit(0)
+    recs, _ = sfm.encode_program([ops])
+    import torch
+    d_ops = torch.from_numpy(recs.view(np.uint8).copy()).cuda()
+    f.apply_program_grid_device(d_ops.data_ptr(), len(recs), 1e-12)
+    with pytest.raises(sfm.SFError) as ei:
+        f.sync()
+    assert ei.value.code == sfm.SF_ETIMEOUT
+    f.set_wait_limit(sfm.WAIT_LIMIT_DEFAULT)
+    f.reset()
+    f.apply_program_grid_device(d_ops.data_ptr(), len(recs), 1e-12)
+    f.sync()
+    o = oracle.FrameOracle(n)
+    c.run(o, ops)
+    frames_equal(f, o)
+    f.close()
