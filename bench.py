@@ -664,6 +664,8 @@ def main():
     ap.add_argument("--campaign-variants", type=int, default=4096)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-multiframe", action="store_true", help="skip the multiframe leg")
+    ap.add_argument("--no-streaming", action="store_true",
+                    help="skip the per-kernel roofline leg of the streaming kernels at 16 words per phase vector")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--serving-rate", type=float, default=8.0)
     ap.add_argument("--serving-slots", type=int, default=32)
@@ -999,6 +1001,17 @@ def main():
     served = None if args.no_serving else serving_leg(sf, args.serving_requests, args.serving_rate,
                                                       args.serving_slots)
     multiframe = None if args.no_multiframe else multiframe_leg(sf)
+    streaming = None
+    if not args.no_streaming:
+        try:
+            from paper_1712_03554_gb300 import kernel_bench
+            streaming = kernel_bench.streaming_roofline(1000, 20, reps=2, peak_gbs=peak_gbs)
+            streaming["peak_source"] = peak_src
+            streaming["workload"] = ("n = 1000 (16 words per phase vector), 2^20 elements after 4000 random Clifford "
+                                     "gates and 20 merged T gates on scrambled qubits; each per-op kernel class "
+                                     "timed alone with CUDA events")
+        except Exception as e:  # the headline line must not depend on this leg
+            streaming = {"error": f"{type(e).__name__}: {e}"}
 
     out = {
         "impl": "gb300", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -1026,6 +1039,7 @@ def main():
         "batched": batched,
         "served": served,
         "multiframe": multiframe,
+        "roofline_streaming_w16": streaming,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:

@@ -12,6 +12,7 @@ amplitudes read and written; index and hash tables are not counted).
   python -m paper_1712_03554_gb300.kernel_bench qft-step [max_frame] (one eager QFT n=20 step, the bench's circuit)
   python -m paper_1712_03554_gb300.kernel_bench qft-grid          (QFT n=20: per-op vs grid program, wall per pass)
   python -m paper_1712_03554_gb300.kernel_bench qft-trace         (QFT n=20 in the grid program: time per phase)
+  python -m paper_1712_03554_gb300.kernel_bench streaming 1000 20 (per-op streaming kernels, n qubits, 2^m elements)
   python -m paper_1712_03554_gb300.kernel_bench campaign-case 64 (one campaign launch, 32 threads, global index)
   python -m paper_1712_03554_gb300.kernel_bench clifford-case 1024 (one Clifford batch of 200 gates at n)
   python -m paper_1712_03554_gb300.kernel_bench cuccaro 5 6 7   (adder: Toffoli by cofactors vs Clifford+7T)
@@ -177,6 +178,109 @@ def qft_grid(reps=5):
     print(json.dumps(res), flush=True)
 
 
+def _random_qubits(f, n):
+    """Qubits whose Z anticommutes with some row of the handle's tableau."""
+    x, _, _ = f.tableau()
+    return [q for q in range(n) if ((x[:, q // 64] >> np.uint64(q % 64)) & np.uint64(1)).any()]
+
+
+def streaming_roofline(n=1000, m=20, reps=3, seed=7, peak_gbs=None):
+    """The per-op streaming kernels on a frame of 2^m elements over n qubits
+    (n = 1000: 16 words per phase vector, 144 B per element; 2^20 elements are
+    151 MB, more than L2): a scramble of 4n random H/S/CNOT gates, then T on m
+    random qubits of the scrambled tableau (masks spread over all words),
+    merged after each.  Each kernel class is timed with CUDA events on the
+    frame's stream, L2 flushed (512 MiB write) before every timed operation;
+    GB/s = algorithmic bytes (phase vectors and amplitudes read and written;
+    index and slot tables are scratch) / device time.  The frame returns to
+    2^m elements after each operation pair."""
+    import torch
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    k = 1 << m
+    f = sf.Frame(n, 4 * k, stream=stream)  # a merge may hold 2 x (2k) children before merging
+    f.apply_clifford([(g[1], g[2], g[3]) for g in c.random_clifford(n, 4 * n, seed)])
+    rq = _random_qubits(f, n)
+    rng = c.rng_for(seed + 1)
+    pick = [rq[int(i)] for i in rng.choice(len(rq), size=m + 2 + 4 * reps, replace=False)]
+    for q in pick[:m]:
+        f.apply_nonclifford_coalesce(c.T, q, 0, 0.0, 1e-12)
+    assert f.size() == k, f.size()
+    W = f.W
+    e = 8 * W + 16
+    qa, qb = pick[m], pick[m + 1]
+    fresh = iter(pick[m + 2:])  # a random qubit for every measurement
+
+    def timed_cls(classes, op, reps=reps):
+        tot = {cl: [0.0, 0] for cl in classes}
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            for cl in classes:  # one class per pass of the op
+                f.time_kernel(cl)
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                torch.cuda.nvtx.range_push("streaming_timed")  # for profiler filters
+                op()
+                torch.cuda.nvtx.range_pop()
+                ms, cnt = f.kernel_time()
+                f.time_kernel(-1)
+                kk = f.size()  # synchronises and reports a deferred device error here
+                assert kk == k, (cl, kk, k)
+                tot[cl][0] += ms
+                tot[cl][1] += cnt
+        return {cl: (v[0] / max(1, v[1]), v[1]) for cl, v in tot.items()}
+
+    rows = {}
+
+    def add(name, cls, ms, bytes_per_launch):
+        gbs = bytes_per_launch / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        rows[name] = {"kernel_class": cls, "us": ms * 1e3, "bytes_per_launch": bytes_per_launch, "GB_s": gbs}
+        if peak_gbs:
+            rows[name]["frac"] = gbs / peak_gbs
+
+    t = timed_cls(["affine"], lambda: f.apply_clifford([(c.S, qa, 0)]))
+    add("K2 phase update (affine, W words per element in and out)", "affine", t["affine"][0], 2 * 8 * W * k)
+
+    def merged_pair():
+        f.apply_nonclifford_coalesce(c.T, qb, 0, 0.0, 1e-12)
+        f.apply_nonclifford_coalesce(c.TDG, qb, 0, 0.0, 1e-12)
+    f.apply_nonclifford_coalesce(c.PHASE, qa, 0, 0.0, 1e-12)  # the index is current before timing
+    t = timed_cls(["branch_merge"], merged_pair)
+    add("K3+K4 branch merged through the index (k -> 2k and 2k -> k)", "branch_merge", t["branch_merge"][0],
+        3 * e * k)
+
+    def unmerged():
+        f.apply_nonclifford(c.T, qb, 0, 0.0)
+        f.coalesce(1e-12)
+        f.apply_nonclifford_coalesce(c.TDG, qb, 0, 0.0, 1e-12)
+    t = timed_cls(["branch", "insert", "compact"], unmerged)
+    add("K3 branch unmerged (k in, 2k out)", "branch", t["branch"][0], 3 * e * k)
+    add("K4 coalesce: insert (2k elements hashed)", "insert", t["insert"][0], 2 * e * k)
+    add("K4 coalesce: compact (2k survivors written)", "compact", t["compact"][0], 2 * e * k)
+
+    def reindex():
+        f.apply_clifford([(c.S, qa, 0)])
+        f.apply_nonclifford_coalesce(c.PHASE, qa, 0, 0.0, 1e-12)
+    t = timed_cls(["index"], reindex)
+    add("index build (phase vectors read)", "index", t["index"][0], 8 * W * k)
+
+    def measure_pair():
+        q = next(fresh)
+        f.measure(q, -1)
+        f.measure(q, 0)
+    t = timed_cls(["cofactor", "prob", "filter"], measure_pair)
+    add("K5 cofactor merge (k in, 2k out)", "cofactor", t["cofactor"][0], 3 * e * k)
+    add("K5 probabilities (one word + amplitude per element)", "prob", t["prob"][0], 24 * 2 * k)
+    add("K5 collapse filter (2k in, k out)", "filter", t["filter"][0], 3 * e * k)
+    assert f.size() == k, f.size()
+    t = timed_cls(["amplitude"], lambda: f.amplitude(12345))
+    add("K6 amplitude query (every element read)", "amplitude", t["amplitude"][0], e * k)
+    f.close()
+    return {"n_qubits": n, "words_per_phase_vector": W, "elements": k, "bytes_per_element": e,
+            "frame_bytes": e * k, "l2": "flushed (512 MiB write) before every timed operation", "kernels": rows}
+
+
 PHASE_NAMES = {1: "clifford", 2: "plan", 3: "branch", 4: "in-place", 5: "merge", 6: "compact", 7: "index",
                8: "map", 10: "check"}
 
@@ -322,6 +426,17 @@ if __name__ == "__main__":
         qft_grid()
     elif mode == "qft-trace":
         qft_trace(args[0] if args else 0)
+    elif mode == "streaming":
+        import os
+        peak = None
+        try:
+            with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                   "MEASURED_PEAKS.json")) as fh:
+                peak = float(json.load(fh)["hbm_gbs"])
+        except Exception:
+            pass
+        print(json.dumps(streaming_roofline(args[0] if args else 1000, args[1] if len(args) > 1 else 20,
+                                            peak_gbs=peak)), flush=True)
     elif mode == "campaign-case":
         campaign_case(args[0] if args else 64)
     elif mode == "cuccaro":
