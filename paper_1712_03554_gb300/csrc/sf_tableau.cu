@@ -164,7 +164,9 @@ __device__ void cta_bits(bool b, uint64_t* words) {
 // amplitude at y is the phi_0 amplitude at w = y ^ qx times i^{q + |qx qz| +
 // 2 |qz w|}; phi_0 has support on the row span of the X block, and at w it is
 // i^{|px pz|} 2^{-r/2} for the product P of the X-block rows picked by the
-// pivot bits of w (zero unless px = w).
+// pivot bits of w (zero unless px = w).  Stabilizer rows commute with each
+// other, and so do destabilizer rows, so neither product depends on the order
+// of the rows: the rows need not be sorted by pivot.
 template <int W>
 __device__ int cta_amp_phi(const Ws<W>& T, int n, int NT, int r, const uint32_t* tau, const uint64_t* y,
                            Scratch<W>& S) {
@@ -174,9 +176,9 @@ __device__ int cta_amp_phi(const Ws<W>& T, int n, int NT, int r, const uint32_t*
     __syncthreads();
     const uint64_t* wv = S.wv;
     bool sel = false;
-    if (h < r) {
+    if (h < n) {  // X-block rows, wherever they sit (their products do not depend on the order)
         const int pv = T.piv[h];
-        sel = (wv[pv >> 6] >> (pv & 63)) & 1;
+        sel = pv < n && ((wv[pv >> 6] >> (pv & 63)) & 1);
     }
     cta_rows_product<W>(T.mx, T.mz, nullptr, NT, sel, S, S.px, S.pz, &S.pe);
     bool ok = true;
@@ -335,6 +337,9 @@ __device__ void cta_permute32(uint32_t* F, uint32_t* tmp, int h, int n, int dst)
 }
 
 template <int W, bool TRACK_A>
+__device__ int cta_sort_rows(const Ws<W>& T, int n, int NT, Scratch<W>& S);
+
+template <int W, bool TRACK_A, bool SORT = true>
 __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
     const int h = threadIdx.x, lane = h & 31, wid = h >> 5, nw = NT >> 5;
     constexpr int INF = 0x7fffffff;
@@ -418,7 +423,19 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
         }
         __syncthreads();
     }
-    // sort by pivot: rank = number of pivots in smaller columns
+    if (!SORT) {  // the caller sorts later (cta_sort_rows); r = rows with an x pivot
+        const int xr = __syncthreads_count(h < n && T.piv[h] < n);
+        return xr;
+    }
+    return cta_sort_rows<W, TRACK_A>(T, n, NT, S);
+}
+
+// Rows sorted by pivot (rank = number of pivots in smaller columns), carrying
+// every per-row field along; returns r, the X-block size.
+template <int W, bool TRACK_A>
+__device__ int cta_sort_rows(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
+    const int h = threadIdx.x;
+    constexpr int INF = 0x7fffffff;
     if (h < 2 * W) S.occ1[h] = 0;
     __syncthreads();
     const int pv = h < n ? T.piv[h] : INF;
@@ -536,8 +553,9 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
             T.t1[h] = 0;
         }
         __syncthreads();
-        // Pauli gates flip signs only: M keeps its bits and stays in RREF
-        if (kind < 3 || kind > 5) r = cta_rref<W, true>(T, n, NT, S);
+        // Pauli gates flip signs only: M keeps its bits and stays in RREF.  The
+        // rows stay where they are until the end of the batch (one sort there)
+        if (kind < 3 || kind > 5) r = cta_rref<W, true, false>(T, n, NT, S);
         if (r < 0) {
             if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 9u);
             return;
@@ -555,6 +573,7 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
         gb += nb + (dr > 0) - (dr < 0);
         __syncthreads();
     }
+    r = cta_sort_rows<W, true>(T, n, NT, S);
     store_tableau<W>(d, T, r);
     if (h == 0) *d.g = cmul(*d.g, cliff_factor(ga, gb));
     // emit the affine map: columns of A (column j = image of e_j) and t as bit words

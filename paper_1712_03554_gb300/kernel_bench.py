@@ -15,6 +15,7 @@ amplitudes read and written; index and hash tables are not counted).
   python -m paper_1712_03554_gb300.kernel_bench streaming 1000 20 (per-op streaming kernels, n qubits, 2^m elements)
   python -m paper_1712_03554_gb300.kernel_bench campaign-case 64 (one campaign launch, 32 threads, global index)
   python -m paper_1712_03554_gb300.kernel_bench clifford-case 1024 (one Clifford batch of 200 gates at n)
+  python -m paper_1712_03554_gb300.kernel_bench clifford-rate     (tableau us per gate, n = 64 ... 1024)
   python -m paper_1712_03554_gb300.kernel_bench cuccaro 5 6 7   (adder: Toffoli by cofactors vs Clifford+7T)
   python -m paper_1712_03554_gb300.kernel_bench cuccaro-mf 4 5 6 7 (adder: one frame vs a multiframe)
 """
@@ -346,6 +347,22 @@ def clifford_case(n=1024, gates=200):
     print("r", f.tableau()[2])
 
 
+def clifford_rate(ns=(64, 128, 256, 512, 1024), gates=1000):
+    """Tableau cost per Clifford gate (class clifford, CUDA events): a batch of
+    `gates` random H/S/CNOT gates on a tableau scrambled by 4n gates, for each n."""
+    out = {}
+    for n in ns:
+        ops = c.random_clifford(n, 4 * n + gates, seed=n, kinds=(c.H, c.S, c.CNOT))
+        g = [(op[1], op[2], op[3]) for op in ops]
+        f = sf.Frame(n, 64)
+        f.apply_clifford(g[:4 * n])
+        f.sync()
+        ms = timed(f, "clifford", lambda: f.apply_clifford(g[4 * n:]), 1)
+        out[f"n{n}_us_per_gate"] = round(ms * 1e3 / gates, 2)
+        f.close()
+    print(json.dumps(out), flush=True)
+
+
 def cuccaro_compare(nbs=(5, 6, 7)):
     """The Cuccaro adder on the equal superposition with every Toffoli applied
     by cofactors (Eq. 2) and as Clifford+7T: wall time of the whole circuit
@@ -445,5 +462,7 @@ if __name__ == "__main__":
         cuccaro_multiframe(args or [4, 5, 6, 7])
     elif mode == "clifford-case":
         clifford_case(args[0] if args else 1024)
+    elif mode == "clifford-rate":
+        clifford_rate(tuple(args) if args else (64, 128, 256, 512, 1024))
     else:
         raise SystemExit(f"unknown mode {mode}")
