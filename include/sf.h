@@ -361,16 +361,24 @@ sf_status sf_apply_program_grid(sf_handle h, const sf_op* dev_ops, uint64_t n_op
  * first (SF_EINVAL, nothing applied, for a bad record or more than 64
  * measurements).  For n_qubits <= 63 the library copies them to the device
  * once (through a pinned staging buffer of the handle) and runs each stretch
- * of Clifford and diagonal records as one sf_apply_program_grid launch;
- * otherwise it applies them with the per-op calls.  A measurement is made as
- * in the campaign engine: outcome 1 iff the record's draw (param) is below
- * p(1), then the frame is collapsed onto it; a conditional gate applies iff
- * the parity of (outcome bits & mask) is 1.  outcomes / n_meas (host,
- * nullable) receive the outcome bits (bit m = measurement m) and their number.
- * Synchronises at each measurement (the draw needs p(1)); otherwise
- * asynchronous, with deferred device errors as for the calls it makes. */
+ * of Clifford and diagonal records as one sf_apply_program_grid launch, a
+ * launch that occupies the whole GPU; otherwise it applies them with the
+ * per-op calls.  flags = SF_RUN_ONE_CTA is for a GPU shared with other
+ * handles' work (e.g. the serving loop below): for n_qubits <= 63 the program
+ * then runs from its first record on one CTA (sf_apply_program) while the
+ * frame has at most min(max_elems, SF_SEGMENT_MAX_ELEMS) elements, and the
+ * per-op calls continue from where it stops, with no whole-GPU launch.  A
+ * measurement is made as in the campaign engine: outcome 1 iff the record's
+ * draw (param) is below p(1), then the frame is collapsed onto it; a
+ * conditional gate applies iff the parity of (outcome bits & mask) is 1.
+ * outcomes / n_meas (host, nullable) receive the outcome bits (bit m =
+ * measurement m) and their number.  Synchronises at each measurement (the
+ * draw needs p(1)) and, with SF_RUN_ONE_CTA, after the one-CTA program;
+ * otherwise asynchronous, with deferred device errors as for the calls it
+ * makes. */
+enum { SF_RUN_ONE_CTA = 1 };
 sf_status sf_run_program(sf_handle h, const sf_op* ops, uint64_t n_ops, double drop_eps, uint64_t* outcomes,
-                         uint32_t* n_meas);
+                         uint32_t* n_meas, uint32_t flags);
 
 /* Bytes of phase vectors (8 per word) and amplitudes (16) that the passes of
  * the last sf_apply_program_grid launch on this handle read and wrote, each

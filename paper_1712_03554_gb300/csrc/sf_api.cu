@@ -32,6 +32,9 @@ struct sf_frame_s {
     OpRec* hops = nullptr;      // their pinned staging buffer
     size_t hops_cap = 0;
     cudaEvent_t ops_ev = nullptr;  // the last copy out of hops
+    unsigned long long* dprog = nullptr;  // records consumed, outcome bits, count (one-CTA program)
+    size_t dprog_cap = 0;
+    unsigned long long* hprog = nullptr;  // their pinned copy
     cudaEvent_t stage_ev = nullptr;
     uint64_t* dy = nullptr;
     uint64_t* hy = nullptr;
@@ -440,6 +443,7 @@ sf_status sf_destroy(sf_handle h) {
     pinned_free(h->hout, 8);
     pinned_free(h->hmeta, 4);
     pinned_free(h->hops, h->hops_cap);
+    pinned_free(h->hprog, 4);
     if (h->ops_ev) cudaEventDestroy(h->ops_ev);
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -584,11 +588,32 @@ sf_status sf_apply_program_grid(sf_handle h, const sf_op* dev_ops, uint64_t n_op
     return SF_OK;
 }
 
+// the records of one stretch [i, j) of Clifford and diagonal records, per op
+static sf_status run_stretch_per_op(sf_handle h, const sf_op* ops, uint64_t i, uint64_t j, double drop_eps,
+                                    std::vector<sf_gate>& gates) {
+    for (uint64_t r = i; r < j; r++) {
+        const sf_op& q = ops[r];
+        if (q.kind <= SF_SWAP) {
+            gates.push_back(sf_gate{q.kind, q.q0, q.q1, 0u});
+            continue;
+        }
+        if (!gates.empty()) {
+            sf_status st = sf_apply_clifford(h, gates.data(), gates.size());
+            gates.clear();
+            if (st) return st;
+        }
+        sf_status st = sf_apply_nonclifford_coalesce(h, q.kind - SF_OP_DIAG, q.q0, q.q1, q.param, drop_eps);
+        if (st) return st;
+    }
+    return SF_OK;
+}
+
 sf_status sf_run_program(sf_handle h, const sf_op* ops, uint64_t n_ops, double drop_eps, uint64_t* outcomes,
-                         uint32_t* n_meas) {
+                         uint32_t* n_meas, uint32_t flags) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
     if (n_ops && !ops) return fail(h, SF_EINVAL, "ops is NULL");
     if (!(drop_eps >= 0.0)) return fail(h, SF_EINVAL, "drop_eps must be >= 0");
+    if (flags & ~(uint32_t)SF_RUN_ONE_CTA) return fail(h, SF_EINVAL, "unknown flags");
     uint32_t nm = 0;
     for (uint64_t i = 0; i < n_ops; i++) {
         const sf_op& o = ops[i];
@@ -601,8 +626,9 @@ sf_status sf_run_program(sf_handle h, const sf_op* ops, uint64_t n_ops, double d
         nm += o.kind == SF_OP_MEASURE;
     }
     if (nm > 64) return fail(h, SF_EINVAL, "more than 64 measurements");
-    const bool grid = h->d.W == 1 && h->d.gp;
-    if (grid && n_ops) {
+    const bool w1 = h->d.W == 1 && h->d.gp;
+    const bool one_cta = (flags & SF_RUN_ONE_CTA) != 0;
+    if (w1 && n_ops) {
         // the records go to the device once, through the pinned staging buffer
         if (!h->ops_ev) SF_CK(h, cudaEventCreateWithFlags(&h->ops_ev, cudaEventDisableTiming));
         SF_CK(h, cudaEventSynchronize(h->ops_ev));  // the previous copy has left the staging buffer
@@ -622,6 +648,25 @@ sf_status sf_run_program(sf_handle h, const sf_op* ops, uint64_t n_ops, double d
     }
     uint64_t bits = 0;
     uint32_t done_m = 0;
+    uint64_t i = 0;
+    if (w1 && one_cta && n_ops) {
+        // the program from its first record on one CTA while the frame is small;
+        // where it stops, the per-op calls continue (outcomes so far carried over)
+        sf_status gs = grow_dev(h, &h->dprog, h->dprog_cap, 4);
+        if (gs) return gs;
+        if (!h->hprog) SF_CK(h, pinned_alloc_n(&h->hprog, 4));
+        sf_status st = sf_apply_program(h, reinterpret_cast<const sf_op*>(h->dops), n_ops, drop_eps, 0,
+                                        reinterpret_cast<uint64_t*>(h->dprog),
+                                        reinterpret_cast<uint64_t*>(h->dprog + 1));
+        if (st) return st;
+        SF_CK(h, cudaMemcpyAsync(h->hprog, h->dprog, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 h->stream));
+        st = sync_check(h);
+        if (st) return st;
+        i = h->hprog[0];
+        bits = h->hprog[1];
+        done_m = (uint32_t)h->hprog[2];
+    }
     std::vector<sf_gate> gates;
     auto flush = [&]() -> sf_status {
         if (gates.empty()) return SF_OK;
@@ -629,7 +674,6 @@ sf_status sf_run_program(sf_handle h, const sf_op* ops, uint64_t n_ops, double d
         gates.clear();
         return st;
     };
-    uint64_t i = 0;
     while (i < n_ops) {
         const sf_op& o = ops[i];
         if (o.kind <= SF_SWAP || (o.kind >= SF_OP_DIAG && o.kind <= SF_OP_DIAG + SF_CPHASE)) {
@@ -637,23 +681,15 @@ sf_status sf_run_program(sf_handle h, const sf_op* ops, uint64_t n_ops, double d
             while (j < n_ops && (ops[j].kind <= SF_SWAP ||
                                  (ops[j].kind >= SF_OP_DIAG && ops[j].kind <= SF_OP_DIAG + SF_CPHASE)))
                 j++;
-            if (grid) {
-                sf_status st = flush();
+            sf_status st = SF_OK;
+            if (w1 && !one_cta) {
+                st = flush();
                 if (!st) st = sf_apply_program_grid(h, reinterpret_cast<const sf_op*>(h->dops + i), j - i, drop_eps,
                                                     nullptr);
-                if (st) return st;
             } else {
-                for (uint64_t r = i; r < j; r++) {
-                    const sf_op& q = ops[r];
-                    if (q.kind <= SF_SWAP) {
-                        gates.push_back(sf_gate{q.kind, q.q0, q.q1, 0u});
-                        continue;
-                    }
-                    sf_status st = flush();
-                    if (!st) st = sf_apply_nonclifford_coalesce(h, q.kind - SF_OP_DIAG, q.q0, q.q1, q.param, drop_eps);
-                    if (st) return st;
-                }
+                st = run_stretch_per_op(h, ops, i, j, drop_eps, gates);
             }
+            if (st) return st;
             i = j;
             continue;
         }

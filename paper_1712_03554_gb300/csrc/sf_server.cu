@@ -78,54 +78,14 @@ struct sf_server_s {
 
 namespace {
 
-// run one request on a slot's handle; fills the result's status and outputs
+// run one request on a slot's handle; fills the result's status and outputs.
+// The GPU is shared with the other slots, so the program runs without
+// whole-GPU launches: on one CTA while the frame is small, then per op.
 void execute(sf_handle h, const Request& rq, sf_result& res) {
     const uint32_t Wabi = (rq.n + 63) / 64;
-    std::vector<sf_gate> gates;
     uint64_t outcomes = 0;
     uint32_t nm = 0;
-    sf_status st = SF_OK;
-    size_t i = 0;
-    const size_t m = rq.ops.size();
-    auto flush = [&]() -> sf_status {
-        if (gates.empty()) return SF_OK;
-        sf_status s = sf_apply_clifford(h, gates.data(), gates.size());
-        gates.clear();
-        return s;
-    };
-    while (i < m && st == SF_OK) {
-        const sf_op& op = rq.ops[i];
-        if (op.kind <= 8) {
-            gates.push_back(sf_gate{op.kind, op.q0, op.q1, 0u});
-        } else if (op.kind == SF_OP_COND) {
-            uint64_t mask;
-            std::memcpy(&mask, &op.param, sizeof(mask));
-            if (op.arg > 8) {
-                st = SF_EINVAL;
-            } else if (__builtin_popcountll(outcomes & mask) & 1) {
-                gates.push_back(sf_gate{op.arg, op.q0, op.q1, 0u});
-            }
-        } else if (op.kind >= SF_OP_DIAG && op.kind < SF_OP_DIAG + 4) {
-            st = flush();
-            if (st == SF_OK)
-                st = sf_apply_nonclifford_coalesce(h, op.kind - SF_OP_DIAG, op.q0, op.q1, op.param, rq.eps);
-        } else if (op.kind == SF_OP_MEASURE) {
-            st = flush();
-            double p0 = 0.0, p1 = 0.0;
-            if (st == SF_OK && nm >= 64) st = SF_EINVAL;
-            if (st == SF_OK) st = sf_measure(h, op.q0, -1, &p0, &p1);
-            if (st == SF_OK) {
-                const int x = op.param < p1 ? 1 : 0;
-                st = sf_measure(h, op.q0, x, nullptr, nullptr);
-                if (x) outcomes |= 1ull << nm;
-                nm++;
-            }
-        } else {
-            st = SF_EINVAL;
-        }
-        i++;
-    }
-    if (st == SF_OK) st = flush();
+    sf_status st = sf_run_program(h, rq.ops.data(), rq.ops.size(), rq.eps, &outcomes, &nm, SF_RUN_ONE_CTA);
     uint64_t k = 0;
     if (st == SF_OK) st = sf_size(h, &k);  // synchronises: reports deferred device errors
     for (uint32_t p = 0; p < rq.n_probes && st == SF_OK; p++)

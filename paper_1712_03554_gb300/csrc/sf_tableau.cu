@@ -521,6 +521,39 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
     int r = d.meta[0];
     int ga = 0, gb = 0;  // the run's phase factor omega^ga sqrt(2)^gb
     __syncthreads();
+    // A run of monomial gates (S, S-dagger, X, Y, Z, CNOT, CZ, SWAP: each maps a
+    // basis state to one basis state times a power of i) is repaired once, at its
+    // end: the rows are conjugated gate by gate, and the run's phase factor comes
+    // from one basis point b carried through it (U|b> = i^k |b'> gives
+    // <b'|U psi> = i^k <b|psi>), starting at b = 0 where <0|phi_0(M)> = 2^{-r/2};
+    // the new representation's amplitude at the final b is then evaluated once.
+    // T.t1 holds the run's composed sign flips.  An H gate closes the run and is
+    // repaired by itself, as before.
+    int run_len = 0, r_run = r;
+    if (h < W) S.y2[h] = 0;
+    if (h == 0) S.iv[0] = 0;
+    auto close_run = [&]() -> bool {
+        r = cta_rref<W, true, false>(T, n, NT, S);
+        if (r < 0) {
+            if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 9u);
+            return false;
+        }
+        const int dq = cta_amp_phi<W>(T, n, NT, r, T.t1, S.y2, S);
+        if (dq < 0) {
+            if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 2u);
+            return false;
+        }
+        ga = (ga + 2 * S.iv[0] + 2 * ((4 - dq) & 3)) & 7;
+        gb += r - r_run;
+        run_len = 0;
+        if (h < W) S.y2[h] = 0;
+        if (h == 0) S.iv[0] = 0;
+        if (h < n) T.t1[h] = 0;
+        __syncthreads();
+        return true;
+    };
+    if (h < n) T.t1[h] = 0;
+    __syncthreads();
     for (int gi = 0; gi < ng; gi++) {
         const uint32_t ukind = gates[gi].kind, uq0 = gates[gi].q0, uq1 = gates[gi].q1;
         const bool two = ukind >= 6;
@@ -529,16 +562,49 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
             return;
         }
         const int kind = (int)ukind, q0 = (int)uq0, q1 = two ? (int)uq1 : 0;
-        // numerator of the phase rule: a point y with <y|U phi_0(M)> != 0, in units of 2^{-r/2}
-        int yq = -1, cq = -1;
-        if (kind == 0) {
-            if (h < W) S.y[h] = (h == (q0 >> 6)) ? (1ull << (q0 & 63)) : 0ull;
+        if (kind != 0) {
+            // ---- monomial gate: conjugate the rows, move the reference point
+            if (run_len == 0) r_run = r;
+            if (h < n) {
+                const uint32_t f = (uint32_t)conj_row(kind, q0, q1, T.mx, T.mz, NT, h);
+                T.t0[h] ^= f;
+                T.t1[h] ^= f;
+                const int fd = conj_row(kind, q0, q1, T.dx, T.dz, NT, h);
+                T.de[h] = (T.de[h] + 2u * (uint32_t)fd) & 3u;
+            }
+            if (h == 0) {
+                uint64_t* b = S.y2;
+                const int b0 = (int)((b[q0 >> 6] >> (q0 & 63)) & 1);
+                const int b1 = two ? (int)((b[q1 >> 6] >> (q1 & 63)) & 1) : 0;
+                int k = S.iv[0];
+                switch (kind) {
+                    case 1: k += b0; break;                                   // S
+                    case 2: k += 3 * b0; break;                               // S-dagger
+                    case 3: b[q0 >> 6] ^= 1ull << (q0 & 63); break;           // X
+                    case 4: k += 1 + 2 * b0; b[q0 >> 6] ^= 1ull << (q0 & 63); break;  // Y
+                    case 5: k += 2 * b0; break;                               // Z
+                    case 6: if (b0) b[q1 >> 6] ^= 1ull << (q1 & 63); break;   // CNOT
+                    case 7: k += 2 * (b0 & b1); break;                        // CZ
+                    default:                                                  // SWAP
+                        if (b0 != b1) {
+                            b[q0 >> 6] ^= 1ull << (q0 & 63);
+                            b[q1 >> 6] ^= 1ull << (q1 & 63);
+                        }
+                }
+                S.iv[0] = k & 3;
+            }
+            run_len++;
             __syncthreads();
-            cq = cta_amp_phi<W>(T, n, NT, r, nullptr, S.y, S);
-            if (cq == 2) yq = q0;
-        } else if (kind == 3 || kind == 4) {
-            yq = q0;
+            continue;
         }
+        if (run_len > 0 && !close_run()) return;
+        // ---- H: numerator of the phase rule, a point y with <y|U phi_0(M)> != 0,
+        // in units of 2^{-r/2}
+        int yq = -1, cq = -1;
+        if (h < W) S.y[h] = (h == (q0 >> 6)) ? (1ull << (q0 & 63)) : 0ull;
+        __syncthreads();
+        cq = cta_amp_phi<W>(T, n, NT, r, nullptr, S.y, S);
+        if (cq == 2) yq = q0;
         int na, nb;
         cliff_num_exp(kind, cq, na, nb);
         const int r_old = r;
@@ -553,9 +619,8 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
             T.t1[h] = 0;
         }
         __syncthreads();
-        // Pauli gates flip signs only: M keeps its bits and stays in RREF.  The
-        // rows stay where they are until the end of the batch (one sort there)
-        if (kind < 3 || kind > 5) r = cta_rref<W, true, false>(T, n, NT, S);
+        // the rows stay where they are until the end of the batch (one sort there)
+        r = cta_rref<W, true, false>(T, n, NT, S);
         if (r < 0) {
             if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 9u);
             return;
@@ -571,8 +636,10 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
         const int dr = r - r_old;
         ga = (ga + na + 2 * ((4 - dq) & 3)) & 7;
         gb += nb + (dr > 0) - (dr < 0);
+        if (h < n) T.t1[h] = 0;
         __syncthreads();
     }
+    if (run_len > 0 && !close_run()) return;
     r = cta_sort_rows<W, true>(T, n, NT, S);
     store_tableau<W>(d, T, r);
     if (h == 0) *d.g = cmul(*d.g, cliff_factor(ga, gb));

@@ -74,7 +74,7 @@ def load(build: bool = True) -> C.CDLL:
         "sf_apply_nonclifford_coalesce": ([H, u32, u32, u32, dbl, dbl], st),
         "sf_apply_program": ([H, C.c_void_p, u64, dbl, u64, C.c_void_p, C.c_void_p], st),
         "sf_apply_program_grid": ([H, C.c_void_p, u64, dbl, C.c_void_p], st),
-        "sf_run_program": ([H, C.c_void_p, u64, dbl, P64, C.POINTER(C.c_uint32)], st),
+        "sf_run_program": ([H, C.c_void_p, u64, dbl, P64, C.POINTER(C.c_uint32), u32], st),
         "sf_set_wait_limit": ([H, u32], st),
         "sf_grid_program_bytes": ([H, P64], st),
         "sf_set_trace": ([H, C.c_int32], st),
@@ -136,6 +136,7 @@ def load(build: bool = True) -> C.CDLL:
 
 COALESCE_NOALLOC_MAX_ELEMS = 65536
 WAIT_LIMIT_DEFAULT = 1048576
+RUN_ONE_CTA = 1
 
 
 def coalesce_noalloc(sigma_in: int, amp_in: int, k_in: int, n_words: int, drop_eps: float, sigma_out: int,
@@ -553,19 +554,20 @@ class Frame:
                                              g.ctypes.data_as(C.POINTER(C.c_double))), self.h)
         return dx, dz, de, complex(g[0], g[1])
 
-    def run_program_records(self, recs: np.ndarray, eps: float = 1e-12) -> Tuple[int, int]:
+    def run_program_records(self, recs: np.ndarray, eps: float = 1e-12, one_cta: bool = False) -> Tuple[int, int]:
         """sf_run_program on an array of sf_op records in host memory (the
-        library copies them); returns (outcome bits, number of measurements)."""
+        library copies them); returns (outcome bits, number of measurements).
+        one_cta: SF_RUN_ONE_CTA (no whole-GPU launch)."""
         recs = np.ascontiguousarray(recs)
         bits, nm = C.c_uint64(), C.c_uint32()
         self._check(self.lib.sf_run_program(self.h, recs.ctypes.data_as(C.c_void_p), len(recs), float(eps),
-                                            C.byref(bits), C.byref(nm)), self.h)
+                                            C.byref(bits), C.byref(nm), RUN_ONE_CTA if one_cta else 0), self.h)
         return int(bits.value), int(nm.value)
 
-    def run_program(self, ops, eps: float = 1e-12) -> Tuple[int, int]:
+    def run_program(self, ops, eps: float = 1e-12, one_cta: bool = False) -> Tuple[int, int]:
         """The ops (circuits.py vocabulary) as one sf_run_program call."""
         recs, _ = encode_program([ops])
-        return self.run_program_records(recs, eps)
+        return self.run_program_records(recs, eps, one_cta)
 
     def grid_program_bytes(self) -> int:
         """sf_grid_program_bytes: element bytes moved by the last grid program launch."""

@@ -246,15 +246,17 @@ def test_grid_program_stage_passes(sfm, seed):
     f.close()
 
 
+@pytest.mark.parametrize("one_cta", [False, True])
 @pytest.mark.parametrize("n,seed", [(10, 0), (30, 1), (63, 2), (70, 3), (200, 4)])
-def test_run_program_from_host_records(sfm, n, seed):
+def test_run_program_from_host_records(sfm, n, seed, one_cta):
     """sf_run_program: the whole circuit (Clifford gates, diagonal gates,
     measurements with draws, conditional gates) from host records, through the
-    grid program (n <= 63) or the per-op calls, against the oracle."""
+    grid program or, with SF_RUN_ONE_CTA, the single-CTA program (n <= 63),
+    or the per-op calls; against the oracle."""
     ops = clifford_diag_circuit(n, 9000 + seed, length=250, with_meas=True)
     ops += [("M", (3 * seed) % n, 0.37)]
     f = sfm.Frame(n, 1 << 16)
-    bits, nm = f.run_program(ops)
+    bits, nm = f.run_program(ops, one_cta=one_cta)
     o = oracle.FrameOracle(n)
     res = c.run(o, ops)
     assert nm == len(res)
@@ -269,11 +271,31 @@ def test_run_program_conditional_gates(sfm):
     n = 5
     ops = [("C", c.H, 0, 0), ("C", c.H, 1, 0), ("N", c.T, 0, 0, 0.0), ("K",), ("M", 0, 0.9), ("M", 1, 0.1),
            ("Q", c.X, 2, 0, 0b11), ("Q", c.H, 3, 0, 0b01), ("N", c.T, 3, 0, 0.0), ("K",), ("M", 3, 0.6)]
-    f = sfm.Frame(n, 1 << 10)
-    bits, nm = f.run_program(ops)
+    for one_cta in (False, True):
+        f = sfm.Frame(n, 1 << 10)
+        bits, nm = f.run_program(ops, one_cta=one_cta)
+        o = oracle.FrameOracle(n)
+        res = c.run(o, ops)
+        assert nm == 3 and bits == sum(r[3] << i for i, r in enumerate(res))
+        frames_equal(f, o)
+        f.close()
+
+
+def test_run_program_one_cta_outgrows_the_single_cta_limit(sfm):
+    """SF_RUN_ONE_CTA with a frame that outgrows the single-CTA limit (16384)
+    part way: the per-op calls continue with the outcomes so far, and a
+    conditional gate after the switch reads a measurement made on one CTA."""
+    n = 24
+    ops = [("C", c.H, q, 0) for q in range(n)] + [("M", 3, 0.2)]
+    for q in range(4, 20):
+        ops += [("N", c.T, q, 0, 0.0), ("K",)]
+    ops += [("Q", c.X, 0, 0, 0b1), ("N", c.T, 0, 0, 0.0), ("K",), ("M", 5, 0.7)]
+    f = sfm.Frame(n, 1 << 18)
+    bits, nm = f.run_program(ops, one_cta=True)
     o = oracle.FrameOracle(n)
     res = c.run(o, ops)
-    assert nm == 3 and bits == sum(r[3] << i for i, r in enumerate(res))
+    assert nm == 2 and bits == sum(r[3] << i for i, r in enumerate(res))
+    assert f.size() > 16384
     frames_equal(f, o)
     f.close()
 
