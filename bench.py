@@ -589,7 +589,7 @@ def _run_stream(sfm, stream, recs, slots, budget):
 
 
 def serving_leg(sfm, n_requests: int, slots: int, budget_gb: int = 96, fractions=(0.5, 0.8, 1.2),
-                cap_sample: int = 12):
+                cap_sample: int = 6):
     """The plain path's capacity (cap_sample requests queued at once, one at a
     time), then the same seeded stream at arrival rates fraction x capacity,
     served (continuous batching over `slots` slots) and one at a time."""
@@ -692,7 +692,7 @@ def main():
     ap.add_argument("--no-multiframe", action="store_true", help="skip the multiframe leg")
     ap.add_argument("--no-streaming", action="store_true",
                     help="skip the per-kernel roofline leg of the streaming kernels at 16 words per phase vector")
-    ap.add_argument("--serving-requests", type=int, default=24, help="requests per load point of the serving sweep")
+    ap.add_argument("--serving-requests", type=int, default=12, help="requests per load point of the serving sweep")
     ap.add_argument("--serving-slots", type=int, default=32)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
