@@ -415,6 +415,23 @@ sf_status sf_grid_program_trace(sf_handle h, uint64_t* rec, uint32_t cap, uint32
 #define SF_WAIT_LIMIT_DEFAULT 1048576u
 sf_status sf_set_wait_limit(sf_handle h, uint32_t polls);
 
+/* Low-rank forms of the per-element maps, for frames of 513..1024 qubits
+ * (and 257..512).  The phase-vector map of a Clifford batch (Sec. III, the row
+ * operations of Invariant 1) and the cofactor's old-to-new destabilizer map
+ * (COFACTOR, Sec. III) differ from the identity by a GF(2) matrix of small rank
+ * after one gate or one measurement.  With `on` (the default) a one-CTA kernel
+ * factors that difference, and the per-element kernels apply it with
+ * 2 r W word operations per element instead of one W-word row per set bit of
+ * the phase vector; a rank above 16 falls back to the per-bit form on the
+ * device, without a host round trip.  `on` = 0 always takes the per-bit form
+ * (the results are identical either way).  Takes effect at the next launch. */
+sf_status sf_set_lowrank(sf_handle h, int32_t on);
+/* Ranks of the last factorisations: ranks[0] the Clifford batch's map,
+ * ranks[1] and ranks[2] the cofactor's U ^ I and V; -1 where the rank exceeded
+ * 16, the form was switched off or never computed (always -1 below 257
+ * qubits).  ranks[1] is -1 also when V was above the limit.  Synchronises. */
+sf_status sf_lowrank_ranks(sf_handle h, int32_t* ranks);
+
 typedef struct sf_campaign_s* sf_campaign;
 
 /* Engine for circuits on n_qubits (1..63) whose frames never exceed

@@ -335,6 +335,7 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     d.W = n_qubits <= 63 ? 1 : std::max(2, pow2_at_least((int)((n_qubits + 63) / 64)));
     d.NT = std::max(32, (int)((n_qubits + 31) / 32) * 32);
     d.cap = max_elems;
+    d.lowrank = 1;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -755,6 +756,28 @@ sf_status sf_grid_program_trace(sf_handle h, uint64_t* rec, uint32_t cap, uint32
 sf_status sf_set_wait_limit(sf_handle h, uint32_t polls) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
     h->wait_limit = polls;
+    return SF_OK;
+}
+
+sf_status sf_set_lowrank(sf_handle h, int32_t on) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    h->d.lowrank = on ? 1 : 0;
+    return SF_OK;
+}
+
+sf_status sf_lowrank_ranks(sf_handle h, int32_t* ranks) {
+    if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
+    if (!ranks) return fail(h, SF_EINVAL, "ranks is NULL");
+    const int n = h->d.n, W = h->d.W;
+    const size_t off[3] = {plan_lr_aff(n, W), plan_lr_u(n, W), plan_lr_v(n, W)};
+    uint64_t v[3] = {SF_LR_NONE, SF_LR_NONE, SF_LR_NONE};
+    if (W >= 8) {
+        for (int i = 0; i < 3; i++)
+            SF_CK(h, cudaMemcpyAsync(&v[i], h->d.plan + off[i], sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
+        sf_status st = sync_check(h);
+        if (st) return st;
+    }
+    for (int i = 0; i < 3; i++) ranks[i] = v[i] > SF_LR_MAX ? -1 : (int32_t)v[i];
     return SF_OK;
 }
 

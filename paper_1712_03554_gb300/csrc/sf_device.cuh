@@ -57,7 +57,7 @@ struct SfDev {
     // slot table used by coalescing (children are hashed into it, amplitudes
     // accumulate there, the compaction pass empties it again)
     uint32_t* tstate;          // [tcap] 0 empty, 1 being written, 2 ready (W > 1 only)
-    uint64_t* tkey;            // [W][tcap] phase vector of the slot (W = 1: all ones = empty)
+    uint64_t* tkey;            // [tcap][W] phase vector of the slot (W = 1: all ones = empty)
     double2* tacc;             // [tcap] accumulated amplitude
     unsigned long long tcap;   // power of two >= 2 cap
     unsigned long long* tsize; // slots in use by the current merge
@@ -76,6 +76,7 @@ struct SfDev {
     unsigned long long* ipend; // index size chosen by CTA 0, published by the last CTA
     unsigned long long* ocnt;  // output counter of the merge kernels
     uint64_t* gp;              // workspace of the grid program (n <= 63 only)
+    int lowrank;               // 1: low-rank forms of the affine and cofactor maps (W >= 8)
 };
 
 // one program record (the layout of sf_op): kind, qubits, conditional-gate
@@ -110,7 +111,48 @@ __host__ __device__ inline size_t cf_vq(int n, int W) { return cf_tau(n, W) + 2 
 __host__ __device__ inline size_t cf_uq(int n, int W) { return cf_vq(n, W) + W; }
 // amplitude-query plan: y[W], zmask[W], zexp[W], flag
 __host__ __device__ inline size_t plan_am(int n, int W) { return cf_uq(n, W) + W; }
-__host__ __device__ inline size_t plan_words(int n, int W) { return plan_am(n, W) + 3 * W + 8; }
+// Low-rank factors of a GF(2) map given by n vectors R_h of W words (W >= 8).
+// Delta_h = R_h ^ e_h for maps near the identity (the affine map of a Clifford
+// gate, the cofactor's old-to-new destabilizer map U) or Delta_h = R_h (the
+// cofactor's V) is written Delta_h = sum_i C[h][i] B_i over a basis
+// B_0..B_{r-1}.  Block: [0] = r, or SF_LR_NONE when r > SF_LR_MAX; then
+// B[SF_LR_MAX][W]; then c[SF_LR_MAX][W], c_i = (C[h][i])_h as an n-bit vector.
+// (With the row sort's permutation rho split off first: see the move list.)
+#define SF_LR_MAX 16
+#define SF_LR_NONE 0xffffffffull
+__host__ __device__ inline size_t lr_words(int W) { return 2 + 2 * (size_t)SF_LR_MAX * W; }
+__host__ __device__ inline size_t lr_B(int W) { return 2; }
+__host__ __device__ inline size_t lr_C(int W) { return 2 + (size_t)SF_LR_MAX * W; }
+// the Clifford batch's map: factors of A ^ I (columns of A)
+__host__ __device__ inline size_t plan_lr_aff(int n, int W) { return plan_am(n, W) + 3 * W + 8; }
+// the cofactor's maps: factors of U ^ I and of V, then K_j[SF_LR_MAX][W] and
+// omega_y[2][W] of the closed-form i-power (k_cof_lowrank)
+__host__ __device__ inline size_t plan_lr_u(int n, int W) { return plan_lr_aff(n, W) + lr_words(W); }
+__host__ __device__ inline size_t plan_lr_v(int n, int W) { return plan_lr_u(n, W) + lr_words(W); }
+__host__ __device__ inline size_t plan_cf_k(int n, int W) { return plan_lr_v(n, W) + lr_words(W); }
+__host__ __device__ inline size_t plan_cf_om(int n, int W) { return plan_cf_k(n, W) + (size_t)SF_LR_MAX * W; }
+// The row sort that ends a Clifford batch or a measurement (Invariant 1)
+// moves the rows whose pivot changed; the others keep their relative order.
+// As a map of phase-vector bits: delete the bits at the old positions a_k
+// (ascending), then insert them at the new positions e_j (ascending), e_j
+// taking the bit of a_{src_j}; isrc is the inverse index.  Block: [0] = m, or
+// SF_LR_NONE when more than SF_MV_MAX rows moved; a[SF_MV_MAX], e[SF_MV_MAX],
+// src[SF_MV_MAX], isrc[SF_MV_MAX].  rho: the new position of every row, as
+// n 32-bit words.  The low-rank factors above are taken of Delta_h = R_h ^
+// e_{rho(h)}, i.e. after this permutation.
+#define SF_MV_MAX 8
+__host__ __device__ inline size_t mv_words() { return 1 + 4 * SF_MV_MAX; }
+__host__ __device__ inline size_t plan_mv_aff(int n, int W) { return plan_cf_om(n, W) + 2 * W; }
+__host__ __device__ inline size_t plan_mv_cf(int n, int W) { return plan_mv_aff(n, W) + mv_words(); }
+__host__ __device__ inline size_t plan_rho_aff(int n, int W) { return plan_mv_cf(n, W) + mv_words(); }
+__host__ __device__ inline size_t plan_rho_cf(int n, int W) { return plan_rho_aff(n, W) + (size_t)(n + 1) / 2; }
+// plan of a diagonal gate written by the one-CTA planning kernel (W >= 8),
+// 16-byte aligned
+#define SF_BR_WORDS(W) (8 + 20 * (W) + 32)
+__host__ __device__ inline size_t plan_br(int n, int W) {
+    return (plan_rho_cf(n, W) + (size_t)(n + 1) / 2 + 1) & ~(size_t)1;
+}
+__host__ __device__ inline size_t plan_words(int n, int W) { return plan_br(n, W) + SF_BR_WORDS(W); }
 
 // ---- Pauli arithmetic -------------------------------------------------------
 template <int W>

@@ -15,6 +15,8 @@
 //   k_export      canonical-convention amplitudes for export
 // Per-element kernels use a fixed grid of d.nblk CTAs and read the element
 // count from device memory, so no host synchronisation is needed between them.
+#include <type_traits>
+
 #include "sf_canon.cuh"
 
 namespace {
@@ -70,6 +72,9 @@ __global__ void __launch_bounds__(kThreads) k_affine(SfDev d, int buf) {
     extern __shared__ uint64_t tab[];
     if (*d.status) return;
     const int n = d.n, nc = (n + 3) >> 2;
+    if constexpr (W >= 8) {
+        if (d.plan[plan_lr_aff(n, W)] <= SF_LR_MAX) return;  // k_affine_lr applies the map
+    }
     const uint64_t* AT = d.plan + plan_AT(n, W);
     for (int e = threadIdx.x; e < nc * W * 16; e += blockDim.x) {
         const int v = e & 15, cw = e >> 4, w = cw % W, c = cw / W;
@@ -124,11 +129,13 @@ __global__ void __launch_bounds__(kThreads) k_affine(SfDev d, int buf) {
     }
 }
 
-// W = 16 (n > 512): iterate over the set bits of sigma, XOR-ing columns of A.
+// W = 16 (n > 512): iterate over the set bits of sigma, XOR-ing columns of A;
+// runs only when A ^ I has rank above SF_LR_MAX (k_affine_lr otherwise).
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_affine_cols(SfDev d, int buf) {
     if (*d.status) return;
     const int n = d.n;
+    if (d.plan[plan_lr_aff(n, W)] <= SF_LR_MAX) return;
     const uint64_t* AT = d.plan + plan_AT(n, W);
     uint64_t t[W];
 #pragma unroll
@@ -153,6 +160,241 @@ __global__ void __launch_bounds__(kThreads) k_affine_cols(SfDev d, int buf) {
             }
         }
         store_sig<W>(S, cap, j, o);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Low-rank form of a GF(2) map near a permutation (W >= 8).  One Clifford gate
+// or one measurement changes the tableau by a few row operations and then
+// sorts the rows by pivot, which moves the few rows whose pivot changed.  The
+// phase-vector map R it induces is therefore the sort's permutation rho plus a
+// matrix of small rank r: with Delta_h = R_h ^ e_{rho(h)} =
+// sum_i C[h][i] B_i, a product sum_{h in sigma} R_h is
+// rho(sigma) ^ sum_i parity(sigma & c_i) B_i -- a few bit moves and 2 r W
+// word operations per element instead of one W-word row per set bit of sigma
+// (n/2 on average).  The decomposition is exact for any rho; the sort's
+// permutation only makes r small.
+
+// the sort's permutation as bit moves, in shared memory (the plan's move list)
+struct Moves {
+    int m;
+    int a[SF_MV_MAX], e[SF_MV_MAX], src[SF_MV_MAX], isrc[SF_MV_MAX];
+};
+
+// threads 0..4*SF_MV_MAX; a __syncthreads must follow
+__device__ __forceinline__ void load_moves(const uint64_t* mv, Moves& M) {
+    const int t = threadIdx.x;
+    if (t == 0) M.m = (int)mv[0];
+    if (t < 4 * SF_MV_MAX) {
+        const int v = (int)mv[1 + t], k = t % SF_MV_MAX;
+        int* dst = t < SF_MV_MAX ? M.a : t < 2 * SF_MV_MAX ? M.e : t < 3 * SF_MV_MAX ? M.src : M.isrc;
+        dst[k] = v;
+    }
+}
+
+// bit p of a W-word vector (p uniform or not; no indexed register access)
+template <int W>
+__device__ __forceinline__ uint32_t bit_at(const uint64_t* v, int p) {
+    uint64_t r = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++)
+        if (w == (p >> 6)) r = (v[w] >> (p & 63)) & 1ull;
+    return (uint32_t)r;
+}
+
+// delete bit position p: the bits above it move down one, a zero enters at the top
+template <int W>
+__device__ __forceinline__ void bits_delete(uint64_t* v, int p) {
+    const int wp = p >> 6;
+    const uint64_t low = (1ull << (p & 63)) - 1ull;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        const uint64_t nxt = (w + 1 < W) ? v[w + 1] : 0ull;
+        const uint64_t sh = (v[w] >> 1) | (nxt << 63);
+        if (w > wp) v[w] = sh;
+        else if (w == wp) v[w] = (v[w] & low) | (sh & ~low);
+    }
+}
+
+// insert bit x at position p: the bits at and above it move up one (the top
+// bit of the vector, always zero here, leaves)
+template <int W>
+__device__ __forceinline__ void bits_insert(uint64_t* v, int p, uint32_t x) {
+    const int wp = p >> 6;
+    const uint64_t low = (1ull << (p & 63)) - 1ull, at = 1ull << (p & 63);
+#pragma unroll
+    for (int w = W - 1; w >= 0; w--) {
+        const uint64_t prv = w > 0 ? v[w - 1] : 0ull;
+        const uint64_t sh = (v[w] << 1) | (prv >> 63);
+        if (w > wp) v[w] = sh;
+        else if (w == wp) v[w] = (v[w] & low) | (sh & ~(low | at)) | ((uint64_t)x << (p & 63));
+    }
+}
+
+// v <- rho(v): bit h moves to rho(h)
+template <int W>
+__device__ __forceinline__ void apply_moves(uint64_t* v, const Moves& M) {
+    const int m = M.m;
+    uint32_t bits = 0;
+#pragma unroll 1
+    for (int k = 0; k < m; k++) bits |= bit_at<W>(v, M.a[k]) << k;
+#pragma unroll 1
+    for (int k = m - 1; k >= 0; k--) bits_delete<W>(v, M.a[k]);
+#pragma unroll 1
+    for (int j = 0; j < m; j++) bits_insert<W>(v, M.e[j], (bits >> M.src[j]) & 1u);
+}
+
+// v <- rho^{-1}(v)
+template <int W>
+__device__ __forceinline__ void apply_moves_inv(uint64_t* v, const Moves& M) {
+    const int m = M.m;
+    uint32_t bits = 0;
+#pragma unroll 1
+    for (int j = 0; j < m; j++) bits |= bit_at<W>(v, M.e[j]) << j;
+#pragma unroll 1
+    for (int j = m - 1; j >= 0; j--) bits_delete<W>(v, M.e[j]);
+#pragma unroll 1
+    for (int k = 0; k < m; k++) bits_insert<W>(v, M.a[k], (bits >> M.isrc[k]) & 1u);
+}
+
+// Gaussian elimination over the n vectors Delta_h, one thread per vector
+// (x: this thread's vector, zero for threads h >= n; consumed): each round the
+// first vector not yet in the span of B_0..B_{m-1} becomes B_m (pivot: its
+// lowest set bit), and every thread clears that pivot from its own remainder.
+// B_m has the pivots of B_0..B_{m-1} clear, so clearing pivot m never sets an
+// earlier one, and a remainder that reaches zero is the sum of the B_i it
+// used.  blockDim.x >= n, a multiple of 32.  Writes the block at out (r, B,
+// c) and returns r, or -1 when r would exceed SF_LR_MAX (the block then reads
+// SF_LR_NONE).
+template <int W>
+__device__ int cta_lowrank(uint64_t* x, int n, uint64_t* out) {
+    __shared__ uint64_t B[SF_LR_MAX][W];
+    __shared__ int piv[SF_LR_MAX];
+    __shared__ int first;
+    __shared__ uint32_t cb[SF_LR_MAX][32];
+    const int h = threadIdx.x;
+    uint32_t used = 0;
+    int r = 0;
+    for (;;) {
+        if (h == 0) first = 0x7fffffff;
+        __syncthreads();
+        bool nz = false;
+#pragma unroll
+        for (int w = 0; w < W; w++) nz |= x[w] != 0ull;
+        if (nz) atomicMin(&first, h);
+        __syncthreads();
+        const int f = first;
+        if (f == 0x7fffffff) break;
+        if (r == SF_LR_MAX) {
+            r = -1;
+            break;
+        }
+        if (h == f) {
+            int p = -1;
+#pragma unroll
+            for (int w = W - 1; w >= 0; w--)
+                if (x[w]) p = 64 * w + __ffsll((long long)x[w]) - 1;
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                B[r][w] = x[w];
+                x[w] = 0ull;
+            }
+            piv[r] = p;
+            used |= 1u << r;
+        }
+        __syncthreads();
+        if (bit_at<W>(x, piv[r])) {
+#pragma unroll
+            for (int w = 0; w < W; w++) x[w] ^= B[r][w];
+            used |= 1u << r;
+        }
+        r++;
+    }
+    if (r < 0) {
+        if (h == 0) out[0] = SF_LR_NONE;
+        __syncthreads();
+        return -1;
+    }
+    for (int e = h; e < SF_LR_MAX * 32; e += blockDim.x) cb[e >> 5][e & 31] = 0u;
+    __syncthreads();
+    for (int i = 0; i < r; i++) {
+        const unsigned bal = __ballot_sync(SF_FULL, (used >> i) & 1u);
+        if ((h & 31) == 0) cb[i][h >> 5] = bal;
+    }
+    __syncthreads();
+    if (h == 0) out[0] = (uint64_t)r;
+    for (int e = h; e < r * W; e += blockDim.x) {
+        const int i = e / W, w = e % W;
+        out[lr_B(W) + (size_t)i * W + w] = B[i][w];
+        out[lr_C(W) + (size_t)i * W + w] = (uint64_t)cb[i][2 * w] | ((uint64_t)cb[i][2 * w + 1] << 32);
+    }
+    __syncthreads();
+    return r;
+}
+
+// factors of the Clifford batch's map (columns of A: sigma' = sum_{j in sigma}
+// col_j ^ t), with Delta_j = col_j ^ e_{rho(j)}
+template <int W>
+__global__ void __launch_bounds__(1024) k_affine_lowrank(SfDev d) {
+    if (*d.status) return;
+    const int n = d.n, h = threadIdx.x;
+    uint64_t* out = d.plan + plan_lr_aff(n, W);
+    if (!d.lowrank || d.plan[plan_mv_aff(n, W)] > SF_MV_MAX) {
+        if (h == 0) out[0] = SF_LR_NONE;
+        return;
+    }
+    uint64_t x[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) x[w] = h < n ? d.plan[plan_AT(n, W) + (size_t)h * W + w] : 0ull;
+    if (h < n) {
+        const int p = (int)reinterpret_cast<const uint32_t*>(d.plan + plan_rho_aff(n, W))[h];
+#pragma unroll
+        for (int w = 0; w < W; w++)
+            if (w == (p >> 6)) x[w] ^= 1ull << (p & 63);
+    }
+    cta_lowrank<W>(x, n, out);
+}
+
+// sigma' = rho(sigma) ^ t ^ sum_i parity(sigma & c_i) B_i; does nothing when
+// the low-rank form is not available (the dense kernel applies the map then)
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_affine_lr(SfDev d, int buf) {
+    __shared__ uint64_t B[SF_LR_MAX][W], C[SF_LR_MAX][W], t[W];
+    __shared__ Moves M;
+    if (*d.status) return;
+    const int n = d.n;
+    const uint64_t* L = d.plan + plan_lr_aff(n, W);
+    const uint64_t rr = L[0];
+    if (rr > SF_LR_MAX) return;
+    const int r = (int)rr;
+    for (int e = threadIdx.x; e < r * W; e += blockDim.x) {
+        B[e / W][e % W] = L[lr_B(W) + e];
+        C[e / W][e % W] = L[lr_C(W) + e];
+    }
+    if (threadIdx.x < W) t[threadIdx.x] = d.plan[plan_t(n, W) + threadIdx.x];
+    load_moves(d.plan + plan_mv_aff(n, W), M);
+    __syncthreads();
+    const unsigned long long k = d.kcnt[buf];
+    uint64_t* S = d.sig[buf];
+    const uint64_t cap = d.cap;
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        uint64_t s[W];
+        load_sig<W>(S, cap, j, s);
+        uint32_t sel = 0;
+#pragma unroll 1
+        for (int i = 0; i < r; i++) sel |= (uint32_t)(popc_and<W>(C[i], s) & 1) << i;
+        apply_moves<W>(s, M);
+#pragma unroll
+        for (int w = 0; w < W; w++) s[w] ^= *(const volatile uint64_t*)&t[w];
+#pragma unroll 1
+        for (int i = 0; i < r; i++) {
+            if ((sel >> i) & 1u) {
+#pragma unroll
+                for (int w = 0; w < W; w++) s[w] ^= B[i][w];
+            }
+        }
+        store_sig<W>(S, cap, j, s);
     }
 }
 
@@ -307,6 +549,143 @@ __device__ void warp_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uin
     }
 }
 
+// The same plan computed once per gate by one CTA of kPlanThreads threads and
+// written to the plan area (W >= 8, where the 16-word Pauli products would
+// otherwise set the register count of every streaming kernel and each of
+// their CTAs would read the whole tableau).  Thread t reads the rows
+// h = t, t + kPlanThreads, ...; u_h reads only the words of the term's qubits.
+// The partial products of distinct rows commute (D_h and M_k anticommute only
+// for h = k, and both factors of one h stay in one thread, D_h first), so the
+// warps' partials may be multiplied in any order.
+constexpr int kPlanThreads = 256;
+
+template <int W>
+__global__ void __launch_bounds__(kPlanThreads) k_branch_plan(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1,
+                                                              SfTerms tm) {
+    __shared__ uint64_t su[SF_BR_MAXT][W], sv[SF_BR_MAXT][W], sodd[W];
+    __shared__ Pauli<W> part[kPlanThreads / 32];
+    __shared__ int epsq[SF_BR_MAXT], sbad;
+    __shared__ BrPlan<W> P;
+    static_assert(sizeof(BrPlan<W>) <= 8 * SF_BR_WORDS(W), "branch plan area too small");
+    if (*d.status) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, n = d.n;
+    const int nt = kind <= 2 ? 2 : 4;
+    const int qa[SF_BR_MAXT] = {-1, (int)q0, (int)q1, (int)q0};
+    for (int e = tid; e < SF_BR_MAXT * W; e += blockDim.x) {
+        su[e / W][e % W] = 0ull;
+        sv[e / W][e % W] = 0ull;
+    }
+    if (tid < W) sodd[tid] = 0ull;
+    if (tid == 0) {
+        sbad = 0;
+        for (int j = 0; j < SF_BR_MAXT; j++) epsq[j] = 0;
+    }
+    __syncthreads();
+    for (int h = tid; h < n; h += blockDim.x)
+        if (__ldg(&d.de[h]) & 1u) atomicOr(reinterpret_cast<unsigned long long*>(&sodd[h >> 6]), 1ull << (h & 63));
+    // terms 1 (and 2 for the two-qubit gates); the identity needs no pass and the
+    // Z_c Z_t term follows from the other two
+    for (int j = 1; j < nt && j <= 2; j++) {
+        uint64_t wz[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) wz[w] = 0ull;
+        wz[qa[j] >> 6] ^= 1ull << (qa[j] & 63);
+        Pauli<W> p;
+        pauli_id<W>(p);
+        for (int h = tid; h < n; h += blockDim.x) {
+            const int qw = qa[j] >> 6, qs = qa[j] & 63;
+            const bool ub = (__ldg(&d.mx[qw * n + h]) >> qs) & 1ull;
+            const bool vb = (__ldg(&d.dx[qw * n + h]) >> qs) & 1ull;
+            if (ub) {
+                Pauli<W> dh;
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    dh.x[w] = __ldg(&d.dx[w * n + h]);
+                    dh.z[w] = __ldg(&d.dz[w * n + h]);
+                }
+                dh.e = (int)__ldg(&d.de[h]);
+                pauli_mul<W>(p, dh);
+                atomicOr(reinterpret_cast<unsigned long long*>(&su[j][h >> 6]), 1ull << (h & 63));
+            }
+            if (vb) {
+                Pauli<W> mh;
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    mh.x[w] = __ldg(&d.mx[w * n + h]);
+                    mh.z[w] = __ldg(&d.mz[w * n + h]);
+                }
+                mh.e = 0;
+                pauli_mul<W>(p, mh);
+                atomicOr(reinterpret_cast<unsigned long long*>(&sv[j][h >> 6]), 1ull << (h & 63));
+            }
+        }
+        warp_pauli_product<W>(p);
+        if (lane == 0) part[wid] = p;
+        __syncthreads();
+        if (tid == 0) {
+            Pauli<W> t = part[0];
+            for (int k = 1; k < (int)(blockDim.x >> 5); k++) pauli_mul<W>(t, part[k]);
+            int bad = 0;
+            for (int w = 0; w < W; w++)
+                if (t.x[w] != 0ull || t.z[w] != wz[w]) bad = 1;
+            sbad |= bad;
+            epsq[j] = (4 - t.e) & 3;
+        }
+        __syncthreads();
+    }
+    if (tid != 0) return;
+    if (kind == 3) {  // as in warp_branch_plan
+        int par = 0;
+        for (int w = 0; w < W; w++) {
+            su[3][w] = su[1][w] ^ su[2][w];
+            sv[3][w] = sv[1][w] ^ sv[2][w];
+            par += __popcll(sv[1][w] & su[2][w]) + __popcll(su[1][w] & su[2][w] & sodd[w]);
+        }
+        epsq[3] = (epsq[1] + epsq[2] + 2 * par) & 3;
+    }
+    int gid[SF_BR_MAXT];
+    int ng = 0;
+    for (int j = 0; j < nt; j++) {
+        int found = -1;
+        for (int j2 = 0; j2 < j; j2++) {
+            bool same = true;
+            for (int w = 0; w < W; w++) same &= su[j2][w] == su[j][w];
+            if (same) { found = gid[j2]; break; }
+        }
+        gid[j] = found >= 0 ? found : ng++;
+    }
+    P.ng = ng;
+    P.bad = sbad;
+    for (int g = 0; g < SF_BR_MAXG; g++) P.nt[g] = 0;
+    for (int j = 0; j < nt; j++) {
+        const int g = gid[j], t = P.nt[g]++;
+        for (int w = 0; w < W; w++) {
+            P.u[g][w] = su[j][w];
+            P.v[g][t][w] = sv[j][w];
+        }
+        P.c[g][t] = ipow_mul(tm.c[j], epsq[j]);
+    }
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(&P);
+    uint64_t* dst = d.plan + plan_br(n, W);
+    for (size_t e = 0; e < sizeof(BrPlan<W>) / 8; e++) dst[e] = src[e];
+}
+
+// the plan of the current diagonal gate in shared memory: computed in place by
+// warp 0 (W <= 4) or copied from the planning kernel's output (W >= 8);
+// followed by a __syncthreads
+template <int W>
+__device__ __forceinline__ void get_branch_plan(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1,
+                                                const SfTerms& tm, BrPlan<W>& P) {
+    if constexpr (W >= 8) {
+        const uint64_t* src = d.plan + plan_br(d.n, W);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(&P);
+        for (int e = threadIdx.x; e < (int)(sizeof(BrPlan<W>) / 8); e += blockDim.x) dst[e] = src[e];
+    } else {
+        if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, tm, P);
+    }
+    __syncthreads();
+}
+
 // coefficient of group g for phase vector s
 template <int W>
 __device__ __forceinline__ double2 group_coef(const BrPlan<W>& P, int g, const uint64_t* s) {
@@ -326,8 +705,7 @@ __global__ void __launch_bounds__(kThreads) k_branch(SfDev d, uint32_t kind, uin
                                                      int in_buf, int out_buf) {
     __shared__ BrPlan<W> P;
     if (*d.status) return;
-    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, tm, P);
-    __syncthreads();
+    get_branch_plan<W>(d, kind, q0, q1, tm, P);
     if (P.bad) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 23u);
         return;
@@ -365,10 +743,11 @@ __global__ void __launch_bounds__(kThreads) k_branch(SfDev d, uint32_t kind, uin
 // Slot table.  W = 1: the key word itself is claimed by compare-and-swap
 // (all ones = empty, never a phase vector).  W > 1: a state word is claimed
 // (empty -> being written), the key is written, then published (ready);
-// readers of a slot being written wait for it with a bounded spin.
+// readers of a slot being written wait for it with a bounded spin.  Keys are
+// slot-major (the W words of a slot contiguous): a random insert or compare
+// touches one W * 8-byte run instead of W separate sectors.
 template <int W>
 __device__ __forceinline__ bool table_insert(const SfDev& d, unsigned long long T, const uint64_t* key, double2 c) {
-    const unsigned long long tcap = d.tcap;
     unsigned long long slot = hash_sig<W>(key) & (T - 1);
     for (unsigned long long probe = 0; probe < T; probe++) {
         if constexpr (W == 1) {
@@ -386,7 +765,7 @@ __device__ __forceinline__ bool table_insert(const SfDev& d, unsigned long long 
                 st = atomicCAS(&d.tstate[slot], 0u, 1u);
                 if (st == 0) {
 #pragma unroll
-                    for (int w = 0; w < W; w++) d.tkey[(size_t)w * tcap + slot] = key[w];
+                    for (int w = 0; w < W; w++) d.tkey[slot * W + w] = key[w];
                     __threadfence();
                     atomicExch(&d.tstate[slot], 2u);
                     atomicAdd(&d.tacc[slot].x, c.x);
@@ -399,7 +778,7 @@ __device__ __forceinline__ bool table_insert(const SfDev& d, unsigned long long 
             __threadfence();
             bool eq = true;
 #pragma unroll
-            for (int w = 0; w < W; w++) eq &= (*(volatile uint64_t*)&d.tkey[(size_t)w * tcap + slot] == key[w]);
+            for (int w = 0; w < W; w++) eq &= (*(volatile uint64_t*)&d.tkey[slot * W + w] == key[w]);
             if (eq) {
                 atomicAdd(&d.tacc[slot].x, c.x);
                 atomicAdd(&d.tacc[slot].y, c.y);
@@ -502,7 +881,6 @@ __global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, doub
     const unsigned long long TI = index_slots(T / 2, d.icap);
     const uint32_t tag = next_tag(d.itag[out_buf]);
     bool ok = true;
-    const unsigned long long tcap = d.tcap;
     const int lane = threadIdx.x & 31;
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -526,7 +904,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, doub
                 a = d.tacc[i];
                 if constexpr (W > 1) {
 #pragma unroll
-                    for (int w = 0; w < W; w++) key[w] = d.tkey[(size_t)w * tcap + i];
+                    for (int w = 0; w < W; w++) key[w] = d.tkey[i * W + w];
                     d.tstate[i] = 0u;
                 } else {
                     d.tkey[i] = SF_EMPTY_KEY;
@@ -768,8 +1146,7 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
         }
         return;
     }
-    if (threadIdx.x < 32) warp_branch_plan<W>(d, kind, q0, q1, tm, P);
-    __syncthreads();
+    get_branch_plan<W>(d, kind, q0, q1, tm, P);
     // xidx[g][g2]: the group whose u is u_g ^ u_g2 (threads 0-15, one entry
     // each); threads 32-95: the coefficient of each group per sign pattern
     int bad = 0;
@@ -889,15 +1266,248 @@ __device__ __forceinline__ bool sig_less(const uint64_t* a, const uint64_t* b) {
     return false;
 }
 
+// Closed form of the cofactor children for W >= 8.  cof_child walks the set
+// bits h of sigma in increasing order: t starts at tau_y, each h adds
+// eps_h + 2 [V_h . t] to the i-power and then XORs U_h into t.  With the
+// measurement's row sort rho split off, U_h = e_{rho(h)} ^ sum_i CU[h][i] B_i,
+// and V'_h = rho^{-1}(V_h) = sum_j CV[h][j] F_j (cta_lowrank):
+//   t = tau_y ^ t0,  t0 = rho(sigma) ^ sum_i parity(sigma & cu_i) B_i,
+//   ip = |sigma & eps0| + 2 |sigma & eps1| + 2 (parity(sigma & omega_y) ^ Q),
+// where omega_y[h] = V_h . tau_y = sum_j (rho(F_j) . tau_y) cv_j[h] and the
+// ordered part Q = sum_{h in sigma} V_h . (sum_{h' in sigma, h' < h} U_h') is,
+// with K_j = F_j ^ sum_i (rho(F_j) . B_i) cu_i (V_h . rho(x) = V'_h . x),
+//   Q = sum_j parity(sigma & cv_j & xpp(sigma & K_j)),
+// xpp(b)[h] the parity of the bits of b below h.  k_cof_lowrank writes K_j and
+// omega_y; the U block's rank word reads SF_LR_NONE when the move list or
+// either rank is over its limit (the dense kernel runs then).
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_cof_merge(SfDev d, double eps2, int in_buf, int out_buf) {
-    __shared__ CofPlan<W> CP;
+__global__ void __launch_bounds__(1024) k_cof_lowrank(SfDev d) {
+    __shared__ int G[SF_LR_MAX][SF_LR_MAX], ft[SF_LR_MAX][2];
+    __shared__ uint64_t Fr[SF_LR_MAX][W];
+    __shared__ Moves M;
+    if (*d.status) return;
+    if (!d.meta[2]) return;
+    const int n = d.n, tid = threadIdx.x;
+    uint64_t* pl = d.plan;
+    uint64_t* LU = pl + plan_lr_u(n, W);
+    uint64_t* LV = pl + plan_lr_v(n, W);
+    if (!d.lowrank || pl[plan_mv_cf(n, W)] > SF_MV_MAX) {
+        if (tid == 0) {
+            LU[0] = SF_LR_NONE;
+            LV[0] = SF_LR_NONE;
+        }
+        return;
+    }
+    load_moves(pl + plan_mv_cf(n, W), M);
+    __syncthreads();
+    uint64_t x[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) x[w] = tid < n ? pl[cf_u(n, W) + (size_t)tid * W + w] : 0ull;
+    if (tid < n) {
+        const int p = (int)reinterpret_cast<const uint32_t*>(pl + plan_rho_cf(n, W))[tid];
+#pragma unroll
+        for (int w = 0; w < W; w++)
+            if (w == (p >> 6)) x[w] ^= 1ull << (p & 63);
+    }
+    const int ru = cta_lowrank<W>(x, n, LU);
+#pragma unroll
+    for (int w = 0; w < W; w++) x[w] = tid < n ? pl[cf_v(n, W) + (size_t)tid * W + w] : 0ull;
+    apply_moves_inv<W>(x, M);
+    const int rv = cta_lowrank<W>(x, n, LV);
+    if (ru < 0 || rv < 0) {
+        if (tid == 0) LU[0] = SF_LR_NONE;
+        return;
+    }
+    if (tid < rv) {  // rho(F_j)
+        uint64_t f[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) f[w] = LV[lr_B(W) + (size_t)tid * W + w];
+        apply_moves<W>(f, M);
+#pragma unroll
+        for (int w = 0; w < W; w++) Fr[tid][w] = f[w];
+    }
+    __syncthreads();
+    for (int e = tid; e < rv * ru; e += blockDim.x) {
+        const int j = e / ru, i = e % ru;
+        G[j][i] = popc_and<W>(Fr[j], LU + lr_B(W) + (size_t)i * W) & 1;
+    }
+    for (int e = tid; e < 2 * rv; e += blockDim.x) {
+        const int j = e >> 1, y = e & 1;
+        ft[j][y] = popc_and<W>(Fr[j], pl + cf_tau(n, W) + (size_t)y * W) & 1;
+    }
+    __syncthreads();
+    for (int e = tid; e < rv * W; e += blockDim.x) {
+        const int j = e / W, w = e % W;
+        uint64_t k = LV[lr_B(W) + (size_t)j * W + w];
+        for (int i = 0; i < ru; i++)
+            if (G[j][i]) k ^= LU[lr_C(W) + (size_t)i * W + w];
+        pl[plan_cf_k(n, W) + (size_t)j * W + w] = k;
+    }
+    for (int e = tid; e < 2 * W; e += blockDim.x) {
+        const int y = e / W, w = e % W;
+        uint64_t o = 0ull;
+        for (int j = 0; j < rv; j++)
+            if (ft[j][y]) o ^= LV[lr_C(W) + (size_t)j * W + w];
+        pl[plan_cf_om(n, W) + (size_t)y * W + w] = o;
+    }
+    // An element s and its partner s ^ uq have the same children: child x of
+    // the partner has y' = y ^ c (c = parity(vq & uq)) and t0 shifted by
+    // U uq = rho(uq) ^ sum_i parity(uq & cu_i) B_i, so tau_{y^c} ^ tau_y must
+    // equal U uq.  Checked once here; k_cof_merge then takes the element's
+    // children for both.
+    if (tid == 0) {
+        const uint64_t* uq = pl + cf_uq(n, W);
+        const uint64_t* vq = pl + cf_vq(n, W);
+        const uint64_t* tau = pl + cf_tau(n, W);
+        const int c = popc_and<W>(vq, uq) & 1;
+        uint32_t sel = 0;
+        for (int i = 0; i < ru; i++) sel |= (uint32_t)(popc_and<W>(LU + lr_C(W) + (size_t)i * W, uq) & 1) << i;
+        uint64_t u[W];
+        for (int w = 0; w < W; w++) u[w] = uq[w];
+        apply_moves<W>(u, M);
+        bool ok = true;
+        for (int w = 0; w < W; w++) {
+            for (int i = 0; i < ru; i++)
+                if ((sel >> i) & 1u) u[w] ^= LU[lr_B(W) + (size_t)i * W + w];
+            ok &= (c ? (tau[w] ^ tau[W + w]) : 0ull) == u[w];
+        }
+        if (!ok) set_status(d.status, SF_ST_INTERNAL, 0, 27u);
+    }
+}
+
+template <int W>
+struct CofLR {
+    double2 kap[2];
+    int ru, rv;
+    Moves M;
+    uint64_t vq[W], eps0[W], eps1[W], tau[2][W], om[2][W];
+    uint64_t B[SF_LR_MAX][W], cu[SF_LR_MAX][W], cv[SF_LR_MAX][W], K[SF_LR_MAX][W];
+};
+
+template <int W>
+__device__ void load_cof_lr(const SfDev& d, CofLR<W>& C) {
+    const int n = d.n, tid = threadIdx.x;
+    const uint64_t* pl = d.plan;
+    const uint64_t* LU = pl + plan_lr_u(n, W);
+    const uint64_t* LV = pl + plan_lr_v(n, W);
+    const int ru = (int)LU[0], rv = (int)LV[0];
+    if (tid == 0) {
+        C.ru = ru;
+        C.rv = rv;
+        const size_t ko = cf_kappa(n, W);
+        C.kap[0] = make_double2(__longlong_as_double((long long)pl[ko]), __longlong_as_double((long long)pl[ko + 1]));
+        C.kap[1] = make_double2(__longlong_as_double((long long)pl[ko + 2]), __longlong_as_double((long long)pl[ko + 3]));
+    }
+    load_moves(pl + plan_mv_cf(n, W), C.M);
+    if (tid < W) {
+        C.vq[tid] = pl[cf_vq(n, W) + tid];
+        C.eps0[tid] = pl[cf_eps(n, W) + tid];
+        C.eps1[tid] = pl[cf_eps(n, W) + W + tid];
+        for (int y = 0; y < 2; y++) {
+            C.tau[y][tid] = pl[cf_tau(n, W) + y * W + tid];
+            C.om[y][tid] = pl[plan_cf_om(n, W) + y * W + tid];
+        }
+    }
+    for (int e = tid; e < ru * W; e += blockDim.x) {
+        C.B[e / W][e % W] = LU[lr_B(W) + e];
+        C.cu[e / W][e % W] = LU[lr_C(W) + e];
+    }
+    for (int e = tid; e < rv * W; e += blockDim.x) {
+        C.cv[e / W][e % W] = LV[lr_C(W) + e];
+        C.K[e / W][e % W] = pl[plan_cf_k(n, W) + e];
+    }
+}
+
+// the y-independent scalars of the closed form for phase vector s ^ m
+// (m = 0 for the element itself, uq for its partner)
+struct CofScal {
+    int pq, pe, pw[2], q;
+};
+
+// |a & b| with a read from shared memory at every use (volatile), so that the
+// plan's loop-invariant vectors are not hoisted into registers across the
+// element loop (seven of them would take 224 registers at W = 16)
+template <int W>
+__device__ __forceinline__ int popc_and_sh(const uint64_t* a, const uint64_t* b) {
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) c += __popcll(*(const volatile uint64_t*)&a[w] & b[w]);
+    return c;
+}
+
+template <int W>
+__device__ __forceinline__ void cof_scalars(const CofLR<W>& C, const uint64_t* s, const uint64_t* m, CofScal& E) {
+    uint64_t v[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) v[w] = s[w] ^ *(const volatile uint64_t*)&m[w];
+    E.pq = popc_and_sh<W>(C.vq, v) & 1;
+    E.pe = popc_and_sh<W>(C.eps0, v) + 2 * popc_and_sh<W>(C.eps1, v);
+    E.pw[0] = popc_and_sh<W>(C.om[0], v) & 1;
+    E.pw[1] = popc_and_sh<W>(C.om[1], v) & 1;
+    int q = 0;
+#pragma unroll 1
+    for (int j = 0; j < C.rv; j++) {
+        uint64_t carry = 0ull;  // all ones when the bits of v & K_j in lower words have odd parity
+        int cnt = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            const uint64_t b = v[w] & C.K[j][w];
+            uint64_t x = b;  // inclusive prefix parity within the word
+            x ^= x << 1;
+            x ^= x << 2;
+            x ^= x << 4;
+            x ^= x << 8;
+            x ^= x << 16;
+            x ^= x << 32;
+            cnt += __popcll(v[w] & C.cv[j][w] & ((x << 1) ^ carry));
+            carry ^= (x >> 63) ? ~0ull : 0ull;
+        }
+        q ^= cnt & 1;
+    }
+    E.q = q;
+}
+
+// t0 = rho(s) ^ sum_i parity(s & cu_i) B_i, in place
+template <int W>
+__device__ __forceinline__ void cof_t0(const CofLR<W>& C, uint64_t* s) {
+    uint32_t sel = 0;
+#pragma unroll 1
+    for (int i = 0; i < C.ru; i++) sel |= (uint32_t)(popc_and<W>(C.cu[i], s) & 1) << i;
+    apply_moves<W>(s, C.M);
+#pragma unroll 1
+    for (int i = 0; i < C.ru; i++) {
+        if ((sel >> i) & 1u) {
+#pragma unroll
+            for (int w = 0; w < W; w++) s[w] ^= C.B[i][w];
+        }
+    }
+}
+
+// amplitude of child x (y = x ^ pq) of an element with scalars E and amplitude a
+template <int W>
+__device__ __forceinline__ double2 cof_amp_lr(const CofLR<W>& C, const CofScal& E, double2 a, int x) {
+    const int y = x ^ E.pq;
+    const int ip = E.pe + 2 * (E.pw[y] ^ E.q);
+    return ipow_mul(cmul(C.kap[y], a), ip & 3);
+}
+
+template <int W, bool LR>
+__global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, double eps2, int in_buf, int out_buf) {
+    using Plan = typename std::conditional<LR, CofLR<W>, CofPlan<W>>::type;
+    __shared__ Plan CP;
     __shared__ uint64_t uq[W];
     __shared__ unsigned int wsum[kThreads / 32];
     __shared__ unsigned long long bbase;
     if (*d.status) return;
     if (!d.meta[2]) return;
-    if (threadIdx.x == 0) {
+    if constexpr (W >= 8) {
+        // exactly one of the two variants runs
+        if ((d.plan[plan_lr_u(d.n, W)] <= SF_LR_MAX) != LR) return;
+    }
+    if constexpr (LR) {
+        load_cof_lr<W>(d, CP);
+        if (threadIdx.x < W) uq[threadIdx.x] = d.plan[cf_uq(d.n, W) + threadIdx.x];
+    } else if (threadIdx.x == 0) {
         load_cof_plan<W>(d, CP);
         for (int w = 0; w < W; w++) uq[w] = d.plan[cf_uq(d.n, W) + w];
     }
@@ -935,9 +1545,46 @@ __global__ void __launch_bounds__(kThreads) k_cof_merge(SfDev d, double eps2, in
             own = l < 0 || sig_less<W>(s, p);
             if (l >= 0) ap = Ai[l];
         }
-        uint64_t t[2][W];
         double2 cc[2];
         unsigned keepm = 0;
+        if constexpr (LR) {
+            // the partner's children are the element's (checked on the plan by
+            // k_cof_lowrank); only their amplitudes differ
+            CofScal es, ep;
+            if (own) {
+                const uint64_t zero[W] = {};
+                cof_scalars<W>(CP, s, zero, es);
+                if (l >= 0) cof_scalars<W>(CP, s, uq, ep);
+                cof_t0<W>(CP, s);  // s now holds t0; the child x is tau_{x ^ pq} ^ t0
+            }
+            for (int x = 0; x < 2; x++) {
+                double2 c = make_double2(0.0, 0.0);
+                if (own) {
+                    c = cof_amp_lr<W>(CP, es, a, x);
+                    if (l >= 0) {
+                        const double2 c2 = cof_amp_lr<W>(CP, ep, ap, x);
+                        c.x += c2.x;
+                        c.y += c2.y;
+                    }
+                }
+                cc[x] = c;
+                if (own && amp_kept(c, kb, eps2)) keepm |= 1u << x;
+            }
+            unsigned long long o = block_out_range(d.ocnt, __popc(keepm), wsum, &bbase);
+#pragma unroll 1
+            for (int x = 0; x < 2; x++) {
+                if (!((keepm >> x) & 1u)) continue;
+                const int y = x ^ es.pq;
+                uint64_t t[W];
+#pragma unroll
+                for (int w = 0; w < W; w++) t[w] = *(const volatile uint64_t*)&CP.tau[y][w] ^ s[w];
+                store_sig<W>(So, cap, o, t);
+                Ao[o] = cc[x];
+                ok &= index_insert<W>(d, out_buf, Tout, tag_out, t, (uint32_t)o);
+                o++;
+            }
+        } else {
+        uint64_t t[2][W];
         for (int x = 0; x < 2; x++) {
             double2 c = make_double2(0.0, 0.0);
             if (own) {
@@ -964,8 +1611,8 @@ __global__ void __launch_bounds__(kThreads) k_cof_merge(SfDev d, double eps2, in
             ok &= index_insert<W>(d, out_buf, Tout, tag_out, t[x], (uint32_t)o);
             o++;
         }
-    }
-    if (!ok) set_status(d.status, SF_ST_TIMEOUT, in_buf);
+        }
+    }    if (!ok) set_status(d.status, SF_ST_TIMEOUT, in_buf);
     if (last_block(d.done) && threadIdx.x == 0) {
         d.kcnt[out_buf] = *d.ocnt;
         *d.ocnt = 0;
@@ -1160,6 +1807,15 @@ __global__ void __launch_bounds__(kThreads) k_export(SfDev d, int buf, int stage
 size_t sf_affine_smem_bytes(int n, int W) { return (size_t)((n + 3) / 4) * W * 16 * 8; }
 
 void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s) {
+    // W >= 8: the map's low-rank form, then whichever of the low-rank and the
+    // dense kernel the rank selects (the other returns at once)
+    if (d.W >= 8) {
+        const int nt = (d.n + 31) & ~31;
+        if (d.W == 16) k_affine_lowrank<16><<<1, nt, 0, s>>>(d);
+        else k_affine_lowrank<8><<<1, nt, 0, s>>>(d);
+        if (d.W == 16) k_affine_lr<16><<<d.nblk, kThreads, 0, s>>>(d, buf);
+        else k_affine_lr<8><<<d.nblk, kThreads, 0, s>>>(d, buf);
+    }
     if (d.W == 16) {
         k_affine_cols<16><<<d.nblk, kThreads, 0, s>>>(d, buf);
         return;
@@ -1177,6 +1833,8 @@ void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s) {
 void sf_launch_branch(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, int in_buf,
                       int out_buf, cudaStream_t s) {
     const SfTerms tm = diag_terms_host(kind, theta);
+    if (d.W == 16) k_branch_plan<16><<<1, kPlanThreads, 0, s>>>(d, kind, q0, q1, tm);
+    if (d.W == 8) k_branch_plan<8><<<1, kPlanThreads, 0, s>>>(d, kind, q0, q1, tm);
     SF_DISPATCH(d.W, k_branch<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, tm, in_buf, out_buf));
 }
 
@@ -1187,11 +1845,25 @@ void sf_launch_insert(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
 void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t q1, double theta, double eps,
                             int in_buf, int out_buf, cudaStream_t s) {
     const SfTerms tm = diag_terms_host(kind, theta);
+    if (d.W == 16) k_branch_plan<16><<<1, kPlanThreads, 0, s>>>(d, kind, q0, q1, tm);
+    if (d.W == 8) k_branch_plan<8><<<1, kPlanThreads, 0, s>>>(d, kind, q0, q1, tm);
     SF_DISPATCH(d.W, k_branch_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, tm, eps * eps, in_buf, out_buf));
 }
 
 void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_cof_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf));
+    // W >= 8: the closed form when U ^ I and V have low rank, else the per-bit
+    // walk (each variant returns at once when the other one applies)
+    if (d.W >= 8) {
+        const int nt = (d.n + 31) & ~31;
+        if (d.W == 16) {
+            k_cof_lowrank<16><<<1, nt, 0, s>>>(d);
+            k_cof_merge<16, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf);
+        } else {
+            k_cof_lowrank<8><<<1, nt, 0, s>>>(d);
+            k_cof_merge<8, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf);
+        }
+    }
+    SF_DISPATCH(d.W, k_cof_merge<WW, false><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf));
 }
 
 void sf_launch_build_index(const SfDev& d, int buf, cudaStream_t s) {

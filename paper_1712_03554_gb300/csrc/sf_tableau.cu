@@ -336,11 +336,19 @@ __device__ void cta_permute32(uint32_t* F, uint32_t* tmp, int h, int n, int dst)
     __syncthreads();
 }
 
+// where the sort records its permutation (W >= 8): the pivots before the
+// kernel ran, the move list and rho in the plan (null: not recorded)
+struct SortRec {
+    const int32_t* old_piv;
+    uint64_t* mv;
+    uint32_t* rho;
+};
+
 template <int W, bool TRACK_A>
-__device__ int cta_sort_rows(const Ws<W>& T, int n, int NT, Scratch<W>& S);
+__device__ int cta_sort_rows(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec rec = {nullptr, nullptr, nullptr});
 
 template <int W, bool TRACK_A, bool SORT = true>
-__device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
+__device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec rec = {nullptr, nullptr, nullptr}) {
     const int h = threadIdx.x, lane = h & 31, wid = h >> 5, nw = NT >> 5;
     constexpr int INF = 0x7fffffff;
     bool asg = false;
@@ -427,13 +435,64 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
         const int xr = __syncthreads_count(h < n && T.piv[h] < n);
         return xr;
     }
-    return cta_sort_rows<W, TRACK_A>(T, n, NT, S);
+    return cta_sort_rows<W, TRACK_A>(T, n, NT, S, rec);
+}
+
+// The sort's permutation as bit moves (the plan's move list): rows whose
+// pivot differs from old_piv moved; the others keep their relative order, so
+// deleting the moved rows' bits and inserting them at their new positions
+// maps a phase vector like the sort maps the rows.  Called by every thread
+// with its row's pre-sort pivot and new position.
+__device__ void cta_record_moves(const SortRec& rec, int n, int h, int pv, int rank) {
+    __shared__ int cnt;
+    __shared__ int la[SF_MV_MAX], le[SF_MV_MAX];
+    if (h == 0) cnt = 0;
+    __syncthreads();
+    if (h < n) {
+        rec.rho[h] = (uint32_t)rank;
+        if (pv != rec.old_piv[h]) {
+            const int k = atomicAdd(&cnt, 1);
+            if (k < SF_MV_MAX) {
+                la[k] = h;
+                le[k] = rank;
+            }
+        }
+    }
+    __syncthreads();
+    if (h == 0) {
+        const int m = cnt;
+        if (m > SF_MV_MAX) {
+            rec.mv[0] = SF_LR_NONE;
+        } else {
+            int a[SF_MV_MAX], e[SF_MV_MAX], ord[SF_MV_MAX];
+            for (int k = 0; k < m; k++) { a[k] = la[k]; e[k] = le[k]; }
+            for (int k = 1; k < m; k++)  // by old position
+                for (int i = k; i > 0 && a[i - 1] > a[i]; i--) {
+                    const int ta = a[i]; a[i] = a[i - 1]; a[i - 1] = ta;
+                    const int te = e[i]; e[i] = e[i - 1]; e[i - 1] = te;
+                }
+            for (int k = 0; k < m; k++) ord[k] = k;
+            for (int k = 1; k < m; k++)  // insertion order: by new position
+                for (int i = k; i > 0 && e[ord[i - 1]] > e[ord[i]]; i--) {
+                    const int t = ord[i]; ord[i] = ord[i - 1]; ord[i - 1] = t;
+                }
+            rec.mv[0] = (uint64_t)m;
+            for (int k = 0; k < SF_MV_MAX; k++) {
+                const bool in = k < m;
+                rec.mv[1 + k] = in ? (uint64_t)a[k] : 0ull;
+                rec.mv[1 + SF_MV_MAX + k] = in ? (uint64_t)e[ord[k]] : 0ull;
+                rec.mv[1 + 2 * SF_MV_MAX + k] = in ? (uint64_t)ord[k] : 0ull;
+                rec.mv[1 + 3 * SF_MV_MAX + (in ? ord[k] : k)] = in ? (uint64_t)k : 0ull;
+            }
+        }
+    }
+    __syncthreads();
 }
 
 // Rows sorted by pivot (rank = number of pivots in smaller columns), carrying
 // every per-row field along; returns r, the X-block size.
 template <int W, bool TRACK_A>
-__device__ int cta_sort_rows(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
+__device__ int cta_sort_rows(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec rec) {
     const int h = threadIdx.x;
     constexpr int INF = 0x7fffffff;
     if (h < 2 * W) S.occ1[h] = 0;
@@ -455,6 +514,7 @@ __device__ int cta_sort_rows(const Ws<W>& T, int n, int NT, Scratch<W>& S) {
 #pragma unroll 1
         for (int w = 0; w < wi; w++) rank += __popcll(S.occ1[w]);
     }
+    if (rec.mv) cta_record_moves(rec, n, h, pv, rank);
     if (__syncthreads_or(rank != h)) {
         // scratch: the Clifford kernel has d0x/d0e free, the measurement kernel
         // (which keeps the old destabilizers there) has A free
@@ -640,7 +700,10 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
         __syncthreads();
     }
     if (run_len > 0 && !close_run()) return;
-    r = cta_sort_rows<W, true>(T, n, NT, S);
+    SortRec rec = {nullptr, nullptr, nullptr};
+    if constexpr (W >= 8)
+        rec = {d.piv, d.plan + plan_mv_aff(n, W), reinterpret_cast<uint32_t*>(d.plan + plan_rho_aff(n, W))};
+    r = cta_sort_rows<W, true>(T, n, NT, S, rec);
     store_tableau<W>(d, T, r);
     if (h == 0) *d.g = cmul(*d.g, cliff_factor(ga, gb));
     // emit the affine map: columns of A (column j = image of e_j) and t as bit words
@@ -782,7 +845,10 @@ __global__ void __launch_bounds__(1024) k_measure_prep(SfDev d, uint32_t q, int 
     }
     T.piv[h] = 0x7fffffff;
     __syncthreads();
-    const int r = cta_rref<W, false>(T, n, NT, S);
+    SortRec rec = {nullptr, nullptr, nullptr};
+    if constexpr (W >= 8)
+        rec = {d.piv, d.plan + plan_mv_cf(n, W), reinterpret_cast<uint32_t*>(d.plan + plan_rho_cf(n, W))};
+    const int r = cta_rref<W, false>(T, n, NT, S, rec);
     if (r < 0) {
         if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 10u);
         return;

@@ -76,6 +76,8 @@ def load(build: bool = True) -> C.CDLL:
         "sf_apply_program_grid": ([H, C.c_void_p, u64, dbl, C.c_void_p], st),
         "sf_run_program": ([H, C.c_void_p, u64, dbl, P64, C.POINTER(C.c_uint32), u32], st),
         "sf_set_wait_limit": ([H, u32], st),
+        "sf_set_lowrank": ([H, C.c_int32], st),
+        "sf_lowrank_ranks": ([H, C.POINTER(C.c_int32)], st),
         "sf_grid_program_bytes": ([H, P64], st),
         "sf_set_trace": ([H, C.c_int32], st),
         "sf_grid_program_trace": ([H, P64, u32, C.POINTER(C.c_uint32)], st),
@@ -590,6 +592,16 @@ class Frame:
     def set_wait_limit(self, polls: int) -> None:
         """sf_set_wait_limit: barrier polls of the grid program before it gives up."""
         self._check(self.lib.sf_set_wait_limit(self.h, int(polls)), self.h)
+
+    def set_lowrank(self, on: bool) -> None:
+        """sf_set_lowrank: low-rank forms of the affine and cofactor maps (n > 256)."""
+        self._check(self.lib.sf_set_lowrank(self.h, 1 if on else 0), self.h)
+
+    def lowrank_ranks(self):
+        """sf_lowrank_ranks: (affine, cofactor U, cofactor V) ranks, -1 = per-bit form."""
+        r = (C.c_int32 * 3)()
+        self._check(self.lib.sf_lowrank_ranks(self.h, r), self.h)
+        return tuple(int(v) for v in r)
 
     def host_state(self) -> int:
         """Token of the host-side bookkeeping (restore it after replaying a graph)."""

@@ -9,9 +9,10 @@
   qubits) on seeded basis inputs: frame and tableau against the oracle, output
   against a + b mod 2^17; the 7-bit adder on the equal superposition sampled
   qubit by qubit, every measurement's probabilities against the oracle's.
-* A frame of 16 words per phase vector (n = 1000) with more than 4096
-  elements: a Clifford scramble, T gates on fresh |+> qubits and on scrambled
-  ones, more Clifford gates on the grown frame and a measurement.
+* Frames of 16 and 8 words per phase vector (n = 1000, 300) with more than
+  4096 elements: a Clifford scramble, T gates on fresh |+> qubits and on
+  scrambled ones, more Clifford gates on the grown frame and a measurement,
+  with the low-rank forms of the maps on and off.
 
 Tableau and phase vectors bit for bit; amplitudes and probabilities within
 1e-10, the global phase included (Def. 1, Sec. III-IV, Sec. VI).
@@ -163,15 +164,18 @@ def _random_qubits(x, n):
     return [q for q in range(n) if ((x[:, q // 64] >> np.uint64(q % 64)) & np.uint64(1)).any()]
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_w16_frame_above_4096_elements(sfm, seed):
-    """n = 1000 (16 words per phase vector): 300 random Clifford gates on the
-    first 988 qubits, H and T on the 12 untouched ones (4096 elements), T and
-    T-dagger on two scrambled random qubits (masks across many words, 16384
-    elements), three Clifford gates on the grown frame and a measurement of a
-    fresh qubit with collapse."""
-    n = 1000
+@pytest.mark.parametrize("n,seed,lowrank", [(1000, 0, True), (1000, 1, True), (1000, 0, False), (300, 2, True),
+                                             (300, 2, False)])
+def test_wide_frame_above_4096_elements(sfm, n, seed, lowrank):
+    """n = 1000 (16 words per phase vector) and n = 300 (8 words): 300 random
+    Clifford gates on the first n - 12 qubits, H and T on the 12 untouched ones
+    (4096 elements), T and T-dagger on two scrambled random qubits (masks across
+    many words, 16384 elements), a batch of three Clifford gates on the grown
+    frame and a measurement of a fresh qubit with collapse.  With the low-rank
+    forms on, the three-gate batch and the measurement must take them (their
+    ranks are read back); off, the per-bit forms run; both match the oracle."""
     g = sfm.Frame(n, 1 << 16)
+    g.set_lowrank(lowrank)
     o = oracle.FrameOracle(n)
     scr = c.random_clifford(n - 12, 300, 100 + seed)
     c.run(g, scr)
@@ -194,7 +198,30 @@ def test_w16_frame_above_4096_elements(sfm, seed):
     ops = [("C", c.H, pick[2], 0), ("C", c.CNOT, pick[3], n - 1), ("C", c.S, pick[4], 0), ("M", n - 3, 0.3)]
     rg = c.run(g, ops)
     ro = c.run(o, ops)
+    ranks = g.lowrank_ranks()
+    if lowrank:
+        assert all(0 <= r <= 16 for r in ranks), ranks
+    else:
+        assert ranks == (-1, -1, -1), ranks
     assert rg[0][3] == ro[0][3]
     assert abs(rg[0][1] - ro[0][1]) <= TOL and abs(rg[0][2] - ro[0][2]) <= TOL
     assert frames_equal(g, o) > 2048
+    g.close()
+
+
+def test_wide_scramble_batch_takes_the_per_bit_form(sfm):
+    """One batch of 300 random Clifford gates on a grown n = 1000 frame: the
+    map's rank exceeds the low-rank limit, the per-bit kernel applies it, and
+    the frame still matches the oracle."""
+    n = 1000
+    g = sfm.Frame(n, 1 << 12)
+    o = oracle.FrameOracle(n)
+    ops = [("C", c.H, q, 0) for q in range(8)]
+    for q in range(8):
+        ops += [("N", c.T, q, 0, 0.0), ("K",)]
+    ops += c.random_clifford(n, 300, 5)
+    c.run(g, ops)
+    c.run(o, ops)
+    assert g.lowrank_ranks()[0] == -1
+    assert frames_equal(g, o) == 256
     g.close()
