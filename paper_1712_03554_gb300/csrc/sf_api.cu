@@ -248,7 +248,7 @@ sf_status merge_seq(sf_handle h, double eps, int in_buf, int out_buf) {
     cudaStream_t s = h->stream;
     SF_LAUNCH(h, SF_K_INSERT, sf_launch_insert(d, in_buf, out_buf, s));
     SF_LAUNCH(h, SF_K_COMPACT, sf_launch_compact(d, eps, out_buf, s));
-    h->idx_ok[out_buf] = true;
+    h->idx_ok[out_buf] = sf_emit_index(d.W);
     return SF_OK;
 }
 
@@ -537,7 +537,7 @@ sf_status sf_apply_nonclifford_coalesce(sf_handle h, uint32_t kind, uint32_t q0,
     SF_LAUNCH(h, SF_K_BRANCH_MERGE,
               sf_launch_branch_merge(h->d, kind, q0, q1v, theta, drop_eps, h->cur, h->cur ^ 1, h->stream));
     h->cur ^= 1;
-    h->idx_ok[h->cur] = true;
+    h->idx_ok[h->cur] = sf_emit_index(h->d.W);
     return SF_OK;
 }
 
@@ -810,7 +810,7 @@ static sf_status cofactor_q(sf_handle h, uint32_t q) {
         if (st) return st;
         SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cof_merge(h->d, h->cur, h->cur ^ 1, h->stream));
         h->cur ^= 1;
-        h->idx_ok[h->cur] = true;
+        h->idx_ok[h->cur] = sf_emit_index(h->d.W);
     }
     return SF_OK;
 }
@@ -856,7 +856,7 @@ sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, d
         SF_CK(h, cudaMemsetAsync(h->d.kcnt + outb, 0, sizeof(unsigned long long), h->stream));
         SF_LAUNCH(h, SF_K_FILTER, sf_launch_filter(h->d, collapse_to, in, outb, h->stream));
         h->cur ^= 1;
-        h->idx_ok[h->cur] = true;
+        h->idx_ok[h->cur] = sf_emit_index(h->d.W);
     }
     return SF_OK;
 }
@@ -1218,7 +1218,7 @@ sf_status mf_cofactor_all(sf_multiframe m, uint32_t q) {
         MF_TRY(m, F, launch(F, SF_K_COFACTOR, "cof_merge",
                             [&] { sf_launch_cof_merge(F->d, F->cur, F->cur ^ 1, m->stream); }));
         F->cur ^= 1;
-        F->idx_ok[F->cur] = true;
+        F->idx_ok[F->cur] = sf_emit_index(F->d.W);
     }
     return SF_OK;
 }

@@ -86,6 +86,14 @@ struct OpRec {
     double param;
 };
 
+// Whether the merging kernels (branch merge, cofactor merge, collapse,
+// compaction) leave an index of their output.  Below 8 words a slot is at most
+// 72 bytes and the index of the next merge is usually wanted; from 8 words on
+// a slot write is a random 72..136-byte access per element, and the per-op
+// path nearly always changes every phase vector (a Clifford batch) before the
+// next merge, so the index is built only when a merge needs it.
+__host__ __device__ constexpr bool sf_emit_index(int W) { return W < 8; }
+
 // An empty one-word slot key: with W = 1 (n <= 63) phase vectors never set
 // bit 63.  Wider keys mark their slots through a separate state word.
 #define SF_EMPTY_KEY 0xffffffffffffffffull
@@ -152,7 +160,10 @@ __host__ __device__ inline size_t plan_rho_cf(int n, int W) { return plan_rho_af
 __host__ __device__ inline size_t plan_br(int n, int W) {
     return (plan_rho_cf(n, W) + (size_t)(n + 1) / 2 + 1) & ~(size_t)1;
 }
-__host__ __device__ inline size_t plan_words(int n, int W) { return plan_br(n, W) + SF_BR_WORDS(W); }
+// the old destabilizers of a measurement, kept for the cofactor tables
+// (W >= 2): x planes [W][n], z planes [W][n], phase exponents [n]
+__host__ __device__ inline size_t plan_d0(int n, int W) { return plan_br(n, W) + SF_BR_WORDS(W); }
+__host__ __device__ inline size_t plan_words(int n, int W) { return plan_d0(n, W) + (size_t)(2 * W + 1) * n; }
 
 // ---- Pauli arithmetic -------------------------------------------------------
 template <int W>
@@ -189,6 +200,23 @@ __device__ __forceinline__ void pauli_mul(Pauli<W>& a, const Pauli<W>& b) {
 #pragma unroll
     for (int w = 0; w < W; w++) { a.x[w] ^= b.x[w]; a.z[w] ^= b.z[w]; }
     a.e = (a.e + b.e + l) & 3;
+}
+
+// product of the 32 lanes' Paulis, in every lane (for factors that commute
+// with one another, where the order does not matter)
+template <int W>
+__device__ __forceinline__ void warp_pauli_product(Pauli<W>& p) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        Pauli<W> o;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            o.x[w] = __shfl_xor_sync(SF_FULL, p.x[w], off);
+            o.z[w] = __shfl_xor_sync(SF_FULL, p.z[w], off);
+        }
+        o.e = __shfl_xor_sync(SF_FULL, p.e, off);
+        pauli_mul<W>(p, o);
+    }
 }
 
 template <int W>

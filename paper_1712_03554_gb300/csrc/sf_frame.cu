@@ -413,20 +413,6 @@ struct BrPlan {
     double2 c[SF_BR_MAXG][SF_BR_MAXT];
 };
 
-template <int W>
-__device__ __forceinline__ void warp_pauli_product(Pauli<W>& p) {
-#pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        Pauli<W> o;
-#pragma unroll
-        for (int w = 0; w < W; w++) {
-            o.x[w] = __shfl_xor_sync(SF_FULL, p.x[w], off);
-            o.z[w] = __shfl_xor_sync(SF_FULL, p.z[w], off);
-        }
-        o.e = __shfl_xor_sync(SF_FULL, p.e, off);
-        pauli_mul<W>(p, o);
-    }
-}
 
 __device__ __forceinline__ uint64_t warp_or(uint64_t v) {
 #pragma unroll
@@ -923,12 +909,12 @@ __global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, doub
                 const unsigned long long o = b + __popc(bal & ((1u << lane) - 1u));
                 store_sig<W>(So, cap, o, key);
                 Ao[o] = a;
-                ok &= index_insert<W>(d, out_buf, TI, tag, key, (uint32_t)o);
+                if constexpr (sf_emit_index(W)) ok &= index_insert<W>(d, out_buf, TI, tag, key, (uint32_t)o);
             }
         }
     }
     if (!ok) set_status(d.status, SF_ST_TIMEOUT, out_buf);
-    if (last_block(d.done) && threadIdx.x == 0) {
+    if (last_block(d.done) && threadIdx.x == 0 && sf_emit_index(W)) {
         d.itag[out_buf] = tag;
         d.isize[out_buf] = TI;
     }
@@ -1084,12 +1070,12 @@ __global__ void __launch_bounds__(kThreads) k_filter(SfDev d, int x, int in_buf,
                 a.x *= scale;
                 a.y *= scale;
                 d.amp[out_buf][o] = a;
-                ok &= index_insert<W>(d, out_buf, TI, tag, s, (uint32_t)o);
+                if constexpr (sf_emit_index(W)) ok &= index_insert<W>(d, out_buf, TI, tag, s, (uint32_t)o);
             }
         }
     }
     if (!ok) set_status(d.status, SF_ST_TIMEOUT, out_buf);
-    if (last_block(d.done) && threadIdx.x == 0) {
+    if (last_block(d.done) && threadIdx.x == 0 && sf_emit_index(W)) {
         d.itag[out_buf] = tag;
         d.isize[out_buf] = TI;
     }
@@ -1141,8 +1127,10 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
         if (last_block(d.done) && threadIdx.x == 0) {
             d.kcnt[out_buf] = *d.ocnt;
             *d.ocnt = 0;
-            d.itag[out_buf] = tag_out;
-            d.isize[out_buf] = *d.ipend;
+            if (sf_emit_index(W)) {
+                d.itag[out_buf] = tag_out;
+                d.isize[out_buf] = *d.ipend;
+            }
         }
         return;
     }
@@ -1241,7 +1229,7 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
             for (int w = 0; w < W; w++) tau[w] = s[w] ^ P.u[g][w];
             store_sig<W>(So, cap, o, tau);
             Ao[o] = amps[g];
-            ok &= index_insert<W>(d, out_buf, Tout, tag_out, tau, (uint32_t)o);
+            if constexpr (sf_emit_index(W)) ok &= index_insert<W>(d, out_buf, Tout, tag_out, tau, (uint32_t)o);
             o++;
         }
     }
@@ -1249,8 +1237,10 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
     if (last_block(d.done) && threadIdx.x == 0) {
         d.kcnt[out_buf] = *d.ocnt;
         *d.ocnt = 0;
-        d.itag[out_buf] = tag_out;
-        d.isize[out_buf] = *d.ipend;
+        if (sf_emit_index(W)) {
+            d.itag[out_buf] = tag_out;
+            d.isize[out_buf] = *d.ipend;
+        }
     }
 }
 
@@ -1580,7 +1570,7 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
                 for (int w = 0; w < W; w++) t[w] = *(const volatile uint64_t*)&CP.tau[y][w] ^ s[w];
                 store_sig<W>(So, cap, o, t);
                 Ao[o] = cc[x];
-                ok &= index_insert<W>(d, out_buf, Tout, tag_out, t, (uint32_t)o);
+                if constexpr (sf_emit_index(W)) ok &= index_insert<W>(d, out_buf, Tout, tag_out, t, (uint32_t)o);
                 o++;
             }
         } else {
@@ -1608,7 +1598,7 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
             if (!((keepm >> x) & 1u)) continue;
             store_sig<W>(So, cap, o, t[x]);
             Ao[o] = cc[x];
-            ok &= index_insert<W>(d, out_buf, Tout, tag_out, t[x], (uint32_t)o);
+            if constexpr (sf_emit_index(W)) ok &= index_insert<W>(d, out_buf, Tout, tag_out, t[x], (uint32_t)o);
             o++;
         }
         }
@@ -1616,8 +1606,10 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
     if (last_block(d.done) && threadIdx.x == 0) {
         d.kcnt[out_buf] = *d.ocnt;
         *d.ocnt = 0;
-        d.itag[out_buf] = tag_out;
-        d.isize[out_buf] = Tout;
+        if (sf_emit_index(W)) {
+            d.itag[out_buf] = tag_out;
+            d.isize[out_buf] = Tout;
+        }
     }
 }
 

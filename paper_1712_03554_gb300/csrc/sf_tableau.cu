@@ -879,57 +879,18 @@ __global__ void __launch_bounds__(1024) k_measure_prep(SfDev d, uint32_t q, int 
         pl[cf_tau(n, W) + h] = S.words[1][h];
         pl[cf_tau(n, W) + W + h] = S.words[2][h];
     }
-    // tables: old D_hh = eps D'^{u'} M'^{v'}
-    Pauli<W> me, de;
+    // the tables (old D_hh = eps D'^{u'} M'^{v'}) are k_measure_tables' work:
+    // keep the old destabilizers for it and clear the eps bit planes
     if (h < n) {
-        load_m<W>(T, NT, h, me);
-        load_d<W>(T, NT, h, de);
-    }
-    if (h < W) { S.words[3][h] = 0; S.y[h] = 0; }
-    __syncthreads();
-    for (int hh = 0; hh < n; hh++) {
-        uint64_t ox[W], oz[W];
+        uint64_t* d0 = pl + plan_d0(n, W);
 #pragma unroll
-        for (int w = 0; w < W; w++) { ox[w] = T.d0x[w * NT + hh]; oz[w] = T.d0z[w * NT + hh]; }
-        const int oe = (int)T.d0e[hh];
-        bool ub = false, vb = false;
-        if (h < n) {
-            ub = (popc_and<W>(ox, me.z) + popc_and<W>(oz, me.x)) & 1;
-            vb = (popc_and<W>(ox, de.z) + popc_and<W>(oz, de.x)) & 1;
+        for (int w = 0; w < W; w++) {
+            d0[(size_t)w * n + h] = T.d0x[w * NT + h];
+            d0[(size_t)(W + w) * n + h] = T.d0z[w * NT + h];
         }
-        if (h < W) { S.words[1][h] = 0; S.words[2][h] = 0; }
-        __syncthreads();
-        cta_bits<W>(ub, S.words[1]);
-        cta_bits<W>(vb, S.words[2]);
-        // prod_h D'_h^{u_h} M'_h^{v_h} = (prod_u D'_h)(prod_v M'_h): a D'_h and an
-        // M'_k anticommute only for h = k, and that pair is never swapped
-        cta_rows_product<W>(T.dx, T.dz, T.de, NT, ub, S, S.qx, S.qz, &S.qe);
-        cta_rows_product<W>(T.mx, T.mz, nullptr, NT, vb, S, S.px, S.pz, &S.pe);
-        if (h < W) {
-            pl[cf_u(n, W) + (size_t)hh * W + h] = S.words[1][h];
-            pl[cf_v(n, W) + (size_t)hh * W + h] = S.words[2][h];
-        }
-        if (h == 0) {
-            bool ok = true;
-            int lam = 0;
-#pragma unroll 1
-            for (int w = 0; w < W; w++) {
-                const uint64_t ax = S.qx[w], az = S.qz[w], bx = S.px[w], bz = S.pz[w];
-                lam += __popcll(ax & az) + __popcll(bx & bz) + 2 * __popcll(az & bx) - __popcll((ax ^ bx) & (az ^ bz));
-                ok &= ((ax ^ bx) == ox[w]) && ((az ^ bz) == oz[w]);
-            }
-            const int pe = (S.qe + S.pe + lam) & 3;
-            const int epsq = (oe - pe + 4) & 3;
-            if (!ok) set_status(d.status, SF_ST_INTERNAL, buf, 5u);
-            if (epsq & 1) S.words[3][hh >> 6] |= 1ull << (hh & 63);
-            if (epsq & 2) S.y[hh >> 6] |= 1ull << (hh & 63);
-        }
-        __syncthreads();
+        d0[(size_t)2 * W * n + h] = T.d0e[h];
     }
-    if (h < W) {
-        pl[cf_eps(n, W) + h] = S.words[3][h];
-        pl[cf_eps(n, W) + W + h] = S.y[h];
-    }
+    if (h < 2 * W) pl[cf_eps(n, W) + h] = 0ull;
     // the Z_q row of the new tableau
     if (h == 0) d.meta[1] = -1;
     __syncthreads();
@@ -937,6 +898,91 @@ __global__ void __launch_bounds__(1024) k_measure_prep(SfDev d, uint32_t q, int 
     if (isrow) d.meta[1] = h;
     if (h == 0) d.meta[2] = 1;
     store_tableau<W>(d, T, r);
+}
+
+// The cofactor tables of a random measurement (COFACTOR, Sec. III), one warp
+// per old destabilizer hh: D_hh = eps_hh D'^{u'} M'^{v'} with
+// u'_h = [D_hh anticommutes with M'_h], v'_h = [D_hh anticommutes with D'_h]
+// over the new tableau (stored by k_measure_prep).  The D' rows commute with
+// one another, and so do the M' rows, so each lane multiplies its own rows
+// and the warp combines the lanes' partial products in any order; the D' part
+// then multiplies the M' part (a D'_h and an M'_k anticommute only for h = k,
+// and no such pair is swapped).  eps_hh is the i-power that makes the product
+// equal to D_hh, written as two bit planes.
+// a <- a * i^be P(x, z), the words of (x, z) read from word-major planes
+// (word w at x[w * n]) as they are used
+template <int W>
+__device__ __forceinline__ void pauli_mul_planes(Pauli<W>& a, const uint64_t* x, const uint64_t* z, int n, int be) {
+    int l = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        const uint64_t bx = __ldg(&x[w * n]), bz = __ldg(&z[w * n]);
+        l += __popcll(a.x[w] & a.z[w]) + __popcll(bx & bz) + 2 * __popcll(a.z[w] & bx) -
+             __popcll((a.x[w] ^ bx) & (a.z[w] ^ bz));
+        a.x[w] ^= bx;
+        a.z[w] ^= bz;
+    }
+    a.e = (a.e + be + l) & 3;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_measure_tables(SfDev d, int buf) {
+    if (*d.status) return;
+    if (!d.meta[2]) return;
+    const int n = d.n, lane = threadIdx.x & 31;
+    const int hh = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (hh >= n) return;  // the whole warp
+    uint64_t* pl = d.plan;
+    const uint64_t* d0 = pl + plan_d0(n, W);
+    uint64_t ox[W], oz[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        ox[w] = d0[(size_t)w * n + hh];
+        oz[w] = d0[(size_t)(W + w) * n + hh];
+    }
+    const int oe = (int)d0[(size_t)2 * W * n + hh];
+    Pauli<W> pd, pm;
+    pauli_id<W>(pd);
+    pauli_id<W>(pm);
+#pragma unroll 1
+    for (int wb = 0; wb < W; wb++) {
+        uint64_t ubits = 0, vbits = 0;
+#pragma unroll 1
+        for (int half = 0; half < 2; half++) {
+            const int h = 64 * wb + 32 * half + lane;
+            bool ub = false, vb = false;
+            if (h < n) {
+                int cu = 0, cv = 0;
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    cu += __popcll(ox[w] & __ldg(&d.mz[w * n + h])) + __popcll(oz[w] & __ldg(&d.mx[w * n + h]));
+                    cv += __popcll(ox[w] & __ldg(&d.dz[w * n + h])) + __popcll(oz[w] & __ldg(&d.dx[w * n + h]));
+                }
+                ub = cu & 1;
+                vb = cv & 1;
+                if (ub) pauli_mul_planes<W>(pd, d.dx + h, d.dz + h, n, (int)__ldg(&d.de[h]));
+                if (vb) pauli_mul_planes<W>(pm, d.mx + h, d.mz + h, n, 0);
+            }
+            ubits |= (uint64_t)__ballot_sync(SF_FULL, ub) << (32 * half);
+            vbits |= (uint64_t)__ballot_sync(SF_FULL, vb) << (32 * half);
+        }
+        if (lane == 0) {
+            pl[cf_u(n, W) + (size_t)hh * W + wb] = ubits;
+            pl[cf_v(n, W) + (size_t)hh * W + wb] = vbits;
+        }
+    }
+    warp_pauli_product<W>(pd);
+    warp_pauli_product<W>(pm);
+    if (lane != 0) return;
+    pauli_mul<W>(pd, pm);
+    bool ok = true;
+#pragma unroll
+    for (int w = 0; w < W; w++) ok &= pd.x[w] == ox[w] && pd.z[w] == oz[w];
+    if (!ok) set_status(d.status, SF_ST_INTERNAL, buf, 5u);
+    const int epsq = (oe - pd.e + 4) & 3;
+    unsigned long long* eps = reinterpret_cast<unsigned long long*>(pl + cf_eps(n, W));
+    if (epsq & 1) atomicOr(&eps[hh >> 6], 1ull << (hh & 63));
+    if (epsq & 2) atomicOr(&eps[W + (hh >> 6)], 1ull << (hh & 63));
 }
 
 // ---------------------------------------------------------------------------
@@ -1069,6 +1115,7 @@ void sf_launch_measure_prep(const SfDev& d, uint32_t q, int buf, uint64_t* gws, 
         size_t sm;
         uint64_t* ws = pick_ws<WW>(d, k_measure_prep<WW>, sm, gws, 1);
         k_measure_prep<WW><<<1, d.NT, sm, s>>>(d, q, buf, ws);
+        k_measure_tables<WW><<<(d.n + 7) / 8, 256, 0, s>>>(d, buf);
     });
 }
 
