@@ -1023,7 +1023,8 @@ def main():
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(n, plan, y, updates)
     batched = None if args.no_campaign else campaign_leg(sf, torch, args.campaign_variants)
-    served = None if args.no_serving else serving_leg(sf, args.serving_requests, args.serving_slots)
+    served = None if (args.no_serving or args.serving_requests <= 0) else serving_leg(sf, args.serving_requests,
+                                                                                       args.serving_slots)
     multiframe = None if args.no_multiframe else multiframe_leg(sf)
     streaming = None
     if not args.no_streaming:

@@ -55,10 +55,38 @@ constexpr int kGpTrace = 512;             // phases recorded by a traced launch
 struct GpPlan {
     BrTab P;
     double2 ctab[4][16];
+    // every term's v is orthogonal to the frame's hull where the record is
+    // applied (set by the planner CTA against a hull that contains the workers'
+    // hull, so it never claims too much; 0: not known)
+    int orth;
+    int pad_[3];
 };
 
-// device workspace, zeroed at handle creation; err, drop, ocnt, fk and moved
-// are cleared before every launch
+// The tableau of the launch.  CTA 0 writes it back at the end.
+struct GpTab {
+    uint64_t mx[64], mz[64], dx[64], dz[64];
+    uint32_t de[64];
+    int piv[64];
+    int rx;       // X-block size
+    double2 g;    // global phase
+};
+
+// One planned step of the program, written by the planner CTA: a Clifford run
+// [oi, oe) with its map and the plans of the diagonal records [oe, oe + np)
+// that follow it, or the plans of a diagonal run [oi, oi + np) alone.
+constexpr int kGpRing = 4;  // planned steps in flight
+struct GpSet {
+    int kind;                   // 0: Clifford run and plans, 1: plans only, 2: a tableau check failed
+    int np;
+    unsigned long long oe;      // end of the Clifford run (kind 0)
+    GpTab tab;                  // the tableau after the run
+    uint64_t at[64], ainv[64];  // columns of A, rows of A^-1
+    uint64_t t;
+    GpPlan plans[kGpPlans];
+};
+
+// device workspace, zeroed at handle creation; err ... cleared_end is cleared
+// before every launch
 struct GpWork {
     unsigned int bar_count, bar_gen;
     unsigned int err[3];         // a failed check in phase p (between barriers p and p + 1): err[p % 3]
@@ -66,6 +94,9 @@ struct GpWork {
     unsigned long long ocnt[3];  // output counters of consecutive merges, rotating
     unsigned long long fk[3][2]; // children kept by consecutive in-place branch passes (s, s ^ u), rotating
     unsigned long long moved;    // element bytes read and written by this launch's passes
+    unsigned long long ring_seq[kGpRing];  // 1 + the step number published in each ring slot
+    unsigned int ring_readers[kGpRing];    // worker CTAs that copied the slot's step
+    unsigned int checked;                  // the records passed the check (the planner may start)
     unsigned long long cleared_end;
     uint64_t hull[64];           // the frame's hull constraints at the end of the last launch
     uint64_t hbasis[64];         // and directions spanning the hull
@@ -75,23 +106,28 @@ struct GpWork {
     // start and arrival time, the last arrival's time and CTA (ns, %globaltimer)
     uint64_t trace[kGpTrace][5];
     uint64_t marks[kGpTrace][8];  // checkpoints inside each traced phase (CTA 0)
+    GpSet ring[kGpRing];
 };
 
-// The tableau of the launch.  Every CTA keeps its own copy in shared memory
-// and applies the same Clifford runs to it (the work is deterministic, so the
-// copies agree); CTA 0 writes it back at the end.
-struct GpTab {
-    uint64_t mx[64], mz[64], dx[64], dz[64];
-    uint32_t de[64];
-    int piv[64];
-    int rx;       // X-block size
-    double2 g;    // global phase
-};
+// CTAs that work on the frame: all but the planner (the last CTA) when the
+// grid has more than one
+__device__ __forceinline__ unsigned gp_nwork() { return gridDim.x > 1 ? gridDim.x - 1 : 1; }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" : : "l"(p), "l"(v) : "memory");
 }
 
 __shared__ unsigned s_phase;   // phase of the grid program this CTA is in
@@ -147,7 +183,7 @@ __device__ bool gp_barrier(GpWork* w, unsigned& gen, uint32_t* status, int buf) 
             w->trace[ti][1] = s_tstart;
             w->trace[ti][2] = t_arr;
         }
-        if (atomicAdd(&w->bar_count, 1u) == gridDim.x - 1) {
+        if (atomicAdd(&w->bar_count, 1u) == gp_nwork() - 1) {
             if (s_trace && ti < (unsigned)kGpTrace) {
                 w->trace[ti][3] = t_arr;
                 w->trace[ti][4] = blockIdx.x;
@@ -344,7 +380,8 @@ __device__ __forceinline__ int diag_count(const OpRec* ops, unsigned long long r
 
 // elements [lo, hi) of CTA b: contiguous chunks, whole warps, all CTAs busy
 __device__ __forceinline__ void gp_chunk(unsigned long long k, unsigned long long& lo, unsigned long long& hi) {
-    const unsigned long long per = ((k + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+    const unsigned nw = gp_nwork();
+    const unsigned long long per = ((k + nw - 1) / nw + 31) / 32 * 32;
     lo = min(k, (unsigned long long)blockIdx.x * per);
     hi = min(k, lo + per);
 }
@@ -409,22 +446,41 @@ __device__ __forceinline__ double2 shfl_down_c(double2 v, int off) {
 // hull directions hb[0 .. nhb), the product of their pair matrices at
 // (s0, s0 ^ u) into *out and true (every lane); otherwise false.
 __device__ bool uniform_run(const GpPlan* spl, int r0, int r1, const uint64_t* hb, int nhb, uint64_t s0, uint64_t u,
-                            Cm2* out) {
+                            bool flags, Cm2* out) {
     const int lane = threadIdx.x & 31;
     const int r = r0 + lane;
-    bool uni = true;
+    if (flags) {  // the planner's per-record verdicts
+        if (!__all_sync(SF_FULL, r >= r1 || spl[r].orth)) return false;
+    } else {
+    // every term against every hull direction: the directions in registers
+    // (lane L holds hb[L] and hb[L + 32]), each record's terms read by all lanes
+    // at once, all of its words in one batch of independent loads
+    const uint64_t h0 = lane < nhb ? hb[lane] : 0ull, h1 = lane + 32 < nhb ? hb[lane + 32] : 0ull;
+    bool odd = false;
+    for (int rr = r0; rr < r1; rr++) {
+        const BrTab& Q = spl[rr].P;
+        const int ng = Q.ng;
+        int nt[4];
+        uint64_t v[4][4];
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            nt[g] = Q.nt[g];
+#pragma unroll
+            for (int t = 0; t < 4; t++) v[g][t] = Q.v[g][t];
+        }
+#pragma unroll
+        for (int g = 0; g < 4; g++)
+#pragma unroll
+            for (int t = 0; t < 4; t++)
+                if (g < ng && t < nt[g]) odd |= ((__popcll(v[g][t] & h0) | __popcll(v[g][t] & h1)) & 1) != 0;
+    }
+    if (__any_sync(SF_FULL, odd)) return false;
+    }
     Cm2 M;
     M.m00 = M.m11 = make_double2(1.0, 0.0);
     M.m01 = M.m10 = make_double2(0.0, 0.0);
     if (r < r1) {
         const BrTab& Q = spl[r].P;
-        for (int g = 0; g < Q.ng && uni; g++)
-            for (int t = 0; t < Q.nt[g] && uni; t++)
-                for (int i = 0; i < nhb; i++)
-                    if (__popcll(Q.v[g][t] & hb[i]) & 1) {
-                        uni = false;
-                        break;
-                    }
         const uint64_t s1 = s0 ^ u;
         M.m00 = half_coef(Q, spl[r].ctab, 0, s0);
         M.m11 = half_coef(Q, spl[r].ctab, 0, s1);
@@ -433,9 +489,8 @@ __device__ bool uniform_run(const GpPlan* spl, int r0, int r1, const uint64_t* h
             M.m10 = half_coef(Q, spl[r].ctab, 1, s0);
         }
     }
-    if (!__all_sync(SF_FULL, uni)) return false;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
+    // ceil(log2(r1 - r0)) levels (lanes past r1 hold the identity)
+    for (int off = 1; off < r1 - r0; off <<= 1) {
         Cm2 o;
         o.m00 = shfl_down_c(M.m00, off);
         o.m01 = shfl_down_c(M.m01, off);
@@ -483,6 +538,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
     __shared__ Cm2 s_comp;                   // product of a run's pair matrices
     __shared__ int s_uni;                    // ... valid for the current pass
     __shared__ uint64_t s_ref;               // a phase vector of the frame (new coordinates)
+    __shared__ int s_take, s_np, s_kind;     // a planned step taken from the ring: ok, records, kind
     __shared__ uint64_t s_pu[64];            // directions whose partners are found by position ...
     __shared__ unsigned long long s_pk[64];  // ... and their strides
     if (*(volatile uint32_t*)d.status) return;
@@ -504,12 +560,214 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
         s_hb[i] = hull_state == 1 ? __ldcg(&w->hbasis[i]) : (hull_state == 0 && i < n ? 1ull << i : 0ull);
         if (i == 0) s_nhb = hull_state == 1 ? (int)__ldcg(&w->nhb) : (hull_state == 0 ? n : 0);
     }
+    for (int row = threadIdx.x; row < n; row += blockDim.x) {
+        s_tab.mx[row] = __ldcg(&d.mx[row]);
+        s_tab.mz[row] = __ldcg(&d.mz[row]);
+        s_tab.dx[row] = __ldcg(&d.dx[row]);
+        s_tab.dz[row] = __ldcg(&d.dz[row]);
+        s_tab.de[row] = __ldcg(&d.de[row]);
+        s_tab.piv[row] = __ldcg(&d.piv[row]);
+    }
+    if (threadIdx.x == 0) {
+        s_tab.rx = __ldcg(&d.meta[0]);
+        s_tab.g = __ldcg(d.g);
+    }
     __syncthreads();
+    if (gridDim.x > 1 && blockIdx.x == gridDim.x - 1) {
+        // ---- the planner CTA.  The Clifford runs, the inverses of their maps and
+        // the plans of the diagonal records depend on the tableau alone, never on
+        // the frame, so this CTA computes them ahead of the workers (up to kGpRing
+        // steps) while they run the passes of earlier steps.  Every wait is
+        // bounded and ends early when a worker has failed.
+        const unsigned nw = gridDim.x - 1;
+        const unsigned long long lim = 64ull * spin_limit;
+        const int nwarps = (int)(blockDim.x >> 5);
+        if (threadIdx.x == 0) {  // the records passed the check (and their e^{i theta} are in trig)
+            unsigned long long spins = 0;
+            int okw = 1;
+            while (ld_acquire(&w->checked) == 0) {
+                if (*(volatile uint32_t*)d.status || ++spins > lim) {
+                    okw = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+            s_uni = okw;
+        }
+        __syncthreads();
+        if (!s_uni) return;
+        unsigned long long poi = 0;
+        unsigned pset = 0;
+        while (poi < n_ops) {
+            const uint32_t kind = ops[poi].kind;
+            const bool cliff = kind <= 8, diag = kind >= SF_OP_DIAG && kind <= SF_OP_DIAG + 3;
+            if (!cliff && !diag) break;  // the workers stop at the same record
+            const unsigned e = pset % kGpRing;
+            if (pset >= kGpRing) {  // the slot's previous step was copied by every worker
+                if (threadIdx.x == 0) {
+                    unsigned long long spins = 0;
+                    int okw = 1;
+                    while (ld_acquire(&w->ring_readers[e]) != nw) {
+                        if (*(volatile uint32_t*)d.status || ++spins > lim) {
+                            okw = 0;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                    s_uni = okw;
+                }
+                __syncthreads();
+                if (!s_uni) return;
+            }
+            GpSet* S = &w->ring[e];
+            int np = 0, skind = cliff ? 0 : 1;
+            unsigned long long oe = poi;
+            if (cliff) {
+                if (warp == 0) {
+                    const unsigned long long o = gp_clifford_run(s_tab, ops, poi, n_ops, n, stage, s_at, s_ainv, &s_t);
+                    if (lane == 0) s_oe = o;
+                }
+                __syncthreads();
+                oe = s_oe;
+                if (oe == ~0ull) {
+                    skind = 2;
+                } else {
+                    np = diag_count(ops, oe, n_ops);
+                    if (warp == 0) {  // rows of A^-1
+                        const uint64_t av[2] = {lane < n ? s_ainv[lane] : 0, lane + 32 < n ? s_ainv[lane + 32] : 0};
+                        uint64_t iv[2];
+                        const bool inv_ok = warp_gf2_inverse(av, n, iv);
+                        __syncwarp();
+                        for (int hf = 0; hf < 2; hf++)
+                            if (lane + 32 * hf < n) s_ainv[lane + 32 * hf] = iv[hf];
+                        if (lane == 0) s_inv_ok = inv_ok;
+                    } else {
+                        for (int r = warp - 1; r < np; r += nwarps - 1)
+                            gp_plan(s_tab, n, ops[oe + r], __ldcg(&trig[oe + r]), spl[r]);
+                    }
+                    __syncthreads();
+                    if (!s_inv_ok) {
+                        skind = 3;
+                    } else {
+                        // the hull moves with the run's map, as in the workers
+                        const int i = threadIdx.x;
+                        uint64_t hc = 0, hb = 0;
+                        if (i < 64) {
+                            const uint64_t c = s_hc[i];
+                            for (int h = 0; h < n; h++)
+                                if ((c >> h) & 1) hc ^= s_ainv[h];
+                            if (i < s_nhb) {
+                                const uint64_t u = s_hb[i];
+                                for (int j = 0; j < n; j++)
+                                    if ((u >> j) & 1) hb ^= s_at[j];
+                            }
+                        }
+                        __syncthreads();
+                        if (i < 64) {
+                            s_hc[i] = hc;
+                            if (i < s_nhb) s_hb[i] = hb;
+                        }
+                        __syncthreads();
+                    }
+                }
+            } else {
+                np = diag_count(ops, poi, n_ops);
+                for (int r = warp; r < np; r += nwarps) gp_plan(s_tab, n, ops[poi + r], __ldcg(&trig[poi + r]), spl[r]);
+                __syncthreads();
+            }
+            if (skind < 2 && warp == 0) {
+                // Per record: are its terms orthogonal to the hull where the workers
+                // apply it?  The hull is followed record by record as the workers
+                // change theirs -- a fresh direction joins after its whole run (the
+                // records that follow with one group or the same mask are checked
+                // against the hull before it), a merge's masks join after it -- except
+                // that it always grows where the workers skip a direction whose
+                // children all vanished, so it contains theirs and a yes is safe.
+                uint64_t pend = 0;
+                bool have_pend = false;
+                for (int r = 0; r < np; r++) {
+                    const BrTab& Q = spl[r].P;
+                    const bool cont = have_pend && (Q.ng == 1 || (Q.ng == 2 && Q.u[1] == pend));
+                    if (!cont && have_pend) {
+                        if (hull_fresh(s_hc, pend)) {
+                            hull_add(s_hc, pend);
+                            if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = pend;
+                            __syncwarp();
+                        }
+                        have_pend = false;
+                    }
+                    const uint64_t h0 = lane < s_nhb ? s_hb[lane] : 0ull;
+                    const uint64_t h1 = lane + 32 < s_nhb ? s_hb[lane + 32] : 0ull;
+                    bool odd = false;
+                    for (int g = 0; g < Q.ng; g++)
+                        for (int t = 0; t < Q.nt[g]; t++) {
+                            const uint64_t v = Q.v[g][t];
+                            odd |= ((__popcll(v & h0) | __popcll(v & h1)) & 1) != 0;
+                        }
+                    const int orth = !__any_sync(SF_FULL, odd);
+                    if (lane == 0) spl[r].orth = orth;
+                    __syncwarp();
+                    if (cont) continue;
+                    if (Q.ng == 2 && hull_fresh(s_hc, Q.u[1])) {
+                        pend = Q.u[1];
+                        have_pend = true;
+                    } else {
+                        for (int g = 1; g < Q.ng; g++) {
+                            if (hull_fresh(s_hc, Q.u[g])) {
+                                hull_add(s_hc, Q.u[g]);
+                                if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = Q.u[g];
+                                __syncwarp();
+                            }
+                        }
+                    }
+                }
+                if (have_pend && hull_fresh(s_hc, pend)) {
+                    hull_add(s_hc, pend);
+                    if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = pend;
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            {
+                const uint64_t* src = reinterpret_cast<const uint64_t*>(&spl[0]);
+                uint64_t* dst = reinterpret_cast<uint64_t*>(&S->plans[0]);
+                const int words = (skind < 2 ? np : 0) * (int)(sizeof(GpPlan) / 8);
+                for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+            }
+            // the tableau after the run and its map go with the plans
+            {
+                const uint64_t* src = reinterpret_cast<const uint64_t*>(&s_tab);
+                uint64_t* dst = reinterpret_cast<uint64_t*>(&S->tab);
+                for (int i = threadIdx.x; i < (int)(sizeof(GpTab) / 8); i += blockDim.x) dst[i] = src[i];
+                if (threadIdx.x < 64) {
+                    S->at[threadIdx.x] = s_at[threadIdx.x];
+                    S->ainv[threadIdx.x] = s_ainv[threadIdx.x];
+                }
+                if (threadIdx.x == 0) {
+                    S->t = s_t;
+                    S->kind = skind;
+                    S->np = np;
+                    S->oe = oe;
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                w->ring_readers[e] = 0;
+                __threadfence();
+                st_release64(&w->ring_seq[e], (unsigned long long)pset + 1ull);
+            }
+            pset++;
+            if (skind >= 2) break;
+            poi = cliff ? oe + np : poi + np;
+        }
+        return;
+    }
     // every record is checked before anything is touched
     {
         bool bad = false;
         for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_ops;
-             i += (unsigned long long)gridDim.x * blockDim.x) {
+             i += (unsigned long long)gp_nwork() * blockDim.x) {
             const OpRec o = ops[i];
             const uint32_t k = o.kind == SF_OP_COND ? o.arg : o.kind;
             const bool two = (k >= 6 && k <= 8) || k == SF_OP_DIAG + 3;
@@ -533,21 +791,10 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
         }
         gp_phase(10, n_ops);
         if (!gp_barrier(w, gen, d.status, cur0)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) st_release32(&w->checked, 1u);
     }
-    for (int row = threadIdx.x; row < n; row += blockDim.x) {
-        s_tab.mx[row] = __ldcg(&d.mx[row]);
-        s_tab.mz[row] = __ldcg(&d.mz[row]);
-        s_tab.dx[row] = __ldcg(&d.dx[row]);
-        s_tab.dz[row] = __ldcg(&d.dz[row]);
-        s_tab.de[row] = __ldcg(&d.de[row]);
-        s_tab.piv[row] = __ldcg(&d.piv[row]);
-    }
-    if (threadIdx.x == 0) {
-        s_tab.rx = __ldcg(&d.meta[0]);
-        s_tab.g = __ldcg(d.g);
-    }
-    __syncthreads();
     int cur = cur0;
+    const bool piped = gridDim.x > 1;  // a planner CTA plans ahead (the workers take its steps)
     unsigned long long k = d.kcnt[cur0];
     uint32_t tag[2] = {d.itag[0], d.itag[1]};
     unsigned long long isz[2] = {d.isize[0], d.isize[1]};
@@ -649,7 +896,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
         }
         __syncthreads();
         if (warp == 0) {
-            const bool uni = k && r1 - r0 >= 3 && uniform_run(spl, r0, r1, s_hb, s_nhb, s_ref, u, &s_comp);
+            const bool uni = k && r1 - r0 >= 3 && uniform_run(spl, r0, r1, s_hb, s_nhb, s_ref, u, piped, &s_comp);
             if (lane == 0) s_uni = uni;
         }
         __syncthreads();
@@ -746,6 +993,64 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             }
         }
     };
+    // the next planned step from the ring (workers, when the grid has a planner
+    // CTA): the tableau after its Clifford run, the run's map and the plans of
+    // its diagonal records, copied into this CTA's shared memory through L2
+    unsigned nset = 0;
+    auto take_set = [&]() -> bool {
+        const unsigned e = nset % kGpRing;
+        if (threadIdx.x == 0) {
+            unsigned long long spins = 0;
+            int okw = 1;
+            while (ld_acquire64(&w->ring_seq[e]) != (unsigned long long)nset + 1ull) {
+                if (*(volatile uint32_t*)d.status || ++spins > s_spin) {
+                    okw = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            s_take = okw;
+        }
+        __syncthreads();
+        if (!s_take) return false;
+        const GpSet* S = &w->ring[e];
+        {
+            const uint64_t* src = reinterpret_cast<const uint64_t*>(&S->tab);
+            uint64_t* dst = reinterpret_cast<uint64_t*>(&s_tab);
+            for (int i = threadIdx.x; i < (int)(sizeof(GpTab) / 8); i += blockDim.x) dst[i] = __ldcg(&src[i]);
+        }
+        if (threadIdx.x < 64) {
+            s_at[threadIdx.x] = __ldcg(&S->at[threadIdx.x]);
+            s_ainv[threadIdx.x] = __ldcg(&S->ainv[threadIdx.x]);
+        }
+        const int np = __ldcg(&S->np);
+        if (threadIdx.x == 0) {
+            s_t = __ldcg(&S->t);
+            s_kind = __ldcg(&S->kind);
+            s_np = np;
+            s_oe = __ldcg(&S->oe);
+        }
+        {
+            const uint64_t* src = reinterpret_cast<const uint64_t*>(&S->plans[0]);
+            uint64_t* dst = reinterpret_cast<uint64_t*>(&spl[0]);
+            const int words = np * (int)(sizeof(GpPlan) / 8);
+            for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldcg(&src[i]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&w->ring_readers[e], 1u);
+        nset++;
+        return true;
+    };
+    // a wait for the planner that ran out: every worker stops at the next barrier
+    auto set_timeout = [&]() {
+        if (threadIdx.x == 0) {
+            set_status(d.status, SF_ST_TIMEOUT, cur, 51u);
+            gp_fail(w);
+        }
+        gp_barrier(w, gen, d.status, cur);
+        if (aff) affine_pass();
+        bail();
+    };
     while (oi < n_ops) {
         const uint32_t kind = ops[oi].kind;
         if (kind <= 8) {
@@ -753,6 +1058,24 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             // then inverts the map (that warp) while its other warps plan the
             // diagonal records that follow; no grid barrier, no global traffic
             gp_mark(w, 0);
+            if (piped) {
+                // the planner CTA ran the Clifford run and planned what follows
+                if (!take_set()) return set_timeout();
+                gp_mark(w, 1);
+                if (s_kind >= 2) {  // a tableau check (2) or the map's inverse (3) failed
+                    if (blockIdx.x == 0 && threadIdx.x == 0)
+                        set_status(d.status, SF_ST_INTERNAL, cur, s_kind == 2 ? 41u : 49u);
+                    if (aff) affine_pass();
+                    return bail();
+                }
+                npre = (unsigned)s_np;
+                have_u = false;
+                oi = s_oe;
+                aff = true;
+                move_hull();
+                gp_mark(w, 3);
+                continue;
+            }
             if (warp == 0) {
                 const unsigned long long oe = gp_clifford_run(s_tab, ops, oi, n_ops, n, stage, s_at, s_ainv, &s_t);
                 if (lane == 0) s_oe = oe;
@@ -798,11 +1121,16 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
         // then the records in passes over the frame
         int nb = (int)npre;
         npre = 0;
-        if (nb == 0) {  // every CTA plans the batch itself, one warp per record
-            nb = diag_count(ops, oi, n_ops);
-            for (int r = warp; r < nb; r += (int)(blockDim.x >> 5))
-                gp_plan(s_tab, n, ops[oi + r], __ldcg(&trig[oi + r]), spl[r]);
-            __syncthreads();
+        if (nb == 0) {  // plans of a diagonal run without a Clifford run before it
+            if (piped) {
+                if (!take_set()) return set_timeout();
+                nb = s_np;
+            } else {  // the one CTA plans it, one warp per record
+                nb = diag_count(ops, oi, n_ops);
+                for (int r = warp; r < nb; r += (int)(blockDim.x >> 5))
+                    gp_plan(s_tab, n, ops[oi + r], __ldcg(&trig[oi + r]), spl[r]);
+                __syncthreads();
+            }
         }
         int t = 0;
         while (t < nb) {

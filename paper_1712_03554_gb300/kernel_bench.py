@@ -303,7 +303,7 @@ def qft_trace(seed=0, reps=3):
         f.sync()
     tr = f.grid_program_trace().astype(np.int64)
     rows, by_kind = [], {}
-    mark_names = ("cliff_start", "cliff_end", "plan_end", "hull_end", "pass_start", "map_tables_end", "loop_end",
+    mark_names = ("step_wait", "step_taken", "plan_end", "hull_end", "pass_start", "map_tables_end", "loop_end",
                   "prev_pass_counts_read")
     for i, rec in enumerate(tr):
         code, t0, arr0, last, who = (int(v) for v in rec[:5])
