@@ -71,10 +71,23 @@ struct GpTab {
     double2 g;    // global phase
 };
 
-// One planned step of the program, written by the planner CTA: a Clifford run
-// [oi, oe) with its map and the plans of the diagonal records [oe, oe + np)
-// that follow it, or the plans of a diagonal run [oi, oi + np) alone.
-constexpr int kGpRing = 4;  // planned steps in flight
+// The planning of the program runs on two CTAs ahead of the workers: the
+// tableau CTA applies the Clifford runs and passes each run's tableau and map
+// on (a GpTabSet), the plan CTA plans the diagonal records that follow and
+// passes the whole step to the workers (a GpSet).  Each ring holds kGpRing
+// steps.
+constexpr int kGpRing = 4;
+struct GpTabSet {
+    int kind;                   // 0: Clifford run [oi, oe), 1: no Clifford run, 2: a tableau check failed, 3: end
+    int np;                     // diagonal records from ds
+    unsigned long long oe, ds;
+    GpTab tab;
+    uint64_t at[64], ainv[64];
+    uint64_t t;
+};
+// One planned step: a Clifford run [oi, oe) with its map and the plans of the
+// diagonal records [oe, oe + np) that follow it, or the plans of a diagonal
+// run [oi, oi + np) alone.
 struct GpSet {
     int kind;                   // 0: Clifford run and plans, 1: plans only, 2: a tableau check failed
     int np;
@@ -96,6 +109,8 @@ struct GpWork {
     unsigned long long moved;    // element bytes read and written by this launch's passes
     unsigned long long ring_seq[kGpRing];  // 1 + the step number published in each ring slot
     unsigned int ring_readers[kGpRing];    // worker CTAs that copied the slot's step
+    unsigned long long tring_seq[kGpRing]; // the same for the tableau CTA's ring
+    unsigned int tring_readers[kGpRing];   // (its one reader: the plan CTA)
     unsigned int checked;                  // the records passed the check (the planner may start)
     unsigned long long cleared_end;
     uint64_t hull[64];           // the frame's hull constraints at the end of the last launch
@@ -107,11 +122,13 @@ struct GpWork {
     uint64_t trace[kGpTrace][5];
     uint64_t marks[kGpTrace][8];  // checkpoints inside each traced phase (CTA 0)
     GpSet ring[kGpRing];
+    GpTabSet tring[kGpRing];
 };
 
-// CTAs that work on the frame: all but the planner (the last CTA) when the
-// grid has more than one
-__device__ __forceinline__ unsigned gp_nwork() { return gridDim.x > 1 ? gridDim.x - 1 : 1; }
+// With three CTAs or more, the last two plan (the tableau CTA, then the plan
+// CTA) and the others work on the frame; otherwise every CTA plans for itself
+__device__ __forceinline__ bool gp_piped() { return gridDim.x >= 3; }
+__device__ __forceinline__ unsigned gp_nwork() { return gp_piped() ? gridDim.x - 2 : gridDim.x; }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -271,13 +288,15 @@ __device__ __forceinline__ long long gp_find(const SfDev& d, int b, unsigned lon
 // ROTATE over the run of Clifford records from oi (warp 0 of a CTA) on the
 // CTA's tableau: the rows in registers, written back with the X-block size and
 // global phase.  The composed affine map sigma' = A sigma ^ t goes to at
-// (column j = image of e_j) and *t, the rows of A to arows; returns the run's
-// end, or ~0 if a tableau check failed.
+// (column j = image of e_j) and *t, the rows of A^-1 to ainv (A^-T tracked
+// through the reduction, so no inversion follows); returns the run's end, or
+// ~0 if a tableau check failed.  cstage: 64 words of shared memory.
 __device__ unsigned long long gp_clifford_run(GpTab& T, const OpRec* ops, unsigned long long oi,
-                                              unsigned long long o1, int n, Row* stage, uint64_t* at,
-                                              uint64_t* arows, uint64_t* t_out) {
+                                              unsigned long long o1, int n, Row* stage, uint64_t* cstage, uint64_t* at,
+                                              uint64_t* ainv, uint64_t* t_out) {
     const int lane = threadIdx.x & 31;
     Row r[2];
+    uint64_t C[2];  // rows of A^-T, riding with the rows
     for (int hf = 0; hf < 2; hf++) {
         const int row = lane + 32 * hf;
         const bool in = row < n;
@@ -288,6 +307,7 @@ __device__ unsigned long long gp_clifford_run(GpTab& T, const OpRec* ops, unsign
         r[hf].de = in ? T.de[row] : 0;
         r[hf].piv = in ? T.piv[row] : 0x7fffffff;
         r[hf].A = in ? (1ull << row) : 0;
+        C[hf] = r[hf].A;
         r[hf].t0 = 0;
         r[hf].t1 = 0;
     }
@@ -311,7 +331,7 @@ __device__ unsigned long long gp_clifford_run(GpTab& T, const OpRec* ops, unsign
         if (gi >= o1 || kind > 8) break;
         const int q0 = (int)__shfl_sync(SF_FULL, wr.q0, src);
         const int q1 = kind >= 6 ? (int)__shfl_sync(SF_FULL, wr.q1, src) : 0;
-        if (!warp_clifford_gate(r, n, rx, (int)kind, q0, q1, stage, ga, gb)) {
+        if (!warp_clifford_gate(r, n, rx, (int)kind, q0, q1, stage, ga, gb, C, cstage)) {
             good = false;
             break;
         }
@@ -326,13 +346,17 @@ __device__ unsigned long long gp_clifford_run(GpTab& T, const OpRec* ops, unsign
             T.dz[row] = r[hf].dz;
             T.de[row] = r[hf].de;
             T.piv[row] = r[hf].piv;
-            arows[row] = r[hf].A;
         }
     }
     for (int j = 0; j < n; j++) {
         const unsigned b0 = __ballot_sync(SF_FULL, lane < n && ((r[0].A >> j) & 1));
         const unsigned b1 = __ballot_sync(SF_FULL, lane + 32 < n && ((r[1].A >> j) & 1));
-        if (lane == 0) at[j] = (uint64_t)b0 | ((uint64_t)b1 << 32);
+        const unsigned c0 = __ballot_sync(SF_FULL, lane < n && ((C[0] >> j) & 1));
+        const unsigned c1 = __ballot_sync(SF_FULL, lane + 32 < n && ((C[1] >> j) & 1));
+        if (lane == 0) {
+            at[j] = (uint64_t)b0 | ((uint64_t)b1 << 32);
+            ainv[j] = (uint64_t)c0 | ((uint64_t)c1 << 32);  // row j of A^-1 = column j of A^-T
+        }
     }
     const unsigned t0 = __ballot_sync(SF_FULL, lane < n && r[0].t0);
     const unsigned t1 = __ballot_sync(SF_FULL, lane + 32 < n && r[1].t0);
@@ -429,24 +453,11 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a
 }
 __device__ __forceinline__ double2 cprod(double2 a, double2 b) { return cfma(a, b, make_double2(0.0, 0.0)); }
 
-__device__ __forceinline__ Cm2 cm2_mul(const Cm2& x, const Cm2& y) {  // x * y
-    Cm2 r;
-    r.m00 = cfma(x.m01, y.m10, cprod(x.m00, y.m00));
-    r.m01 = cfma(x.m01, y.m11, cprod(x.m00, y.m01));
-    r.m10 = cfma(x.m11, y.m10, cprod(x.m10, y.m00));
-    r.m11 = cfma(x.m11, y.m11, cprod(x.m10, y.m01));
-    return r;
-}
-
-__device__ __forceinline__ double2 shfl_down_c(double2 v, int off) {
-    return make_double2(__shfl_down_sync(SF_FULL, v.x, off), __shfl_down_sync(SF_FULL, v.y, off));
-}
-
 // Warp 0: if every term of records [r0, r1) (at most 32) is orthogonal to the
 // hull directions hb[0 .. nhb), the product of their pair matrices at
 // (s0, s0 ^ u) into *out and true (every lane); otherwise false.
 __device__ bool uniform_run(const GpPlan* spl, int r0, int r1, const uint64_t* hb, int nhb, uint64_t s0, uint64_t u,
-                            bool flags, Cm2* out) {
+                            bool flags, double (*cm)[8], Cm2* out) {
     const int lane = threadIdx.x & 31;
     const int r = r0 + lane;
     if (flags) {  // the planner's per-record verdicts
@@ -489,16 +500,63 @@ __device__ bool uniform_run(const GpPlan* spl, int r0, int r1, const uint64_t* h
             M.m10 = half_coef(Q, spl[r].ctab, 1, s0);
         }
     }
-    // ceil(log2(r1 - r0)) levels (lanes past r1 hold the identity)
-    for (int off = 1; off < r1 - r0; off <<= 1) {
-        Cm2 o;
-        o.m00 = shfl_down_c(M.m00, off);
-        o.m01 = shfl_down_c(M.m01, off);
-        o.m10 = shfl_down_c(M.m10, off);
-        o.m11 = shfl_down_c(M.m11, off);
-        if ((lane & (2 * off - 1)) == 0) M = cm2_mul(o, M);  // later records on the left
+    // The product, later records on the left, as a tree of ceil(log2(records))
+    // levels through shared memory: each 2x2 complex product is spread over 8
+    // lanes, one real output each (4 fused multiply-adds), so that 4 products
+    // fill one warp instruction -- a double-precision instruction occupies the
+    // pipe as long for one active lane as for 32.
+    if (r < r1) {
+        cm[lane][0] = M.m00.x; cm[lane][1] = M.m00.y;
+        cm[lane][2] = M.m01.x; cm[lane][3] = M.m01.y;
+        cm[lane][4] = M.m10.x; cm[lane][5] = M.m10.y;
+        cm[lane][6] = M.m11.x; cm[lane][7] = M.m11.y;
     }
-    if (lane == 0) *out = M;
+    __syncwarp();
+    const int o = lane & 7, e = o >> 1, im = o & 1, ri = e >> 1, cj = e & 1;
+    for (int cnt = r1 - r0; cnt > 1;) {
+        const int np = cnt >> 1;  // products (2q + 1) x (2q); an odd last matrix carries over
+        double res[4];
+#pragma unroll
+        for (int rd = 0; rd < 4; rd++) {
+            const int q = 4 * rd + (lane >> 3);
+            double v = 0.0;
+            if (q < np) {
+                const double* X = cm[2 * q + 1];
+                const double* Y = cm[2 * q];
+                // entry (ri, cj) = X[ri][0] Y[0][cj] + X[ri][1] Y[1][cj]
+                const double a0r = X[(2 * ri) * 2], a0i = X[(2 * ri) * 2 + 1];
+                const double a1r = X[(2 * ri + 1) * 2], a1i = X[(2 * ri + 1) * 2 + 1];
+                const double b0r = Y[cj * 2], b0i = Y[cj * 2 + 1];
+                const double b1r = Y[(2 + cj) * 2], b1i = Y[(2 + cj) * 2 + 1];
+                // re: a0r b0r - a0i b0i + a1r b1r - a1i b1i
+                // im: a0r b0i + a0i b0r + a1r b1i + a1i b1r
+                // (operands selected and signs flipped by integer operations, so
+                // every lane issues the same four double-precision instructions)
+                const double y1 = im ? b0i : b0r, y2 = im ? b0r : b0i;
+                const double y3 = im ? b1i : b1r, y4 = im ? b1r : b1i;
+                const double x2 = dneg_if(a0i, !im), x4 = dneg_if(a1i, !im);
+                v = fma(a0r, y1, fma(x2, y2, fma(a1r, y3, x4 * y4)));
+            }
+            res[rd] = v;
+        }
+        const double carry = (cnt & 1) && lane < 8 ? cm[cnt - 1][lane] : 0.0;
+        __syncwarp();
+#pragma unroll
+        for (int rd = 0; rd < 4; rd++) {
+            const int q = 4 * rd + (lane >> 3);
+            if (q < np) cm[q][o] = res[rd];
+        }
+        if ((cnt & 1) && lane < 8) cm[np][lane] = carry;
+        __syncwarp();
+        cnt = np + (cnt & 1);
+    }
+    if (lane == 0) {
+        M.m00 = make_double2(cm[0][0], cm[0][1]);
+        M.m01 = make_double2(cm[0][2], cm[0][3]);
+        M.m10 = make_double2(cm[0][4], cm[0][5]);
+        M.m11 = make_double2(cm[0][6], cm[0][7]);
+        *out = M;
+    }
     __syncwarp();
     return true;
 }
@@ -529,13 +587,14 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
     __shared__ unsigned long long s_oe;
     __shared__ uint64_t tab[16 * 16];
     __shared__ Row stage[64];
+    __shared__ uint64_t s_cst[64];
     __shared__ unsigned int wsum[kGpThreads / 32];
     __shared__ unsigned long long bbase;
-    __shared__ int s_inv_ok;
     __shared__ uint64_t s_hc[64];            // hull constraints
     __shared__ uint64_t s_hb[64];            // directions spanning the hull
     __shared__ int s_nhb;
     __shared__ Cm2 s_comp;                   // product of a run's pair matrices
+    __shared__ double s_cm[32][8];           // ... and the levels of its tree
     __shared__ int s_uni;                    // ... valid for the current pass
     __shared__ uint64_t s_ref;               // a phase vector of the frame (new coordinates)
     __shared__ int s_take, s_np, s_kind;     // a planned step taken from the ring: ok, records, kind
@@ -573,109 +632,165 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
         s_tab.g = __ldcg(d.g);
     }
     __syncthreads();
-    if (gridDim.x > 1 && blockIdx.x == gridDim.x - 1) {
-        // ---- the planner CTA.  The Clifford runs, the inverses of their maps and
-        // the plans of the diagonal records depend on the tableau alone, never on
-        // the frame, so this CTA computes them ahead of the workers (up to kGpRing
-        // steps) while they run the passes of earlier steps.  Every wait is
-        // bounded and ends early when a worker has failed.
-        const unsigned nw = gridDim.x - 1;
+    if (gp_piped() && blockIdx.x >= gridDim.x - 2) {
+        // ---- the planning CTAs.  The Clifford runs, their maps and the plans of
+        // the diagonal records depend on the tableau alone, never on the frame,
+        // so they run ahead of the workers while those run the passes of earlier
+        // steps: the tableau CTA applies the Clifford runs (the only chain from
+        // step to step), the plan CTA plans each step's records from the
+        // tableau it is handed.  Every wait is bounded and ends early when a
+        // worker has failed.
+        const unsigned nw = gp_nwork();
         const unsigned long long lim = 64ull * spin_limit;
         const int nwarps = (int)(blockDim.x >> 5);
-        if (threadIdx.x == 0) {  // the records passed the check (and their e^{i theta} are in trig)
-            unsigned long long spins = 0;
-            int okw = 1;
-            while (ld_acquire(&w->checked) == 0) {
-                if (*(volatile uint32_t*)d.status || ++spins > lim) {
-                    okw = 0;
-                    break;
-                }
-                __nanosleep(100);
-            }
-            s_uni = okw;
-        }
-        __syncthreads();
-        if (!s_uni) return;
-        unsigned long long poi = 0;
-        unsigned pset = 0;
-        while (poi < n_ops) {
-            const uint32_t kind = ops[poi].kind;
-            const bool cliff = kind <= 8, diag = kind >= SF_OP_DIAG && kind <= SF_OP_DIAG + 3;
-            if (!cliff && !diag) break;  // the workers stop at the same record
-            const unsigned e = pset % kGpRing;
-            if (pset >= kGpRing) {  // the slot's previous step was copied by every worker
-                if (threadIdx.x == 0) {
-                    unsigned long long spins = 0;
-                    int okw = 1;
-                    while (ld_acquire(&w->ring_readers[e]) != nw) {
-                        if (*(volatile uint32_t*)d.status || ++spins > lim) {
-                            okw = 0;
-                            break;
-                        }
-                        __nanosleep(100);
+        // thread 0 polls *p until it reads v (eq) or anything but v (!eq)
+        auto wait_u32 = [&](const unsigned* p, unsigned v) -> bool {
+            if (threadIdx.x == 0) {
+                unsigned long long spins = 0;
+                int okw = 1;
+                while (ld_acquire(p) != v) {
+                    if (*(volatile uint32_t*)d.status || ++spins > lim) {
+                        okw = 0;
+                        break;
                     }
-                    s_uni = okw;
+                    __nanosleep(100);
                 }
-                __syncthreads();
-                if (!s_uni) return;
+                s_uni = okw;
             }
-            GpSet* S = &w->ring[e];
-            int np = 0, skind = cliff ? 0 : 1;
-            unsigned long long oe = poi;
-            if (cliff) {
-                if (warp == 0) {
-                    const unsigned long long o = gp_clifford_run(s_tab, ops, poi, n_ops, n, stage, s_at, s_ainv, &s_t);
-                    if (lane == 0) s_oe = o;
+            __syncthreads();
+            return s_uni != 0;
+        };
+        if (blockIdx.x == gridDim.x - 2) {
+            // ---- tableau CTA
+            if (!wait_u32(&w->checked, 1u)) return;  // the records passed the check
+            unsigned long long poi = 0;
+            unsigned tset = 0;
+            int tk = 0;
+            for (;;) {
+                bool cliff = false, stop = poi >= n_ops;
+                if (!stop) {
+                    const uint32_t kind = ops[poi].kind;
+                    cliff = kind <= 8;
+                    stop = !cliff && !(kind >= SF_OP_DIAG && kind <= SF_OP_DIAG + 3);
                 }
-                __syncthreads();
-                oe = s_oe;
-                if (oe == ~0ull) {
-                    skind = 2;
-                } else {
-                    np = diag_count(ops, oe, n_ops);
-                    if (warp == 0) {  // rows of A^-1
-                        const uint64_t av[2] = {lane < n ? s_ainv[lane] : 0, lane + 32 < n ? s_ainv[lane + 32] : 0};
-                        uint64_t iv[2];
-                        const bool inv_ok = warp_gf2_inverse(av, n, iv);
-                        __syncwarp();
-                        for (int hf = 0; hf < 2; hf++)
-                            if (lane + 32 * hf < n) s_ainv[lane + 32 * hf] = iv[hf];
-                        if (lane == 0) s_inv_ok = inv_ok;
-                    } else {
-                        for (int r = warp - 1; r < np; r += nwarps - 1)
-                            gp_plan(s_tab, n, ops[oe + r], __ldcg(&trig[oe + r]), spl[r]);
+                const unsigned e = tset % kGpRing;
+                if (tset >= kGpRing && !wait_u32(&w->tring_readers[e], 1u)) return;
+                GpTabSet* T = &w->tring[e];
+                int np = 0;
+                unsigned long long oe = poi, ds = poi;
+                if (stop) {
+                    tk = 3;
+                } else if (cliff) {
+                    if (warp == 0) {
+                        const unsigned long long o =
+                            gp_clifford_run(s_tab, ops, poi, n_ops, n, stage, s_cst, s_at, s_ainv, &s_t);
+                        if (lane == 0) s_oe = o;
                     }
                     __syncthreads();
-                    if (!s_inv_ok) {
-                        skind = 3;
+                    oe = s_oe;
+                    if (oe == ~0ull) {
+                        tk = 2;
                     } else {
-                        // the hull moves with the run's map, as in the workers
-                        const int i = threadIdx.x;
-                        uint64_t hc = 0, hb = 0;
-                        if (i < 64) {
-                            const uint64_t c = s_hc[i];
-                            for (int h = 0; h < n; h++)
-                                if ((c >> h) & 1) hc ^= s_ainv[h];
-                            if (i < s_nhb) {
-                                const uint64_t u = s_hb[i];
-                                for (int j = 0; j < n; j++)
-                                    if ((u >> j) & 1) hb ^= s_at[j];
-                            }
-                        }
-                        __syncthreads();
-                        if (i < 64) {
-                            s_hc[i] = hc;
-                            if (i < s_nhb) s_hb[i] = hb;
-                        }
-                        __syncthreads();
+                        tk = 0;
+                        ds = oe;
+                        np = diag_count(ops, oe, n_ops);
+                    }
+                } else {
+                    tk = 1;
+                    np = diag_count(ops, poi, n_ops);
+                }
+                {
+                    const uint64_t* src = reinterpret_cast<const uint64_t*>(&s_tab);
+                    uint64_t* dst = reinterpret_cast<uint64_t*>(&T->tab);
+                    for (int i = threadIdx.x; i < (int)(sizeof(GpTab) / 8); i += blockDim.x) dst[i] = src[i];
+                    if (threadIdx.x < 64) {
+                        T->at[threadIdx.x] = s_at[threadIdx.x];
+                        T->ainv[threadIdx.x] = s_ainv[threadIdx.x];
+                    }
+                    if (threadIdx.x == 0) {
+                        T->t = s_t;
+                        T->kind = tk;
+                        T->np = np;
+                        T->oe = oe;
+                        T->ds = ds;
                     }
                 }
-            } else {
-                np = diag_count(ops, poi, n_ops);
-                for (int r = warp; r < np; r += nwarps) gp_plan(s_tab, n, ops[poi + r], __ldcg(&trig[poi + r]), spl[r]);
+                __threadfence();
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    w->tring_readers[e] = 0;
+                    __threadfence();
+                    st_release64(&w->tring_seq[e], (unsigned long long)tset + 1ull);
+                }
+                tset++;
+                if (tk >= 2) break;
+                poi = ds + np;
+            }
+            return;
+        }
+        // ---- plan CTA
+        unsigned pset = 0;
+        for (;;) {
+            const unsigned te = pset % kGpRing;
+            if (threadIdx.x == 0) {  // the tableau CTA's step pset
+                unsigned long long spins = 0;
+                int okw = 1;
+                while (ld_acquire64(&w->tring_seq[te]) != (unsigned long long)pset + 1ull) {
+                    if (*(volatile uint32_t*)d.status || ++spins > lim) {
+                        okw = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                s_uni = okw;
+            }
+            __syncthreads();
+            if (!s_uni) return;
+            const GpTabSet* T = &w->tring[te];
+            {
+                const uint64_t* src = reinterpret_cast<const uint64_t*>(&T->tab);
+                uint64_t* dst = reinterpret_cast<uint64_t*>(&s_tab);
+                for (int i = threadIdx.x; i < (int)(sizeof(GpTab) / 8); i += blockDim.x) dst[i] = __ldcg(&src[i]);
+                if (threadIdx.x < 64) {
+                    s_at[threadIdx.x] = __ldcg(&T->at[threadIdx.x]);
+                    s_ainv[threadIdx.x] = __ldcg(&T->ainv[threadIdx.x]);
+                }
+            }
+            const int tk = __ldcg(&T->kind), np = __ldcg(&T->np);
+            const unsigned long long oe = __ldcg(&T->oe), ds = __ldcg(&T->ds);
+            if (threadIdx.x == 0) s_t = __ldcg(&T->t);
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(&w->tring_readers[te], 1u);
+            if (tk == 3) return;  // the workers stop at the same record
+            const unsigned e = pset % kGpRing;
+            if (pset >= kGpRing && !wait_u32(&w->ring_readers[e], nw)) return;
+            GpSet* S = &w->ring[e];
+            if (tk < 2) {
+                for (int r = warp; r < np; r += nwarps) gp_plan(s_tab, n, ops[ds + r], __ldcg(&trig[ds + r]), spl[r]);
                 __syncthreads();
             }
-            if (skind < 2 && warp == 0) {
+            if (tk == 0) {
+                // the hull moves with the run's map, as in the workers
+                const int i = threadIdx.x;
+                uint64_t hc = 0, hb = 0;
+                if (i < 64) {
+                    const uint64_t c = s_hc[i];
+                    for (int h = 0; h < n; h++)
+                        if ((c >> h) & 1) hc ^= s_ainv[h];
+                    if (i < s_nhb) {
+                        const uint64_t u = s_hb[i];
+                        for (int j = 0; j < n; j++)
+                            if ((u >> j) & 1) hb ^= s_at[j];
+                    }
+                }
+                __syncthreads();
+                if (i < 64) {
+                    s_hc[i] = hc;
+                    if (i < s_nhb) s_hb[i] = hb;
+                }
+                __syncthreads();
+            }
+            if (tk < 2 && warp == 0) {
                 // Per record: are its terms orthogonal to the hull where the workers
                 // apply it?  The hull is followed record by record as the workers
                 // change theirs -- a fresh direction joins after its whole run (the
@@ -683,11 +798,16 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 // against the hull before it), a merge's masks join after it -- except
                 // that it always grows where the workers skip a direction whose
                 // children all vanished, so it contains theirs and a yes is safe.
+                // Directions are only appended within a batch, so the walk records
+                // for each record how many of them it is checked against (lane 0
+                // keeps the count), and the checks then run one lane per record.
                 uint64_t pend = 0;
                 bool have_pend = false;
                 for (int r = 0; r < np; r++) {
                     const BrTab& Q = spl[r].P;
-                    const bool cont = have_pend && (Q.ng == 1 || (Q.ng == 2 && Q.u[1] == pend));
+                    const int ng = Q.ng;
+                    const uint64_t u1 = Q.u[1];
+                    const bool cont = have_pend && (ng == 1 || (ng == 2 && u1 == pend));
                     if (!cont && have_pend) {
                         if (hull_fresh(s_hc, pend)) {
                             hull_add(s_hc, pend);
@@ -696,26 +816,18 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                         }
                         have_pend = false;
                     }
-                    const uint64_t h0 = lane < s_nhb ? s_hb[lane] : 0ull;
-                    const uint64_t h1 = lane + 32 < s_nhb ? s_hb[lane + 32] : 0ull;
-                    bool odd = false;
-                    for (int g = 0; g < Q.ng; g++)
-                        for (int t = 0; t < Q.nt[g]; t++) {
-                            const uint64_t v = Q.v[g][t];
-                            odd |= ((__popcll(v & h0) | __popcll(v & h1)) & 1) != 0;
-                        }
-                    const int orth = !__any_sync(SF_FULL, odd);
-                    if (lane == 0) spl[r].orth = orth;
+                    if (lane == 0) spl[r].orth = s_nhb;  // directions the record is checked against
                     __syncwarp();
                     if (cont) continue;
-                    if (Q.ng == 2 && hull_fresh(s_hc, Q.u[1])) {
-                        pend = Q.u[1];
+                    if (ng == 2 && hull_fresh(s_hc, u1)) {
+                        pend = u1;
                         have_pend = true;
                     } else {
-                        for (int g = 1; g < Q.ng; g++) {
-                            if (hull_fresh(s_hc, Q.u[g])) {
-                                hull_add(s_hc, Q.u[g]);
-                                if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = Q.u[g];
+                        for (int g = 1; g < ng; g++) {
+                            const uint64_t ug = Q.u[g];
+                            if (hull_fresh(s_hc, ug)) {
+                                hull_add(s_hc, ug);
+                                if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = ug;
                                 __syncwarp();
                             }
                         }
@@ -724,28 +836,35 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 if (have_pend && hull_fresh(s_hc, pend)) {
                     hull_add(s_hc, pend);
                     if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = pend;
-                    __syncwarp();
                 }
-            }
-            __syncthreads();
+                __syncwarp();
+                for (int r = lane; r < np; r += 32) {
+                    const BrTab& Q = spl[r].P;
+                    const int m = spl[r].orth;
+                    bool odd = false;
+                    for (int i = 0; i < m && !odd; i++) {
+                        const uint64_t h = s_hb[i];
+                        for (int g = 0; g < Q.ng; g++)
+                            for (int t = 0; t < Q.nt[g]; t++) odd |= (__popcll(Q.v[g][t] & h) & 1) != 0;
+                    }
+                    spl[r].orth = !odd;
+                }
+            }            __syncthreads();
             {
                 const uint64_t* src = reinterpret_cast<const uint64_t*>(&spl[0]);
                 uint64_t* dst = reinterpret_cast<uint64_t*>(&S->plans[0]);
-                const int words = (skind < 2 ? np : 0) * (int)(sizeof(GpPlan) / 8);
+                const int words = (tk < 2 ? np : 0) * (int)(sizeof(GpPlan) / 8);
                 for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-            }
-            // the tableau after the run and its map go with the plans
-            {
-                const uint64_t* src = reinterpret_cast<const uint64_t*>(&s_tab);
-                uint64_t* dst = reinterpret_cast<uint64_t*>(&S->tab);
-                for (int i = threadIdx.x; i < (int)(sizeof(GpTab) / 8); i += blockDim.x) dst[i] = src[i];
+                const uint64_t* tsrc = reinterpret_cast<const uint64_t*>(&s_tab);
+                uint64_t* tdst = reinterpret_cast<uint64_t*>(&S->tab);
+                for (int i = threadIdx.x; i < (int)(sizeof(GpTab) / 8); i += blockDim.x) tdst[i] = tsrc[i];
                 if (threadIdx.x < 64) {
                     S->at[threadIdx.x] = s_at[threadIdx.x];
                     S->ainv[threadIdx.x] = s_ainv[threadIdx.x];
                 }
                 if (threadIdx.x == 0) {
                     S->t = s_t;
-                    S->kind = skind;
+                    S->kind = tk;
                     S->np = np;
                     S->oe = oe;
                 }
@@ -758,10 +877,8 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 st_release64(&w->ring_seq[e], (unsigned long long)pset + 1ull);
             }
             pset++;
-            if (skind >= 2) break;
-            poi = cliff ? oe + np : poi + np;
+            if (tk == 2) return;
         }
-        return;
     }
     // every record is checked before anything is touched
     {
@@ -794,7 +911,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
         if (blockIdx.x == 0 && threadIdx.x == 0) st_release32(&w->checked, 1u);
     }
     int cur = cur0;
-    const bool piped = gridDim.x > 1;  // a planner CTA plans ahead (the workers take its steps)
+    const bool piped = gp_piped();  // the planning CTAs plan ahead (the workers take their steps)
     unsigned long long k = d.kcnt[cur0];
     uint32_t tag[2] = {d.itag[0], d.itag[1]};
     unsigned long long isz[2] = {d.isize[0], d.isize[1]};
@@ -896,7 +1013,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
         }
         __syncthreads();
         if (warp == 0) {
-            const bool uni = k && r1 - r0 >= 3 && uniform_run(spl, r0, r1, s_hb, s_nhb, s_ref, u, piped, &s_comp);
+            const bool uni = k && r1 - r0 >= 3 && uniform_run(spl, r0, r1, s_hb, s_nhb, s_ref, u, piped, s_cm, &s_comp);
             if (lane == 0) s_uni = uni;
         }
         __syncthreads();
@@ -1062,9 +1179,8 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 // the planner CTA ran the Clifford run and planned what follows
                 if (!take_set()) return set_timeout();
                 gp_mark(w, 1);
-                if (s_kind >= 2) {  // a tableau check (2) or the map's inverse (3) failed
-                    if (blockIdx.x == 0 && threadIdx.x == 0)
-                        set_status(d.status, SF_ST_INTERNAL, cur, s_kind == 2 ? 41u : 49u);
+                if (s_kind >= 2) {  // a tableau check failed
+                    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, cur, 41u);
                     if (aff) affine_pass();
                     return bail();
                 }
@@ -1077,7 +1193,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 continue;
             }
             if (warp == 0) {
-                const unsigned long long oe = gp_clifford_run(s_tab, ops, oi, n_ops, n, stage, s_at, s_ainv, &s_t);
+                const unsigned long long oe = gp_clifford_run(s_tab, ops, oi, n_ops, n, stage, s_cst, s_at, s_ainv, &s_t);
                 if (lane == 0) s_oe = oe;
             }
             __syncthreads();
@@ -1088,25 +1204,9 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 return bail();
             }
             const int np = diag_count(ops, oe, n_ops);
-            if (warp == 0) {
-                // rows of A^-1: for a merge that reads the phase vectors before the map,
-                // and for the hull constraints
-                const uint64_t av[2] = {lane < n ? s_ainv[lane] : 0, lane + 32 < n ? s_ainv[lane + 32] : 0};
-                uint64_t iv[2];
-                const bool inv_ok = warp_gf2_inverse(av, n, iv);
-                __syncwarp();
-                for (int hf = 0; hf < 2; hf++)
-                    if (lane + 32 * hf < n) s_ainv[lane + 32 * hf] = iv[hf];
-                if (lane == 0) s_inv_ok = inv_ok;
-            } else {
-                for (int r = warp - 1; r < np; r += (int)(blockDim.x >> 5) - 1)
-                    gp_plan(s_tab, n, ops[oe + r], __ldcg(&trig[oe + r]), spl[r]);
-            }
+            for (int r = warp; r < np; r += (int)(blockDim.x >> 5))
+                gp_plan(s_tab, n, ops[oe + r], __ldcg(&trig[oe + r]), spl[r]);
             __syncthreads();
-            if (!s_inv_ok) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, cur, 49u);
-                return bail();
-            }
             gp_mark(w, 2);
             npre = (unsigned)np;
             have_u = false;

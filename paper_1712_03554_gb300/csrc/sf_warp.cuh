@@ -186,7 +186,13 @@ __device__ __forceinline__ unsigned pivot_key(const Row& a, int c, int n, int ro
     return (rank << 6) | (unsigned)row;
 }
 
-__device__ __forceinline__ int warp_rref(Row* r, int n, Row* stage) {
+// Optionally (C, cstage non-null) the rows of C = A^-T ride along, two per
+// lane like the rows: a step A_a ^= A_p over the eliminated rows a is
+// C_p ^= XOR of their C_a (A' = E A with E = I + s e_p^T, E^-1 = E, so
+// A'^-T = E^T A^-T), and the sort moves C with its row (cstage: 64 words of
+// shared memory owned by the warp).  The rows of A^-1 are then C's columns.
+__device__ __forceinline__ int warp_rref(Row* r, int n, Row* stage, uint64_t* C = nullptr,
+                                         uint64_t* cstage = nullptr) {
     const int lane = threadIdx.x & 31;
     constexpr int INF = 0x7fffffff;
     const bool v0 = lane < n, v1 = lane + 32 < n;
@@ -224,10 +230,18 @@ __device__ __forceinline__ int warp_rref(Row* r, int n, Row* stage) {
         uint64_t dx = 0, dz = 0;
         int de = 0;
         bool any = false;
+        const bool e0 = v0 && lane != p && col_in(c, n, r[0].mx, r[0].mz);
+        const bool e1 = v1 && lane + 32 != p && col_in(c, n, r[1].mx, r[1].mz);
         if (v0 && lane != p) elim_row(r[0], pv, c, n, dx, dz, de, any);
         if (v1 && lane + 32 != p) elim_row(r[1], pv, c, n, dx, dz, de, any);
         const bool with_d = __any_sync(SF_FULL, any);
         if (with_d) warp_prod(dx, dz, de);
+        if (C) {
+            uint64_t cs = (e0 ? C[0] : 0ull) ^ (e1 ? C[1] : 0ull);
+#pragma unroll
+            for (int off = 16; off; off >>= 1) cs ^= __shfl_xor_sync(SF_FULL, cs, off);
+            if (lane == (p & 31)) C[p >> 5] ^= cs;
+        }
         if (lane == (p & 31)) {
             if (p < 32) { take_pivot(r[0], c, with_d, dx, dz, de); asg0 = true; }
             else { take_pivot(r[1], c, with_d, dx, dz, de); asg1 = true; }
@@ -247,9 +261,17 @@ __device__ __forceinline__ int warp_rref(Row* r, int n, Row* stage) {
     if (__any_sync(SF_FULL, k0 != lane || k1 != lane + 32)) {
         if (v0) stage[k0] = r[0];
         if (v1) stage[k1] = r[1];
+        if (C) {
+            if (v0) cstage[k0] = C[0];
+            if (v1) cstage[k1] = C[1];
+        }
         __syncwarp();
         if (v0) r[0] = stage[lane];
         if (v1) r[1] = stage[lane + 32];
+        if (C) {
+            if (v0) C[0] = cstage[lane];
+            if (v1) C[1] = cstage[lane + 32];
+        }
         __syncwarp();
     }
     return rx;
@@ -413,55 +435,13 @@ __device__ __forceinline__ int warp_measure_prep(Row* r, int n, int rx, int q, C
     return rx2;
 }
 
-// Rows of the inverse of the GF(2) matrix whose rows are a[] (lane L: rows L
-// and L + 32 of n), by Gauss-Jordan elimination over the warp.  Returns false
-// if the matrix is singular.
-__device__ __forceinline__ bool warp_gf2_inverse(const uint64_t* a_in, int n, uint64_t* inv) {
-    const int lane = threadIdx.x & 31;
-    uint64_t a[2] = {a_in[0], a_in[1]};
-    uint64_t b[2] = {lane < n ? 1ull << lane : 0, lane + 32 < n ? 1ull << (lane + 32) : 0};
-    for (int c = 0; c < n; c++) {
-        // pivot: the first row p >= c with bit c set
-        const unsigned m0 = __ballot_sync(SF_FULL, lane >= c && lane < n && ((a[0] >> c) & 1));
-        const unsigned m1 = __ballot_sync(SF_FULL, lane + 32 >= c && lane + 32 < n && ((a[1] >> c) & 1));
-        if (!m0 && !m1) return false;
-        const int p = m0 ? __ffs(m0) - 1 : 32 + __ffs(m1) - 1;
-        const uint64_t pa0 = __shfl_sync(SF_FULL, a[0], p & 31), pa1 = __shfl_sync(SF_FULL, a[1], p & 31);
-        const uint64_t pb0 = __shfl_sync(SF_FULL, b[0], p & 31), pb1 = __shfl_sync(SF_FULL, b[1], p & 31);
-        const uint64_t ca0 = __shfl_sync(SF_FULL, a[0], c & 31), ca1 = __shfl_sync(SF_FULL, a[1], c & 31);
-        const uint64_t cb0 = __shfl_sync(SF_FULL, b[0], c & 31), cb1 = __shfl_sync(SF_FULL, b[1], c & 31);
-        const uint64_t pa = p < 32 ? pa0 : pa1, pb = p < 32 ? pb0 : pb1;
-        const uint64_t ca = c < 32 ? ca0 : ca1, cb = c < 32 ? cb0 : cb1;
-        for (int hf = 0; hf < 2; hf++) {
-            const int row = lane + 32 * hf;
-            if (row >= n) continue;
-            if (row == c) {  // rows c and p swap
-                a[hf] = pa;
-                b[hf] = pb;
-            } else {
-                if (row == p) {
-                    a[hf] = ca;
-                    b[hf] = cb;
-                }
-                if ((a[hf] >> c) & 1) {  // clear column c
-                    a[hf] ^= pa;
-                    b[hf] ^= pb;
-                }
-            }
-        }
-    }
-    inv[0] = b[0];
-    inv[1] = b[1];
-    return true;
-}
-
 // One Clifford gate on the rows in registers (ROTATE, Sec. III, Table 2):
 // conjugate M and D (sign flips of M to t0, composed, and t1, this gate),
 // restore Invariant 1, and multiply the run's phase factor omega^ga sqrt(2)^gb
 // by the gate's.  rx is the X-block size.  Returns false if the phase rule
 // finds no point (an internal error).
 __device__ __forceinline__ bool warp_clifford_gate(Row* r, int n, int& rx, int kind, int q0, int q1, Row* stage,
-                                                   int& ga, int& gb) {
+                                                   int& ga, int& gb, uint64_t* C = nullptr, uint64_t* cstage = nullptr) {
     const int lane = threadIdx.x & 31;
     // numerator of the phase rule: a point y with <y|U phi_0(M)> != 0
     int yq = -1, cq = -1;
@@ -487,7 +467,7 @@ __device__ __forceinline__ bool warp_clifford_gate(Row* r, int n, int& rx, int k
         }
     }
     // Pauli gates flip signs only: M keeps its bits and stays in RREF
-    if (kind < 3 || kind > 5) rx = warp_rref(r, n, stage);
+    if (kind < 3 || kind > 5) rx = warp_rref(r, n, stage, C, cstage);
     // denominator: <y| D'^{t1} phi_0(M')>
     const int dq = rx < 0 ? -1 : warp_amp_phi(r, n, rx, true, yq >= 0 ? (1ull << yq) : 0ull);
     if (dq < 0) return false;
