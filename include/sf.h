@@ -249,8 +249,11 @@ sf_status sf_coalesce_noalloc(const uint64_t* sigma_in, const double* amp_in, ui
                               void* cuda_stream);
 
 /* Host-side bookkeeping of the handle: which of its two frame buffers holds
- * the current frame, which buffers carry a valid phase-vector index, and what
- * the grid program may assume about the frame's phase vectors.  A
+ * the current frame, which buffers carry a valid phase-vector index, what the
+ * grid program may assume about the frame's phase vectors, and whether the
+ * frame's elements are still where the last grid program left them (a
+ * measurement then finds cofactor partners by position).  The token is below
+ * 64.  A
  * CUDA graph captured from this handle's stream replays device work only, so
  * read the token right after the capture ends and restore it with
  * sf_set_host_state after every replay, before the next call on the handle. */

@@ -45,6 +45,9 @@ struct sf_frame_s {
     std::vector<void*> dallocs;
     std::string err;
     bool idx_ok[2] = {false, false};  // buffer b has a valid phase-vector index
+    // no kernel has moved or changed the frame's elements since the last grid
+    // program launch (whose layout, if it left one known, is still valid)
+    bool layout = false;
     // what the grid program may assume about the hull of the frame (the span of
     // the differences of its phase vectors): 0 nothing, 1 the constraints its
     // last launch left in its workspace, 2 the frame is one element
@@ -194,6 +197,18 @@ sf_status launch(sf_handle h, int id, const char* what, F&& fn) {
     // a kernel that moves phase vectors to other coordinates or adds new ones
     // invalidates what the grid program knows about the frame's hull; subsets
     // of the frame (coalescing, collapse) keep it valid
+    // the grid program's layout survives kernels that leave the elements where
+    // and as they are
+    switch (id) {
+        case SF_K_GPROG:
+            h->layout = true;
+            break;
+        case SF_K_INDEX: case SF_K_PROB: case SF_K_REDUCE: case SF_K_AMP_PREP: case SF_K_AMPLITUDE:
+        case SF_K_EXPORT: case SF_K_MEASURE_PREP:
+            break;
+        default:
+            h->layout = false;
+    }
     switch (id) {
         case SF_K_CLIFFORD:
         case SF_K_AFFINE:
@@ -227,6 +242,7 @@ sf_status sync_check(sf_handle h) {
         h->cur = (int)((st >> 8) & 1u);
         h->idx_ok[0] = h->idx_ok[1] = false;
         h->hull = 0;
+        h->layout = false;
         SF_CK(h, cudaMemsetAsync(h->d.status, 0, sizeof(uint32_t), h->stream));
         SF_CK(h, cudaMemsetAsync(h->d.done, 0, sizeof(unsigned int), h->stream));
         SF_CK(h, cudaMemsetAsync(h->d.ocnt, 0, sizeof(unsigned long long), h->stream));
@@ -806,11 +822,23 @@ static sf_status cofactor_q(sf_handle h, uint32_t q) {
     sf_status st = sync_check(h);
     if (st) return st;
     if (h->hmeta[2]) {
-        st = need_index(h, h->cur);
-        if (st) return st;
-        SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cof_merge(h->d, h->cur, h->cur ^ 1, h->stream));
-        h->cur ^= 1;
-        h->idx_ok[h->cur] = sf_emit_index(h->d.W);
+        if (h->d.W == 1 && h->layout && h->d.gp) {
+            // partners by position where the grid program left the layout known
+            // (decided on the device; otherwise the index is built and used)
+            const int in = h->cur;
+            if (!h->idx_ok[in])
+                SF_LAUNCH(h, SF_K_INDEX, sf_launch_build_index_unless_layout(h->d, in, h->stream));
+            SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cof_pos(h->d, in, in ^ 1, h->stream));
+            h->idx_ok[in] = false;  // maybe not built
+            h->cur ^= 1;
+            h->idx_ok[h->cur] = false;  // maybe not written
+        } else {
+            st = need_index(h, h->cur);
+            if (st) return st;
+            SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cof_merge(h->d, h->cur, h->cur ^ 1, h->stream));
+            h->cur ^= 1;
+            h->idx_ok[h->cur] = sf_emit_index(h->d.W);
+        }
     }
     return SF_OK;
 }
@@ -956,16 +984,17 @@ uint32_t sf_words(sf_handle h) { return h ? (uint32_t)h->Wabi : 0u; }
 uint32_t sf_host_state(sf_handle h) {
     if (!h) return 0u;
     return (uint32_t)h->cur | ((uint32_t)h->idx_ok[0] << 1) | ((uint32_t)h->idx_ok[1] << 2) |
-           ((uint32_t)h->hull << 3);
+           ((uint32_t)h->hull << 3) | ((uint32_t)h->layout << 5);
 }
 
 sf_status sf_set_host_state(sf_handle h, uint32_t token) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
-    if (token > 31u || (token >> 3) > 2u) return fail(h, SF_EINVAL, "invalid host-state token");
+    if (token > 63u || ((token >> 3) & 3u) > 2u) return fail(h, SF_EINVAL, "invalid host-state token");
     h->cur = (int)(token & 1u);
     h->idx_ok[0] = (token >> 1) & 1u;
     h->idx_ok[1] = (token >> 2) & 1u;
-    h->hull = (int)(token >> 3);
+    h->hull = (int)((token >> 3) & 3u);
+    h->layout = (token >> 5) & 1u;
     return SF_OK;
 }
 

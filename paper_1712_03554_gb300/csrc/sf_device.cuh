@@ -79,6 +79,17 @@ struct SfDev {
     int lowrank;               // 1: low-rank forms of the affine and cofactor maps (W >= 8)
 };
 
+// What the grid program leaves known about the layout of its frame (the first
+// member of its workspace d.gp): after a launch that started from one element
+// and whose branches all doubled the frame in place, the element at position
+// j is s_0 ^ (XOR of u[i] over the set bits i of j), n = log2(frame size).
+// ok = 0: nothing known.  Valid until a kernel moves or changes the elements
+// (the host tracks that and passes its verdict to the kernels that use it).
+struct GpLayout {
+    unsigned ok, n;
+    uint64_t u[64];
+};
+
 // one program record (the layout of sf_op): kind, qubits, conditional-gate
 // kind or parameter bits
 struct OpRec {
@@ -520,6 +531,8 @@ void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t
 // cofactor split with merging of the two parents of each child
 void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s);
 void sf_launch_build_index(const SfDev& d, int buf, cudaStream_t s);
+void sf_launch_cof_pos(const SfDev& d, int in_buf, int out_buf, cudaStream_t s);
+void sf_launch_build_index_unless_layout(const SfDev& d, int buf, cudaStream_t s);
 void sf_launch_filter(const SfDev& d, int x, int in_buf, int out_buf, cudaStream_t s);
 void sf_launch_cond(const SfDev& d, int buf, int kind, int c1, int c2, int t, double alpha, cudaStream_t s);
 void sf_launch_prob(const SfDev& d, int buf, cudaStream_t s);

@@ -1084,8 +1084,10 @@ __global__ void __launch_bounds__(kThreads) k_filter(SfDev d, int x, int in_buf,
 // ---------------------------------------------------------------------------
 // (Re)build the index of buffer b.
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_build_index(SfDev d, int b) {
+__global__ void __launch_bounds__(kThreads) k_build_index(SfDev d, int b, int lay) {
     if (*d.status) return;
+    // a cofactor that finds its partners by position needs no index
+    if (lay && reinterpret_cast<const GpLayout*>(d.gp)->ok) return;
     const unsigned long long k = d.kcnt[b];
     const unsigned long long TI = index_slots(k, d.icap);
     const uint32_t tag = next_tag(d.itag[b]);
@@ -1482,7 +1484,8 @@ __device__ __forceinline__ double2 cof_amp_lr(const CofLR<W>& C, const CofScal& 
 }
 
 template <int W, bool LR>
-__global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, double eps2, int in_buf, int out_buf) {
+__global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, double eps2, int in_buf, int out_buf,
+                                                                    int lay) {
     using Plan = typename std::conditional<LR, CofLR<W>, CofPlan<W>>::type;
     __shared__ Plan CP;
     __shared__ uint64_t uq[W];
@@ -1490,6 +1493,7 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
     __shared__ unsigned long long bbase;
     if (*d.status) return;
     if (!d.meta[2]) return;
+    if (lay && reinterpret_cast<const GpLayout*>(d.gp)->ok) return;  // k_cof_pos runs instead
     if constexpr (W >= 8) {
         // exactly one of the two variants runs
         if ((d.plan[plan_lr_u(d.n, W)] <= SF_LR_MAX) != LR) return;
@@ -1610,6 +1614,199 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
             d.itag[out_buf] = tag_out;
             d.isize[out_buf] = Tout;
         }
+    }
+}
+
+// Cofactor split with merging on a frame whose layout the grid program left
+// known (n <= 63): element j is s_0 ^ (XOR of u[i] over the set bits of j), so
+// the partner s ^ uq of element j sits at j ^ c when uq = XOR of u[i] over the
+// set bits of c, and no element has a partner when uq lies outside the span of
+// the u[i].  No index is read or written, and the work goes by pairs (one
+// thread per pair, so no lane idles through the double-precision pipe).
+// The children are those of cof_child, rewritten: with P the XOR of U_h over
+// the set bits of sigma, t = tau_y ^ P, and the i-power
+//   ip_y = |sigma & eps0| + 2 |sigma & eps1| + 2 (parity(sigma & omega_y) ^ Q),
+// omega_y[h] = V_h . tau_y, Q = sum over set bits h of V_h . (XOR of U_h'
+// over the set bits h' < h) -- one walk over the bits serves both outcomes.
+// kappa_y = sc i^{e_y} (a real scale times an i-power, as the measurement
+// prep builds it), so a child amplitude is sc i^{e_y + ip_y} a: an exact
+// rotation, the partners' two summed, then one real scaling.  Does nothing
+// when the layout is not known (the guarded index build and k_cof_merge run
+// then).
+__global__ void __launch_bounds__(kThreads) k_cof_pos(SfDev d, double eps2, int in_buf, int out_buf) {
+    __shared__ uint64_t sU[64], sV[64];
+    __shared__ unsigned int wsum[kThreads / 32];
+    __shared__ unsigned long long bbase, s_c, s_om[2];
+    __shared__ int s_span, s_e[2];
+    __shared__ double s_sc;
+    if (*d.status) return;
+    if (!d.meta[2]) return;
+    const GpLayout* L = reinterpret_cast<const GpLayout*>(d.gp);
+    if (!L->ok) return;
+    const int n = d.n;
+    const uint64_t* pl = d.plan;
+    const uint64_t uq = pl[cf_uq(n, 1)], vq = pl[cf_vq(n, 1)];
+    const uint64_t eps0 = pl[cf_eps(n, 1)], eps1 = pl[cf_eps(n, 1) + 1];
+    const uint64_t tau[2] = {pl[cf_tau(n, 1)], pl[cf_tau(n, 1) + 1]};
+    if (threadIdx.x < 64) {
+        const int h = threadIdx.x;
+        sU[h] = h < n ? pl[cf_u(n, 1) + h] : 0ull;
+        sV[h] = h < n ? pl[cf_v(n, 1) + h] : 0ull;
+    }
+    if (threadIdx.x == 33) s_om[0] = s_om[1] = 0ull;
+    if (threadIdx.x == 32) {  // kappa_y = sc i^{e_y}
+        bool ok = true;
+        double sc = 0.0;
+        for (int y = 0; y < 2; y++) {
+            const size_t ko = cf_kappa(n, 1) + 2 * y;
+            const double kx = __longlong_as_double((long long)pl[ko]), ky = __longlong_as_double((long long)pl[ko + 1]);
+            ok &= (kx == 0.0) != (ky == 0.0);
+            s_e[y] = kx > 0.0 ? 0 : (ky > 0.0 ? 1 : (kx < 0.0 ? 2 : 3));
+            const double m = fabs(kx) + fabs(ky);
+            ok &= y == 0 || m == sc;
+            sc = m;
+        }
+        s_sc = sc;
+        if (!ok) set_status(d.status, SF_ST_INTERNAL, in_buf, 29u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {  // omega_y
+        const int h = threadIdx.x;
+        const bool o0 = (__popcll(sV[h] & tau[0]) & 1) != 0, o1 = (__popcll(sV[h] & tau[1]) & 1) != 0;
+        const unsigned b0 = __ballot_sync(SF_FULL, o0), b1 = __ballot_sync(SF_FULL, o1);
+        if ((h & 31) == 0) {
+            atomicOr(&s_om[0], (unsigned long long)b0 << h);
+            atomicOr(&s_om[1], (unsigned long long)b1 << h);
+        }
+    }
+    if (threadIdx.x < 32) {
+        // uq in the basis u[0..m): Gauss-Jordan over the bit columns (lane i
+        // holds u[i] and u[i + 32] with their combinations), then uq reduced
+        const int lane = threadIdx.x, m = (int)L->n;
+        uint64_t v[2] = {lane < m ? L->u[lane] : 0ull, lane + 32 < m ? L->u[lane + 32] : 0ull};
+        uint64_t cmb[2] = {lane < m ? 1ull << lane : 0ull, lane + 32 < m ? 1ull << (lane + 32) : 0ull};
+        bool used[2] = {false, false};
+        uint64_t x = uq, cx = 0;
+        for (int b = 0; b < 64; b++) {
+            const bool h0 = !used[0] && ((v[0] >> b) & 1), h1 = !used[1] && ((v[1] >> b) & 1);
+            const unsigned b0 = __ballot_sync(SF_FULL, h0), b1 = __ballot_sync(SF_FULL, h1);
+            if (!(b0 | b1)) continue;
+            const int p = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+            const uint64_t pv = __shfl_sync(SF_FULL, p < 32 ? v[0] : v[1], p & 31);
+            const uint64_t pc = __shfl_sync(SF_FULL, p < 32 ? cmb[0] : cmb[1], p & 31);
+            for (int hf = 0; hf < 2; hf++) {
+                const int idx = lane + 32 * hf;
+                if (idx == p) used[hf] = true;
+                else if ((v[hf] >> b) & 1) {
+                    v[hf] ^= pv;
+                    cmb[hf] ^= pc;
+                }
+            }
+            if ((x >> b) & 1) {
+                x ^= pv;
+                cx ^= pc;
+            }
+        }
+        if (lane == 0) {
+            s_span = x == 0 && cx != 0;
+            s_c = cx;
+        }
+    }
+    __syncthreads();
+    const unsigned long long k = d.kcnt[in_buf];
+    const bool span = s_span != 0 && (s_c >> L->n) == 0;
+    const unsigned long long cmask = s_c;
+    if (!span && 2 * k > d.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_CAPACITY, in_buf);
+        return;
+    }
+    const int bl = span ? __ffsll((long long)cmask) - 1 : 0;  // pairs: the element with bit bl clear
+    const unsigned long long units = span ? k / 2 : k;
+    const uint64_t om0 = s_om[0], om1 = s_om[1];
+    const int e0 = s_e[0], e1 = s_e[1];
+    const double sc = s_sc;
+    const uint64_t* Si = d.sig[in_buf];
+    const double2* Ai = d.amp[in_buf];
+    uint64_t* So = d.sig[out_buf];
+    double2* Ao = d.amp[out_buf];
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long kb = keep_bits(eps2);
+    // the walk over the set bits of an element: P and Q
+    auto walk = [&](uint64_t x, uint64_t& P, int& Q) {
+        P = 0;
+        Q = 0;
+        while (x) {
+            const int h = __ffsll((long long)x) - 1;
+            x &= x - 1;
+            Q ^= __popcll(sV[h] & P) & 1;
+            P ^= sU[h];
+        }
+    };
+    // exponent of child x of element x_el (walk P, Q): y and e_y + ip_y
+    auto expo = [&](uint64_t el, int Q, int x, int& y) {
+        y = x ^ (__popcll(vq & el) & 1);
+        const int pw = __popcll(el & (y ? om1 : om0)) & 1;
+        return (y ? e1 : e0) + __popcll(el & eps0) + 2 * __popcll(el & eps1) + 2 * (pw ^ Q);
+    };
+    bool bad = false;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < units; base += stride) {
+        const unsigned long long m = base + threadIdx.x;
+        const bool act = m < units;
+        unsigned keepm = 0;
+        uint64_t t[2] = {0, 0};
+        double2 cc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+        if (act) {
+            unsigned long long j = m, pj = 0;
+            if (span) {
+                j = ((m >> bl) << (bl + 1)) | (m & ((1ull << bl) - 1ull));
+                pj = j ^ cmask;
+            }
+            uint64_t s0 = Si[j];
+            double2 a0 = Ai[j];
+            uint64_t s1 = 0;
+            double2 a1 = make_double2(0.0, 0.0);
+            if (span) {
+                s1 = Si[pj];
+                a1 = Ai[pj];
+                bad |= s1 != (s0 ^ uq);  // the layout says the partner is there
+                if (s1 < s0) {  // the owner (smaller phase vector) first, as in k_cof_merge
+                    const uint64_t ts = s0; s0 = s1; s1 = ts;
+                    const double2 ta = a0; a0 = a1; a1 = ta;
+                }
+            }
+            uint64_t P0, P1 = 0;
+            int Q0, Q1 = 0;
+            walk(s0, P0, Q0);
+            if (span) walk(s1, P1, Q1);
+#pragma unroll
+            for (int x = 0; x < 2; x++) {
+                int y0, y1 = 0;
+                const int m0 = expo(s0, Q0, x, y0);
+                t[x] = tau[y0] ^ P0;
+                double2 z = ipow_mul(a0, m0 & 3);
+                if (span) {
+                    const int m1 = expo(s1, Q1, x, y1);
+                    bad |= (tau[y1] ^ P1) != t[x];
+                    const double2 z1 = ipow_mul(a1, m1 & 3);
+                    z.x += z1.x;
+                    z.y += z1.y;
+                }
+                cc[x] = make_double2(sc * z.x, sc * z.y);
+                if (amp_kept(cc[x], kb, eps2)) keepm |= 1u << x;
+            }
+        }
+        unsigned long long o = block_out_range(d.ocnt, __popc(keepm), wsum, &bbase);
+        for (int x = 0; x < 2; x++) {
+            if (!((keepm >> x) & 1u)) continue;
+            So[o] = t[x];
+            Ao[o] = cc[x];
+            o++;
+        }
+    }
+    if (bad) set_status(d.status, SF_ST_INTERNAL, in_buf, 28u);
+    if (last_block(d.done) && threadIdx.x == 0) {
+        d.kcnt[out_buf] = *d.ocnt;
+        *d.ocnt = 0;
     }
 }
 
@@ -1842,6 +2039,18 @@ void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t
     SF_DISPATCH(d.W, k_branch_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, tm, eps * eps, in_buf, out_buf));
 }
 
+// the cofactor of a frame whose layout the grid program may have left known
+// (n <= 63, lay: no kernel has moved the elements since): the positional
+// kernel, or, when the device finds no layout, the index-based merge
+void sf_launch_cof_pos(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
+    k_cof_pos<<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf);
+    k_cof_merge<1, false><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf, 1);
+}
+
+void sf_launch_build_index_unless_layout(const SfDev& d, int buf, cudaStream_t s) {
+    k_build_index<1><<<d.nblk, kThreads, 0, s>>>(d, buf, 1);
+}
+
 void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
     // W >= 8: the closed form when U ^ I and V have low rank, else the per-bit
     // walk (each variant returns at once when the other one applies)
@@ -1849,17 +2058,17 @@ void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s
         const int nt = (d.n + 31) & ~31;
         if (d.W == 16) {
             k_cof_lowrank<16><<<1, nt, 0, s>>>(d);
-            k_cof_merge<16, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf);
+            k_cof_merge<16, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf, 0);
         } else {
             k_cof_lowrank<8><<<1, nt, 0, s>>>(d);
-            k_cof_merge<8, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf);
+            k_cof_merge<8, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf, 0);
         }
     }
-    SF_DISPATCH(d.W, k_cof_merge<WW, false><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf));
+    SF_DISPATCH(d.W, k_cof_merge<WW, false><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf, 0));
 }
 
 void sf_launch_build_index(const SfDev& d, int buf, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_build_index<WW><<<d.nblk, kThreads, 0, s>>>(d, buf));
+    SF_DISPATCH(d.W, k_build_index<WW><<<d.nblk, kThreads, 0, s>>>(d, buf, 0));
 }
 
 void sf_launch_compact(const SfDev& d, double eps, int out_buf, cudaStream_t s) {

@@ -101,6 +101,7 @@ struct GpSet {
 // device workspace, zeroed at handle creation; err ... cleared_end is cleared
 // before every launch
 struct GpWork {
+    GpLayout lay;                // the frame's layout after the last launch (read by the positional cofactor)
     unsigned int bar_count, bar_gen;
     unsigned int err[3];         // a failed check in phase p (between barriers p and p + 1): err[p % 3]
     unsigned int drop[3];        // an amplitude dropped in phase p: drop[p % 3]
@@ -913,6 +914,8 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
     int cur = cur0;
     const bool piped = gp_piped();  // the planning CTAs plan ahead (the workers take their steps)
     unsigned long long k = d.kcnt[cur0];
+    const unsigned long long k_init = k;
+    if (blockIdx.x == 0 && threadIdx.x == 0) w->lay.ok = 0;  // written again at a normal end
     uint32_t tag[2] = {d.itag[0], d.itag[1]};
     unsigned long long isz[2] = {d.isize[0], d.isize[1]};
     bool ivalid[2] = {false, false};  // the index of buffer b describes its current contents
@@ -1573,6 +1576,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
     }
     store_tableau();
     if (blockIdx.x == 0) {
+        if (threadIdx.x < 64) w->lay.u[threadIdx.x] = threadIdx.x < npos ? s_pu[threadIdx.x] : 0ull;
         if (threadIdx.x < 64 && hull_state != 0) {
             w->hull[threadIdx.x] = s_hc[threadIdx.x];
             w->hbasis[threadIdx.x] = s_hb[threadIdx.x];
@@ -1586,6 +1590,11 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             }
             if (consumed) *consumed = oi;
             if (trace) w->ntrace = gen - s_gen0;
+            // positions still enumerate the span of the doubling directions
+            bool lay = k_init == 1 && npos < 64 && k == (1ull << npos);
+            for (int i = 0; i < npos && lay; i++) lay = s_pk[i] == (1ull << i);
+            w->lay.n = (unsigned)npos;
+            w->lay.ok = lay ? 1u : 0u;
         }
     }
 }
