@@ -819,19 +819,20 @@ sf_status sf_coalesce(sf_handle h, double drop_eps, uint64_t* out_size) {
 static sf_status cofactor_q(sf_handle h, uint32_t q) {
     SF_LAUNCH(h, SF_K_MEASURE_PREP, sf_launch_measure_prep(h->d, q, h->cur, h->gws, h->stream));
     SF_CK(h, cudaMemcpyAsync(h->hmeta, h->d.meta, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    // the layout the last grid program left, read in the same round trip
+    // (hmeta[3]: its ok word, when no kernel has moved the elements since)
+    const bool lay = h->d.W == 1 && h->layout && h->d.gp;
+    if (lay)
+        SF_CK(h, cudaMemcpyAsync(&h->hmeta[3], &reinterpret_cast<const GpLayout*>(h->d.gp)->ok, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, h->stream));
     sf_status st = sync_check(h);
     if (st) return st;
     if (h->hmeta[2]) {
-        if (h->d.W == 1 && h->layout && h->d.gp) {
-            // partners by position where the grid program left the layout known
-            // (decided on the device; otherwise the index is built and used)
-            const int in = h->cur;
-            if (!h->idx_ok[in])
-                SF_LAUNCH(h, SF_K_INDEX, sf_launch_build_index_unless_layout(h->d, in, h->stream));
-            SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cof_pos(h->d, in, in ^ 1, h->stream));
-            h->idx_ok[in] = false;  // maybe not built
+        if (lay && h->hmeta[3]) {
+            // partners by position: no index read or written
+            SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cof_pos(h->d, h->cur, h->cur ^ 1, h->stream));
             h->cur ^= 1;
-            h->idx_ok[h->cur] = false;  // maybe not written
+            h->idx_ok[h->cur] = false;
         } else {
             st = need_index(h, h->cur);
             if (st) return st;

@@ -1084,10 +1084,8 @@ __global__ void __launch_bounds__(kThreads) k_filter(SfDev d, int x, int in_buf,
 // ---------------------------------------------------------------------------
 // (Re)build the index of buffer b.
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_build_index(SfDev d, int b, int lay) {
+__global__ void __launch_bounds__(kThreads) k_build_index(SfDev d, int b) {
     if (*d.status) return;
-    // a cofactor that finds its partners by position needs no index
-    if (lay && reinterpret_cast<const GpLayout*>(d.gp)->ok) return;
     const unsigned long long k = d.kcnt[b];
     const unsigned long long TI = index_slots(k, d.icap);
     const uint32_t tag = next_tag(d.itag[b]);
@@ -1484,8 +1482,7 @@ __device__ __forceinline__ double2 cof_amp_lr(const CofLR<W>& C, const CofScal& 
 }
 
 template <int W, bool LR>
-__global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, double eps2, int in_buf, int out_buf,
-                                                                    int lay) {
+__global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, double eps2, int in_buf, int out_buf) {
     using Plan = typename std::conditional<LR, CofLR<W>, CofPlan<W>>::type;
     __shared__ Plan CP;
     __shared__ uint64_t uq[W];
@@ -1493,7 +1490,6 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
     __shared__ unsigned long long bbase;
     if (*d.status) return;
     if (!d.meta[2]) return;
-    if (lay && reinterpret_cast<const GpLayout*>(d.gp)->ok) return;  // k_cof_pos runs instead
     if constexpr (W >= 8) {
         // exactly one of the two variants runs
         if ((d.plan[plan_lr_u(d.n, W)] <= SF_LR_MAX) != LR) return;
@@ -1631,8 +1627,7 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
 // kappa_y = sc i^{e_y} (a real scale times an i-power, as the measurement
 // prep builds it), so a child amplitude is sc i^{e_y + ip_y} a: an exact
 // rotation, the partners' two summed, then one real scaling.  Does nothing
-// when the layout is not known (the guarded index build and k_cof_merge run
-// then).
+// when the layout is not known (the host checks that before it launches it).
 __global__ void __launch_bounds__(kThreads) k_cof_pos(SfDev d, double eps2, int in_buf, int out_buf) {
     __shared__ uint64_t sU[64], sV[64];
     __shared__ unsigned int wsum[kThreads / 32];
@@ -2039,16 +2034,10 @@ void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t
     SF_DISPATCH(d.W, k_branch_merge<WW><<<d.nblk, kThreads, 0, s>>>(d, kind, q0, q1, tm, eps * eps, in_buf, out_buf));
 }
 
-// the cofactor of a frame whose layout the grid program may have left known
-// (n <= 63, lay: no kernel has moved the elements since): the positional
-// kernel, or, when the device finds no layout, the index-based merge
+// the cofactor of a frame whose layout the grid program left known (n <= 63;
+// the host has checked that no kernel moved the elements since)
 void sf_launch_cof_pos(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
     k_cof_pos<<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf);
-    k_cof_merge<1, false><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf, 1);
-}
-
-void sf_launch_build_index_unless_layout(const SfDev& d, int buf, cudaStream_t s) {
-    k_build_index<1><<<d.nblk, kThreads, 0, s>>>(d, buf, 1);
 }
 
 void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
@@ -2058,17 +2047,17 @@ void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s
         const int nt = (d.n + 31) & ~31;
         if (d.W == 16) {
             k_cof_lowrank<16><<<1, nt, 0, s>>>(d);
-            k_cof_merge<16, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf, 0);
+            k_cof_merge<16, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf);
         } else {
             k_cof_lowrank<8><<<1, nt, 0, s>>>(d);
-            k_cof_merge<8, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf, 0);
+            k_cof_merge<8, true><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf);
         }
     }
-    SF_DISPATCH(d.W, k_cof_merge<WW, false><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf, 0));
+    SF_DISPATCH(d.W, k_cof_merge<WW, false><<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf));
 }
 
 void sf_launch_build_index(const SfDev& d, int buf, cudaStream_t s) {
-    SF_DISPATCH(d.W, k_build_index<WW><<<d.nblk, kThreads, 0, s>>>(d, buf, 0));
+    SF_DISPATCH(d.W, k_build_index<WW><<<d.nblk, kThreads, 0, s>>>(d, buf));
 }
 
 void sf_launch_compact(const SfDev& d, double eps, int out_buf, cudaStream_t s) {
