@@ -59,7 +59,10 @@ struct GpPlan {
     // applied (set by the planner CTA against a hull that contains the workers'
     // hull, so it never claims too much; 0: not known)
     int orth;
-    int pad_[3];
+    // the end of the run a fresh branch along this record's mask would take
+    // (the records after it with one group or the same mask; planning CTAs)
+    int rend;
+    int pad_[2];
 };
 
 // The tableau of the launch.  CTA 0 writes it back at the end.
@@ -330,6 +333,42 @@ __device__ unsigned long long gp_clifford_run(GpTab& T, const OpRec* ops, unsign
         const int src = (int)(gi - wb);
         const uint32_t kind = __shfl_sync(SF_FULL, wr.kind, src);
         if (gi >= o1 || kind > 8) break;
+        if (kind >= 3 && kind <= 5) {
+            // consecutive Pauli gates multiplied into P = i^e X^a Z^b (each gate
+            // applied after the product so far: X_q flips a_q; Z_q X^a = (-1)^{a_q}
+            // X^a Z_q; Y_q = i X_q Z_q), then applied once
+            uint64_t pa = 0, pb = 0;
+            int pe = 0;
+            for (;;) {
+                if (gi - wb >= 32) {
+                    wb = gi;
+                    wr.kind = 0xffffffffu;
+                    if (wb + lane < o1) wr = ops[wb + lane];
+                }
+                const int sp = (int)(gi - wb);
+                const uint32_t kp = __shfl_sync(SF_FULL, wr.kind, sp);
+                if (gi >= o1 || kp < 3 || kp > 5) break;
+                const int q = (int)__shfl_sync(SF_FULL, wr.q0, sp);
+                const uint64_t m = 1ull << q;
+                const int aq = (int)((pa >> q) & 1);
+                if (kp == 3) {
+                    pa ^= m;
+                } else if (kp == 5) {
+                    pe += 2 * aq;
+                    pb ^= m;
+                } else {
+                    pe += 1 + 2 * aq;
+                    pa ^= m;
+                    pb ^= m;
+                }
+                gi++;
+            }
+            if (!warp_pauli_run(r, n, rx, pa, pb, pe & 3, ga)) {
+                good = false;
+                break;
+            }
+            continue;
+        }
         const int q0 = (int)__shfl_sync(SF_FULL, wr.q0, src);
         const int q1 = kind >= 6 ? (int)__shfl_sync(SF_FULL, wr.q1, src) : 0;
         if (!warp_clifford_gate(r, n, rx, (int)kind, q0, q1, stage, ga, gb, C, cstage)) {
@@ -599,6 +638,8 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
     __shared__ int s_uni;                    // ... valid for the current pass
     __shared__ uint64_t s_ref;               // a phase vector of the frame (new coordinates)
     __shared__ int s_take, s_np, s_kind;     // a planned step taken from the ring: ok, records, kind
+    __shared__ int s_png[kGpPlans], s_pm[kGpPlans];  // plan CTA: groups (-1 bad) and hull size per record
+    __shared__ uint64_t s_pu1[kGpPlans];             // ... and the mask of group 1
     __shared__ uint64_t s_pu[64];            // directions whose partners are found by position ...
     __shared__ unsigned long long s_pk[64];  // ... and their strides
     if (*(volatile uint32_t*)d.status) return;
@@ -791,6 +832,22 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 }
                 __syncthreads();
             }
+            if (tk < 2) {
+                // what the scans below read of each plan, one thread per record
+                for (int r = threadIdx.x; r < np; r += blockDim.x) {
+                    s_png[r] = spl[r].P.bad ? -1 : spl[r].P.ng;
+                    s_pu1[r] = spl[r].P.u[1];
+                }
+                __syncthreads();
+                // the run a fresh branch at record r would take: the records after
+                // it with one group or the same mask
+                for (int r = threadIdx.x; r < np; r += blockDim.x) {
+                    const uint64_t u = s_pu1[r];
+                    int t2 = r + 1;
+                    while (t2 < np && (s_png[t2] == 1 || (s_png[t2] == 2 && s_pu1[t2] == u))) t2++;
+                    spl[r].rend = t2;
+                }
+            }
             if (tk < 2 && warp == 0) {
                 // Per record: are its terms orthogonal to the hull where the workers
                 // apply it?  The hull is followed record by record as the workers
@@ -805,9 +862,8 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 uint64_t pend = 0;
                 bool have_pend = false;
                 for (int r = 0; r < np; r++) {
-                    const BrTab& Q = spl[r].P;
-                    const int ng = Q.ng;
-                    const uint64_t u1 = Q.u[1];
+                    const int ng = s_png[r];
+                    const uint64_t u1 = s_pu1[r];
                     const bool cont = have_pend && (ng == 1 || (ng == 2 && u1 == pend));
                     if (!cont && have_pend) {
                         if (hull_fresh(s_hc, pend)) {
@@ -817,7 +873,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                         }
                         have_pend = false;
                     }
-                    if (lane == 0) spl[r].orth = s_nhb;  // directions the record is checked against
+                    if (lane == 0) s_pm[r] = s_nhb;  // directions the record is checked against
                     __syncwarp();
                     if (cont) continue;
                     if (ng == 2 && hull_fresh(s_hc, u1)) {
@@ -825,7 +881,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                         have_pend = true;
                     } else {
                         for (int g = 1; g < ng; g++) {
-                            const uint64_t ug = Q.u[g];
+                            const uint64_t ug = spl[r].P.u[g];
                             if (hull_fresh(s_hc, ug)) {
                                 hull_add(s_hc, ug);
                                 if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = ug;
@@ -841,14 +897,29 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 __syncwarp();
                 for (int r = lane; r < np; r += 32) {
                     const BrTab& Q = spl[r].P;
-                    const int m = spl[r].orth;
-                    bool odd = false;
-                    for (int i = 0; i < m && !odd; i++) {
-                        const uint64_t h = s_hb[i];
-                        for (int g = 0; g < Q.ng; g++)
-                            for (int t = 0; t < Q.nt[g]; t++) odd |= (__popcll(Q.v[g][t] & h) & 1) != 0;
+                    const int ng = Q.ng, m = s_pm[r];
+                    int nt[4];
+                    uint64_t v[4][4];
+#pragma unroll
+                    for (int g = 0; g < 4; g++) {
+                        nt[g] = g < ng ? Q.nt[g] : 0;
+#pragma unroll
+                        for (int t = 0; t < 4; t++) v[g][t] = Q.v[g][t];
                     }
-                    spl[r].orth = !odd;
+#pragma unroll
+                    for (int g = 0; g < 4; g++)
+#pragma unroll
+                        for (int t = 0; t < 4; t++)
+                            if (t >= nt[g]) v[g][t] = 0ull;
+                    uint64_t acc = 0;  // OR over the hull directions of each term's parity, one bit per term
+                    for (int i = 0; i < m; i++) {
+                        const uint64_t h = s_hb[i];
+#pragma unroll
+                        for (int g = 0; g < 4; g++)
+#pragma unroll
+                            for (int t = 0; t < 4; t++) acc |= (uint64_t)(__popcll(v[g][t] & h) & 1) << (4 * g + t);
+                    }
+                    spl[r].orth = acc == 0;
                 }
             }            __syncthreads();
             {
@@ -1252,9 +1323,13 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             if (ng == 2 && hull_fresh(s_hc, P0.u[1])) {
                 const uint64_t u = P0.u[1];
                 int t2 = t + 1;
-                while (t2 < nb && !spl[t2].P.bad &&
-                       (spl[t2].P.ng == 1 || (spl[t2].P.ng == 2 && spl[t2].P.u[1] == u)))
-                    t2++;
+                if (piped) {
+                    t2 = spl[t].rend;  // the plan CTA found it
+                } else {
+                    while (t2 < nb && !spl[t2].P.bad &&
+                           (spl[t2].P.ng == 1 || (spl[t2].P.ng == 2 && spl[t2].P.u[1] == u)))
+                        t2++;
+                }
                 if (2 * k > d.cap) {
                     if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_CAPACITY, cur, 0u);
                     if (aff) affine_pass();

@@ -435,6 +435,31 @@ __device__ __forceinline__ int warp_measure_prep(Row* r, int n, int rx, int q, C
     return rx2;
 }
 
+// A run of Pauli gates as one Pauli P = i^e X^a Z^b (ROTATE, Sec. III): the
+// rows that anticommute with P change sign (M's to t0, composed, and t1; D's
+// to de), M keeps its bits and stays in RREF, and the phase rule takes one
+// point: <a|P phi_0> = i^e <0|phi_0> (0 lies in the support of phi_0), over
+// <a|D^{t1} phi_0>.  The product of the gates' own factors is the same number.
+__device__ __forceinline__ bool warp_pauli_run(Row* r, int n, int rx, uint64_t a, uint64_t b, int e, int& ga) {
+    const int lane = threadIdx.x & 31;
+    for (int hf = 0; hf < 2; hf++) {
+        const int row = lane + 32 * hf;
+        if (row < n) {
+            const uint32_t f = (uint32_t)((__popcll(r[hf].mx & b) + __popcll(r[hf].mz & a)) & 1);
+            r[hf].t0 ^= f;
+            r[hf].t1 = f;
+            const uint32_t fd = (uint32_t)((__popcll(r[hf].dx & b) + __popcll(r[hf].dz & a)) & 1);
+            r[hf].de = (r[hf].de + 2u * fd) & 3u;
+        } else {
+            r[hf].t1 = 0;
+        }
+    }
+    const int dq = warp_amp_phi(r, n, rx, true, a);
+    if (dq < 0) return false;
+    ga = (ga + 2 * e + 2 * ((4 - dq) & 3)) & 7;
+    return true;
+}
+
 // One Clifford gate on the rows in registers (ROTATE, Sec. III, Table 2):
 // conjugate M and D (sign flips of M to t0, composed, and t1, this gate),
 // restore Invariant 1, and multiply the run's phase factor omega^ga sqrt(2)^gb
