@@ -521,6 +521,19 @@ def campaign_leg(sfm, torch, n_variants: int, plain_sample: int = 16):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     status = out["status"].cpu().numpy()
+    # both coalescing strategies in the chosen shape (the autotuner searched them all)
+    sorted_chosen = eng.coalesce_sorted()
+    strat_ms = {}
+    for srt in (False, True):
+        eng.set_coalesce(srt)
+        eng.launch(ops, off, nc, DROP_EPS, out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        eng.launch(ops, off, nc, DROP_EPS, out)
+        e1.record()
+        torch.cuda.synchronize()
+        strat_ms["sort" if srt else "hash"] = e0.elapsed_time(e1)
+    eng.set_coalesce(sorted_chosen)
     # end to end: program from pinned host memory, results back to the host
     h_ops = torch.from_numpy(recs.view(np.uint8).copy()).pin_memory()
     h_off = torch.from_numpy(offs.view(np.int64).copy()).pin_memory()
@@ -552,7 +565,8 @@ def campaign_leg(sfm, torch, n_variants: int, plain_sample: int = 16):
             "e2e_circuits_per_s": nc / (statistics.median(e2e) * 1e-3),
             "e2e_h2d_bytes": int(recs.nbytes + offs.nbytes),
             "shape": {"threads_per_circuit": threads, "index_in_shared_memory": smem_index, "ctas": ctas,
-                      "chosen_by": "sf_campaign_autotune"},
+                      "coalescing": "sort" if sorted_chosen else "hash", "chosen_by": "sf_campaign_autotune",
+                      "ms_by_coalescing_in_this_shape": strat_ms},
             "plain_circuits_per_s": plain_sample / plain_s,
             "plain_sample": f"first {plain_sample} variants, one at a time through sf_create/sf_apply_*/sf_measure",
             "speedup_vs_plain": (nc / (med * 1e-3)) / (plain_sample / plain_s),

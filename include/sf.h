@@ -486,9 +486,20 @@ uint32_t sf_campaign_ctas(sf_campaign c);
 sf_status sf_campaign_set_shape(sf_campaign c, uint32_t threads_per_circuit, uint32_t smem_index);
 sf_status sf_campaign_get_shape(sf_campaign c, uint32_t* threads_per_circuit, uint32_t* smem_index, uint32_t* ctas);
 
+/* Coalescing strategy of the merges (Def. 1: a branch or cofactor output
+ * meets the element with the same phase vector): sorted_index = 0 finds it
+ * through a hash index of the frame's phase vectors (built with one
+ * compare-and-swap per element), 1 through the frame's positions sorted by
+ * phase vector (a CTA radix sort over the n phase-vector bits, then binary
+ * searches).  Both find the same partners, so the results are bit for bit the
+ * same; only the time differs.  The default is the hash index. */
+sf_status sf_campaign_set_coalesce(sf_campaign c, uint32_t sorted_index);
+uint32_t sf_campaign_get_coalesce(sf_campaign c);
+
 /* Autotuner: runs the given program (device pointers as for sf_campaign_run)
- * once untimed and `reps` (1..16) times timed in every shape, keeps the
- * fastest, and writes its mean time per run to *best_ms (nullable).  Uses
+ * once untimed and `reps` (1..16) times timed in every shape (threads per
+ * circuit and index location) with each coalescing strategy, keeps the
+ * fastest pair, and writes its mean time per run to *best_ms (nullable).  Uses
  * temporary device buffers for the outputs.  Synchronises. */
 sf_status sf_campaign_autotune(sf_campaign c, const sf_op* dev_ops, const uint64_t* dev_offsets,
                                uint32_t n_circuits, double drop_eps, uint32_t reps, float* best_ms);

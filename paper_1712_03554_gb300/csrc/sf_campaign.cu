@@ -47,6 +47,7 @@ struct CampDev {
     uint64_t* ex_sig;  // [ncirc][cap] or null
     double2* ex_amp;   // [ncirc][cap]
     uint64_t* ex_tab;  // [ncirc][129]: x rows, z rows, r
+    int sorted;        // coalescing strategy: 0 hash index, 1 positions sorted by phase vector
 };
 
 struct Shared {
@@ -125,6 +126,80 @@ __device__ void build_index(uint32_t* idx, const uint64_t* sig, unsigned k) {
         }
     }
     __syncthreads();
+}
+
+// The sorted alternative (the campaign's coalescing strategy "sort"): idx[0..k)
+// holds the positions of the frame ordered by phase vector, found by a stable
+// LSD radix sort over the n phase-vector bits, 4 bits per pass, through
+// idx[k..2k) (the slot array holds at least 2k entries); lookups are binary
+// searches.  Within each pass, tiles of blockDim elements keep their order: a
+// warp ranks its equal digits with a match, warps before it add their counts.
+__device__ void build_sorted(uint32_t* idx, const uint64_t* sig, unsigned k, int nbits) {
+    __shared__ unsigned cnt[kMaxWarps][16];
+    __shared__ unsigned base[16];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+    uint32_t* src = idx;
+    uint32_t* dst = idx + k;
+    for (unsigned j = tid; j < k; j += blockDim.x) src[j] = j;
+    for (int shift = 0; shift < nbits; shift += 4) {
+        if (tid < 16) {
+            base[tid] = 0;
+            for (int w = 0; w < nw; w++) cnt[w][tid] = 0;
+        }
+        __syncthreads();
+        for (unsigned j = tid; j < k; j += blockDim.x) atomicAdd(&base[(sig[src[j]] >> shift) & 15], 1u);
+        __syncthreads();
+        if (tid == 0) {
+            unsigned acc = 0;
+            for (int d = 0; d < 16; d++) {
+                const unsigned c = base[d];
+                base[d] = acc;
+                acc += c;
+            }
+        }
+        __syncthreads();
+        for (unsigned tile = 0; tile < k; tile += blockDim.x) {
+            const unsigned j = tile + tid;
+            const bool act = j < k;
+            const uint32_t pos = act ? src[j] : 0u;
+            const unsigned d = act ? (unsigned)((sig[pos] >> shift) & 15) : 16u;
+            const unsigned peers = __match_any_sync(SF_FULL, d);
+            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+            if (act && lane == __ffs(peers) - 1) cnt[warp][d] = __popc(peers);
+            __syncthreads();
+            if (act) {
+                unsigned off = base[d] + rank;
+                for (int w = 0; w < warp; w++) off += cnt[w][d];
+                dst[off] = pos;
+            }
+            __syncthreads();
+            if (tid < 16) {
+                unsigned add = 0;
+                for (int w = 0; w < nw; w++) {
+                    add += cnt[w][tid];
+                    cnt[w][tid] = 0;
+                }
+                base[tid] += add;
+            }
+            __syncthreads();
+        }
+        uint32_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != idx)
+        for (unsigned j = tid; j < k; j += blockDim.x) idx[j] = src[j];
+    __syncthreads();
+}
+
+__device__ __forceinline__ int find_sorted(const uint32_t* idx, const uint64_t* sig, unsigned k, uint64_t key) {
+    unsigned lo = 0, hi = k;
+    while (lo < hi) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (sig[idx[mid]] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < k && sig[idx[lo]] == key) ? (int)idx[lo] : -1;
 }
 
 __device__ __forceinline__ int find_index(const uint32_t* idx, const uint64_t* sig, unsigned k, uint64_t key) {
@@ -245,9 +320,17 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                                                       double2* const* ampb, uint32_t* idx, const OpRec* ops,
                                                       unsigned long long o0, unsigned long long o1, unsigned cap,
                                                       double eps2, unsigned stop_cap, BrTab* pb,
-                                                      double2 (*cb)[4][16], int nbm) {
+                                                      double2 (*cb)[4][16], int nbm, bool sorted = false) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long oi = o0;
+    // the frame's index: hash slots, or positions sorted by phase vector
+    const auto rebuild = [&](const uint64_t* sg, unsigned kk) {
+        if (sorted) build_sorted(idx, sg, kk, n);
+        else build_index(idx, sg, kk);
+    };
+    const auto lookup = [&](const uint64_t* sg, unsigned kk, uint64_t key) {
+        return sorted ? find_sorted(idx, sg, kk, key) : find_index(idx, sg, kk, key);
+    };
     unsigned long long pbase = 0, pend = 0;  // records planned in the current batch (the same in every thread)
     bool have_u = false;  // the frame is closed under the mask cu (s in F => s ^ cu in F)
     uint64_t cu = 0;
@@ -345,7 +428,7 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                 sg[j] = o;
             }
             __syncthreads();
-            build_index(idx, sg, S.k);
+            rebuild(sg, S.k);
             have_u = false;
             oi = S.oe;
             continue;
@@ -458,7 +541,7 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                 double2* ai = ampb[S.cur];
                 bool drop = false, miss = false;
                 const auto plan = [&](int r2) { return PlanRef{&pb[r2], cb[r2]}; };
-                const auto find = [&](uint64_t key) { return (long long)find_index(idx, si, k, key); };
+                const auto find = [&](uint64_t key) { return (long long)lookup(si, k, key); };
                 for (unsigned base = 64u * warp; base < k; base += 64u * (blockDim.x >> 5))
                     inplace_run_warp<false>(si, ai, base, k, pairs, cu, t, t2, plan, find, kb, eps2, drop, miss);
                 if (__syncthreads_or(miss)) {  // the frame was not closed after all
@@ -488,7 +571,7 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                     S.cur = ob;
                 }
                 __syncthreads();
-                build_index(idx, sigb[S.cur], S.k);
+                rebuild(sigb[S.cur], S.k);
                 have_u = false;
                 continue;
             }
@@ -517,7 +600,7 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                 if (act) {
                     s = si[j];
                     a = ai[j];
-                    for (int g = 1; g < ng; g++) id[g] = find_index(idx, si, k, s ^ P.u[g]);
+                    for (int g = 1; g < ng; g++) id[g] = lookup(si, k, s ^ P.u[g]);
                 }
                 double2 amps[4];
                 unsigned keepm = 0;
@@ -555,7 +638,7 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                 S.cur = ob;
             }
             __syncthreads();
-            build_index(idx, sigb[S.cur], S.k);
+            rebuild(sigb[S.cur], S.k);
             oi++;
             continue;
         }
@@ -604,7 +687,7 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                         s = si[j];
                         a = ai[j];
                         p = s ^ S.C.uq;
-                        l = find_index(idx, si, k, p);
+                        l = lookup(si, k, p);
                         own = l < 0 || s < p;
                         if (l >= 0) ap = ai[l];
                     }
@@ -681,7 +764,7 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                 }
                 __syncthreads();
             }
-            build_index(idx, sigb[S.cur], S.k);
+            rebuild(sigb[S.cur], S.k);
             have_u = false;
             oi++;
             continue;
@@ -736,8 +819,10 @@ __global__ void __launch_bounds__(CT) k_campaign(CampDev D) {
             ampb[0][0] = make_double2(1.0, 0.0);
         }
         __syncthreads();
-        build_index(idx, sigb[0], 1);
-        run_ops(S, r, n, sigb, ampb, idx, D.ops, D.off[ci], D.off[ci + 1], D.cap, D.eps2, 0u, &S.P, &S.ctab, 1);
+        if (D.sorted) build_sorted(idx, sigb[0], 1, n);
+        else build_index(idx, sigb[0], 1);
+        run_ops(S, r, n, sigb, ampb, idx, D.ops, D.off[ci], D.off[ci + 1], D.cap, D.eps2, 0u, &S.P, &S.ctab, 1,
+                D.sorted != 0);
         __syncthreads();
         // results
         double nr = 0.0;
@@ -956,6 +1041,7 @@ struct sf_campaign_s {
     unsigned cap = 0;
     cudaStream_t stream = nullptr;
     int shape = 0;
+    int sorted = 0;  // coalescing strategy (CampDev::sorted)
     int nblk_of[kShapes] = {};
     size_t smem_of[kShapes] = {};
     int max_nblk = 0;
@@ -992,6 +1078,7 @@ sf_status launch_campaign(sf_campaign c, int shape, const sf_op* dev_ops, const 
     D.ex_sig = ex_sig;
     D.ex_amp = reinterpret_cast<double2*>(ex_amp);
     D.ex_tab = ex_tab;
+    D.sorted = c->sorted;
     if (cudaMemsetAsync(c->next, 0, sizeof(unsigned), c->stream) != cudaSuccess) return SF_ECUDA;
     const int threads = 32 << (shape >> 1);
     kKernels[shape]<<<c->nblk_of[shape], threads, c->smem_of[shape], c->stream>>>(D);
@@ -1090,6 +1177,14 @@ sf_status sf_campaign_set_shape(sf_campaign c, uint32_t threads_per_circuit, uin
     return SF_OK;
 }
 
+sf_status sf_campaign_set_coalesce(sf_campaign c, uint32_t sorted_index) {
+    if (!c || sorted_index > 1) return SF_EINVAL;
+    c->sorted = (int)sorted_index;
+    return SF_OK;
+}
+
+uint32_t sf_campaign_get_coalesce(sf_campaign c) { return c ? (uint32_t)c->sorted : 0u; }
+
 sf_status sf_campaign_get_shape(sf_campaign c, uint32_t* threads_per_circuit, uint32_t* smem_index,
                                 uint32_t* ctas) {
     if (!c) return SF_EINVAL;
@@ -1117,10 +1212,13 @@ sf_status sf_campaign_autotune(sf_campaign c, const sf_op* dev_ops, const uint64
         cudaEventCreate(&e1) != cudaSuccess) {
         res = SF_ENOMEM;
     }
-    int best = -1;
+    int best = -1, best_sorted = 0;
     float best_t = 0.f;
-    for (int i = 0; i < kShapes && res == SF_OK; i++) {
+    const int sorted0 = c->sorted;
+    for (int cfg = 0; cfg < 2 * kShapes && res == SF_OK; cfg++) {
+        const int i = cfg >> 1;
         if (c->nblk_of[i] == 0) continue;
+        c->sorted = cfg & 1;
         // one untimed launch, then the mean of reps timed launches
         res = launch_campaign(c, i, dev_ops, dev_offsets, n_circuits, drop_eps, outc, nm, kf, nr, st, nullptr,
                               nullptr, nullptr);
@@ -1138,11 +1236,14 @@ sf_status sf_campaign_autotune(sf_campaign c, const sf_op* dev_ops, const uint64
         ms /= (float)reps;
         if (best < 0 || ms < best_t) {
             best = i;
+            best_sorted = c->sorted;
             best_t = ms;
         }
     }
+    c->sorted = sorted0;
     if (res == SF_OK && best >= 0) {
         c->shape = best;
+        c->sorted = best_sorted;
         if (best_ms) *best_ms = best_t;
     }
     if (outc) cudaFree(outc);

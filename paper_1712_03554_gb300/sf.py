@@ -114,6 +114,8 @@ def load(build: bool = True) -> C.CDLL:
         "sf_server_destroy": ([H], st),
         "sf_campaign_set_shape": ([H, u32, u32], st),
         "sf_campaign_get_shape": ([H, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)], st),
+        "sf_campaign_set_coalesce": ([H, u32], st),
+        "sf_campaign_get_coalesce": ([H], u32),
         "sf_campaign_autotune": ([H, C.c_void_p, C.c_void_p, u32, dbl, u32, C.POINTER(C.c_float)], st),
         "sf_mf_create": ([u32, u64, u32, C.c_void_p, C.POINTER(C.c_void_p)], st),
         "sf_mf_destroy": ([H], st),
@@ -217,6 +219,16 @@ class Campaign:
         t, sm, n = C.c_uint32(), C.c_uint32(), C.c_uint32()
         self.lib.sf_campaign_get_shape(self.h, C.byref(t), C.byref(sm), C.byref(n))
         return int(t.value), bool(sm.value), int(n.value)
+
+    def set_coalesce(self, sorted_index: bool) -> None:
+        """sf_campaign_set_coalesce: merges find partners through a hash index
+        (False) or the positions sorted by phase vector (True)."""
+        code = self.lib.sf_campaign_set_coalesce(self.h, 1 if sorted_index else 0)
+        if code != SF_OK:
+            raise SFError(code, "sf_campaign_set_coalesce failed")
+
+    def coalesce_sorted(self) -> bool:
+        return bool(self.lib.sf_campaign_get_coalesce(self.h))
 
     def autotune(self, ops, off, nc: int, drop_eps: float = 1e-12, reps: int = 2) -> float:
         """sf_campaign_autotune on an uploaded program; returns the best ms per run."""

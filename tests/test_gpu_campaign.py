@@ -233,3 +233,54 @@ def test_stage_circuits_vs_oracle(sfm, threads):
     for i, ops in enumerate(circuits):
         check_against_oracle(res, i, n, ops)
     eng.close()
+
+
+@pytest.mark.parametrize("threads", [32, 128, 256])
+def test_sorted_coalescing_vs_oracle_and_hash(sfm, threads):
+    """The sorted coalescing strategy (positions ordered by phase vector, binary
+    searches) against the oracle on Steane variants, random Clifford+T circuits,
+    the QFT and the stage circuits (frames up to thousands of elements), and bit
+    for bit against the hash strategy in the same shape: both find the same
+    partners."""
+    n = 12
+    circuits = ([c.stage_circuit(n, 5100 + s, stages=9, per_stage=20) for s in range(3)] +
+                [c.qft_random_input(n, seed=3)[1]] + [c.random_clifford_t(n, 400, 8, seed=21 + i) for i in range(6)])
+    eng = sfm.Campaign(n, sfm.CAMPAIGN_MAX_ELEMS)
+    eng.set_shape(threads, 0)
+    eng.set_coalesce(False)
+    ref = eng.run(circuits, export=True)
+    eng.set_coalesce(True)
+    assert eng.coalesce_sorted()
+    res = eng.run(circuits, export=True)
+    for i, ops in enumerate(circuits):
+        check_against_oracle(res, i, n, ops)
+    for key in ("outcomes", "n_meas", "k_final", "status"):
+        assert np.array_equal(res[key], ref[key]), key
+    assert np.array_equal(res["norm"], ref["norm"])
+    for fa, fb in zip(res["frames"], ref["frames"]):
+        for a, b in zip(fa, fb):
+            assert np.array_equal(np.asarray(a), np.asarray(b))
+    eng.close()
+    steane = c.steane_campaign(48, seed=6)
+    eng = sfm.Campaign(c.STEANE_N, 4096)
+    eng.set_coalesce(True)
+    res = eng.run(steane, export=True)
+    for i, ops in enumerate(steane):
+        check_against_oracle(res, i, c.STEANE_N, ops)
+    eng.close()
+
+
+def test_autotuner_searches_both_strategies(sfm):
+    """The autotuner times every shape with each strategy and keeps one; the
+    kept configuration reproduces the results."""
+    circuits = c.steane_campaign(96, seed=8)
+    eng = sfm.Campaign(c.STEANE_N, 4096)
+    ref = eng.run(circuits)
+    ops, off, nc = eng.upload(circuits)
+    ms = eng.autotune(ops, off, nc, reps=1)
+    assert ms > 0
+    assert eng.coalesce_sorted() in (False, True)
+    res = eng.run(circuits)
+    assert np.array_equal(res["outcomes"], ref["outcomes"])
+    assert np.array_equal(res["k_final"], ref["k_final"])
+    eng.close()
