@@ -394,7 +394,7 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
     unsigned long long icap = 64;
     while (icap < 2 * cap) icap <<= 1;
     d.icap = icap;
-    for (int b = 0; b < 2; b++) SF_ALLOC(d.islot[b], (W + 1) * icap);
+    for (int b = 0; b < 2; b++) SF_ALLOC(d.islot[b], (size_t)slot_words((int)W) * icap);
     SF_ALLOC(d.itag, 2);
     SF_ALLOC(d.isize, 2);
     SF_ALLOC(d.done, 1);
@@ -421,7 +421,8 @@ sf_status sf_create(uint32_t n_qubits, uint64_t max_elems, void* cuda_stream, sf
         return fail(nullptr, SF_ENOMEM, "pinned host allocation failed");
     }
     cudaMemsetAsync(d.status, 0, sizeof(uint32_t), h->stream);
-    for (int b = 0; b < 2; b++) cudaMemsetAsync(d.islot[b], 0, (W + 1) * icap * sizeof(uint64_t), h->stream);
+    for (int b = 0; b < 2; b++)
+        cudaMemsetAsync(d.islot[b], 0, (size_t)slot_words((int)W) * icap * sizeof(uint64_t), h->stream);
     cudaMemsetAsync(d.itag, 0, 2 * sizeof(uint32_t), h->stream);
     cudaMemsetAsync(d.isize, 0, 2 * sizeof(unsigned long long), h->stream);
     cudaMemsetAsync(d.done, 0, sizeof(unsigned int), h->stream);
@@ -1057,7 +1058,7 @@ uint64_t sf_footprint_bytes(uint32_t n_qubits, uint64_t max_elems) {
                  + 2 * (8 * W + 16) * cap               // two frame buffers
                  + 8 * plan_words((int)n, (int)W)       // plan
                  + (W > 1 ? 4 * slots : 0) + (8 * W + 16) * slots  // slot table
-                 + 2 * 8 * (W + 1) * icap               // phase-vector indexes
+                 + 2 * 8 * (uint64_t)slot_words((int)W) * icap  // phase-vector indexes
                  + 32 * (uint64_t)std::max(1, sms) * 4 + 8 * W + 16 * 256 + 4096;
     const size_t wsb = sf_tableau_smem_bytes((int)n, (int)W, (int)NT);
     if (wsb > 200 * 1024) b += (wsb + 7) / 8 * 8;

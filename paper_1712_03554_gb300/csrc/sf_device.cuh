@@ -66,8 +66,9 @@ struct SfDev {
     // index of each frame buffer: phase vector -> position.  Slots carry the
     // generation tag of the index that wrote them, so an index is replaced by
     // bumping the tag, never by clearing the table.
-    // slot s of buffer b's index is the W + 1 words islot[b][s * (W + 1) ..]:
-    // word 0 = tag << 32 | position, words 1..W = phase vector
+    // slot s of buffer b's index is the slot_words(W) words islot[b][s * slot_words(W) ..]:
+    // word 0 = tag << 32 | position, then the phase vector (word 1 for W = 1,
+    // words 2 .. W + 1 otherwise, 16-byte aligned for 128-bit accesses)
     uint64_t* islot[2];
     unsigned long long icap;   // power of two >= 2 cap
     uint32_t* itag;            // [2] tag of the valid index of each buffer (0 = none)
@@ -104,6 +105,10 @@ struct OpRec {
 // path nearly always changes every phase vector (a Clifford batch) before the
 // next merge, so the index is built only when a merge needs it.
 __host__ __device__ constexpr bool sf_emit_index(int W) { return W < 8; }
+
+// words per index slot and where its key starts (see SfDev::islot)
+__host__ __device__ constexpr int slot_words(int W) { return W == 1 ? 2 : W + 2; }
+__host__ __device__ constexpr int slot_key(int W) { return W == 1 ? 1 : 2; }
 
 // An empty one-word slot key: with W = 1 (n <= 63) phase vectors never set
 // bit 63.  Wider keys mark their slots through a separate state word.
@@ -395,13 +400,18 @@ __device__ __forceinline__ bool index_insert(const SfDev& d, int b, unsigned lon
     const unsigned long long mine = ((unsigned long long)tag << 32) | pos;
     unsigned long long slot = hash_sig<W>(key) & (T - 1);
     for (unsigned long long probe = 0; probe < T; probe++) {
-        unsigned long long* tv = sl + slot * (W + 1);
+        unsigned long long* tv = sl + slot * slot_words(W);
         unsigned long long cur = *(volatile unsigned long long*)tv;
         while ((uint32_t)(cur >> 32) != tag) {
             const unsigned long long old = atomicCAS(tv, cur, mine);
             if (old == cur) {
+                if constexpr (W == 1) {
+                    tv[1] = key[0];
+                } else {
+                    ulonglong2* kv = reinterpret_cast<ulonglong2*>(tv + slot_key(W));
 #pragma unroll
-                for (int w = 0; w < W; w++) tv[1 + w] = key[w];
+                    for (int w = 0; w < W / 2; w++) kv[w] = make_ulonglong2(key[2 * w], key[2 * w + 1]);
+                }
                 return true;
             }
             cur = old;
@@ -434,12 +444,16 @@ __device__ __forceinline__ long long index_find(const SfDev& d, int b, unsigned 
         return -1;
     }
     for (unsigned long long probe = 0; probe < T; probe++) {
-        const uint64_t* p = sl + slot * (W + 1);
-        const uint64_t tv = __ldg(p), k0 = __ldg(p + 1);
+        const uint64_t* p = sl + slot * slot_words(W);
+        const uint64_t tv = __ldg(p);
         if ((uint32_t)(tv >> 32) != tag) return -1;
-        bool eq = k0 == key[0];
+        const ulonglong2* kv = reinterpret_cast<const ulonglong2*>(p + slot_key(W));
+        bool eq = true;
 #pragma unroll
-        for (int w = 1; w < W; w++) eq &= (__ldg(p + 1 + w) == key[w]);
+        for (int w = 0; w < W / 2; w++) {
+            const ulonglong2 v = __ldg(kv + w);
+            eq &= v.x == key[2 * w] && v.y == key[2 * w + 1];
+        }
         if (eq) return (long long)(uint32_t)tv;
         slot = (slot + 1) & (T - 1);
     }

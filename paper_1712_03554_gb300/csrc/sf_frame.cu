@@ -732,6 +732,15 @@ __global__ void __launch_bounds__(kThreads) k_branch(SfDev d, uint32_t kind, uin
 // readers of a slot being written wait for it with a bounded spin.  Keys are
 // slot-major (the W words of a slot contiguous): a random insert or compare
 // touches one W * 8-byte run instead of W separate sectors.
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
 template <int W>
 __device__ __forceinline__ bool table_insert(const SfDev& d, unsigned long long T, const uint64_t* key, double2 c) {
     unsigned long long slot = hash_sig<W>(key) & (T - 1);
@@ -746,25 +755,29 @@ __device__ __forceinline__ bool table_insert(const SfDev& d, unsigned long long 
                 return true;
             }
         } else {
-            uint32_t st = *(volatile uint32_t*)&d.tstate[slot];
+            // the key is published by a release store of the state word and read
+            // after an acquire load of it; keys are W / 2 16-byte words
+            ulonglong2* kv = reinterpret_cast<ulonglong2*>(d.tkey + slot * W);
+            uint32_t st = ld_acquire_u32(&d.tstate[slot]);
             if (st == 0) {
                 st = atomicCAS(&d.tstate[slot], 0u, 1u);
                 if (st == 0) {
 #pragma unroll
-                    for (int w = 0; w < W; w++) d.tkey[slot * W + w] = key[w];
-                    __threadfence();
-                    atomicExch(&d.tstate[slot], 2u);
+                    for (int w = 0; w < W / 2; w++) kv[w] = make_ulonglong2(key[2 * w], key[2 * w + 1]);
+                    st_release_u32(&d.tstate[slot], 2u);
                     atomicAdd(&d.tacc[slot].x, c.x);
                     atomicAdd(&d.tacc[slot].y, c.y);
                     return true;
                 }
             }
-            for (int spin = 0; st == 1u && spin < (1 << 22); spin++) st = *(volatile uint32_t*)&d.tstate[slot];
+            for (int spin = 0; st == 1u && spin < (1 << 22); spin++) st = ld_acquire_u32(&d.tstate[slot]);
             if (st != 2u) return false;
-            __threadfence();
             bool eq = true;
 #pragma unroll
-            for (int w = 0; w < W; w++) eq &= (*(volatile uint64_t*)&d.tkey[slot * W + w] == key[w]);
+            for (int w = 0; w < W / 2; w++) {
+                const ulonglong2 v = __ldcg(kv + w);
+                eq &= v.x == key[2 * w] && v.y == key[2 * w + 1];
+            }
             if (eq) {
                 atomicAdd(&d.tacc[slot].x, c.x);
                 atomicAdd(&d.tacc[slot].y, c.y);
@@ -889,8 +902,13 @@ __global__ void __launch_bounds__(kThreads) k_compact(SfDev d, int out_buf, doub
             if (occ) {
                 a = d.tacc[i];
                 if constexpr (W > 1) {
+                    const ulonglong2* kv = reinterpret_cast<const ulonglong2*>(d.tkey + i * W);
 #pragma unroll
-                    for (int w = 0; w < W; w++) key[w] = d.tkey[i * W + w];
+                    for (int w = 0; w < W / 2; w++) {
+                        const ulonglong2 v = kv[w];
+                        key[2 * w] = v.x;
+                        key[2 * w + 1] = v.y;
+                    }
                     d.tstate[i] = 0u;
                 } else {
                     d.tkey[i] = SF_EMPTY_KEY;

@@ -213,7 +213,11 @@ def streaming_roofline(n=1000, m=20, reps=3, seed=7, peak_gbs=None):
     fresh = iter(pick[m + 2:])  # a random qubit for every measurement
 
     def timed_cls(classes, op, reps=reps):
-        tot = {cl: [0.0, 0] for cl in classes}
+        # one untimed pass first (first-use costs of the driver stay out), then
+        # the median over the timed passes of the time per launch
+        op()
+        assert f.size() == k
+        per = {cl: [] for cl in classes}
         for _ in range(reps):
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -228,9 +232,13 @@ def streaming_roofline(n=1000, m=20, reps=3, seed=7, peak_gbs=None):
                 f.time_kernel(-1)
                 kk = f.size()  # synchronises and reports a deferred device error here
                 assert kk == k, (cl, kk, k)
-                tot[cl][0] += ms
-                tot[cl][1] += cnt
-        return {cl: (v[0] / max(1, v[1]), v[1]) for cl, v in tot.items()}
+                if cnt:
+                    per[cl].append((ms / cnt, cnt))
+        out = {}
+        for cl, v in per.items():
+            v = sorted(v)
+            out[cl] = v[len(v) // 2] if v else (0.0, 0)
+        return out
 
     rows = {}
 
