@@ -460,6 +460,47 @@ __device__ __forceinline__ long long index_find(const SfDev& d, int b, unsigned 
     return -1;
 }
 
+// index_find of the key s ^ m, formed word by word (m in shared memory, read
+// at each use): no W-word copy of the key is kept in registers
+template <int W>
+__device__ __forceinline__ long long index_find_xor(const SfDev& d, int b, unsigned long long T, uint32_t tag,
+                                                    const uint64_t* s, const uint64_t* m) {
+    if constexpr (W == 1) {
+        const uint64_t key = s[0] ^ m[0];
+        return index_find<1>(d, b, T, tag, &key);
+    } else {
+        uint64_t h = 0x9E3779B97F4A7C15ull;  // hash_sig over the words of s ^ m
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            uint64_t v = (s[w] ^ *(const volatile uint64_t*)&m[w]) + h;
+            v ^= v >> 30;
+            v *= 0xBF58476D1CE4E5B9ull;
+            v ^= v >> 27;
+            v *= 0x94D049BB133111EBull;
+            v ^= v >> 31;
+            h = v + 0x9E3779B97F4A7C15ull * (uint64_t)(w + 1);
+        }
+        const uint64_t* sl = d.islot[b];
+        unsigned long long slot = h & (T - 1);
+        for (unsigned long long probe = 0; probe < T; probe++) {
+            const uint64_t* p = sl + slot * slot_words(W);
+            const uint64_t tv = __ldg(p);
+            if ((uint32_t)(tv >> 32) != tag) return -1;
+            const ulonglong2* kv = reinterpret_cast<const ulonglong2*>(p + slot_key(W));
+            bool eq = true;
+#pragma unroll
+            for (int w = 0; w < W / 2; w++) {
+                const ulonglong2 v = __ldg(kv + w);
+                eq &= v.x == (s[2 * w] ^ *(const volatile uint64_t*)&m[2 * w]) &&
+                      v.y == (s[2 * w + 1] ^ *(const volatile uint64_t*)&m[2 * w + 1]);
+            }
+            if (eq) return (long long)(uint32_t)tv;
+            slot = (slot + 1) & (T - 1);
+        }
+        return -1;
+    }
+}
+
 // Reserve cnt consecutive output positions for each thread of the block with
 // one atomic per block: returns the first position of this thread's range.
 // Every thread of the block must call it (it synchronises the block).

@@ -1205,12 +1205,7 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
         if (act) {
             load_sig<W>(Si, cap, j, s);
             a = Ai[j];
-            for (int g = 1; g < ng; g++) {
-                uint64_t key[W];
-#pragma unroll
-                for (int w = 0; w < W; w++) key[w] = s[w] ^ P.u[g][w];
-                idx[g] = index_find<W>(d, in_buf, Tin, tag_in, key);
-            }
+            for (int g = 1; g < ng; g++) idx[g] = index_find_xor<W>(d, in_buf, Tin, tag_in, s, P.u[g]);
         } else {
 #pragma unroll
             for (int w = 0; w < W; w++) s[w] = 0;
@@ -1226,12 +1221,14 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
                 for (int g2 = 0; g2 < ng; g2++) {
                     const int m = xidx[g][g2];
                     if (idx[m] < 0) continue;
-                    uint64_t px[W];  // parent tau ^ u_g2 = s ^ u_m
-#pragma unroll
-                    for (int w = 0; w < W; w++) px[w] = s[w] ^ P.u[m][w];
                     const double2 ap = m == 0 ? a : Ai[idx[m]];
-                    int pat = 0;
-                    for (int t = 0; t < P.nt[g2]; t++) pat |= (popc_and<W>(P.v[g2][t], px) & 1) << t;
+                    int pat = 0;  // sign pattern of the parent tau ^ u_g2 = s ^ u_m
+                    for (int t = 0; t < P.nt[g2]; t++) {
+                        int c = 0;
+#pragma unroll
+                        for (int w = 0; w < W; w++) c += __popcll(P.v[g2][t][w] & (s[w] ^ P.u[m][w]));
+                        pat |= (c & 1) << t;
+                    }
                     cmul_acc(amp, ctab[g2][pat], ap);
                 }
             }
@@ -1242,12 +1239,17 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
         unsigned long long o = block_out_range(d.ocnt, __popc(keepm), wsum, &bbase);
         for (int g = 0; g < ng; g++) {
             if (!((keepm >> g) & 1u)) continue;
-            uint64_t tau[W];
+            if constexpr (sf_emit_index(W)) {
+                uint64_t tau[W];
 #pragma unroll
-            for (int w = 0; w < W; w++) tau[w] = s[w] ^ P.u[g][w];
-            store_sig<W>(So, cap, o, tau);
+                for (int w = 0; w < W; w++) tau[w] = s[w] ^ P.u[g][w];
+                store_sig<W>(So, cap, o, tau);
+                ok &= index_insert<W>(d, out_buf, Tout, tag_out, tau, (uint32_t)o);
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; w++) So[(size_t)w * cap + o] = s[w] ^ *(const volatile uint64_t*)&P.u[g][w];
+            }
             Ao[o] = amps[g];
-            if constexpr (sf_emit_index(W)) ok &= index_insert<W>(d, out_buf, Tout, tag_out, tau, (uint32_t)o);
             o++;
         }
     }
