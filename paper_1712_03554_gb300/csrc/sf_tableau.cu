@@ -17,6 +17,10 @@
 namespace {
 
 constexpr int kMaxWarps = 32;
+constexpr int kLeadSlots = 64;  // open-addressing table of lead columns in one repair step
+constexpr int kLeadMax = 32;    // distinct leads counted by ballots; more: one full occupancy pass
+constexpr int kDirtyMax = 32;   // changed columns listed for a repair; more: every row is examined
+constexpr int kRunMax = 512;    // monomial gates held back before a repair is forced
 
 template <int W>
 struct Ws {
@@ -50,11 +54,17 @@ struct Scratch {
     int wmin[2][kMaxWarps];
     uint64_t y[W], y2[W], words[5][W];
     uint64_t occ1[2 * W], occ2[2 * W];  // columns holding >= 1 / >= 2 ones (x words, then z words)
-    uint64_t wx[kMaxWarps][W], wz[kMaxWarps][W], wp[kMaxWarps][W];  // per-warp word totals of a product
-    uint64_t px[W], pz[W], qx[W], qz[W], wv[W];                    // product results, amplitude point
+    uint64_t wx[kMaxWarps][W], wz[kMaxWarps][W];  // per-warp word totals of a product
+    uint64_t px[W], pz[W], qx[W], qz[W], wv[W];  // product results, amplitude point
     int pe, qe, ired[kMaxWarps];
     int iv[8];
     double dv[8];
+    // repair bookkeeping
+    uint64_t pol[2 * W];    // columns not known to hold a single 1 (see cta_rref)
+    uint64_t dmask[2 * W];  // columns changed by the gates since the last repair
+    int dl[kDirtyMax], ndl;  // the same columns as a list (ndl > kDirtyMax: not listed)
+    int lkey[kLeadSlots], lcnt[kLeadSlots], llist[kLeadMax], nlead;
+    int wmin2[kMaxWarps];
 };
 
 template <int W>
@@ -87,62 +97,72 @@ __device__ __forceinline__ uint64_t warp_xor64(uint64_t v) {
 // per-thread Pauli in registers.  The product P_1 ... P_m is
 //   i^e P(X, Z),  X = xor x_i,  Z = xor z_i,
 //   e = sum_i (e_i + |x_i & z_i|) + 2 sum_{i<j} |z_i & x_j| - |X & Z|  (mod 4)
-// (Table 1 applied factor by factor); the ordered cross term takes a prefix
-// xor of z along the rows: in-warp by a shuffle scan per word, across warps
-// through the per-warp totals.  Results in ox / oz / *oe (shared), visible to
-// every thread on return.
+// (Table 1 applied factor by factor).  Only the parity of the cross term
+// matters, so it splits into an in-warp part (a shuffle scan of z along the
+// lanes) and a cross-warp part: for warp v, the z total of the earlier warps
+// against the xor of x over warp v.  Warps without a selected row skip the
+// scan; one warp combines the per-warp totals.  Words are fetched four at a
+// time so that their loads are in flight together.  Results in ox / oz / *oe
+// (shared), visible to every thread on return.
 template <int W>
 __device__ void cta_rows_product(const uint64_t* X, const uint64_t* Z, const uint32_t* E, int NT, bool sel,
                                  Scratch<W>& S, uint64_t* ox, uint64_t* oz, int* oe) {
     const int h = threadIdx.x, lane = h & 31, wid = h >> 5, nw = blockDim.x >> 5;
-    int acc = (sel && E) ? (int)E[h] : 0;
-    int par = 0;
+    constexpr int CH = W < 4 ? W : 4;
+    int tot = 0;
+    if (__any_sync(SF_FULL, sel)) {
+        int acc = (sel && E) ? (int)E[h] : 0;
+        int par = 0;
 #pragma unroll 1
-    for (int w = 0; w < W; w++) {
-        const uint64_t x = sel ? X[w * NT + h] : 0ull;
-        const uint64_t z = sel ? Z[w * NT + h] : 0ull;
-        acc += __popcll(x & z);
-        uint64_t inc = z;
+        for (int b = 0; b < W; b += CH) {
+            uint64_t xs[CH], zs[CH];
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint64_t t = __shfl_up_sync(SF_FULL, inc, off);
-            if (lane >= off) inc ^= t;
+            for (int k = 0; k < CH; k++) {
+                xs[k] = sel ? X[(b + k) * NT + h] : 0ull;
+                zs[k] = sel ? Z[(b + k) * NT + h] : 0ull;
+            }
+#pragma unroll
+            for (int k = 0; k < CH; k++) {
+                const uint64_t x = xs[k], z = zs[k];
+                acc += __popcll(x & z);
+                uint64_t inc = z;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint64_t t = __shfl_up_sync(SF_FULL, inc, off);
+                    if (lane >= off) inc ^= t;
+                }
+                par ^= __popcll((inc ^ z) & x) & 1;
+                const uint64_t xt = warp_xor64(x);
+                if (lane == 31) S.wz[wid][b + k] = inc;
+                if (lane == 0) S.wx[wid][b + k] = xt;
+            }
         }
-        par ^= __popcll((inc ^ z) & x) & 1;
-        const uint64_t xt = warp_xor64(x);
-        if (lane == 31) S.wz[wid][w] = inc;
-        if (lane == 0) S.wx[wid][w] = xt;
+        tot = __reduce_add_sync(SF_FULL, (acc + 2 * par) & 3);
+    } else {
+        for (int w = lane; w < W; w += 32) {
+            S.wz[wid][w] = 0ull;
+            S.wx[wid][w] = 0ull;
+        }
     }
-    __syncthreads();
-    // xor of the z totals of the earlier warps, per warp and word
-    for (int t = h; t < nw * W; t += blockDim.x) {
-        const int v = t / W, w = t % W;
-        uint64_t a = 0;
-        for (int u = 0; u < v; u++) a ^= S.wz[u][w];
-        S.wp[v][w] = a;
-    }
-    __syncthreads();
-    if (sel) {
-#pragma unroll 1
-        for (int w = 0; w < W; w++) par ^= __popcll(S.wp[wid][w] & X[w * NT + h]) & 1;
-    }
-    const int tot = __reduce_add_sync(SF_FULL, (acc + 2 * par) & 3);
     if (lane == 0) S.ired[wid] = tot;
-    if (h < W) {
-        uint64_t a = 0, b = 0;
-        for (int v = 0; v < nw; v++) {
-            a ^= S.wx[v][h];
-            b ^= S.wz[v][h];
-        }
-        ox[h] = a;
-        oz[h] = b;
-    }
     __syncthreads();
-    if (h == 0) {
+    if (wid == 0) {  // lane w combines word w over the warps, in row order
+        uint64_t zp = 0, xa = 0;
         int e = 0;
-        for (int v = 0; v < nw; v++) e += S.ired[v];
-        for (int w = 0; w < W; w++) e -= __popcll(ox[w] & oz[w]);
-        *oe = e & 3;
+        if (lane < W) {
+            for (int v = 0; v < nw; v++) {
+                const uint64_t xv = S.wx[v][lane];
+                e += 2 * __popcll(zp & xv);
+                zp ^= S.wz[v][lane];
+                xa ^= xv;
+            }
+            ox[lane] = xa;
+            oz[lane] = zp;
+            e -= __popcll(xa & zp);
+        }
+        if (lane < nw) e += S.ired[lane];
+        e = __reduce_add_sync(SF_FULL, e);
+        if (lane == 0) *oe = e & 3;
     }
     __syncthreads();
 }
@@ -171,7 +191,12 @@ template <int W>
 __device__ int cta_amp_phi(const Ws<W>& T, int n, int NT, int r, const uint32_t* tau, const uint64_t* y,
                            Scratch<W>& S) {
     const int h = threadIdx.x;
-    cta_rows_product<W>(T.dx, T.dz, T.de, NT, tau && h < n && tau[h], S, S.qx, S.qz, &S.qe);
+    if (tau) {
+        cta_rows_product<W>(T.dx, T.dz, T.de, NT, h < n && tau[h], S, S.qx, S.qz, &S.qe);
+    } else {  // Q = I
+        if (h < W) S.qx[h] = S.qz[h] = 0ull;
+        if (h == 0) S.qe = 0;
+    }
     if (h < W) S.wv[h] = y[h] ^ S.qx[h];  // w
     __syncthreads();
     const uint64_t* wv = S.wv;
@@ -236,50 +261,52 @@ __device__ __forceinline__ int conj_row(int kind, int q0, int q1, uint64_t* X, u
 }
 
 // ---- Invariant 1 repair without row movement (CTA version) -----------------
-// The reduction of the warp kernel at block scale: rows stay in place while
-// pivots are chosen; every unassigned row whose leading column holds no other
-// 1 in the tableau takes it as pivot at once (Gauss-Jordan would reach it with
-// nothing to eliminate, in any order); otherwise the smallest leading column c
-// among unassigned rows takes one elimination step, its pivot p being the
-// unassigned row leading at c whose next 1 lies furthest right: every other
-// row with bit c gets M_h <- M_h M_p, mirrored as D_p <- D_p D_h, A_h ^= A_p
-// and t_h ^= t_p ^ c.
-// A final permutation sorts the rows by pivot.  Each gate dirties a few
-// columns, so a gate costs a few block-wide passes instead of one barrier
-// round per column.  Returns r, or -1 if a row has no bits (dependent rows).
+// First set bit of plane P (row h) at or after word w0, word w0 masked by m0;
+// -1 if none.  Words are fetched eight at a time so that their loads are in
+// flight together.
 template <int W>
-__device__ __forceinline__ int row_lead(const Ws<W>& T, int NT, int h, int n) {
+__device__ __forceinline__ int plane_first(const uint64_t* P, int NT, int h, int w0, uint64_t m0) {
+    constexpr int CH = W < 8 ? W : 8;
 #pragma unroll 1
-    for (int w = 0; w < W; w++) {
-        const uint64_t v = T.mx[w * NT + h];
-        if (v) return 64 * w + __ffsll((long long)v) - 1;
+    for (int b = w0; b < W; b += CH) {
+        uint64_t v[CH];
+#pragma unroll
+        for (int k = 0; k < CH; k++) v[k] = (b + k < W) ? P[(b + k) * NT + h] : 0ull;
+        if (b == w0) v[0] &= m0;
+#pragma unroll
+        for (int k = 0; k < CH; k++)
+            if (v[k]) return 64 * (b + k) + __ffsll((long long)v[k]) - 1;
     }
-#pragma unroll 1
-    for (int w = 0; w < W; w++) {
-        const uint64_t v = T.mz[w * NT + h];
-        if (v) return n + 64 * w + __ffsll((long long)v) - 1;
-    }
-    return 0x7fffffff;
+    return -1;
 }
 
-// first 1 of row h after column c (columns x_0..x_{n-1}, z_0..z_{n-1})
+// leading column of row h (columns x_0..x_{n-1}, z_0..z_{n-1})
+template <int W>
+__device__ __forceinline__ int row_lead(const Ws<W>& T, int NT, int h, int n) {
+    int b = plane_first<W>(T.mx, NT, h, 0, ~0ull);
+    if (b >= 0) return b;
+    b = plane_first<W>(T.mz, NT, h, 0, ~0ull);
+    return b >= 0 ? n + b : 0x7fffffff;
+}
+
+// first 1 of row h after column c, for a row that leads at c
 template <int W>
 __device__ __forceinline__ int row_next_lead(const Ws<W>& T, int NT, int h, int n, int c) {
-#pragma unroll 1
-    for (int w = 0; w < W; w++) {
-        uint64_t v = T.mx[w * NT + h];
-        if (c < n && (c >> 6) == w) v &= ~(1ull << (c & 63));
-        if (c < n && (c >> 6) > w) v = 0;
-        if (v) return 64 * w + __ffsll((long long)v) - 1;
+    if (c < n) {
+        int b = plane_first<W>(T.mx, NT, h, c >> 6, ~((2ull << (c & 63)) - 1ull));
+        if (b >= 0) return b;
+        b = plane_first<W>(T.mz, NT, h, 0, ~0ull);
+        return b >= 0 ? n + b : 0x7fffffff;
     }
-#pragma unroll 1
-    for (int w = 0; w < W; w++) {
-        uint64_t v = T.mz[w * NT + h];
-        if (c >= n && ((c - n) >> 6) == w) v &= ~(1ull << ((c - n) & 63));
-        if (c >= n && ((c - n) >> 6) > w) v = 0;
-        if (v) return n + 64 * w + __ffsll((long long)v) - 1;
-    }
-    return 0x7fffffff;
+    const int cz = c - n;
+    const int b = plane_first<W>(T.mz, NT, h, cz >> 6, ~((2ull << (cz & 63)) - 1ull));
+    return b >= 0 ? n + b : 0x7fffffff;
+}
+
+// bit of row h in column c
+template <int W>
+__device__ __forceinline__ bool row_bit(const Ws<W>& T, int NT, int h, int n, int c) {
+    return c < n ? ((T.mx[(c >> 6) * NT + h] >> (c & 63)) & 1) : ((T.mz[((c - n) >> 6) * NT + h] >> ((c - n) & 63)) & 1);
 }
 
 __device__ __forceinline__ bool col_set(const uint64_t* occ, int W, int c, int n) {
@@ -292,23 +319,33 @@ __device__ __forceinline__ bool col_set(const uint64_t* occ, int W, int c, int n
 template <int W>
 __device__ void cta_occupancy(const Ws<W>& T, int NT, Scratch<W>& S) {
     const int h = threadIdx.x, lane = h & 31;
+    constexpr int CH = W < 4 ? 2 * W : 4;  // words fetched together
     if (h < 2 * W) { S.occ1[h] = 0; S.occ2[h] = 0; }
     __syncthreads();
 #pragma unroll 1
-    for (int w = 0; w < 2 * W; w++) {
-        uint64_t o = w < W ? T.mx[w * NT + h] : T.mz[(w - W) * NT + h];
-        if (!__any_sync(SF_FULL, o != 0)) continue;
-        uint64_t m = 0;
+    for (int b = 0; b < 2 * W; b += CH) {
+        uint64_t ov[CH];
 #pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            const uint64_t oo = __shfl_xor_sync(SF_FULL, o, off);
-            const uint64_t om = __shfl_xor_sync(SF_FULL, m, off);
-            m |= om | (o & oo);
-            o |= oo;
+        for (int k = 0; k < CH; k++) {
+            const int w = b + k;
+            ov[k] = w < W ? T.mx[w * NT + h] : T.mz[(w - W) * NT + h];
         }
-        if (lane == 0 && o) {
-            const unsigned long long prev = atomicOr(reinterpret_cast<unsigned long long*>(&S.occ1[w]), o);
-            if (m | (prev & o)) atomicOr(reinterpret_cast<unsigned long long*>(&S.occ2[w]), m | (prev & o));
+#pragma unroll
+        for (int k = 0; k < CH; k++) {
+            uint64_t o = ov[k];
+            if (!__any_sync(SF_FULL, o != 0)) continue;
+            uint64_t m = 0;
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                const uint64_t oo = __shfl_xor_sync(SF_FULL, o, off);
+                const uint64_t om = __shfl_xor_sync(SF_FULL, m, off);
+                m |= om | (o & oo);
+                o |= oo;
+            }
+            if (lane == 0 && o) {
+                const unsigned long long prev = atomicOr(reinterpret_cast<unsigned long long*>(&S.occ1[b + k]), o);
+                if (m | (prev & o)) atomicOr(reinterpret_cast<unsigned long long*>(&S.occ2[b + k]), m | (prev & o));
+            }
         }
     }
     __syncthreads();
@@ -347,15 +384,102 @@ struct SortRec {
 template <int W, bool TRACK_A>
 __device__ int cta_sort_rows(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec rec = {nullptr, nullptr, nullptr});
 
+// Record the lead column l of the calling lane in the lead table (lanes with
+// l < 0 take no part); equal leads in a warp are inserted once.  Returns the
+// slot, or -1 when the table is full (S.nlead is then pushed past kLeadMax).
+template <int W>
+__device__ __forceinline__ int lead_insert(Scratch<W>& S, int l) {
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(SF_FULL, l);
+    const int leader = __ffs(grp) - 1;
+    int slot = -1;
+    if (l >= 0 && lane == leader && *reinterpret_cast<volatile int*>(&S.nlead) <= kLeadMax) {
+        int s = (int)(((unsigned)l * 0x9E3779B1u) >> 26);  // 64 slots
+        for (int i = 0; i < 16; i++) {  // at most 16 probes (load factor <= 1/2)
+            const int k = atomicCAS(&S.lkey[s], -1, l);
+            if (k == -1) {
+                const int idx = atomicAdd(&S.nlead, 1);
+                if (idx < kLeadMax) S.llist[idx] = s;
+                slot = s;
+                break;
+            }
+            if (k == l) {
+                slot = s;
+                break;
+            }
+            s = (s + 1) & (kLeadSlots - 1);
+        }
+        if (slot < 0) atomicAdd(&S.nlead, kLeadMax + 1);
+    }
+    return __shfl_sync(SF_FULL, slot, leader);
+}
+
+// The repair.  Rows stay in place while pivots are chosen: every unassigned
+// row whose leading column holds no other 1 in the tableau takes it as pivot
+// at once (Gauss-Jordan would reach it with nothing to eliminate, in any
+// order); otherwise the smallest leading column c among unassigned rows takes
+// one elimination step, its pivot p being the unassigned row leading at c
+// whose next 1 lies furthest right: every other row with bit c gets
+// M_h <- M_h M_p, mirrored as D_p <- D_p D_h, A_h ^= A_p and t_h ^= t_p ^ c.
+// The leading columns of unassigned rows are counted over all rows by
+// ballots (one full occupancy pass only when more than kLeadMax distinct
+// leads are open).  dirty: the tableau was in RREF with pivots T.piv before
+// gates that changed only the columns S.dl / S.dmask.  Then a row is settled
+// without a count while its lead is its old pivot column and that column is
+// not "polluted" (S.pol: the changed columns and the old pivots of the rows
+// used as elimination pivots), because such a column still holds its one 1:
+// the gates did not touch it, and every elimination pivot other than its
+// owner has a 0 there.  The decisions are those of the plain algorithm.
+// Returns r (SORT: after sorting the rows by pivot), or -1 if a row has no
+// bits (dependent rows).
 template <int W, bool TRACK_A, bool SORT = true>
-__device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec rec = {nullptr, nullptr, nullptr}) {
+__device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec rec = {nullptr, nullptr, nullptr},
+                        bool dirty = false) {
     const int h = threadIdx.x, lane = h & 31, wid = h >> 5, nw = NT >> 5;
     constexpr int INF = 0x7fffffff;
+    const int pv0 = h < n ? T.piv[h] : INF;
     bool asg = false;
+    if (h < 2 * W) S.pol[h] = dirty ? S.dmask[h] : ~0ull;
+    if (h < kLeadSlots) {
+        S.lkey[h] = -1;
+        S.lcnt[h] = 0;
+    }
+    if (h == 0) S.nlead = 0;
+    if (dirty && h < n && pv0 < 2 * n && !col_set(S.dmask, W, pv0, n)) {
+        // settled: no 1 in a changed column left of the old pivot
+        bool cl = true;
+        const int nd = S.ndl;
+#pragma unroll 4
+        for (int i = 0; i < nd; i++) {
+            const int c = S.dl[i];
+            if (c < pv0 && row_bit<W>(T, NT, h, n, c)) cl = false;
+        }
+        asg = cl;
+    }
+    __syncthreads();
     for (int it = 0; it <= n; it++) {
-        cta_occupancy<W>(T, NT, S);
         const int l = (h < n && !asg) ? row_lead<W>(T, NT, h, n) : INF;
-        if (l != INF && !col_set(S.occ2, W, l, n)) {
+        if (l != INF && l == pv0 && !col_set(S.pol, W, l, n)) asg = true;  // T.piv[h] == l already
+        const bool need = h < n && !asg && l != INF;
+        const int slot = lead_insert<W>(S, need ? l : -1);
+        __syncthreads();
+        bool uniq = false;
+        if (S.nlead > kLeadMax) {  // many open leads: count every column once
+            cta_occupancy<W>(T, NT, S);
+            uniq = need && !col_set(S.occ2, W, l, n);
+        } else {
+            const int K = S.nlead;
+#pragma unroll 4
+            for (int k = 0; k < K; k++) {
+                const int sl = S.llist[k];
+                const bool b = h < n && row_bit<W>(T, NT, h, n, S.lkey[sl]);
+                const unsigned bal = __ballot_sync(SF_FULL, b);
+                if (lane == 0 && bal) atomicAdd(&S.lcnt[sl], __popc(bal));
+            }
+            __syncthreads();
+            uniq = need && S.lcnt[slot] < 2;
+        }
+        if (uniq) {
             asg = true;
             T.piv[h] = l;
         }
@@ -365,11 +489,23 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec re
         // keep their own next 1 as lead and no chain of steps follows
         const int lk = (h < n && !asg && l != INF) ? l : INF;
         const int wl = __reduce_min_sync(SF_FULL, lk);
-        if (lane == 0) S.wmin[0][wid] = wl;
+        const bool wdone = __all_sync(SF_FULL, asg || h >= n);
+        if (lane == 0) {
+            S.wmin[0][wid] = wl;
+            S.wmin2[wid] = wdone ? 1 : 0;
+        }
         __syncthreads();
         int c = INF;
-        for (int i = 0; i < nw; i++) c = min(c, S.wmin[0][i]);
-        const int none_left = __syncthreads_and(asg || h >= n);
+        bool none_left = true;
+        for (int i = 0; i < nw; i++) {
+            c = min(c, S.wmin[0][i]);
+            none_left = none_left && S.wmin2[i];
+        }
+        if (h < kLeadSlots) {  // the table is read again only after the next barriers
+            S.lkey[h] = -1;
+            S.lcnt[h] = 0;
+        }
+        if (h == 0) S.nlead = 0;
         if (c == INF) {
             if (!none_left) return -1;  // an unassigned row without bits
             break;
@@ -390,31 +526,53 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec re
         const int cc = c < n ? c : c - n;
         const bool el = (h < n) && (h != p) && ((plane[(cc >> 6) * NT + h] >> (cc & 63)) & 1);
         if (el) {
-            // sign bit of the row product, then the row update, one word at a time
+            // sign bit of the row product and the row update, a few words at a time
+            constexpr int CH = W < 2 ? W : 2;
             int lam = 0;
-#pragma unroll 4
-            for (int w = 0; w < W; w++) {
-                const uint64_t xh = T.mx[w * NT + h], zh = T.mz[w * NT + h];
-                const uint64_t xi = T.mx[w * NT + p], zi = T.mz[w * NT + p];
-                lam += __popcll(xh & zh) + __popcll(xi & zi) + 2 * __popcll(zh & xi) - __popcll((xh ^ xi) & (zh ^ zi));
+#pragma unroll 1
+            for (int b = 0; b < W; b += CH) {
+                uint64_t xh[CH], zh[CH], xi[CH], zi[CH];
+#pragma unroll
+                for (int k = 0; k < CH; k++) {
+                    const int o = (b + k) * NT;
+                    xh[k] = T.mx[o + h];
+                    zh[k] = T.mz[o + h];
+                    xi[k] = T.mx[o + p];
+                    zi[k] = T.mz[o + p];
+                }
+#pragma unroll
+                for (int k = 0; k < CH; k++) {
+                    const int o = (b + k) * NT;
+                    lam += __popcll(xh[k] & zh[k]) + __popcll(xi[k] & zi[k]) + 2 * __popcll(zh[k] & xi[k]) -
+                           __popcll((xh[k] ^ xi[k]) & (zh[k] ^ zi[k]));
+                    T.mx[o + h] = xh[k] ^ xi[k];
+                    T.mz[o + h] = zh[k] ^ zi[k];
+                }
+            }
+            if (TRACK_A) {
+                constexpr int CA = W < 4 ? W : 4;
+#pragma unroll 1
+                for (int b = 0; b < W; b += CA) {
+                    uint64_t ah[CA], ai[CA];
+#pragma unroll
+                    for (int k = 0; k < CA; k++) {
+                        ah[k] = T.A[(b + k) * NT + h];
+                        ai[k] = T.A[(b + k) * NT + p];
+                    }
+#pragma unroll
+                    for (int k = 0; k < CA; k++) T.A[(b + k) * NT + h] = ah[k] ^ ai[k];
+                }
             }
             const uint32_t cbit = (uint32_t)((lam & 3) >> 1) & 1u;
-#pragma unroll 4
-            for (int w = 0; w < W; w++) {
-                T.mx[w * NT + h] ^= T.mx[w * NT + p];
-                T.mz[w * NT + h] ^= T.mz[w * NT + p];
-                if (TRACK_A) T.A[w * NT + h] ^= T.A[w * NT + p];
-            }
             T.t0[h] ^= T.t0[p] ^ cbit;
             T.t1[h] ^= T.t1[p] ^ cbit;
         }
         if (__syncthreads_or(el)) {
-            // D_p <- D_p * prod_{eliminated h} D_h
+            // D_p <- D_p * prod_{eliminated h} D_h, one lane of warp 0 per word
             cta_rows_product<W>(T.dx, T.dz, T.de, NT, el, S, S.qx, S.qz, &S.qe);
-            if (h == p) {
+            if (wid == 0) {
                 int lam = 0;
-#pragma unroll 1
-                for (int w = 0; w < W; w++) {
+                for (int w = lane; w < W; w += 32) {
                     const uint64_t ax = T.dx[w * NT + p], az = T.dz[w * NT + p];
                     const uint64_t bx = S.qx[w], bz = S.qz[w];
                     lam += __popcll(ax & az) + __popcll(bx & bz) + 2 * __popcll(az & bx) -
@@ -422,12 +580,18 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec re
                     T.dx[w * NT + p] = ax ^ bx;
                     T.dz[w * NT + p] = az ^ bz;
                 }
-                T.de[p] = (T.de[p] + (uint32_t)S.qe + (uint32_t)lam) & 3u;
+                lam = __reduce_add_sync(SF_FULL, lam);
+                if (lane == 0) T.de[p] = (T.de[p] + (uint32_t)S.qe + (uint32_t)lam) & 3u;
             }
         }
         if (h == p) {
             asg = true;
             T.piv[p] = c;
+            if (pv0 < 2 * n) {  // p's old pivot column now holds p's 1 in the eliminated rows
+                const int wi = pv0 < n ? (pv0 >> 6) : W + ((pv0 - n) >> 6);
+                const int bb = pv0 < n ? (pv0 & 63) : ((pv0 - n) & 63);
+                atomicOr(reinterpret_cast<unsigned long long*>(&S.pol[wi]), 1ull << bb);
+            }
         }
         __syncthreads();
     }
@@ -567,11 +731,84 @@ __device__ void store_tableau(const SfDev& d, const Ws<W>& T, int r) {
 }
 
 // ---------------------------------------------------------------------------
+// Basis-point bookkeeping of a run of monomial gates (one thread, bits in
+// shared words).
+__device__ __forceinline__ int bit_of(const uint64_t* v, int q) { return (int)((v[q >> 6] >> (q & 63)) & 1); }
+__device__ __forceinline__ void flip_bit(uint64_t* v, int q) { v[q >> 6] ^= 1ull << (q & 63); }
+
+// U|v> = i^k |v'> for a monomial gate U: moves v to v', returns k
+__device__ __forceinline__ int mono_step(int kind, int q0, int q1, uint64_t* v) {
+    const int b0 = bit_of(v, q0), b1 = kind >= 6 ? bit_of(v, q1) : 0;
+    switch (kind) {
+        case 1: return b0;                          // S
+        case 2: return 3 * b0;                      // S-dagger
+        case 3: flip_bit(v, q0); return 0;          // X
+        case 4: flip_bit(v, q0); return 1 + 2 * b0; // Y
+        case 5: return 2 * b0;                      // Z
+        case 6: if (b0) flip_bit(v, q1); return 0;  // CNOT
+        case 7: return 2 * (b0 & b1);               // CZ
+        default:                                    // SWAP
+            if (b0 != b1) {
+                flip_bit(v, q0);
+                flip_bit(v, q1);
+            }
+            return 0;
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_gate(uint32_t kind, uint32_t q0, uint32_t q1) {
+    return kind | (q0 << 4) | (q1 << 18);
+}
+
+// record a changed column (thread 0)
+template <int W>
+__device__ __forceinline__ void mark_col(Scratch<W>& S, int n, int c) {
+    const int wi = c < n ? (c >> 6) : W + ((c - n) >> 6);
+    const uint64_t m = 1ull << (c < n ? (c & 63) : ((c - n) & 63));
+    if (S.dmask[wi] & m) return;
+    S.dmask[wi] |= m;
+    if (S.ndl < kDirtyMax) S.dl[S.ndl] = c;
+    S.ndl++;
+}
+
+// the columns a gate changes (x_q: q, z_q: n + q); Paulis change signs only
+template <int W>
+__device__ __forceinline__ void mark_gate(Scratch<W>& S, int n, int kind, int q0, int q1) {
+    switch (kind) {
+        case 0: mark_col(S, n, q0); mark_col(S, n, n + q0); break;         // H swaps x_q and z_q
+        case 1: case 2: mark_col(S, n, n + q0); break;                     // S: z_q ^= x_q
+        case 6: mark_col(S, n, q1); mark_col(S, n, n + q0); break;         // CNOT: x_t ^= x_c, z_c ^= z_t
+        case 7: mark_col(S, n, n + q0); mark_col(S, n, n + q1); break;     // CZ
+        case 8:                                                            // SWAP
+            mark_col(S, n, q0); mark_col(S, n, q1);
+            mark_col(S, n, n + q0); mark_col(S, n, n + q1);
+            break;
+        default: break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ROTATE for a batch.  A run of monomial gates (S, S-dagger, X, Y, Z, CNOT,
+// CZ, SWAP: each maps a basis state to one basis state times a power of i) is
+// held back and applied to the rows together with the H gate that ends it,
+// followed by one repair.  Its effect on the global factor comes from basis
+// points: the run maps b to pi(b) with U|b> = i^{kappa(b)} |pi(b)>; thread 0
+// carries b0 = pi(0) and kappa(0) along (<0|phi_0(M)> = 2^{-r/2}), and for the
+// H on q the other point of the pair, pi^{-1}(b0 ^ e_q) = L^{-1} e_q (L the
+// run's linear part, walked backwards), whose amplitude on the representation
+// before the run gives
+//   psi(b0 ^ e_q) / psi(b0) = i^{kappa(v) - kappa(0)} phi_0(v) / phi_0(0).
+// The numerator of the phase rule at y = b0 with bit q cleared (or set, when
+// the two terms cancel) then follows as for a lone H, and the denominator is
+// the new representation's amplitude at y.  A run longer than kRunMax, and
+// the run at the end of the batch, are applied and repaired by themselves.
 template <int W>
 __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* gates, int ng, int buf,
                                                    uint64_t* gws) {
     extern __shared__ uint64_t smem[];
     __shared__ Scratch<W> S;
+    __shared__ uint32_t run[kRunMax];
+    __shared__ uint32_t gbuf[1024];
     if (*d.status) return;
     const int n = d.n, NT = d.NT, h = threadIdx.x;
     const Ws<W> T = carve<W>(gws ? gws : smem, NT);
@@ -579,132 +816,145 @@ __global__ void __launch_bounds__(1024) k_clifford(SfDev d, const sf_gate_rec* g
 #pragma unroll
     for (int w = 0; w < W; w++) T.A[w * NT + h] = (h < n && (h >> 6) == w) ? (1ull << (h & 63)) : 0ull;
     int r = d.meta[0];
-    int ga = 0, gb = 0;  // the run's phase factor omega^ga sqrt(2)^gb
-    __syncthreads();
-    // A run of monomial gates (S, S-dagger, X, Y, Z, CNOT, CZ, SWAP: each maps a
-    // basis state to one basis state times a power of i) is repaired once, at its
-    // end: the rows are conjugated gate by gate, and the run's phase factor comes
-    // from one basis point b carried through it (U|b> = i^k |b'> gives
-    // <b'|U psi> = i^k <b|psi>), starting at b = 0 where <0|phi_0(M)> = 2^{-r/2};
-    // the new representation's amplitude at the final b is then evaluated once.
-    // T.t1 holds the run's composed sign flips.  An H gate closes the run and is
-    // repaired by itself, as before.
-    int run_len = 0, r_run = r;
+    int ga = 0, gb = 0;  // the batch's phase factor omega^ga sqrt(2)^gb
     if (h < W) S.y2[h] = 0;
-    if (h == 0) S.iv[0] = 0;
-    auto close_run = [&]() -> bool {
-        r = cta_rref<W, true, false>(T, n, NT, S);
-        if (r < 0) {
+    if (h < 2 * W) S.dmask[h] = 0;
+    if (h == 0) {
+        S.iv[0] = 0;
+        S.ndl = 0;
+    }
+    if (h < n) T.t1[h] = 0;
+    int nrun = 0;  // monomial gates held back (the same count in every thread)
+
+    // Apply the held-back gates (and the H on hq, if hq >= 0), repair, and
+    // update the global factor.  Returns false after setting the status.
+    auto flush = [&](int hq) -> bool {
+        int na = 0, nb = 0, cq = 0;
+        if (hq >= 0) {
+            if (h == 0) {
+                uint64_t* v = S.y;
+                for (int w = 0; w < W; w++) v[w] = 0ull;
+                flip_bit(v, hq);
+                for (int i = nrun - 1; i >= 0; i--) {  // L^{-1} e_q
+                    const uint32_t g = run[i];
+                    const int kind = (int)(g & 15u), a = (int)((g >> 4) & 0x3fffu), b = (int)(g >> 18);
+                    if (kind == 6) {
+                        if (bit_of(v, a)) flip_bit(v, b);
+                    } else if (kind == 8 && bit_of(v, a) != bit_of(v, b)) {
+                        flip_bit(v, a);
+                        flip_bit(v, b);
+                    }
+                }
+                uint64_t* u = S.words[1];
+                for (int w = 0; w < W; w++) u[w] = v[w];
+                int kv = 0;
+                for (int i = 0; i < nrun; i++) {
+                    const uint32_t g = run[i];
+                    kv += mono_step((int)(g & 15u), (int)((g >> 4) & 0x3fffu), (int)(g >> 18), u);
+                }
+                S.iv[1] = kv & 3;
+                mark_gate(S, n, 0, hq, 0);
+            }
+            __syncthreads();
+            const int cv = cta_amp_phi<W>(T, n, NT, r, nullptr, S.y, S);
+            cq = cv < 0 ? -1 : (S.iv[1] - S.iv[0] + cv) & 3;
+            cliff_num_exp(0, cq, na, nb);
+            if (cq == 2 && bit_of(S.y2, hq)) na += 4;
+        } else {
+            __syncthreads();
+        }
+        na += 2 * S.iv[0];
+        // conjugate every row by the held-back gates; sign flips of M go to t0
+        // (composed over the batch) and t1 (since the last repair)
+        if (h < n) {
+            uint32_t f = 0;
+            int fd = 0;
+#pragma unroll 1
+            for (int i = 0; i < nrun; i++) {
+                const uint32_t g = run[i];
+                const int kind = (int)(g & 15u), a = (int)((g >> 4) & 0x3fffu), b = (int)(g >> 18);
+                f ^= (uint32_t)conj_row(kind, a, b, T.mx, T.mz, NT, h);
+                fd += conj_row(kind, a, b, T.dx, T.dz, NT, h);
+            }
+            if (hq >= 0) {
+                f ^= (uint32_t)conj_row(0, hq, 0, T.mx, T.mz, NT, h);
+                fd += conj_row(0, hq, 0, T.dx, T.dz, NT, h);
+            }
+            T.t0[h] ^= f;
+            T.t1[h] ^= f;
+            T.de[h] = (T.de[h] + 2u * (uint32_t)fd) & 3u;
+        }
+        __syncthreads();
+        const int r_new = cta_rref<W, true, false>(T, n, NT, S, {nullptr, nullptr, nullptr}, S.ndl <= kDirtyMax);
+        if (r_new < 0) {
             if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 9u);
             return false;
         }
-        const int dq = cta_amp_phi<W>(T, n, NT, r, T.t1, S.y2, S);
+        // denominator: <y| D'^{t1} phi_0(M')>
+        if (h < W) {
+            uint64_t v = S.y2[h];
+            if (hq >= 0 && (hq >> 6) == h) {
+                v &= ~(1ull << (hq & 63));
+                if (cq == 2) v |= 1ull << (hq & 63);
+            }
+            S.y[h] = v;
+        }
+        __syncthreads();
+        const int dq = cta_amp_phi<W>(T, n, NT, r_new, T.t1, S.y, S);
         if (dq < 0) {
-            if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 2u);
+            if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, hq >= 0 ? 1u : 2u);
             return false;
         }
-        ga = (ga + 2 * S.iv[0] + 2 * ((4 - dq) & 3)) & 7;
-        gb += r - r_run;
-        run_len = 0;
-        if (h < W) S.y2[h] = 0;
-        if (h == 0) S.iv[0] = 0;
+        ga = (ga + na + 2 * ((4 - dq) & 3)) & 7;
+        gb += nb + r_new - r;
+        r = r_new;
+        nrun = 0;
         if (h < n) T.t1[h] = 0;
+        if (h < W) S.y2[h] = 0;
+        if (h < 2 * W) S.dmask[h] = 0;
+        if (h == 0) {
+            S.iv[0] = 0;
+            S.ndl = 0;
+        }
         __syncthreads();
         return true;
     };
-    if (h < n) T.t1[h] = 0;
-    __syncthreads();
-    for (int gi = 0; gi < ng; gi++) {
-        const uint32_t ukind = gates[gi].kind, uq0 = gates[gi].q0, uq1 = gates[gi].q1;
-        const bool two = ukind >= 6;
-        if (ukind > 8 || uq0 >= (uint32_t)n || (two && (uq1 >= (uint32_t)n || uq1 == uq0))) {
+
+    for (int base = 0; base < ng; base += NT) {
+        const int cnt = min(NT, ng - base);
+        __syncthreads();  // the previous chunk is no longer read
+        bool bad = false;
+        if (h < cnt) {
+            const sf_gate_rec g = gates[base + h];
+            const bool two = g.kind >= 6;
+            bad = g.kind > 8 || g.q0 >= (uint32_t)n || (two && (g.q1 >= (uint32_t)n || g.q1 == g.q0));
+            gbuf[h] = pack_gate(g.kind & 15u, g.q0 & 0x3fffu, two ? (g.q1 & 0x3fffu) : 0u);
+        }
+        if (__syncthreads_or(bad)) {
             if (h == 0) set_status(d.status, 1u, buf);  // SF_EINVAL: bad gate in a device list
             return;
         }
-        const int kind = (int)ukind, q0 = (int)uq0, q1 = two ? (int)uq1 : 0;
-        if (kind != 0) {
-            // ---- monomial gate: conjugate the rows, move the reference point
-            if (run_len == 0) r_run = r;
-            if (h < n) {
-                const uint32_t f = (uint32_t)conj_row(kind, q0, q1, T.mx, T.mz, NT, h);
-                T.t0[h] ^= f;
-                T.t1[h] ^= f;
-                const int fd = conj_row(kind, q0, q1, T.dx, T.dz, NT, h);
-                T.de[h] = (T.de[h] + 2u * (uint32_t)fd) & 3u;
-            }
-            if (h == 0) {
-                uint64_t* b = S.y2;
-                const int b0 = (int)((b[q0 >> 6] >> (q0 & 63)) & 1);
-                const int b1 = two ? (int)((b[q1 >> 6] >> (q1 & 63)) & 1) : 0;
-                int k = S.iv[0];
-                switch (kind) {
-                    case 1: k += b0; break;                                   // S
-                    case 2: k += 3 * b0; break;                               // S-dagger
-                    case 3: b[q0 >> 6] ^= 1ull << (q0 & 63); break;           // X
-                    case 4: k += 1 + 2 * b0; b[q0 >> 6] ^= 1ull << (q0 & 63); break;  // Y
-                    case 5: k += 2 * b0; break;                               // Z
-                    case 6: if (b0) b[q1 >> 6] ^= 1ull << (q1 & 63); break;   // CNOT
-                    case 7: k += 2 * (b0 & b1); break;                        // CZ
-                    default:                                                  // SWAP
-                        if (b0 != b1) {
-                            b[q0 >> 6] ^= 1ull << (q0 & 63);
-                            b[q1 >> 6] ^= 1ull << (q1 & 63);
-                        }
+        for (int k = 0; k < cnt; k++) {
+            const uint32_t g = gbuf[k];
+            const int kind = (int)(g & 15u), q0 = (int)((g >> 4) & 0x3fffu), q1 = (int)(g >> 18);
+            if (kind != 0) {
+                if (h == 0) {
+                    S.iv[0] = (S.iv[0] + mono_step(kind, q0, q1, S.y2)) & 3;
+                    run[nrun] = g;
+                    mark_gate(S, n, kind, q0, q1);
                 }
-                S.iv[0] = k & 3;
+                if (++nrun == kRunMax && !flush(-1)) return;
+                continue;
             }
-            run_len++;
-            __syncthreads();
-            continue;
+            if (!flush(q0)) return;
         }
-        if (run_len > 0 && !close_run()) return;
-        // ---- H: numerator of the phase rule, a point y with <y|U phi_0(M)> != 0,
-        // in units of 2^{-r/2}
-        int yq = -1, cq = -1;
-        if (h < W) S.y[h] = (h == (q0 >> 6)) ? (1ull << (q0 & 63)) : 0ull;
-        __syncthreads();
-        cq = cta_amp_phi<W>(T, n, NT, r, nullptr, S.y, S);
-        if (cq == 2) yq = q0;
-        int na, nb;
-        cliff_num_exp(kind, cq, na, nb);
-        const int r_old = r;
-        // conjugate all rows; sign flips of M go to t0 (composed) and t1 (this gate)
-        if (h < n) {
-            const uint32_t f = (uint32_t)conj_row(kind, q0, q1, T.mx, T.mz, NT, h);
-            T.t0[h] ^= f;
-            T.t1[h] = f;
-            const int fd = conj_row(kind, q0, q1, T.dx, T.dz, NT, h);
-            T.de[h] = (T.de[h] + 2u * (uint32_t)fd) & 3u;
-        } else {
-            T.t1[h] = 0;
-        }
-        __syncthreads();
-        // the rows stay where they are until the end of the batch (one sort there)
-        r = cta_rref<W, true, false>(T, n, NT, S);
-        if (r < 0) {
-            if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 9u);
-            return;
-        }
-        // denominator: <y| D'^{t1} phi_0(M')>
-        if (h < W) S.y[h] = (yq >= 0 && h == (yq >> 6)) ? (1ull << (yq & 63)) : 0ull;
-        __syncthreads();
-        const int dq = cta_amp_phi<W>(T, n, NT, r, T.t1, S.y, S);
-        if (dq < 0) {
-            if (h == 0) set_status(d.status, SF_ST_INTERNAL, buf, 1u);
-            return;
-        }
-        const int dr = r - r_old;
-        ga = (ga + na + 2 * ((4 - dq) & 3)) & 7;
-        gb += nb + (dr > 0) - (dr < 0);
-        if (h < n) T.t1[h] = 0;
-        __syncthreads();
     }
-    if (run_len > 0 && !close_run()) return;
+    if (nrun > 0 && !flush(-1)) return;
     SortRec rec = {nullptr, nullptr, nullptr};
     if constexpr (W >= 8)
         rec = {d.piv, d.plan + plan_mv_aff(n, W), reinterpret_cast<uint32_t*>(d.plan + plan_rho_aff(n, W))};
-    r = cta_sort_rows<W, true>(T, n, NT, S, rec);
-    store_tableau<W>(d, T, r);
+    const int rs = cta_sort_rows<W, true>(T, n, NT, S, rec);
+    store_tableau<W>(d, T, rs);
     if (h == 0) *d.g = cmul(*d.g, cliff_factor(ga, gb));
     // emit the affine map: columns of A (column j = image of e_j) and t as bit words
     uint64_t* AT = T.d0x;  // free in this kernel; W*NT >= n*W words

@@ -101,6 +101,25 @@ def test_all_kinds_mixed(sfm, n, seed):
     frames_equal(g, o)
 
 
+@pytest.mark.parametrize("n,seed", [(64, 0), (300, 1), (1024, 2)])
+def test_long_monomial_runs(sfm, n, seed):
+    """Runs of monomial gates (every kind but H) on a scrambled tableau: one
+    longer than the tableau kernel holds back before a repair, one that
+    changes more columns than it lists, short ones; each ended by H gates
+    whose paired basis point the run's CNOTs and SWAPs have moved; T gates and
+    coalescing between the blocks."""
+    g0 = c.rng_for(3000 + seed)
+    mono = tuple(k for k in range(9) if k != c.H)
+    ops = c.random_clifford(n, min(3 * n, 600), seed + 77)
+    for blk, length in enumerate((700, 60, 5, 1)):
+        ops += c.random_clifford(n, length, seed * 10 + blk, kinds=mono)
+        for _ in range(3):
+            ops.append(("C", c.H, int(g0.integers(n)), 0))
+        ops += [("N", c.T, int(g0.integers(n)), 0, 0.0), ("K",)]
+    g, o = run_both(sfm, n, ops, cap=1 << 10)
+    frames_equal(g, o)
+
+
 def test_batched_vs_single_clifford(sfm):
     n = 10
     ops = c.random_clifford_t(n, 300, 5, 17, t_kinds=(c.T, c.TDG))
