@@ -49,7 +49,7 @@ from . import FrameOracle
 
 TOL = 1e-9
 _IPOW = (1, 1j, -1, -1j)
-H, S, CNOT = 0, 1, 6  # Clifford kinds of the C ABI (sf_clifford_kind)
+H, S, SDG, CNOT, CZ = 0, 1, 2, 6, 7  # Clifford kinds of the C ABI (sf_clifford_kind)
 
 
 def zk_rows(x: np.ndarray, z: np.ndarray) -> Dict[int, int]:
@@ -127,6 +127,91 @@ def coalesce_frame(F: FrameOracle, tol: float = TOL) -> Tuple[List[FrameOracle],
     return out, sum(len(o) for o in classes.values())
 
 
+def canonical_circuit(x: np.ndarray, z: np.ndarray, n: int) -> List[Tuple[int, int, int]]:
+    """A stabilizer circuit C with C M C^dagger made of Z_k-rows (Sec. IV,
+    extended coalescing, via Corollary 1's computational-basis form).  Signs
+    are ignored: only the unsigned group matters for the rows' form.  Steps:
+    Gauss-Jordan on the X part (row operations leave the group unchanged);
+    CNOT(p_i, j) clears the X bit of row i at each non-pivot column j; the
+    X-free rows, reduced, are single Z literals off the X pivots and clear the
+    X rows' Z bits there; S on p_i clears a Y, CZ(p_i, p_k) clears the
+    symmetric pair of Z bits between two X rows; H on every X pivot."""
+    X = np.array([[(int(x[r][q >> 6]) >> (q & 63)) & 1 for q in range(n)] for r in range(n)], dtype=bool)
+    Z = np.array([[(int(z[r][q >> 6]) >> (q & 63)) & 1 for q in range(n)] for r in range(n)], dtype=bool)
+    gates: List[Tuple[int, int, int]] = []
+
+    def conj(kind, a, b=0):
+        gates.append((kind, a, b))
+        if kind == H:
+            X[:, a], Z[:, a] = Z[:, a].copy(), X[:, a].copy()
+        elif kind == S:
+            Z[:, a] ^= X[:, a]
+        elif kind == CNOT:
+            X[:, b] ^= X[:, a]
+            Z[:, a] ^= Z[:, b]
+        else:  # CZ
+            Z[:, b] ^= X[:, a]
+            Z[:, a] ^= X[:, b]
+
+    def reduce(P, first):
+        """Gauss-Jordan of plane P with pivot rows taken from rows first.. and
+        every other row reduced; returns the pivot columns."""
+        piv, r = [], first
+        for col in range(n):
+            rows = [i for i in range(r, n) if P[i, col]]
+            if not rows:
+                continue
+            i0 = rows[0]
+            X[[r, i0]] = X[[i0, r]]
+            Z[[r, i0]] = Z[[i0, r]]
+            for i in range(n):
+                if i != r and P[i, col]:
+                    X[i] ^= X[r]
+                    Z[i] ^= Z[r]
+            piv.append(col)
+            r += 1
+        return piv
+
+    piv = reduce(X, 0)
+    rx = len(piv)
+    for i, p in enumerate(piv):
+        for j in range(n):
+            if j not in piv and X[i, j]:
+                conj(CNOT, p, j)
+    reduce(Z, rx)  # the X-free rows: single Z literals off the X pivots
+    for i, p in enumerate(piv):
+        if Z[i, p]:
+            conj(S, p)
+    for i in range(rx):
+        for k in range(i + 1, rx):
+            if Z[i, piv[k]]:
+                conj(CZ, piv[i], piv[k])
+    for p in piv:
+        conj(H, p)
+    assert not X.any() and all(Z[i].sum() == 1 for i in range(n))
+    return gates
+
+
+def coalesce_frame_extended(F: FrameOracle, tol: float = TOL) -> Tuple[List[FrameOracle], int]:
+    """Extended COALESCE (Sec. IV): ROTATE F by a circuit C that maps M to
+    computational-basis form (every row a Z_k-row), COALESCE, and ROTATE every
+    frame produced back by C^dagger."""
+    n = F.n
+    x, z, _ = F.tableau()
+    C = canonical_circuit(x, z, n)
+    sig, amp = F.frame()
+    G = FrameOracle(n)
+    G.set_state(x, z, sig, amp)
+    if C:
+        G.apply_clifford(C)
+    out, pairs = coalesce_frame(G, tol)
+    Cinv = [(SDG if k == S else k, a, b) for (k, a, b) in reversed(C)]
+    if Cinv:
+        for o in out:
+            o.apply_clifford(Cinv)
+    return out, pairs
+
+
 def merge_frames(frames: List[FrameOracle], eps: float = 1e-12) -> List[FrameOracle]:
     """A16: frames with equal stabilizer matrices become one frame (the union
     of their elements, then Def. 1 coalescing).  Empty frames are dropped."""
@@ -153,7 +238,13 @@ def merge_frames(frames: List[FrameOracle], eps: float = 1e-12) -> List[FrameOra
 class MultiFrameOracle:
     """A list of FrameOracle frames representing one state (Sec. IV)."""
 
-    def __init__(self, n: int, tol: float = TOL, eps: float = 1e-12):
+    def __init__(self, n: int, tol: float = TOL, eps: float = 1e-12, reading: str = "printed"):
+        """reading: "printed" (COALESCE on the Z_k-rows of the frame's own
+        matrix, the GPU library's reading) or "extended" (each frame first
+        rotated to computational-basis form)."""
+        if reading not in ("printed", "extended"):
+            raise ValueError(reading)
+        self.reading = reading
         self.n = n
         self.W = (n + 63) // 64
         self.tol = tol
@@ -188,8 +279,9 @@ class MultiFrameOracle:
         frames = merge_frames(self.frames, self.eps)
         while True:
             new, pairs = [], 0
+            step = coalesce_frame_extended if self.reading == "extended" else coalesce_frame
             for F in frames:
-                out, p = coalesce_frame(F, self.tol)
+                out, p = step(F, self.tol)
                 new += out
                 pairs += p
             frames = merge_frames(new, self.eps)

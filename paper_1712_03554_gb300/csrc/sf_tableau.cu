@@ -65,6 +65,8 @@ struct Scratch {
     int dl[kDirtyMax], ndl;  // the same columns as a list (ndl > kDirtyMax: not listed)
     int lkey[kLeadSlots], lcnt[kLeadSlots], llist[kLeadMax], nlead;
     int wmin2[kMaxWarps];
+    uint64_t prow[3 * W];  // the elimination pivot's x, z and A words
+    int nlp;               // its next 1 after the eliminated column
 };
 
 template <int W>
@@ -445,21 +447,32 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec re
         S.lcnt[h] = 0;
     }
     if (h == 0) S.nlead = 0;
-    if (dirty && h < n && pv0 < 2 * n && !col_set(S.dmask, W, pv0, n)) {
-        // settled: no 1 in a changed column left of the old pivot
-        bool cl = true;
-        const int nd = S.ndl;
+    // l: the lead of an unassigned row, kept up to date across the steps (an
+    // elimination changes only the rows that lead at its column)
+    int l = INF;
+    if (h < n) {
+        if (dirty && pv0 < 2 * n) {
+            // the row led at pv0 before the gates, which changed only the listed columns
+            int dmin = INF;
+            const int nd = S.ndl;
 #pragma unroll 4
-        for (int i = 0; i < nd; i++) {
-            const int c = S.dl[i];
-            if (c < pv0 && row_bit<W>(T, NT, h, n, c)) cl = false;
+            for (int i = 0; i < nd; i++) {
+                const int c = S.dl[i];
+                if (c < pv0 && row_bit<W>(T, NT, h, n, c)) dmin = min(dmin, c);
+            }
+            if (dmin != INF)
+                l = dmin;
+            else if (!col_set(S.dmask, W, pv0, n))
+                asg = true;  // settled: its lead and pivot column are untouched
+            else
+                l = row_bit<W>(T, NT, h, n, pv0) ? pv0 : row_next_lead<W>(T, NT, h, n, pv0);
+        } else {
+            l = row_lead<W>(T, NT, h, n);
         }
-        asg = cl;
     }
     __syncthreads();
     for (int it = 0; it <= n; it++) {
-        const int l = (h < n && !asg) ? row_lead<W>(T, NT, h, n) : INF;
-        if (l != INF && l == pv0 && !col_set(S.pol, W, l, n)) asg = true;  // T.piv[h] == l already
+        if (!asg && l != INF && l == pv0 && !col_set(S.pol, W, l, n)) asg = true;  // T.piv[h] == l already
         const bool need = h < n && !asg && l != INF;
         const int slot = lead_insert<W>(S, need ? l : -1);
         __syncthreads();
@@ -467,7 +480,7 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec re
         if (S.nlead > kLeadMax) {  // many open leads: count every column once
             cta_occupancy<W>(T, NT, S);
             uniq = need && !col_set(S.occ2, W, l, n);
-        } else {
+        } else if (S.nlead > 0) {
             const int K = S.nlead;
 #pragma unroll 4
             for (int k = 0; k < K; k++) {
@@ -511,9 +524,10 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec re
             break;
         }
         unsigned pk = 0xffffffffu;
+        int nl = INF;
         if (lk == c) {
-            const int nl = row_next_lead<W>(T, NT, h, n, c);
-            pk = ((nl == INF ? 0u : (unsigned)(2047 - nl)) << 10) | (unsigned)h;
+            nl = row_next_lead<W>(T, NT, h, n, c);  // nl <= 2n - 1 <= 2047
+            pk = ((nl == INF ? 0u : (unsigned)(2048 - nl)) << 10) | (unsigned)h;
         }
         const unsigned wp = __reduce_min_sync(SF_FULL, pk);
         if (lane == 0) S.wmin[1][wid] = (int)wp;
@@ -521,46 +535,47 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec re
         unsigned pmin = 0xffffffffu;
         for (int i = 0; i < nw; i++) pmin = min(pmin, (unsigned)S.wmin[1][i]);
         const int p = (int)(pmin & 1023u);
+        // the pivot row (and its A row) in shared memory, with its next 1
+        for (int e = h; e < (TRACK_A ? 3 : 2) * W; e += NT) {
+            const int w = e % W, pl = e / W;
+            S.prow[e] = (pl == 0 ? T.mx : pl == 1 ? T.mz : T.A)[w * NT + p];
+        }
+        if (h == p) S.nlp = nl;
         // elimination step at column c with pivot row p
         const uint64_t* plane = c < n ? T.mx : T.mz;
         const int cc = c < n ? c : c - n;
         const bool el = (h < n) && (h != p) && ((plane[(cc >> 6) * NT + h] >> (cc & 63)) & 1);
+        __syncthreads();
         if (el) {
-            // sign bit of the row product and the row update, a few words at a time
-            constexpr int CH = W < 2 ? W : 2;
+            // sign bit of the row product and the row update, four words at a time
+            constexpr int CH = W < 4 ? W : 4;
             int lam = 0;
 #pragma unroll 1
             for (int b = 0; b < W; b += CH) {
-                uint64_t xh[CH], zh[CH], xi[CH], zi[CH];
+                uint64_t xh[CH], zh[CH];
 #pragma unroll
                 for (int k = 0; k < CH; k++) {
-                    const int o = (b + k) * NT;
-                    xh[k] = T.mx[o + h];
-                    zh[k] = T.mz[o + h];
-                    xi[k] = T.mx[o + p];
-                    zi[k] = T.mz[o + p];
+                    xh[k] = T.mx[(b + k) * NT + h];
+                    zh[k] = T.mz[(b + k) * NT + h];
                 }
 #pragma unroll
                 for (int k = 0; k < CH; k++) {
                     const int o = (b + k) * NT;
-                    lam += __popcll(xh[k] & zh[k]) + __popcll(xi[k] & zi[k]) + 2 * __popcll(zh[k] & xi[k]) -
-                           __popcll((xh[k] ^ xi[k]) & (zh[k] ^ zi[k]));
-                    T.mx[o + h] = xh[k] ^ xi[k];
-                    T.mz[o + h] = zh[k] ^ zi[k];
+                    const uint64_t xi = S.prow[b + k], zi = S.prow[W + b + k];
+                    lam += __popcll(xh[k] & zh[k]) + __popcll(xi & zi) + 2 * __popcll(zh[k] & xi) -
+                           __popcll((xh[k] ^ xi) & (zh[k] ^ zi));
+                    T.mx[o + h] = xh[k] ^ xi;
+                    T.mz[o + h] = zh[k] ^ zi;
                 }
             }
             if (TRACK_A) {
-                constexpr int CA = W < 4 ? W : 4;
 #pragma unroll 1
-                for (int b = 0; b < W; b += CA) {
-                    uint64_t ah[CA], ai[CA];
+                for (int b = 0; b < W; b += CH) {
+                    uint64_t ah[CH];
 #pragma unroll
-                    for (int k = 0; k < CA; k++) {
-                        ah[k] = T.A[(b + k) * NT + h];
-                        ai[k] = T.A[(b + k) * NT + p];
-                    }
+                    for (int k = 0; k < CH; k++) ah[k] = T.A[(b + k) * NT + h];
 #pragma unroll
-                    for (int k = 0; k < CA; k++) T.A[(b + k) * NT + h] = ah[k] ^ ai[k];
+                    for (int k = 0; k < CH; k++) T.A[(b + k) * NT + h] = ah[k] ^ S.prow[2 * W + b + k];
                 }
             }
             const uint32_t cbit = (uint32_t)((lam & 3) >> 1) & 1u;
@@ -583,6 +598,12 @@ __device__ int cta_rref(const Ws<W>& T, int n, int NT, Scratch<W>& S, SortRec re
                 lam = __reduce_add_sync(SF_FULL, lam);
                 if (lane == 0) T.de[p] = (T.de[p] + (uint32_t)S.qe + (uint32_t)lam) & 3u;
             }
+        }
+        if (el && lk == c) {
+            // a candidate other than p: its bits up to its own next 1 are p's zeros,
+            // so that is its new lead, unless p's next 1 is the same column
+            const int nlp = S.nlp;
+            l = nl < nlp ? nl : (nl == INF ? INF : row_next_lead<W>(T, NT, h, n, nl));
         }
         if (h == p) {
             asg = true;

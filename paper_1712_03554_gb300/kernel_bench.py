@@ -16,6 +16,7 @@ amplitudes read and written; index and hash tables are not counted).
   python -m paper_1712_03554_gb300.kernel_bench campaign-case 64 (one campaign launch, 32 threads, global index)
   python -m paper_1712_03554_gb300.kernel_bench clifford-case 1024 (one Clifford batch of 200 gates at n)
   python -m paper_1712_03554_gb300.kernel_bench clifford-rate     (tableau us per gate, n = 64 ... 1024)
+  python -m paper_1712_03554_gb300.kernel_bench clifford-mix 1024 (tableau us per gate by gate mix)
   python -m paper_1712_03554_gb300.kernel_bench cuccaro 5 6 7   (adder: Toffoli by cofactors vs Clifford+7T)
   python -m paper_1712_03554_gb300.kernel_bench cuccaro-mf 4 5 6 7 (adder: one frame vs a multiframe)
 """
@@ -371,6 +372,26 @@ def clifford_rate(ns=(64, 128, 256, 512, 1024), gates=1000):
     print(json.dumps(out), flush=True)
 
 
+def clifford_mix(n=1024, gates=1000):
+    """Tableau cost per gate at n by gate mix (class clifford, CUDA events), on a
+    tableau scrambled by 4n random H/S/CNOT gates: H only; monomial gates only
+    (S, CNOT, CZ: one repair at the end of the batch); H/S/CNOT."""
+    out = {"n": n, "gates": gates}
+    mixes = {"h_only": (c.H,), "monomial_only": (c.S, c.CNOT, c.CZ), "h_s_cnot": (c.H, c.S, c.CNOT)}
+    for name, kinds in mixes.items():
+        pre = c.random_clifford(n, 4 * n, seed=n, kinds=(c.H, c.S, c.CNOT))
+        ops = c.random_clifford(n, gates, seed=n + 1, kinds=kinds)
+        f = sf.Frame(n, 64)
+        f.apply_clifford([(op[1], op[2], op[3]) for op in pre])
+        f.sync()
+        g = [(op[1], op[2], op[3]) for op in ops]
+        timed(f, "clifford", lambda: f.apply_clifford(g), 1)  # warm-up
+        ms = timed(f, "clifford", lambda: f.apply_clifford(g), 2)
+        out[f"{name}_us_per_gate"] = round(ms * 1e3 / gates, 2)
+        f.close()
+    print(json.dumps(out), flush=True)
+
+
 def cuccaro_compare(nbs=(5, 6, 7)):
     """The Cuccaro adder on the equal superposition with every Toffoli applied
     by cofactors (Eq. 2) and as Clifford+7T: wall time of the whole circuit
@@ -472,5 +493,7 @@ if __name__ == "__main__":
         clifford_case(args[0] if args else 1024)
     elif mode == "clifford-rate":
         clifford_rate(tuple(args) if args else (64, 128, 256, 512, 1024))
+    elif mode == "clifford-mix":
+        clifford_mix(args[0] if args else 1024)
     else:
         raise SystemExit(f"unknown mode {mode}")

@@ -201,3 +201,71 @@ def test_one_coalesce_halves_a_fully_paired_frame(n):
     out, pairs = mfo.coalesce_frame(F)
     assert pairs == 1 << (n - 1)
     assert sum(G.size() for G in out) == 1 << (n - 1)
+
+
+# ---- the two COALESCE readings on the Cuccaro adder (Sec. IV, Sec. VI) ------
+
+@pytest.mark.parametrize("nb", [1, 2, 3])
+def test_extended_reading_keeps_the_state(nb):
+    """Extended COALESCE (ROTATE to computational-basis form, COALESCE, ROTATE
+    back) on the adder with superposed inputs: the same state as the state
+    vector, and every frame's matrix made of Z_k-rows after the canonical
+    circuit of its own tableau."""
+    ops = c.cuccaro(nb, superpose=True, toffoli="cofactor", coalesce=False)
+    n = 2 * nb + 2
+    mf = mfo.MultiFrameOracle(n, reading="extended")
+    dense = oracle.DenseOracle(n)
+    c.run(mf, ops)
+    c.run(dense, ops)
+    dense_equal(mf, dense, n)
+    for F in mf.frames:
+        x, z, _ = F.tableau()
+        G = oracle.FrameOracle(n)
+        sig, amp = F.frame()
+        G.set_state(x, z, sig, amp)
+        G.apply_clifford(mfo.canonical_circuit(x, z, n))
+        gx, gz, _ = G.tableau()
+        assert len(mfo.zk_rows(gx, gz)) == n
+
+
+def test_state_counts_of_both_readings():
+    """States at the end of the adder, nb = 1..5: the printed reading grows
+    about 2.45x per bit, the extended one exactly 2x; neither is linear."""
+    want = {"printed": [2, 4, 10, 22, 54], "extended": [2, 4, 8, 16, 32]}
+    for reading, counts in want.items():
+        got = []
+        for nb in range(1, 6):
+            mf = mfo.MultiFrameOracle(2 * nb + 2, reading=reading)
+            c.run(mf, c.cuccaro(nb, superpose=True, toffoli="cofactor", coalesce=False))
+            got.append(mf.count()[1])
+        assert got == counts, (reading, got)
+
+
+def _affine(points):
+    t0 = next(iter(points))
+    return all((a ^ b ^ t0) in points for a in points for b in points) and \
+        len(points) & (len(points) - 1) == 0
+
+
+@pytest.mark.parametrize("nb", [2, 3])
+def test_middle_of_the_adder_has_no_coalescable_pair(nb):
+    """After the MAJ chain the state is a sum over the propagate pattern p of
+    2^nb stabilizer states with disjoint supports, each the graph of a linear
+    map that differs for every p; no two of them sum to a stabilizer state (the
+    union of their supports is never an affine space), so pairwise COALESCE
+    cannot go below 2^nb states there.  The extended reading reaches exactly
+    that decomposition."""
+    n = 2 * nb + 2
+    ops = c.cuccaro(nb, superpose=True, toffoli="cofactor", coalesce=False)[:2 * nb + 3 * nb]
+    assert sum(op[0] == "T3" for op in ops) == nb
+    mf = mfo.MultiFrameOracle(n, reading="extended")
+    c.run(mf, ops)
+    assert mf.count() == (1 << nb, 1 << nb)
+    supports = []
+    for F in mf.frames:
+        supports.append({y for y in range(1 << n) if abs(F.amplitude(y)) > 1e-9})
+    assert all(_affine(s) for s in supports)
+    for i in range(len(supports)):
+        for k in range(i + 1, len(supports)):
+            assert not (supports[i] & supports[k])
+            assert not _affine(supports[i] | supports[k])
