@@ -603,14 +603,16 @@ def _run_stream(sfm, stream, recs, slots, budget):
 
 
 def serving_leg(sfm, n_requests: int, slots: int, budget_gb: int = 96, fractions=(0.5, 0.8, 1.2),
-                cap_sample: int = 6):
-    """The plain path's capacity (cap_sample requests queued at once, one at a
-    time), then the same seeded stream at arrival rates fraction x capacity,
-    served (continuous batching over `slots` slots) and one at a time."""
+                cap_sample: int = 12):
+    """The capacities of the plain path (cap_sample requests queued at once,
+    one at a time) and of the server (the same burst over `slots` slots), then
+    the same seeded stream at arrival rates fraction x plain capacity, served
+    and one at a time."""
     budget = budget_gb << 30
     burst = c.serving_stream(cap_sample, 1e9, seed=1)  # every request arrives at once
     burst_recs = [sfm.encode_program([r["ops"]])[0] for r in burst]
     _, cap_stats = _run_stream(sfm, burst, burst_recs, 1, budget)
+    _, scap_stats = _run_stream(sfm, burst, burst_recs, slots, budget)
     capacity = cap_stats["circuits_per_s"]
     sweep = []
     all_same, max_diff = True, 0.0
@@ -639,6 +641,10 @@ def serving_leg(sfm, n_requests: int, slots: int, budget_gb: int = 96, fractions
             "max_active": slots, "hbm_budget_gb": budget_gb,
             "plain_capacity": {"circuits_per_s": capacity, "sample": f"{cap_sample} requests queued at once, "
                                                                     f"one at a time", "stats": cap_stats},
+            "served_capacity": {"circuits_per_s": scap_stats["circuits_per_s"],
+                                "sample": f"the same {cap_sample} requests queued at once, over {slots} slots",
+                                "stats": scap_stats,
+                                "over_plain_capacity": scap_stats["circuits_per_s"] / capacity},
             "sweep": sweep, "results_same_alone_and_mixed": all_same, "max_amp_diff_alone_vs_mixed": max_diff,
             "note": ("the stated stream has 2000 requests; this run takes the largest count that keeps the bench "
                      "within a few minutes (--serving-requests sets it)")}
@@ -706,7 +712,7 @@ def main():
     ap.add_argument("--no-multiframe", action="store_true", help="skip the multiframe leg")
     ap.add_argument("--no-streaming", action="store_true",
                     help="skip the per-kernel roofline leg of the streaming kernels at 16 words per phase vector")
-    ap.add_argument("--serving-requests", type=int, default=12, help="requests per load point of the serving sweep")
+    ap.add_argument("--serving-requests", type=int, default=30, help="requests per load point of the serving sweep")
     ap.add_argument("--serving-slots", type=int, default=32)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -816,8 +816,10 @@ sf_status sf_coalesce(sf_handle h, double drop_eps, uint64_t* out_size) {
 
 // COFACTOR(F, q) (Sec. III): the tableau update and, if q is random, the
 // merged split of every element into its two cofactors.  Synchronises (the
-// host learns whether q was random).
-static sf_status cofactor_q(sf_handle h, uint32_t q) {
+// host learns whether q was random).  prob_done (optional): set when the
+// cofactor kernel also left the per-CTA probability partials of q.
+static sf_status cofactor_q(sf_handle h, uint32_t q, bool* prob_done = nullptr) {
+    if (prob_done) *prob_done = false;
     SF_LAUNCH(h, SF_K_MEASURE_PREP, sf_launch_measure_prep(h->d, q, h->cur, h->gws, h->stream));
     SF_CK(h, cudaMemcpyAsync(h->hmeta, h->d.meta, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     // the layout the last grid program left, read in the same round trip
@@ -831,9 +833,10 @@ static sf_status cofactor_q(sf_handle h, uint32_t q) {
     if (h->hmeta[2]) {
         if (lay && h->hmeta[3]) {
             // partners by position: no index read or written
-            SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cof_pos(h->d, h->cur, h->cur ^ 1, h->stream));
+            SF_LAUNCH(h, SF_K_COFACTOR, sf_launch_cof_pos(h->d, h->cur, h->cur ^ 1, prob_done != nullptr, h->stream));
             h->cur ^= 1;
             h->idx_ok[h->cur] = false;
+            if (prob_done) *prob_done = true;
         } else {
             st = need_index(h, h->cur);
             if (st) return st;
@@ -870,9 +873,10 @@ sf_status sf_apply_cr_cofactor(sf_handle h, uint32_t c, uint32_t t, double alpha
 sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, double* p1) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
     if (q >= h->n || collapse_to < -1 || collapse_to > 1) return fail(h, SF_EINVAL, "bad measurement arguments");
-    sf_status st = cofactor_q(h, q);
+    bool prob_done = false;
+    sf_status st = cofactor_q(h, q, &prob_done);
     if (st) return st;
-    SF_LAUNCH(h, SF_K_PROB, sf_launch_prob(h->d, h->cur, h->stream));
+    if (!prob_done) SF_LAUNCH(h, SF_K_PROB, sf_launch_prob(h->d, h->cur, h->stream));
     SF_LAUNCH(h, SF_K_REDUCE, sf_launch_reduce_final(h->d, 0, h->stream));
     SF_CK(h, cudaMemcpyAsync(h->hout, h->d.out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     st = sync_check(h);

@@ -586,7 +586,7 @@ void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t
 // cofactor split with merging of the two parents of each child
 void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s);
 void sf_launch_build_index(const SfDev& d, int buf, cudaStream_t s);
-void sf_launch_cof_pos(const SfDev& d, int in_buf, int out_buf, cudaStream_t s);
+void sf_launch_cof_pos(const SfDev& d, int in_buf, int out_buf, bool prob, cudaStream_t s);
 void sf_launch_filter(const SfDev& d, int x, int in_buf, int out_buf, cudaStream_t s);
 void sf_launch_cond(const SfDev& d, int buf, int kind, int c1, int c2, int t, double alpha, cudaStream_t s);
 void sf_launch_prob(const SfDev& d, int buf, cudaStream_t s);

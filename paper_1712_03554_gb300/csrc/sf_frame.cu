@@ -1648,17 +1648,26 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
 // prep builds it), so a child amplitude is sc i^{e_y + ip_y} a: an exact
 // rotation, the partners' two summed, then one real scaling.  Does nothing
 // when the layout is not known (the host checks that before it launches it).
-__global__ void __launch_bounds__(kThreads) k_cof_pos(SfDev d, double eps2, int in_buf, int out_buf) {
+// With prob set it also leaves what k_prob computes: per CTA, the summed
+// |a|^2 of the children it keeps, split by their bit on row meta[1] (the
+// measured qubit's row), for k_reduce_final.
+__global__ void __launch_bounds__(kThreads) k_cof_pos(SfDev d, double eps2, int in_buf, int out_buf, int prob) {
     __shared__ uint64_t sU[64], sV[64];
     __shared__ unsigned int wsum[kThreads / 32];
     __shared__ unsigned long long bbase, s_c, s_om[2];
     __shared__ int s_span, s_e[2];
     __shared__ double s_sc;
+    __shared__ double shp[2][32];
     if (*d.status) return;
     if (!d.meta[2]) return;
     const GpLayout* L = reinterpret_cast<const GpLayout*>(d.gp);
     if (!L->ok) return;
     const int n = d.n;
+    const int R = d.meta[1];
+    if (prob && (R < 0 || R >= n)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.status, SF_ST_INTERNAL, in_buf, 21u);
+        return;
+    }
     const uint64_t* pl = d.plan;
     const uint64_t uq = pl[cf_uq(n, 1)], vq = pl[cf_vq(n, 1)];
     const uint64_t eps0 = pl[cf_eps(n, 1)], eps1 = pl[cf_eps(n, 1) + 1];
@@ -1764,6 +1773,7 @@ __global__ void __launch_bounds__(kThreads) k_cof_pos(SfDev d, double eps2, int 
         return (y ? e1 : e0) + __popcll(el & eps0) + 2 * __popcll(el & eps1) + 2 * (pw ^ Q);
     };
     bool bad = false;
+    double pr[2] = {0.0, 0.0};
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < units; base += stride) {
         const unsigned long long m = base + threadIdx.x;
         const bool act = m < units;
@@ -1816,9 +1826,17 @@ __global__ void __launch_bounds__(kThreads) k_cof_pos(SfDev d, double eps2, int 
             So[o] = t[x];
             Ao[o] = cc[x];
             o++;
+            pr[(t[x] >> (R & 63)) & 1] += cc[x].x * cc[x].x + cc[x].y * cc[x].y;
         }
     }
     if (bad) set_status(d.status, SF_ST_INTERNAL, in_buf, 28u);
+    if (prob) {
+        block_sum<2>(pr, shp);
+        if (threadIdx.x == 0) {
+            d.red[2 * blockIdx.x] = pr[0];
+            d.red[2 * blockIdx.x + 1] = pr[1];
+        }
+    }
     if (last_block(d.done) && threadIdx.x == 0) {
         d.kcnt[out_buf] = *d.ocnt;
         *d.ocnt = 0;
@@ -1839,12 +1857,26 @@ __global__ void __launch_bounds__(kThreads) k_prob(SfDev d, int buf) {
     const uint64_t* plane = d.sig[buf] + (size_t)(R >> 6) * d.cap;
     const double2* A = d.amp[buf];
     double p[2] = {0.0, 0.0};
-    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        const double2 a = A[j];
-        const double m = a.x * a.x + a.y * a.y;
-        if ((plane[j] >> (R & 63)) & 1) p[1] += m;
-        else p[0] += m;
+    // four elements of the thread's grid-stride sequence per round, their
+    // loads in flight together (the sums keep the sequence's order)
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long j0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j0 < k;
+         j0 += 4 * stride) {
+        double2 av[4];
+        uint64_t pw[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const unsigned long long j = j0 + u * stride;
+            av[u] = j < k ? A[j] : make_double2(0.0, 0.0);
+            pw[u] = j < k ? plane[j] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (j0 + u * stride >= k) break;
+            const double m = av[u].x * av[u].x + av[u].y * av[u].y;
+            if ((pw[u] >> (R & 63)) & 1) p[1] += m;
+            else p[0] += m;
+        }
     }
     block_sum<2>(p, sh);
     if (threadIdx.x == 0) {
@@ -1900,30 +1932,45 @@ __global__ void __launch_bounds__(kThreads) k_amplitude(SfDev d, int buf) {
         }
         for (int R = threadIdx.x; R < 64; R += blockDim.x) pv[R] = R < r ? (__ldg(&d.piv[R]) & 63) : 0;
         __syncthreads();
-        for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
-             j += (unsigned long long)gridDim.x * blockDim.x) {
-            const uint64_t s = d.sig[buf][j];
-            if ((s & zm[0]) != ze[0]) continue;
-            Pauli<1> q;
-            pauli_id<1>(q);
-            for (int c = 0; c < nc; c++) pauli_mul<1>(q, DT[c][(s >> (4 * c)) & 15]);
-            const uint64_t wv = y[0] ^ q.x[0];
-            Pauli<1> p;
-            pauli_id<1>(p);
-            for (int c = 0; c < rc; c++) {
-                int v = 0;
-                for (int bb = 0; bb < 4; bb++) {
-                    const int R = 4 * c + bb;
-                    if (R < r) v |= (int)((wv >> pv[R]) & 1) << bb;
-                }
-                pauli_mul<1>(p, MT[c][v]);
+        // four elements of the thread's grid-stride sequence per round, their
+        // loads in flight together (the sums keep the sequence's order)
+        const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+        for (unsigned long long j0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j0 < k;
+             j0 += 4 * stride) {
+            uint64_t sv[4];
+            double2 av[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const unsigned long long j = j0 + u * stride;
+                sv[u] = j < k ? d.sig[buf][j] : 0ull;
+                av[u] = j < k ? d.amp[buf][j] : make_double2(0.0, 0.0);
             }
-            if (p.x[0] != wv) continue;
-            const int ip = (q.e + __popcll(q.x[0] & q.z[0]) + 2 * __popcll(q.z[0] & wv) + p.e +
-                            __popcll(p.x[0] & p.z[0])) & 3;
-            const double2 c = ipow_mul(d.amp[buf][j], ip);
-            acc[0] += c.x;
-            acc[1] += c.y;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (j0 + u * stride >= k) break;
+                const uint64_t s = sv[u];
+                if ((s & zm[0]) != ze[0]) continue;
+                Pauli<1> q;
+                pauli_id<1>(q);
+                for (int c = 0; c < nc; c++) pauli_mul<1>(q, DT[c][(s >> (4 * c)) & 15]);
+                const uint64_t wv = y[0] ^ q.x[0];
+                Pauli<1> p;
+                pauli_id<1>(p);
+                for (int c = 0; c < rc; c++) {
+                    int v = 0;
+                    for (int bb = 0; bb < 4; bb++) {
+                        const int R = 4 * c + bb;
+                        if (R < r) v |= (int)((wv >> pv[R]) & 1) << bb;
+                    }
+                    pauli_mul<1>(p, MT[c][v]);
+                }
+                if (p.x[0] != wv) continue;
+                const int ip = (q.e + __popcll(q.x[0] & q.z[0]) + 2 * __popcll(q.z[0] & wv) + p.e +
+                                __popcll(p.x[0] & p.z[0])) & 3;
+                const double2 c = ipow_mul(av[u], ip);
+                acc[0] += c.x;
+                acc[1] += c.y;
+            }
         }
     } else {
         for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
@@ -2056,8 +2103,8 @@ void sf_launch_branch_merge(const SfDev& d, uint32_t kind, uint32_t q0, uint32_t
 
 // the cofactor of a frame whose layout the grid program left known (n <= 63;
 // the host has checked that no kernel moved the elements since)
-void sf_launch_cof_pos(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
-    k_cof_pos<<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf);
+void sf_launch_cof_pos(const SfDev& d, int in_buf, int out_buf, bool prob, cudaStream_t s) {
+    k_cof_pos<<<d.nblk, kThreads, 0, s>>>(d, 1e-24, in_buf, out_buf, prob ? 1 : 0);
 }
 
 void sf_launch_cof_merge(const SfDev& d, int in_buf, int out_buf, cudaStream_t s) {
