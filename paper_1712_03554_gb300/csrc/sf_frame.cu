@@ -231,13 +231,29 @@ __device__ __forceinline__ void bits_insert(uint64_t* v, int p, uint32_t x) {
     }
 }
 
+// bits pos[0..m) of v, packed (bit k = bit pos[k] of v).  Words outside,
+// positions inside: a word picked by a run-time position would take v out of
+// registers.
+template <int W>
+__device__ __forceinline__ uint32_t bits_gather(const uint64_t* v, const int* pos, int m) {
+    uint32_t bits = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        const uint64_t x = v[w];
+#pragma unroll 1
+        for (int k = 0; k < m; k++) {
+            const int p = pos[k];
+            if ((p >> 6) == w) bits |= (uint32_t)((x >> (p & 63)) & 1ull) << k;
+        }
+    }
+    return bits;
+}
+
 // v <- rho(v): bit h moves to rho(h)
 template <int W>
 __device__ __forceinline__ void apply_moves(uint64_t* v, const Moves& M) {
     const int m = M.m;
-    uint32_t bits = 0;
-#pragma unroll 1
-    for (int k = 0; k < m; k++) bits |= bit_at<W>(v, M.a[k]) << k;
+    const uint32_t bits = bits_gather<W>(v, M.a, m);
 #pragma unroll 1
     for (int k = m - 1; k >= 0; k--) bits_delete<W>(v, M.a[k]);
 #pragma unroll 1
@@ -248,9 +264,7 @@ __device__ __forceinline__ void apply_moves(uint64_t* v, const Moves& M) {
 template <int W>
 __device__ __forceinline__ void apply_moves_inv(uint64_t* v, const Moves& M) {
     const int m = M.m;
-    uint32_t bits = 0;
-#pragma unroll 1
-    for (int j = 0; j < m; j++) bits |= bit_at<W>(v, M.e[j]) << j;
+    const uint32_t bits = bits_gather<W>(v, M.e, m);
 #pragma unroll 1
     for (int j = m - 1; j >= 0; j--) bits_delete<W>(v, M.e[j]);
 #pragma unroll 1
@@ -1127,6 +1141,14 @@ __global__ void __launch_bounds__(kThreads) k_build_index(SfDev d, int b) {
 // s such that no tau ^ u_g' with g' < g is in the frame; its amplitude sums the
 // contributions of every parent tau ^ u_g'' found through the index of in_buf,
 // in a fixed order.  No amplitude atomics; the output frame is indexed.
+// idx[m] for m in [0, SF_BR_MAXG) by masks, with no run-time subscript
+__device__ __forceinline__ long long pick_idx(const long long* idx, int m) {
+    long long r = 0;
+#pragma unroll
+    for (int g = 0; g < SF_BR_MAXG; g++) r |= idx[g] & -(long long)(g == m);
+    return r;
+}
+
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1,
                                                            SfTerms tm, double eps2, int in_buf, int out_buf) {
@@ -1200,28 +1222,39 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
         const bool act = j < k;
         uint64_t s[W];
         double2 a = make_double2(0.0, 0.0);
+        // the loops over groups are unrolled over SF_BR_MAXG with guards, and
+        // idx is read through pick_idx, so that idx, amps and s stay in
+        // registers (a run-time subscript would put them in local memory)
         long long idx[SF_BR_MAXG];
         idx[0] = act ? (long long)j : -1;
         if (act) {
             load_sig<W>(Si, cap, j, s);
             a = Ai[j];
-            for (int g = 1; g < ng; g++) idx[g] = index_find_xor<W>(d, in_buf, Tin, tag_in, s, P.u[g]);
         } else {
 #pragma unroll
             for (int w = 0; w < W; w++) s[w] = 0;
-            for (int g = 1; g < ng; g++) idx[g] = -1;
         }
+#pragma unroll
+        for (int g = 1; g < SF_BR_MAXG; g++)
+            idx[g] = (act && g < ng) ? index_find_xor<W>(d, in_buf, Tin, tag_in, s, P.u[g]) : -1;
         double2 amps[SF_BR_MAXG];
         unsigned keepm = 0;
-        for (int g = 0; g < ng; g++) {
+#pragma unroll
+        for (int g = 0; g < SF_BR_MAXG; g++) {
+            amps[g] = make_double2(0.0, 0.0);
+            if (g >= ng) continue;
             bool own = act;
-            for (int g2 = 0; g2 < g; g2++) own &= idx[xidx[g][g2]] < 0;
+#pragma unroll
+            for (int g2 = 0; g2 < g; g2++) own &= pick_idx(idx, xidx[g][g2]) < 0;
             double2 amp = make_double2(0.0, 0.0);
             if (own) {
-                for (int g2 = 0; g2 < ng; g2++) {
+#pragma unroll
+                for (int g2 = 0; g2 < SF_BR_MAXG; g2++) {
+                    if (g2 >= ng) continue;
                     const int m = xidx[g][g2];
-                    if (idx[m] < 0) continue;
-                    const double2 ap = m == 0 ? a : Ai[idx[m]];
+                    const long long im = pick_idx(idx, m);
+                    if (im < 0) continue;
+                    const double2 ap = m == 0 ? a : Ai[im];
                     int pat = 0;  // sign pattern of the parent tau ^ u_g2 = s ^ u_m
                     for (int t = 0; t < P.nt[g2]; t++) {
                         int c = 0;
@@ -1237,7 +1270,8 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
         }
         // one reservation per iteration for all kept outputs of the block
         unsigned long long o = block_out_range(d.ocnt, __popc(keepm), wsum, &bbase);
-        for (int g = 0; g < ng; g++) {
+#pragma unroll
+        for (int g = 0; g < SF_BR_MAXG; g++) {
             if (!((keepm >> g) & 1u)) continue;
             if constexpr (sf_emit_index(W)) {
                 uint64_t tau[W];
@@ -1449,7 +1483,7 @@ template <int W>
 __device__ __forceinline__ void cof_scalars(const CofLR<W>& C, const uint64_t* s, const uint64_t* m, CofScal& E) {
     uint64_t v[W];
 #pragma unroll
-    for (int w = 0; w < W; w++) v[w] = s[w] ^ *(const volatile uint64_t*)&m[w];
+    for (int w = 0; w < W; w++) v[w] = m ? s[w] ^ *(const volatile uint64_t*)&m[w] : s[w];
     E.pq = popc_and_sh<W>(C.vq, v) & 1;
     E.pe = popc_and_sh<W>(C.eps0, v) + 2 * popc_and_sh<W>(C.eps1, v);
     E.pw[0] = popc_and_sh<W>(C.om[0], v) & 1;
@@ -1562,8 +1596,7 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
             // k_cof_lowrank); only their amplitudes differ
             CofScal es, ep;
             if (own) {
-                const uint64_t zero[W] = {};
-                cof_scalars<W>(CP, s, zero, es);
+                cof_scalars<W>(CP, s, nullptr, es);  // m in shared memory, or null for m = 0
                 if (l >= 0) cof_scalars<W>(CP, s, uq, ep);
                 cof_t0<W>(CP, s);  // s now holds t0; the child x is tau_{x ^ pq} ^ t0
             }
