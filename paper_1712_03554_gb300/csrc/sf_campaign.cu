@@ -596,23 +596,34 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                 const bool act = j < k;
                 uint64_t s = 0;
                 double2 a = make_double2(0.0, 0.0);
-                int id[4] = {act ? (int)j : -1, -1, -1, -1};
+                // group loops unrolled with guards and id read through pick_grp,
+                // so that id and amps stay in registers
+                int id[SF_BR_MAXG] = {act ? (int)j : -1, -1, -1, -1};
                 if (act) {
                     s = si[j];
                     a = ai[j];
-                    for (int g = 1; g < ng; g++) id[g] = lookup(si, k, s ^ P.u[g]);
                 }
-                double2 amps[4];
+#pragma unroll
+                for (int g = 1; g < SF_BR_MAXG; g++)
+                    if (act && g < ng) id[g] = lookup(si, k, s ^ P.u[g]);
+                double2 amps[SF_BR_MAXG];
                 unsigned keepm = 0;
-                for (int g = 0; g < ng; g++) {
+#pragma unroll
+                for (int g = 0; g < SF_BR_MAXG; g++) {
+                    amps[g] = make_double2(0.0, 0.0);
+                    if (g >= ng) continue;
                     bool own = act;
-                    for (int g2 = 0; g2 < g; g2++) own &= id[P.xidx[g][g2]] < 0;
+#pragma unroll
+                    for (int g2 = 0; g2 < g; g2++) own &= pick_grp(id, P.xidx[g][g2]) < 0;
                     double2 amp = make_double2(0.0, 0.0);
                     if (own) {
-                        for (int g2 = 0; g2 < ng; g2++) {
+#pragma unroll
+                        for (int g2 = 0; g2 < SF_BR_MAXG; g2++) {
+                            if (g2 >= ng) continue;
                             const int m = P.xidx[g][g2];
-                            if (id[m] < 0) continue;
-                            const double2 ap = m == 0 ? a : ai[id[m]];
+                            const int im = pick_grp(id, m);
+                            if (im < 0) continue;
+                            const double2 ap = m == 0 ? a : ai[im];
                             cmul_acc(amp, half_coef(P, ctab, g2, s ^ P.u[m]), ap);
                         }
                     }
@@ -621,7 +632,8 @@ __device__ __forceinline__ unsigned long long run_ops(Shared& S, Row* r, int n, 
                     else if (own) drop = true;
                 }
                 unsigned long long o = block_scan_advance(S, __popc(keepm));
-                for (int g = 0; g < ng; g++) {
+#pragma unroll
+                for (int g = 0; g < SF_BR_MAXG; g++) {
                     if (!((keepm >> g) & 1u)) continue;
                     sigb[ob][o] = s ^ P.u[g];
                     ampb[ob][o] = amps[g];

@@ -37,7 +37,10 @@ __device__ int elem_amp_phi(const SfDev& d, const uint64_t* s, const uint64_t* y
     pauli_id<W>(p);
     for (int R = 0; R < r; R++) {
         const int pv = __ldg(&d.piv[R]);
-        if ((wv[pv >> 6] >> (pv & 63)) & 1) {
+        uint64_t wpv = 0;  // wv[pv >> 6] by masks: a run-time subscript would put wv in local memory
+#pragma unroll
+        for (int u = 0; u < W; u++) wpv |= wv[u] & (0ull - (uint64_t)(u == (pv >> 6)));
+        if ((wpv >> (pv & 63)) & 1) {
             Pauli<W> m;
 #pragma unroll
             for (int u = 0; u < W; u++) { m.x[u] = __ldg(&d.mx[u * n + R]); m.z[u] = __ldg(&d.mz[u * n + R]); }

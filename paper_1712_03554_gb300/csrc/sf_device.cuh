@@ -122,6 +122,16 @@ __host__ __device__ inline size_t plan_t(int n, int W) { return (size_t)n * W; }
 // at most four Z-type Pauli terms per diagonal gate, grouped by anticommutation mask
 #define SF_BR_MAXG 4
 #define SF_BR_MAXT 4
+
+// v[m] for m in [0, SF_BR_MAXG) by masks: a run-time subscript into a small
+// per-thread array puts the array in local memory
+template <typename T>
+__device__ __forceinline__ T pick_grp(const T* v, int m) {
+    T r = 0;
+#pragma unroll
+    for (int g = 0; g < SF_BR_MAXG; g++) r |= v[g] & (T)(0 - (T)(g == m));
+    return r;
+}
 // cofactor plan
 __host__ __device__ inline size_t plan_cf(int n, int W) { return (size_t)n * W + W; }
 // cofactor: u'[n][W], v'[n][W], eps i-powers as two bit planes [2][W], kappa[4] doubles, tau0[W], tau1[W], v[W]

@@ -1087,7 +1087,9 @@ __global__ void __launch_bounds__(kThreads) k_filter(SfDev d, int x, int in_buf,
         uint64_t s[W];
         if (j < k) {
             load_sig<W>(Si, cap, j, s);
-            keep = (int)((s[R >> 6] >> (R & 63)) & 1) == x;
+            // the word of row R loaded once more (an L1 hit): s[R >> 6] would put s
+            // in local memory
+            keep = (int)((Si[(size_t)(R >> 6) * cap + j] >> (R & 63)) & 1) == x;
         }
         const unsigned bal = __ballot_sync(SF_FULL, keep);
         if (bal) {
@@ -1141,14 +1143,6 @@ __global__ void __launch_bounds__(kThreads) k_build_index(SfDev d, int b) {
 // s such that no tau ^ u_g' with g' < g is in the frame; its amplitude sums the
 // contributions of every parent tau ^ u_g'' found through the index of in_buf,
 // in a fixed order.  No amplitude atomics; the output frame is indexed.
-// idx[m] for m in [0, SF_BR_MAXG) by masks, with no run-time subscript
-__device__ __forceinline__ long long pick_idx(const long long* idx, int m) {
-    long long r = 0;
-#pragma unroll
-    for (int g = 0; g < SF_BR_MAXG; g++) r |= idx[g] & -(long long)(g == m);
-    return r;
-}
-
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kind, uint32_t q0, uint32_t q1,
                                                            SfTerms tm, double eps2, int in_buf, int out_buf) {
@@ -1223,7 +1217,7 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
         uint64_t s[W];
         double2 a = make_double2(0.0, 0.0);
         // the loops over groups are unrolled over SF_BR_MAXG with guards, and
-        // idx is read through pick_idx, so that idx, amps and s stay in
+        // idx is read through pick_grp, so that idx, amps and s stay in
         // registers (a run-time subscript would put them in local memory)
         long long idx[SF_BR_MAXG];
         idx[0] = act ? (long long)j : -1;
@@ -1245,14 +1239,14 @@ __global__ void __launch_bounds__(kThreads) k_branch_merge(SfDev d, uint32_t kin
             if (g >= ng) continue;
             bool own = act;
 #pragma unroll
-            for (int g2 = 0; g2 < g; g2++) own &= pick_idx(idx, xidx[g][g2]) < 0;
+            for (int g2 = 0; g2 < g; g2++) own &= pick_grp(idx, xidx[g][g2]) < 0;
             double2 amp = make_double2(0.0, 0.0);
             if (own) {
 #pragma unroll
                 for (int g2 = 0; g2 < SF_BR_MAXG; g2++) {
                     if (g2 >= ng) continue;
                     const int m = xidx[g][g2];
-                    const long long im = pick_idx(idx, m);
+                    const long long im = pick_grp(idx, m);
                     if (im < 0) continue;
                     const double2 ap = m == 0 ? a : Ai[im];
                     int pat = 0;  // sign pattern of the parent tau ^ u_g2 = s ^ u_m

@@ -1572,23 +1572,34 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 const bool act = j < hi;
                 uint64_t s = 0;
                 double2 a = make_double2(0.0, 0.0);
-                long long id[4] = {act ? (long long)j : -1, -1, -1, -1};
+                // group loops unrolled with guards and id read through pick_grp,
+                // so that id and amps stay in registers
+                long long id[SF_BR_MAXG] = {act ? (long long)j : -1, -1, -1, -1};
                 if (act) {
                     s = __ldcg(&Si[j]);
                     a = __ldcg(&Ai[j]);
-                    for (int g = 1; g < ng; g++) id[g] = gp_find(d, in, Tin, tag_in, s ^ P.u[g]);
                 }
-                double2 amps[4];
+#pragma unroll
+                for (int g = 1; g < SF_BR_MAXG; g++)
+                    if (act && g < ng) id[g] = gp_find(d, in, Tin, tag_in, s ^ P.u[g]);
+                double2 amps[SF_BR_MAXG];
                 unsigned keepm = 0;
-                for (int g = 0; g < ng; g++) {
+#pragma unroll
+                for (int g = 0; g < SF_BR_MAXG; g++) {
+                    amps[g] = make_double2(0.0, 0.0);
+                    if (g >= ng) continue;
                     bool own = act;
-                    for (int g2 = 0; g2 < g; g2++) own &= id[P.xidx[g][g2]] < 0;
+#pragma unroll
+                    for (int g2 = 0; g2 < g; g2++) own &= pick_grp(id, P.xidx[g][g2]) < 0;
                     double2 amp = make_double2(0.0, 0.0);
                     if (own) {
-                        for (int g2 = 0; g2 < ng; g2++) {
+#pragma unroll
+                        for (int g2 = 0; g2 < SF_BR_MAXG; g2++) {
+                            if (g2 >= ng) continue;
                             const int m = P.xidx[g][g2];
-                            if (id[m] < 0) continue;
-                            const double2 ap = m == 0 ? a : __ldcg(&Ai[id[m]]);
+                            const long long im = pick_grp(id, m);
+                            if (im < 0) continue;
+                            const double2 ap = m == 0 ? a : __ldcg(&Ai[im]);
                             cmul_acc(amp, half_coef(P, ctab, g2, s ^ P.u[m]), ap);
                         }
                     }
@@ -1598,7 +1609,8 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 }
                 unsigned long long o = block_out_range(ctr, __popc(keepm), wsum, &bbase);
                 const uint64_t sn = aff && act ? affine_of(s) : s;  // the parent in the new coordinates
-                for (int g = 0; g < ng; g++) {
+#pragma unroll
+                for (int g = 0; g < SF_BR_MAXG; g++) {
                     if (!((keepm >> g) & 1u)) continue;
                     const uint64_t tau = sn ^ P0.u[g];
                     So[o] = tau;
