@@ -1529,6 +1529,91 @@ __device__ __forceinline__ double2 cof_amp_lr(const CofLR<W>& C, const CofScal& 
     return ipow_mul(cmul(C.kap[y], a), ip & 3);
 }
 
+// The partner's scalars from the element's.  Every scalar of the closed form
+// is linear in the phase vector v except the ordered part Q, which is a sum of
+// bilinear forms f_j(a, b) = parity(a & cv_j & xpp(b & K_j)) at a = b = v, so
+// for v = s ^ u
+//   Q(s ^ u) = Q(s) ^ Q(u) ^ parity(s & Wu),
+//   Wu = sum_j [cv_j & xpp(u & K_j)  ^  K_j & spp(u & cv_j)],
+// with xpp (spp) the parity of the bits strictly below (above) each bit: the
+// second term is f_j(u, s) rewritten by exchanging the two sums over bits.
+// The count |(s ^ u) & eps0| is |s & eps0| + |u & eps0| - 2 |s & u & eps0|.
+template <int W>
+struct CofPart {
+    uint64_t wu[W], ue0[W];
+    int qu, pqu, peu, pwu[2];
+};
+
+// warp 0: the per-mask constants of the partner rule for u = uq
+template <int W>
+__device__ __noinline__ void cof_partner_setup(const CofLR<W>& C, const uint64_t* u, CofPart<W>& P) {
+    const int lane = threadIdx.x & 31;
+    uint64_t acc[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) acc[w] = 0ull;
+    int qj = 0;
+    if (lane < C.rv) {
+        const int j = lane;
+        uint64_t carry = 0ull;  // parity of the lower words of u & K_j, as a full word
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            uint64_t x = u[w] & C.K[j][w];  // inclusive prefix parity within the word
+            x ^= x << 1;
+            x ^= x << 2;
+            x ^= x << 4;
+            x ^= x << 8;
+            x ^= x << 16;
+            x ^= x << 32;
+            const uint64_t xp = (x << 1) ^ carry;  // strictly below
+            acc[w] ^= C.cv[j][w] & xp;
+            qj ^= __popcll(u[w] & C.cv[j][w] & xp) & 1;
+            carry ^= (x >> 63) ? ~0ull : 0ull;
+        }
+        carry = 0ull;  // parity of the higher words of u & cv_j
+#pragma unroll
+        for (int w = W - 1; w >= 0; w--) {
+            uint64_t y = u[w] & C.cv[j][w];  // inclusive suffix parity within the word
+            y ^= y >> 1;
+            y ^= y >> 2;
+            y ^= y >> 4;
+            y ^= y >> 8;
+            y ^= y >> 16;
+            y ^= y >> 32;
+            const uint64_t sp = (y >> 1) ^ carry;  // strictly above
+            acc[w] ^= C.K[j][w] & sp;
+            carry ^= (y & 1ull) ? ~0ull : 0ull;
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        const unsigned lo = __reduce_xor_sync(SF_FULL, (unsigned)acc[w]);
+        const unsigned hi = __reduce_xor_sync(SF_FULL, (unsigned)(acc[w] >> 32));
+        if (lane == 0) {
+            P.wu[w] = (uint64_t)lo | ((uint64_t)hi << 32);
+            P.ue0[w] = u[w] & C.eps0[w];
+        }
+    }
+    const int q = __reduce_xor_sync(SF_FULL, (unsigned)qj) & 1;
+    if (lane == 0) {
+        P.qu = q;
+        P.pqu = popc_and<W>(C.vq, u) & 1;
+        P.peu = (popc_and<W>(C.eps0, u) + 2 * popc_and<W>(C.eps1, u)) & 3;
+        P.pwu[0] = popc_and<W>(C.om[0], u) & 1;
+        P.pwu[1] = popc_and<W>(C.om[1], u) & 1;
+    }
+}
+
+// the partner's scalars (v = s ^ u) from the element's (v = s)
+template <int W>
+__device__ __forceinline__ void cof_scalars_partner(const CofPart<W>& P, const uint64_t* s, const CofScal& es,
+                                                    CofScal& ep) {
+    ep.pq = es.pq ^ P.pqu;
+    ep.pe = es.pe + P.peu + 2 * (popc_and_sh<W>(P.ue0, s) & 1);
+    ep.pw[0] = es.pw[0] ^ P.pwu[0];
+    ep.pw[1] = es.pw[1] ^ P.pwu[1];
+    ep.q = es.q ^ P.qu ^ (popc_and_sh<W>(P.wu, s) & 1);
+}
+
 template <int W, bool LR>
 __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, double eps2, int in_buf, int out_buf) {
     using Plan = typename std::conditional<LR, CofLR<W>, CofPlan<W>>::type;
@@ -1536,6 +1621,7 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
     __shared__ uint64_t uq[W];
     __shared__ unsigned int wsum[kThreads / 32];
     __shared__ unsigned long long bbase;
+    __shared__ CofPart<W> PP;  // LR: the partner rule's constants
     if (*d.status) return;
     if (!d.meta[2]) return;
     if constexpr (W >= 8) {
@@ -1545,6 +1631,8 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
     if constexpr (LR) {
         load_cof_lr<W>(d, CP);
         if (threadIdx.x < W) uq[threadIdx.x] = d.plan[cf_uq(d.n, W) + threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x < 32) cof_partner_setup<W>(CP, uq, PP);
     } else if (threadIdx.x == 0) {
         load_cof_plan<W>(d, CP);
         for (int w = 0; w < W; w++) uq[w] = d.plan[cf_uq(d.n, W) + w];
@@ -1590,8 +1678,8 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
             // k_cof_lowrank); only their amplitudes differ
             CofScal es, ep;
             if (own) {
-                cof_scalars<W>(CP, s, nullptr, es);  // m in shared memory, or null for m = 0
-                if (l >= 0) cof_scalars<W>(CP, s, uq, ep);
+                cof_scalars<W>(CP, s, nullptr, es);
+                if (l >= 0) cof_scalars_partner<W>(PP, s, es, ep);
                 cof_t0<W>(CP, s);  // s now holds t0; the child x is tau_{x ^ pq} ^ t0
             }
             for (int x = 0; x < 2; x++) {
