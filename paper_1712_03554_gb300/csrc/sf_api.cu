@@ -876,8 +876,8 @@ sf_status sf_measure(sf_handle h, uint32_t q, int32_t collapse_to, double* p0, d
     bool prob_done = false;
     sf_status st = cofactor_q(h, q, &prob_done);
     if (st) return st;
+    // the probabilities' last CTA (or the positional cofactor's) leaves them in d.out
     if (!prob_done) SF_LAUNCH(h, SF_K_PROB, sf_launch_prob(h->d, h->cur, h->stream));
-    SF_LAUNCH(h, SF_K_REDUCE, sf_launch_reduce_final(h->d, 0, h->stream));
     SF_CK(h, cudaMemcpyAsync(h->hout, h->d.out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     st = sync_check(h);
     if (st) return st;
@@ -903,8 +903,7 @@ sf_status sf_amplitude(sf_handle h, const uint64_t* x_bits, double* re, double* 
     if (h->n % 64) h->hy[h->Wabi - 1] &= (1ull << (h->n % 64)) - 1ull;
     SF_CK(h, cudaMemcpyAsync(h->dy, h->hy, W * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
     SF_LAUNCH(h, SF_K_AMP_PREP, sf_launch_amp_prep(h->d, h->dy, h->stream));
-    SF_LAUNCH(h, SF_K_AMPLITUDE, sf_launch_amplitude(h->d, h->cur, h->stream));
-    SF_LAUNCH(h, SF_K_REDUCE, sf_launch_reduce_final(h->d, 1, h->stream));
+    SF_LAUNCH(h, SF_K_AMPLITUDE, sf_launch_amplitude(h->d, h->cur, h->stream));  // its last CTA sums
     SF_CK(h, cudaMemcpyAsync(h->hout, h->d.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     sf_status st = sync_check(h);
     if (st) return st;
@@ -1612,7 +1611,6 @@ sf_status sf_mf_amplitude(sf_multiframe m, const uint64_t* x_bits, double* re, d
         MF_CK(m, cudaMemcpyAsync(F->dy, F->hy, sizeof(uint64_t), cudaMemcpyHostToDevice, m->stream));
         MF_TRY(m, F, launch(F, SF_K_AMP_PREP, "amp_prep", [&] { sf_launch_amp_prep(F->d, F->dy, m->stream); }));
         MF_TRY(m, F, launch(F, SF_K_AMPLITUDE, "amplitude", [&] { sf_launch_amplitude(F->d, F->cur, m->stream); }));
-        MF_TRY(m, F, launch(F, SF_K_REDUCE, "reduce", [&] { sf_launch_reduce_final(F->d, 1, m->stream); }));
         MF_CK(m, cudaMemcpyAsync(F->hout, F->d.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
     }
     std::vector<uint64_t> k;

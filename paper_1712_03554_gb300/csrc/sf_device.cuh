@@ -600,7 +600,6 @@ void sf_launch_cof_pos(const SfDev& d, int in_buf, int out_buf, bool prob, cudaS
 void sf_launch_filter(const SfDev& d, int x, int in_buf, int out_buf, cudaStream_t s);
 void sf_launch_cond(const SfDev& d, int buf, int kind, int c1, int c2, int t, double alpha, cudaStream_t s);
 void sf_launch_prob(const SfDev& d, int buf, cudaStream_t s);
-void sf_launch_reduce_final(const SfDev& d, int what, cudaStream_t s);
 void sf_launch_amplitude(const SfDev& d, int buf, cudaStream_t s);
 void sf_launch_export(const SfDev& d, int buf, int stage_buf, cudaStream_t s);
 size_t sf_affine_smem_bytes(int n, int W);

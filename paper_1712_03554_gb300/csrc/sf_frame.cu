@@ -63,6 +63,32 @@ __device__ void block_sum(double* v, double (*sh)[32]) {
     }
 }
 
+// Fixed-order sum of the per-CTA partials d.red[2b], d.red[2b + 1] over the
+// grid, by the last CTA to finish (all its threads; every CTA wrote its
+// partials before counting itself done).  what 0: probabilities -> out[0..1];
+// what 1: amplitude -> out[2..3], scaled by g 2^{-r/2}.
+__device__ void reduce_partials(const SfDev& d, int what, double (*sh)[32]) {
+    double v[2] = {0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        v[0] += __ldcg(&d.red[2 * b]);
+        v[1] += __ldcg(&d.red[2 * b + 1]);
+    }
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0) {
+        if (what == 0) {
+            d.out[0] = v[0];
+            d.out[1] = v[1];
+        } else {
+            // 2^{-r/2} exactly: a power of two, times 1/sqrt(2) for odd r
+            const int r = d.meta[0];
+            const double sc = ldexp(1.0, -((r + 1) >> 1)) * ((r & 1) ? 1.41421356237309504880 : 1.0);
+            const double2 c = cmul(*d.g, make_double2(v[0] * sc, v[1] * sc));
+            d.out[2] = c.x;
+            d.out[3] = c.y;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // sigma' = A sigma ^ t via 4-bit chunk tables: tab[c][w][v] = (A restricted
 // to columns 4c..4c+3) applied to v, word w.  16 consecutive words per (c,w)
@@ -1763,9 +1789,9 @@ __global__ void __launch_bounds__(kThreads, LR ? 2 : 1) k_cof_merge(SfDev d, dou
 // prep builds it), so a child amplitude is sc i^{e_y + ip_y} a: an exact
 // rotation, the partners' two summed, then one real scaling.  Does nothing
 // when the layout is not known (the host checks that before it launches it).
-// With prob set it also leaves what k_prob computes: per CTA, the summed
-// |a|^2 of the children it keeps, split by their bit on row meta[1] (the
-// measured qubit's row), for k_reduce_final.
+// With prob set it also does what k_prob does: per CTA, the summed |a|^2 of
+// the children it keeps, split by their bit on row meta[1] (the measured
+// qubit's row), summed over the grid by the last CTA into d.out[0..1].
 __global__ void __launch_bounds__(kThreads) k_cof_pos(SfDev d, double eps2, int in_buf, int out_buf, int prob) {
     __shared__ uint64_t sU[64], sV[64];
     __shared__ unsigned int wsum[kThreads / 32];
@@ -1952,9 +1978,12 @@ __global__ void __launch_bounds__(kThreads) k_cof_pos(SfDev d, double eps2, int 
             d.red[2 * blockIdx.x + 1] = pr[1];
         }
     }
-    if (last_block(d.done) && threadIdx.x == 0) {
-        d.kcnt[out_buf] = *d.ocnt;
-        *d.ocnt = 0;
+    if (last_block(d.done)) {
+        if (threadIdx.x == 0) {
+            d.kcnt[out_buf] = *d.ocnt;
+            *d.ocnt = 0;
+        }
+        if (prob) reduce_partials(d, 0, shp);
     }
 }
 
@@ -1998,6 +2027,7 @@ __global__ void __launch_bounds__(kThreads) k_prob(SfDev d, int buf) {
         d.red[2 * blockIdx.x] = p[0];
         d.red[2 * blockIdx.x + 1] = p[1];
     }
+    if (last_block(d.done)) reduce_partials(d, 0, sh);
 }
 
 template <int W>
@@ -2108,31 +2138,7 @@ __global__ void __launch_bounds__(kThreads) k_amplitude(SfDev d, int buf) {
         d.red[2 * blockIdx.x] = acc[0];
         d.red[2 * blockIdx.x + 1] = acc[1];
     }
-}
-
-// fixed-order sum of the per-CTA partials.  what 0: probabilities -> out[0..1];
-// what 1: amplitude -> out[2..3] scaled by g 2^{-r/2}.
-__global__ void k_reduce_final(SfDev d, int what) {
-    __shared__ double sh[2][32];
-    double v[2] = {0.0, 0.0};
-    for (int b = threadIdx.x; b < d.nblk; b += blockDim.x) {
-        v[0] += d.red[2 * b];
-        v[1] += d.red[2 * b + 1];
-    }
-    block_sum<2>(v, sh);
-    if (threadIdx.x == 0) {
-        if (what == 0) {
-            d.out[0] = v[0];
-            d.out[1] = v[1];
-        } else {
-            // 2^{-r/2} exactly: a power of two, times 1/sqrt(2) for odd r
-            const int r = d.meta[0];
-            const double sc = ldexp(1.0, -((r + 1) >> 1)) * ((r & 1) ? 1.41421356237309504880 : 1.0);
-            const double2 c = cmul(*d.g, make_double2(v[0] * sc, v[1] * sc));
-            d.out[2] = c.x;
-            d.out[3] = c.y;
-        }
-    }
+    if (last_block(d.done)) reduce_partials(d, 1, sh);
 }
 
 template <int W>
@@ -2259,8 +2265,6 @@ void sf_launch_prob(const SfDev& d, int buf, cudaStream_t s) {
     SF_DISPATCH(d.W, k_prob<WW><<<d.nblk, kThreads, 0, s>>>(d, buf));
 }
 
-// 128 threads: one warp per SM sub-partition, whose FP64 pipe does the sums
-void sf_launch_reduce_final(const SfDev& d, int what, cudaStream_t s) { k_reduce_final<<<1, 128, 0, s>>>(d, what); }
 
 void sf_launch_amplitude(const SfDev& d, int buf, cudaStream_t s) {
     SF_DISPATCH(d.W, k_amplitude<WW><<<d.nblk, kThreads, 0, s>>>(d, buf));
