@@ -409,6 +409,15 @@ sf_status sf_grid_program_bytes(sf_handle h, uint64_t* bytes);
 sf_status sf_set_trace(sf_handle h, int32_t on);
 sf_status sf_grid_program_trace(sf_handle h, uint64_t* rec, uint32_t cap, uint32_t* n);
 
+/* The planning CTAs of the last traced launch (the tableau CTA applies each
+ * step's Clifford run, the plan CTA plans its diagonal records): for planning
+ * steps 0..cap-1, 8 times each (global nanosecond timer, 0 where not reached):
+ * the tableau CTA's start of the step and its publication; the plan CTA's take
+ * of the step's tableau, end of its copy, end of the plans, end of the runs'
+ * extents and hull map, end of the hull walk and verdicts, its publication.
+ * Synchronises. */
+sf_status sf_grid_program_plan_trace(sf_handle h, uint64_t* rec, uint32_t cap);
+
 /* Bounded device waits: a grid barrier of sf_apply_program_grid polls at most
  * `polls` times, about 100 ns apart, before the launch gives up with
  * SF_ETIMEOUT (every CTA leaves at its next barrier; no kernel waits without

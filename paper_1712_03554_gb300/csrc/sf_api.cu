@@ -770,6 +770,16 @@ sf_status sf_grid_program_trace(sf_handle h, uint64_t* rec, uint32_t cap, uint32
     return SF_OK;
 }
 
+sf_status sf_grid_program_plan_trace(sf_handle h, uint64_t* rec, uint32_t cap) {
+    if (!h || (cap && !rec)) return fail(h, SF_EINVAL, "NULL argument");
+    if (!h->d.gp) return fail(h, SF_EINVAL, "no grid program on this handle (n_qubits > 63)");
+    sf_status st = sync_check(h);
+    if (st) return st;
+    SF_CK(h, sf_gprog_plan_marks(h->d, rec, cap, h->stream));
+    SF_CK(h, cudaStreamSynchronize(h->stream));
+    return SF_OK;
+}
+
 sf_status sf_set_wait_limit(sf_handle h, uint32_t polls) {
     if (!h) return fail(nullptr, SF_EINVAL, "NULL handle");
     h->wait_limit = polls;

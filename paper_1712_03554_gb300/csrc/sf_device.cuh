@@ -581,6 +581,7 @@ cudaError_t sf_launch_gprog(const SfDev& d, const void* ops, unsigned long long 
                             unsigned long long* consumed, cudaStream_t s);
 cudaError_t sf_gprog_trace(const SfDev& d, uint64_t* host, unsigned cap, unsigned* n, cudaStream_t s);
 cudaError_t sf_gprog_marks(const SfDev& d, uint64_t* host, unsigned m, cudaStream_t s);
+cudaError_t sf_gprog_plan_marks(const SfDev& d, uint64_t* host, unsigned m, cudaStream_t s);
 size_t sf_tableau_smem_bytes(int n, int W, int NT);
 
 void sf_launch_affine(const SfDev& d, int buf, cudaStream_t s);

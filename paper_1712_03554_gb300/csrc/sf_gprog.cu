@@ -125,6 +125,11 @@ struct GpWork {
     // start and arrival time, the last arrival's time and CTA (ns, %globaltimer)
     uint64_t trace[kGpTrace][5];
     uint64_t marks[kGpTrace][8];  // checkpoints inside each traced phase (CTA 0)
+    // per planning step of a traced launch (%globaltimer, thread 0 of the planning
+    // CTAs): the tableau CTA's start and publication of the step, then the plan
+    // CTA's take of the tableau, copy done, plans done, runs' ends and hull map
+    // done, hull walk and verdicts done, publication
+    uint64_t pmarks[kGpTrace][8];
     GpSet ring[kGpRing];
     GpTabSet tring[kGpRing];
 };
@@ -171,6 +176,11 @@ __device__ __forceinline__ void gp_mark(GpWork* w, int i) {
         const unsigned ti = s_phase - s_gen0;
         if (ti < (unsigned)kGpTrace) w->marks[ti][i] = gtimer();
     }
+}
+
+// checkpoint i of planning step st (traced launches, thread 0 of a planning CTA)
+__device__ __forceinline__ void gp_pmark(GpWork* w, unsigned st, int i) {
+    if (s_trace && threadIdx.x == 0 && st < (unsigned)kGpTrace) w->pmarks[st][i] = gtimer();
 }
 
 // the phase about to end ran `code` over k elements (traced launches, CTA 0)
@@ -267,6 +277,22 @@ __device__ __forceinline__ void hull_add(uint64_t* hc, uint64_t u) {
     if (o1) c1 ^= cp;
     hc[lane] = c0;
     hc[lane + 32] = c1;
+}
+
+// The same on constraints held in registers by warp 0 (lane i: constraints i
+// and i + 32), for a walk that tests and grows the hull many times in a row.
+__device__ __forceinline__ bool hull_fresh_r(uint64_t c0, uint64_t c1, uint64_t u) {
+    const bool odd = (__popcll(c0 & u) & 1) | (__popcll(c1 & u) & 1);
+    return __any_sync(SF_FULL, odd);
+}
+__device__ __forceinline__ void hull_add_r(uint64_t& c0, uint64_t& c1, uint64_t u) {
+    const bool o0 = __popcll(c0 & u) & 1, o1 = __popcll(c1 & u) & 1;
+    const unsigned b0 = __ballot_sync(SF_FULL, o0), b1 = __ballot_sync(SF_FULL, o1);
+    if (!(b0 | b1)) return;
+    const int p = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+    const uint64_t cp = __shfl_sync(SF_FULL, p < 32 ? c0 : c1, p & 31);
+    if (o0) c0 ^= cp;
+    if (o1) c1 ^= cp;
 }
 
 // position of key in the index of buffer b (written in this launch), or -1.
@@ -717,6 +743,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 }
                 const unsigned e = tset % kGpRing;
                 if (tset >= kGpRing && !wait_u32(&w->tring_readers[e], 1u)) return;
+                gp_pmark(w, tset, 0);
                 GpTabSet* T = &w->tring[e];
                 int np = 0;
                 unsigned long long oe = poi, ds = poi;
@@ -764,6 +791,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                     __threadfence();
                     st_release64(&w->tring_seq[e], (unsigned long long)tset + 1ull);
                 }
+                gp_pmark(w, tset, 1);
                 tset++;
                 if (tk >= 2) break;
                 poi = ds + np;
@@ -788,6 +816,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             }
             __syncthreads();
             if (!s_uni) return;
+            gp_pmark(w, pset, 2);
             const GpTabSet* T = &w->tring[te];
             {
                 const uint64_t* src = reinterpret_cast<const uint64_t*>(&T->tab);
@@ -803,6 +832,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             if (threadIdx.x == 0) s_t = __ldcg(&T->t);
             __syncthreads();
             if (threadIdx.x == 0) atomicAdd(&w->tring_readers[te], 1u);
+            gp_pmark(w, pset, 3);
             if (tk == 3) return;  // the workers stop at the same record
             const unsigned e = pset % kGpRing;
             if (pset >= kGpRing && !wait_u32(&w->ring_readers[e], nw)) return;
@@ -811,6 +841,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 for (int r = warp; r < np; r += nwarps) gp_plan(s_tab, n, ops[ds + r], __ldcg(&trig[ds + r]), spl[r]);
                 __syncthreads();
             }
+            gp_pmark(w, pset, 4);
             if (tk == 0) {
                 // the hull moves with the run's map, as in the workers
                 const int i = threadIdx.x;
@@ -848,6 +879,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                     spl[r].rend = t2;
                 }
             }
+            gp_pmark(w, pset, 5);
             if (tk < 2 && warp == 0) {
                 // Per record: are its terms orthogonal to the hull where the workers
                 // apply it?  The hull is followed record by record as the workers
@@ -858,7 +890,11 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 // children all vanished, so it contains theirs and a yes is safe.
                 // Directions are only appended within a batch, so the walk records
                 // for each record how many of them it is checked against (lane 0
-                // keeps the count), and the checks then run one lane per record.
+                // keeps the count), and the checks then run on every warp.
+                // the constraints stay in registers for the walk (lane i: i, i + 32)
+                // and the direction count in lane 0's register
+                uint64_t c0 = s_hc[lane], c1 = s_hc[lane + 32];
+                int nhb = s_nhb;
                 uint64_t pend = 0;
                 bool have_pend = false;
                 for (int r = 0; r < np; r++) {
@@ -866,62 +902,65 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                     const uint64_t u1 = s_pu1[r];
                     const bool cont = have_pend && (ng == 1 || (ng == 2 && u1 == pend));
                     if (!cont && have_pend) {
-                        if (hull_fresh(s_hc, pend)) {
-                            hull_add(s_hc, pend);
-                            if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = pend;
-                            __syncwarp();
+                        if (hull_fresh_r(c0, c1, pend)) {
+                            hull_add_r(c0, c1, pend);
+                            if (lane == 0 && nhb < 64) s_hb[nhb] = pend;
+                            nhb += nhb < 64;
                         }
                         have_pend = false;
                     }
-                    if (lane == 0) s_pm[r] = s_nhb;  // directions the record is checked against
-                    __syncwarp();
+                    if (lane == 0) s_pm[r] = nhb;  // directions the record is checked against
                     if (cont) continue;
-                    if (ng == 2 && hull_fresh(s_hc, u1)) {
+                    if (ng == 2 && hull_fresh_r(c0, c1, u1)) {
                         pend = u1;
                         have_pend = true;
                     } else {
                         for (int g = 1; g < ng; g++) {
                             const uint64_t ug = spl[r].P.u[g];
-                            if (hull_fresh(s_hc, ug)) {
-                                hull_add(s_hc, ug);
-                                if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = ug;
-                                __syncwarp();
+                            if (hull_fresh_r(c0, c1, ug)) {
+                                hull_add_r(c0, c1, ug);
+                                if (lane == 0 && nhb < 64) s_hb[nhb] = ug;
+                                nhb += nhb < 64;
                             }
                         }
                     }
                 }
-                if (have_pend && hull_fresh(s_hc, pend)) {
-                    hull_add(s_hc, pend);
-                    if (lane == 0 && s_nhb < 64) s_hb[s_nhb++] = pend;
+                if (have_pend && hull_fresh_r(c0, c1, pend)) {
+                    hull_add_r(c0, c1, pend);
+                    if (lane == 0 && nhb < 64) s_hb[nhb] = pend;
+                    nhb += nhb < 64;
                 }
+                s_hc[lane] = c0;
+                s_hc[lane + 32] = c1;
+                if (lane == 0) s_nhb = nhb;
                 __syncwarp();
-                for (int r = lane; r < np; r += 32) {
+            }
+            __syncthreads();
+            if (tk < 2) {
+                // the verdicts, one record per warp and one hull direction per
+                // lane (the walk above fixed how many directions each record is
+                // checked against): a term fails when its parity with some
+                // direction is odd
+                for (int r = warp; r < np; r += nwarps) {
                     const BrTab& Q = spl[r].P;
                     const int ng = Q.ng, m = s_pm[r];
-                    int nt[4];
-                    uint64_t v[4][4];
-#pragma unroll
-                    for (int g = 0; g < 4; g++) {
-                        nt[g] = g < ng ? Q.nt[g] : 0;
-#pragma unroll
-                        for (int t = 0; t < 4; t++) v[g][t] = Q.v[g][t];
-                    }
-#pragma unroll
-                    for (int g = 0; g < 4; g++)
-#pragma unroll
-                        for (int t = 0; t < 4; t++)
-                            if (t >= nt[g]) v[g][t] = 0ull;
-                    uint64_t acc = 0;  // OR over the hull directions of each term's parity, one bit per term
-                    for (int i = 0; i < m; i++) {
+                    unsigned acc = 0;  // bit 4 g + t: term t of group g has odd parity with a direction
+                    for (int i = lane; i < m; i += 32) {
                         const uint64_t h = s_hb[i];
 #pragma unroll
-                        for (int g = 0; g < 4; g++)
+                        for (int g = 0; g < 4; g++) {
+                            const int nt = g < ng ? Q.nt[g] : 0;
 #pragma unroll
-                            for (int t = 0; t < 4; t++) acc |= (uint64_t)(__popcll(v[g][t] & h) & 1) << (4 * g + t);
+                            for (int t = 0; t < 4; t++)
+                                if (t < nt) acc |= (unsigned)(__popcll(Q.v[g][t] & h) & 1) << (4 * g + t);
+                        }
                     }
-                    spl[r].orth = acc == 0;
+                    acc = __reduce_or_sync(SF_FULL, acc);
+                    if (lane == 0) spl[r].orth = acc == 0;
                 }
-            }            __syncthreads();
+            }
+            __syncthreads();
+            gp_pmark(w, pset, 6);
             {
                 const uint64_t* src = reinterpret_cast<const uint64_t*>(&spl[0]);
                 uint64_t* dst = reinterpret_cast<uint64_t*>(&S->plans[0]);
@@ -948,6 +987,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
                 __threadfence();
                 st_release64(&w->ring_seq[e], (unsigned long long)pset + 1ull);
             }
+            gp_pmark(w, pset, 7);
             pset++;
             if (tk == 2) return;
         }
@@ -1707,6 +1747,14 @@ cudaError_t sf_gprog_marks(const SfDev& d, uint64_t* host, unsigned m, cudaStrea
     GpWork* w = reinterpret_cast<GpWork*>(d.gp);
     m = std::min(m, (unsigned)kGpTrace);
     return m ? cudaMemcpyAsync(host, &w->marks[0][0], m * 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s)
+             : cudaSuccess;
+}
+
+// the planning CTAs' checkpoints of the last traced launch (8 per step)
+cudaError_t sf_gprog_plan_marks(const SfDev& d, uint64_t* host, unsigned m, cudaStream_t s) {
+    GpWork* w = reinterpret_cast<GpWork*>(d.gp);
+    m = std::min(m, (unsigned)kGpTrace);
+    return m ? cudaMemcpyAsync(host, &w->pmarks[0][0], m * 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s)
              : cudaSuccess;
 }
 

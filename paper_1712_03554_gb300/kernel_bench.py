@@ -332,6 +332,30 @@ def qft_trace(seed=0, reps=3):
                       "moved_bytes": f.grid_program_bytes()}), flush=True)
     for r in rows:
         print(json.dumps(r), flush=True)
+    # the planning CTAs, per step: durations of each stage (us) and the gap
+    # between consecutive publications of the plan CTA
+    pt = f.grid_program_plan_trace(64).astype(np.int64)
+    t_ref = int(tr[0][1]) if len(tr) else 0
+    prev_pub = None
+    plan_rows = []
+    for st, m in enumerate(pt):
+        if not m.any():
+            continue
+        row = {"step": st,
+               "tableau_us": (m[1] - m[0]) / 1e3 if m[1] and m[0] else None,
+               "plan_wait_us": (m[2] - m[1]) / 1e3 if m[2] and m[1] else None,
+               "plan_copy_us": (m[3] - m[2]) / 1e3 if m[3] and m[2] else None,
+               "plans_us": (m[4] - m[3]) / 1e3 if m[4] and m[3] else None,
+               "extents_hull_map_us": (m[5] - m[4]) / 1e3 if m[5] and m[4] else None,
+               "walk_verdicts_us": (m[6] - m[5]) / 1e3 if m[6] and m[5] else None,
+               "publish_us": (m[7] - m[6]) / 1e3 if m[7] and m[6] else None,
+               "published_at_us": (m[7] - t_ref) / 1e3 if m[7] else None,
+               "since_last_publication_us": (m[7] - prev_pub) / 1e3 if m[7] and prev_pub else None}
+        if m[7]:
+            prev_pub = int(m[7])
+        plan_rows.append(row)
+    for r in plan_rows:
+        print(json.dumps({"plan": r}), flush=True)
     y = 12345
     print(json.dumps({"amp_err": abs(f.amplitude(y) - c.qft_expected_amplitude(20, x, y))}), flush=True)
 

@@ -81,6 +81,7 @@ def load(build: bool = True) -> C.CDLL:
         "sf_grid_program_bytes": ([H, P64], st),
         "sf_set_trace": ([H, C.c_int32], st),
         "sf_grid_program_trace": ([H, P64, u32, C.POINTER(C.c_uint32)], st),
+        "sf_grid_program_plan_trace": ([H, P64, u32], st),
         "sf_apply_toffoli": ([H, u32, u32, u32], st),
         "sf_apply_cr_cofactor": ([H, u32, u32, dbl], st),
         "sf_coalesce": ([H, dbl, P64], st),
@@ -600,6 +601,13 @@ class Frame:
         self._check(self.lib.sf_grid_program_trace(self.h, buf.ctypes.data_as(C.POINTER(C.c_uint64)), 512,
                                                    C.byref(n)), self.h)
         return buf[:n.value].copy()
+
+    def grid_program_plan_trace(self, steps: int = 64) -> np.ndarray:
+        """sf_grid_program_plan_trace: (steps, 8) uint64 stamps of the planning CTAs."""
+        buf = np.zeros((steps, 8), dtype=np.uint64)
+        self._check(self.lib.sf_grid_program_plan_trace(self.h, buf.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                                        steps), self.h)
+        return buf
 
     def set_wait_limit(self, polls: int) -> None:
         """sf_set_wait_limit: barrier polls of the grid program before it gives up."""
