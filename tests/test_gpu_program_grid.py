@@ -324,3 +324,33 @@ def test_grid_barrier_timeout_is_reported_and_the_handle_recovers(sfm):
     c.run(o, ops)
     frames_equal(f, o)
     f.close()
+
+
+def test_traced_launch_same_frame_and_ordered_stamps(sfm):
+    """A traced grid-program launch (sf_set_trace) gives the same frame as the
+    oracle; its phase records and the planning CTAs' per-step stamps
+    (sf_grid_program_plan_trace) are in time order: each step's tableau is
+    published after it starts, the plan CTA takes it after it is published,
+    and the plan CTA's stages follow one another."""
+    x, ops = c.qft_random_input(12, seed=3)
+    f = sfm.Frame(12, 1 << 13)
+    f.set_trace(True)
+    assert f.apply_program_grid(ops) == len(ops)
+    o = oracle.FrameOracle(12)
+    c.run(o, ops)
+    assert frames_equal(f, o) == 1 << 11
+    tr = f.grid_program_trace().astype(np.int64)
+    assert len(tr) >= 12
+    starts = tr[:, 1]
+    assert np.all(starts > 0) and np.all(np.diff(starts) >= 0)
+    assert np.all(tr[:, 2] >= tr[:, 1])
+    pt = f.grid_program_plan_trace(64).astype(np.int64)
+    steps = [m for m in pt if m[7]]  # steps the plan CTA published
+    assert len(steps) >= 11
+    for m in steps:
+        assert m[0] <= m[1] <= m[2], m
+        assert np.all(np.diff(m[2:8]) >= 0), m
+    pubs = [int(m[7]) for m in steps]
+    assert pubs == sorted(pubs)
+    f.set_trace(False)
+    f.close()
