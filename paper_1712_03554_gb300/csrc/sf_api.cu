@@ -25,7 +25,7 @@ struct sf_frame_s {
     size_t dgates_cap = 0;
     sf_gate_rec* hstage = nullptr;
     size_t hstage_cap = 0;
-    double2* dtrig = nullptr;   // e^{i theta} scratch of the grid program, one per record
+    double2* dtrig = nullptr;   // term coefficients of the grid program's diagonal records, four per record
     size_t dtrig_cap = 0;
     OpRec* dops = nullptr;      // program records copied by sf_run_program
     size_t dops_cap = 0;
@@ -591,7 +591,7 @@ sf_status sf_apply_program_grid(sf_handle h, const sf_op* dev_ops, uint64_t n_op
         if (dev_consumed) SF_CK(h, cudaMemsetAsync(dev_consumed, 0, sizeof(uint64_t), h->stream));
         return SF_OK;
     }
-    sf_status gs = grow_dev(h, &h->dtrig, h->dtrig_cap, n_ops);
+    sf_status gs = grow_dev(h, &h->dtrig, h->dtrig_cap, 4 * (size_t)n_ops);  // four term coefficients per record
     if (gs) return gs;
     cudaError_t ge = cudaSuccess;
     SF_LAUNCH(h, SF_K_GPROG,

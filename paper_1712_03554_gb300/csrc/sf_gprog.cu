@@ -435,9 +435,9 @@ __device__ unsigned long long gp_clifford_run(GpTab& T, const OpRec* ops, unsign
     return good ? gi : ~0ull;
 }
 
-// Plan of diagonal record o (one warp) from the CTA's tableau, with its
-// e^{i theta} = cs + i sn from the launch's table
-__device__ void gp_plan(const GpTab& T, int n, const OpRec& o, double2 trig, GpPlan& out) {
+// Plan of diagonal record o (one warp) from the CTA's tableau, with its four
+// term coefficients from the launch's table
+__device__ void gp_plan(const GpTab& T, int n, const OpRec& o, const double2* cf, GpPlan& out) {
     const int lane = threadIdx.x & 31;
     Row r[2];
     for (int hf = 0; hf < 2; hf++) {
@@ -450,8 +450,10 @@ __device__ void gp_plan(const GpTab& T, int n, const OpRec& o, double2 trig, GpP
         r[hf].de = in ? T.de[row] : 0;
     }
     const uint32_t kind = o.kind - SF_OP_DIAG;
-    const SfTerms Tm = diag_terms(kind, trig.x, trig.y);
-    warp_branch_plan_regs(r, n, kind, (int)o.q0, kind == 3 ? (int)o.q1 : 0, Tm.c, out.P, out.ctab);
+    double2 c[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) c[j] = __ldcg(&cf[j]);
+    warp_branch_plan_regs(r, n, kind, (int)o.q0, kind == 3 ? (int)o.q1 : 0, c, out.P, out.ctab);
     __syncwarp();
 }
 
@@ -838,7 +840,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             if (pset >= kGpRing && !wait_u32(&w->ring_readers[e], nw)) return;
             GpSet* S = &w->ring[e];
             if (tk < 2) {
-                for (int r = warp; r < np; r += nwarps) gp_plan(s_tab, n, ops[ds + r], __ldcg(&trig[ds + r]), spl[r]);
+                for (int r = warp; r < np; r += nwarps) gp_plan(s_tab, n, ops[ds + r], &trig[4 * (ds + r)], spl[r]);
                 __syncthreads();
             }
             gp_pmark(w, pset, 4);
@@ -1004,14 +1006,17 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             if (o.kind == SF_OP_COND) ok &= o.arg <= 8;
             else ok &= k <= 8 || (k >= SF_OP_DIAG && k <= SF_OP_DIAG + 3) || k == SF_OP_MEASURE;
             bad |= !ok;
-            // e^{i theta} of every diagonal record, computed once here, spread over
-            // the grid (the double-precision pipe of one SM is narrow)
+            // the term coefficients of every diagonal record (from e^{i theta}),
+            // computed once here, spread over the grid (the double-precision
+            // pipe of one SM is narrow, and the plans are the planner's pace)
             if (ok && o.kind >= SF_OP_DIAG && o.kind <= SF_OP_DIAG + 3) {
                 const uint32_t kd = o.kind - SF_OP_DIAG;
                 const double th = kd == 0 ? 0.78539816339744830962 : (kd == 1 ? -0.78539816339744830962 : o.param);
                 double sn, cs;
                 sincos(th, &sn, &cs);
-                trig[i] = make_double2(cs, sn);
+                const SfTerms Tm = diag_terms(kd, cs, sn);
+#pragma unroll
+                for (int j = 0; j < 4; j++) trig[4 * i + j] = Tm.c[j];
             }
         }
         if (__syncthreads_or(bad) && threadIdx.x == 0) {
@@ -1319,7 +1324,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             }
             const int np = diag_count(ops, oe, n_ops);
             for (int r = warp; r < np; r += (int)(blockDim.x >> 5))
-                gp_plan(s_tab, n, ops[oe + r], __ldcg(&trig[oe + r]), spl[r]);
+                gp_plan(s_tab, n, ops[oe + r], &trig[4 * (oe + r)], spl[r]);
             __syncthreads();
             gp_mark(w, 2);
             npre = (unsigned)np;
@@ -1342,7 +1347,7 @@ __global__ void __launch_bounds__(kGpThreads) k_gprog(SfDev d, GpWork* w, const 
             } else {  // the one CTA plans it, one warp per record
                 nb = diag_count(ops, oi, n_ops);
                 for (int r = warp; r < nb; r += (int)(blockDim.x >> 5))
-                    gp_plan(s_tab, n, ops[oi + r], __ldcg(&trig[oi + r]), spl[r]);
+                    gp_plan(s_tab, n, ops[oi + r], &trig[4 * (oi + r)], spl[r]);
                 __syncthreads();
             }
         }
